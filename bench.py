@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark: exact lineal path function of a 512x512 periodic two-phase image.
+
+Workload (one step): the full lineal path function of both phases over every
+vector |dx|, |dy| <= 256 of a seeded synthetic 512x512 image of overlapping
+ellipses (semi-axes 6-20 px, uniform orientation, phase-1 fraction 0.35),
+int64 counts.  One step = pack the image, walk the prefix tree of all
+canonical segments, fill the mirrored half; the path tables are built once
+before timing (the paper likewise excludes its setup).
+
+Metric: pixel-segment tests per second = 2 phases * W*H start pixels *
+(2*256+1)^2 vectors per step / step time (output-equivalent, like the
+paper's full-domain timings).
+
+Prints one JSON line.  Under torchrun every rank runs an independent replica
+(the method needs no exchange between GPUs) and rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 512
+RX = RY = 256
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+ALU_LANES_PER_SM = 64       # LOP3/SHF issue: 16 lanes per SM sub-partition per clock
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def _source_sha(path: str) -> str:
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def _traffic_record():
+    """DRAM bytes per launch of the walk kernel from a committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    f = os.path.join(ROOT, "profiles", "walk_kernel_512_traffic.json")
+    try:
+        rec = json.load(open(f))
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_1601_04359_gb300", "csrc", "lpf_full.cu")
+    if rec.get("source_sha") != _source_sha(src):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def cpu_baseline_sample(img, seconds: float = 12.0, seed: int = 0):
+    """The oracle (plain C, Alg. 1, OpenMP over vectors) on a bounded random
+    sample of the window's vectors; returns tests/s and the sample size."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(seed)
+    vecs = np.stack([rng.integers(-RX, RX + 1, 100000), rng.integers(-RY, RY + 1, 100000)], axis=1)
+    done = 0
+    t0 = time.perf_counter()
+    chunk = 4 * max(1, oracle.num_threads())
+    while time.perf_counter() - t0 < seconds and done < len(vecs):
+        oracle.count_list(img, vecs[done:done + chunk])
+        done += chunk
+    dt = time.perf_counter() - t0
+    tests = 2 * H * W * done
+    return tests / dt, done, dt
+
+
+def run_reference(args, ws, rank):
+    """The oracle arm: times the plain CPU oracle on the same workload and metric."""
+    if rank != 0:
+        return
+    import synth
+    import oracle
+    img = synth.config2_image()
+    per_step = max(1.0, 30.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline_sample(img, seconds=min(per_step, 2.0))
+    total_tests = 0.0
+    total_t = 0.0
+    n_vec = 0
+    for k in range(args.steps):
+        v, n, dt = cpu_baseline_sample(img, seconds=per_step, seed=k + 1)
+        total_tests += 2 * H * W * n
+        total_t += dt
+        n_vec += n
+    value = total_tests / total_t
+    line = {
+        "impl": "reference", "metric": "LPF pixel-segment tests/s at 512^2", "value": value, "unit": "tests/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "lpf_full 512x512 ellipses f=0.35 |dx|,|dy|<=256, both phases", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "tests/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{n_vec} random vectors of the 512x512 window over {args.steps} steps "
+                                   f"(each step a bounded sample of ~{per_step:.1f} s)"},
+        "e2e": {"value": value, "unit": "tests/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1601_04359_gb300 as lpf
+    import synth
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    lpf.load()
+
+    img = synth.config2_image()
+    paths = lpf.lpf_build_paths(RX, RY)
+    stats = lpf.lpf_paths_stats(paths)
+    d_img = torch.from_numpy(img).cuda()
+    counts = torch.empty((2, paths.n_full), dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        lpf.lpf_full(d_img, paths, counts)
+    torch.cuda.synchronize()
+    assert lpf.lpf_paths_status(paths) == 0
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in kev:  # create the underlying events before handing them to the library
+        a.record(); b.record()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.fill_(k & 255)                       # evict L2 between timed iterations
+        lpf.lpf_paths_set_timer(paths, kev[k][0], kev[k][1])
+        ev[k][0].record(stream)
+        lpf.lpf_full(d_img, paths, counts)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    clocks = sampler.stop()
+    lpf.lpf_paths_set_timer(paths, None, None)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / K
+    walk_ms = sum(a.elapsed_time(b) for a, b in kev) / K
+    step_ms_max = _max_over_ranks(ws, step_ms)
+    assert lpf.lpf_paths_status(paths) == 0
+
+    tests_per_step = 2 * H * W * paths.n_full
+    value = ws * tests_per_step / (step_ms_max / 1000.0)
+
+    # end to end through the public API from pinned host buffers
+    h_img = torch.from_numpy(img).pin_memory()
+    h_counts = torch.empty((2, paths.n_full), dtype=torch.int64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for k in range(K):
+        flush.fill_(k & 255)
+        e0.record(stream)
+        d_img.copy_(h_img, non_blocking=True)
+        lpf.lpf_full(d_img, paths, counts)
+        h_counts.copy_(counts, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms /= K
+    e2e_ms = _max_over_ranks(ws, e2e_ms)
+    ref_counts = counts.cpu()
+    assert torch.equal(h_counts, ref_counts)
+
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    words = H * ((W + 31) // 32)
+    alu_ops = 2.0 * stats["n_tree_nodes"] * words  # 1 funnel shift + 1 LOP3 per (tree node, word)
+    achieved = alu_ops / (walk_ms / 1000.0)
+    peak = n_sm * ALU_LANES_PER_SM * sm_max * 1e6
+    traffic = _traffic_record()
+
+    line = {
+        "metric": "LPF pixel-segment tests/s at 512^2",
+        "value": value,
+        "unit": "tests/s",
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": step_ms_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": "lpf_full 512x512 ellipses f=0.35 |dx|,|dy|<=256, both phases, int64 counts",
+                   "tests_per_step": tests_per_step, "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "ALU op/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "walk_kernel", "kernel_ms": walk_ms,
+                     "peak_basis": f"{n_sm} SMs x {ALU_LANES_PER_SM} LOP3/SHF lanes/clk x {sm_max:.0f} MHz (max clock)",
+                     "work_basis": f"{stats['n_tree_nodes']} prefix-tree nodes x {words} translation words x 2 ops"},
+        "e2e": {"value": ws * tests_per_step / (e2e_ms / 1000.0), "unit": "tests/s",
+                "h2d_bytes_per_step": int(img.nbytes), "d2h_bytes_per_step": int(2 * paths.n_full * 8)},
+        "gpu_launches": 3 * K,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, n, dt = cpu_baseline_sample(img)
+        import oracle
+        line["cpu_baseline"] = {"value": v, "unit": "tests/s", "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": f"{n} random vectors of the 512x512 window, both phases, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,152 @@
+/*
+ * liblpf -- exact lineal path function of periodic two-phase 2D images on
+ * NVIDIA GB300 (sm_103a), after Havelka, Kucerova & Sykora, "Compression and
+ * Reconstruction of Random Microstructures using Accelerated Lineal Path
+ * Function" (arXiv:1601.04359).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Image     uint8, H rows x W columns, row-major: pixel (x, y) is img[y*W + x]
+ *            (x = column, y = row).  Values must be 0 or 1; "phase p" is the
+ *            set of pixels with value p.  The medium is periodic: coordinates
+ *            wrap modulo W and H (the "%" convention of Eq. (S2dis), Sec. 2.1).
+ *  Vectors   v = (dx, dy), dx a column offset, dy a row offset, in the window
+ *            |dx| <= rx, |dy| <= ry with 0 <= rx < W and 0 <= ry < H.  The
+ *            paper's full domain is rx = W-1, ry = H-1 (Eq. (segments), Sec. 2.2).
+ *  Segment   S(v): the Bresenham pixels from (0,0) to v (Sec. 2.2).  For v in
+ *            the half-domain D (dy > 0, or dy == 0 and dx >= 0) step i = 0..a,
+ *            a = max(|dx|,|dy|), moves i along the major axis and round(i*b/a)
+ *            along the minor one (b = min(|dx|,|dy|)), an exact half rounding
+ *            away from the start; outside D, S(v) = v + S(-v) (the same pixels
+ *            seen from the other end), so L(v) = L(-v) exactly (Eq. (symmetry)).
+ *  Count     count_p(v) = #{x : img[(x + s) mod (W,H)] == p for all s in S(v)};
+ *            the lineal path function is L_p(v) = count_p(v) / (W*H)
+ *            (Sec. 2.2 definition; Alg. 1 of Sec. 3.1).
+ *  Layouts   full:      [2][(2ry+1)(2rx+1)], entry (dy+ry)*(2rx+1) + (dx+rx),
+ *                       phase 0 first.
+ *            canonical: [n_canon] with n_canon = ry*(2rx+1) + rx + 1; the
+ *                       canonical entries are the tail of the full layout that
+ *                       starts at v = (0,0): canonical index = full index - base,
+ *                       base = (n_full - 1) / 2.
+ *  Memory    "_dev" pointers are device memory owned by the caller; "_host"
+ *            pointers are host memory owned by the caller.  Device calls are
+ *            asynchronous on the given stream (a cudaStream_t; NULL = legacy
+ *            default stream) and return once the work is enqueued.
+ *  Errors    every int-returning call returns LPF_OK (0) or a negative code;
+ *            arguments are validated on the host before anything is enqueued,
+ *            and on error nothing is enqueued.  lpf_strerror() names a code.
+ *  Threads   a paths handle is not thread-safe: calls that use one handle must
+ *            be issued from one host thread and ordered on one stream (the
+ *            handle keeps device tables and a work area that calls reuse).
+ */
+#ifndef LPF_H
+#define LPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LPF_OK 0
+#define LPF_EINVAL (-1)      /* bad argument: size, window, pointer, count */
+#define LPF_ENOMEM (-2)      /* host or device allocation failed */
+#define LPF_ECUDA (-3)       /* a CUDA runtime call failed (no device, launch error) */
+#define LPF_ETIMEOUT (-4)    /* a device-side bounded wait gave up (see lpf_paths_status) */
+#define LPF_EUNSUPPORTED (-5) /* size beyond what this build supports */
+
+typedef struct CUstream_st *lpf_stream_t; /* same type as cudaStream_t */
+typedef struct lpf_paths lpf_paths;        /* opaque, owned by the library */
+
+/* Name of a status code (static string). */
+const char *lpf_strerror(int code);
+
+/*
+ * Build the discretised segments of every vector of the window |dx| <= rx,
+ * |dy| <= ry (Sec. 2.2 segments; Sec. 3.1 step 1, done once) and the
+ * evaluation program that shares the work of common segment prefixes (the
+ * enhanced evaluation of Sec. 3.2, generalised to all shared prefixes).
+ * Host-only; touches no GPU.  rx, ry in [0, 4095].  *out receives a handle
+ * to release with lpf_paths_free().  Device tables are uploaded lazily by the
+ * first device call that uses the handle (see lpf_full).
+ * Errors: LPF_EINVAL (radius out of range, out == NULL), LPF_ENOMEM.
+ */
+int lpf_build_paths(int32_t rx, int32_t ry, lpf_paths **out);
+
+/*
+ * Sizes of a handle's tables: n_vec_full = (2rx+1)(2ry+1), n_vec_canon =
+ * canonical vectors, n_offsets = total pixels of the canonical segments.
+ * Any output pointer may be NULL.  Errors: LPF_EINVAL (paths == NULL).
+ */
+int lpf_paths_info(const lpf_paths *paths, int64_t *n_vec_full, int64_t *n_vec_canon,
+                   int64_t *n_offsets);
+
+/*
+ * Copy the canonical segments into caller-sized host arrays (CSR form):
+ * vec_dxdy_host [n_vec_canon][2] (dx, dy) in canonical order,
+ * ptr_host [n_vec_canon + 1] (segment c is offsets ptr[c] .. ptr[c+1]-1),
+ * off_dxdy_host [n_offsets][2] (sx, sy) pixel offsets from the start pixel,
+ * start pixel first.  Any output pointer may be NULL.
+ * Errors: LPF_EINVAL (paths == NULL).
+ */
+int lpf_paths_export(const lpf_paths *paths, int16_t *vec_dxdy_host, int64_t *ptr_host,
+                     int16_t *off_dxdy_host);
+
+/*
+ * Work statistics: n_tree_nodes = pixels the prefix-sharing program visits
+ * per translation word, stack_depth = masks it keeps at once, n_pieces =
+ * independent program pieces the kernels spread over thread blocks.
+ * Any output pointer may be NULL.
+ */
+int lpf_paths_stats(const lpf_paths *paths, int64_t *n_tree_nodes, int32_t *stack_depth,
+                    int32_t *n_pieces);
+
+/* Release a handle and its device memory (NULL is ignored).  Synchronises
+ * the device before freeing device tables. */
+void lpf_paths_free(lpf_paths *paths);
+
+/*
+ * Full lineal path counts of both phases for every vector of the handle's
+ * window (Sec. 2.2; Alg. 1/Alg. 2 of Sec. 3.1 with the prefix sharing of
+ * Sec. 3.2).  img_dev: H*W uint8 (0/1), counts_dev: int64 full layout
+ * [2][n_vec_full], overwritten.  Vectors outside D are filled by the point
+ * symmetry of Eq. (symmetry).
+ * Requires rx < W, ry < H, 1 <= H, W <= 8192.  The first call with a new
+ * image width uploads the handle's program for that width and may allocate
+ * the handle's device work area (make that first call before any stream
+ * capture); later calls with the same or smaller sizes allocate nothing.
+ * Errors: LPF_EINVAL, LPF_EUNSUPPORTED (image band too large for shared
+ * memory), LPF_ENOMEM, LPF_ECUDA.
+ */
+int lpf_full(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
+             int64_t *counts_dev, lpf_stream_t stream);
+
+/*
+ * Same as lpf_full but evaluates every segment from scratch, one vector after
+ * another (the "standard" evaluation of Sec. 3.2, i.e. Alg. 1 order without
+ * any shared work).  Same arguments, layout and errors; for comparison runs.
+ */
+int lpf_full_standard(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
+                      int64_t *counts_dev, lpf_stream_t stream);
+
+/*
+ * Measurement hook: when ev_start/ev_stop (cudaEvent_t, created by the
+ * caller) are non-NULL, every later device call on this handle records
+ * ev_start on its stream right before its dominant kernel and ev_stop right
+ * after it, so a caller can time that kernel alone.  NULL, NULL turns it off.
+ * The events stay owned by the caller.  Errors: LPF_EINVAL (paths == NULL).
+ */
+int lpf_paths_set_timer(lpf_paths *paths, void *ev_start, void *ev_stop);
+
+/*
+ * Device-side status of the handle's last calls: synchronises `stream`,
+ * returns LPF_ETIMEOUT if a bounded wait inside a kernel gave up since the
+ * last check (and clears the flag), LPF_OK otherwise.
+ */
+int lpf_paths_status(lpf_paths *paths, lpf_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LPF_H */

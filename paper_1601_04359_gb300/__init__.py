@@ -1,0 +1,170 @@
+"""Python binding of liblpf, the GB300 (sm_103a) lineal-path-function library.
+
+Every function here marshals arguments to the C ABI declared in
+``include/lpf.h`` and returns; all computation runs in the library's CUDA
+kernels.  PyTorch is used only to own device memory and to name streams.
+There is no CPU fallback: if the library cannot be loaded or a call fails,
+an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "load", "LpfError", "Paths", "lpf_build_paths", "lpf_paths_info", "lpf_paths_export",
+    "lpf_paths_stats", "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer",
+    "lpf_strerror",
+]
+
+_lib = None
+LIB_PATH = _build.LIB
+
+
+class LpfError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {lpf_strerror(code)} ({code})")
+        self.code = code
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load liblpf.so (building it in-tree first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblpf not built: {path}")
+    lib = ctypes.CDLL(path)
+    i32, i64, p = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    sig = {
+        "lpf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "lpf_build_paths": (ctypes.c_int, [i32, i32, ctypes.POINTER(p)]),
+        "lpf_paths_info": (ctypes.c_int, [p, P64, P64, P64]),
+        "lpf_paths_export": (ctypes.c_int, [p, p, p, p]),
+        "lpf_paths_stats": (ctypes.c_int, [p, P64, P32, P32]),
+        "lpf_paths_free": (None, [p]),
+        "lpf_full": (ctypes.c_int, [p, i32, i32, p, p, p]),
+        "lpf_full_standard": (ctypes.c_int, [p, i32, i32, p, p, p]),
+        "lpf_paths_status": (ctypes.c_int, [p, p]),
+        "lpf_paths_set_timer": (ctypes.c_int, [p, p, p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def lpf_strerror(code: int) -> str:
+    return load().lpf_strerror(int(code)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise LpfError(rc, what)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev_ptr(t, dtype_name: str, what: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"{what} must be {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return t.data_ptr()
+
+
+class Paths:
+    """Owning wrapper of an ``lpf_paths*`` handle (freed on garbage collection)."""
+
+    def __init__(self, handle: int, rx: int, ry: int):
+        self.handle = handle
+        self.rx, self.ry = rx, ry
+        self.n_full, self.n_canon, self.n_offsets = lpf_paths_info(self)
+        self.base = (self.n_full - 1) // 2
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.lpf_paths_free(h)
+            self.handle = None
+
+
+def lpf_build_paths(rx: int, ry: int) -> Paths:
+    h = ctypes.c_void_p()
+    _check(load().lpf_build_paths(int(rx), int(ry), ctypes.byref(h)), "lpf_build_paths")
+    return Paths(h.value, int(rx), int(ry))
+
+
+def lpf_paths_info(paths: Paths):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().lpf_paths_info(paths.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "lpf_paths_info")
+    return a.value, b.value, c.value
+
+
+def lpf_paths_export(paths: Paths):
+    """(vec [n_canon][2] int16, ptr [n_canon+1] int64, off [n_offsets][2] int16)."""
+    vec = np.zeros((paths.n_canon, 2), np.int16)
+    ptr = np.zeros(paths.n_canon + 1, np.int64)
+    off = np.zeros((paths.n_offsets, 2), np.int16)
+    _check(load().lpf_paths_export(paths.handle, vec.ctypes.data, ptr.ctypes.data, off.ctypes.data),
+           "lpf_paths_export")
+    return vec, ptr, off
+
+
+def lpf_paths_stats(paths: Paths):
+    a, b, c = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().lpf_paths_stats(paths.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "lpf_paths_stats")
+    return {"n_tree_nodes": a.value, "stack_depth": b.value, "n_pieces": c.value}
+
+
+def lpf_full(img, paths: Paths, counts=None, stream=None):
+    """Counts of both phases for every vector: int64 CUDA tensor [2][n_full]."""
+    import torch
+    H, W = img.shape
+    if counts is None:
+        counts = torch.empty((2, paths.n_full), dtype=torch.int64, device=img.device)
+    _check(load().lpf_full(_dev_ptr(img, "uint8", "img"), H, W, paths.handle,
+                           _dev_ptr(counts, "int64", "counts"), _stream_ptr(stream)), "lpf_full")
+    return counts
+
+
+def lpf_full_standard(img, paths: Paths, counts=None, stream=None):
+    import torch
+    H, W = img.shape
+    if counts is None:
+        counts = torch.empty((2, paths.n_full), dtype=torch.int64, device=img.device)
+    _check(load().lpf_full_standard(_dev_ptr(img, "uint8", "img"), H, W, paths.handle,
+                                    _dev_ptr(counts, "int64", "counts"), _stream_ptr(stream)),
+           "lpf_full_standard")
+    return counts
+
+
+def lpf_paths_set_timer(paths: Paths, ev_start=None, ev_stop=None):
+    """Record torch.cuda.Event pair around the dominant kernel of later calls."""
+    a = ev_start.cuda_event if ev_start is not None else None
+    b = ev_stop.cuda_event if ev_stop is not None else None
+    _check(load().lpf_paths_set_timer(paths.handle, a, b), "lpf_paths_set_timer")
+
+
+def lpf_paths_status(paths: Paths, stream=None) -> int:
+    return int(load().lpf_paths_status(paths.handle, _stream_ptr(stream)))

@@ -1,0 +1,438 @@
+// Full lineal path function of a periodic two-phase image (Sec. 2.2, Alg. 1
+// and Alg. 2 of Sec. 3.1, prefix sharing after Sec. 3.2), bit-parallel.
+//
+// Layout.  Phase-1 pixels are bit-packed along rows (bit = 1 for phase 1),
+// each row periodically extended so that any column offset in [-rx, rx] is a
+// plain funnel shift of two adjacent words, and the rows periodically
+// extended downwards by ry so that canonical row offsets (0 <= sy <= ry) never
+// wrap.  A 32-bit word of a mask holds 32 consecutive translations x of one
+// row; one funnel-shifted image word serves both phases (the phase-0 mask
+// ANDs its complement).
+//
+// Work split.  A block owns one band of 32 translation rows (lane = row, so
+// the 32 lanes of a warp read 32 different rows: an odd row stride in words
+// puts them in 32 different shared-memory banks) and all words of the row
+// (warp g owns words g*T .. g*T+T-1).  The band's image rows are staged in
+// shared memory with one TMA bulk copy.  Every warp then runs one piece of
+// the evaluation program: a depth-first walk of the prefix tree of all
+// canonical segments, ANDing one shifted image word per tree node and
+// counting (popc + warp sum + one atomic per phase) where a node ends a
+// canonical vector.  Masks of branching nodes are kept on a per-thread stack.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "lpf_device.cuh"
+#include "lpf_state.hpp"
+
+namespace lpf {
+
+constexpr int kDevStack = 24;   // deepest prefix-tree stack the kernels hold
+constexpr int kMaxSmem = 227 * 1024;
+
+int make_geometry(int H, int W, int rx, int ry, int T, Geometry& g) {
+  g.H = H; g.W = W; g.rx = rx; g.ry = ry;
+  g.nw = (W + 31) / 32;
+  if (T <= 0) T = g.nw >= 4 ? 4 : (g.nw >= 2 ? 2 : 1);
+  while ((g.nw + T - 1) / T > 32 && T < 8) T *= 2;  // at most 1024 threads per block
+  g.T = T;
+  g.G = (g.nw + T - 1) / T;
+  g.r32 = ((rx + 31) / 32) * 32;
+  const int nwp = g.G * T;
+  g.S = nwp + ((g.r32 + rx) >> 5) + 1;
+  if ((g.S & 1) == 0) g.S += 1;
+  g.nbands = (H + 31) / 32;
+  g.rows = 32 * g.nbands + ry;
+  const size_t band = (size_t)(32 + ry) * g.S * 4;
+  g.band_bytes = (uint32_t)((band + 15) & ~size_t(15));
+  g.packed_words = (size_t)g.rows * g.S + 4;
+  if (g.G > 32 || band > (size_t)kMaxSmem - 64) return LPF_EUNSUPPORTED;
+  return LPF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+
+// packed[y][k]: bit b is the pixel at row y mod H, column (32k + b - r32) mod W.
+__global__ void pack_rows_kernel(const uint8_t* __restrict__ img, int H, int W, int r32, int S, int rows,
+                                 uint32_t* __restrict__ packed) {
+  const int64_t total = (int64_t)rows * S;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(i / S), k = (int)(i % S);
+    const uint8_t* row = img + (int64_t)(y % H) * W;
+    int x = (32 * k - r32) % W;
+    if (x < 0) x += W;
+    uint32_t bits = 0;
+#pragma unroll 4
+    for (int b = 0; b < 32; ++b) {
+      bits |= (uint32_t)(row[x] != 0) << b;
+      if (++x == W) x = 0;
+    }
+    packed[i] = bits;
+  }
+}
+
+// counts[p][n_full-1-i] = counts[p][i] for the canonical entries i > base
+// (Eq. (symmetry): the segment of -v is the segment of v).
+__global__ void mirror_kernel(unsigned long long* __restrict__ counts, int64_t n_full, int64_t base) {
+  const int64_t n = n_full - base - 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i / n, j = base + 1 + i % n;
+    counts[p * n_full + (n_full - 1 - j)] = counts[p * n_full + j];
+  }
+}
+
+template <int T>
+__global__ void __launch_bounds__(1024) walk_kernel(const uint32_t* __restrict__ packed, int H, int W, int S,
+                                                   int ry, int nw, uint32_t band_bytes,
+                                                   const uint32_t* __restrict__ prog,
+                                                   const int64_t* __restrict__ piece,
+                                                   unsigned long long* __restrict__ counts, int64_t n_full,
+                                                   int64_t base, int* __restrict__ status) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ __align__(8) uint64_t bar;
+  const int band = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, band_bytes);
+    bulk_g2s(sm, packed + (size_t)band * 32 * S, band_bytes, &bar);
+  }
+  if (!mbar_wait(&bar, 0)) {
+    atomicOr(status, 1);
+    return;
+  }
+
+  const int y = band * 32 + lane;
+  uint32_t valid[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int j = warp * T + t;
+    uint32_t v = 0;
+    if (y < H && j < nw) {
+      const int rem = W - 32 * j;
+      v = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    }
+    valid[t] = v;
+  }
+  const uint32_t* lane_base = sm + lane * S + warp * T;
+
+  uint32_t m1[T], m0[T];
+  uint32_t st1[kDevStack][T], st0[kDevStack][T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
+
+  int64_t pc = piece[blockIdx.y];
+  const int64_t end = piece[blockIdx.y + 1];
+  while (pc < end) {
+    const uint32_t hdr = __ldg(prog + pc++);
+    if (hdr & kReset) {
+#pragma unroll
+      for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
+    }
+    if (hdr & kRestore) {
+      const int l = (hdr >> kRlevelShift) & kLevelMask;
+#pragma unroll
+      for (int t = 0; t < T; ++t) { m1[t] = st1[l][t]; m0[t] = st0[l][t]; }
+    }
+    int vec = -1;
+    if (hdr & kEmit) vec = (int)__ldg(prog + pc++);
+    const int n = (int)(hdr & kNpixMask);
+    const uint32_t* pp = prog + pc;
+    pc += n;
+    int i = 0;
+    for (; i + 1 < n; i += 2) {
+      const uint32_t pa = __ldg(pp + i), pb = __ldg(pp + i + 1);
+      const uint32_t* sa = lane_base + (pa >> 5);
+      const uint32_t* sb = lane_base + (pb >> 5);
+      uint32_t wa[T + 1], wb[T + 1];
+#pragma unroll
+      for (int t = 0; t <= T; ++t) { wa[t] = sa[t]; wb[t] = sb[t]; }
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], pa);
+        const uint32_t b = __funnelshift_r(wb[t], wb[t + 1], pb);
+        m1[t] &= a & b;
+        m0[t] &= ~(a | b);
+      }
+    }
+    if (i < n) {
+      const uint32_t pa = __ldg(pp + i);
+      const uint32_t* sa = lane_base + (pa >> 5);
+      uint32_t wa[T + 1];
+#pragma unroll
+      for (int t = 0; t <= T; ++t) wa[t] = sa[t];
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], pa);
+        m1[t] &= a;
+        m0[t] &= ~a;
+      }
+    }
+    if (vec >= 0) {
+      uint32_t c = 0;
+#pragma unroll
+      for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
+      c = warp_sum(c);
+      if (lane == 0) {
+        const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
+        if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);
+        if (c1) atomicAdd(counts + n_full + base + vec, (unsigned long long)c1);
+      }
+    }
+    if (hdr & kPush) {
+      const int l = (hdr >> kPlevelShift) & kLevelMask;
+#pragma unroll
+      for (int t = 0; t < T; ++t) { st1[l][t] = m1[t]; st0[l][t] = m0[t]; }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+
+static int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return LPF_OK;
+  if (e == cudaErrorMemoryAllocation) return LPF_ENOMEM;
+  return LPF_ECUDA;
+}
+
+int ensure_device(lpf_paths* p, size_t packed_words) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LPF_ECUDA;
+  if (p->device < 0) {
+    p->device = dev;
+  } else if (p->device != dev) {
+    return LPF_EINVAL;  // handle is bound to another device
+  }
+  if (!p->d_status) {
+    if (cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess) return LPF_ENOMEM;
+    if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return LPF_ECUDA;
+  }
+  if (packed_words > p->packed_cap) {
+    if (p->d_packed) {
+      cudaDeviceSynchronize();
+      cudaFree(p->d_packed);
+      p->d_packed = nullptr;
+      p->packed_cap = 0;
+    }
+    if (cudaMalloc(&p->d_packed, packed_words * 4) != cudaSuccess) return LPF_ENOMEM;
+    p->packed_cap = packed_words;
+  }
+  return LPF_OK;
+}
+
+int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
+  if (b.d_words && b.W == g.W && b.S == g.S && b.r32 == g.r32) return LPF_OK;
+  if (b.d_words) {
+    cudaDeviceSynchronize();
+    cudaFree(b.d_words);
+    cudaFree(b.d_piece);
+    b.d_words = nullptr;
+    b.d_piece = nullptr;
+  }
+  const std::vector<uint32_t>& w = prog.words;
+  std::vector<uint32_t> out(w.size());
+  const std::vector<int16_t>& np = p->host.node_pix;
+  for (size_t i = 0; i < w.size();) {
+    const uint32_t h = w[i];
+    out[i++] = h;
+    if (h & kEmit) { out[i] = w[i]; ++i; }
+    const uint32_t n = h & kNpixMask;
+    for (uint32_t k = 0; k < n; ++k, ++i) {
+      const int node = (int)w[i];
+      const int sx = np[2 * node], sy = np[2 * node + 1];
+      const int sxp = sx + g.r32;              // >= 0
+      const uint32_t off = (uint32_t)(sy * g.S + (sxp >> 5));
+      out[i] = (off << 5) | (uint32_t)(sxp & 31);
+    }
+  }
+  if (cudaMalloc(&b.d_words, out.size() * 4) != cudaSuccess) return LPF_ENOMEM;
+  if (cudaMalloc(&b.d_piece, prog.piece_begin.size() * 8) != cudaSuccess) return LPF_ENOMEM;
+  if (cudaMemcpy(b.d_words, out.data(), out.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return LPF_ECUDA;
+  if (cudaMemcpy(b.d_piece, prog.piece_begin.data(), prog.piece_begin.size() * 8, cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return LPF_ECUDA;
+  b.W = g.W;
+  b.S = g.S;
+  b.r32 = g.r32;
+  b.n_pieces = (int)prog.piece_begin.size() - 1;
+  return LPF_OK;
+}
+
+static std::once_flag g_attr_once;
+static void set_kernel_attributes() {
+  cudaFuncSetAttribute(walk_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+  cudaFuncSetAttribute(walk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+  cudaFuncSetAttribute(walk_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+  cudaFuncSetAttribute(walk_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+}
+
+static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* counts, cudaStream_t s,
+                    bool standard) {
+  if (!p || !img || !counts) return LPF_EINVAL;
+  if (H < 1 || W < 1 || H > 8192 || W > 8192) return LPF_EINVAL;
+  if (p->host.rx >= W || p->host.ry >= H) return LPF_EINVAL;
+  const Program& prog = standard ? p->host.plain : p->host.tree;
+  if (prog.stack_depth > kDevStack) return LPF_EUNSUPPORTED;
+  Geometry g;
+  int rc = make_geometry(H, W, p->host.rx, p->host.ry, 0, g);
+  if (rc) return rc;
+  rc = ensure_device(p, g.packed_words);
+  if (rc) return rc;
+  Baked& b = standard ? p->plain : p->tree;
+  rc = bake(p, prog, g, b);
+  if (rc) return rc;
+  std::call_once(g_attr_once, set_kernel_attributes);
+
+  const int64_t n_full = p->host.n_full, base = p->host.base;
+  if (cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * n_full, s) != cudaSuccess) return LPF_ECUDA;
+  {
+    const int64_t total = (int64_t)g.rows * g.S;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    pack_rows_kernel<<<blocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, p->d_packed);
+  }
+  {
+    dim3 grid(g.nbands, b.n_pieces);
+    dim3 block(32 * g.G);
+    unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
+    if (p->ev_start) cudaEventRecord(p->ev_start, s);
+    switch (g.T) {
+      case 1: walk_kernel<1><<<grid, block, g.band_bytes, s>>>(p->d_packed, H, W, g.S, g.ry, g.nw, g.band_bytes, b.d_words, b.d_piece, c, n_full, base, p->d_status); break;
+      case 2: walk_kernel<2><<<grid, block, g.band_bytes, s>>>(p->d_packed, H, W, g.S, g.ry, g.nw, g.band_bytes, b.d_words, b.d_piece, c, n_full, base, p->d_status); break;
+      case 4: walk_kernel<4><<<grid, block, g.band_bytes, s>>>(p->d_packed, H, W, g.S, g.ry, g.nw, g.band_bytes, b.d_words, b.d_piece, c, n_full, base, p->d_status); break;
+      default: walk_kernel<8><<<grid, block, g.band_bytes, s>>>(p->d_packed, H, W, g.S, g.ry, g.nw, g.band_bytes, b.d_words, b.d_piece, c, n_full, base, p->d_status); break;
+    }
+    if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
+  }
+  if (n_full > 1) {
+    const int64_t n = 2 * (n_full - base - 1);
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    mirror_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<unsigned long long*>(counts), n_full, base);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace lpf
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+const char* lpf_strerror(int code) {
+  switch (code) {
+    case LPF_OK: return "ok";
+    case LPF_EINVAL: return "invalid argument";
+    case LPF_ENOMEM: return "out of memory";
+    case LPF_ECUDA: return "CUDA runtime error";
+    case LPF_ETIMEOUT: return "device-side wait timed out";
+    case LPF_EUNSUPPORTED: return "size not supported";
+    default: return "unknown status";
+  }
+}
+
+int lpf_build_paths(int32_t rx, int32_t ry, lpf_paths** out) {
+  if (!out) return LPF_EINVAL;
+  *out = nullptr;
+  if (rx < 0 || ry < 0 || rx > 4095 || ry > 4095) return LPF_EINVAL;
+  lpf_paths* p = new (std::nothrow) lpf_paths();
+  if (!p) return LPF_ENOMEM;
+  std::string err;
+  // Enough pieces for ~8 waves of blocks over 152 SMs on large windows,
+  // fewer on small ones (each piece repeats a prologue of one segment).
+  const int64_t n_canon = (int64_t)ry * (2 * rx + 1) + rx + 1;
+  const int pieces = (int)std::max<int64_t>(1, std::min<int64_t>(256, n_canon / 256));
+  int rc;
+  try {
+    rc = lpf::build_paths(rx, ry, pieces, p->host, err);
+  } catch (const std::bad_alloc&) {
+    rc = LPF_ENOMEM;
+  }
+  if (rc != 0) {
+    delete p;
+    return rc == LPF_ENOMEM ? LPF_ENOMEM : LPF_EUNSUPPORTED;
+  }
+  *out = p;
+  return LPF_OK;
+}
+
+int lpf_paths_info(const lpf_paths* p, int64_t* n_full, int64_t* n_canon, int64_t* n_off) {
+  if (!p) return LPF_EINVAL;
+  if (n_full) *n_full = p->host.n_full;
+  if (n_canon) *n_canon = p->host.n_canon;
+  if (n_off) *n_off = p->host.ptr.back();
+  return LPF_OK;
+}
+
+int lpf_paths_export(const lpf_paths* p, int16_t* vec, int64_t* ptr, int16_t* off) {
+  if (!p) return LPF_EINVAL;
+  if (vec) std::memcpy(vec, p->host.vec.data(), p->host.vec.size() * sizeof(int16_t));
+  if (ptr) std::memcpy(ptr, p->host.ptr.data(), p->host.ptr.size() * sizeof(int64_t));
+  if (off) std::memcpy(off, p->host.off.data(), p->host.off.size() * sizeof(int16_t));
+  return LPF_OK;
+}
+
+int lpf_paths_stats(const lpf_paths* p, int64_t* n_tree_nodes, int32_t* stack_depth, int32_t* n_pieces) {
+  if (!p) return LPF_EINVAL;
+  if (n_tree_nodes) *n_tree_nodes = p->host.n_nodes();
+  if (stack_depth) *stack_depth = p->host.tree.stack_depth;
+  if (n_pieces) *n_pieces = (int32_t)p->host.tree.piece_pixels.size();
+  return LPF_OK;
+}
+
+void lpf_paths_free(lpf_paths* p) {
+  if (!p) return;
+  if (p->device >= 0) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    cudaFree(p->tree.d_words);
+    cudaFree(p->tree.d_piece);
+    cudaFree(p->plain.d_words);
+    cudaFree(p->plain.d_piece);
+    cudaFree(p->d_packed);
+    cudaFree(p->d_status);
+    if (cur >= 0) cudaSetDevice(cur);
+  }
+  delete p;
+}
+
+int lpf_full(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, int64_t* counts_dev,
+             lpf_stream_t stream) {
+  return lpf::run_full(img_dev, H, W, paths, counts_dev, (cudaStream_t)stream, false);
+}
+
+int lpf_full_standard(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, int64_t* counts_dev,
+                      lpf_stream_t stream) {
+  return lpf::run_full(img_dev, H, W, paths, counts_dev, (cudaStream_t)stream, true);
+}
+
+int lpf_paths_set_timer(lpf_paths* p, void* ev_start, void* ev_stop) {
+  if (!p) return LPF_EINVAL;
+  p->ev_start = (cudaEvent_t)ev_start;
+  p->ev_stop = (cudaEvent_t)ev_stop;
+  return LPF_OK;
+}
+
+int lpf_paths_status(lpf_paths* p, lpf_stream_t stream) {
+  if (!p) return LPF_EINVAL;
+  if (!p->d_status) return LPF_OK;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return LPF_ECUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LPF_ECUDA;
+  if (h) {
+    cudaMemset(p->d_status, 0, sizeof(int));
+    return LPF_ETIMEOUT;
+  }
+  return LPF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,361 @@
+// Host-side construction of the discretised segments and of the evaluation
+// programs (see lpf_paths.hpp).
+#include "lpf_paths.hpp"
+
+#include <algorithm>
+#include <cstdlib>
+
+namespace lpf {
+
+// Bresenham segment in integer error-term form (Sec. 2.2).  For v in the
+// half-domain D, the major axis advances one pixel per step; the minor axis
+// advances when the accumulated error reaches a full pixel.  The error starts
+// at half a step so the minor coordinate is the one nearest the ideal line,
+// and an exact half-way point advances (ties go away from the start pixel).
+void segment_canonical(int dx, int dy, std::vector<int16_t>& out) {
+  const int ax = std::abs(dx), ay = std::abs(dy);
+  const bool xmajor = ax >= ay;
+  const int a = xmajor ? ax : ay;  // steps along the major axis
+  const int b = xmajor ? ay : ax;
+  const int gx = dx < 0 ? -1 : 1, gy = dy < 0 ? -1 : 1;
+  out.clear();
+  int minor = 0;
+  int err = a;  // scaled by 2a: err / (2a) is the fractional minor position + 1/2
+  for (int i = 0; i <= a; ++i) {
+    if (i > 0) {
+      err += 2 * b;
+      if (err >= 2 * a) { err -= 2 * a; ++minor; }
+    }
+    const int px = xmajor ? gx * i : gx * minor;
+    const int py = xmajor ? gy * minor : gy * i;
+    out.push_back((int16_t)px);
+    out.push_back((int16_t)py);
+  }
+}
+
+namespace {
+
+// Child slot of a one-pixel move inside a canonical segment: the move is
+// (mx, my) with my in {0, 1} and mx in {-1, 0, 1}, never (0, 0).
+inline int move_slot(int mx, int my) { return my == 0 ? (mx < 0 ? 0 : 1) : 2 + (mx + 1); }
+
+struct Trie {
+  std::vector<int32_t> parent;
+  std::vector<int16_t> pix;       // [n][2]
+  std::vector<int32_t> vec;
+  std::vector<int32_t> child5;    // [n][5]
+  std::vector<int32_t> depth;
+
+  int32_t add(int32_t par, int16_t x, int16_t y, int32_t d) {
+    const int32_t id = (int32_t)parent.size();
+    parent.push_back(par);
+    pix.push_back(x);
+    pix.push_back(y);
+    vec.push_back(-1);
+    depth.push_back(d);
+    for (int k = 0; k < 5; ++k) child5.push_back(-1);
+    return id;
+  }
+};
+
+struct Event {            // one step of the depth-first walk
+  enum Kind : uint8_t { kRestoreEv, kPixEv, kEmitEv, kPushEv } kind;
+  int32_t a;              // level, node or vector id
+};
+
+struct Walker {
+  const Trie& t;
+  const std::vector<int64_t>& subtree;   // nodes in subtree (work)
+  const std::vector<int32_t>& cstart;    // CSR children, ordered light -> heavy
+  const std::vector<int32_t>& clist;
+  std::vector<Event> ev;
+  int max_level = 0;
+
+  void node(int32_t n, int level) {
+    // Mask of n's parent is current; AND n's pixel, count, then branch.
+    for (;;) {
+      ev.push_back({Event::kPixEv, n});
+      if (t.vec[n] >= 0) ev.push_back({Event::kEmitEv, t.vec[n]});
+      const int32_t c0 = cstart[n], c1 = cstart[n + 1];
+      const int nc = c1 - c0;
+      if (nc == 0) return;
+      if (nc == 1) { n = clist[c0]; continue; }
+      ev.push_back({Event::kPushEv, level});
+      max_level = std::max(max_level, level + 1);
+      for (int i = 0; i < nc; ++i) {
+        if (i > 0) ev.push_back({Event::kRestoreEv, level});
+        if (i < nc - 1) node(clist[c0 + i], level + 1);
+      }
+      // last (heaviest) child reuses this level: tail position
+      n = clist[c1 - 1];
+    }
+  }
+};
+
+}  // namespace
+
+// Turn the event list into records.  At every record start the current node
+// and the live stack entries (levels 0..top-1, all ancestors of the next
+// node) are kept so that the list can be cut into independent pieces.
+static void emit_records(const std::vector<Event>& ev, Program& prog,
+                         std::vector<int64_t>& rec_word, std::vector<int64_t>& rec_pix,
+                         std::vector<int32_t>& rec_cur, std::vector<std::vector<int32_t>>& rec_stack,
+                         std::vector<uint8_t>& rec_restores) {
+  std::vector<uint32_t>& w = prog.words;
+  w.clear();
+  std::vector<int32_t> stack(kMaxStack, -1);
+  int top = 0;
+  int32_t cur = -1;
+  size_t i = 0;
+  int64_t pix_total = 0;
+  std::vector<uint32_t> pixels;
+  while (i < ev.size()) {
+    rec_word.push_back((int64_t)w.size());
+    rec_pix.push_back(pix_total);
+    uint32_t hdr = 0;
+    bool restores = false;
+    if (ev[i].kind == Event::kRestoreEv) {
+      hdr |= kRestore | ((uint32_t)ev[i].a << kRlevelShift);
+      cur = stack[ev[i].a];
+      top = ev[i].a + 1;
+      restores = true;
+      ++i;
+    }
+    rec_cur.push_back(cur);
+    rec_restores.push_back(restores ? 1 : 0);
+    rec_stack.emplace_back(stack.begin(), stack.begin() + top);
+    const size_t hdr_pos = w.size();
+    w.push_back(0);  // header placeholder
+    uint32_t npix = 0;
+    pixels.clear();
+    while (i < ev.size() && ev[i].kind == Event::kPixEv) {
+      pixels.push_back((uint32_t)ev[i].a);  // trie node id until baked
+      cur = ev[i].a;
+      ++npix;
+      ++i;
+    }
+    if (i < ev.size() && ev[i].kind == Event::kEmitEv) {
+      hdr |= kEmit;
+      w.push_back((uint32_t)ev[i].a);
+      ++i;
+    }
+    if (i < ev.size() && ev[i].kind == Event::kPushEv) {
+      hdr |= kPush | ((uint32_t)ev[i].a << kPlevelShift);
+      stack[ev[i].a] = cur;
+      top = ev[i].a + 1;
+      ++i;
+    }
+    hdr |= npix;
+    w[hdr_pos] = hdr;
+    for (uint32_t q : pixels) w.push_back(q);
+    pix_total += npix;
+  }
+  rec_word.push_back((int64_t)w.size());
+  rec_pix.push_back(pix_total);
+}
+
+int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err) {
+  if (rx < 0 || ry < 0 || rx > 4095 || ry > 4095) { err = "window radius out of range [0, 4095]"; return -1; }
+  p = Paths();
+  p.rx = rx;
+  p.ry = ry;
+  p.n_full = (int64_t)(2 * rx + 1) * (2 * ry + 1);
+  p.base = (p.n_full - 1) / 2;
+  p.n_canon = p.n_full - p.base;
+  p.vec.resize(2 * p.n_canon);
+  p.ptr.assign(p.n_canon + 1, 0);
+  std::vector<int16_t> seg;
+  for (int64_t c = 0; c < p.n_canon; ++c) {
+    const int64_t k = p.base + c;
+    const int dy = (int)(k / (2 * rx + 1)) - ry, dx = (int)(k % (2 * rx + 1)) - rx;
+    p.vec[2 * c] = (int16_t)dx;
+    p.vec[2 * c + 1] = (int16_t)dy;
+    segment_canonical(dx, dy, seg);
+    p.ptr[c + 1] = p.ptr[c] + (int64_t)seg.size() / 2;
+    p.off.insert(p.off.end(), seg.begin(), seg.end());
+  }
+
+  // Prefix tree of all canonical segments; node 0 is pixel (0,0).
+  Trie t;
+  t.add(-1, 0, 0, 0);
+  for (int64_t c = 0; c < p.n_canon; ++c) {
+    int32_t n = 0;
+    for (int64_t j = p.ptr[c] + 1; j < p.ptr[c + 1]; ++j) {
+      const int16_t x = p.off[2 * j], y = p.off[2 * j + 1];
+      const int slot = move_slot(x - t.pix[2 * n], y - t.pix[2 * n + 1]);
+      int32_t ch = t.child5[5 * (int64_t)n + slot];
+      if (ch < 0) {
+        ch = t.add(n, x, y, t.depth[n] + 1);
+        t.child5[5 * (int64_t)n + slot] = ch;
+      }
+      n = ch;
+    }
+    t.vec[n] = (int32_t)c;
+  }
+  const int64_t nn = (int64_t)t.parent.size();
+  // subtree sizes (children have larger ids than parents)
+  std::vector<int64_t> sub(nn, 1);
+  for (int64_t n = nn - 1; n > 0; --n) sub[t.parent[n]] += sub[n];
+  std::vector<int32_t> cstart(nn + 1, 0), clist;
+  clist.reserve(nn);
+  for (int64_t n = 0; n < nn; ++n) {
+    int32_t cs[5];
+    int m = 0;
+    for (int k = 0; k < 5; ++k) if (t.child5[5 * n + k] >= 0) cs[m++] = t.child5[5 * n + k];
+    std::sort(cs, cs + m, [&](int32_t a, int32_t b) { return sub[a] != sub[b] ? sub[a] < sub[b] : a < b; });
+    for (int k = 0; k < m; ++k) clist.push_back(cs[k]);
+    cstart[n + 1] = (int32_t)clist.size();
+  }
+  std::vector<int32_t>().swap(t.child5);
+
+  // Depth-first walk -> events -> records.
+  Walker wk{t, sub, cstart, clist, {}, 0};
+  wk.ev.reserve(nn + 3 * p.n_canon);
+  wk.node(0, 0);
+  if (wk.max_level > kMaxStack) { err = "prefix-tree stack deeper than supported"; return -2; }
+
+  std::vector<int64_t> rec_word, rec_pix;
+  std::vector<int32_t> rec_cur;
+  std::vector<std::vector<int32_t>> rec_stack;
+  std::vector<uint8_t> rec_restores;
+  Program full;
+  emit_records(wk.ev, full, rec_word, rec_pix, rec_cur, rec_stack, rec_restores);
+  full.stack_depth = wk.max_level;
+  full.n_pixel_words = rec_pix.back();
+
+  // Cut into pieces of similar pixel count; each piece gets a prologue that
+  // rebuilds its starting state from the root (no emits).
+  const int64_t nrec = (int64_t)rec_word.size() - 1;
+  const int64_t total = rec_pix.back();
+  if (n_pieces < 1) n_pieces = 1;
+  std::vector<int64_t> cuts{0};
+  for (int q = 1; q < n_pieces; ++q) {
+    const int64_t target = total * q / n_pieces;
+    int64_t r = std::lower_bound(rec_pix.begin(), rec_pix.end() - 1, target) - rec_pix.begin();
+    if (r <= cuts.back()) continue;
+    if (r >= nrec) break;
+    cuts.push_back(r);
+  }
+  cuts.push_back(nrec);
+  Program& tree = p.tree;
+  tree.words.clear();
+  tree.piece_begin.clear();
+  tree.piece_pixels.clear();
+  tree.stack_depth = full.stack_depth;
+  tree.n_pixel_words = 0;
+  for (size_t q = 0; q + 1 < cuts.size(); ++q) {
+    const int64_t r0 = cuts[q], r1 = cuts[q + 1];
+    tree.piece_begin.push_back((int64_t)tree.words.size());
+    int64_t pix = 0;
+    // prologue: walk root -> deepest node of the state, pushing stack entries
+    {
+      const std::vector<int32_t>& live = rec_stack[r0];
+      // after a restore the state is the restored entry; otherwise the
+      // current node (a descendant of every live entry)
+      const int32_t target = rec_cur[r0];
+      std::vector<int32_t> chain;
+      for (int32_t x = target; x >= 0; x = t.parent[x]) chain.push_back(x);
+      std::reverse(chain.begin(), chain.end());
+      size_t li = 0;
+      std::vector<uint32_t> run;
+      bool first = true;
+      for (size_t ci = 0; ci < chain.size(); ++ci) {
+        run.push_back((uint32_t)chain[ci]);
+        const bool is_push = li < live.size() && live[li] == chain[ci];
+        if (is_push || ci + 1 == chain.size()) {
+          uint32_t hdr = (uint32_t)run.size() | (first ? kReset : 0u);
+          if (is_push) { hdr |= kPush | ((uint32_t)li << kPlevelShift); ++li; }
+          tree.words.push_back(hdr);
+          for (uint32_t n : run) tree.words.push_back(n);
+          pix += (int64_t)run.size();
+          run.clear();
+          first = false;
+        }
+      }
+    }
+    // body: copy records r0..r1-1; the first record of piece 0 needs reset
+    for (int64_t r = r0; r < r1; ++r) {
+      const int64_t wb = rec_word[r], we = rec_word[r + 1];
+      uint32_t hdr = full.words[wb];
+      if (r == 0) hdr |= kReset;
+      tree.words.push_back(hdr);
+      for (int64_t j = wb + 1; j < we; ++j) tree.words.push_back(full.words[j]);
+      pix += rec_pix[r + 1] - rec_pix[r];
+    }
+    tree.piece_pixels.push_back(pix);
+    tree.n_pixel_words += pix;
+  }
+  tree.piece_begin.push_back((int64_t)tree.words.size());
+
+  // Plain program: every canonical segment from scratch (Alg. 1 order).
+  Program& plain = p.plain;
+  plain.words.clear();
+  plain.stack_depth = 0;
+  plain.n_pixel_words = 0;
+  // pixel words of the plain program refer to trie nodes as well: walk each
+  // segment down the tree to recover its node chain.
+  {
+    std::vector<int32_t> chain;
+    for (int64_t c = 0; c < p.n_canon; ++c) {
+      // find node of vector c by walking pixels
+      chain.clear();
+      int32_t n = 0;
+      chain.push_back(0);
+      for (int64_t j = p.ptr[c] + 1; j < p.ptr[c + 1]; ++j) {
+        const int16_t x = p.off[2 * j], y = p.off[2 * j + 1];
+        int32_t found = -1;
+        for (int32_t k = cstart[n]; k < cstart[n + 1]; ++k) {
+          const int32_t ch = clist[k];
+          if (t.pix[2 * ch] == x && t.pix[2 * ch + 1] == y) { found = ch; break; }
+        }
+        n = found;
+        chain.push_back(n);
+      }
+      plain.words.push_back(kReset | kEmit | (uint32_t)chain.size());
+      plain.words.push_back((uint32_t)c);
+      for (int32_t x : chain) plain.words.push_back((uint32_t)x);
+      plain.n_pixel_words += (int64_t)chain.size();
+    }
+  }
+  split_program(p, plain, n_pieces);
+
+  p.node_parent = std::move(t.parent);
+  p.node_pix = std::move(t.pix);
+  p.node_vec = std::move(t.vec);
+  return 0;
+}
+
+void split_program(const Paths&, Program& prog, int n_pieces) {
+  // Plain programs have only independent records (each starts with reset),
+  // so cutting at any record boundary needs no prologue.
+  std::vector<int64_t> starts, pixc;
+  int64_t pix = 0;
+  for (int64_t w = 0; w < (int64_t)prog.words.size();) {
+    const uint32_t h = prog.words[w];
+    starts.push_back(w);
+    pixc.push_back(pix);
+    const int64_t np = h & kNpixMask;
+    pix += np;
+    w += 1 + ((h & kEmit) ? 1 : 0) + np;
+  }
+  starts.push_back((int64_t)prog.words.size());
+  pixc.push_back(pix);
+  prog.piece_begin.clear();
+  prog.piece_pixels.clear();
+  if (n_pieces < 1) n_pieces = 1;
+  std::vector<int64_t> cut_rec{0};
+  const int64_t nrec = (int64_t)starts.size() - 1;
+  for (int q = 1; q < n_pieces; ++q) {
+    int64_t r = std::lower_bound(pixc.begin(), pixc.end() - 1, pix * q / n_pieces) - pixc.begin();
+    if (r <= cut_rec.back() || r >= nrec) continue;
+    cut_rec.push_back(r);
+  }
+  cut_rec.push_back(nrec);
+  for (size_t q = 0; q + 1 < cut_rec.size(); ++q) {
+    prog.piece_begin.push_back(starts[cut_rec[q]]);
+    prog.piece_pixels.push_back(pixc[cut_rec[q + 1]] - pixc[cut_rec[q]]);
+  }
+  prog.piece_begin.push_back(starts[nrec]);
+}
+
+}  // namespace lpf

@@ -1,0 +1,76 @@
+// Host-side path tables and evaluation programs for the lineal path function.
+//
+// A "program" is the order in which the kernels visit the discretised
+// segments of every canonical vector.  Segments that share their first pixels
+// share the work for those pixels (the idea of the "enhanced" evaluation,
+// Sec. 3.2, generalised from the longest shorter overlapping segment to every
+// common prefix): the segments form a prefix tree whose nodes are pixels; a
+// depth-first walk ANDs one shifted image word per node, counts at nodes that
+// end a canonical vector, and keeps the masks of branching nodes on a small
+// stack.  Children are visited smallest subtree first and the largest last,
+// which bounds the stack by log2 of the node count.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace lpf {
+
+// Record header word (int32) of a program; pixel words follow it.
+//   bits  0..13  number of pixel words that follow (n_pix)
+//   bit   14     emit: count the mask into vector `vec` (next word)
+//   bit   15     restore: mask <- stack[rlevel] before the pixels
+//   bit   16     push: stack[plevel] <- mask after the pixels (and emit)
+//   bits 17..23  rlevel
+//   bits 24..30  plevel
+//   bit   31     reset: mask <- all valid translations before the pixels
+constexpr uint32_t kNpixMask = 0x3FFFu;
+constexpr uint32_t kEmit = 1u << 14;
+constexpr uint32_t kRestore = 1u << 15;
+constexpr uint32_t kPush = 1u << 16;
+constexpr int kRlevelShift = 17;
+constexpr int kPlevelShift = 24;
+constexpr uint32_t kLevelMask = 0x7Fu;
+constexpr uint32_t kReset = 1u << 31;
+constexpr int kMaxStack = 32;
+
+struct Program {
+  // Words: headers, vec ids and pixel words.  Pixel words hold an index into
+  // `pix` (the (sx, sy) offsets) until they are baked for an image width.
+  std::vector<uint32_t> words;
+  std::vector<int64_t> piece_begin;   // word offsets where pieces start (size n_pieces + 1)
+  std::vector<int64_t> piece_pixels;  // pixel words per piece (incl. prologue)
+  int stack_depth = 0;                // levels used
+  int64_t n_pixel_words = 0;          // total pixel words (work per translation word)
+};
+
+struct Paths {
+  int32_t rx = 0, ry = 0;
+  int64_t n_full = 0, n_canon = 0, base = 0;
+  // Canonical vectors in canonical order (canonical index = full index - base).
+  std::vector<int16_t> vec;          // [n_canon][2] (dx, dy)
+  std::vector<int64_t> ptr;          // [n_canon + 1] CSR into off
+  std::vector<int16_t> off;          // [ptr[n_canon]][2] (sx, sy) pixel offsets
+  // Prefix tree of the canonical segments.
+  std::vector<int32_t> node_parent;  // -1 for the root (pixel (0,0))
+  std::vector<int16_t> node_pix;     // [n_nodes][2]
+  std::vector<int32_t> node_vec;     // canonical index ending here, or -1
+  // Programs: tree walk (shared prefixes) and plain (every segment from scratch).
+  Program tree;
+  Program plain;
+  int64_t n_nodes() const { return (int64_t)node_parent.size(); }
+};
+
+// Canonical half: dy > 0, or dy == 0 and dx >= 0.
+inline bool is_canonical(int dx, int dy) { return dy > 0 || (dy == 0 && dx >= 0); }
+
+// Pixel offsets of the segment (0,0) -> (dx,dy), for canonical (dx,dy).
+void segment_canonical(int dx, int dy, std::vector<int16_t>& out_xy);
+
+// Build tables and both programs.  Returns 0 or a negative status.
+int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err);
+
+// Split a program into pieces of similar pixel count; fills piece tables.
+void split_program(const Paths& p, Program& prog, int n_pieces);
+
+}  // namespace lpf

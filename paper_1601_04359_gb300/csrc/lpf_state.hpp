@@ -1,0 +1,58 @@
+// The opaque paths handle and the per-image geometry the kernels use.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <string>
+
+#include "../../include/lpf.h"
+#include "lpf_paths.hpp"
+
+namespace lpf {
+
+// Geometry of the bit-packed, periodically extended image for one (H, W) and
+// one window.  Packed row y (0 <= y < rows) holds pixels of image row y mod H;
+// bit e (word e / 32, bit e % 32) of a row is the pixel at column
+// (e - r32) mod W, so a translation x plus an offset sx in [-rx, rx] reads bit
+// x + sx + r32 >= 0 of the row without wrapping.
+struct Geometry {
+  int H = 0, W = 0, rx = 0, ry = 0;
+  int nw = 0;      // words holding the W translations of a row
+  int T = 0;       // words per thread
+  int G = 0;       // warps per block (word groups), G*T >= nw
+  int r32 = 0;     // rx rounded up to a multiple of 32
+  int S = 0;       // words per packed row (odd, so that 32 rows hit 32 banks)
+  int nbands = 0;  // 32-row bands of translations
+  int rows = 0;    // packed rows = 32*nbands + ry
+  uint32_t band_bytes = 0;   // shared memory of one band's rows (multiple of 16)
+  size_t packed_words = 0;   // rows*S plus padding for the last band's bulk copy
+};
+
+int make_geometry(int H, int W, int rx, int ry, int T, Geometry& g);
+
+// A program with its pixel words converted to packed offsets for one width.
+struct Baked {
+  int W = -1, S = -1, r32 = -1;
+  uint32_t* d_words = nullptr;
+  int64_t* d_piece = nullptr;
+  int n_pieces = 0;
+};
+
+}  // namespace lpf
+
+struct lpf_paths {
+  lpf::Paths host;
+  int device = -1;
+  lpf::Baked tree, plain;
+  uint32_t* d_packed = nullptr;  // work area: packed image (one at a time)
+  size_t packed_cap = 0;         // words
+  int* d_status = nullptr;       // bounded-wait timeouts since the last check
+  cudaEvent_t ev_start = nullptr, ev_stop = nullptr;  // optional kernel timer
+};
+
+namespace lpf {
+// Upload/convert `prog` for geometry g (no-op if already baked for g.W/S).
+int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b);
+// Make sure the handle is bound to the current device and has a status word
+// and a packed-image area of at least `words`.
+int ensure_device(lpf_paths* p, size_t packed_words);
+}  // namespace lpf

@@ -1,0 +1,68 @@
+"""Host-side checks of the C ABI: the library loads, exports every declared
+symbol, and its host-only entry points (path tables) work without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1601_04359_gb300 as lpf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", f)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"\b(lpf_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lpf.load()
+    names = _declared()
+    assert "lpf_full" in names and "lpf_build_paths" in names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_build_paths_tables_match_oracle_segments():
+    for rx, ry in [(0, 0), (3, 2), (12, 12), (7, 19)]:
+        p = lpf.lpf_build_paths(rx, ry)
+        n_full, n_canon, base = oracle.window_sizes(rx, ry)
+        assert (p.n_full, p.n_canon, p.base) == (n_full, n_canon, base)
+        vec, ptr, off = lpf.lpf_paths_export(p)
+        for c in range(n_canon):
+            k = base + c
+            dy, dx = k // (2 * rx + 1) - ry, k % (2 * rx + 1) - rx
+            assert tuple(vec[c]) == (dx, dy)
+            np.testing.assert_array_equal(off[ptr[c]:ptr[c + 1]], oracle.segment(dx, dy))
+
+
+def test_prefix_program_statistics():
+    # The prefix tree visits far fewer pixels than the segments hold.
+    p = lpf.lpf_build_paths(64, 64)
+    st = lpf.lpf_paths_stats(p)
+    assert p.n_offsets == 366081
+    assert st["n_tree_nodes"] < 0.25 * p.n_offsets
+    assert 1 <= st["stack_depth"] <= 24 and st["n_pieces"] >= 1
+
+
+def test_invalid_arguments_rejected_on_host():
+    lib = lpf.load()
+    h = ctypes.c_void_p()
+    assert lib.lpf_build_paths(-1, 3, ctypes.byref(h)) == -1
+    assert lib.lpf_build_paths(4096, 3, ctypes.byref(h)) == -1
+    assert lib.lpf_build_paths(3, 3, None) == -1
+    p = lpf.lpf_build_paths(4, 4)
+    # null image / counts and a window wider than the image: rejected before any CUDA call
+    assert lib.lpf_full(None, 8, 8, p.handle, None, None) == -1
+    assert lib.lpf_full(ctypes.c_void_p(16), 8, 4, p.handle, ctypes.c_void_p(16), None) == -1
+    assert lib.lpf_full(ctypes.c_void_p(16), 0, 8, p.handle, ctypes.c_void_p(16), None) == -1
+    assert lpf.lpf_strerror(-1) == "invalid argument"

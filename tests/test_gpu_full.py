@@ -1,0 +1,91 @@
+"""GPU parity of lpf_full / lpf_full_standard against the CPU oracle.
+
+Counts are integers: the bar is bit-exact equality with the oracle on every
+entry (small cases) or on sampled vectors evaluated one by one by the oracle
+(full-size cases), plus properties that hold at any size.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(lpf, img, rx, ry, standard=False):
+    p = lpf.lpf_build_paths(rx, ry)
+    d = torch.from_numpy(np.ascontiguousarray(img)).cuda()
+    f = lpf.lpf_full_standard if standard else lpf.lpf_full
+    c = f(d, p)
+    torch.cuda.synchronize()
+    assert lpf.lpf_paths_status(p) == 0
+    return c.cpu().numpy(), p
+
+
+CASES = [
+    ("config1 64x64 r32", lambda: synth.config1_image(), 32, 32),
+    ("ragged 37x45", lambda: synth.random_binary(37, 45, 0.6, 1), 20, 11),
+    ("tiny 5x7 full domain", lambda: synth.random_binary(5, 7, 0.5, 2), 6, 4),
+    ("tall 70x33 rx=32 ry=69", lambda: synth.random_binary(70, 33, 0.55, 3), 32, 69),
+    ("chess 40 full domain", lambda: synth.chess(40, 40, 10), 39, 39),
+    ("1x1", lambda: np.ones((1, 1), np.uint8), 0, 0),
+    ("1xW row", lambda: synth.random_binary(1, 70, 0.7, 4), 69, 0),
+    ("Hx1 column", lambda: synth.random_binary(77, 1, 0.7, 5), 0, 76),
+    ("all ones", lambda: np.ones((33, 65), np.uint8), 17, 9),
+    ("all zeros", lambda: np.zeros((33, 65), np.uint8), 17, 9),
+    ("ellipses 96x130", lambda: synth.ellipses(96, 130, 0.35, seed=7), 48, 40),
+]
+
+
+@pytest.mark.parametrize("name,make,rx,ry", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("standard", [False, True], ids=["tree", "standard"])
+def test_full_matches_oracle(gpu_lib, name, make, rx, ry, standard):
+    img = make()
+    got, _ = _run(gpu_lib, img, rx, ry, standard)
+    ref = oracle.lpf_full(img, rx, ry)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_config2_512_sampled_and_properties(gpu_lib):
+    # Full size (512x512, |dx|,|dy| <= 256), in the launch configuration the
+    # benchmark times: sampled vectors checked one by one against the oracle.
+    img = synth.config2_image()
+    got, p = _run(gpu_lib, img, 256, 256)
+    n_full, _, base = oracle.window_sizes(256, 256)
+    rng = np.random.default_rng(0)
+    vecs = [(0, 0), (1, 0), (256, 0), (-256, 0), (0, 256), (256, 256), (-256, 256), (256, -256),
+            (255, 3), (-7, 200), (17, -129)]
+    vecs += [(int(a), int(b)) for a, b in rng.integers(-256, 257, size=(24, 2))]
+    ref = oracle.count_list(img, vecs)
+    for (dx, dy), r in zip(vecs, ref):
+        k = oracle.full_index(dx, dy, 256, 256)
+        assert got[0, k] == r[0] and got[1, k] == r[1], (dx, dy)
+    # properties at full size
+    assert got[1, base] == int(img.sum()) and got[0, base] == img.size - int(img.sum())
+    np.testing.assert_array_equal(got, got[:, ::-1])
+    assert (got >= 0).all()
+
+
+def test_tree_equals_standard_at_full_size(gpu_lib):
+    img = synth.config2_image()
+    a, _ = _run(gpu_lib, img, 256, 256, standard=False)
+    b, _ = _run(gpu_lib, img, 256, 256, standard=True)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_repeated_calls_and_width_change(gpu_lib):
+    # One handle used with several image widths (program re-baked) and reused.
+    p = gpu_lib.lpf_build_paths(12, 9)
+    for H, W, seed in [(40, 50, 1), (40, 13, 2), (40, 50, 3), (64, 64, 4)]:
+        img = synth.random_binary(H, W, 0.5, seed)
+        c = gpu_lib.lpf_full(torch.from_numpy(img).cuda(), p)
+        np.testing.assert_array_equal(c.cpu().numpy(), oracle.lpf_full(img, 12, 9))
+
+
+def test_invalid_window_raises(gpu_lib):
+    p = gpu_lib.lpf_build_paths(40, 4)
+    img = torch.zeros((32, 32), dtype=torch.uint8, device="cuda")
+    with pytest.raises(gpu_lib.LpfError):
+        gpu_lib.lpf_full(img, p)
