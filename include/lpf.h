@@ -61,6 +61,10 @@ typedef struct lpf_paths lpf_paths;        /* opaque, owned by the library */
 /* Name of a status code (static string). */
 const char *lpf_strerror(int code);
 
+/* Text of the last CUDA runtime error seen by this thread inside the library
+ * (empty if none); stays valid until the thread's next library call. */
+const char *lpf_last_error_message(void);
+
 /*
  * Build the discretised segments of every vector of the window |dx| <= rx,
  * |dy| <= ry (Sec. 2.2 segments; Sec. 3.1 step 1, done once) and the
@@ -130,6 +134,41 @@ int lpf_full_standard(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *p
                       int64_t *counts_dev, lpf_stream_t stream);
 
 /*
+ * Count changes for a batch of candidate pixel exchanges, and the change of
+ * the least-square error they cause -- the modification operator and the
+ * objective of the annealer (Sec. 4, swap of two pixels of different phases;
+ * Eq. (LSE)).  The paper re-evaluates the whole descriptor per candidate; this
+ * call evaluates only the translations whose segment contains a swapped pixel.
+ *   img_dev      H*W uint8 (0/1): the current cell (not modified).
+ *   pairs_dev    int32 [K][2] linear pixel indices (y*W + x) of the two
+ *                pixels of each candidate, in either order.  A pair whose
+ *                pixels hold the same value (including a == b) is the
+ *                identity: all its changes are 0.  An index outside [0, H*W)
+ *                is treated as the identity and raises a device status
+ *                flag that lpf_paths_status reports as LPF_EINVAL.
+ *   dcounts_dev  int32 [K][2][n_vec_canon] or NULL: count after the exchange
+ *                minus count before, phase 0 first, canonical order.
+ *   target_dev   float [2][n_vec_full] target descriptor (already divided by
+ *                its own image area) and counts_dev int64 [2][n_vec_full] the
+ *                current cell's counts (from lpf_full): needed when de_dev is
+ *                given.
+ *   de_dev       float [K] or NULL: e(after) - e(before) with
+ *                e = sum over both phases and the canonical half of
+ *                (target - counts/(H*W))^2, computed in float32 from the exact
+ *                integer changes; summed in a fixed order (bitwise
+ *                reproducible).
+ * At least one of dcounts_dev, de_dev must be non-NULL.  Cell limits: the
+ * periodically extended cell (W+2rx)*(H+2ry) bytes must fit in shared memory
+ * (about 227 KB), else LPF_EUNSUPPORTED.  The first call for a cell width, or
+ * with a larger K than before, allocates the handle's tables / work area.
+ * Errors: LPF_EINVAL, LPF_EUNSUPPORTED, LPF_ENOMEM, LPF_ECUDA.
+ */
+int lpf_delta_swap(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
+                   const int32_t *pairs_dev, int32_t K, int32_t *dcounts_dev,
+                   const float *target_dev, const int64_t *counts_dev, float *de_dev,
+                   lpf_stream_t stream);
+
+/*
  * Measurement hook: when ev_start/ev_stop (cudaEvent_t, created by the
  * caller) are non-NULL, every later device call on this handle records
  * ev_start on its stream right before its dominant kernel and ev_stop right
@@ -140,8 +179,9 @@ int lpf_paths_set_timer(lpf_paths *paths, void *ev_start, void *ev_stop);
 
 /*
  * Device-side status of the handle's last calls: synchronises `stream`,
- * returns LPF_ETIMEOUT if a bounded wait inside a kernel gave up since the
- * last check (and clears the flag), LPF_OK otherwise.
+ * returns LPF_ETIMEOUT if a bounded wait inside a kernel gave up, LPF_EINVAL
+ * if a kernel met an out-of-range pixel index, since the last check (and
+ * clears the flags), LPF_OK otherwise.
  */
 int lpf_paths_status(lpf_paths *paths, lpf_stream_t stream);
 

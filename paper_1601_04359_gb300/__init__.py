@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = [
     "load", "LpfError", "Paths", "lpf_build_paths", "lpf_paths_info", "lpf_paths_export",
     "lpf_paths_stats", "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer",
-    "lpf_strerror",
+    "lpf_delta_swap", "lpf_strerror",
 ]
 
 _lib = None
@@ -27,7 +27,10 @@ LIB_PATH = _build.LIB
 
 class LpfError(RuntimeError):
     def __init__(self, code: int, what: str):
-        super().__init__(f"{what}: {lpf_strerror(code)} ({code})")
+        detail = ""
+        if code == -3 and _lib is not None:
+            detail = " [" + _lib.lpf_last_error_message().decode() + "]"
+        super().__init__(f"{what}: {lpf_strerror(code)} ({code}){detail}")
         self.code = code
 
 
@@ -45,6 +48,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     P32 = ctypes.POINTER(ctypes.c_int32)
     sig = {
         "lpf_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "lpf_last_error_message": (ctypes.c_char_p, []),
         "lpf_build_paths": (ctypes.c_int, [i32, i32, ctypes.POINTER(p)]),
         "lpf_paths_info": (ctypes.c_int, [p, P64, P64, P64]),
         "lpf_paths_export": (ctypes.c_int, [p, p, p, p]),
@@ -54,6 +58,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_full_standard": (ctypes.c_int, [p, i32, i32, p, p, p]),
         "lpf_paths_status": (ctypes.c_int, [p, p]),
         "lpf_paths_set_timer": (ctypes.c_int, [p, p, p]),
+        "lpf_delta_swap": (ctypes.c_int, [p, i32, i32, p, p, i32, p, p, p, p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -157,6 +162,27 @@ def lpf_full_standard(img, paths: Paths, counts=None, stream=None):
                                     _dev_ptr(counts, "int64", "counts"), _stream_ptr(stream)),
            "lpf_full_standard")
     return counts
+
+
+def lpf_delta_swap(img, paths: Paths, pairs, dcounts=None, target=None, counts=None, de=None,
+                   want_dcounts: bool = True, want_de: bool = False, stream=None):
+    """Count changes (int32 [K][2][n_canon]) and/or error changes (float32 [K])
+    for candidate exchanges pairs (int32 CUDA tensor [K][2])."""
+    import torch
+    H, W = img.shape
+    K = int(pairs.shape[0])
+    if want_dcounts and dcounts is None:
+        dcounts = torch.empty((K, 2, paths.n_canon), dtype=torch.int32, device=img.device)
+    if want_de and de is None:
+        de = torch.empty(K, dtype=torch.float32, device=img.device)
+    _check(load().lpf_delta_swap(
+        _dev_ptr(img, "uint8", "img"), H, W, paths.handle, _dev_ptr(pairs, "int32", "pairs"), K,
+        _dev_ptr(dcounts, "int32", "dcounts") if dcounts is not None else None,
+        _dev_ptr(target, "float32", "target") if target is not None else None,
+        _dev_ptr(counts, "int64", "counts") if counts is not None else None,
+        _dev_ptr(de, "float32", "de") if de is not None else None,
+        _stream_ptr(stream)), "lpf_delta_swap")
+    return dcounts, de
 
 
 def lpf_paths_set_timer(paths: Paths, ev_start=None, ev_stop=None):

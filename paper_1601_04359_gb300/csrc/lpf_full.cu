@@ -197,23 +197,28 @@ __global__ void __launch_bounds__(1024) walk_kernel(const uint32_t* __restrict__
 // ---------------------------------------------------------------------------
 // Host side
 
-static int cuda_status(cudaError_t e) {
+thread_local char g_last_error[256] = "";
+
+int set_cuda_error(cudaError_t e) {
   if (e == cudaSuccess) return LPF_OK;
-  if (e == cudaErrorMemoryAllocation) return LPF_ENOMEM;
-  return LPF_ECUDA;
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? LPF_ENOMEM : LPF_ECUDA;
 }
+
+static int cuda_status(cudaError_t e) { return set_cuda_error(e); }
 
 int ensure_device(lpf_paths* p, size_t packed_words) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return LPF_ECUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
   if (p->device < 0) {
     p->device = dev;
   } else if (p->device != dev) {
     return LPF_EINVAL;  // handle is bound to another device
   }
   if (!p->d_status) {
-    if (cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess) return LPF_ENOMEM;
-    if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return LPF_ECUDA;
+    if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) return set_cuda_error(e);
   }
   if (packed_words > p->packed_cap) {
     if (p->d_packed) {
@@ -222,7 +227,7 @@ int ensure_device(lpf_paths* p, size_t packed_words) {
       p->d_packed = nullptr;
       p->packed_cap = 0;
     }
-    if (cudaMalloc(&p->d_packed, packed_words * 4) != cudaSuccess) return LPF_ENOMEM;
+    if ((e = cudaMalloc(&p->d_packed, packed_words * 4)) != cudaSuccess) return set_cuda_error(e);
     p->packed_cap = packed_words;
   }
   return LPF_OK;
@@ -253,12 +258,14 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
       out[i] = (off << 5) | (uint32_t)(sxp & 31);
     }
   }
-  if (cudaMalloc(&b.d_words, out.size() * 4) != cudaSuccess) return LPF_ENOMEM;
-  if (cudaMalloc(&b.d_piece, prog.piece_begin.size() * 8) != cudaSuccess) return LPF_ENOMEM;
-  if (cudaMemcpy(b.d_words, out.data(), out.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return LPF_ECUDA;
-  if (cudaMemcpy(b.d_piece, prog.piece_begin.data(), prog.piece_begin.size() * 8, cudaMemcpyHostToDevice) !=
+  cudaError_t e;
+  if ((e = cudaMalloc(&b.d_words, out.size() * 4)) != cudaSuccess) return set_cuda_error(e);
+  if ((e = cudaMalloc(&b.d_piece, prog.piece_begin.size() * 8)) != cudaSuccess) return set_cuda_error(e);
+  if ((e = cudaMemcpy(b.d_words, out.data(), out.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return set_cuda_error(e);
+  if ((e = cudaMemcpy(b.d_piece, prog.piece_begin.data(), prog.piece_begin.size() * 8, cudaMemcpyHostToDevice)) !=
       cudaSuccess)
-    return LPF_ECUDA;
+    return set_cuda_error(e);
   b.W = g.W;
   b.S = g.S;
   b.r32 = g.r32;
@@ -267,11 +274,31 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
 }
 
 static std::once_flag g_attr_once;
+static int g_attr_status = LPF_OK;
+static int g_max_dyn_smem = 0;  // dynamic shared memory a walk block may use
+
+template <typename K>
+static int allow_smem(K kernel, int optin, int& max_dyn) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  const int dyn = optin - (int)fa.sharedSizeBytes;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  max_dyn = max_dyn == 0 ? dyn : std::min(max_dyn, dyn);
+  return LPF_OK;
+}
+
 static void set_kernel_attributes() {
-  cudaFuncSetAttribute(walk_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-  cudaFuncSetAttribute(walk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-  cudaFuncSetAttribute(walk_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-  cudaFuncSetAttribute(walk_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) { g_attr_status = set_cuda_error(e); return; }
+  int rc = allow_smem(walk_kernel<1>, optin, g_max_dyn_smem);
+  if (!rc) rc = allow_smem(walk_kernel<2>, optin, g_max_dyn_smem);
+  if (!rc) rc = allow_smem(walk_kernel<4>, optin, g_max_dyn_smem);
+  if (!rc) rc = allow_smem(walk_kernel<8>, optin, g_max_dyn_smem);
+  g_attr_status = rc;
 }
 
 static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* counts, cudaStream_t s,
@@ -281,18 +308,22 @@ static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* cou
   if (p->host.rx >= W || p->host.ry >= H) return LPF_EINVAL;
   const Program& prog = standard ? p->host.plain : p->host.tree;
   if (prog.stack_depth > kDevStack) return LPF_EUNSUPPORTED;
+  std::call_once(g_attr_once, set_kernel_attributes);
+  if (g_attr_status) return g_attr_status;
   Geometry g;
   int rc = make_geometry(H, W, p->host.rx, p->host.ry, 0, g);
   if (rc) return rc;
+  if ((int)g.band_bytes > g_max_dyn_smem) return LPF_EUNSUPPORTED;
   rc = ensure_device(p, g.packed_words);
   if (rc) return rc;
   Baked& b = standard ? p->plain : p->tree;
   rc = bake(p, prog, g, b);
   if (rc) return rc;
-  std::call_once(g_attr_once, set_kernel_attributes);
+  (void)cudaGetLastError();  // clear a stale error left by earlier, unrelated calls
 
   const int64_t n_full = p->host.n_full, base = p->host.base;
-  if (cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * n_full, s) != cudaSuccess) return LPF_ECUDA;
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * n_full, s);
+  if (e != cudaSuccess) return set_cuda_error(e);
   {
     const int64_t total = (int64_t)g.rows * g.S;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
@@ -325,6 +356,8 @@ static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* cou
 // C ABI
 
 extern "C" {
+
+const char* lpf_last_error_message(void) { return lpf::g_last_error; }
 
 const char* lpf_strerror(int code) {
   switch (code) {
@@ -400,6 +433,10 @@ void lpf_paths_free(lpf_paths* p) {
     cudaFree(p->plain.d_piece);
     cudaFree(p->d_packed);
     cudaFree(p->d_status);
+    cudaFree(p->delta.d_doff);
+    cudaFree(p->delta.d_dptr);
+    cudaFree(p->delta.d_chunk);
+    cudaFree(p->d_partial);
     if (cur >= 0) cudaSetDevice(cur);
   }
   delete p;
@@ -430,7 +467,7 @@ int lpf_paths_status(lpf_paths* p, lpf_stream_t stream) {
   if (cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LPF_ECUDA;
   if (h) {
     cudaMemset(p->d_status, 0, sizeof(int));
-    return LPF_ETIMEOUT;
+    return (h & 1) ? LPF_ETIMEOUT : LPF_EINVAL;
   }
   return LPF_OK;
 }

@@ -37,6 +37,15 @@ struct Baked {
   int n_pieces = 0;
 };
 
+// Tables of the swap-delta kernel for one extended cell width.
+struct DeltaTables {
+  int We = -1;
+  int32_t* d_doff = nullptr;   // per segment pixel: sy*We + sx
+  int32_t* d_dptr = nullptr;   // CSR pointers [n_canon + 1]
+  int32_t* d_chunk = nullptr;  // vector chunk bounds [n_chunks + 1]
+  int n_chunks = 0;
+};
+
 }  // namespace lpf
 
 struct lpf_paths {
@@ -47,12 +56,23 @@ struct lpf_paths {
   size_t packed_cap = 0;         // words
   int* d_status = nullptr;       // bounded-wait timeouts since the last check
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;  // optional kernel timer
+  lpf::DeltaTables delta;
+  float* d_partial = nullptr;    // work area: per (candidate, chunk) error changes
+  size_t partial_cap = 0;        // floats
 };
 
 namespace lpf {
+// Record a CUDA error for lpf_last_error_message(); returns the status code.
+int set_cuda_error(cudaError_t e);
 // Upload/convert `prog` for geometry g (no-op if already baked for g.W/S).
 int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b);
 // Make sure the handle is bound to the current device and has a status word
 // and a packed-image area of at least `words`.
 int ensure_device(lpf_paths* p, size_t packed_words);
+// Swap-delta: check sizes, bake tables, size the partial-sum work area for K.
+int delta_prepare(lpf_paths* p, int H, int W, int K);
+// Enqueue the swap-delta kernels (k_dev: optional device count <= K).
+int delta_launch(const uint8_t* img, int H, int W, lpf_paths* p, const int32_t* pairs, int K,
+                 const int32_t* k_dev, int32_t* dcounts, const float* target, const int64_t* counts, float* de,
+                 float* partial, cudaStream_t s);
 }  // namespace lpf
