@@ -216,6 +216,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
+    shape = lpf.lpf_autotune_full(d_img, paths, counts)  # setup: pick the walk launch shape
     for _ in range(args.warmup):
         lpf.lpf_full(d_img, paths, counts)
     torch.cuda.synchronize()
@@ -294,7 +295,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": "lpf_full 512x512 ellipses f=0.35 |dx|,|dy|<=256, both phases, int64 counts",
                    "tests_per_step": tests_per_step, "l2": "flushed between timed steps (512 MB write)",
-                   "parallelism": f"replicas x{ws}"},
+                   "parallelism": f"replicas x{ws}", "walk_shape": {"T": shape[0], "BB": shape[1]}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "ALU op/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "walk_kernel", "kernel_ms": walk_ms,

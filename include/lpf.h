@@ -126,6 +126,27 @@ int lpf_full(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
              int64_t *counts_dev, lpf_stream_t stream);
 
 /*
+ * Autotuner for lpf_full: times every admissible launch shape (words per
+ * thread T in {1,2,4,8}, 32-row bands per block BB in {1,2,4,8}) of the walk
+ * kernel on this image (3 timed runs each, fastest kept) and stores the
+ * fastest in the handle for later lpf_full calls with the same H, W.  Runs
+ * and synchronises on `stream`; counts_dev receives valid counts.  best_T /
+ * best_BB (may be NULL) receive the choice.  Not for use inside stream
+ * capture.  Errors as lpf_full.
+ */
+int lpf_autotune_full(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
+                      int64_t *counts_dev, lpf_stream_t stream, int32_t *best_T, int32_t *best_BB);
+
+/*
+ * Fix the walk-kernel launch shape used by lpf_full for images of size H x W
+ * (T words per thread in {1,2,4,8}, BB bands of 32 rows per block, 1..16),
+ * overriding defaults or an autotuned choice.  Host-only.  Errors:
+ * LPF_EINVAL (bad value), LPF_EUNSUPPORTED (shape not admissible for this
+ * size: more than 16 warps per block, or shared memory too small).
+ */
+int lpf_set_launch_shape(lpf_paths *paths, int32_t H, int32_t W, int32_t T, int32_t BB);
+
+/*
  * Same as lpf_full but evaluates every segment from scratch, one vector after
  * another (the "standard" evaluation of Sec. 3.2, i.e. Alg. 1 order without
  * any shared work).  Same arguments, layout and errors; for comparison runs.

@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = [
     "load", "LpfError", "Paths", "lpf_build_paths", "lpf_paths_info", "lpf_paths_export",
     "lpf_paths_stats", "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer",
-    "lpf_delta_swap", "lpf_strerror",
+    "lpf_delta_swap", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror",
 ]
 
 _lib = None
@@ -59,6 +59,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_paths_status": (ctypes.c_int, [p, p]),
         "lpf_paths_set_timer": (ctypes.c_int, [p, p, p]),
         "lpf_delta_swap": (ctypes.c_int, [p, i32, i32, p, p, i32, p, p, p, p, p]),
+        "lpf_autotune_full": (ctypes.c_int, [p, i32, i32, p, p, p, P32, P32]),
+        "lpf_set_launch_shape": (ctypes.c_int, [p, i32, i32, i32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -151,6 +153,23 @@ def lpf_full(img, paths: Paths, counts=None, stream=None):
     _check(load().lpf_full(_dev_ptr(img, "uint8", "img"), H, W, paths.handle,
                            _dev_ptr(counts, "int64", "counts"), _stream_ptr(stream)), "lpf_full")
     return counts
+
+
+def lpf_autotune_full(img, paths: Paths, counts=None, stream=None):
+    """Pick the fastest walk-kernel launch shape for this image size; returns (T, BB)."""
+    import torch
+    H, W = img.shape
+    if counts is None:
+        counts = torch.empty((2, paths.n_full), dtype=torch.int64, device=img.device)
+    t, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().lpf_autotune_full(_dev_ptr(img, "uint8", "img"), H, W, paths.handle,
+                                    _dev_ptr(counts, "int64", "counts"), _stream_ptr(stream),
+                                    ctypes.byref(t), ctypes.byref(b)), "lpf_autotune_full")
+    return t.value, b.value
+
+
+def lpf_set_launch_shape(paths: Paths, H: int, W: int, T: int, BB: int):
+    _check(load().lpf_set_launch_shape(paths.handle, int(H), int(W), int(T), int(BB)), "lpf_set_launch_shape")
 
 
 def lpf_full_standard(img, paths: Paths, counts=None, stream=None):

@@ -33,23 +33,28 @@ namespace lpf {
 constexpr int kDevStack = 24;   // deepest prefix-tree stack the kernels hold
 constexpr int kMaxSmem = 227 * 1024;
 
-int make_geometry(int H, int W, int rx, int ry, int T, Geometry& g) {
+int make_geometry(int H, int W, int rx, int ry, int T, int BB, Geometry& g) {
   g.H = H; g.W = W; g.rx = rx; g.ry = ry;
   g.nw = (W + 31) / 32;
-  if (T <= 0) T = g.nw >= 4 ? 4 : (g.nw >= 2 ? 2 : 1);
-  while ((g.nw + T - 1) / T > 32 && T < 8) T *= 2;  // at most 1024 threads per block
+  if (T <= 0) T = g.nw >= 6 ? 8 : (g.nw >= 3 ? 4 : (g.nw >= 2 ? 2 : 1));
+  while ((g.nw + T - 1) / T > 16 && T < 8) T *= 2;  // at most 16 warps per band
   g.T = T;
   g.G = (g.nw + T - 1) / T;
+  g.nbands = (H + 31) / 32;
+  if (BB <= 0) BB = std::max(1, std::min(4, 8 / g.G));
+  BB = std::max(1, std::min(BB, g.nbands));
+  while (BB > 1 && g.G * BB > 16) --BB;              // at most 512 threads per block
+  g.BB = BB;
+  g.nbg = (g.nbands + BB - 1) / BB;
   g.r32 = ((rx + 31) / 32) * 32;
   const int nwp = g.G * T;
   g.S = nwp + ((g.r32 + rx) >> 5) + 1;
   if ((g.S & 1) == 0) g.S += 1;
-  g.nbands = (H + 31) / 32;
-  g.rows = 32 * g.nbands + ry;
-  const size_t band = (size_t)(32 + ry) * g.S * 4;
+  g.rows = 32 * BB * g.nbg + ry;
+  const size_t band = (size_t)(32 * BB + ry) * g.S * 4;
   g.band_bytes = (uint32_t)((band + 15) & ~size_t(15));
   g.packed_words = (size_t)g.rows * g.S + 4;
-  if (g.G > 32 || band > (size_t)kMaxSmem - 64) return LPF_EUNSUPPORTED;
+  if (g.G > 16 || band > (size_t)kMaxSmem - 64) return LPF_EUNSUPPORTED;
   return LPF_OK;
 }
 
@@ -86,111 +91,154 @@ __global__ void mirror_kernel(unsigned long long* __restrict__ counts, int64_t n
   }
 }
 
+// AND of one funnel-shifted image word into both phase masks, for 4 pixels.
 template <int T>
-__global__ void __launch_bounds__(1024) walk_kernel(const uint32_t* __restrict__ packed, int H, int W, int S,
-                                                   int ry, int nw, uint32_t band_bytes,
-                                                   const uint32_t* __restrict__ prog,
-                                                   const int64_t* __restrict__ piece,
-                                                   unsigned long long* __restrict__ counts, int64_t n_full,
-                                                   int64_t base, int* __restrict__ status) {
-  extern __shared__ __align__(16) uint32_t sm[];
-  __shared__ __align__(8) uint64_t bar;
-  const int band = blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    mbar_expect_tx(&bar, band_bytes);
-    bulk_g2s(sm, packed + (size_t)band * 32 * S, band_bytes, &bar);
-  }
-  if (!mbar_wait(&bar, 0)) {
-    atomicOr(status, 1);
-    return;
-  }
-
-  const int y = band * 32 + lane;
-  uint32_t valid[T];
+__device__ __forceinline__ void and4(const uint32_t* lane_base, uint4 P, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
+  const uint32_t* sa = lane_base + (P.x >> 7);
+  const uint32_t* sb = lane_base + (P.y >> 7);
+  const uint32_t* sc = lane_base + (P.z >> 7);
+  const uint32_t* sd = lane_base + (P.w >> 7);
+  uint32_t wa[T + 1], wb[T + 1], wc[T + 1], wd[T + 1];
+#pragma unroll
+  for (int t = 0; t <= T; ++t) { wa[t] = sa[t]; wb[t] = sb[t]; wc[t] = sc[t]; wd[t] = sd[t]; }
 #pragma unroll
   for (int t = 0; t < T; ++t) {
-    const int j = warp * T + t;
-    uint32_t v = 0;
-    if (y < H && j < nw) {
-      const int rem = W - 32 * j;
-      v = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
-    }
-    valid[t] = v;
+    const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], P.x);
+    const uint32_t b = __funnelshift_r(wb[t], wb[t + 1], P.y);
+    const uint32_t c = __funnelshift_r(wc[t], wc[t + 1], P.z);
+    const uint32_t d = __funnelshift_r(wd[t], wd[t + 1], P.w);
+    m1[t] = (m1[t] & a & b) & (c & d);
+    m0[t] = (m0[t] & ~(a | b)) & ~(c | d);
   }
-  const uint32_t* lane_base = sm + lane * S + warp * T;
+}
 
-  uint32_t m1[T], m0[T];
-  uint32_t st1[kDevStack][T], st0[kDevStack][T];
+template <int T>
+__device__ __forceinline__ void and1(const uint32_t* lane_base, uint32_t p, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
+  const uint32_t* sa = lane_base + (p >> 7);
+  uint32_t wa[T + 1];
 #pragma unroll
-  for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
+  for (int t = 0; t <= T; ++t) wa[t] = sa[t];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], p);
+    m1[t] &= a;
+    m0[t] &= ~a;
+  }
+}
 
-  int64_t pc = piece[blockIdx.y];
-  const int64_t end = piece[blockIdx.y + 1];
-  while (pc < end) {
-    const uint32_t hdr = __ldg(prog + pc++);
-    if (hdr & kReset) {
-#pragma unroll
-      for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
+// Persistent walk kernel.  Work items are (block-band group, program piece)
+// pairs taken from an atomic counter in band-major order, so a block usually
+// keeps its staged band across consecutive items and re-stages it (one bulk
+// copy) only when the band changes.
+template <int T>
+__global__ void __launch_bounds__(512) walk_kernel(const uint32_t* __restrict__ packed, int H, int W, int S,
+                                                  int nw, int G, int BB, uint32_t band_bytes, int n_bg,
+                                                  int n_pieces, const uint32_t* __restrict__ prog,
+                                                  const int64_t* __restrict__ piece,
+                                                  unsigned long long* __restrict__ counts, int64_t n_full,
+                                                  int64_t base, int* __restrict__ ctl) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_item, s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bl = warp / G, grp = warp - (warp / G) * G;
+  if (threadIdx.x == 0) { mbar_init(&bar, 1); s_abort = 0; }
+  __syncthreads();
+  uint32_t parity = 0;
+  int cur_bg = -1;
+  const int n_items = n_bg * n_pieces;
+  const uint32_t* lane_base = sm + (bl * 32 + lane) * S + grp * T;
+  bool copy_pending = false;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(ctl + 1, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_items) break;
+    const int bg = item / n_pieces, pi = item - (item / n_pieces) * n_pieces;
+    if (bg != cur_bg) {
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar, band_bytes);
+        bulk_g2s(sm, packed + (size_t)bg * 32 * BB * S, band_bytes, &bar);
+      }
+      copy_pending = true;
+      if (mbar_wait(&bar, parity)) copy_pending = false;
+      else s_abort = 1;
+      parity ^= 1u;
+      cur_bg = bg;
+      __syncthreads();
+      if (s_abort) break;
     }
-    if (hdr & kRestore) {
-      const int l = (hdr >> kRlevelShift) & kLevelMask;
+
+    const int y = (bg * BB + bl) * 32 + lane;
+    uint32_t valid[T];
 #pragma unroll
-      for (int t = 0; t < T; ++t) { m1[t] = st1[l][t]; m0[t] = st0[l][t]; }
+    for (int t = 0; t < T; ++t) {
+      const int j = grp * T + t;
+      uint32_t v = 0;
+      if (y < H && j < nw) {
+        const int rem = W - 32 * j;
+        v = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+      }
+      valid[t] = v;
     }
-    int vec = -1;
-    if (hdr & kEmit) vec = (int)__ldg(prog + pc++);
-    const int n = (int)(hdr & kNpixMask);
-    const uint32_t* pp = prog + pc;
-    pc += n;
-    int i = 0;
-    for (; i + 1 < n; i += 2) {
-      const uint32_t pa = __ldg(pp + i), pb = __ldg(pp + i + 1);
-      const uint32_t* sa = lane_base + (pa >> 5);
-      const uint32_t* sb = lane_base + (pb >> 5);
-      uint32_t wa[T + 1], wb[T + 1];
+    uint32_t m1[T], m0[T];
+    uint32_t st1[kDevStack][T], st0[kDevStack][T];
 #pragma unroll
-      for (int t = 0; t <= T; ++t) { wa[t] = sa[t]; wb[t] = sb[t]; }
+    for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
+
+    int64_t pc = piece[pi];
+    const int64_t end = piece[pi + 1];
+    while (pc < end) {
+      const uint32_t hdr = __ldg(prog + pc++);
+      if (hdr & kReset) {
 #pragma unroll
-      for (int t = 0; t < T; ++t) {
-        const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], pa);
-        const uint32_t b = __funnelshift_r(wb[t], wb[t + 1], pb);
-        m1[t] &= a & b;
-        m0[t] &= ~(a | b);
+        for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
+      }
+      if (hdr & kRestore) {
+        const int l = (hdr >> kRlevelShift) & kLevelMask;
+#pragma unroll
+        for (int t = 0; t < T; ++t) { m1[t] = st1[l][t]; m0[t] = st0[l][t]; }
+      }
+      int vec = -1;
+      if (hdr & kEmit) vec = (int)__ldg(prog + pc++);
+      pc = (pc + 3) & ~int64_t(3);
+      const int n = (int)(hdr & kNpixMask);
+      const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
+      const int n4 = n >> 2;
+      if (n4 > 0) {
+        uint4 nxt = __ldg(q4);
+        for (int q = 0; q < n4; ++q) {
+          const uint4 cur = nxt;
+          if (q + 1 < n4) nxt = __ldg(q4 + q + 1);
+          and4<T>(lane_base, cur, m1, m0);
+        }
+      }
+      for (int i = n4 * 4; i < n; ++i) and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
+      pc += n;
+      if (vec >= 0) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
+        c = warp_sum(c);
+        if (lane == 0) {
+          const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
+          if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);
+          if (c1) atomicAdd(counts + n_full + base + vec, (unsigned long long)c1);
+        }
+      }
+      if (hdr & kPush) {
+        const int l = (hdr >> kPlevelShift) & kLevelMask;
+#pragma unroll
+        for (int t = 0; t < T; ++t) { st1[l][t] = m1[t]; st0[l][t] = m0[t]; }
       }
     }
-    if (i < n) {
-      const uint32_t pa = __ldg(pp + i);
-      const uint32_t* sa = lane_base + (pa >> 5);
-      uint32_t wa[T + 1];
-#pragma unroll
-      for (int t = 0; t <= T; ++t) wa[t] = sa[t];
-#pragma unroll
-      for (int t = 0; t < T; ++t) {
-        const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], pa);
-        m1[t] &= a;
-        m0[t] &= ~a;
-      }
-    }
-    if (vec >= 0) {
-      uint32_t c = 0;
-#pragma unroll
-      for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
-      c = warp_sum(c);
-      if (lane == 0) {
-        const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
-        if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);
-        if (c1) atomicAdd(counts + n_full + base + vec, (unsigned long long)c1);
-      }
-    }
-    if (hdr & kPush) {
-      const int l = (hdr >> kPlevelShift) & kLevelMask;
-#pragma unroll
-      for (int t = 0; t < T; ++t) { st1[l][t] = m1[t]; st0[l][t] = m0[t]; }
-    }
+    __syncthreads();  // every warp is done with the staged band before it may be replaced
+  }
+  if (s_abort) {
+    atomicOr(ctl, 1);
+    if (copy_pending) (void)mbar_wait(&bar, parity ^ 1u);  // let an outstanding copy land
   }
 }
 
@@ -217,8 +265,8 @@ int ensure_device(lpf_paths* p, size_t packed_words) {
     return LPF_EINVAL;  // handle is bound to another device
   }
   if (!p->d_status) {
-    if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return set_cuda_error(e);
-    if ((e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMalloc(&p->d_status, 4 * sizeof(int))) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemset(p->d_status, 0, 4 * sizeof(int))) != cudaSuccess) return set_cuda_error(e);
   }
   if (packed_words > p->packed_cap) {
     if (p->d_packed) {
@@ -249,13 +297,14 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
     const uint32_t h = w[i];
     out[i++] = h;
     if (h & kEmit) { out[i] = w[i]; ++i; }
+    while (i % 4) { out[i] = w[i]; ++i; }  // alignment padding
     const uint32_t n = h & kNpixMask;
     for (uint32_t k = 0; k < n; ++k, ++i) {
       const int node = (int)w[i];
       const int sx = np[2 * node], sy = np[2 * node + 1];
       const int sxp = sx + g.r32;              // >= 0
       const uint32_t off = (uint32_t)(sy * g.S + (sxp >> 5));
-      out[i] = (off << 5) | (uint32_t)(sxp & 31);
+      out[i] = (off << 7) | (uint32_t)(sxp & 31);  // word offset << 7 | funnel shift
     }
   }
   cudaError_t e;
@@ -301,8 +350,28 @@ static void set_kernel_attributes() {
   g_attr_status = rc;
 }
 
+static int g_num_sms = 0;
+
+template <int T>
+static int walk_blocks(const Geometry& g) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<T>, 32 * g.G * g.BB,
+                                                                g.band_bytes);
+  if (e != cudaSuccess) return -set_cuda_error(e);
+  return std::max(1, per_sm) * g_num_sms;
+}
+
+template <int T>
+static void launch_walk(const Geometry& g, const Baked& b, lpf_paths* p, unsigned long long* c, int blocks,
+                        cudaStream_t s) {
+  walk_kernel<T><<<blocks, 32 * g.G * g.BB, g.band_bytes, s>>>(
+      p->d_packed, g.H, g.W, g.S, g.nw, g.G, g.BB, g.band_bytes, g.nbg, b.n_pieces, b.d_words, b.d_piece, c,
+      p->host.n_full, p->host.base, p->d_status);
+}
+
+// Enqueue one full evaluation with launch shape (T, BB) (<= 0: tuned or default).
 static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* counts, cudaStream_t s,
-                    bool standard) {
+                    bool standard, int T = 0, int BB = 0) {
   if (!p || !img || !counts) return LPF_EINVAL;
   if (H < 1 || W < 1 || H > 8192 || W > 8192) return LPF_EINVAL;
   if (p->host.rx >= W || p->host.ry >= H) return LPF_EINVAL;
@@ -310,8 +379,11 @@ static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* cou
   if (prog.stack_depth > kDevStack) return LPF_EUNSUPPORTED;
   std::call_once(g_attr_once, set_kernel_attributes);
   if (g_attr_status) return g_attr_status;
+  if (T <= 0)
+    for (const Tuned& t : p->tuned)
+      if (t.H == H && t.W == W) { T = t.T; BB = t.BB; }
   Geometry g;
-  int rc = make_geometry(H, W, p->host.rx, p->host.ry, 0, g);
+  int rc = make_geometry(H, W, p->host.rx, p->host.ry, T, BB, g);
   if (rc) return rc;
   if ((int)g.band_bytes > g_max_dyn_smem) return LPF_EUNSUPPORTED;
   rc = ensure_device(p, g.packed_words);
@@ -319,35 +391,93 @@ static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* cou
   Baked& b = standard ? p->plain : p->tree;
   rc = bake(p, prog, g, b);
   if (rc) return rc;
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return set_cuda_error(e);
+  }
+  int blocks = 0;
+  switch (g.T) {
+    case 1: blocks = walk_blocks<1>(g); break;
+    case 2: blocks = walk_blocks<2>(g); break;
+    case 4: blocks = walk_blocks<4>(g); break;
+    default: blocks = walk_blocks<8>(g); break;
+  }
+  if (blocks < 0) return -blocks;
+  blocks = std::min(blocks, g.nbg * b.n_pieces);
   (void)cudaGetLastError();  // clear a stale error left by earlier, unrelated calls
 
   const int64_t n_full = p->host.n_full, base = p->host.base;
   cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * n_full, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status + 1, 0, sizeof(int), s);  // work counter
   if (e != cudaSuccess) return set_cuda_error(e);
   {
     const int64_t total = (int64_t)g.rows * g.S;
-    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-    pack_rows_kernel<<<blocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, p->d_packed);
+    const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    pack_rows_kernel<<<pblocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, p->d_packed);
   }
-  {
-    dim3 grid(g.nbands, b.n_pieces);
-    dim3 block(32 * g.G);
-    unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
-    if (p->ev_start) cudaEventRecord(p->ev_start, s);
-    switch (g.T) {
-      case 1: walk_kernel<1><<<grid, block, g.band_bytes, s>>>(p->d_packed, H, W, g.S, g.ry, g.nw, g.band_bytes, b.d_words, b.d_piece, c, n_full, base, p->d_status); break;
-      case 2: walk_kernel<2><<<grid, block, g.band_bytes, s>>>(p->d_packed, H, W, g.S, g.ry, g.nw, g.band_bytes, b.d_words, b.d_piece, c, n_full, base, p->d_status); break;
-      case 4: walk_kernel<4><<<grid, block, g.band_bytes, s>>>(p->d_packed, H, W, g.S, g.ry, g.nw, g.band_bytes, b.d_words, b.d_piece, c, n_full, base, p->d_status); break;
-      default: walk_kernel<8><<<grid, block, g.band_bytes, s>>>(p->d_packed, H, W, g.S, g.ry, g.nw, g.band_bytes, b.d_words, b.d_piece, c, n_full, base, p->d_status); break;
-    }
-    if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
+  unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
+  if (p->ev_start) cudaEventRecord(p->ev_start, s);
+  switch (g.T) {
+    case 1: launch_walk<1>(g, b, p, c, blocks, s); break;
+    case 2: launch_walk<2>(g, b, p, c, blocks, s); break;
+    case 4: launch_walk<4>(g, b, p, c, blocks, s); break;
+    default: launch_walk<8>(g, b, p, c, blocks, s); break;
   }
+  if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
   if (n_full > 1) {
     const int64_t n = 2 * (n_full - base - 1);
-    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-    mirror_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<unsigned long long*>(counts), n_full, base);
+    const int mblocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    mirror_kernel<<<mblocks, 256, 0, s>>>(c, n_full, base);
   }
   return cuda_status(cudaGetLastError());
+}
+
+// Time every admissible (T, BB) for this image size and keep the fastest.
+static int autotune_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* counts, cudaStream_t s,
+                         int* bestT, int* bestBB) {
+  const int nw = (W + 31) / 32;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LPF_ECUDA;
+  float best = 1e30f;
+  int bt = 0, bb = 0;
+  int rc = LPF_OK;
+  for (int T : {1, 2, 4, 8}) {
+    if (T > 1 && (T / 2) >= nw) continue;          // more words per thread than a row has
+    for (int BB : {1, 2, 4, 8}) {
+      Geometry g;
+      if (make_geometry(H, W, p->host.rx, p->host.ry, T, BB, g) != LPF_OK) continue;
+      if (g.T != T || g.BB != BB) continue;         // shape not admissible as asked
+      if ((int)g.band_bytes > g_max_dyn_smem && g_max_dyn_smem > 0) continue;
+      rc = run_full(img, H, W, p, counts, s, false, T, BB);  // warm-up (uploads tables)
+      if (rc) break;
+      float t_min = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, s);
+        rc = run_full(img, H, W, p, counts, s, false, T, BB);
+        cudaEventRecord(e1, s);
+        if (rc) break;
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t_min = std::min(t_min, ms);
+      }
+      if (rc) break;
+      if (t_min < best) { best = t_min; bt = T; bb = BB; }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (bt == 0) return LPF_EUNSUPPORTED;
+  for (Tuned& t : p->tuned)
+    if (t.H == H && t.W == W) { t.T = bt; t.BB = bb; bt = -bt; break; }
+  if (bt > 0) p->tuned.push_back({H, W, bt, bb});
+  if (bestT) *bestT = std::abs(bt);
+  if (bestBB) *bestBB = bb;
+  return LPF_OK;
 }
 
 }  // namespace lpf
@@ -450,6 +580,31 @@ int lpf_full(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, int
 int lpf_full_standard(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, int64_t* counts_dev,
                       lpf_stream_t stream) {
   return lpf::run_full(img_dev, H, W, paths, counts_dev, (cudaStream_t)stream, true);
+}
+
+int lpf_autotune_full(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, int64_t* counts_dev,
+                      lpf_stream_t stream, int32_t* best_T, int32_t* best_BB) {
+  if (!paths) return LPF_EINVAL;
+  cudaEvent_t a = paths->ev_start, b = paths->ev_stop;
+  paths->ev_start = paths->ev_stop = nullptr;
+  const int rc = lpf::autotune_full(img_dev, H, W, paths, counts_dev, (cudaStream_t)stream, best_T, best_BB);
+  paths->ev_start = a;
+  paths->ev_stop = b;
+  return rc;
+}
+
+int lpf_set_launch_shape(lpf_paths* p, int32_t H, int32_t W, int32_t T, int32_t BB) {
+  if (!p || H < 1 || W < 1) return LPF_EINVAL;
+  if (T != 1 && T != 2 && T != 4 && T != 8) return LPF_EINVAL;
+  if (BB < 1 || BB > 16) return LPF_EINVAL;
+  lpf::Geometry g;
+  const int rc = lpf::make_geometry(H, W, p->host.rx, p->host.ry, T, BB, g);
+  if (rc) return rc;
+  if (g.T != T || g.BB != std::min<int>(BB, g.nbands)) return LPF_EUNSUPPORTED;
+  for (lpf::Tuned& t : p->tuned)
+    if (t.H == H && t.W == W) { t.T = T; t.BB = BB; return LPF_OK; }
+  p->tuned.push_back({H, W, T, BB});
+  return LPF_OK;
 }
 
 int lpf_paths_set_timer(lpf_paths* p, void* ev_start, void* ev_stop) {

@@ -318,11 +318,37 @@ int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err
     }
   }
   split_program(p, plain, n_pieces);
+  align_program(tree);
+  align_program(plain);
 
   p.node_parent = std::move(t.parent);
   p.node_pix = std::move(t.pix);
   p.node_vec = std::move(t.vec);
   return 0;
+}
+
+// Re-lay a program so that every record's pixel list starts on a 16-byte
+// boundary (words after the header/vec id are padded with zeros up to the
+// next multiple of 4), which lets the kernels fetch pixel words four at a
+// time.  Piece offsets are remapped.
+void align_program(Program& prog) {
+  std::vector<uint32_t> out;
+  out.reserve(prog.words.size() + prog.words.size() / 4);
+  std::vector<int64_t> remap_from, remap_to;
+  size_t pi = 0;
+  std::vector<int64_t> new_begin(prog.piece_begin.size(), 0);
+  for (size_t i = 0; i < prog.words.size();) {
+    while (pi < prog.piece_begin.size() && prog.piece_begin[pi] == (int64_t)i) new_begin[pi++] = (int64_t)out.size();
+    const uint32_t h = prog.words[i++];
+    out.push_back(h);
+    if (h & kEmit) out.push_back(prog.words[i++]);
+    while (out.size() % 4) out.push_back(0);
+    const uint32_t n = h & kNpixMask;
+    for (uint32_t k = 0; k < n; ++k) out.push_back(prog.words[i++]);
+  }
+  while (pi < prog.piece_begin.size()) new_begin[pi++] = (int64_t)out.size();
+  prog.words.swap(out);
+  prog.piece_begin.swap(new_begin);
 }
 
 void split_program(const Paths&, Program& prog, int n_pieces) {

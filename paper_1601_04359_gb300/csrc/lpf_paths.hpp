@@ -16,7 +16,8 @@
 
 namespace lpf {
 
-// Record header word (int32) of a program; pixel words follow it.
+// Record header word (int32) of a program; an optional vector id follows it,
+// then zero padding up to the next multiple of 4 words, then the pixel words.
 //   bits  0..13  number of pixel words that follow (n_pix)
 //   bit   14     emit: count the mask into vector `vec` (next word)
 //   bit   15     restore: mask <- stack[rlevel] before the pixels
@@ -72,5 +73,7 @@ int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err
 
 // Split a program into pieces of similar pixel count; fills piece tables.
 void split_program(const Paths& p, Program& prog, int n_pieces);
+// Pad records so that pixel lists start on 16-byte boundaries.
+void align_program(Program& prog);
 
 }  // namespace lpf

@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <string>
+#include <vector>
 
 #include "../../include/lpf.h"
 #include "lpf_paths.hpp"
@@ -18,16 +19,24 @@ struct Geometry {
   int H = 0, W = 0, rx = 0, ry = 0;
   int nw = 0;      // words holding the W translations of a row
   int T = 0;       // words per thread
-  int G = 0;       // warps per block (word groups), G*T >= nw
+  int G = 0;       // warps per band (word groups), G*T >= nw
+  int BB = 0;      // 32-row bands per block
+  int nbg = 0;     // block-band groups = ceil(nbands / BB)
   int r32 = 0;     // rx rounded up to a multiple of 32
   int S = 0;       // words per packed row (odd, so that 32 rows hit 32 banks)
   int nbands = 0;  // 32-row bands of translations
-  int rows = 0;    // packed rows = 32*nbands + ry
-  uint32_t band_bytes = 0;   // shared memory of one band's rows (multiple of 16)
+  int rows = 0;    // packed rows = 32*BB*nbg + ry
+  uint32_t band_bytes = 0;   // shared memory of one block's rows (multiple of 16)
   size_t packed_words = 0;   // rows*S plus padding for the last band's bulk copy
 };
 
-int make_geometry(int H, int W, int rx, int ry, int T, Geometry& g);
+// T, BB <= 0 pick defaults.
+int make_geometry(int H, int W, int rx, int ry, int T, int BB, Geometry& g);
+
+// Walk-kernel launch shape chosen for one image size (by lpf_autotune_full).
+struct Tuned {
+  int H = 0, W = 0, T = 0, BB = 0;
+};
 
 // A program with its pixel words converted to packed offsets for one width.
 struct Baked {
@@ -54,7 +63,8 @@ struct lpf_paths {
   lpf::Baked tree, plain;
   uint32_t* d_packed = nullptr;  // work area: packed image (one at a time)
   size_t packed_cap = 0;         // words
-  int* d_status = nullptr;       // bounded-wait timeouts since the last check
+  int* d_status = nullptr;       // [0] status flags since the last check, [1] work counter
+  std::vector<lpf::Tuned> tuned; // autotuned walk launch shapes
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;  // optional kernel timer
   lpf::DeltaTables delta;
   float* d_partial = nullptr;    // work area: per (candidate, chunk) error changes

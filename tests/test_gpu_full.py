@@ -89,3 +89,31 @@ def test_invalid_window_raises(gpu_lib):
     img = torch.zeros((32, 32), dtype=torch.uint8, device="cuda")
     with pytest.raises(gpu_lib.LpfError):
         gpu_lib.lpf_full(img, p)
+
+
+def test_every_launch_shape(gpu_lib):
+    # Each admissible (words per thread, bands per block) shape gives the same counts.
+    img = synth.ellipses(100, 300, 0.35, seed=11)
+    rx, ry = 60, 45
+    ref = oracle.lpf_full(img, rx, ry)
+    d = torch.from_numpy(img).cuda()
+    tried = 0
+    for T in (1, 2, 4, 8):
+        for BB in (1, 2, 4):
+            p = gpu_lib.lpf_build_paths(rx, ry)
+            try:
+                gpu_lib.lpf_set_launch_shape(p, 100, 300, T, BB)
+            except gpu_lib.LpfError:
+                continue
+            np.testing.assert_array_equal(gpu_lib.lpf_full(d, p).cpu().numpy(), ref, err_msg=f"T={T} BB={BB}")
+            tried += 1
+    assert tried >= 8
+
+
+def test_autotune_then_full(gpu_lib):
+    img = synth.config1_image()
+    p = gpu_lib.lpf_build_paths(32, 32)
+    d = torch.from_numpy(img).cuda()
+    T, BB = gpu_lib.lpf_autotune_full(d, p)
+    assert T in (1, 2, 4, 8) and BB >= 1
+    np.testing.assert_array_equal(gpu_lib.lpf_full(d, p).cpu().numpy(), oracle.lpf_full(img, 32, 32))
