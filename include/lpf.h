@@ -189,6 +189,84 @@ int lpf_delta_swap(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *path
                    const float *target_dev, const int64_t *counts_dev, float *de_dev,
                    lpf_stream_t stream);
 
+/* ---- Simulated annealing (Sec. 4, Alg. 3) on exact lineal path counts ---- */
+
+typedef struct lpf_sa lpf_sa; /* opaque annealer state, owned by the library */
+
+typedef struct {
+  int64_t n_step;      /* swap evaluations in the whole run (N_step) */
+  int64_t c_max;       /* attempts per temperature stage */
+  int64_t s_max;       /* acceptances per temperature stage */
+  double t_max;        /* initial temperature; <= 0: chosen so that an average
+                          uphill move of the initial image is accepted with
+                          probability 1/2 (the paper tunes it by hand for s/c ~ 0.5) */
+  double t_min_ratio;  /* T_min / T_max (Tab. annealing: 0.01) */
+  int32_t k_max;       /* candidates per batch, upper bound (e.g. 4096) */
+  int32_t k_min;       /* candidates per batch, lower bound (e.g. 32) */
+  uint64_t seed;       /* Philox-4x32-10 key of the run */
+} lpf_sa_params;
+
+typedef struct {
+  int64_t n_eval;        /* swap evaluations consumed (as a sequential annealer counts them) */
+  int64_t n_accept;      /* accepted swaps */
+  int64_t n_batches;     /* batches run */
+  int64_t n_candidates;  /* candidates evaluated on the GPU, including those discarded
+                            after an earlier acceptance in the same batch */
+  double temperature;    /* current T */
+  double error;          /* current Eq. (LSE) error (running sum of accepted changes) */
+  double t_max;          /* initial temperature actually used */
+  int32_t next_batch;    /* candidates the next batch will evaluate */
+  int32_t done;          /* 1 once n_eval reached n_step (or no swap is possible) */
+} lpf_sa_stats;
+
+/*
+ * Start an annealing run on the cell cell_dev (H*W uint8, 0/1, modified in
+ * place by later lpf_sa_run calls; the caller supplies the random initial
+ * image with the wanted volume fraction, Alg. 3 create_random_image).
+ * target_dev: float [2][n_vec_full] target descriptor (counts of the original
+ * divided by its area, e.g. from lpf_full on the original with the same
+ * window: the descriptor cut of Sec. 6).  counts_dev: int64 [2][n_vec_full],
+ * filled here with the cell's counts and kept current by the run.  The
+ * paths window must satisfy the lpf_delta_swap limits.  Candidate n of the
+ * run (n = 0, 1, ...) is an interfacial phase-1 / phase-0 pixel pair drawn
+ * with Philox-4x32-10 (counter n, key seed) from the then-current cell, and
+ * its Metropolis uniform comes from the same draw, so the run equals the
+ * sequential annealer step for step whatever the batch sizes.
+ * Synchronises `stream`; allocates the run's device buffers.
+ * Errors: LPF_EINVAL, LPF_EUNSUPPORTED, LPF_ENOMEM, LPF_ECUDA.
+ */
+int lpf_sa_create(uint8_t *cell_dev, int32_t H, int32_t W, lpf_paths *paths,
+                  const float *target_dev, int64_t *counts_dev, const lpf_sa_params *params,
+                  lpf_stream_t stream, lpf_sa **out);
+
+/*
+ * Enqueue n_batches annealing batches on `stream` without synchronising:
+ * each batch proposes the next k candidates, evaluates all of them with the
+ * swap-delta kernel, accepts the first that passes the Metropolis test
+ * (Delta e <= 0 or U < exp(-Delta e / T)), applies it to the cell and the
+ * counts, and updates the temperature stage; k adapts to the acceptance
+ * rate between k_min and k_max.  Batches after the run is done do nothing.
+ * The first call with n_batches >= 8 captures 8 batches as a CUDA graph,
+ * replayed afterwards.  Errors: LPF_EINVAL, LPF_ECUDA.
+ */
+int lpf_sa_run(lpf_sa *sa, int32_t n_batches, lpf_stream_t stream);
+
+/* Synchronise `stream` and copy the run's counters to *out. */
+int lpf_sa_read(lpf_sa *sa, lpf_sa_stats *out, lpf_stream_t stream);
+
+/* Recompute the error from the exact counts in double precision, store it
+ * as the run's current error and return it in *e (may be NULL). Synchronises. */
+int lpf_sa_recompute_error(lpf_sa *sa, double *e, lpf_stream_t stream);
+
+/* The next k candidates the run would draw from its current state
+ * (pairs_dev int32 [k][2]: phase-1 pixel, phase-0 pixel; u_dev float [k]
+ * Metropolis uniforms), without advancing the run.  k <= k_max.
+ * Synchronises.  For inspection and tests. */
+int lpf_sa_propose(lpf_sa *sa, int32_t k, int32_t *pairs_dev, float *u_dev, lpf_stream_t stream);
+
+/* Release a run (NULL is ignored); synchronises the device. */
+void lpf_sa_free(lpf_sa *sa);
+
 /*
  * Measurement hook: when ev_start/ev_stop (cudaEvent_t, created by the
  * caller) are non-NULL, every later device call on this handle records

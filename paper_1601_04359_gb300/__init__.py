@@ -19,10 +19,29 @@ __all__ = [
     "load", "LpfError", "Paths", "lpf_build_paths", "lpf_paths_info", "lpf_paths_export",
     "lpf_paths_stats", "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer",
     "lpf_delta_swap", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror",
+    "SaParams", "SaStats", "Annealer", "lpf_sa_create", "lpf_sa_run", "lpf_sa_read", "lpf_sa_recompute_error",
+    "lpf_sa_propose",
 ]
 
 _lib = None
 LIB_PATH = _build.LIB
+
+
+class SaParams(ctypes.Structure):
+    """lpf_sa_params of include/lpf.h."""
+    _fields_ = [("n_step", ctypes.c_int64), ("c_max", ctypes.c_int64), ("s_max", ctypes.c_int64),
+                ("t_max", ctypes.c_double), ("t_min_ratio", ctypes.c_double), ("k_max", ctypes.c_int32),
+                ("k_min", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class SaStats(ctypes.Structure):
+    """lpf_sa_stats of include/lpf.h."""
+    _fields_ = [("n_eval", ctypes.c_int64), ("n_accept", ctypes.c_int64), ("n_batches", ctypes.c_int64),
+                ("n_candidates", ctypes.c_int64), ("temperature", ctypes.c_double), ("error", ctypes.c_double),
+                ("t_max", ctypes.c_double), ("next_batch", ctypes.c_int32), ("done", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class LpfError(RuntimeError):
@@ -61,6 +80,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_delta_swap": (ctypes.c_int, [p, i32, i32, p, p, i32, p, p, p, p, p]),
         "lpf_autotune_full": (ctypes.c_int, [p, i32, i32, p, p, p, P32, P32]),
         "lpf_set_launch_shape": (ctypes.c_int, [p, i32, i32, i32, i32]),
+        "lpf_sa_create": (ctypes.c_int, [p, i32, i32, p, p, p, ctypes.POINTER(SaParams), p, ctypes.POINTER(p)]),
+        "lpf_sa_run": (ctypes.c_int, [p, i32, p]),
+        "lpf_sa_read": (ctypes.c_int, [p, ctypes.POINTER(SaStats), p]),
+        "lpf_sa_recompute_error": (ctypes.c_int, [p, ctypes.POINTER(ctypes.c_double), p]),
+        "lpf_sa_propose": (ctypes.c_int, [p, i32, p, p, p]),
+        "lpf_sa_free": (None, [p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -209,6 +234,62 @@ def lpf_paths_set_timer(paths: Paths, ev_start=None, ev_stop=None):
     a = ev_start.cuda_event if ev_start is not None else None
     b = ev_stop.cuda_event if ev_stop is not None else None
     _check(load().lpf_paths_set_timer(paths.handle, a, b), "lpf_paths_set_timer")
+
+
+class Annealer:
+    """Owning wrapper of an lpf_sa* run (keeps its device buffers alive)."""
+
+    def __init__(self, handle, cell, paths, target, counts):
+        self.handle = handle
+        self.cell, self.paths, self.target, self.counts = cell, paths, target, counts
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.lpf_sa_free(h)
+            self.handle = None
+
+
+def lpf_sa_create(cell, paths: Paths, target, counts=None, n_step=1_000_000, c_max=None, s_max=None,
+                  t_max=0.0, t_min_ratio=0.01, k_max=4096, k_min=32, seed=1, stream=None) -> Annealer:
+    """Start an annealing run on the CUDA uint8 cell (modified in place)."""
+    import torch
+    H, W = cell.shape
+    if counts is None:
+        counts = torch.empty((2, paths.n_full), dtype=torch.int64, device=cell.device)
+    prm = SaParams(int(n_step), int(c_max if c_max is not None else max(1, n_step // 10)),
+                   int(s_max if s_max is not None else max(1, n_step // 100)), float(t_max), float(t_min_ratio),
+                   int(k_max), int(k_min), int(seed))
+    h = ctypes.c_void_p()
+    _check(load().lpf_sa_create(_dev_ptr(cell, "uint8", "cell"), H, W, paths.handle,
+                                _dev_ptr(target, "float32", "target"), _dev_ptr(counts, "int64", "counts"),
+                                ctypes.byref(prm), _stream_ptr(stream), ctypes.byref(h)), "lpf_sa_create")
+    return Annealer(h.value, cell, paths, target, counts)
+
+
+def lpf_sa_run(sa: Annealer, n_batches: int, stream=None):
+    _check(load().lpf_sa_run(sa.handle, int(n_batches), _stream_ptr(stream)), "lpf_sa_run")
+
+
+def lpf_sa_read(sa: Annealer, stream=None) -> dict:
+    st = SaStats()
+    _check(load().lpf_sa_read(sa.handle, ctypes.byref(st), _stream_ptr(stream)), "lpf_sa_read")
+    return st.as_dict()
+
+
+def lpf_sa_recompute_error(sa: Annealer, stream=None) -> float:
+    e = ctypes.c_double()
+    _check(load().lpf_sa_recompute_error(sa.handle, ctypes.byref(e), _stream_ptr(stream)), "lpf_sa_recompute_error")
+    return e.value
+
+
+def lpf_sa_propose(sa: Annealer, k: int, stream=None):
+    import torch
+    pairs = torch.empty((k, 2), dtype=torch.int32, device=sa.cell.device)
+    u = torch.empty(k, dtype=torch.float32, device=sa.cell.device)
+    _check(load().lpf_sa_propose(sa.handle, int(k), pairs.data_ptr(), u.data_ptr(), _stream_ptr(stream)),
+           "lpf_sa_propose")
+    return pairs, u
 
 
 def lpf_paths_status(paths: Paths, stream=None) -> int:

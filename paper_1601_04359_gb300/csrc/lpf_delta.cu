@@ -61,7 +61,7 @@ __device__ void mark_copies(uint8_t* sm, int c, uint8_t val, int H, int W, int W
 __global__ void __launch_bounds__(kDeltaThreads) delta_kernel(
     const uint8_t* __restrict__ img, int H, int W, int rx, int ry, int We, int He,
     const int32_t* __restrict__ dptr, const int32_t* __restrict__ doff, const int32_t* __restrict__ chunk,
-    int n_chunks, const int32_t* __restrict__ pairs, int K, const int32_t* __restrict__ k_dev, int KC,
+    int n_chunks, const int32_t* __restrict__ pairs, int K, const int32_t* __restrict__ k_dev,
     int32_t* __restrict__ dcounts, int64_t n_canon, const float* __restrict__ target,
     const int64_t* __restrict__ counts, int64_t n_full, int64_t base, float* __restrict__ partial,
     int* __restrict__ status) {
@@ -71,8 +71,7 @@ __global__ void __launch_bounds__(kDeltaThreads) delta_kernel(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ch = blockIdx.x;
   const int Keff = k_dev ? min(K, *k_dev) : K;
-  const int k0 = blockIdx.y * KC;
-  if (k0 >= Keff) return;
+  if ((int)blockIdx.y >= Keff) return;
 
   // extended cell: sm[ey*We + ex] = img[(ey - ry) mod H][(ex - rx) mod W]
   const int total = We * He;
@@ -88,7 +87,7 @@ __global__ void __launch_bounds__(kDeltaThreads) delta_kernel(
   const float invN = 1.0f / ((float)H * (float)W);
   const int npix = H * W;
 
-  for (int k = k0; k < min(k0 + KC, Keff); ++k) {
+  for (int k = blockIdx.y; k < Keff; k += gridDim.y) {
     if (threadIdx.x == 0) {
       int a = pairs[2 * k], b = pairs[2 * k + 1];
       int skip = 0;
@@ -268,15 +267,19 @@ int delta_launch(const uint8_t* img, int H, int W, lpf_paths* p, const int32_t* 
                  float* partial, cudaStream_t s) {
   const DeltaGeom g = delta_geom(H, W, p->host.rx, p->host.ry);
   const int n_chunks = p->delta.n_chunks;
-  // candidates per block: enough blocks to fill the GPU several times over
-  const int target_blocks = 152 * 8;
-  int KC = std::max(1, (K * n_chunks + target_blocks - 1) / target_blocks);
-  KC = std::min(KC, 16);
-  dim3 grid(n_chunks, (K + KC - 1) / KC);
+  // blocks stride over the candidates: enough of them to fill every SM a few
+  // times whatever the (possibly device-side) number of candidates
+  int sms = 152;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int per_chunk = std::max(1, (sms * 8 + n_chunks - 1) / n_chunks);
+  dim3 grid(n_chunks, std::min(K, per_chunk));
   if (p->ev_start) cudaEventRecord(p->ev_start, s);
   delta_kernel<<<grid, kDeltaThreads, g.smem, s>>>(
       img, H, W, p->host.rx, p->host.ry, g.We, g.He, p->delta.d_dptr, p->delta.d_doff, p->delta.d_chunk, n_chunks,
-      pairs, K, k_dev, KC, dcounts, p->host.n_canon, target, counts, p->host.n_full, p->host.base,
+      pairs, K, k_dev, dcounts, p->host.n_canon, target, counts, p->host.n_full, p->host.base,
       de ? partial : nullptr, p->d_status);
   if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
   if (de) {

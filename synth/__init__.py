@@ -128,6 +128,15 @@ def random_binary(H: int, W: int, fraction: float, seed: int) -> np.ndarray:
     return (rng.random((H, W)) < fraction).astype(np.uint8)
 
 
+def exact_fraction_shuffle(H: int, W: int, n_ones: int, seed: int) -> np.ndarray:
+    """Random image with exactly n_ones phase-1 pixels, uniformly placed (the
+    annealer's random initial image with the original's volume fraction)."""
+    rng = np.random.default_rng(seed)
+    flat = np.zeros(H * W, np.uint8)
+    flat[rng.choice(H * W, size=n_ones, replace=False)] = 1
+    return flat.reshape(H, W)
+
+
 # ---- the named workloads ---------------------------------------------------
 
 def config1_image() -> np.ndarray:
