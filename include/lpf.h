@@ -189,6 +189,55 @@ int lpf_delta_swap(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *path
                    const float *target_dev, const int64_t *counts_dev, float *de_dev,
                    lpf_stream_t stream);
 
+/* ---- Many independent images in one persistent launch ---- */
+
+typedef struct lpf_batch lpf_batch; /* opaque, owned by the library */
+
+/*
+ * Prepare a batch: n_img images of possibly different sizes, each with its
+ * own paths handle (its own window), evaluated together as in lpf_full.
+ * Host arrays of n_img entries: imgs_dev[i] device pointer to H[i]*W[i]
+ * uint8 (0/1), paths[i] handle (a handle may serve several images only if
+ * they have the same H and W), counts_dev[i] device pointer to int64
+ * [2][n_vec_full of paths[i]].  The pointers are bound to the batch: later
+ * runs read the images' current contents and overwrite the counts.
+ * words_per_thread: NULL (cost model) or n_img values in {1,2,4,8} (the
+ * walk kernel's words per thread for each image; each image's row words
+ * must split into 1, 2, 4 or 8 warp groups).  Uploads the programs and
+ * allocates the batch's work area (synchronous).
+ * Errors: LPF_EINVAL, LPF_EUNSUPPORTED, LPF_ENOMEM, LPF_ECUDA.
+ */
+int lpf_batch_create(int32_t n_img, const uint8_t *const *imgs_dev, const int32_t *H,
+                     const int32_t *W, lpf_paths *const *paths, int64_t *const *counts_dev,
+                     const int32_t *words_per_thread, lpf_batch **out);
+
+/*
+ * Enqueue one evaluation of every image of the batch: four kernel launches
+ * (zero counts, pack, one persistent walk over a work queue of (image, band
+ * group, program piece) items, mirror), no host-device copies.  use_graph != 0
+ * captures those launches as a CUDA graph on the first call and replays it.
+ * Errors: LPF_EINVAL, LPF_ECUDA.
+ */
+int lpf_batch_run(lpf_batch *batch, int32_t use_graph, lpf_stream_t stream);
+
+/*
+ * Autotuner for a batch: for each class of images with the same number of
+ * 32-pixel words per row, times every admissible words-per-thread choice on
+ * the whole batch (3 runs each) and keeps the fastest; chosen_T (NULL or
+ * n_img entries) receives the final choice.  The same host arrays as at
+ * creation must be passed.  Synchronous; not for use inside stream capture.
+ */
+int lpf_batch_autotune(lpf_batch *batch, const uint8_t *const *imgs_dev, const int32_t *H,
+                       const int32_t *W, int64_t *const *counts_dev, lpf_stream_t stream,
+                       int32_t *chosen_T);
+
+/* Synchronise `stream`; LPF_ETIMEOUT if a bounded wait in the batch's walk
+ * kernel gave up during a run so far, else LPF_OK. */
+int lpf_batch_status(lpf_batch *batch, lpf_stream_t stream);
+
+/* Release a batch (NULL is ignored); synchronises the device. */
+void lpf_batch_free(lpf_batch *batch);
+
 /* ---- Simulated annealing (Sec. 4, Alg. 3) on exact lineal path counts ---- */
 
 typedef struct lpf_sa lpf_sa; /* opaque annealer state, owned by the library */

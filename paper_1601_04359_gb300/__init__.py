@@ -20,7 +20,7 @@ __all__ = [
     "lpf_paths_stats", "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer",
     "lpf_delta_swap", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror",
     "SaParams", "SaStats", "Annealer", "lpf_sa_create", "lpf_sa_run", "lpf_sa_read", "lpf_sa_recompute_error",
-    "lpf_sa_propose",
+    "lpf_sa_propose", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune", "lpf_batch_status",
 ]
 
 _lib = None
@@ -80,6 +80,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_delta_swap": (ctypes.c_int, [p, i32, i32, p, p, i32, p, p, p, p, p]),
         "lpf_autotune_full": (ctypes.c_int, [p, i32, i32, p, p, p, P32, P32]),
         "lpf_set_launch_shape": (ctypes.c_int, [p, i32, i32, i32, i32]),
+        "lpf_batch_create": (ctypes.c_int, [i32, p, p, p, p, p, p, ctypes.POINTER(p)]),
+        "lpf_batch_run": (ctypes.c_int, [p, i32, p]),
+        "lpf_batch_autotune": (ctypes.c_int, [p, p, p, p, p, p, p]),
+        "lpf_batch_status": (ctypes.c_int, [p, p]),
+        "lpf_batch_free": (None, [p]),
         "lpf_sa_create": (ctypes.c_int, [p, i32, i32, p, p, p, ctypes.POINTER(SaParams), p, ctypes.POINTER(p)]),
         "lpf_sa_run": (ctypes.c_int, [p, i32, p]),
         "lpf_sa_read": (ctypes.c_int, [p, ctypes.POINTER(SaStats), p]),
@@ -234,6 +239,63 @@ def lpf_paths_set_timer(paths: Paths, ev_start=None, ev_stop=None):
     a = ev_start.cuda_event if ev_start is not None else None
     b = ev_stop.cuda_event if ev_stop is not None else None
     _check(load().lpf_paths_set_timer(paths.handle, a, b), "lpf_paths_set_timer")
+
+
+class Batch:
+    """Owning wrapper of an lpf_batch* (keeps the bound tensors and handles alive)."""
+
+    def __init__(self, handle, imgs, paths, counts, arrays):
+        self.handle = handle
+        self.imgs, self.paths, self.counts = imgs, paths, counts
+        self._arrays = arrays
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.lpf_batch_free(h)
+            self.handle = None
+
+
+def _batch_arrays(imgs, paths, counts):
+    n = len(imgs)
+    ptrs = (ctypes.c_void_p * n)(*[_dev_ptr(t, "uint8", "img") for t in imgs])
+    Hs = (ctypes.c_int32 * n)(*[int(t.shape[0]) for t in imgs])
+    Ws = (ctypes.c_int32 * n)(*[int(t.shape[1]) for t in imgs])
+    hs = (ctypes.c_void_p * n)(*[p.handle for p in paths])
+    cs = (ctypes.c_void_p * n)(*[_dev_ptr(c, "int64", "counts") for c in counts])
+    return ptrs, Hs, Ws, hs, cs
+
+
+def lpf_batch_create(imgs, paths, counts=None, words_per_thread=None) -> Batch:
+    """Bind CUDA uint8 images, their paths handles and int64 count buffers."""
+    import torch
+    if counts is None:
+        counts = [torch.empty((2, p.n_full), dtype=torch.int64, device=t.device) for t, p in zip(imgs, paths)]
+    arrays = _batch_arrays(imgs, paths, counts)
+    wpt = None
+    if words_per_thread is not None:
+        wpt = (ctypes.c_int32 * len(imgs))(*[int(x) for x in words_per_thread])
+    h = ctypes.c_void_p()
+    _check(load().lpf_batch_create(len(imgs), *arrays, wpt, ctypes.byref(h)), "lpf_batch_create")
+    return Batch(h.value, list(imgs), list(paths), counts, arrays)
+
+
+def lpf_batch_run(batch: Batch, use_graph: bool = True, stream=None):
+    _check(load().lpf_batch_run(batch.handle, 1 if use_graph else 0, _stream_ptr(stream)), "lpf_batch_run")
+    return batch.counts
+
+
+def lpf_batch_autotune(batch: Batch, stream=None):
+    n = len(batch.imgs)
+    chosen = (ctypes.c_int32 * n)()
+    ptrs, Hs, Ws, _, cs = batch._arrays
+    _check(load().lpf_batch_autotune(batch.handle, ptrs, Hs, Ws, cs, _stream_ptr(stream), chosen),
+           "lpf_batch_autotune")
+    return list(chosen)
+
+
+def lpf_batch_status(batch: Batch, stream=None) -> int:
+    return int(load().lpf_batch_status(batch.handle, _stream_ptr(stream)))
 
 
 class Annealer:

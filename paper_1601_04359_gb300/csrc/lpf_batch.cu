@@ -1,0 +1,411 @@
+// Batched full lineal path functions of many independent images of uneven
+// sizes in one persistent kernel (the batching form of the evaluation; the
+// paper evaluates one image at a time, Sec. 3.1).
+//
+// Every image brings its own window and program (its own paths handle).  A
+// batch is prepared once (programs uploaded, work area allocated, a device
+// table of per-image descriptors written); a run is then four launches with
+// no host-device copies -- zero the counts, pack every image into bit rows,
+// one persistent walk kernel, fill the mirrored halves -- and can be replayed
+// as a CUDA graph.  The walk kernel pulls work items (image, band group,
+// program piece) from an atomic counter; all blocks have 8 warps, and each
+// image gets its own split of those warps into word groups x bands (G x BB,
+// G*BB = 8) and its own words per thread T, chosen by a waste/load cost model
+// or by the batch autotuner.  A block re-stages its rows (one bulk copy) only
+// when the image or band group changes.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "../../include/lpf.h"
+#include "lpf_device.cuh"
+#include "lpf_state.hpp"
+#include "lpf_walk.cuh"
+
+namespace lpf {
+
+constexpr int kBatchWarps = 8;
+constexpr int kBatchThreads = 32 * kBatchWarps;
+
+struct BatchDesc {
+  const uint8_t* img;
+  unsigned long long* counts;
+  uint32_t* packed;
+  const uint32_t* prog;
+  const int64_t* piece;
+  int64_t n_full, base, item0;
+  int H, W, S, nw, G, BB, T, r32, rows, nbg, n_pieces;
+  uint32_t band_bytes;
+};
+
+__global__ void batch_zero_kernel(const BatchDesc* __restrict__ d) {
+  const BatchDesc& b = d[blockIdx.y];
+  const int64_t n = 2 * b.n_full;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b.counts[i] = 0ull;
+}
+
+__global__ void batch_pack_kernel(const BatchDesc* __restrict__ d) {
+  const BatchDesc& b = d[blockIdx.y];
+  const int64_t total = (int64_t)b.rows * b.S;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(i / b.S), k = (int)(i % b.S);
+    const uint8_t* row = b.img + (int64_t)(y % b.H) * b.W;
+    int x = (32 * k - b.r32) % b.W;
+    if (x < 0) x += b.W;
+    uint32_t bits = 0;
+    for (int bit = 0; bit < 32; ++bit) {
+      bits |= (uint32_t)(row[x] != 0) << bit;
+      if (++x == b.W) x = 0;
+    }
+    b.packed[i] = bits;
+  }
+}
+
+__global__ void batch_mirror_kernel(const BatchDesc* __restrict__ d) {
+  const BatchDesc& b = d[blockIdx.y];
+  const int64_t n = b.n_full - b.base - 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i / n, j = b.base + 1 + i % n;
+    b.counts[p * b.n_full + (b.n_full - 1 - j)] = b.counts[p * b.n_full + j];
+  }
+}
+
+template <int T>
+__device__ __forceinline__ void batch_item(const BatchDesc& b, int bg, int pi, const uint32_t* sm, int warp, int lane) {
+  const int bl = warp / b.G, grp = warp - (warp / b.G) * b.G;
+  if (bl >= b.BB) return;
+  const int y = (bg * b.BB + bl) * 32 + lane;
+  uint32_t valid[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int j = grp * T + t;
+    uint32_t v = 0;
+    if (y < b.H && j < b.nw) {
+      const int rem = b.W - 32 * j;
+      v = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    }
+    valid[t] = v;
+  }
+  const uint32_t* lane_base = sm + (bl * 32 + lane) * b.S + grp * T;
+  walk_piece<T>(b.prog, b.piece[pi], b.piece[pi + 1], lane_base, valid, lane, b.counts, b.n_full, b.base);
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 2) batch_walk_kernel(const BatchDesc* __restrict__ d, int n_img,
+                                                                   int64_t total_items, int* __restrict__ ctl) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int64_t s_item;
+  __shared__ int s_img, s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) { mbar_init(&bar, 1); s_abort = 0; }
+  __syncthreads();
+  uint32_t parity = 0;
+  int cur_img = -1, cur_bg = -1;
+  bool copy_pending = false;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int64_t item = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctl + 2), 1ull);
+      int lo = 0, hi = n_img;  // last image with item0 <= item
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (d[mid].item0 <= item) lo = mid; else hi = mid;
+      }
+      s_item = item;
+      s_img = lo;
+    }
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= total_items) break;
+    const int im = s_img;
+    const BatchDesc& b = d[im];
+    const int64_t local = item - b.item0;
+    const int bg = (int)(local / b.n_pieces), pi = (int)(local - (int64_t)bg * b.n_pieces);
+    if (im != cur_img || bg != cur_bg) {
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar, b.band_bytes);
+        bulk_g2s(sm, b.packed + (size_t)bg * 32 * b.BB * b.S, b.band_bytes, &bar);
+      }
+      copy_pending = true;
+      if (mbar_wait(&bar, parity)) copy_pending = false;
+      else s_abort = 1;
+      parity ^= 1u;
+      cur_img = im;
+      cur_bg = bg;
+      __syncthreads();
+      if (s_abort) break;
+    }
+    switch (b.T) {
+      case 1: batch_item<1>(b, bg, pi, sm, warp, lane); break;
+      case 2: batch_item<2>(b, bg, pi, sm, warp, lane); break;
+      case 4: batch_item<4>(b, bg, pi, sm, warp, lane); break;
+      default: batch_item<8>(b, bg, pi, sm, warp, lane); break;
+    }
+    __syncthreads();
+  }
+  if (s_abort) {
+    atomicOr(ctl, 1);
+    if (copy_pending) (void)mbar_wait(&bar, parity ^ 1u);
+  }
+}
+
+// Cost of a (T) choice for one image when a block has 8 warps split G x BB:
+// translation words covered per useful word, times shared loads per word.
+static double shape_cost(int H, int W, int T) {
+  const int nw = (W + 31) / 32;
+  const int G = (nw + T - 1) / T;
+  if (G > kBatchWarps || kBatchWarps % G) return 1e30;
+  const int BB = kBatchWarps / G;
+  const int nbands = (H + 31) / 32;
+  const int nbg = (nbands + BB - 1) / BB;
+  const double covered = (double)G * T * 32.0 * BB * 32.0 * nbg;
+  const double useful = (double)W * H;
+  return covered / useful * (double)(T + 1) / T;
+}
+
+}  // namespace lpf
+
+struct lpf_batch {
+  int n = 0;
+  std::vector<lpf_paths*> paths;
+  std::vector<lpf::BatchDesc> desc;
+  lpf::BatchDesc* d_desc = nullptr;
+  uint32_t* d_packed = nullptr;
+  int* d_ctl = nullptr;          // [0] status, [2..3] 64-bit work counter
+  int64_t total_items = 0;
+  uint32_t max_band = 0;
+  int blocks = 0;
+  int max_pack = 0, max_full = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace lpf {
+
+static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t* H, const int32_t* W,
+                       int64_t* const* counts, const int32_t* T_choice) {
+  // geometry, programs on the device, work-area layout
+  size_t packed_total = 0;
+  std::vector<size_t> offs(bt->n);
+  bt->desc.assign(bt->n, BatchDesc{});
+  int64_t items = 0;
+  bt->max_band = 0;
+  for (int i = 0; i < bt->n; ++i) {
+    lpf_paths* p = bt->paths[i];
+    if (!p || !imgs[i] || !counts[i]) return LPF_EINVAL;
+    if (H[i] < 1 || W[i] < 1 || H[i] > 8192 || W[i] > 8192) return LPF_EINVAL;
+    if (p->host.rx >= W[i] || p->host.ry >= H[i]) return LPF_EINVAL;
+    if (p->host.tree.stack_depth > kWalkStack) return LPF_EUNSUPPORTED;
+    int T = T_choice ? T_choice[i] : 0;
+    if (T <= 0) {
+      double best = 1e30;
+      for (int t : {1, 2, 4, 8}) {
+        const double c = shape_cost(H[i], W[i], t);
+        if (c < best) { best = c; T = t; }
+      }
+    }
+    const int nw = (W[i] + 31) / 32;
+    const int G = (nw + T - 1) / T;
+    if (G > kBatchWarps || kBatchWarps % G) return LPF_EUNSUPPORTED;
+    Geometry g;
+    int rc = make_geometry(H[i], W[i], p->host.rx, p->host.ry, T, kBatchWarps / G, g);
+    if (rc) return rc;
+    if (g.T != T || g.G != G) return LPF_EUNSUPPORTED;
+    // keep G*BB = 8 even if the image has fewer bands (the extra warps idle)
+    g.BB = kBatchWarps / G;
+    g.nbg = (g.nbands + g.BB - 1) / g.BB;
+    g.rows = 32 * g.BB * g.nbg + g.ry;
+    const size_t band = (size_t)(32 * g.BB + g.ry) * g.S * 4;
+    g.band_bytes = (uint32_t)((band + 15) & ~size_t(15));
+    g.packed_words = (size_t)g.rows * g.S + 4;
+    rc = ensure_device(p, 0);
+    if (rc) return rc;
+    rc = bake(p, p->host.tree, g, p->tree);
+    if (rc) return rc;
+    BatchDesc& d = bt->desc[i];
+    d.img = imgs[i];
+    d.counts = reinterpret_cast<unsigned long long*>(counts[i]);
+    d.prog = p->tree.d_words;
+    d.piece = p->tree.d_piece;
+    d.n_full = p->host.n_full;
+    d.base = p->host.base;
+    d.item0 = items;
+    d.H = g.H; d.W = g.W; d.S = g.S; d.nw = g.nw; d.G = g.G; d.BB = g.BB; d.T = g.T; d.r32 = g.r32;
+    d.rows = g.rows; d.nbg = g.nbg; d.n_pieces = p->tree.n_pieces; d.band_bytes = g.band_bytes;
+    items += (int64_t)g.nbg * d.n_pieces;
+    offs[i] = packed_total;
+    packed_total += (g.packed_words + 3) & ~size_t(3);  // keep every image 16-byte aligned
+    bt->max_band = std::max(bt->max_band, g.band_bytes);
+    bt->max_pack = std::max<int>(bt->max_pack, (int)std::min<int64_t>(((int64_t)g.rows * g.S + 255) / 256, 64));
+    bt->max_full = std::max<int>(bt->max_full, (int)std::min<int64_t>((2 * d.n_full + 255) / 256, 64));
+  }
+  bt->total_items = items;
+  cudaError_t e;
+  if (bt->d_packed) { cudaFree(bt->d_packed); bt->d_packed = nullptr; }
+  if ((e = cudaMalloc(&bt->d_packed, std::max<size_t>(16, packed_total * 4))) != cudaSuccess) return set_cuda_error(e);
+  for (int i = 0; i < bt->n; ++i) bt->desc[i].packed = bt->d_packed + offs[i];
+  if (!bt->d_desc && (e = cudaMalloc(&bt->d_desc, sizeof(BatchDesc) * bt->n)) != cudaSuccess) return set_cuda_error(e);
+  if ((e = cudaMemcpy(bt->d_desc, bt->desc.data(), sizeof(BatchDesc) * bt->n, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return set_cuda_error(e);
+  if (!bt->d_ctl) {
+    if ((e = cudaMalloc(&bt->d_ctl, 4 * sizeof(int))) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemset(bt->d_ctl, 0, 4 * sizeof(int))) != cudaSuccess) return set_cuda_error(e);
+  }
+  int dev = 0, optin = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, batch_walk_kernel)) != cudaSuccess) return set_cuda_error(e);
+  const int max_dyn = optin - (int)fa.sharedSizeBytes;
+  if ((int)bt->max_band > max_dyn) return LPF_EUNSUPPORTED;
+  if ((e = cudaFuncSetAttribute(batch_walk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn)) != cudaSuccess)
+    return set_cuda_error(e);
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_walk_kernel, kBatchThreads, bt->max_band)) !=
+      cudaSuccess)
+    return set_cuda_error(e);
+  bt->blocks = (int)std::min<int64_t>((int64_t)std::max(1, per_sm) * sms, std::max<int64_t>(1, items));
+  if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
+  if (bt->graph) { cudaGraphDestroy(bt->graph); bt->graph = nullptr; }
+  return LPF_OK;
+}
+
+static void batch_enqueue(lpf_batch* bt, cudaStream_t s) {
+  cudaMemsetAsync(bt->d_ctl, 0, 4 * sizeof(int), s);
+  batch_zero_kernel<<<dim3(bt->max_full, bt->n), 256, 0, s>>>(bt->d_desc);
+  batch_pack_kernel<<<dim3(bt->max_pack, bt->n), 256, 0, s>>>(bt->d_desc);
+  batch_walk_kernel<<<bt->blocks, kBatchThreads, bt->max_band, s>>>(bt->d_desc, bt->n, bt->total_items, bt->d_ctl);
+  batch_mirror_kernel<<<dim3(bt->max_full, bt->n), 256, 0, s>>>(bt->d_desc);
+}
+
+}  // namespace lpf
+
+extern "C" {
+
+int lpf_batch_create(int32_t n_img, const uint8_t* const* imgs_dev, const int32_t* H, const int32_t* W,
+                     lpf_paths* const* paths, int64_t* const* counts_dev, const int32_t* words_per_thread,
+                     lpf_batch** out) {
+  if (!out) return LPF_EINVAL;
+  *out = nullptr;
+  if (n_img < 1 || !imgs_dev || !H || !W || !paths || !counts_dev) return LPF_EINVAL;
+  for (int i = 0; i < n_img; ++i)
+    for (int j = 0; j < i; ++j)
+      if (paths[i] == paths[j] && (H[i] != H[j] || W[i] != W[j])) return LPF_EINVAL;  // one program per handle
+  lpf_batch* bt = new (std::nothrow) lpf_batch();
+  if (!bt) return LPF_ENOMEM;
+  bt->n = n_img;
+  bt->paths.assign(paths, paths + n_img);
+  const int rc = lpf::batch_build(bt, imgs_dev, H, W, counts_dev, words_per_thread);
+  if (rc) { lpf_batch_free(bt); return rc; }
+  *out = bt;
+  return LPF_OK;
+}
+
+int lpf_batch_run(lpf_batch* bt, int32_t use_graph, lpf_stream_t stream) {
+  if (!bt) return LPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  (void)cudaGetLastError();
+  if (!use_graph) {
+    lpf::batch_enqueue(bt, s);
+    return lpf::set_cuda_error(cudaGetLastError());
+  }
+  cudaError_t e = cudaSuccess;
+  if (!bt->exec) {
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return lpf::set_cuda_error(e);
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      lpf::batch_enqueue(bt, cs);
+      e = cudaStreamEndCapture(cs, &bt->graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) { bt->exec = nullptr; return lpf::set_cuda_error(e); }
+  }
+  e = cudaGraphLaunch(bt->exec, s);
+  return lpf::set_cuda_error(e);
+}
+
+int lpf_batch_status(lpf_batch* bt, lpf_stream_t stream) {
+  if (!bt) return LPF_EINVAL;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return lpf::set_cuda_error(e);
+  int h = 0;
+  e = cudaMemcpy(&h, bt->d_ctl, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return lpf::set_cuda_error(e);
+  return h ? LPF_ETIMEOUT : LPF_OK;
+}
+
+int lpf_batch_autotune(lpf_batch* bt, const uint8_t* const* imgs_dev, const int32_t* H, const int32_t* W,
+                       int64_t* const* counts_dev, lpf_stream_t stream, int32_t* chosen_T) {
+  // Per image size class (words per row), try every admissible T with the
+  // whole batch and keep the fastest; classes are tuned one after another.
+  if (!bt || !imgs_dev || !H || !W || !counts_dev) return LPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int32_t> T(bt->n);
+  for (int i = 0; i < bt->n; ++i) T[i] = bt->desc[i].T;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto time_it = [&](float& ms_out) -> int {
+    int rc = lpf::batch_build(bt, imgs_dev, H, W, counts_dev, T.data());
+    if (rc) return rc;
+    lpf::batch_enqueue(bt, s);  // warm-up
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      cudaEventRecord(e0, s);
+      lpf::batch_enqueue(bt, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms);
+    }
+    ms_out = best;
+    return lpf::set_cuda_error(cudaGetLastError());
+  };
+  float cur = 0;
+  int rc = time_it(cur);
+  for (int nw = 1; nw <= 256 && !rc; ++nw) {
+    bool present = false;
+    for (int i = 0; i < bt->n; ++i) present |= ((W[i] + 31) / 32 == nw);
+    if (!present) continue;
+    int bestT = -1;
+    for (int t : {1, 2, 4, 8}) {
+      const int G = (nw + t - 1) / t;
+      if (G > lpf::kBatchWarps || lpf::kBatchWarps % G) continue;
+      std::vector<int32_t> keep = T;
+      for (int i = 0; i < bt->n; ++i)
+        if ((W[i] + 31) / 32 == nw) T[i] = t;
+      float ms = 0;
+      rc = time_it(ms);
+      if (rc) break;
+      if (ms < cur) { cur = ms; bestT = t; }
+      else T = keep;
+    }
+    (void)bestT;
+  }
+  if (!rc) rc = lpf::batch_build(bt, imgs_dev, H, W, counts_dev, T.data());
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!rc && chosen_T)
+    for (int i = 0; i < bt->n; ++i) chosen_T[i] = T[i];
+  return rc;
+}
+
+void lpf_batch_free(lpf_batch* bt) {
+  if (!bt) return;
+  cudaDeviceSynchronize();
+  if (bt->exec) cudaGraphExecDestroy(bt->exec);
+  if (bt->graph) cudaGraphDestroy(bt->graph);
+  cudaFree(bt->d_desc);
+  cudaFree(bt->d_packed);
+  cudaFree(bt->d_ctl);
+  delete bt;
+}
+
+}  // extern "C"

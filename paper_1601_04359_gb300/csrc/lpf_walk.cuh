@@ -1,0 +1,111 @@
+// One warp's walk of one program piece over its translation words (the body
+// shared by the single-image and the batched walk kernels).
+//
+// The program is a depth-first walk of the prefix tree of the canonical
+// segments (see lpf_paths.hpp for the record format): every pixel word ANDs
+// one funnel-shifted image word into the phase-1 mask and its complement into
+// the phase-0 mask; emit records count both masks (popc, warp sum, one atomic
+// per phase); push/restore records keep branch masks on a small stack.
+#pragma once
+#include <cstdint>
+
+#include "lpf_device.cuh"
+#include "lpf_paths.hpp"
+
+namespace lpf {
+
+constexpr int kWalkStack = 24;
+
+template <int T>
+__device__ __forceinline__ void walk_and4(const uint32_t* lane_base, uint4 P, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
+  const uint32_t* sa = lane_base + (P.x >> 7);
+  const uint32_t* sb = lane_base + (P.y >> 7);
+  const uint32_t* sc = lane_base + (P.z >> 7);
+  const uint32_t* sd = lane_base + (P.w >> 7);
+  uint32_t wa[T + 1], wb[T + 1], wc[T + 1], wd[T + 1];
+#pragma unroll
+  for (int t = 0; t <= T; ++t) { wa[t] = sa[t]; wb[t] = sb[t]; wc[t] = sc[t]; wd[t] = sd[t]; }
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], P.x);
+    const uint32_t b = __funnelshift_r(wb[t], wb[t + 1], P.y);
+    const uint32_t c = __funnelshift_r(wc[t], wc[t + 1], P.z);
+    const uint32_t d = __funnelshift_r(wd[t], wd[t + 1], P.w);
+    m1[t] = (m1[t] & a & b) & (c & d);
+    m0[t] = (m0[t] & ~(a | b)) & ~(c | d);
+  }
+}
+
+template <int T>
+__device__ __forceinline__ void walk_and1(const uint32_t* lane_base, uint32_t p, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
+  const uint32_t* sa = lane_base + (p >> 7);
+  uint32_t wa[T + 1];
+#pragma unroll
+  for (int t = 0; t <= T; ++t) wa[t] = sa[t];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], p);
+    m1[t] &= a;
+    m0[t] &= ~a;
+  }
+}
+
+// Walk program words [pc, end) for this warp's T words.  lane_base points at
+// the lane's first staged word (row = lane's translation row); valid[t] masks
+// the translations that exist (x < W, row < H).
+template <int T>
+__device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, int64_t pc, int64_t end,
+                                           const uint32_t* lane_base, const uint32_t (&valid)[T], int lane,
+                                           unsigned long long* __restrict__ counts, int64_t n_full,
+                                           int64_t base) {
+  uint32_t m1[T], m0[T];
+  uint32_t st1[kWalkStack][T], st0[kWalkStack][T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
+  while (pc < end) {
+    const uint32_t hdr = __ldg(prog + pc++);
+    if (hdr & kReset) {
+#pragma unroll
+      for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
+    }
+    if (hdr & kRestore) {
+      const int l = (hdr >> kRlevelShift) & kLevelMask;
+#pragma unroll
+      for (int t = 0; t < T; ++t) { m1[t] = st1[l][t]; m0[t] = st0[l][t]; }
+    }
+    int vec = -1;
+    if (hdr & kEmit) vec = (int)__ldg(prog + pc++);
+    pc = (pc + 3) & ~int64_t(3);
+    const int n = (int)(hdr & kNpixMask);
+    const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
+    const int n4 = n >> 2;
+    if (n4 > 0) {
+      uint4 nxt = __ldg(q4);
+      for (int q = 0; q < n4; ++q) {
+        const uint4 cur = nxt;
+        if (q + 1 < n4) nxt = __ldg(q4 + q + 1);
+        walk_and4<T>(lane_base, cur, m1, m0);
+      }
+    }
+    for (int i = n4 * 4; i < n; ++i) walk_and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
+    pc += n;
+    if (vec >= 0) {
+      uint32_t c = 0;
+#pragma unroll
+      for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
+      c = warp_sum(c);
+      if (lane == 0) {
+        const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
+        if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);
+        if (c1) atomicAdd(counts + n_full + base + vec, (unsigned long long)c1);
+      }
+    }
+    if (hdr & kPush) {
+      const int l = (hdr >> kPlevelShift) & kLevelMask;
+#pragma unroll
+      for (int t = 0; t < T; ++t) { st1[l][t] = m1[t]; st0[l][t] = m0[t]; }
+    }
+  }
+}
+
+}  // namespace lpf

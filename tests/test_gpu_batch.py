@@ -1,0 +1,78 @@
+"""Batched evaluation of many images of uneven sizes against the oracle and
+against per-image lpf_full."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _images(n, lo, hi, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        H, W = int(rng.integers(lo, hi + 1)), int(rng.integers(lo, hi + 1))
+        f = float(rng.uniform(0.2, 0.6))
+        s = int(rng.integers(0, 2 ** 31 - 1))
+        out.append([synth.boolean_disks(H, W, 5.0, synth.disks_for_fraction(H, W, 5.0, f), seed=s),
+                    synth.ellipses(H, W, f, seed=s), synth.clustered_disks(H, W, f, seed=s)][i % 3])
+    return out
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_matches_oracle(gpu_lib, use_graph):
+    imgs = _images(10, 33, 100, 3)
+    paths = [gpu_lib.lpf_build_paths(min(W // 2, W - 1), min(H // 2, H - 1)) for H, W in (i.shape for i in imgs)]
+    d = [torch.from_numpy(i).cuda() for i in imgs]
+    b = gpu_lib.lpf_batch_create(d, paths)
+    for _ in range(2):  # a second run on the same batch (graph replay) gives the same counts
+        counts = gpu_lib.lpf_batch_run(b, use_graph=use_graph)
+        torch.cuda.synchronize()
+        assert gpu_lib.lpf_batch_status(b) == 0
+        for img, p, c in zip(imgs, paths, counts):
+            np.testing.assert_array_equal(c.cpu().numpy(), oracle.lpf_full(img, p.rx, p.ry))
+
+
+def test_batch_every_words_per_thread_choice(gpu_lib):
+    imgs = _images(6, 40, 130, 5)
+    paths = [gpu_lib.lpf_build_paths(W // 2, H // 2) for H, W in (i.shape for i in imgs)]
+    d = [torch.from_numpy(i).cuda() for i in imgs]
+    refs = [oracle.lpf_full(img, p.rx, p.ry) for img, p in zip(imgs, paths)]
+    for T in (1, 2, 4, 8):
+        choice = []
+        for img in imgs:
+            nw = (img.shape[1] + 31) // 32
+            G = (nw + T - 1) // T
+            choice.append(T if 8 % G == 0 else 8)
+        b = gpu_lib.lpf_batch_create(d, paths, words_per_thread=choice)
+        counts = gpu_lib.lpf_batch_run(b, use_graph=False)
+        for c, r in zip(counts, refs):
+            np.testing.assert_array_equal(c.cpu().numpy(), r)
+
+
+def test_config4_batch_equals_per_image_and_sampled_oracle(gpu_lib):
+    # 256 images, 48..256 px, windows r = size/2; autotuned; every image equal
+    # to its own lpf_full; a few vectors per image checked by the oracle.
+    imgs = synth.config4_images(256, seed=4)
+    paths = [gpu_lib.lpf_build_paths(W // 2, H // 2) for H, W in (i.shape for i in imgs)]
+    d = [torch.from_numpy(i).cuda() for i in imgs]
+    b = gpu_lib.lpf_batch_create(d, paths)
+    chosen = gpu_lib.lpf_batch_autotune(b)
+    assert set(chosen) <= {1, 2, 4, 8}
+    counts = gpu_lib.lpf_batch_run(b, use_graph=True)
+    torch.cuda.synchronize()
+    assert gpu_lib.lpf_batch_status(b) == 0
+    rng = np.random.default_rng(1)
+    for k, (img, p, c) in enumerate(zip(imgs, paths, counts)):
+        single = gpu_lib.lpf_full(d[k], gpu_lib.lpf_build_paths(p.rx, p.ry))
+        assert torch.equal(c, single), k
+        if k % 16 == 0:
+            vecs = [(int(rng.integers(-p.rx, p.rx + 1)), int(rng.integers(-p.ry, p.ry + 1))) for _ in range(4)]
+            ref = oracle.count_list(img, vecs)
+            cc = c.cpu().numpy()
+            for (dx, dy), r in zip(vecs, ref):
+                kk = oracle.full_index(dx, dy, p.rx, p.ry)
+                assert cc[0, kk] == r[0] and cc[1, kk] == r[1]
