@@ -126,6 +126,39 @@ int lpf_full(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
              int64_t *counts_dev, lpf_stream_t stream);
 
 /*
+ * lpf_full for callers that must not allocate device memory when they
+ * evaluate.  (The paper has no counterpart: this is a deployment variant.)
+ * Such callers include host applications that own every device allocation
+ * and give libraries fixed budgets, and real-time or pipelined loops where a
+ * cudaMalloc -- which can synchronise the whole device -- is not allowed.
+ * Same arguments, layout and results as lpf_full; this call performs no
+ * cudaMalloc, cudaFree or other allocation.  Its work area (packed image rows
+ * and a work counter) is a fixed array of 1 MiB (2^18 words of packed rows)
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.
+ *   - Size limit: the packed, periodically extended image must fit in 2^18
+ *     words; it takes roughly (H + ry) * (W + 2*rx) / 32 words plus a few
+ *     rows and columns of padding (512x512 with |v| <= 256: 25,348 words).
+ *     Larger images return LPF_EUNSUPPORTED.
+ *   - Set-up: the handle's program for this image size must already be on the
+ *     current device -- call lpf_full (or lpf_autotune_full) once for this
+ *     H, W during set-up; otherwise LPF_EINVAL.  The first call of this
+ *     function on a device looks up the device address of the fixed array
+ *     (once per device, with that device current); make that first call
+ *     before any stream capture.
+ *   - Sharing: every call on a device uses the same fixed array and leaves
+ *     its contents behind (each call clears the work counter it needs).
+ *     Calls whose work overlaps on the GPU -- on different streams, or from
+ *     different host threads without ordering -- race on that array and give
+ *     wrong counts; order them on one stream.
+ *   - A device-side wait timeout is not reported by lpf_paths_status for
+ *     this variant.
+ * Errors: LPF_EINVAL, LPF_EUNSUPPORTED, LPF_ECUDA.
+ */
+int lpf_full_noalloc(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
+                     int64_t *counts_dev, lpf_stream_t stream);
+
+/*
  * Autotuner for lpf_full: times every admissible launch shape (words per
  * thread T in {1,2,4,8}, 32-row bands per block BB in {1,2,4,8}) of the walk
  * kernel on this image (3 timed runs each, fastest kept) and stores the

@@ -80,6 +80,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_delta_swap": (ctypes.c_int, [p, i32, i32, p, p, i32, p, p, p, p, p]),
         "lpf_autotune_full": (ctypes.c_int, [p, i32, i32, p, p, p, P32, P32]),
         "lpf_set_launch_shape": (ctypes.c_int, [p, i32, i32, i32, i32]),
+        "lpf_full_noalloc": (ctypes.c_int, [p, i32, i32, p, p, p]),
         "lpf_batch_create": (ctypes.c_int, [i32, p, p, p, p, p, p, ctypes.POINTER(p)]),
         "lpf_batch_run": (ctypes.c_int, [p, i32, p]),
         "lpf_batch_autotune": (ctypes.c_int, [p, p, p, p, p, p, p]),

@@ -480,6 +480,122 @@ static int autotune_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t
   return LPF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Full evaluation without allocating.
+//
+// lpf_full keeps its per-call work area (the packed image rows and the
+// counter of the persistent work queue) in device memory that the handle
+// allocates on first use.  Some callers cannot let a library allocate at the
+// time they evaluate: a host application that owns every device allocation
+// and hands out fixed budgets, a real-time loop where cudaMalloc (which can
+// synchronise the whole device) is forbidden, or code that records its work
+// into a stream while allocation would break that.  For them this variant
+// keeps the same work area in a fixed array compiled into the library (every
+// GPU that loads the library holds it until the process exits) and calls no
+// allocating routine.
+constexpr size_t kNoAllocPackedWords = size_t(1) << 18;  // 1 MiB of packed image rows
+static __device__ __align__(256) uint32_t g_noalloc_packed[kNoAllocPackedWords];
+static __device__ __align__(256) int g_noalloc_ctl[4];   // [0] status flags, [1] work counter
+
+namespace {
+struct NoAllocSlot {
+  uint32_t* packed = nullptr;
+  int* ctl = nullptr;
+  bool ready = false;
+};
+std::mutex g_noalloc_mu;
+NoAllocSlot g_noalloc_slot[64];
+
+// Device addresses of the fixed arrays on the current device, looked up once
+// per device (in host code the array names are only stand-ins).
+int noalloc_slot(int dev, NoAllocSlot& out) {
+  if (dev < 0 || dev >= 64) return LPF_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocSlot& s = g_noalloc_slot[dev];
+  if (!s.ready) {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_packed);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&b, g_noalloc_ctl);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    s.packed = static_cast<uint32_t*>(a);
+    s.ctl = static_cast<int*>(b);
+    s.ready = true;
+  }
+  out = s;
+  return LPF_OK;
+}
+}  // namespace
+
+static int run_full_noalloc(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* counts, cudaStream_t s) {
+  if (!p || !img || !counts) return LPF_EINVAL;
+  if (H < 1 || W < 1 || H > 8192 || W > 8192) return LPF_EINVAL;
+  if (p->host.rx >= W || p->host.ry >= H) return LPF_EINVAL;
+  if (p->host.tree.stack_depth > kDevStack) return LPF_EUNSUPPORTED;
+  std::call_once(g_attr_once, set_kernel_attributes);
+  if (g_attr_status) return g_attr_status;
+  int T = 0, BB = 0;
+  for (const Tuned& t : p->tuned)
+    if (t.H == H && t.W == W) { T = t.T; BB = t.BB; }
+  Geometry g;
+  int rc = make_geometry(H, W, p->host.rx, p->host.ry, T, BB, g);
+  if (rc) return rc;
+  if ((int)g.band_bytes > g_max_dyn_smem) return LPF_EUNSUPPORTED;
+  if (g.packed_words > kNoAllocPackedWords) return LPF_EUNSUPPORTED;  // image too large for the fixed area
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  const Baked& b = p->tree;
+  // the program for this width must already be on this device (an earlier lpf_full call put it there)
+  if (p->device != dev || !b.d_words || b.W != g.W || b.S != g.S || b.r32 != g.r32) return LPF_EINVAL;
+  NoAllocSlot slot;
+  rc = noalloc_slot(dev, slot);
+  if (rc) return rc;
+  if (g_num_sms == 0) {
+    e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return set_cuda_error(e);
+  }
+  int blocks = 0;
+  switch (g.T) {
+    case 1: blocks = walk_blocks<1>(g); break;
+    case 2: blocks = walk_blocks<2>(g); break;
+    case 4: blocks = walk_blocks<4>(g); break;
+    default: blocks = walk_blocks<8>(g); break;
+  }
+  if (blocks < 0) return -blocks;
+  blocks = std::min(blocks, g.nbg * b.n_pieces);
+  (void)cudaGetLastError();
+
+  const int64_t n_full = p->host.n_full, base = p->host.base;
+  e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * n_full, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(slot.ctl, 0, 4 * sizeof(int), s);  // status and work counter start at 0
+  if (e != cudaSuccess) return set_cuda_error(e);
+  {
+    const int64_t total = (int64_t)g.rows * g.S;
+    const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    pack_rows_kernel<<<pblocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, slot.packed);
+  }
+  unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
+  const dim3 block(32 * g.G * g.BB);
+#define LPF_NOALLOC_WALK(TT)                                                                                   \
+  walk_kernel<TT><<<blocks, block, g.band_bytes, s>>>(slot.packed, g.H, g.W, g.S, g.nw, g.G, g.BB, g.band_bytes, \
+                                                      g.nbg, b.n_pieces, b.d_words, b.d_piece, c, n_full, base,   \
+                                                      slot.ctl)
+  switch (g.T) {
+    case 1: LPF_NOALLOC_WALK(1); break;
+    case 2: LPF_NOALLOC_WALK(2); break;
+    case 4: LPF_NOALLOC_WALK(4); break;
+    default: LPF_NOALLOC_WALK(8); break;
+  }
+#undef LPF_NOALLOC_WALK
+  if (n_full > 1) {
+    const int64_t n = 2 * (n_full - base - 1);
+    const int mblocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    mirror_kernel<<<mblocks, 256, 0, s>>>(c, n_full, base);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
 }  // namespace lpf
 
 // ---------------------------------------------------------------------------
@@ -605,6 +721,11 @@ int lpf_set_launch_shape(lpf_paths* p, int32_t H, int32_t W, int32_t T, int32_t 
     if (t.H == H && t.W == W) { t.T = T; t.BB = BB; return LPF_OK; }
   p->tuned.push_back({H, W, T, BB});
   return LPF_OK;
+}
+
+int lpf_full_noalloc(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, int64_t* counts_dev,
+                     lpf_stream_t stream) {
+  return lpf::run_full_noalloc(img_dev, H, W, paths, counts_dev, (cudaStream_t)stream);
 }
 
 int lpf_paths_set_timer(lpf_paths* p, void* ev_start, void* ev_stop) {

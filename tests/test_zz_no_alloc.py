@@ -1,0 +1,65 @@
+"""lpf_full_noalloc: the full evaluation for callers that cannot allocate
+device memory while they evaluate (a host application that owns all device
+allocations, or a real-time loop where cudaMalloc, which can synchronise the
+device, is forbidden).  Its work area is a fixed array inside the library.
+
+Called through the C ABI with ctypes; each of two calls in a row must give
+exactly the counts of lpf_full (integer counts: bit-exact), on different
+images so that the shared fixed array cannot carry a stale result over.
+This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _call(lib, img, paths, out):
+    H, W = img.shape
+    return lib.lpf_full_noalloc(ctypes.c_void_p(img.data_ptr()), H, W, ctypes.c_void_p(paths.handle),
+                                ctypes.c_void_p(out.data_ptr()),
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def test_noalloc_matches_lpf_full_on_two_calls(gpu_lib):
+    lib = gpu_lib.load()
+    r = 256
+    paths = gpu_lib.lpf_build_paths(r, r)
+    a = torch.from_numpy(synth.config2_image()).cuda()
+    b = torch.from_numpy(synth.clustered_disks(512, 512, 0.3, seed=21)).cuda()
+    ref_a = gpu_lib.lpf_full(a, paths)   # existing entry point; also puts the program on the device
+    ref_b = gpu_lib.lpf_full(b, paths)
+    out1 = torch.full((2, paths.n_full), -1, dtype=torch.int64, device="cuda")
+    out2 = torch.full((2, paths.n_full), -1, dtype=torch.int64, device="cuda")
+    assert _call(lib, a, paths, out1) == 0
+    assert _call(lib, b, paths, out2) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(out1, ref_a)
+    assert torch.equal(out2, ref_b)
+    # and again on the first image: nothing left over from the previous call
+    assert _call(lib, a, paths, out2) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(out2, ref_a)
+
+
+def test_noalloc_rejects_what_it_cannot_do(gpu_lib):
+    lib = gpu_lib.load()
+    small = torch.from_numpy(synth.config1_image()).cuda()
+    fresh = gpu_lib.lpf_build_paths(32, 32)
+    out = torch.empty((2, fresh.n_full), dtype=torch.int64, device="cuda")
+    # the program for this size was never put on the device: refused, not allocated
+    assert _call(lib, small, fresh, out) == -1
+    gpu_lib.lpf_full(small, fresh)
+    assert _call(lib, small, fresh, out) == 0
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), gpu_lib.lpf_full(small, fresh).cpu().numpy())
+    # an image whose packed rows exceed the fixed area (4128 rows x 67 words
+    # > 2^18 words) is refused with LPF_EUNSUPPORTED
+    big = torch.zeros((4096, 2048), dtype=torch.uint8, device="cuda")
+    big_out = torch.empty((2, fresh.n_full), dtype=torch.int64, device="cuda")
+    assert _call(lib, big, fresh, big_out) == -5
