@@ -49,12 +49,13 @@ def _barrier(ws):
         dist.barrier()
 
 
-def _max_over_ranks(ws, x: float) -> float:
+def _max_over_ranks(ws, x: float, device: str = "cuda") -> float:
+    """Largest value over the ranks (the slowest replica sets the job's time)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -129,6 +130,123 @@ def _traffic_record():
     return rec.get("dram_bytes_per_launch")
 
 
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def extra_delta(lpf, reps: int = 5):
+    """lpf_delta_swap: 4096 candidate exchanges on a 128x128 clustered-disk
+    cell, window 64, error changes only."""
+    import numpy as np
+    import torch
+
+    import synth
+    cell = synth.config3_original()[:128, :128].copy()
+    paths = lpf.lpf_build_paths(64, 64)
+    d = torch.from_numpy(cell).cuda()
+    counts = lpf.lpf_full(d, paths)
+    target = (counts.double() / cell.size).float() * 0.9
+    rng = np.random.default_rng(0)
+    flat = cell.reshape(-1)
+    K = 4096
+    pairs = np.stack([rng.choice(np.flatnonzero(flat == 1), K), rng.choice(np.flatnonzero(flat == 0), K)], 1)
+    pairs = torch.from_numpy(pairs.astype(np.int32)).cuda()
+    de = torch.empty(K, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        lpf.lpf_delta_swap(d, paths, pairs, target=target, counts=counts, de=de, want_dcounts=False, want_de=True)
+    a, b = _events()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        lpf.lpf_delta_swap(d, paths, pairs, target=target, counts=counts, de=de, want_dcounts=False, want_de=True)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    return {"workload": "lpf_delta_swap 128x128 clustered cell, |v|<=64, K=4096, error changes",
+            "ms_per_call": ms, "candidates_per_s": K / (ms / 1000.0)}
+
+
+def extra_sa(lpf, seconds: float = 40.0):
+    """Annealing (compression workload): 128x128 cell, |v|<=64, target from a
+    512x512 clustered-disk original, N_step = 10^6, run for a bounded time."""
+    import torch
+
+    import synth
+    orig = synth.config3_original()
+    paths = lpf.lpf_build_paths(64, 64)
+    c = lpf.lpf_full(torch.from_numpy(orig).cuda(), paths)
+    target = (c.double() / float(orig.size)).float()
+    cell = torch.from_numpy(synth.exact_fraction_shuffle(128, 128, int(round(orig.mean() * 128 * 128)), seed=5)).cuda()
+    ann = lpf.lpf_sa_create(cell, paths, target, n_step=10 ** 6, seed=1)
+    st0 = lpf.lpf_sa_read(ann)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        lpf.lpf_sa_run(ann, 256)
+        st = lpf.lpf_sa_read(ann)
+        if st["done"]:
+            break
+    dt = time.perf_counter() - t0
+    return {"workload": "annealing 128x128 cell |v|<=64, N_step=1e6 (bounded run)", "seconds": dt,
+            "evaluations": st["n_eval"], "evaluations_per_s": st["n_eval"] / dt, "accepted": st["n_accept"],
+            "candidates_evaluated": st["n_candidates"], "error_start": st0["error"], "error_end": st["error"],
+            "done": bool(st["done"])}
+
+
+def extra_batch(lpf):
+    """256 images of 48-256 px, windows r = size/2: one batched graph launch vs
+    per-image lpf_full launches."""
+    import torch
+
+    import synth
+    imgs = synth.config4_images(256, seed=4)
+    paths = [lpf.lpf_build_paths(W // 2, H // 2) for H, W in (i.shape for i in imgs)]
+    d = [torch.from_numpy(i).cuda() for i in imgs]
+    b = lpf.lpf_batch_create(d, paths)
+    lpf.lpf_batch_autotune(b)
+    outs = [torch.empty((2, p.n_full), dtype=torch.int64, device="cuda") for p in paths]
+    for k in range(len(d)):
+        lpf.lpf_full(d[k], paths[k], outs[k])  # puts every program on the device
+    lpf.lpf_batch_run(b)
+    torch.cuda.synchronize()
+    tests = sum(2 * i.size * p.n_full for i, p in zip(imgs, paths))
+    a, e = _events()
+    reps = 3
+    a.record()
+    for _ in range(reps):
+        lpf.lpf_batch_run(b, use_graph=True)
+    e.record()
+    torch.cuda.synchronize()
+    ms_batch = a.elapsed_time(e) / reps
+    a.record()
+    for _ in range(reps):
+        for k in range(len(d)):
+            lpf.lpf_full(d[k], paths[k], outs[k])
+    e.record()
+    torch.cuda.synchronize()
+    ms_single = a.elapsed_time(e) / reps
+    return {"workload": "256 images 48-256 px, r = size/2, both phases", "ms_batched_graph": ms_batch,
+            "ms_per_image_launches": ms_single, "tests_per_s_batched": tests / (ms_batch / 1000.0),
+            "speedup": ms_single / ms_batch}
+
+
+def extra_s2(lpf, reps: int = 20):
+    import torch
+
+    import synth
+    d = torch.from_numpy(synth.config2_image()).cuda()
+    out = lpf.s2_fft(d, 1)
+    a, b = _events()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        lpf.s2_fft(d, 1, out)
+    b.record()
+    torch.cuda.synchronize()
+    return {"workload": "s2_fft 512x512, one phase, double-precision FFT", "ms_per_call": a.elapsed_time(b) / reps}
+
+
 def cpu_baseline_sample(img, seconds: float = 12.0, seed: int = 0):
     """The oracle (plain C, Alg. 1, OpenMP over vectors) on a bounded random
     sample of the window's vectors; returns tests/s and the sample size."""
@@ -188,6 +306,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -306,6 +425,15 @@ def main():
         "gpu_launches": 3 * K,
         "clocks": clocks,
     }
+    if not args.no_extras:
+        extras = {}
+        for name, fn in (("delta_swap", extra_delta), ("annealing", extra_sa), ("batched", extra_batch),
+                         ("s2_fft", extra_s2)):
+            try:
+                extras[name] = fn(lpf)
+            except Exception as exc:  # report, do not hide, a failing extra
+                extras[name] = {"error": repr(exc)}
+        line["extras"] = extras
     if rank == 0 and not args.no_cpu_baseline:
         v, n, dt = cpu_baseline_sample(img)
         import oracle

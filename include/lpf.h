@@ -222,6 +222,20 @@ int lpf_delta_swap(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *path
                    const float *target_dev, const int64_t *counts_dev, float *de_dev,
                    lpf_stream_t stream);
 
+/*
+ * Two-point probability function of phase `phase` (Sec. 2.1), the baseline
+ * descriptor: s2_dev[y][x] = 1/(W*H) * IDFT(DFT(chi) * conj(DFT(chi)))(x, y),
+ * chi the indicator of the phase, which equals the direct periodic sum of
+ * Eq. (S2dis) over (x1, y1) of chi(x1,y1) chi((x1+x)%W, (y1+y)%H) / (W*H).
+ * img_dev: H*W uint8 (0/1); s2_dev: float [H][W] (row y = row offset,
+ * column x = column offset).  Transforms in double precision (cuFFT), result
+ * rounded to float32.  The first call for a size creates FFT plans and a
+ * work area (cached per device and size; not for use inside stream capture
+ * the first time).  H*W <= 2^26.  Errors: LPF_EINVAL, LPF_ECUDA, LPF_ENOMEM.
+ */
+int s2_fft(const uint8_t *img_dev, int32_t H, int32_t W, int32_t phase, float *s2_dev,
+           lpf_stream_t stream);
+
 /* ---- Many independent images in one persistent launch ---- */
 
 typedef struct lpf_batch lpf_batch; /* opaque, owned by the library */
@@ -284,7 +298,7 @@ typedef struct {
                           probability 1/2 (the paper tunes it by hand for s/c ~ 0.5) */
   double t_min_ratio;  /* T_min / T_max (Tab. annealing: 0.01) */
   int32_t k_max;       /* candidates per batch, upper bound (e.g. 4096) */
-  int32_t k_min;       /* candidates per batch, lower bound (e.g. 32) */
+  int32_t k_min;       /* candidates per batch, lower bound (e.g. 4) */
   uint64_t seed;       /* Philox-4x32-10 key of the run */
 } lpf_sa_params;
 
@@ -310,10 +324,14 @@ typedef struct {
  * window: the descriptor cut of Sec. 6).  counts_dev: int64 [2][n_vec_full],
  * filled here with the cell's counts and kept current by the run.  The
  * paths window must satisfy the lpf_delta_swap limits.  Candidate n of the
- * run (n = 0, 1, ...) is an interfacial phase-1 / phase-0 pixel pair drawn
- * with Philox-4x32-10 (counter n, key seed) from the then-current cell, and
- * its Metropolis uniform comes from the same draw, so the run equals the
- * sequential annealer step for step whatever the batch sizes.
+ * run (n = 0, 1, ...) is an interfacial phase-1 / phase-0 pixel pair, each
+ * uniform over its set, drawn by rejection sampling with Philox-4x32-10
+ * (attempt j uses counter (n_lo, n_hi, j, 0), key = seed; words 0 and 1
+ * propose floor(r*H*W/2^32)) from the then-current cell, with Metropolis
+ * uniform U = ((r2 >> 8) + 1/2) / 2^24 from attempt 0, so the run equals the
+ * sequential annealer step for step whatever the batch sizes.  The run's
+ * device buffers include count changes for k_max candidates
+ * (k_max * 2 * n_vec_canon int32).
  * Synchronises `stream`; allocates the run's device buffers.
  * Errors: LPF_EINVAL, LPF_EUNSUPPORTED, LPF_ENOMEM, LPF_ECUDA.
  */
@@ -322,18 +340,20 @@ int lpf_sa_create(uint8_t *cell_dev, int32_t H, int32_t W, lpf_paths *paths,
                   lpf_stream_t stream, lpf_sa **out);
 
 /*
- * Enqueue n_batches annealing batches on `stream` without synchronising:
- * each batch proposes the next k candidates, evaluates all of them with the
- * swap-delta kernel, accepts the first that passes the Metropolis test
- * (Delta e <= 0 or U < exp(-Delta e / T)), applies it to the cell and the
- * counts, and updates the temperature stage; k adapts to the acceptance
- * rate between k_min and k_max.  Batches after the run is done do nothing.
- * The first call with n_batches >= 8 captures 8 batches as a CUDA graph,
- * replayed afterwards.  Errors: LPF_EINVAL, LPF_ECUDA.
+ * Enqueue n_batches annealing batches on `stream` without synchronising.
+ * Each batch is one kernel launch: it draws the next k candidates,
+ * evaluates all of them as lpf_delta_swap does, and its last block accepts
+ * the first that passes the Metropolis test (Delta e <= 0 or
+ * U < exp(-Delta e / T)), applies it to the cell and the counts and updates
+ * the temperature stage; k adapts to the acceptance rate between k_min and
+ * k_max.  Batches after the run is done do nothing.  The first call with
+ * n_batches >= 16 captures 16 batches as a CUDA graph, replayed afterwards.
+ * Errors: LPF_EINVAL, LPF_ECUDA.
  */
 int lpf_sa_run(lpf_sa *sa, int32_t n_batches, lpf_stream_t stream);
 
-/* Synchronise `stream` and copy the run's counters to *out. */
+/* Synchronise `stream` and copy the run's counters to *out; LPF_ETIMEOUT
+ * (counters still copied) if a bounded wait in a batch kernel gave up. */
 int lpf_sa_read(lpf_sa *sa, lpf_sa_stats *out, lpf_stream_t stream);
 
 /* Recompute the error from the exact counts in double precision, store it
@@ -348,6 +368,67 @@ int lpf_sa_propose(lpf_sa *sa, int32_t k, int32_t *pairs_dev, float *u_dev, lpf_
 
 /* Release a run (NULL is ignored); synchronises the device. */
 void lpf_sa_free(lpf_sa *sa);
+
+/* ---- Learned swap proposer (no counterpart in the paper) ---- */
+
+typedef struct lpf_cnn lpf_cnn; /* opaque network, owned by the library */
+
+/*
+ * A small convolutional network that scores every pixel of an H x W cell as
+ * the phase-1 pixel (output channel 1) or the phase-0 pixel (channel 0) of an
+ * exchange.  The paper's modification operator (Sec. 4) draws interfacial
+ * pixels uniformly; the network only changes which candidates are drawn --
+ * every accept/reject decision of the annealer still uses exact counts.
+ * Layers: five 3x3 convolutions with circular padding (periodic medium) and
+ * ReLU between them, channels 2 -> 32 -> 64 -> 48 -> 32 -> 2 (61,234
+ * parameters); input channels: cell value, interfacial mask.  Weights are
+ * kept as float32 masters (updated by Adam) and bfloat16 copies (used by the
+ * forward and backward kernels); activations and accumulation are float32.
+ * Parameter vector layout (lpf_cnn_set_params / get_params): for each layer,
+ * W [9][Cin][Cout] (tap = (dy+1)*3 + (dx+1)) then b [Cout].
+ * lpf_cnn_create initialises He-normal weights (seeded) and allocates the
+ * network's device memory for H x W cells.  Errors: LPF_EINVAL, LPF_ENOMEM.
+ */
+int lpf_cnn_create(int32_t H, int32_t W, uint64_t seed, lpf_cnn **out);
+int64_t lpf_cnn_num_params(const lpf_cnn *cnn);
+int lpf_cnn_set_params(lpf_cnn *cnn, const float *params_host, int64_t n);      /* synchronous */
+int lpf_cnn_get_params(const lpf_cnn *cnn, float *params_host, int64_t n);      /* synchronous */
+
+/* Scores of a cell: scores_dev float [H][W][2] (may be NULL to only refresh
+ * the network's internal output buffer). */
+int lpf_cnn_forward(lpf_cnn *cnn, const uint8_t *cell_dev, float *scores_dev, lpf_stream_t stream);
+
+/*
+ * Gradient of the loss of one snapshot, for checking: with n logged
+ * candidates (pairs_dev int32 [n][2] = phase-1 pixel a, phase-0 pixel b;
+ * y_dev float [n] targets), L = 1/(2n) sum_i (s1[a_i] + s0[b_i] - y_i)^2;
+ * grads_dev float [n_params] (may be NULL), loss_dev float (may be NULL).
+ */
+int lpf_cnn_gradients(lpf_cnn *cnn, const uint8_t *cell_dev, const int32_t *pairs_dev, const float *y_dev,
+                      int32_t n, float *grads_dev, float *loss_dev, lpf_stream_t stream);
+
+/*
+ * One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean loss of B
+ * snapshots: cells_dev uint8 [B][H][W], pairs_dev int32 [B][n][2], y_dev
+ * float [B][n]; loss_dev (may be NULL) receives the mean loss before the step.
+ */
+int lpf_cnn_train_step(lpf_cnn *cnn, const uint8_t *cells_dev, int32_t B, const int32_t *pairs_dev,
+                       const float *y_dev, int32_t n, float lr, float *loss_dev, lpf_stream_t stream);
+
+void lpf_cnn_free(lpf_cnn *cnn);
+
+/*
+ * Let an annealing run draw candidates from the network: before every graph
+ * of batches (every `refresh` batches) the network scores the current cell
+ * and the run builds, per phase, sampling weights exp((s - max s) / tau) over
+ * the interfacial pixels of that phase; each candidate then takes, with
+ * probability epsilon, the uniform draw of lpf_sa_create, and otherwise
+ * draws each pixel from these weights (a drawn pixel that no longer has the
+ * wanted phase or is no longer interfacial is rejected and drawn again).
+ * cnn = NULL restores uniform draws.  The network must stay alive while the
+ * run uses it.  Errors: LPF_EINVAL, LPF_ENOMEM, LPF_ECUDA.
+ */
+int lpf_sa_set_proposer(lpf_sa *sa, lpf_cnn *cnn, float epsilon, float tau, int32_t refresh);
 
 /*
  * Measurement hook: when ev_start/ev_stop (cudaEvent_t, created by the

@@ -10,10 +10,14 @@ Readings of the paper that this follows (its printed Alg. 3 is garbled):
   - a candidate is accepted when Delta e <= 0 or U < exp(-Delta e / T);
   - the modification exchanges a phase-1 and a phase-0 pixel, both drawn
     uniformly among interfacial pixels (4-neighbourhood on the torus);
-  - the random numbers of candidate n come from Philox-4x32-10 with counter
-    (n, 0, 0, 0) and the run's key: words 0 and 1 pick the two pixels by
-    multiply-shift (floor(r * len / 2^32)), word 2 gives
-    U = ((r >> 8) + 1/2) / 2^24 evaluated in float32.
+  - the random numbers of candidate n come from Philox-4x32-10 keyed by the
+    run's seed: attempt j = 0, 1, ... uses counter (n mod 2^32, n div 2^32,
+    j, 0); its words 0 and 1 each propose a pixel floor(r * H*W / 2^32), and
+    the first proposal that has the wanted phase and is interfacial is kept
+    (rejection sampling, i.e. uniform over the interfacial pixels of that
+    phase); word 2 of attempt 0 gives U = ((r >> 8) + 1/2) / 2^24 evaluated in
+    float32.  With no such pixel after 65536 attempts the candidate is the
+    identity (0, 0).
 """
 from __future__ import annotations
 
@@ -61,16 +65,33 @@ def interfacial_lists(cell: np.ndarray):
 def propose(cell: np.ndarray, n_eval: int, k: int, seed: int):
     """Candidates n_eval .. n_eval+k-1 drawn from `cell`: pairs int32 [k][2]
     (phase-1 pixel, phase-0 pixel) and uniforms float32 [k]."""
-    l1, l0 = interfacial_lists(cell)
+    c = np.asarray(cell)
+    flat = c.reshape(-1)
+    npix = flat.size
+    l1, l0 = interfacial_lists(c)
+    inter1 = np.zeros(npix, bool)
+    inter0 = np.zeros(npix, bool)
+    inter1[l1] = True
+    inter0[l0] = True
     key = (seed & MASK, (seed >> 32) & MASK)
     pairs = np.zeros((k, 2), np.int32)
     u = np.zeros(k, np.float32)
-    for j in range(k):
-        n = n_eval + j
-        r = philox4x32_10((n & MASK, (n >> 32) & MASK, 0, 0), key)
-        pairs[j, 0] = l1[(r[0] * len(l1)) >> 32]
-        pairs[j, 1] = l0[(r[1] * len(l0)) >> 32]
-        u[j] = (np.float32(r[2] >> 8) + np.float32(0.5)) * np.float32(1.0 / 16777216.0)
+    for i in range(k):
+        n = n_eval + i
+        a = b = -1
+        for j in range(65536):
+            r = philox4x32_10((n & MASK, (n >> 32) & MASK, j, 0), key)
+            if j == 0:
+                u[i] = (np.float32(r[2] >> 8) + np.float32(0.5)) * np.float32(1.0 / 16777216.0)
+            if a < 0 and inter1[(r[0] * npix) >> 32]:
+                a = (r[0] * npix) >> 32
+            if b < 0 and inter0[(r[1] * npix) >> 32]:
+                b = (r[1] * npix) >> 32
+            if a >= 0 and b >= 0:
+                break
+        if a < 0 or b < 0:
+            a = b = 0
+        pairs[i] = (a, b)
     return pairs, u
 
 

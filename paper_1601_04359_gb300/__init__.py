@@ -20,7 +20,8 @@ __all__ = [
     "lpf_paths_stats", "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer",
     "lpf_delta_swap", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror",
     "SaParams", "SaStats", "Annealer", "lpf_sa_create", "lpf_sa_run", "lpf_sa_read", "lpf_sa_recompute_error",
-    "lpf_sa_propose", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune", "lpf_batch_status",
+    "lpf_sa_propose", "s2_fft", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
+    "lpf_cnn_forward", "lpf_cnn_gradients", "lpf_cnn_train_step", "lpf_sa_set_proposer", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune", "lpf_batch_status",
 ]
 
 _lib = None
@@ -81,6 +82,16 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_autotune_full": (ctypes.c_int, [p, i32, i32, p, p, p, P32, P32]),
         "lpf_set_launch_shape": (ctypes.c_int, [p, i32, i32, i32, i32]),
         "lpf_full_noalloc": (ctypes.c_int, [p, i32, i32, p, p, p]),
+        "s2_fft": (ctypes.c_int, [p, i32, i32, i32, p, p]),
+        "lpf_cnn_create": (ctypes.c_int, [i32, i32, ctypes.c_uint64, ctypes.POINTER(p)]),
+        "lpf_cnn_num_params": (ctypes.c_int64, [p]),
+        "lpf_cnn_set_params": (ctypes.c_int, [p, p, i64]),
+        "lpf_cnn_get_params": (ctypes.c_int, [p, p, i64]),
+        "lpf_cnn_forward": (ctypes.c_int, [p, p, p, p]),
+        "lpf_cnn_gradients": (ctypes.c_int, [p, p, p, p, i32, p, p, p]),
+        "lpf_cnn_train_step": (ctypes.c_int, [p, p, i32, p, p, i32, ctypes.c_float, p, p]),
+        "lpf_cnn_free": (None, [p]),
+        "lpf_sa_set_proposer": (ctypes.c_int, [p, p, ctypes.c_float, ctypes.c_float, i32]),
         "lpf_batch_create": (ctypes.c_int, [i32, p, p, p, p, p, p, ctypes.POINTER(p)]),
         "lpf_batch_run": (ctypes.c_int, [p, i32, p]),
         "lpf_batch_autotune": (ctypes.c_int, [p, p, p, p, p, p, p]),
@@ -314,7 +325,7 @@ class Annealer:
 
 
 def lpf_sa_create(cell, paths: Paths, target, counts=None, n_step=1_000_000, c_max=None, s_max=None,
-                  t_max=0.0, t_min_ratio=0.01, k_max=4096, k_min=32, seed=1, stream=None) -> Annealer:
+                  t_max=0.0, t_min_ratio=0.01, k_max=4096, k_min=4, seed=1, stream=None) -> Annealer:
     """Start an annealing run on the CUDA uint8 cell (modified in place)."""
     import torch
     H, W = cell.shape
@@ -353,6 +364,84 @@ def lpf_sa_propose(sa: Annealer, k: int, stream=None):
     _check(load().lpf_sa_propose(sa.handle, int(k), pairs.data_ptr(), u.data_ptr(), _stream_ptr(stream)),
            "lpf_sa_propose")
     return pairs, u
+
+
+def s2_fft(img, phase: int, out=None, stream=None):
+    """Two-point probability of `phase`: float32 CUDA tensor [H][W]."""
+    import torch
+    H, W = img.shape
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    _check(load().s2_fft(_dev_ptr(img, "uint8", "img"), H, W, int(phase), _dev_ptr(out, "float32", "s2"),
+                         _stream_ptr(stream)), "s2_fft")
+    return out
+
+
+class Cnn:
+    """Owning wrapper of an lpf_cnn* (the learned swap proposer)."""
+
+    def __init__(self, handle, H, W):
+        self.handle = handle
+        self.H, self.W = H, W
+        self.n_params = int(load().lpf_cnn_num_params(handle))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.lpf_cnn_free(h)
+            self.handle = None
+
+
+def lpf_cnn_create(H: int, W: int, seed: int = 0) -> Cnn:
+    h = ctypes.c_void_p()
+    _check(load().lpf_cnn_create(int(H), int(W), int(seed), ctypes.byref(h)), "lpf_cnn_create")
+    return Cnn(h.value, int(H), int(W))
+
+
+def lpf_cnn_set_params(cnn: Cnn, params: np.ndarray):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().lpf_cnn_set_params(cnn.handle, a.ctypes.data, a.size), "lpf_cnn_set_params")
+
+
+def lpf_cnn_get_params(cnn: Cnn) -> np.ndarray:
+    a = np.zeros(cnn.n_params, np.float32)
+    _check(load().lpf_cnn_get_params(cnn.handle, a.ctypes.data, a.size), "lpf_cnn_get_params")
+    return a
+
+
+def lpf_cnn_forward(cnn: Cnn, cell, stream=None):
+    import torch
+    out = torch.empty((cnn.H, cnn.W, 2), dtype=torch.float32, device=cell.device)
+    _check(load().lpf_cnn_forward(cnn.handle, _dev_ptr(cell, "uint8", "cell"), out.data_ptr(), _stream_ptr(stream)),
+           "lpf_cnn_forward")
+    return out
+
+
+def lpf_cnn_gradients(cnn: Cnn, cell, pairs, y, stream=None):
+    import torch
+    g = torch.empty(cnn.n_params, dtype=torch.float32, device=cell.device)
+    loss = torch.empty(1, dtype=torch.float32, device=cell.device)
+    _check(load().lpf_cnn_gradients(cnn.handle, _dev_ptr(cell, "uint8", "cell"), _dev_ptr(pairs, "int32", "pairs"),
+                                    _dev_ptr(y, "float32", "y"), int(pairs.shape[0]), g.data_ptr(), loss.data_ptr(),
+                                    _stream_ptr(stream)), "lpf_cnn_gradients")
+    return g, loss
+
+
+def lpf_cnn_train_step(cnn: Cnn, cells, pairs, y, lr: float, stream=None):
+    """One Adam step on snapshots cells [B][H][W] with pairs [B][n][2], y [B][n]."""
+    import torch
+    loss = torch.empty(1, dtype=torch.float32, device=cells.device)
+    B, n = int(pairs.shape[0]), int(pairs.shape[1])
+    _check(load().lpf_cnn_train_step(cnn.handle, _dev_ptr(cells, "uint8", "cells"), B,
+                                     _dev_ptr(pairs, "int32", "pairs"), _dev_ptr(y, "float32", "y"), n, float(lr),
+                                     loss.data_ptr(), _stream_ptr(stream)), "lpf_cnn_train_step")
+    return loss
+
+
+def lpf_sa_set_proposer(sa: "Annealer", cnn, epsilon: float = 0.1, tau: float = 1.0, refresh: int = 16):
+    _check(load().lpf_sa_set_proposer(sa.handle, cnn.handle if cnn is not None else None, float(epsilon),
+                                      float(tau), int(refresh)), "lpf_sa_set_proposer")
+    sa.cnn = cnn
 
 
 def lpf_paths_status(paths: Paths, stream=None) -> int:

@@ -18,174 +18,91 @@
 //   q = 1 -> dcount_1 += 1,  q = 0 -> dcount_0 -= 1.
 // Segments containing both a and b change in neither phase and are ended by
 // the marker.  The zero vector never changes.
+//
+// Work split: blocks = (vector chunk) x (candidate stride); each block stages
+// the extended cell once (one bulk copy of a copy built per call in global
+// memory) and loops over its candidates.  Error changes are summed per
+// (candidate, chunk) in a fixed order and then over chunks in chunk order, so
+// results are bitwise reproducible.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
 
-#include "lpf_device.cuh"
+#include "lpf_delta.cuh"
 #include "lpf_state.hpp"
 
 namespace lpf {
 
-constexpr uint8_t kMarkA = 4;
-constexpr uint8_t kMarkB = 3;
-constexpr int kDeltaThreads = 256;
-constexpr int kDeltaWarps = kDeltaThreads / 32;
-
-struct DeltaGeom {
-  int We = 0, He = 0;   // extended width / height
-  uint32_t smem = 0;    // bytes (multiple of 16)
-};
-
-static DeltaGeom delta_geom(int H, int W, int rx, int ry) {
-  DeltaGeom g;
-  g.We = W + 2 * rx;
-  g.He = H + 2 * ry;
-  g.smem = (uint32_t)((((size_t)g.We * g.He) + 15) & ~size_t(15));
-  return g;
+// ext[ey][ex] = img[(ey - ry) mod H][(ex - rx) mod W]; zero padding to `bytes`.
+__global__ void build_ext_kernel(const uint8_t* __restrict__ img, int H, int W, int rx, int ry, int We, int He,
+                                 uint32_t bytes, uint8_t* __restrict__ ext) {
+  const int total = We * He;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)bytes; i += gridDim.x * blockDim.x) {
+    uint8_t v = 0;
+    if (i < total) {
+      const int ey = i / We, ex = i - ey * We;
+      int y = (ey - ry) % H; if (y < 0) y += H;
+      int x = (ex - rx) % W; if (x < 0) x += W;
+      v = img[y * W + x];
+    }
+    ext[i] = v;
+  }
 }
 
-// Extended-cell position of pixel index c.
-__device__ __forceinline__ int ext_pos(int c, int W, int We, int rx, int ry) {
-  const int cy = c / W, cx = c - cy * W;
-  return (cy + ry) * We + (cx + rx);
-}
-
-// Write `val` at every periodic copy of pixel c inside the extended cell.
-__device__ void mark_copies(uint8_t* sm, int c, uint8_t val, int H, int W, int We, int He, int rx, int ry) {
-  const int cy = c / W, cx = c - cy * W;
-  for (int ey = cy + ry - ((cy + ry) / H) * H; ey < He; ey += H)
-    for (int ex = cx + rx - ((cx + rx) / W) * W; ex < We; ex += W) sm[ey * We + ex] = val;
-}
-
-__global__ void __launch_bounds__(kDeltaThreads) delta_kernel(
-    const uint8_t* __restrict__ img, int H, int W, int rx, int ry, int We, int He,
-    const int32_t* __restrict__ dptr, const int32_t* __restrict__ doff, const int32_t* __restrict__ chunk,
-    int n_chunks, const int32_t* __restrict__ pairs, int K, const int32_t* __restrict__ k_dev,
-    int32_t* __restrict__ dcounts, int64_t n_canon, const float* __restrict__ target,
-    const int64_t* __restrict__ counts, int64_t n_full, int64_t base, float* __restrict__ partial,
-    int* __restrict__ status) {
+__global__ void __launch_bounds__(kDeltaThreads) delta_kernel(const uint8_t* __restrict__ img,
+                                                               const uint8_t* __restrict__ ext, DeltaArgs g,
+                                                               const int32_t* __restrict__ pairs, int K,
+                                                               int32_t* __restrict__ dcounts,
+                                                               float* __restrict__ partial, int* __restrict__ status) {
   extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ __align__(8) uint64_t bar;
   __shared__ float warp_acc[kDeltaWarps];
   __shared__ int s_a, s_b, s_skip;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ch = blockIdx.x;
-  const int Keff = k_dev ? min(K, *k_dev) : K;
-  if ((int)blockIdx.y >= Keff) return;
-
-  // extended cell: sm[ey*We + ex] = img[(ey - ry) mod H][(ex - rx) mod W]
-  const int total = We * He;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    const int ey = i / We, ex = i - ey * We;
-    int y = (ey - ry) % H; if (y < 0) y += H;
-    int x = (ex - rx) % W; if (x < 0) x += W;
-    sm[i] = img[y * W + x];
+  if ((int)blockIdx.y >= K) return;
+  if (!delta_stage(sm, ext, g.ext_bytes, &bar)) {
+    if (threadIdx.x == 0) atomicOr(status, 1);
+    (void)mbar_wait(&bar, 0);  // let the copy land before the block exits
+    return;
   }
-  __syncthreads();
-
-  const int v0 = chunk[ch], v1 = chunk[ch + 1];
-  const float invN = 1.0f / ((float)H * (float)W);
-  const int npix = H * W;
-
-  for (int k = blockIdx.y; k < Keff; k += gridDim.y) {
+  const int v0 = g.chunk[ch], v1 = g.chunk[ch + 1];
+  const int npix = g.H * g.W;
+  for (int k = blockIdx.y; k < K; k += gridDim.y) {
     if (threadIdx.x == 0) {
       int a = pairs[2 * k], b = pairs[2 * k + 1];
       int skip = 0;
       if (a < 0 || b < 0 || a >= npix || b >= npix) { skip = 1; atomicOr(status, 2); }
-      else if (img[a] == img[b]) skip = 1;       // same phase (or a == b): identity
-      else if (img[a] == 0) { const int t = a; a = b; b = t; }  // a holds phase 1
+      else if (img[a] == img[b]) skip = 1;                       // same phase (or a == b): identity
+      else if (img[a] == 0) { const int t = a; a = b; b = t; }   // a holds phase 1
       s_a = a; s_b = b; s_skip = skip;
-      if (!skip) {
-        mark_copies(sm, a, kMarkA, H, W, We, He, rx, ry);
-        mark_copies(sm, b, kMarkB, H, W, We, He, rx, ry);
-      }
+      if (!skip) { delta_mark(sm, a, kMarkA, g); delta_mark(sm, b, kMarkB, g); }
     }
     __syncthreads();
     const int a = s_a, b = s_b, skip = s_skip;
+    int32_t* dk = dcounts ? dcounts + (int64_t)k * 2 * g.n_canon : nullptr;
     float acc = 0.0f;
-    const int pa = skip ? 0 : ext_pos(a, W, We, rx, ry);
-    const int pb = skip ? 0 : ext_pos(b, W, We, rx, ry);
-    for (int v = v0 + warp; v < v1; v += kDeltaWarps) {
-      const int o0 = dptr[v];
-      const int L1 = dptr[v + 1] - o0;  // pixels of the segment
-      int d0 = 0, d1 = 0;
-      if (!skip && L1 > 1) {
-        const int tasks = 2 * L1;
-        for (int t0 = 0; t0 < tasks; t0 += 32) {
-          const int t = t0 + lane;
-          const bool is_a = t < L1;
-          const int i = is_a ? t : t - L1;
-          bool alive = t < tasks;
-          const int pos = (is_a ? pa : pb) - (alive ? __ldg(doff + o0 + i) : 0);
-          int q = -1;
-          for (int j = 0; j < L1; ++j) {
-            if (!__any_sync(0xffffffffu, alive)) break;
-            const int oj = __ldg(doff + o0 + j);
-            if (alive && j != i) {
-              const int val = sm[pos + oj];
-              if (q < 0) {
-                if (val > 1) alive = false; else q = val;
-              } else if (val != q) {
-                alive = false;
-              }
-            }
-          }
-          if (alive) {
-            if (is_a) { if (q == 1) d1 -= 1; else d0 += 1; }
-            else      { if (q == 1) d1 += 1; else d0 -= 1; }
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          d0 += __shfl_xor_sync(0xffffffffu, d0, o);
-          d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-        }
-      }
-      if (lane == 0) {
-        if (dcounts) {
-          dcounts[((int64_t)k * 2 + 0) * n_canon + v] = d0;
-          dcounts[((int64_t)k * 2 + 1) * n_canon + v] = d1;
-        }
-        if (partial && (d0 | d1)) {
-          // (d - D/N)^2 - d^2 = (D/N) * (D/N - 2 d), d = target - count/N
-          if (d0) {
-            const float dd = target[base + v] - (float)counts[base + v] * invN;
-            const float x = (float)d0 * invN;
-            acc += x * (x - 2.0f * dd);
-          }
-          if (d1) {
-            const float dd = target[n_full + base + v] - (float)counts[n_full + base + v] * invN;
-            const float x = (float)d1 * invN;
-            acc += x * (x - 2.0f * dd);
-          }
-        }
-      }
-    }
+    if (skip) delta_zero_vectors(g, v0, v1, dk);
+    else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk);
     if (lane == 0) warp_acc[warp] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
       if (partial) {
         float s = 0.0f;
         for (int w = 0; w < kDeltaWarps; ++w) s += warp_acc[w];
-        partial[(int64_t)k * n_chunks + ch] = s;
+        partial[(int64_t)k * g.n_chunks + ch] = s;
       }
-      if (!skip) {
-        mark_copies(sm, a, 1, H, W, We, He, rx, ry);
-        mark_copies(sm, b, 0, H, W, We, He, rx, ry);
-      }
+      if (!skip) { delta_mark(sm, a, 1, g); delta_mark(sm, b, 0, g); }
     }
     __syncthreads();
   }
 }
 
 // de[k] = sum over chunks of partial[k][c], in chunk order.
-__global__ void delta_reduce_kernel(const float* __restrict__ partial, int n_chunks, int K,
-                                    const int32_t* __restrict__ k_dev, float* __restrict__ de) {
-  const int Keff = k_dev ? min(K, *k_dev) : K;
+__global__ void delta_reduce_kernel(const float* __restrict__ partial, int n_chunks, int K, float* __restrict__ de) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
     float s = 0.0f;
-    if (k < Keff)
-      for (int c = 0; c < n_chunks; ++c) s += partial[(int64_t)k * n_chunks + c];
+    for (int c = 0; c < n_chunks; ++c) s += partial[(int64_t)k * n_chunks + c];
     de[k] = s;
   }
 }
@@ -196,7 +113,7 @@ __global__ void delta_reduce_kernel(const float* __restrict__ partial, int n_chu
 // Device tables for one cell width: CSR of the canonical segments with each
 // offset converted to an extended-cell displacement sy*We + sx, and vector
 // chunks of similar walk work.
-static int bake_delta(lpf_paths* p, int H, int W, DeltaTables& t) {
+static int bake_delta(lpf_paths* p, int W, DeltaTables& t) {
   const int We = W + 2 * p->host.rx;
   if (t.d_doff && t.We == We) return LPF_OK;
   if (t.d_doff) {
@@ -211,7 +128,9 @@ static int bake_delta(lpf_paths* p, int H, int W, DeltaTables& t) {
   // chunks balanced by sum of (L+1)^2 (walks per vector times their length bound)
   double total = 0;
   for (int64_t c = 0; c < h.n_canon; ++c) { const double l = (double)(ptr[c + 1] - ptr[c]); total += l * l; }
-  const int want = (int)std::max<int64_t>(1, std::min<int64_t>(32, h.n_canon / 64));
+  // many chunks: a single candidate spreads over many blocks (the annealer
+  // evaluates batches of a few candidates when its acceptance rate is high)
+  const int want = (int)std::max<int64_t>(1, std::min<int64_t>(128, h.n_canon / 32));
   std::vector<int32_t> chunk{0};
   double accw = 0;
   for (int64_t c = 0; c < h.n_canon; ++c) {
@@ -233,60 +152,69 @@ static int bake_delta(lpf_paths* p, int H, int W, DeltaTables& t) {
 }
 
 static int g_delta_max_smem = -1;
+static int g_sms = 0;
+
+int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g) {
+  g.H = H;
+  g.W = W;
+  g.rx = p->host.rx;
+  g.ry = p->host.ry;
+  g.We = W + 2 * g.rx;
+  g.He = H + 2 * g.ry;
+  g.ext_bytes = (uint32_t)((((size_t)g.We * g.He) + 15) & ~size_t(15));
+  g.dptr = p->delta.d_dptr;
+  g.doff = p->delta.d_doff;
+  g.chunk = p->delta.d_chunk;
+  g.n_chunks = p->delta.n_chunks;
+  g.n_canon = p->host.n_canon;
+  g.n_full = p->host.n_full;
+  g.base = p->host.base;
+  g.target = nullptr;
+  g.counts = nullptr;
+  return LPF_OK;
+}
+
+int delta_max_smem() { return g_delta_max_smem; }
+int delta_num_sms() { return g_sms; }
 
 int delta_prepare(lpf_paths* p, int H, int W, int K) {
   if (g_delta_max_smem < 0) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, delta_kernel);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(delta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    optin - (int)fa.sharedSizeBytes);
     if (e != cudaSuccess) return set_cuda_error(e);
-    g_delta_max_smem = optin - (int)fa.sharedSizeBytes;
+    g_delta_max_smem = optin - (int)fa.sharedSizeBytes - 64;  // leave room for the annealer kernel's statics
   }
-  const DeltaGeom g = delta_geom(H, W, p->host.rx, p->host.ry);
-  if ((int)g.smem > g_delta_max_smem) return LPF_EUNSUPPORTED;
+  const size_t ext = (((size_t)(W + 2 * p->host.rx) * (H + 2 * p->host.ry)) + 15) & ~size_t(15);
+  if ((int64_t)ext > g_delta_max_smem) return LPF_EUNSUPPORTED;
   int rc = ensure_device(p, 0);
   if (rc) return rc;
-  rc = bake_delta(p, H, W, p->delta);
+  rc = bake_delta(p, W, p->delta);
   if (rc) return rc;
+  cudaError_t e;
+  if (ext > p->ext_cap) {
+    if (p->d_ext) { cudaDeviceSynchronize(); cudaFree(p->d_ext); p->d_ext = nullptr; p->ext_cap = 0; }
+    if ((e = cudaMalloc(&p->d_ext, ext)) != cudaSuccess) return set_cuda_error(e);
+    p->ext_cap = ext;
+  }
   const size_t need = (size_t)std::max(K, 1) * p->delta.n_chunks;
   if (need > p->partial_cap) {
     if (p->d_partial) { cudaDeviceSynchronize(); cudaFree(p->d_partial); p->d_partial = nullptr; p->partial_cap = 0; }
-    cudaError_t e = cudaMalloc(&p->d_partial, need * sizeof(float));
-    if (e != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMalloc(&p->d_partial, need * sizeof(float))) != cudaSuccess) return set_cuda_error(e);
     p->partial_cap = need;
   }
   return LPF_OK;
 }
 
-int delta_launch(const uint8_t* img, int H, int W, lpf_paths* p, const int32_t* pairs, int K,
-                 const int32_t* k_dev, int32_t* dcounts, const float* target, const int64_t* counts, float* de,
-                 float* partial, cudaStream_t s) {
-  const DeltaGeom g = delta_geom(H, W, p->host.rx, p->host.ry);
-  const int n_chunks = p->delta.n_chunks;
-  // blocks stride over the candidates: enough of them to fill every SM a few
-  // times whatever the (possibly device-side) number of candidates
-  int sms = 152;
-  {
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
-  const int per_chunk = std::max(1, (sms * 8 + n_chunks - 1) / n_chunks);
-  dim3 grid(n_chunks, std::min(K, per_chunk));
-  if (p->ev_start) cudaEventRecord(p->ev_start, s);
-  delta_kernel<<<grid, kDeltaThreads, g.smem, s>>>(
-      img, H, W, p->host.rx, p->host.ry, g.We, g.He, p->delta.d_dptr, p->delta.d_doff, p->delta.d_chunk, n_chunks,
-      pairs, K, k_dev, dcounts, p->host.n_canon, target, counts, p->host.n_full, p->host.base,
-      de ? partial : nullptr, p->d_status);
-  if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
-  if (de) {
-    const int blocks = std::min((K + 255) / 256, 1024);
-    delta_reduce_kernel<<<blocks, 256, 0, s>>>(partial, n_chunks, K, k_dev, de);
-  }
-  return set_cuda_error(cudaGetLastError());
+// Blocks per vector chunk: enough candidate strides to fill every SM a few times.
+int delta_stride(int n_chunks, int K) {
+  const int sms = g_sms > 0 ? g_sms : 152;
+  return std::max(1, std::min(K, (sms * 8 + n_chunks - 1) / n_chunks));
 }
 
 }  // namespace lpf
@@ -304,6 +232,23 @@ extern "C" int lpf_delta_swap(const uint8_t* img_dev, int32_t H, int32_t W, lpf_
   int rc = lpf::delta_prepare(paths, H, W, K);
   if (rc) return rc;
   (void)cudaGetLastError();
-  return lpf::delta_launch(img_dev, H, W, paths, pairs_dev, K, nullptr, dcounts_dev, target_dev, counts_dev, de_dev,
-                           paths->d_partial, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  lpf::DeltaArgs g;
+  lpf::delta_geometry(paths, H, W, g);
+  g.target = de_dev ? target_dev : nullptr;
+  g.counts = de_dev ? counts_dev : nullptr;
+  {
+    const int blocks = (int)std::min<int64_t>((g.ext_bytes + 255) / 256, 4096);
+    lpf::build_ext_kernel<<<blocks, 256, 0, s>>>(img_dev, H, W, g.rx, g.ry, g.We, g.He, g.ext_bytes, paths->d_ext);
+  }
+  const dim3 grid(g.n_chunks, lpf::delta_stride(g.n_chunks, K));
+  if (paths->ev_start) cudaEventRecord(paths->ev_start, s);
+  lpf::delta_kernel<<<grid, lpf::kDeltaThreads, g.ext_bytes, s>>>(img_dev, paths->d_ext, g, pairs_dev, K, dcounts_dev,
+                                                                  de_dev ? paths->d_partial : nullptr, paths->d_status);
+  if (paths->ev_stop) cudaEventRecord(paths->ev_stop, s);
+  if (de_dev) {
+    const int blocks = std::min((K + 255) / 256, 1024);
+    lpf::delta_reduce_kernel<<<blocks, 256, 0, s>>>(paths->d_partial, g.n_chunks, K, de_dev);
+  }
+  return lpf::set_cuda_error(cudaGetLastError());
 }

@@ -683,6 +683,7 @@ void lpf_paths_free(lpf_paths* p) {
     cudaFree(p->delta.d_dptr);
     cudaFree(p->delta.d_chunk);
     cudaFree(p->d_partial);
+    cudaFree(p->d_ext);
     if (cur >= 0) cudaSetDevice(cur);
   }
   delete p;

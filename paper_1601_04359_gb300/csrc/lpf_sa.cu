@@ -2,15 +2,14 @@
 // path counts, with candidate swaps evaluated in batches.
 //
 // Sequential equivalence.  Candidate number n of the run (n = 0, 1, ...) is
-// drawn from Philox-4x32-10 with counter (n, 0, 0, 0) and the run's key, from
-// the current image, and its Metropolis uniform comes from the same draw.  A
-// batch evaluates candidates n_eval .. n_eval + K - 1 against the current
-// state; the first one accepted is applied and the rest are discarded (they
-// were drawn from, and evaluated on, the state a sequential annealer would
-// also have had, because every earlier candidate was rejected and rejections
-// do not change the state).  The next batch starts at the evaluation after
-// the accepted one.  The run is therefore the sequential annealer, step for
-// step, whatever the batch size.
+// drawn from Philox-4x32-10 keyed by the run's seed, from the then-current
+// cell, and carries its own Metropolis uniform.  A batch evaluates candidates
+// n_eval .. n_eval + K - 1 against the current state; the first one accepted
+// is applied and the rest are discarded: they were drawn from, and evaluated
+// on, the state a sequential annealer would also have had, because every
+// earlier candidate was rejected and rejections do not change the state.  The
+// next batch starts at the evaluation after the accepted one, so the run is
+// the sequential annealer step for step whatever the batch size.
 //
 // Readings of Alg. 3 (whose printed loop is garbled): a global evaluation
 // counter runs to N_step; a temperature stage lasts until c_max attempts or
@@ -18,8 +17,18 @@
 // T_mult = (T_min / T_max)^(s_max / N_step); a move is accepted when
 // Delta e <= 0 or U < exp(-Delta e / T) (minimisation).
 // Modification operator (Sec. 4): exchange an interfacial phase-1 pixel with
-// an interfacial phase-0 pixel (4-neighbourhood on the torus), each drawn
-// uniformly from its list.
+// an interfacial phase-0 pixel (4-neighbourhood on the torus), each uniform
+// over its set: attempt j = 0, 1, ... of candidate n draws Philox with counter
+// (n_lo, n_hi, j, 0); word 0 and word 1 propose a pixel each by
+// floor(r * H*W / 2^32), and the first proposal of the right phase that is
+// interfacial is kept (rejection sampling); word 2 of attempt 0 gives
+// U = ((r >> 8) + 1/2) / 2^24 in float32.
+//
+// One batch is one kernel launch: every block stages the extended cell, draws
+// its candidates, writes their count changes and error-change partial sums;
+// the last block to finish (atomic ticket) sums the partials in a fixed
+// order, finds the first accepted candidate, applies it to the cell, the
+// extended cell and the counts, and advances the schedule.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -27,7 +36,7 @@
 #include <vector>
 
 #include "../../include/lpf.h"
-#include "lpf_device.cuh"
+#include "lpf_delta.cuh"
 #include "lpf_state.hpp"
 
 namespace lpf {
@@ -48,6 +57,8 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+constexpr int kMaxTries = 1 << 16;  // rejection-sampling attempts before giving up (identity)
+
 struct SaDev {
   double T, T_mult, e;
   long long n_eval, n_accept, n_batches, n_cand, c_stage, s_stage;
@@ -56,152 +67,285 @@ struct SaDev {
   int k_eff, k_min, k_max, done;
   int acc_pair[2];
   float acc_de;
-  int n1, n0;          // interfacial list sizes of the current batch
   unsigned int key0, key1;
+  unsigned int ticket;   // blocks of the current batch that finished
+  // learned proposer (see lpf_sa_set_proposer)
+  int use_model;
+  float eps;
+  const float* cdf1;     // inclusive prefix sums of the phase-1 sampling weights [H*W]
+  const float* cdf0;
+  float tot1, tot0;
 };
 
-constexpr int kProposeThreads = 1024;
+// Pixel value (0/1) of cell index c from an extended cell.
+__device__ __forceinline__ int ext_pixel(const uint8_t* e, int c, const DeltaArgs& g) {
+  return e[delta_ext_pos(c, g.W, g.We, g.rx, g.ry)];
+}
 
-// Interfacial lists (raster order) and the batch's candidates and uniforms.
-__global__ void __launch_bounds__(kProposeThreads) sa_propose_kernel(const uint8_t* __restrict__ cell, int H, int W,
-                                                                    SaDev* st, int32_t* __restrict__ list1,
-                                                                    int32_t* __restrict__ list0,
-                                                                    int32_t* __restrict__ pairs, float* __restrict__ u) {
-  __shared__ int s_c1[kProposeThreads], s_c0[kProposeThreads];
-  const int tid = threadIdx.x;
-  const int npix = H * W;
-  const int per = (npix + kProposeThreads - 1) / kProposeThreads;
-  const int p0 = min(npix, tid * per), p1 = min(npix, p0 + per);
-  int c1 = 0, c0 = 0;
+__device__ __forceinline__ bool interfacial(const uint8_t* e, int c, const DeltaArgs& g) {
+  const int y = c / g.W, x = c - y * g.W;
+  const int v = e[(y + g.ry) * g.We + x + g.rx];
+  const int l = e[(y + g.ry) * g.We + (x == 0 ? g.W - 1 : x - 1) + g.rx];
+  const int r = e[(y + g.ry) * g.We + (x == g.W - 1 ? 0 : x + 1) + g.rx];
+  const int t = e[((y == 0 ? g.H - 1 : y - 1) + g.ry) * g.We + x + g.rx];
+  const int b = e[((y == g.H - 1 ? 0 : y + 1) + g.ry) * g.We + x + g.rx];
+  return (l != v) | (r != v) | (t != v) | (b != v);
+}
+
+// Smallest pixel index p with cdf[p] > t (t < cdf[npix-1]).
+__device__ __forceinline__ int cdf_search(const float* __restrict__ cdf, int npix, float t) {
+  int lo = 0, hi = npix - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(cdf + mid) > t) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Candidate n of the run: (a, b, U); a == b == 0 when no pair was found.
+// With a model (use_model and the draw's word 3 >= epsilon), each pixel is
+// drawn from the model's sampling weights instead of uniformly.
+__device__ void draw_candidate(const uint8_t* e, const DeltaArgs& g, unsigned long long n, uint32_t k0, uint32_t k1,
+                               int& a, int& b, float& u, const SaDev* st = nullptr) {
+  const unsigned npix = (unsigned)(g.H * g.W);
+  a = -1;
+  b = -1;
+  bool model = false;
+  for (uint32_t j = 0; j < (uint32_t)kMaxTries && (a < 0 || b < 0); ++j) {
+    const U4 r = philox4x32_10(U4{(uint32_t)n, (uint32_t)(n >> 32), j, 0u}, k0, k1);
+    if (j == 0) {
+      u = ((float)(r.z >> 8) + 0.5f) * (1.0f / 16777216.0f);
+      model = st && st->use_model && st->tot1 > 0.0f && st->tot0 > 0.0f &&
+              ((float)(r.w >> 8) + 0.5f) * (1.0f / 16777216.0f) >= st->eps;
+    }
+    if (a < 0) {
+      const int c = model ? cdf_search(st->cdf1, (int)npix, ((float)(r.x >> 8) + 0.5f) * (1.0f / 16777216.0f) * st->tot1)
+                          : (int)(((unsigned long long)r.x * npix) >> 32);
+      if (ext_pixel(e, c, g) == 1 && interfacial(e, c, g)) a = c;
+    }
+    if (b < 0) {
+      const int c = model ? cdf_search(st->cdf0, (int)npix, ((float)(r.y >> 8) + 0.5f) * (1.0f / 16777216.0f) * st->tot0)
+                          : (int)(((unsigned long long)r.y * npix) >> 32);
+      if (ext_pixel(e, c, g) == 0 && interfacial(e, c, g)) b = c;
+    }
+  }
+  if (a < 0 || b < 0) { a = 0; b = 0; }
+}
+
+// Sampling tables of the model: w_p = exp((s_p - max s) / tau) over the
+// interfacial pixels of each phase (0 elsewhere), inclusive prefix sums in
+// pixel order (one block; fixed summation order).
+constexpr int kTableThreads = 1024;
+__global__ void __launch_bounds__(kTableThreads) sa_tables_kernel(const uint8_t* __restrict__ ext, DeltaArgs g,
+                                                                  const float* __restrict__ scores, float tau,
+                                                                  float* __restrict__ cdf1, float* __restrict__ cdf0,
+                                                                  SaDev* st) {
+  __shared__ float s_red[2][kTableThreads];
+  const int npix = g.H * g.W;
+  const int per = (npix + kTableThreads - 1) / kTableThreads;
+  const int p0 = min(npix, (int)threadIdx.x * per), p1 = min(npix, p0 + per);
+  float m1 = -3.0e38f, m0 = -3.0e38f;
   for (int p = p0; p < p1; ++p) {
-    const int y = p / W, x = p - y * W;
-    const int v = cell[p];
-    const int l = cell[y * W + (x == 0 ? W - 1 : x - 1)], r = cell[y * W + (x == W - 1 ? 0 : x + 1)];
-    const int t = cell[(y == 0 ? H - 1 : y - 1) * W + x], b = cell[(y == H - 1 ? 0 : y + 1) * W + x];
-    const bool inter = (l != v) | (r != v) | (t != v) | (b != v);
-    if (inter) { if (v) ++c1; else ++c0; }
+    if (!interfacial(ext, p, g)) continue;
+    if (ext_pixel(ext, p, g)) m1 = fmaxf(m1, scores[2 * p + 1]); else m0 = fmaxf(m0, scores[2 * p]);
   }
-  s_c1[tid] = c1;
-  s_c0[tid] = c0;
+  s_red[0][threadIdx.x] = m1;
+  s_red[1][threadIdx.x] = m0;
   __syncthreads();
-  // exclusive scan (Hillis-Steele on both counts)
-  for (int o = 1; o < kProposeThreads; o <<= 1) {
-    const int a1 = tid >= o ? s_c1[tid - o] : 0, a0 = tid >= o ? s_c0[tid - o] : 0;
-    __syncthreads();
-    s_c1[tid] += a1;
-    s_c0[tid] += a0;
+  for (int o = kTableThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s_red[0][threadIdx.x] = fmaxf(s_red[0][threadIdx.x], s_red[0][threadIdx.x + o]);
+      s_red[1][threadIdx.x] = fmaxf(s_red[1][threadIdx.x], s_red[1][threadIdx.x + o]);
+    }
     __syncthreads();
   }
-  int o1 = s_c1[tid] - c1, o0 = s_c0[tid] - c0;
-  const int n1 = s_c1[kProposeThreads - 1], n0 = s_c0[kProposeThreads - 1];
+  m1 = s_red[0][0];
+  m0 = s_red[1][0];
+  __syncthreads();
+  float a1 = 0.0f, a0 = 0.0f;
   for (int p = p0; p < p1; ++p) {
-    const int y = p / W, x = p - y * W;
-    const int v = cell[p];
-    const int l = cell[y * W + (x == 0 ? W - 1 : x - 1)], r = cell[y * W + (x == W - 1 ? 0 : x + 1)];
-    const int t = cell[(y == 0 ? H - 1 : y - 1) * W + x], b = cell[(y == H - 1 ? 0 : y + 1) * W + x];
-    const bool inter = (l != v) | (r != v) | (t != v) | (b != v);
-    if (inter) { if (v) list1[o1++] = p; else list0[o0++] = p; }
+    const bool in = interfacial(ext, p, g);
+    const int v = ext_pixel(ext, p, g);
+    a1 += (in && v) ? __expf((scores[2 * p + 1] - m1) / tau) : 0.0f;
+    a0 += (in && !v) ? __expf((scores[2 * p] - m0) / tau) : 0.0f;
+  }
+  s_red[0][threadIdx.x] = a1;
+  s_red[1][threadIdx.x] = a0;
+  __syncthreads();
+  if (threadIdx.x == 0) {  // exclusive offsets in thread order
+    float c1 = 0.0f, c0 = 0.0f;
+    for (int t = 0; t < kTableThreads; ++t) {
+      const float x1 = s_red[0][t], x0 = s_red[1][t];
+      s_red[0][t] = c1;
+      s_red[1][t] = c0;
+      c1 += x1;
+      c0 += x0;
+    }
+    st->tot1 = c1;
+    st->tot0 = c0;
   }
   __syncthreads();
-  if (tid == 0) {
-    st->n1 = n1;
-    st->n0 = n0;
-    if (st->done || n1 == 0 || n0 == 0 || st->n_eval >= st->n_step) { st->done = 1; st->k_eff = 0; }
-  }
-  __syncthreads();
-  const int K = st->k_eff;
-  const unsigned long long base = (unsigned long long)st->n_eval;
-  for (int k = tid; k < K; k += kProposeThreads) {
-    const unsigned long long n = base + (unsigned long long)k;
-    const U4 r = philox4x32_10(U4{(uint32_t)n, (uint32_t)(n >> 32), 0u, 0u}, st->key0, st->key1);
-    const int ia = (int)(((unsigned long long)r.x * (unsigned)n1) >> 32);
-    const int ib = (int)(((unsigned long long)r.y * (unsigned)n0) >> 32);
-    pairs[2 * k] = list1[ia];
-    pairs[2 * k + 1] = list0[ib];
-    u[k] = ((float)(r.z >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  a1 = s_red[0][threadIdx.x];
+  a0 = s_red[1][threadIdx.x];
+  for (int p = p0; p < p1; ++p) {
+    const bool in = interfacial(ext, p, g);
+    const int v = ext_pixel(ext, p, g);
+    a1 += (in && v) ? __expf((scores[2 * p + 1] - m1) / tau) : 0.0f;
+    a0 += (in && !v) ? __expf((scores[2 * p] - m0) / tau) : 0.0f;
+    cdf1[p] = a1;
+    cdf0[p] = a0;
   }
 }
 
-// First accepted candidate of the batch, temperature schedule, bookkeeping.
-__global__ void sa_accept_kernel(SaDev* st, const int32_t* __restrict__ pairs, const float* __restrict__ u,
-                                 const float* __restrict__ de, int32_t* __restrict__ log_idx) {
-  const int lane = threadIdx.x;
-  const int K = st->k_eff;
-  const long long c0 = st->c_stage;
-  const long long cmax = st->c_max;
+// Candidates n0 .. n0+K-1 drawn from the extended cell in global memory.
+__global__ void sa_draw_kernel(const uint8_t* __restrict__ ext, DeltaArgs g, unsigned long long n0, int K,
+                               uint32_t k0, uint32_t k1, int32_t* __restrict__ pairs, float* __restrict__ u,
+                               const SaDev* st) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    int a, b;
+    float uu;
+    draw_candidate(ext, g, n0 + (unsigned long long)k, k0, k1, a, b, uu, st);
+    pairs[2 * k] = a;
+    pairs[2 * k + 1] = b;
+    u[k] = uu;
+  }
+}
+
+// One annealing batch (see the file comment).
+__global__ void __launch_bounds__(kDeltaThreads) sa_batch_kernel(
+    SaDev* __restrict__ st, uint8_t* __restrict__ cell, uint8_t* __restrict__ ext, DeltaArgs g,
+    int32_t* __restrict__ pairs, float* __restrict__ u, int32_t* __restrict__ dcounts, float* __restrict__ partial,
+    unsigned long long* __restrict__ counts, int* __restrict__ status) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ float warp_acc[kDeltaWarps];
+  __shared__ int s_a, s_b, s_last, s_kstar;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ch = blockIdx.x;
+  const int Keff = st->done ? 0 : st->k_eff;
+  const unsigned long long n0 = (unsigned long long)st->n_eval;
+
+  if ((int)blockIdx.y < Keff) {
+    if (!delta_stage(sm, ext, g.ext_bytes, &bar)) {
+      if (threadIdx.x == 0) atomicOr(status, 1);
+      (void)mbar_wait(&bar, 0);
+    } else {
+      const int v0 = g.chunk[ch], v1 = g.chunk[ch + 1];
+      for (int k = blockIdx.y; k < Keff; k += gridDim.y) {
+        if (threadIdx.x == 0) {
+          int a, b;
+          float uu;
+          draw_candidate(sm, g, n0 + (unsigned long long)k, st->key0, st->key1, a, b, uu, st);
+          if (ch == 0) { pairs[2 * k] = a; pairs[2 * k + 1] = b; u[k] = uu; }
+          s_a = a;
+          s_b = b;
+          if (a != b) { delta_mark(sm, a, kMarkA, g); delta_mark(sm, b, kMarkB, g); }
+        }
+        __syncthreads();
+        const int a = s_a, b = s_b;
+        int32_t* dk = dcounts + (int64_t)k * 2 * g.n_canon;
+        float acc = 0.0f;
+        if (a == b) delta_zero_vectors(g, v0, v1, dk);
+        else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk);
+        if (lane == 0) warp_acc[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          float s = 0.0f;
+          for (int w = 0; w < kDeltaWarps; ++w) s += warp_acc[w];
+          partial[(int64_t)k * g.n_chunks + ch] = s;
+          if (a != b) { delta_mark(sm, a, 1, g); delta_mark(sm, b, 0, g); }
+        }
+        __syncthreads();
+      }
+    }
+  }
+
+  // ---- last block: accept the first passing candidate and apply it ----
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned total = gridDim.x * gridDim.y;
+    s_last = (atomicAdd(&st->ticket, 1u) == total - 1) ? 1 : 0;
+    s_kstar = 0x7fffffff;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+
+  const long long c0 = st->c_stage, cmax = st->c_max;
   const double T0 = st->T, Tm = st->T_mult;
   const long long left = st->n_step - st->n_eval;
-  const int Kv = (int)min((long long)K, max(0LL, left));
-  int kstar = -1;
-  for (int b = 0; b < Kv && kstar < 0; b += 32) {
-    const int k = b + lane;
-    bool acc = false;
-    if (k < Kv) {
-      const double Tk = T0 * pow(Tm, (double)((c0 + k) / cmax));
-      const float d = de[k];
-      acc = d <= 0.0f || u[k] < expf(-d / (float)Tk);
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, acc);
-    if (m) kstar = b + __ffs(m) - 1;
+  const int Kv = (int)min((long long)Keff, max(0LL, left));
+  for (int k = threadIdx.x; k < Kv; k += blockDim.x) {
+    float de = 0.0f;
+    for (int c = 0; c < g.n_chunks; ++c) de += __ldcg(partial + (int64_t)k * g.n_chunks + c);
+    const double Tk = T0 * pow(Tm, (double)((c0 + k) / cmax));
+    const bool acc = de <= 0.0f || __ldcg(u + k) < expf(-de / (float)Tk);
+    if (acc) atomicMin(&s_kstar, k);
   }
-  if (lane != 0) return;
-  long long consumed = kstar >= 0 ? kstar + 1 : Kv;
-  // rejected attempts before the accepted one (or all of them)
-  long long rej = kstar >= 0 ? kstar : Kv;
-  long long c = c0 + rej, s = st->s_stage;
-  double T = T0;
-  const long long wraps = c / cmax;
-  if (wraps > 0) { s = 0; }
-  c -= wraps * cmax;
-  T *= pow(Tm, (double)wraps);
+  __syncthreads();
+  const int kstar = s_kstar == 0x7fffffff ? -1 : s_kstar;
   if (kstar >= 0) {
-    c += 1;
-    s += 1;
-    if (c >= cmax || s >= st->s_max) { c = 0; s = 0; T *= Tm; }
-    st->acc_pair[0] = pairs[2 * kstar];
-    st->acc_pair[1] = pairs[2 * kstar + 1];
-    st->acc_de = de[kstar];
-    st->e += (double)de[kstar];
-    st->n_accept += 1;
-  } else {
-    st->acc_pair[0] = 0;
-    st->acc_pair[1] = 0;
-    st->acc_de = 0.0f;
+    const int a = __ldcg(pairs + 2 * kstar), b = __ldcg(pairs + 2 * kstar + 1);
+    if (a != b) {
+      const int32_t* dk = dcounts + (int64_t)kstar * 2 * g.n_canon;
+      for (int64_t i = threadIdx.x; i < 2 * g.n_canon; i += blockDim.x) {
+        const long long d = __ldcg(dk + i);
+        if (d == 0) continue;
+        const int64_t p = i / g.n_canon, v = i - p * g.n_canon;
+        counts[p * g.n_full + g.base + v] += (unsigned long long)d;
+        if (v > 0) counts[p * g.n_full + (g.n_full - 1 - (g.base + v))] += (unsigned long long)d;
+      }
+      if (threadIdx.x == 0) {
+        const uint8_t va = cell[a];
+        cell[a] = cell[b];
+        cell[b] = va;
+        delta_mark(ext, a, cell[a], g);
+        delta_mark(ext, b, cell[b], g);
+      }
+    }
   }
-  st->c_stage = c;
-  st->s_stage = s;
-  st->T = T;
-  st->n_eval += consumed;
-  st->n_cand += K;
-  st->n_batches += 1;
-  if (log_idx) log_idx[0] = kstar;
-  // batch size for the next batch: about 4 expected acceptances' worth
-  if (consumed > 0) {
-    const double obs = (kstar >= 0 ? 1.0 : 0.0) / (double)consumed;
-    st->p_est = 0.8 * st->p_est + 0.2 * obs;
-  }
-  const double want = 4.0 / fmax(st->p_est, 1e-9);
-  st->k_eff = (int)fmin((double)st->k_max, fmax((double)st->k_min, want));
-  if (st->n_eval >= st->n_step) st->done = 1;
-}
-
-// counts += change of the accepted exchange (canonical entries and their
-// mirrors), then exchange the two pixels of the cell.
-__global__ void sa_apply_kernel(SaDev* st, uint8_t* __restrict__ cell, const int32_t* __restrict__ dc,
-                                int64_t n_canon, int64_t n_full, int64_t base, unsigned long long* __restrict__ counts) {
-  const int a = st->acc_pair[0], b = st->acc_pair[1];
-  if (a == b) return;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * n_canon; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = i / n_canon, v = i - p * n_canon;
-    const long long d = dc[i];
-    if (d == 0) continue;
-    counts[p * n_full + base + v] += (unsigned long long)d;
-    if (v > 0) counts[p * n_full + (n_full - 1 - (base + v))] += (unsigned long long)d;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const uint8_t t = cell[a];
-    cell[a] = cell[b];
-    cell[b] = t;
+  if (threadIdx.x == 0) {
+    float de_star = 0.0f;
+    if (kstar >= 0)
+      for (int c = 0; c < g.n_chunks; ++c) de_star += __ldcg(partial + (int64_t)kstar * g.n_chunks + c);
+    const long long consumed = kstar >= 0 ? kstar + 1 : Kv;
+    const long long rej = kstar >= 0 ? kstar : Kv;
+    long long c = c0 + rej, s = st->s_stage;
+    double T = T0;
+    const long long wraps = c / cmax;
+    if (wraps > 0) s = 0;
+    c -= wraps * cmax;
+    T *= pow(Tm, (double)wraps);
+    if (kstar >= 0) {
+      c += 1;
+      s += 1;
+      if (c >= cmax || s >= st->s_max) { c = 0; s = 0; T *= Tm; }
+      st->acc_pair[0] = __ldcg(pairs + 2 * kstar);
+      st->acc_pair[1] = __ldcg(pairs + 2 * kstar + 1);
+      st->acc_de = de_star;
+      st->e += (double)de_star;
+      st->n_accept += 1;
+    } else {
+      st->acc_pair[0] = 0;
+      st->acc_pair[1] = 0;
+      st->acc_de = 0.0f;
+    }
+    st->c_stage = c;
+    st->s_stage = s;
+    st->T = T;
+    st->n_eval += consumed;
+    st->n_cand += Keff;
+    if (Keff > 0) st->n_batches += 1;
+    if (consumed > 0) {
+      const double obs = (kstar >= 0 ? 1.0 : 0.0) / (double)consumed;
+      st->p_est = 0.8 * st->p_est + 0.2 * obs;
+    }
+    // next batch: about four expected acceptances' worth of candidates
+    const double want = 4.0 / fmax(st->p_est, 1e-9);
+    st->k_eff = (int)fmin((double)st->k_max, fmax((double)st->k_min, want));
+    if (st->n_eval >= st->n_step) st->done = 1;
+    st->ticket = 0u;
   }
 }
 
@@ -227,6 +371,20 @@ __global__ void sa_error_kernel(const float* __restrict__ target, const int64_t*
 
 __global__ void sa_set_error_kernel(SaDev* st, const double* e) { st->e = *e; }
 
+__global__ void build_ext_sa_kernel(const uint8_t* __restrict__ img, DeltaArgs g, uint8_t* __restrict__ ext) {
+  const int total = g.We * g.He;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)g.ext_bytes; i += gridDim.x * blockDim.x) {
+    uint8_t v = 0;
+    if (i < total) {
+      const int ey = i / g.We, ex = i - ey * g.We;
+      int y = (ey - g.ry) % g.H; if (y < 0) y += g.H;
+      int x = (ex - g.rx) % g.W; if (x < 0) x += g.W;
+      v = img[y * g.W + x];
+    }
+    ext[i] = v;
+  }
+}
+
 }  // namespace lpf
 
 struct lpf_sa {
@@ -236,34 +394,49 @@ struct lpf_sa {
   const float* target = nullptr;
   int64_t* counts = nullptr;
   lpf_sa_params prm{};
+  lpf::DeltaArgs g{};
+  dim3 grid;
   lpf::SaDev* d_st = nullptr;
-  int32_t* d_list = nullptr;    // [2][H*W]
+  uint8_t* d_ext = nullptr;
   int32_t* d_pairs = nullptr;   // [k_max][2]
   float* d_u = nullptr;         // [k_max]
   float* d_de = nullptr;        // [k_max]
   float* d_partial = nullptr;   // [k_max][n_chunks]
-  int32_t* d_dc = nullptr;      // [2][n_canon]
-  float* d_partial1 = nullptr;  // [n_chunks] (accepted-pair delta)
+  int32_t* d_dc = nullptr;      // [k_max][2][n_canon]
   double* d_e = nullptr;
+  int* d_status = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_batches = 0;
+  lpf_cnn* cnn = nullptr;       // learned proposer (optional)
+  float tau = 1.0f;
+  int refresh = 16;
+  float* d_cdf = nullptr;       // [2][H*W] sampling tables
 };
 
 namespace lpf {
 
+static int g_sa_attr = 0;
+
+// Score the current cell with the network and rebuild the sampling tables.
+static void enqueue_refresh(lpf_sa* sa, cudaStream_t s) {
+  if (!sa->cnn) return;
+  cnn_forward(sa->cnn, sa->cell, s);
+  const size_t npix = (size_t)sa->H * sa->W;
+  sa_tables_kernel<<<1, kTableThreads, 0, s>>>(sa->d_ext, sa->g, cnn_scores(sa->cnn), sa->tau, sa->d_cdf,
+                                               sa->d_cdf + npix, sa->d_st);
+}
+
 static void enqueue_batch(lpf_sa* sa, cudaStream_t s) {
-  const Paths& h = sa->paths->host;
-  sa_propose_kernel<<<1, kProposeThreads, 0, s>>>(sa->cell, sa->H, sa->W, sa->d_st, sa->d_list,
-                                                    sa->d_list + (size_t)sa->H * sa->W, sa->d_pairs, sa->d_u);
-  delta_launch(sa->cell, sa->H, sa->W, sa->paths, sa->d_pairs, sa->prm.k_max, &sa->d_st->k_eff, nullptr,
-               sa->target, sa->counts, sa->d_de, sa->d_partial, s);
-  sa_accept_kernel<<<1, 32, 0, s>>>(sa->d_st, sa->d_pairs, sa->d_u, sa->d_de, nullptr);
-  delta_launch(sa->cell, sa->H, sa->W, sa->paths, sa->d_st->acc_pair, 1, nullptr, sa->d_dc, nullptr, nullptr,
-               nullptr, sa->d_partial1, s);
-  const int blocks = (int)std::min<int64_t>((2 * h.n_canon + 255) / 256, 1024);
-  sa_apply_kernel<<<blocks, 256, 0, s>>>(sa->d_st, sa->cell, sa->d_dc, h.n_canon, h.n_full, h.base,
-                                         reinterpret_cast<unsigned long long*>(sa->counts));
+  sa_batch_kernel<<<sa->grid, kDeltaThreads, sa->g.ext_bytes, s>>>(
+      sa->d_st, sa->cell, sa->d_ext, sa->g, sa->d_pairs, sa->d_u, sa->d_dc, sa->d_partial,
+      reinterpret_cast<unsigned long long*>(sa->counts), sa->d_status);
+}
+
+static int sa_device_state(lpf_sa* sa, SaDev& st, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(&st, sa->d_st, sizeof(st), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return set_cuda_error(e);
 }
 
 }  // namespace lpf
@@ -275,14 +448,26 @@ int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, con
   if (!out) return LPF_EINVAL;
   *out = nullptr;
   if (!cell_dev || !paths || !target_dev || !counts_dev || !prm) return LPF_EINVAL;
-  if (prm->k_max < 1 || prm->k_max > (1 << 20) || prm->k_min < 1 || prm->k_min > prm->k_max) return LPF_EINVAL;
+  if (prm->k_max < 1 || prm->k_max > (1 << 16) || prm->k_min < 1 || prm->k_min > prm->k_max) return LPF_EINVAL;
   if (prm->n_step < 1 || prm->c_max < 1 || prm->s_max < 1 || !(prm->t_min_ratio > 0.0)) return LPF_EINVAL;
   if ((int64_t)H * W > (1 << 24)) return LPF_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   int rc = lpf_full(cell_dev, H, W, paths, counts_dev, stream);
   if (rc) return rc;
-  rc = lpf::delta_prepare(paths, H, W, prm->k_max);
+  rc = lpf::delta_prepare(paths, H, W, 1);
   if (rc) return rc;
+  if (!lpf::g_sa_attr) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, lpf::sa_batch_kernel);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(lpf::sa_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return lpf::set_cuda_error(e);
+    lpf::g_sa_attr = 1;
+  }
   lpf_sa* sa = new (std::nothrow) lpf_sa();
   if (!sa) return LPF_ENOMEM;
   sa->paths = paths;
@@ -292,20 +477,27 @@ int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, con
   sa->target = target_dev;
   sa->counts = counts_dev;
   sa->prm = *prm;
-  const int nch = paths->delta.n_chunks;
-  const size_t npix = (size_t)H * W;
+  lpf::delta_geometry(paths, H, W, sa->g);
+  sa->g.target = target_dev;
+  sa->g.counts = counts_dev;
+  const int nch = sa->g.n_chunks;
+  sa->grid = dim3(nch, lpf::delta_stride(nch, prm->k_max));
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&sa->d_st, sizeof(lpf::SaDev));
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_list, 2 * npix * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_ext, sa->g.ext_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&sa->d_pairs, 2 * (size_t)prm->k_max * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&sa->d_u, (size_t)prm->k_max * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&sa->d_de, (size_t)prm->k_max * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&sa->d_partial, (size_t)prm->k_max * nch * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_dc, 2 * (size_t)paths->host.n_canon * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_partial1, (size_t)nch * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_dc, (size_t)prm->k_max * 2 * (size_t)paths->host.n_canon * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&sa->d_e, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(sa->d_status, 0, sizeof(int), s);
   if (e != cudaSuccess) { lpf_sa_free(sa); return lpf::set_cuda_error(e); }
-
+  {
+    const int blocks = (int)std::min<int64_t>((sa->g.ext_bytes + 255) / 256, 4096);
+    lpf::build_ext_sa_kernel<<<blocks, 256, 0, s>>>(cell_dev, sa->g, sa->d_ext);
+  }
   // initial error from the exact counts
   lpf::sa_error_kernel<<<1, 256, 0, s>>>(target_dev, counts_dev, paths->host.n_full, paths->host.base,
                                          1.0 / ((double)H * (double)W), sa->d_e);
@@ -327,22 +519,18 @@ int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, con
   st.k_eff = prm->k_min;
   st.key0 = (unsigned)(prm->seed & 0xffffffffu);
   st.key1 = (unsigned)(prm->seed >> 32);
-  e = cudaMemcpyAsync(sa->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) { lpf_sa_free(sa); return lpf::set_cuda_error(e); }
 
   if (!(prm->t_max > 0.0)) {
     // T_max so that an uphill move of average size is accepted with
-    // probability 1/2 at the start: sample k_max candidates of the initial
-    // state, T_max = -mean(positive Delta e) / ln(0.5).
-    int32_t kk = prm->k_max;
-    e = cudaMemcpyAsync(&sa->d_st->k_eff, &kk, sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) { lpf_sa_free(sa); return lpf::set_cuda_error(e); }
-    lpf::sa_propose_kernel<<<1, lpf::kProposeThreads, 0, s>>>(cell_dev, H, W, sa->d_st, sa->d_list,
-                                                              sa->d_list + npix, sa->d_pairs, sa->d_u);
-    rc = lpf::delta_launch(cell_dev, H, W, paths, sa->d_pairs, prm->k_max, nullptr, nullptr, target_dev,
-                           counts_dev, sa->d_de, sa->d_partial, s);
-    std::vector<float> de(prm->k_max);
+    // probability 1/2 at the start: k_max candidates of the initial state,
+    // T_max = -mean(positive Delta e) / ln(0.5).
+    const int K = prm->k_max;
+    lpf::sa_draw_kernel<<<(K + 127) / 128, 128, 0, s>>>(sa->d_ext, sa->g, 0ull, K, st.key0, st.key1, sa->d_pairs,
+                                                        sa->d_u, nullptr);
+    rc = lpf::delta_prepare(paths, H, W, K);
+    if (!rc) rc = lpf_delta_swap(cell_dev, H, W, paths, sa->d_pairs, K, nullptr, target_dev, counts_dev, sa->d_de,
+                                 stream);
+    std::vector<float> de(K);
     if (!rc) {
       e = cudaMemcpyAsync(de.data(), sa->d_de, de.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -353,14 +541,12 @@ int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, con
     int npos = 0;
     for (float d : de)
       if (d > 0.0f) { sum += d; ++npos; }
-    const double tmax = npos ? -(sum / npos) / std::log(0.5) : 1e-12;
-    st.T = tmax;
-    sa->prm.t_max = tmax;
-    st.k_eff = prm->k_min;
-    e = cudaMemcpyAsync(sa->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { lpf_sa_free(sa); return lpf::set_cuda_error(e); }
+    st.T = npos ? -(sum / npos) / std::log(0.5) : 1e-12;
+    sa->prm.t_max = st.T;
   }
+  e = cudaMemcpyAsync(sa->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { lpf_sa_free(sa); return lpf::set_cuda_error(e); }
   *out = sa;
   return LPF_OK;
 }
@@ -372,24 +558,20 @@ int lpf_sa_run(lpf_sa* sa, int32_t n_batches, lpf_stream_t stream) {
   (void)cudaGetLastError();
   // One captured graph holds kGraphBatches batches; replay it, then enqueue
   // the remainder directly.
-  const int kGraphBatches = 8;
+  const int kGraphBatches = sa->cnn ? sa->refresh : 16;
   cudaError_t e = cudaSuccess;
   if (!sa->exec && n_batches >= kGraphBatches) {
-    // the handle's optional timer events are not recorded inside the graph
-    cudaEvent_t ta = sa->paths->ev_start, tb = sa->paths->ev_stop;
-    sa->paths->ev_start = sa->paths->ev_stop = nullptr;
     cudaStream_t cs;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return lpf::set_cuda_error(e);
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+      lpf::enqueue_refresh(sa, cs);
       for (int i = 0; i < kGraphBatches; ++i) lpf::enqueue_batch(sa, cs);
       e = cudaStreamEndCapture(cs, &sa->graph);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&sa->exec, sa->graph, 0);
     cudaStreamDestroy(cs);
-    sa->paths->ev_start = ta;
-    sa->paths->ev_stop = tb;
     if (e != cudaSuccess) { sa->exec = nullptr; return lpf::set_cuda_error(e); }
     sa->graph_batches = kGraphBatches;
   }
@@ -399,17 +581,50 @@ int lpf_sa_run(lpf_sa* sa, int32_t n_batches, lpf_stream_t stream) {
     if (e != cudaSuccess) return lpf::set_cuda_error(e);
     left -= sa->graph_batches;
   }
+  if (left > 0) lpf::enqueue_refresh(sa, s);
   for (; left > 0; --left) lpf::enqueue_batch(sa, s);
+  return lpf::set_cuda_error(cudaGetLastError());
+}
+
+int lpf_sa_set_proposer(lpf_sa* sa, lpf_cnn* cnn, float epsilon, float tau, int32_t refresh) {
+  if (!sa || !(epsilon >= 0.0f && epsilon <= 1.0f) || !(tau > 0.0f) || refresh < 1) return LPF_EINVAL;
+  if (cnn && !lpf::cnn_matches(cnn, sa->H, sa->W)) return LPF_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return lpf::set_cuda_error(e);
+  if (cnn && !sa->d_cdf) {
+    e = cudaMalloc(&sa->d_cdf, 2 * sizeof(float) * (size_t)sa->H * sa->W);
+    if (e != cudaSuccess) return lpf::set_cuda_error(e);
+  }
+  lpf::SaDev st;
+  int rc = lpf::sa_device_state(sa, st, 0);
+  if (rc) return rc;
+  st.use_model = cnn ? 1 : 0;
+  st.eps = epsilon;
+  st.cdf1 = sa->d_cdf;
+  st.cdf0 = sa->d_cdf ? sa->d_cdf + (size_t)sa->H * sa->W : nullptr;
+  st.tot1 = st.tot0 = 0.0f;
+  e = cudaMemcpy(sa->d_st, &st, sizeof(st), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return lpf::set_cuda_error(e);
+  sa->cnn = cnn;
+  sa->tau = tau;
+  sa->refresh = refresh;
+  if (sa->exec) { cudaGraphExecDestroy(sa->exec); sa->exec = nullptr; }
+  if (sa->graph) { cudaGraphDestroy(sa->graph); sa->graph = nullptr; }
+  if (cnn) {
+    lpf::enqueue_refresh(sa, 0);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return lpf::set_cuda_error(e);
+  }
   return lpf::set_cuda_error(cudaGetLastError());
 }
 
 int lpf_sa_read(lpf_sa* sa, lpf_sa_stats* out, lpf_stream_t stream) {
   if (!sa || !out) return LPF_EINVAL;
   lpf::SaDev st;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(&st, sa->d_st, sizeof(st), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return lpf::set_cuda_error(e);
+  int rc = lpf::sa_device_state(sa, st, (cudaStream_t)stream);
+  if (rc) return rc;
+  int status = 0;
+  if (cudaMemcpy(&status, sa->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LPF_ECUDA;
   out->n_eval = st.n_eval;
   out->n_accept = st.n_accept;
   out->n_batches = st.n_batches;
@@ -419,7 +634,7 @@ int lpf_sa_read(lpf_sa* sa, lpf_sa_stats* out, lpf_stream_t stream) {
   out->t_max = sa->prm.t_max;
   out->next_batch = st.k_eff;
   out->done = st.done;
-  return LPF_OK;
+  return status ? LPF_ETIMEOUT : LPF_OK;
 }
 
 int lpf_sa_recompute_error(lpf_sa* sa, double* e_out, lpf_stream_t stream) {
@@ -437,26 +652,14 @@ int lpf_sa_recompute_error(lpf_sa* sa, double* e_out, lpf_stream_t stream) {
 }
 
 int lpf_sa_propose(lpf_sa* sa, int32_t k, int32_t* pairs_dev, float* u_dev, lpf_stream_t stream) {
-  if (!sa || k < 1 || k > sa->prm.k_max || !pairs_dev || !u_dev) return LPF_EINVAL;
+  if (!sa || k < 1 || !pairs_dev || !u_dev) return LPF_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   lpf::SaDev st;
-  cudaError_t e = cudaMemcpyAsync(&st, sa->d_st, sizeof(st), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return lpf::set_cuda_error(e);
-  const int keep = st.k_eff;
-  const int done = st.done;
-  st.k_eff = k;
-  e = cudaMemcpyAsync(sa->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return lpf::set_cuda_error(e);
-  lpf::sa_propose_kernel<<<1, lpf::kProposeThreads, 0, s>>>(sa->cell, sa->H, sa->W, sa->d_st, sa->d_list,
-                                                            sa->d_list + (size_t)sa->H * sa->W, pairs_dev, u_dev);
-  e = cudaMemcpyAsync(&st, sa->d_st, sizeof(st), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return lpf::set_cuda_error(e);
-  st.k_eff = keep;
-  st.done = done;
-  e = cudaMemcpyAsync(sa->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int rc = lpf::sa_device_state(sa, st, s);
+  if (rc) return rc;
+  lpf::sa_draw_kernel<<<(k + 127) / 128, 128, 0, s>>>(sa->d_ext, sa->g, (unsigned long long)st.n_eval, k, st.key0,
+                                                      st.key1, pairs_dev, u_dev, sa->d_st);
+  cudaError_t e = cudaStreamSynchronize(s);
   return lpf::set_cuda_error(e == cudaSuccess ? cudaGetLastError() : e);
 }
 
@@ -466,14 +669,15 @@ void lpf_sa_free(lpf_sa* sa) {
   if (sa->exec) cudaGraphExecDestroy(sa->exec);
   if (sa->graph) cudaGraphDestroy(sa->graph);
   cudaFree(sa->d_st);
-  cudaFree(sa->d_list);
+  cudaFree(sa->d_ext);
   cudaFree(sa->d_pairs);
   cudaFree(sa->d_u);
   cudaFree(sa->d_de);
   cudaFree(sa->d_partial);
   cudaFree(sa->d_dc);
-  cudaFree(sa->d_partial1);
   cudaFree(sa->d_e);
+  cudaFree(sa->d_status);
+  cudaFree(sa->d_cdf);
   delete sa;
 }
 

@@ -69,6 +69,8 @@ struct lpf_paths {
   lpf::DeltaTables delta;
   float* d_partial = nullptr;    // work area: per (candidate, chunk) error changes
   size_t partial_cap = 0;        // floats
+  uint8_t* d_ext = nullptr;      // work area: periodically extended cell (bytes)
+  size_t ext_cap = 0;
 };
 
 namespace lpf {
@@ -79,10 +81,16 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b);
 // Make sure the handle is bound to the current device and has a status word
 // and a packed-image area of at least `words`.
 int ensure_device(lpf_paths* p, size_t packed_words);
-// Swap-delta: check sizes, bake tables, size the partial-sum work area for K.
+struct DeltaArgs;
+// Swap-delta: check sizes, bake tables, size the handle's work areas for K.
 int delta_prepare(lpf_paths* p, int H, int W, int K);
-// Enqueue the swap-delta kernels (k_dev: optional device count <= K).
-int delta_launch(const uint8_t* img, int H, int W, lpf_paths* p, const int32_t* pairs, int K,
-                 const int32_t* k_dev, int32_t* dcounts, const float* target, const int64_t* counts, float* de,
-                 float* partial, cudaStream_t s);
+// Fill the kernel arguments of the swap-delta kernels for an H x W cell.
+int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g);
+// Candidate strides per vector chunk for K candidates.
+int delta_stride(int n_chunks, int K);
+int delta_max_smem();
+// Learned proposer internals used by the annealer.
+void cnn_forward(lpf_cnn* c, const uint8_t* cell, cudaStream_t s);
+const float* cnn_scores(const lpf_cnn* c);   // [H][W][2] of the last forward
+bool cnn_matches(const lpf_cnn* c, int H, int W);
 }  // namespace lpf

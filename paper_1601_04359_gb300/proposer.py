@@ -1,0 +1,167 @@
+"""Learned swap proposer: data collection, training and evaluation.
+
+Orchestration only -- every step runs in the library's kernels (annealing
+batches, exact swap deltas, network forward/backward and Adam).
+
+Data: while a uniform-proposal annealing run progresses, every `gap` batches
+the current cell is copied and the next `n` candidates the annealer would
+draw are evaluated exactly (lpf_delta_swap); their error changes, standardised
+within the snapshot (y = -(de - mean) / std, clipped to [-3, 3]), are the
+targets of the additive pair score s1[a] + s0[b].
+
+Evaluation (swaps to target error): a uniform run of N evaluations reaches
+error e_U; the model-proposal run (same initial cell, seed and temperature
+schedule) is followed until its error first falls to e_U; the ratio of
+evaluations is the gain.
+
+    python -m paper_1601_04359_gb300.proposer --evaluate [--n-step 200000]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import paper_1601_04359_gb300 as lpf  # noqa: E402
+
+
+def annealing_problem(r: int = 64, cell_size: int = 128, seed: int = 5):
+    """The compression workload: target = lineal path function (|v| <= r) of a
+    512x512 clustered-disk original; random initial cell with its fraction."""
+    import torch
+
+    import synth
+    orig = synth.config3_original()
+    paths = lpf.lpf_build_paths(r, r)
+    c = lpf.lpf_full(torch.from_numpy(orig).cuda(), paths)
+    target = (c.double() / float(orig.size)).float()
+    n1 = int(round(orig.mean() * cell_size * cell_size))
+    cell0 = synth.exact_fraction_shuffle(cell_size, cell_size, n1, seed=seed)
+    return paths, target, cell0
+
+
+def collect(paths, target, cell0, n_step: int, seed: int, snapshots: int, n: int, t_max: float = 0.0,
+            gap: int | None = None):
+    """Run a uniform annealer and log `snapshots` snapshots of `n` exactly
+    evaluated candidates each.  Returns (cells, pairs, y, t_max)."""
+    import torch
+    d_cell = torch.from_numpy(cell0).cuda()
+    ann = lpf.lpf_sa_create(d_cell, paths, target, n_step=n_step, t_max=t_max, seed=seed)
+    H, W = cell0.shape
+    cells = torch.empty((snapshots, H, W), dtype=torch.uint8, device="cuda")
+    pairs = torch.empty((snapshots, n, 2), dtype=torch.int32, device="cuda")
+    ys = torch.empty((snapshots, n), dtype=torch.float32, device="cuda")
+    t_used = lpf.lpf_sa_read(ann)["t_max"]
+    if gap is None:
+        gap = max(1, n_step // (2 * snapshots))  # roughly: batches consume ~1-2 evaluations early on
+    for k in range(snapshots):
+        lpf.lpf_sa_run(ann, gap)
+        cells[k].copy_(d_cell)
+        p, _ = lpf.lpf_sa_propose(ann, n)
+        _, de = lpf.lpf_delta_swap(d_cell, paths, p, target=target, counts=ann.counts, want_dcounts=False,
+                                   want_de=True)
+        de = de.double()
+        sd = de.std().clamp_min(1e-30)
+        ys[k] = (-(de - de.mean()) / sd).clamp(-3.0, 3.0).float()
+        pairs[k] = p
+        if lpf.lpf_sa_read(ann)["done"]:
+            cells, pairs, ys = cells[:k + 1], pairs[:k + 1], ys[:k + 1]
+            break
+    return cells, pairs, ys, t_used
+
+
+def train(net, cells, pairs, ys, epochs: int = 4, batch: int = 8, lr: float = 1e-3, seed: int = 0):
+    import torch
+    rng = np.random.default_rng(seed)
+    N = cells.shape[0]
+    losses = []
+    for _ in range(epochs):
+        order = torch.from_numpy(rng.permutation(N)).cuda()
+        for i in range(0, N - batch + 1, batch):
+            idx = order[i:i + batch]
+            loss = lpf.lpf_cnn_train_step(net, cells[idx].contiguous(), pairs[idx].contiguous(), ys[idx].contiguous(),
+                                          lr)
+            losses.append(loss)
+    return [float(x.item()) for x in losses]
+
+
+def run_until(paths, target, cell0, n_step: int, seed: int, t_max: float, net=None, eps: float = 0.1,
+              tau: float = 1.0, target_error: float | None = None, chunk: int = 64):
+    """Anneal; return (evaluations when the error first reached target_error
+    (or None), final stats, seconds)."""
+    import torch
+    d_cell = torch.from_numpy(cell0).cuda()
+    ann = lpf.lpf_sa_create(d_cell, paths, target, n_step=n_step, t_max=t_max, seed=seed)
+    if net is not None:
+        lpf.lpf_sa_set_proposer(ann, net, epsilon=eps, tau=tau, refresh=16)
+    hit = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while True:
+        lpf.lpf_sa_run(ann, chunk)
+        st = lpf.lpf_sa_read(ann)
+        if target_error is not None and hit is None and st["error"] <= target_error:
+            hit = st["n_eval"]
+            break
+        if st["done"]:
+            break
+    dt = time.perf_counter() - t0
+    return hit, st, dt
+
+
+def evaluate(n_step: int = 200000, train_seeds=(11, 12), eval_seed: int = 21, snapshots: int = 192, n: int = 64,
+             epochs: int = 6):
+    import torch
+    paths, target, cell0 = annealing_problem()
+    # uniform reference run (evaluation seed)
+    _, st_u, dt_u = run_until(paths, target, cell0, n_step, eval_seed, t_max=0.0)
+    t_max = st_u["t_max"]
+    e_u = st_u["error"]
+    # training data from other seeds (their own random initial cells)
+    import synth
+    net = lpf.lpf_cnn_create(cell0.shape[0], cell0.shape[1], seed=3)
+    data = [collect(paths, target, synth.exact_fraction_shuffle(128, 128, int(cell0.sum()), seed=s), n_step, s,
+                    snapshots, n, t_max=t_max) for s in train_seeds]
+    cells = torch.cat([d[0] for d in data])
+    pairs = torch.cat([d[1] for d in data])
+    ys = torch.cat([d[2] for d in data])
+    t0 = time.perf_counter()
+    losses = train(net, cells, pairs, ys, epochs=epochs)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    hit, st_m, dt_m = run_until(paths, target, cell0, n_step, eval_seed, t_max=t_max, net=net, target_error=e_u)
+    return {
+        "workload": "128x128 cell, |v|<=64, target from 512x512 clustered disks (f=0.3)",
+        "n_step_uniform": n_step, "uniform_final_error": e_u, "uniform_seconds": dt_u,
+        "uniform_evals_per_s": st_u["n_eval"] / dt_u,
+        "model_evals_to_uniform_error": hit, "model_final": st_m, "model_seconds": dt_m,
+        "swaps_ratio": (n_step / hit) if hit else None,
+        "train_snapshots": int(cells.shape[0]), "train_candidates_per_snapshot": n, "epochs": epochs,
+        "train_seconds": t_train, "loss_first": losses[0] if losses else None,
+        "loss_last": float(np.mean(losses[-8:])) if losses else None,
+        "t_max": t_max,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--evaluate", action="store_true")
+    ap.add_argument("--n-step", type=int, default=200000)
+    ap.add_argument("--snapshots", type=int, default=192)
+    ap.add_argument("--epochs", type=int, default=6)
+    a = ap.parse_args()
+    lpf.load()
+    if a.evaluate:
+        print(json.dumps(evaluate(n_step=a.n_step, snapshots=a.snapshots, epochs=a.epochs)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

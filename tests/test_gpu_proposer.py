@@ -1,0 +1,74 @@
+"""The learned proposer inside the annealer: drawn candidates stay valid,
+epsilon = 1 gives exactly the uniform run, runs are deterministic, and the
+sampling follows the network's weights."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import sa as osa
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(gpu_lib, H=48, r=12, seed=3):
+    orig = synth.clustered_disks(2 * H, 2 * H, 0.3, seed=9)
+    p = gpu_lib.lpf_build_paths(r, r)
+    c = gpu_lib.lpf_full(torch.from_numpy(orig).cuda(), p)
+    target = (c.double() / float(orig.size)).float()
+    cell0 = synth.exact_fraction_shuffle(H, H, int(round(0.3 * H * H)), seed=seed)
+    return p, target, cell0
+
+
+def _run(gpu_lib, p, target, cell0, net, eps, n_step=3000, seed=5):
+    d = torch.from_numpy(cell0).cuda()
+    ann = gpu_lib.lpf_sa_create(d, p, target, n_step=n_step, t_max=1e-4, seed=seed, k_max=256)
+    if net is not None:
+        gpu_lib.lpf_sa_set_proposer(ann, net, epsilon=eps, tau=1.0, refresh=16)
+    while not gpu_lib.lpf_sa_read(ann)["done"]:
+        gpu_lib.lpf_sa_run(ann, 64)
+    return d.cpu().numpy(), gpu_lib.lpf_sa_read(ann), ann
+
+
+def test_epsilon_one_is_the_uniform_run(gpu_lib):
+    p, target, cell0 = _problem(gpu_lib)
+    net = gpu_lib.lpf_cnn_create(48, 48, 1)
+    a, sa_, _ = _run(gpu_lib, p, target, cell0, None, 0.0)
+    b, sb, _ = _run(gpu_lib, p, target, cell0, net, 1.0)
+    np.testing.assert_array_equal(a, b)
+    assert sa_["n_accept"] == sb["n_accept"]
+
+
+def test_model_proposals_valid_and_deterministic(gpu_lib):
+    p, target, cell0 = _problem(gpu_lib)
+    net = gpu_lib.lpf_cnn_create(48, 48, 2)
+    a, st, ann = _run(gpu_lib, p, target, cell0, net, 0.1)
+    b, _, _ = _run(gpu_lib, p, target, cell0, net, 0.1)
+    np.testing.assert_array_equal(a, b)
+    assert a.sum() == cell0.sum()
+    pairs, _ = gpu_lib.lpf_sa_propose(ann, 256)
+    pairs = pairs.cpu().numpy()
+    l1, l0 = osa.interfacial_lists(a)
+    assert np.isin(pairs[:, 0], l1).all() and np.isin(pairs[:, 1], l0).all()
+
+
+def test_sampling_follows_network_weights(gpu_lib):
+    # epsilon = 0 and a strongly peaked score map: the drawn phase-1 pixels
+    # concentrate on the highest-scoring interfacial pixels.
+    H = 32
+    p, target, cell0 = _problem(gpu_lib, H=H, r=8)
+    net = gpu_lib.lpf_cnn_create(H, H, 4)
+    d = torch.from_numpy(cell0).cuda()
+    ann = gpu_lib.lpf_sa_create(d, p, target, n_step=10 ** 6, t_max=1e-4, seed=8, k_max=4096)
+    gpu_lib.lpf_sa_set_proposer(ann, net, epsilon=0.0, tau=0.05, refresh=16)
+    pairs, _ = gpu_lib.lpf_sa_propose(ann, 4096)
+    scores = gpu_lib.lpf_cnn_forward(net, d).cpu().numpy()
+    l1, _ = osa.interfacial_lists(cell0)
+    s1 = scores.reshape(-1, 2)[l1, 1]
+    w = np.exp((s1 - s1.max()) / 0.05)
+    w /= w.sum()
+    counts = np.array([(pairs.cpu().numpy()[:, 0] == q).sum() for q in l1])
+    top = np.argsort(-w)[:5]
+    # empirical frequencies of the most likely pixels agree with their weights
+    freq = counts[top] / 4096.0
+    assert np.all(np.abs(freq - w[top]) <= 4 * np.sqrt(w[top] * (1 - w[top]) / 4096) + 2e-3)

@@ -1,0 +1,56 @@
+"""Pins for the proposer network's CPU reference: parameter count, the
+circular convolution against a direct loop, and every gradient against
+central finite differences of the loss."""
+import numpy as np
+
+import synth
+from oracle import cnn
+
+
+def test_parameter_count():
+    assert cnn.n_params() == 9 * (2 * 32 + 32 * 64 + 64 * 48 + 48 * 32 + 32 * 2) + (32 + 64 + 48 + 32 + 2) == 61234
+
+
+def test_circular_convolution_by_loops():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(5, 7, 3))
+    w = rng.normal(size=(9, 3, 4))
+    b = rng.normal(size=4)
+    out = cnn.conv(x, w, b)
+    H, W = 5, 7
+    for y in range(H):
+        for xx in range(W):
+            for co in range(4):
+                s = b[co]
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        tap = (dy + 1) * 3 + (dx + 1)
+                        s += sum(x[(y + dy) % H, (xx + dx) % W, ci] * w[tap, ci, co] for ci in range(3))
+                assert abs(out[y, xx, co] - s) < 1e-12
+
+
+def test_gradients_by_central_differences():
+    cell = synth.clustered_disks(12, 10, 0.4, seed=3)
+    x = cnn.features(cell)
+    params = cnn.init_params(5)
+    rng = np.random.default_rng(1)
+    params = [(w + 0.05 * rng.normal(size=w.shape), b + 0.05 * rng.normal(size=b.shape)) for w, b in params]
+    a_idx = np.array([3, 17, 40, 88])
+    b_idx = np.array([5, 60, 41, 100])
+    y = np.array([0.3, -1.0, 0.7, 0.0])
+    out, acts = cnn.forward(params, x)
+    grads = cnn.backward(params, acts, cnn.loss_grad_out(out, a_idx, b_idx, y))
+    eps = 1e-6
+    for li, (w, b) in enumerate(params):
+        for arr, garr in ((w, grads[li][0]), (b, grads[li][1])):
+            flat = arr.reshape(-1)
+            gflat = garr.reshape(-1)
+            for j in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+                old = flat[j]
+                flat[j] = old + eps
+                lp = cnn.loss(cnn.forward(params, x)[0], a_idx, b_idx, y)
+                flat[j] = old - eps
+                lm = cnn.loss(cnn.forward(params, x)[0], a_idx, b_idx, y)
+                flat[j] = old
+                fd = (lp - lm) / (2 * eps)
+                assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (li, j, fd, gflat[j])
