@@ -39,7 +39,37 @@ def lpf_full_512_standard(repeat):
     torch.cuda.synchronize()
 
 
-WORKLOADS = {"lpf_full_512": lpf_full_512, "lpf_full_512_standard": lpf_full_512_standard}
+def delta_128(repeat):
+    """lpf_delta_swap, 128x128 clustered cell, |v| <= 64, 4096 candidates, error changes."""
+    import numpy as np
+    cell = synth.config3_original()[:128, :128].copy()
+    p = lpf.lpf_build_paths(64, 64)
+    d = torch.from_numpy(cell).cuda()
+    counts = lpf.lpf_full(d, p)
+    target = (counts.double() / cell.size).float() * 0.9
+    rng = np.random.default_rng(0)
+    flat = cell.reshape(-1)
+    pairs = np.stack([rng.choice(np.flatnonzero(flat == 1), 4096), rng.choice(np.flatnonzero(flat == 0), 4096)], 1)
+    pairs = torch.from_numpy(pairs.astype(np.int32)).cuda()
+    for _ in range(1 + repeat):
+        lpf.lpf_delta_swap(d, p, pairs, target=target, counts=counts, want_dcounts=False, want_de=True)
+    torch.cuda.synchronize()
+
+
+def sa_128(repeat):
+    """Annealing batches on the 128x128 compression workload (one kernel per batch)."""
+    orig = synth.config3_original()
+    p = lpf.lpf_build_paths(64, 64)
+    c = lpf.lpf_full(torch.from_numpy(orig).cuda(), p)
+    target = (c.double() / float(orig.size)).float()
+    cell = torch.from_numpy(synth.exact_fraction_shuffle(128, 128, int(round(orig.mean() * 128 * 128)), seed=5)).cuda()
+    ann = lpf.lpf_sa_create(cell, p, target, n_step=10 ** 6, seed=1)
+    lpf.lpf_sa_run(ann, 8 + repeat)  # below the graph size: one launch per batch
+    torch.cuda.synchronize()
+
+
+WORKLOADS = {"lpf_full_512": lpf_full_512, "lpf_full_512_standard": lpf_full_512_standard, "delta_128": delta_128,
+             "sa_128": sa_128}
 
 
 def main():

@@ -118,7 +118,7 @@ def run_until(paths, target, cell0, n_step: int, seed: int, t_max: float, net=No
 
 
 def evaluate(n_step: int = 200000, train_seeds=(11, 12), eval_seed: int = 21, snapshots: int = 192, n: int = 64,
-             epochs: int = 6):
+             epochs: int = 6, taus=(1.0,), epss=(0.1,)):
     import torch
     paths, target, cell0 = annealing_problem()
     # uniform reference run (evaluation seed)
@@ -137,13 +137,20 @@ def evaluate(n_step: int = 200000, train_seeds=(11, 12), eval_seed: int = 21, sn
     losses = train(net, cells, pairs, ys, epochs=epochs)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    hit, st_m, dt_m = run_until(paths, target, cell0, n_step, eval_seed, t_max=t_max, net=net, target_error=e_u)
+    runs = []
+    for tau in taus:
+        for eps in epss:
+            hit, st_m, dt_m = run_until(paths, target, cell0, n_step, eval_seed, t_max=t_max, net=net, eps=eps,
+                                        tau=tau, target_error=e_u)
+            runs.append({"tau": tau, "epsilon": eps, "model_evals_to_uniform_error": hit,
+                         "swaps_ratio": (n_step / hit) if hit else None, "model_seconds": dt_m,
+                         "model_final_error": st_m["error"], "model_accepted": st_m["n_accept"]})
+    best = max(runs, key=lambda r: r["swaps_ratio"] or 0.0)
     return {
         "workload": "128x128 cell, |v|<=64, target from 512x512 clustered disks (f=0.3)",
         "n_step_uniform": n_step, "uniform_final_error": e_u, "uniform_seconds": dt_u,
-        "uniform_evals_per_s": st_u["n_eval"] / dt_u,
-        "model_evals_to_uniform_error": hit, "model_final": st_m, "model_seconds": dt_m,
-        "swaps_ratio": (n_step / hit) if hit else None,
+        "uniform_evals_per_s": st_u["n_eval"] / dt_u, "eval_seed": eval_seed, "train_seeds": list(train_seeds),
+        "runs": runs, "best": best,
         "train_snapshots": int(cells.shape[0]), "train_candidates_per_snapshot": n, "epochs": epochs,
         "train_seconds": t_train, "loss_first": losses[0] if losses else None,
         "loss_last": float(np.mean(losses[-8:])) if losses else None,
@@ -157,10 +164,14 @@ def main():
     ap.add_argument("--n-step", type=int, default=200000)
     ap.add_argument("--snapshots", type=int, default=192)
     ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--train-seeds", type=int, nargs="+", default=[11, 12])
+    ap.add_argument("--tau", type=float, nargs="+", default=[1.0])
+    ap.add_argument("--eps", type=float, nargs="+", default=[0.1])
     a = ap.parse_args()
     lpf.load()
     if a.evaluate:
-        print(json.dumps(evaluate(n_step=a.n_step, snapshots=a.snapshots, epochs=a.epochs)), flush=True)
+        print(json.dumps(evaluate(n_step=a.n_step, train_seeds=tuple(a.train_seeds), snapshots=a.snapshots,
+                                  epochs=a.epochs, taus=tuple(a.tau), epss=tuple(a.eps))), flush=True)
 
 
 if __name__ == "__main__":
