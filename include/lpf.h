@@ -298,7 +298,7 @@ typedef struct {
                           probability 1/2 (the paper tunes it by hand for s/c ~ 0.5) */
   double t_min_ratio;  /* T_min / T_max (Tab. annealing: 0.01) */
   int32_t k_max;       /* candidates per batch, upper bound (e.g. 4096) */
-  int32_t k_min;       /* candidates per batch, lower bound (e.g. 4) */
+  int32_t k_min;       /* candidates per batch, lower bound (e.g. 1) */
   uint64_t seed;       /* Philox-4x32-10 key of the run */
 } lpf_sa_params;
 
@@ -345,9 +345,11 @@ int lpf_sa_create(uint8_t *cell_dev, int32_t H, int32_t W, lpf_paths *paths,
  * evaluates all of them as lpf_delta_swap does, and its last block accepts
  * the first that passes the Metropolis test (Delta e <= 0 or
  * U < exp(-Delta e / T)), applies it to the cell and the counts and updates
- * the temperature stage; k adapts to the acceptance rate between k_min and
- * k_max.  Batches after the run is done do nothing.  The first call with
- * n_batches >= 16 captures 16 batches as a CUDA graph, replayed afterwards.
+ * the temperature stage; k adapts to the acceptance rate p (running
+ * estimate) as ceil(1/(2p)), clamped to [k_min, k_max].  Batches after the
+ * run is done do nothing.  The first call with n_batches >= 16 (or >= the
+ * proposer's refresh interval when a proposer is set) captures that many
+ * batches as a CUDA graph, replayed afterwards.
  * Errors: LPF_EINVAL, LPF_ECUDA.
  */
 int lpf_sa_run(lpf_sa *sa, int32_t n_batches, lpf_stream_t stream);

@@ -325,7 +325,7 @@ class Annealer:
 
 
 def lpf_sa_create(cell, paths: Paths, target, counts=None, n_step=1_000_000, c_max=None, s_max=None,
-                  t_max=0.0, t_min_ratio=0.01, k_max=4096, k_min=4, seed=1, stream=None) -> Annealer:
+                  t_max=0.0, t_min_ratio=0.01, k_max=4096, k_min=1, seed=1, stream=None) -> Annealer:
     """Start an annealing run on the CUDA uint8 cell (modified in place)."""
     import torch
     H, W = cell.shape

@@ -341,8 +341,10 @@ __global__ void __launch_bounds__(kDeltaThreads) sa_batch_kernel(
       const double obs = (kstar >= 0 ? 1.0 : 0.0) / (double)consumed;
       st->p_est = 0.8 * st->p_est + 0.2 * obs;
     }
-    // next batch: about four expected acceptances' worth of candidates
-    const double want = 4.0 / fmax(st->p_est, 1e-9);
+    // next batch size: a batch costs a fixed latency plus a share per
+    // candidate and yields (1 - (1-p)^K) / p evaluations; with the measured
+    // costs that ratio is best near K = 1/(2p)
+    const double want = ceil(0.5 / fmax(st->p_est, 1e-9));
     st->k_eff = (int)fmin((double)st->k_max, fmax((double)st->k_min, want));
     if (st->n_eval >= st->n_step) st->done = 1;
     st->ticket = 0u;

@@ -9,12 +9,16 @@ draw are evaluated exactly (lpf_delta_swap); their error changes, standardised
 within the snapshot (y = -(de - mean) / std, clipped to [-3, 3]), are the
 targets of the additive pair score s1[a] + s0[b].
 
-Evaluation (swaps to target error): a uniform run of N evaluations reaches
-error e_U; the model-proposal run (same initial cell, seed and temperature
-schedule) is followed until its error first falls to e_U; the ratio of
-evaluations is the gain.
+Training runs in two rounds: first on candidates of uniform-proposal runs,
+then also on candidates drawn by runs that already use the network (seeds
+distinct from the evaluation seeds).
 
-    python -m paper_1601_04359_gb300.proposer --evaluate [--n-step 200000]
+Evaluation (swaps to target error): for each evaluation seed, a uniform run
+of N evaluations reaches error e_U; the model-proposal run (same initial cell,
+seed and temperature schedule) is followed until its error first falls to
+e_U; the ratio of evaluations is the gain, reported as the median over seeds.
+
+    python -m paper_1601_04359_gb300.proposer --evaluate [--n-step 100000]
 """
 from __future__ import annotations
 
@@ -49,21 +53,26 @@ def annealing_problem(r: int = 64, cell_size: int = 128, seed: int = 5):
 
 
 def collect(paths, target, cell0, n_step: int, seed: int, snapshots: int, n: int, t_max: float = 0.0,
-            gap: int | None = None):
-    """Run a uniform annealer and log `snapshots` snapshots of `n` exactly
-    evaluated candidates each.  Returns (cells, pairs, y, t_max)."""
+            net=None, eps: float = 0.1, tau: float = 1.0):
+    """Run an annealer (uniform proposals, or the network's when `net` is
+    given) and log `snapshots` snapshots, evenly spaced in evaluations, of the
+    next `n` candidates it would draw, each evaluated exactly.
+    Returns (cells, pairs, y, t_max)."""
     import torch
     d_cell = torch.from_numpy(cell0).cuda()
     ann = lpf.lpf_sa_create(d_cell, paths, target, n_step=n_step, t_max=t_max, seed=seed)
+    if net is not None:
+        lpf.lpf_sa_set_proposer(ann, net, epsilon=eps, tau=tau, refresh=16)
     H, W = cell0.shape
     cells = torch.empty((snapshots, H, W), dtype=torch.uint8, device="cuda")
     pairs = torch.empty((snapshots, n, 2), dtype=torch.int32, device="cuda")
     ys = torch.empty((snapshots, n), dtype=torch.float32, device="cuda")
     t_used = lpf.lpf_sa_read(ann)["t_max"]
-    if gap is None:
-        gap = max(1, n_step // (2 * snapshots))  # roughly: batches consume ~1-2 evaluations early on
+    k = 0
     for k in range(snapshots):
-        lpf.lpf_sa_run(ann, gap)
+        goal = (k * n_step) // snapshots
+        while lpf.lpf_sa_read(ann)["n_eval"] < goal:
+            lpf.lpf_sa_run(ann, 16)
         cells[k].copy_(d_cell)
         p, _ = lpf.lpf_sa_propose(ann, n)
         _, de = lpf.lpf_delta_swap(d_cell, paths, p, target=target, counts=ann.counts, want_dcounts=False,
@@ -72,9 +81,6 @@ def collect(paths, target, cell0, n_step: int, seed: int, snapshots: int, n: int
         sd = de.std().clamp_min(1e-30)
         ys[k] = (-(de - de.mean()) / sd).clamp(-3.0, 3.0).float()
         pairs[k] = p
-        if lpf.lpf_sa_read(ann)["done"]:
-            cells, pairs, ys = cells[:k + 1], pairs[:k + 1], ys[:k + 1]
-            break
     return cells, pairs, ys, t_used
 
 
@@ -117,61 +123,84 @@ def run_until(paths, target, cell0, n_step: int, seed: int, t_max: float, net=No
     return hit, st, dt
 
 
-def evaluate(n_step: int = 200000, train_seeds=(11, 12), eval_seed: int = 21, snapshots: int = 192, n: int = 64,
-             epochs: int = 6, taus=(1.0,), epss=(0.1,)):
+def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22, 23), snapshots: int = 256,
+             n: int = 64, epochs: int = 8, taus=(0.7,), epss=(0.1,), on_policy: bool = True):
+    """Swaps-to-target gain of the learned proposer (median over eval seeds)."""
     import torch
-    paths, target, cell0 = annealing_problem()
-    # uniform reference run (evaluation seed)
-    _, st_u, dt_u = run_until(paths, target, cell0, n_step, eval_seed, t_max=0.0)
-    t_max = st_u["t_max"]
-    e_u = st_u["error"]
-    # training data from other seeds (their own random initial cells)
+
     import synth
-    net = lpf.lpf_cnn_create(cell0.shape[0], cell0.shape[1], seed=3)
-    data = [collect(paths, target, synth.exact_fraction_shuffle(128, 128, int(cell0.sum()), seed=s), n_step, s,
-                    snapshots, n, t_max=t_max) for s in train_seeds]
+    paths, target, cell0 = annealing_problem()
+    n1 = int(cell0.sum())
+    cells0 = {s: synth.exact_fraction_shuffle(128, 128, n1, seed=1000 + s) for s in eval_seeds}
+    # uniform reference runs
+    ref = {}
+    t_max = None
+    for s in eval_seeds:
+        _, st_u, dt_u = run_until(paths, target, cells0[s], n_step, s, t_max=t_max or 0.0)
+        t_max = t_max or st_u["t_max"]
+        ref[s] = (st_u["error"], dt_u, st_u["n_eval"] / dt_u)
+    net = lpf.lpf_cnn_create(128, 128, seed=3)
+    t0 = time.perf_counter()
+    data = [collect(paths, target, synth.exact_fraction_shuffle(128, 128, n1, seed=s), n_step, s, snapshots, n,
+                    t_max=t_max) for s in train_seeds]
     cells = torch.cat([d[0] for d in data])
     pairs = torch.cat([d[1] for d in data])
     ys = torch.cat([d[2] for d in data])
-    t0 = time.perf_counter()
     losses = train(net, cells, pairs, ys, epochs=epochs)
+    rounds = 1
+    if on_policy:
+        # second round: candidates drawn by the annealer while it uses the network
+        data2 = [collect(paths, target, synth.exact_fraction_shuffle(128, 128, n1, seed=s + 100), n_step, s + 100,
+                         snapshots, n, t_max=t_max, net=net, eps=epss[0], tau=taus[0]) for s in train_seeds]
+        cells = torch.cat([cells] + [d[0] for d in data2])
+        pairs = torch.cat([pairs] + [d[1] for d in data2])
+        ys = torch.cat([ys] + [d[2] for d in data2])
+        losses += train(net, cells, pairs, ys, epochs=max(1, epochs // 2), seed=1)
+        rounds = 2
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     runs = []
     for tau in taus:
         for eps in epss:
-            hit, st_m, dt_m = run_until(paths, target, cell0, n_step, eval_seed, t_max=t_max, net=net, eps=eps,
-                                        tau=tau, target_error=e_u)
-            runs.append({"tau": tau, "epsilon": eps, "model_evals_to_uniform_error": hit,
-                         "swaps_ratio": (n_step / hit) if hit else None, "model_seconds": dt_m,
-                         "model_final_error": st_m["error"], "model_accepted": st_m["n_accept"]})
-    best = max(runs, key=lambda r: r["swaps_ratio"] or 0.0)
+            per_seed = []
+            for s in eval_seeds:
+                e_u = ref[s][0]
+                hit, st_m, dt_m = run_until(paths, target, cells0[s], n_step, s, t_max=t_max, net=net, eps=eps,
+                                            tau=tau, target_error=e_u)
+                per_seed.append({"seed": s, "uniform_error": e_u, "model_evals": hit,
+                                 "ratio": (n_step / hit) if hit else None, "model_seconds": dt_m})
+            ratios = sorted(r["ratio"] or 0.0 for r in per_seed)
+            runs.append({"tau": tau, "epsilon": eps, "median_ratio": ratios[len(ratios) // 2], "per_seed": per_seed})
+    best = max(runs, key=lambda r: r["median_ratio"])
     return {
         "workload": "128x128 cell, |v|<=64, target from 512x512 clustered disks (f=0.3)",
-        "n_step_uniform": n_step, "uniform_final_error": e_u, "uniform_seconds": dt_u,
-        "uniform_evals_per_s": st_u["n_eval"] / dt_u, "eval_seed": eval_seed, "train_seeds": list(train_seeds),
-        "runs": runs, "best": best,
+        "n_step_uniform": n_step, "uniform": {str(s): {"error": v[0], "seconds": v[1], "evals_per_s": v[2]}
+                                              for s, v in ref.items()},
+        "train_seeds": list(train_seeds), "eval_seeds": list(eval_seeds), "rounds": rounds,
+        "runs": runs, "best": {"tau": best["tau"], "epsilon": best["epsilon"], "median_ratio": best["median_ratio"]},
         "train_snapshots": int(cells.shape[0]), "train_candidates_per_snapshot": n, "epochs": epochs,
-        "train_seconds": t_train, "loss_first": losses[0] if losses else None,
-        "loss_last": float(np.mean(losses[-8:])) if losses else None,
-        "t_max": t_max,
+        "train_and_collect_seconds": t_train, "loss_first": losses[0] if losses else None,
+        "loss_last": float(np.mean(losses[-8:])) if losses else None, "t_max": t_max,
     }
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--evaluate", action="store_true")
-    ap.add_argument("--n-step", type=int, default=200000)
-    ap.add_argument("--snapshots", type=int, default=192)
-    ap.add_argument("--epochs", type=int, default=6)
-    ap.add_argument("--train-seeds", type=int, nargs="+", default=[11, 12])
-    ap.add_argument("--tau", type=float, nargs="+", default=[1.0])
+    ap.add_argument("--n-step", type=int, default=100000)
+    ap.add_argument("--snapshots", type=int, default=256)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--train-seeds", type=int, nargs="+", default=[11, 12, 13])
+    ap.add_argument("--eval-seeds", type=int, nargs="+", default=[21, 22, 23])
+    ap.add_argument("--tau", type=float, nargs="+", default=[0.7])
     ap.add_argument("--eps", type=float, nargs="+", default=[0.1])
+    ap.add_argument("--no-on-policy", action="store_true")
     a = ap.parse_args()
     lpf.load()
     if a.evaluate:
-        print(json.dumps(evaluate(n_step=a.n_step, train_seeds=tuple(a.train_seeds), snapshots=a.snapshots,
-                                  epochs=a.epochs, taus=tuple(a.tau), epss=tuple(a.eps))), flush=True)
+        print(json.dumps(evaluate(n_step=a.n_step, train_seeds=tuple(a.train_seeds), eval_seeds=tuple(a.eval_seeds),
+                                  snapshots=a.snapshots, epochs=a.epochs, taus=tuple(a.tau), epss=tuple(a.eps),
+                                  on_policy=not a.no_on_policy)), flush=True)
 
 
 if __name__ == "__main__":
