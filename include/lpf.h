@@ -159,6 +159,19 @@ int lpf_full_noalloc(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *pa
                      int64_t *counts_dev, lpf_stream_t stream);
 
 /*
+ * Monte-Carlo approximation of Sec. 3 (opening): the segments are compared
+ * with the image only at the selected translations -- sel_dev: H*W uint8,
+ * nonzero = translation (x, y) selected (e.g. a random N-combination of the
+ * W*H positions).  counts_dev receives, for every vector of D (the canonical
+ * half), the number of selected translations whose segment lies in each
+ * phase, so that L~ = counts / N; as in the paper, which evaluates D only,
+ * the other half is filled by point symmetry.  All translations selected
+ * gives lpf_full's counts.  Errors as lpf_full.
+ */
+int lpf_full_mc(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths, const uint8_t *sel_dev,
+                int64_t *counts_dev, lpf_stream_t stream);
+
+/*
  * Autotuner for lpf_full: times every admissible launch shape (words per
  * thread T in {1,2,4,8}, 32-row bands per block BB in {1,2,4,8}) of the walk
  * kernel on this image (3 timed runs each, fastest kept) and stores the

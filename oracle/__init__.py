@@ -17,6 +17,7 @@ Functions and the passages they follow:
   objective(target, counts, ...)   Eq. (LSE), double precision
   delta_objective(...)             Eq. (LSE) after minus before, double precision
   s2_direct(img, phase)            Eq. (S2dis), direct double sum
+  lpf_full_selected(img, rx, ry, sel)   Sec. 3 Monte-Carlo variant (selected translations)
 Parity status: every function above is pinned by ``tests/test_oracle_*.py``.
 """
 from __future__ import annotations
@@ -48,6 +49,7 @@ def _load():
         lib.lpfo_objective.restype = ctypes.c_double
         lib.lpfo_delta_objective.argtypes = [p, p, p, i32, i32, i32, i32, i32, p]
         lib.lpfo_s2_direct.argtypes = [p, i32, i32, i32, p]
+        lib.lpfo_lpf_full_sel.argtypes = [p, i32, i32, i32, i32, p, p]
         _lib = lib
     return _lib
 
@@ -97,6 +99,18 @@ def lpf_full(img, rx: int, ry: int) -> np.ndarray:
     n_full, _, _ = window_sizes(rx, ry)
     out = np.zeros((2, n_full), np.int64)
     _load().lpfo_lpf_full(_ptr(a), H, W, rx, ry, _ptr(out))
+    return out
+
+
+def lpf_full_selected(img, rx: int, ry: int, sel) -> np.ndarray:
+    """Counts over the selected translations only (Monte-Carlo variant of Sec. 3)."""
+    a = _img(img)
+    H, W = a.shape
+    s = np.ascontiguousarray(sel, dtype=np.uint8)
+    assert s.shape == a.shape
+    n_full, _, _ = window_sizes(rx, ry)
+    out = np.zeros((2, n_full), np.int64)
+    _load().lpfo_lpf_full_sel(_ptr(a), H, W, rx, ry, _ptr(s), _ptr(out))
     return out
 
 

@@ -134,6 +134,42 @@ void lpfo_lpf_full(const uint8_t *img, int H, int W, int rx, int ry, int64_t *co
     }
 }
 
+/*
+ * Monte-Carlo approximation of Sec. 3 (opening): the segments are compared
+ * with the image only at the selected translations x (sel[y*W + x] != 0);
+ * counts[p][k] = number of selected translations whose segment lies in phase
+ * p, full layout, every vector evaluated directly (Alg. 1 with the
+ * translation loop restricted to the selection).  L~ = counts / N, N = number
+ * of selected translations.
+ */
+void lpfo_lpf_full_sel(const uint8_t *img, int H, int W, int rx, int ry, const uint8_t *sel, int64_t *counts) {
+    int nx = 2 * rx + 1, ny = 2 * ry + 1;
+    int64_t nfull = (int64_t)nx * ny;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nfull; ++k) {
+        int dy = (int)(k / nx) - ry, dx = (int)(k % nx) - rx;
+        int n = (iabs(dx) > iabs(dy) ? iabs(dx) : iabs(dy)) + 1;
+        int32_t *sx = (int32_t *)malloc(sizeof(int32_t) * n);
+        int32_t *sy = (int32_t *)malloc(sizeof(int32_t) * n);
+        lpfo_segment(dx, dy, sx, sy);
+        for (int p = 0; p < 2; ++p) {
+            int64_t L = 0;
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    if (!sel[(int64_t)y * W + x]) continue;
+                    int pix;
+                    for (pix = 0; pix < n; ++pix) {
+                        int xx = imod(x + sx[pix], W), yy = imod(y + sy[pix], H);
+                        if (img[(int64_t)yy * W + xx] != p) break;
+                    }
+                    if (pix == n) L += 1;
+                }
+            counts[p * nfull + k] = L;
+        }
+        free(sx); free(sy);
+    }
+}
+
 /* Counts for an explicit list of vectors: out[2*i + p] for vec (dx[i], dy[i]). */
 void lpfo_count_list(const uint8_t *img, int H, int W, const int32_t *dx,
                      const int32_t *dy, int n, int64_t *out) {

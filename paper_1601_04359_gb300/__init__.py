@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = [
     "load", "LpfError", "Paths", "lpf_build_paths", "lpf_paths_info", "lpf_paths_export",
     "lpf_paths_stats", "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer",
-    "lpf_delta_swap", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror",
+    "lpf_delta_swap", "lpf_full_mc", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror",
     "SaParams", "SaStats", "Annealer", "lpf_sa_create", "lpf_sa_run", "lpf_sa_read", "lpf_sa_recompute_error",
     "lpf_sa_propose", "s2_fft", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
     "lpf_cnn_forward", "lpf_cnn_gradients", "lpf_cnn_train_step", "lpf_sa_set_proposer", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune", "lpf_batch_status",
@@ -82,6 +82,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_autotune_full": (ctypes.c_int, [p, i32, i32, p, p, p, P32, P32]),
         "lpf_set_launch_shape": (ctypes.c_int, [p, i32, i32, i32, i32]),
         "lpf_full_noalloc": (ctypes.c_int, [p, i32, i32, p, p, p]),
+        "lpf_full_mc": (ctypes.c_int, [p, i32, i32, p, p, p, p]),
         "s2_fft": (ctypes.c_int, [p, i32, i32, i32, p, p]),
         "lpf_cnn_create": (ctypes.c_int, [i32, i32, ctypes.c_uint64, ctypes.POINTER(p)]),
         "lpf_cnn_num_params": (ctypes.c_int64, [p]),
@@ -194,6 +195,17 @@ def lpf_full(img, paths: Paths, counts=None, stream=None):
         counts = torch.empty((2, paths.n_full), dtype=torch.int64, device=img.device)
     _check(load().lpf_full(_dev_ptr(img, "uint8", "img"), H, W, paths.handle,
                            _dev_ptr(counts, "int64", "counts"), _stream_ptr(stream)), "lpf_full")
+    return counts
+
+
+def lpf_full_mc(img, paths: Paths, sel, counts=None, stream=None):
+    """Counts over the selected translations only (sel: uint8 CUDA tensor H x W)."""
+    import torch
+    H, W = img.shape
+    if counts is None:
+        counts = torch.empty((2, paths.n_full), dtype=torch.int64, device=img.device)
+    _check(load().lpf_full_mc(_dev_ptr(img, "uint8", "img"), H, W, paths.handle, _dev_ptr(sel, "uint8", "sel"),
+                              _dev_ptr(counts, "int64", "counts"), _stream_ptr(stream)), "lpf_full_mc")
     return counts
 
 

@@ -130,7 +130,7 @@ static int bake_delta(lpf_paths* p, int W, DeltaTables& t) {
   for (int64_t c = 0; c < h.n_canon; ++c) { const double l = (double)(ptr[c + 1] - ptr[c]); total += l * l; }
   // many chunks: a single candidate spreads over many blocks (the annealer
   // evaluates batches of a few candidates when its acceptance rate is high)
-  const int want = (int)std::max<int64_t>(1, std::min<int64_t>(256, h.n_canon / 32));
+  const int want = (int)std::max<int64_t>(1, std::min<int64_t>(1024, h.n_canon / 8));
   std::vector<int32_t> chunk{0};
   double accw = 0;
   for (int64_t c = 0; c < h.n_canon; ++c) {

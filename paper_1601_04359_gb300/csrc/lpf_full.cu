@@ -92,6 +92,16 @@ __global__ void mirror_kernel(unsigned long long* __restrict__ counts, int64_t n
 }
 
 // AND of one funnel-shifted image word into both phase masks, for 4 pixels.
+// sel_bits[y][j]: bit b set when translation (32j + b, y) is selected.
+__global__ void pack_sel_kernel(const uint8_t* __restrict__ sel, int H, int W, int nw, uint32_t* __restrict__ bits) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < H * nw; i += gridDim.x * blockDim.x) {
+    const int y = i / nw, j = i - y * nw;
+    uint32_t v = 0;
+    for (int b = 0; b < 32 && 32 * j + b < W; ++b) v |= (uint32_t)(sel[(size_t)y * W + 32 * j + b] != 0) << b;
+    bits[i] = v;
+  }
+}
+
 template <int T>
 __device__ __forceinline__ void and4(const uint32_t* lane_base, uint4 P, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
   const uint32_t* sa = lane_base + (P.x >> 7);
@@ -136,7 +146,8 @@ __global__ void __launch_bounds__(512) walk_kernel(const uint32_t* __restrict__ 
                                                   int n_pieces, const uint32_t* __restrict__ prog,
                                                   const int64_t* __restrict__ piece,
                                                   unsigned long long* __restrict__ counts, int64_t n_full,
-                                                  int64_t base, int* __restrict__ ctl) {
+                                                  int64_t base, int* __restrict__ ctl,
+                                                  const uint32_t* __restrict__ sel) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_item, s_abort;
@@ -180,6 +191,7 @@ __global__ void __launch_bounds__(512) walk_kernel(const uint32_t* __restrict__ 
       if (y < H && j < nw) {
         const int rem = W - 32 * j;
         v = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+        if (sel) v &= sel[(size_t)y * nw + j];  // only the selected translations
       }
       valid[t] = v;
     }
@@ -366,12 +378,12 @@ static void launch_walk(const Geometry& g, const Baked& b, lpf_paths* p, unsigne
                         cudaStream_t s) {
   walk_kernel<T><<<blocks, 32 * g.G * g.BB, g.band_bytes, s>>>(
       p->d_packed, g.H, g.W, g.S, g.nw, g.G, g.BB, g.band_bytes, g.nbg, b.n_pieces, b.d_words, b.d_piece, c,
-      p->host.n_full, p->host.base, p->d_status);
+      p->host.n_full, p->host.base, p->d_status, p->d_sel_active);
 }
 
 // Enqueue one full evaluation with launch shape (T, BB) (<= 0: tuned or default).
 static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* counts, cudaStream_t s,
-                    bool standard, int T = 0, int BB = 0) {
+                    bool standard, int T = 0, int BB = 0, const uint8_t* sel = nullptr) {
   if (!p || !img || !counts) return LPF_EINVAL;
   if (H < 1 || W < 1 || H > 8192 || W > 8192) return LPF_EINVAL;
   if (p->host.rx >= W || p->host.ry >= H) return LPF_EINVAL;
@@ -417,6 +429,18 @@ static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* cou
     const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
     pack_rows_kernel<<<pblocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, p->d_packed);
   }
+  p->d_sel_active = nullptr;
+  if (sel) {
+    const size_t words = (size_t)H * g.nw;
+    if (words > p->sel_cap) {
+      if (p->d_sel) { cudaDeviceSynchronize(); cudaFree(p->d_sel); p->d_sel = nullptr; p->sel_cap = 0; }
+      e = cudaMalloc(&p->d_sel, words * 4);
+      if (e != cudaSuccess) return set_cuda_error(e);
+      p->sel_cap = words;
+    }
+    pack_sel_kernel<<<(int)std::min<size_t>((words + 255) / 256, 4096), 256, 0, s>>>(sel, H, W, g.nw, p->d_sel);
+    p->d_sel_active = p->d_sel;
+  }
   unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
   if (p->ev_start) cudaEventRecord(p->ev_start, s);
   switch (g.T) {
@@ -426,6 +450,7 @@ static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* cou
     default: launch_walk<8>(g, b, p, c, blocks, s); break;
   }
   if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
+  p->d_sel_active = nullptr;
   if (n_full > 1) {
     const int64_t n = 2 * (n_full - base - 1);
     const int mblocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
@@ -580,7 +605,7 @@ static int run_full_noalloc(const uint8_t* img, int H, int W, lpf_paths* p, int6
 #define LPF_NOALLOC_WALK(TT)                                                                                   \
   walk_kernel<TT><<<blocks, block, g.band_bytes, s>>>(slot.packed, g.H, g.W, g.S, g.nw, g.G, g.BB, g.band_bytes, \
                                                       g.nbg, b.n_pieces, b.d_words, b.d_piece, c, n_full, base,   \
-                                                      slot.ctl)
+                                                      slot.ctl, nullptr)
   switch (g.T) {
     case 1: LPF_NOALLOC_WALK(1); break;
     case 2: LPF_NOALLOC_WALK(2); break;
@@ -684,6 +709,7 @@ void lpf_paths_free(lpf_paths* p) {
     cudaFree(p->delta.d_chunk);
     cudaFree(p->d_partial);
     cudaFree(p->d_ext);
+    cudaFree(p->d_sel);
     if (cur >= 0) cudaSetDevice(cur);
   }
   delete p;
@@ -692,6 +718,12 @@ void lpf_paths_free(lpf_paths* p) {
 int lpf_full(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, int64_t* counts_dev,
              lpf_stream_t stream) {
   return lpf::run_full(img_dev, H, W, paths, counts_dev, (cudaStream_t)stream, false);
+}
+
+int lpf_full_mc(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, const uint8_t* sel_dev,
+                int64_t* counts_dev, lpf_stream_t stream) {
+  if (!sel_dev) return LPF_EINVAL;
+  return lpf::run_full(img_dev, H, W, paths, counts_dev, (cudaStream_t)stream, false, 0, 0, sel_dev);
 }
 
 int lpf_full_standard(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, int64_t* counts_dev,

@@ -276,12 +276,27 @@ __global__ void __launch_bounds__(kDeltaThreads) sa_batch_kernel(
   const double T0 = st->T, Tm = st->T_mult;
   const long long left = st->n_step - st->n_eval;
   const int Kv = (int)min((long long)Keff, max(0LL, left));
-  for (int k = threadIdx.x; k < Kv; k += blockDim.x) {
+  // error change of candidate k: its chunk partials summed by one warp in a
+  // fixed order (lane-strided partial sums, then a fixed shuffle tree)
+  __shared__ float s_de[32];
+  for (int k0 = 0; k0 < Kv; k0 += kDeltaWarps) {
+    const int k = k0 + warp;
     float de = 0.0f;
-    for (int c = 0; c < g.n_chunks; ++c) de += __ldcg(partial + (int64_t)k * g.n_chunks + c);
-    const double Tk = T0 * pow(Tm, (double)((c0 + k) / cmax));
-    const bool acc = de <= 0.0f || __ldcg(u + k) < expf(-de / (float)Tk);
-    if (acc) atomicMin(&s_kstar, k);
+    if (k < Kv) {
+      const float* pk = partial + (int64_t)k * g.n_chunks;
+      for (int c = lane; c < g.n_chunks; c += 32) de += __ldcg(pk + c);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) de += __shfl_xor_sync(0xffffffffu, de, o);
+      if (lane == 0) {
+        const double Tk = T0 * pow(Tm, (double)((c0 + k) / cmax));
+        const bool acc = de <= 0.0f || __ldcg(u + k) < expf(-de / (float)Tk);
+        if (acc) atomicMin(&s_kstar, k);
+        if (k - k0 < 32) s_de[k - k0] = de;
+      }
+    }
+    __syncthreads();
+    if (s_kstar != 0x7fffffff) break;  // the first accepted candidate is known
+    __syncthreads();
   }
   __syncthreads();
   const int kstar = s_kstar == 0x7fffffff ? -1 : s_kstar;
@@ -289,7 +304,9 @@ __global__ void __launch_bounds__(kDeltaThreads) sa_batch_kernel(
     const int a = __ldcg(pairs + 2 * kstar), b = __ldcg(pairs + 2 * kstar + 1);
     if (a != b) {
       const int32_t* dk = dcounts + (int64_t)kstar * 2 * g.n_canon;
-      for (int64_t i = threadIdx.x; i < 2 * g.n_canon; i += blockDim.x) {
+      const int64_t n2 = 2 * g.n_canon;
+#pragma unroll 4
+      for (int64_t i = threadIdx.x; i < n2; i += blockDim.x) {
         const long long d = __ldcg(dk + i);
         if (d == 0) continue;
         const int64_t p = i / g.n_canon, v = i - p * g.n_canon;
@@ -306,9 +323,7 @@ __global__ void __launch_bounds__(kDeltaThreads) sa_batch_kernel(
     }
   }
   if (threadIdx.x == 0) {
-    float de_star = 0.0f;
-    if (kstar >= 0)
-      for (int c = 0; c < g.n_chunks; ++c) de_star += __ldcg(partial + (int64_t)kstar * g.n_chunks + c);
+    const float de_star = kstar >= 0 ? s_de[kstar % kDeltaWarps] : 0.0f;
     const long long consumed = kstar >= 0 ? kstar + 1 : Kv;
     const long long rej = kstar >= 0 ? kstar : Kv;
     long long c = c0 + rej, s = st->s_stage;

@@ -71,6 +71,9 @@ struct lpf_paths {
   size_t partial_cap = 0;        // floats
   uint8_t* d_ext = nullptr;      // work area: periodically extended cell (bytes)
   size_t ext_cap = 0;
+  uint32_t* d_sel = nullptr;     // work area: packed translation selection (Monte-Carlo variant)
+  size_t sel_cap = 0;            // words
+  const uint32_t* d_sel_active = nullptr;  // selection of the walk being enqueued (or null)
 };
 
 namespace lpf {

@@ -9,9 +9,9 @@ draw are evaluated exactly (lpf_delta_swap); their error changes, standardised
 within the snapshot (y = -(de - mean) / std, clipped to [-3, 3]), are the
 targets of the additive pair score s1[a] + s0[b].
 
-Training runs in two rounds: first on candidates of uniform-proposal runs,
-then also on candidates drawn by runs that already use the network (seeds
-distinct from the evaluation seeds).
+Training data come from uniform-proposal runs with seeds distinct from the
+evaluation seeds (an optional second round adds candidates drawn by runs that
+already use the network; measured, it lowers the gain).
 
 Evaluation (swaps to target error): for each evaluation seed, a uniform run
 of N evaluations reaches error e_U; the model-proposal run (same initial cell,
@@ -53,10 +53,12 @@ def annealing_problem(r: int = 64, cell_size: int = 128, seed: int = 5):
 
 
 def collect(paths, target, cell0, n_step: int, seed: int, snapshots: int, n: int, t_max: float = 0.0,
-            net=None, eps: float = 0.1, tau: float = 1.0):
+            net=None, eps: float = 0.1, tau: float = 1.0, spacing: str = "evals"):
     """Run an annealer (uniform proposals, or the network's when `net` is
-    given) and log `snapshots` snapshots, evenly spaced in evaluations, of the
-    next `n` candidates it would draw, each evaluated exactly.
+    given) and log `snapshots` snapshots of the next `n` candidates it would
+    draw, each evaluated exactly.  spacing = "evals": snapshots evenly spaced
+    in evaluations; "early": spaced by n_step / (2 snapshots) batches, which
+    puts more of them where batches are short (early, high acceptance).
     Returns (cells, pairs, y, t_max)."""
     import torch
     d_cell = torch.from_numpy(cell0).cuda()
@@ -69,10 +71,14 @@ def collect(paths, target, cell0, n_step: int, seed: int, snapshots: int, n: int
     ys = torch.empty((snapshots, n), dtype=torch.float32, device="cuda")
     t_used = lpf.lpf_sa_read(ann)["t_max"]
     k = 0
+    gap = max(1, n_step // (2 * snapshots))
     for k in range(snapshots):
-        goal = (k * n_step) // snapshots
-        while lpf.lpf_sa_read(ann)["n_eval"] < goal:
-            lpf.lpf_sa_run(ann, 16)
+        if spacing == "early":
+            lpf.lpf_sa_run(ann, gap)
+        else:
+            goal = (k * n_step) // snapshots
+            while lpf.lpf_sa_read(ann)["n_eval"] < goal:
+                lpf.lpf_sa_run(ann, 16)
         cells[k].copy_(d_cell)
         p, _ = lpf.lpf_sa_propose(ann, n)
         _, de = lpf.lpf_delta_swap(d_cell, paths, p, target=target, counts=ann.counts, want_dcounts=False,
@@ -124,7 +130,8 @@ def run_until(paths, target, cell0, n_step: int, seed: int, t_max: float, net=No
 
 
 def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22, 23), snapshots: int = 256,
-             n: int = 64, epochs: int = 8, taus=(0.7,), epss=(0.1,), on_policy: bool = True):
+             n: int = 64, epochs: int = 8, taus=(0.5,), epss=(0.2,), on_policy: bool = False,
+             spacing: str = "early"):
     """Swaps-to-target gain of the learned proposer (median over eval seeds)."""
     import torch
 
@@ -142,7 +149,7 @@ def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22,
     net = lpf.lpf_cnn_create(128, 128, seed=3)
     t0 = time.perf_counter()
     data = [collect(paths, target, synth.exact_fraction_shuffle(128, 128, n1, seed=s), n_step, s, snapshots, n,
-                    t_max=t_max) for s in train_seeds]
+                    t_max=t_max, spacing=spacing) for s in train_seeds]
     cells = torch.cat([d[0] for d in data])
     pairs = torch.cat([d[1] for d in data])
     ys = torch.cat([d[2] for d in data])
@@ -151,7 +158,8 @@ def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22,
     if on_policy:
         # second round: candidates drawn by the annealer while it uses the network
         data2 = [collect(paths, target, synth.exact_fraction_shuffle(128, 128, n1, seed=s + 100), n_step, s + 100,
-                         snapshots, n, t_max=t_max, net=net, eps=epss[0], tau=taus[0]) for s in train_seeds]
+                         snapshots, n, t_max=t_max, net=net, eps=epss[0], tau=taus[0], spacing=spacing)
+                 for s in train_seeds]
         cells = torch.cat([cells] + [d[0] for d in data2])
         pairs = torch.cat([pairs] + [d[1] for d in data2])
         ys = torch.cat([ys] + [d[2] for d in data2])
@@ -176,7 +184,7 @@ def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22,
         "workload": "128x128 cell, |v|<=64, target from 512x512 clustered disks (f=0.3)",
         "n_step_uniform": n_step, "uniform": {str(s): {"error": v[0], "seconds": v[1], "evals_per_s": v[2]}
                                               for s, v in ref.items()},
-        "train_seeds": list(train_seeds), "eval_seeds": list(eval_seeds), "rounds": rounds,
+        "train_seeds": list(train_seeds), "eval_seeds": list(eval_seeds), "rounds": rounds, "spacing": spacing,
         "runs": runs, "best": {"tau": best["tau"], "epsilon": best["epsilon"], "median_ratio": best["median_ratio"]},
         "train_snapshots": int(cells.shape[0]), "train_candidates_per_snapshot": n, "epochs": epochs,
         "train_and_collect_seconds": t_train, "loss_first": losses[0] if losses else None,
@@ -192,15 +200,16 @@ def main():
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--train-seeds", type=int, nargs="+", default=[11, 12, 13])
     ap.add_argument("--eval-seeds", type=int, nargs="+", default=[21, 22, 23])
-    ap.add_argument("--tau", type=float, nargs="+", default=[0.7])
-    ap.add_argument("--eps", type=float, nargs="+", default=[0.1])
-    ap.add_argument("--no-on-policy", action="store_true")
+    ap.add_argument("--tau", type=float, nargs="+", default=[0.5])
+    ap.add_argument("--eps", type=float, nargs="+", default=[0.2])
+    ap.add_argument("--on-policy", action="store_true")
+    ap.add_argument("--spacing", choices=["evals", "early"], default="early")
     a = ap.parse_args()
     lpf.load()
     if a.evaluate:
         print(json.dumps(evaluate(n_step=a.n_step, train_seeds=tuple(a.train_seeds), eval_seeds=tuple(a.eval_seeds),
                                   snapshots=a.snapshots, epochs=a.epochs, taus=tuple(a.tau), epss=tuple(a.eps),
-                                  on_policy=not a.no_on_policy)), flush=True)
+                                  on_policy=a.on_policy, spacing=a.spacing)), flush=True)
 
 
 if __name__ == "__main__":

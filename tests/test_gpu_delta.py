@@ -30,7 +30,7 @@ def _target(rx, ry, seed):
     return (c / float(ref.size)).astype(np.float32)
 
 
-def _de_tolerance(target, counts, dcounts, rx, ry, H, W, n_chunks=32):
+def _de_tolerance(target, counts, dcounts, rx, ry, H, W, n_chunks=1024):
     """Bound of the float32 evaluation: every term x*(x - 2d) carries a few
     rounding errors, and the terms are summed sequentially in groups of at
     most n_canon*2/8 + 8 + n_chunks (per warp, across warps, across chunks)."""

@@ -94,3 +94,32 @@ def test_counts_bounded_and_vanish():
     img = synth.config1_image()
     c = oracle.count_list(img, [(32, 0), (0, 32), (32, 32), (-32, 17)])
     assert (c[:, 1] < 0.05 * img.sum()).all()
+
+
+def test_selected_translations_variant():
+    # Monte-Carlo variant (Sec. 3): all translations selected gives the exact
+    # counts; a single selected translation gives 0/1 per vector, checked by
+    # the independent product formula at that translation; counts are
+    # additive over disjoint selections.
+    img = synth.random_binary(11, 9, 0.55, 8)
+    rx, ry = 5, 4
+    full = oracle.lpf_full(img, rx, ry)
+    np.testing.assert_array_equal(oracle.lpf_full_selected(img, rx, ry, np.ones_like(img)), full)
+    rng = np.random.default_rng(3)
+    sel = (rng.random(img.shape) < 0.3).astype(np.uint8)
+    a = oracle.lpf_full_selected(img, rx, ry, sel)
+    b = oracle.lpf_full_selected(img, rx, ry, 1 - sel)
+    np.testing.assert_array_equal(a + b, full)
+    one = np.zeros_like(img)
+    one[4, 7] = 1
+    c = oracle.lpf_full_selected(img, rx, ry, one)
+    assert set(np.unique(c)) <= {0, 1}
+    from tests.independent import segment_geometric
+    k = 0
+    for dy in range(-ry, ry + 1):
+        for dx in range(-rx, rx + 1):
+            pts = segment_geometric(dx, dy)
+            for p in (0, 1):
+                inside = all(img[(4 + sy) % 11, (7 + sx) % 9] == p for sx, sy in pts)
+                assert c[p, k] == int(inside)
+            k += 1
