@@ -18,6 +18,7 @@ Functions and the passages they follow:
   delta_objective(...)             Eq. (LSE) after minus before, double precision
   s2_direct(img, phase)            Eq. (S2dis), direct double sum
   lpf_full_selected(img, rx, ry, sel)   Sec. 3 Monte-Carlo variant (selected translations)
+  s2_counts(img), s2_delta_objective(img, target, pairs)   Eq. (S2dis) counts; Eq. (LSE) on S2, by recount
 Parity status: every function above is pinned by ``tests/test_oracle_*.py``.
 """
 from __future__ import annotations
@@ -45,11 +46,13 @@ def _load():
         lib.lpfo_lpf_full.argtypes = [p, i32, i32, i32, i32, p]
         lib.lpfo_count_list.argtypes = [p, i32, i32, p, p, i32, p]
         lib.lpfo_delta_swap.argtypes = [p, i32, i32, i32, i32, p, i32, p]
-        lib.lpfo_objective.argtypes = [p, p, i32, i32, i32, i32]
+        lib.lpfo_objective.argtypes = [p, p, i32, i32, i32, i32, i32]
         lib.lpfo_objective.restype = ctypes.c_double
-        lib.lpfo_delta_objective.argtypes = [p, p, p, i32, i32, i32, i32, i32, p]
+        lib.lpfo_delta_objective.argtypes = [p, p, p, i32, i32, i32, i32, i32, i32, p]
         lib.lpfo_s2_direct.argtypes = [p, i32, i32, i32, p]
         lib.lpfo_lpf_full_sel.argtypes = [p, i32, i32, i32, i32, p, p]
+        lib.lpfo_s2_counts.argtypes = [p, i32, i32, p]
+        lib.lpfo_s2_delta_objective.argtypes = [p, i32, i32, p, p, i32, p]
         _lib = lib
     return _lib
 
@@ -144,19 +147,40 @@ def delta_swap(img, rx: int, ry: int, pairs) -> np.ndarray:
     return out
 
 
-def objective(target, counts, rx: int, ry: int, H: int, W: int) -> float:
+def objective(target, counts, rx: int, ry: int, H: int, W: int, phases: int = 3) -> float:
+    """Eq. (LSE) over the phases in the bit mask `phases` (bit p: phase p)."""
     t = np.ascontiguousarray(target, dtype=np.float32)
     c = np.ascontiguousarray(counts, dtype=np.int64)
-    return float(_load().lpfo_objective(_ptr(t), _ptr(c), rx, ry, H, W))
+    return float(_load().lpfo_objective(_ptr(t), _ptr(c), rx, ry, H, W, int(phases)))
 
 
-def delta_objective(target, counts, dcounts, rx: int, ry: int, H: int, W: int) -> np.ndarray:
+def delta_objective(target, counts, dcounts, rx: int, ry: int, H: int, W: int, phases: int = 3) -> np.ndarray:
     t = np.ascontiguousarray(target, dtype=np.float32)
     c = np.ascontiguousarray(counts, dtype=np.int64)
     d = np.ascontiguousarray(dcounts, dtype=np.int64)
     K = d.shape[0]
     out = np.zeros(K, np.float64)
-    _load().lpfo_delta_objective(_ptr(t), _ptr(c), _ptr(d), K, rx, ry, H, W, _ptr(out))
+    _load().lpfo_delta_objective(_ptr(t), _ptr(c), _ptr(d), K, rx, ry, H, W, int(phases), _ptr(out))
+    return out
+
+
+def s2_counts(img) -> np.ndarray:
+    """int64 [H][W] phase-1 autocorrelation counts (W*H * S2, exact)."""
+    a = _img(img)
+    H, W = a.shape
+    out = np.zeros((H, W), np.int64)
+    _load().lpfo_s2_counts(_ptr(a), H, W, _ptr(out))
+    return out
+
+
+def s2_delta_objective(img, target, pairs) -> np.ndarray:
+    """float64 [K]: change of sum_d (t[d] - C[d]/(W H))^2 for each exchange, by recount."""
+    a = _img(img)
+    H, W = a.shape
+    t = np.ascontiguousarray(target, dtype=np.float32)
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    out = np.zeros(len(pr), np.float64)
+    _load().lpfo_s2_delta_objective(_ptr(a), H, W, _ptr(t), _ptr(pr), len(pr), _ptr(out))
     return out
 
 

@@ -226,17 +226,20 @@ void lpfo_delta_swap(const uint8_t *img, int H, int W, int rx, int ry,
 
 /*
  * Least-square error of Eq. (LSE) (Sec. 4) between a target descriptor and
- * the descriptor of the current image, over both phases and over the
+ * the descriptor of the current image, over the phases set in `phases`
+ * (bit 0: phase 0, bit 1: phase 1; 3 = both, the L2 of Sec. 6's Tab. mutual,
+ * 1 or 2 = the single-phase L2^b or L2^w compressions) and over the
  * canonical half D of the window, in double precision.
  * target: float32 [2][n_full] (already normalised, e.g. counts / (W0*H0) of
  * the original); counts: int64 [2][n_full]; the image descriptor is
  * counts / (W*H) of the current cell.
  */
-double lpfo_objective(const float *target, const int64_t *counts, int rx, int ry, int H, int W) {
+double lpfo_objective(const float *target, const int64_t *counts, int rx, int ry, int H, int W, int phases) {
     int64_t nfull = (int64_t)(2 * rx + 1) * (2 * ry + 1);
     int64_t base = (nfull - 1) / 2;
     double n = (double)H * (double)W, e = 0.0;
     for (int p = 0; p < 2; ++p)
+        if (phases & (1 << p))
         for (int64_t k = base; k < nfull; ++k) {
             double d = (double)target[p * nfull + k] - (double)counts[p * nfull + k] / n;
             e += d * d;
@@ -246,10 +249,11 @@ double lpfo_objective(const float *target, const int64_t *counts, int rx, int ry
 
 /*
  * Change of Eq. (LSE) for every candidate: e(counts + dcounts[k]) - e(counts),
- * in double precision, each term written out as the definition.
+ * over the phases set in `phases` as above, in double precision, each term
+ * written out as the definition.
  */
 void lpfo_delta_objective(const float *target, const int64_t *counts, const int64_t *dcounts,
-                          int K, int rx, int ry, int H, int W, double *de) {
+                          int K, int rx, int ry, int H, int W, int phases, double *de) {
     int64_t nfull = (int64_t)(2 * rx + 1) * (2 * ry + 1);
     int64_t base = (nfull - 1) / 2;
     int64_t ncanon = nfull - base;
@@ -257,7 +261,8 @@ void lpfo_delta_objective(const float *target, const int64_t *counts, const int6
     for (int q = 0; q < K; ++q) {
         const int64_t *dq = dcounts + (int64_t)q * 2 * ncanon;
         double after = 0.0, before = 0.0;
-        for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < 2; ++p) {
+            if (!(phases & (1 << p))) continue;
             for (int64_t c = 0; c < ncanon; ++c) {
                 double t = (double)target[p * nfull + base + c];
                 double c0 = (double)counts[p * nfull + base + c];
@@ -266,8 +271,58 @@ void lpfo_delta_objective(const float *target, const int64_t *counts, const int6
                 before += d0 * d0;
                 after += d1 * d1;
             }
+        }
         de[q] = after - before;
     }
+}
+
+/*
+ * Autocorrelation counts of phase 1, C[y][x] = sum over (x1, y1) of
+ * chi(x1,y1) * chi((x1+x)%W, (y1+y)%H): W*H times S2 of Eq. (S2dis), as
+ * exact integers (direct double sum).
+ */
+void lpfo_s2_counts(const uint8_t *img, int H, int W, int64_t *C) {
+    #pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t acc = 0;
+            for (int y1 = 0; y1 < H; ++y1)
+                for (int x1 = 0; x1 < W; ++x1)
+                    acc += (img[(int64_t)y1 * W + x1] == 1) &&
+                           (img[(int64_t)((y1 + y) % H) * W + (x1 + x) % W] == 1);
+            C[(int64_t)y * W + x] = acc;
+        }
+}
+
+/*
+ * Change of the least-square S2 error e = sum over all offsets d of
+ * (t[d] - C[d]/(W*H))^2 (Eq. (LSE) with the phase-1 two-point probability)
+ * for exchanging the values of pixels a and b, by definition: recompute the
+ * counts on the exchanged image.  Double precision.
+ */
+void lpfo_s2_delta_objective(const uint8_t *img, int H, int W, const float *t, const int32_t *pairs, int K,
+                             double *de) {
+    int64_t npix = (int64_t)H * W;
+    int64_t *C0 = (int64_t *)malloc(sizeof(int64_t) * npix);
+    int64_t *C1 = (int64_t *)malloc(sizeof(int64_t) * npix);
+    uint8_t *work = (uint8_t *)malloc((size_t)npix);
+    lpfo_s2_counts(img, H, W, C0);
+    double inv = 1.0 / (double)npix;
+    for (int q = 0; q < K; ++q) {
+        memcpy(work, img, (size_t)npix);
+        uint8_t v = work[pairs[2 * q]];
+        work[pairs[2 * q]] = work[pairs[2 * q + 1]];
+        work[pairs[2 * q + 1]] = v;
+        lpfo_s2_counts(work, H, W, C1);
+        double before = 0.0, after = 0.0;
+        for (int64_t d = 0; d < npix; ++d) {
+            double e0 = (double)t[d] - (double)C0[d] * inv, e1 = (double)t[d] - (double)C1[d] * inv;
+            before += e0 * e0;
+            after += e1 * e1;
+        }
+        de[q] = after - before;
+    }
+    free(C0); free(C1); free(work);
 }
 
 /*

@@ -96,11 +96,16 @@ def propose(cell: np.ndarray, n_eval: int, k: int, seed: int):
 
 
 def anneal(cell: np.ndarray, target: np.ndarray, counts: np.ndarray, rx: int, ry: int, n_step: int,
-           c_max: int, s_max: int, t_max: float, t_min_ratio: float, seed: int):
+           c_max: int, s_max: int, t_max: float, t_min_ratio: float, seed: int, phases: int = 3,
+           objective: str = "l2"):
     """Sequential Alg. 3 with the readings above; Delta e from the oracle's
     recount (double precision, rounded to float32 as the error change of a
-    candidate).  Returns (final cell, n_accept, final T)."""
-    from . import delta_objective
+    candidate).  objective "l2": Eq. (LSE) on the lineal path counts of the
+    phases in the bit mask `phases` (counts int64 [2][n_full], target
+    [2][n_full]); "s2": Eq. (LSE) on the phase-1 two-point probability over
+    all W*H offsets of the cell (target [H*W]; counts and rx, ry unused).
+    Returns (final cell, n_accept, final T)."""
+    from . import delta_objective, s2_delta_objective
     cell = np.array(cell, np.uint8)
     counts = np.array(counts, np.int64)
     H, W = cell.shape
@@ -112,8 +117,11 @@ def anneal(cell: np.ndarray, target: np.ndarray, counts: np.ndarray, rx: int, ry
     n_accept = 0
     for n in range(n_step):
         pairs, u = propose(cell, n, 1, seed)
-        d = delta_swap(cell, rx, ry, pairs)
-        de = np.float32(delta_objective(target, counts, d, rx, ry, H, W)[0])
+        if objective == "s2":
+            de = np.float32(s2_delta_objective(cell, target, pairs)[0])
+        else:
+            d = delta_swap(cell, rx, ry, pairs)
+            de = np.float32(delta_objective(target, counts, d, rx, ry, H, W, phases)[0])
         c += 1
         accept = de <= 0 or u[0] < np.float32(math.exp(-float(de) / T))
         if accept:
@@ -122,8 +130,9 @@ def anneal(cell: np.ndarray, target: np.ndarray, counts: np.ndarray, rx: int, ry
             a, b = pairs[0]
             flat = cell.reshape(-1)
             flat[a], flat[b] = flat[b], flat[a]
-            counts[:, base:] += d[0]
-            counts[:, :base] = counts[:, base + 1:][:, ::-1]
+            if objective != "s2":
+                counts[:, base:] += d[0]
+                counts[:, :base] = counts[:, base + 1:][:, ::-1]
         if c >= c_max or s >= s_max:
             T *= t_mult
             c = s = 0

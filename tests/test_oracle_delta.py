@@ -90,3 +90,10 @@ def test_objective_definition_on_hand_example():
     d[0, 1, 1] = -2
     de = oracle.delta_objective(target, counts, d, rx, ry, H, W)
     assert de[0] == pytest.approx(-(0.5 ** 2), rel=1e-15)
+    # single-phase errors (the L2^b / L2^w compressions of Sec. 6, Tab. mutual):
+    # phase 0 contributes nothing here, phase 1 everything; the change of -2
+    # sits in phase 1
+    assert oracle.objective(target, counts, rx, ry, H, W, phases=1) == 0.0
+    assert oracle.objective(target, counts, rx, ry, H, W, phases=2) == pytest.approx(e, rel=1e-15)
+    assert oracle.delta_objective(target, counts, d, rx, ry, H, W, phases=1)[0] == 0.0
+    assert oracle.delta_objective(target, counts, d, rx, ry, H, W, phases=2)[0] == pytest.approx(-(0.5 ** 2), rel=1e-15)
