@@ -313,6 +313,10 @@ typedef struct {
   int32_t k_max;       /* candidates per batch, upper bound (e.g. 4096) */
   int32_t k_min;       /* candidates per batch, lower bound (e.g. 1) */
   uint64_t seed;       /* Philox-4x32-10 key of the run */
+  int32_t phases;      /* lineal-path runs: phases in the error, bit p = phase p
+                          (0 or 3: both, the L2 compression of Sec. 6; 2: phase 1
+                          only, L2^w of Tab. mutual with phase 1 the particles;
+                          1: phase 0 only, L2^b).  Ignored by s2_sa_create. */
 } lpf_sa_params;
 
 typedef struct {
@@ -383,6 +387,62 @@ int lpf_sa_propose(lpf_sa *sa, int32_t k, int32_t *pairs_dev, float *u_dev, lpf_
 
 /* Release a run (NULL is ignored); synchronises the device. */
 void lpf_sa_free(lpf_sa *sa);
+
+/* ---- Two-point probability as the annealing objective (Sec. 2.1, Sec. 6) ---- */
+
+/*
+ * Exact autocorrelation counts of phase 1 (Eq. (S2dis) times W*H):
+ * counts_dev[y][x] = sum over (x1, y1) of chi(x1, y1) * chi((x1+x)%W, (y1+y)%H),
+ * chi the phase-1 indicator of img_dev (H*W uint8, 0/1).  counts_dev: int64
+ * [H][W], device memory owned by the caller.  Direct double sum on bit-packed
+ * rows (H*W*H*ceil(W/32) word operations), meant for annealing cells; the
+ * float descriptor of a large original comes from s2_fft.  Allocates a work
+ * area on `stream` (stream-ordered).  H*W <= 2^20, else LPF_EUNSUPPORTED.
+ * Errors: LPF_EINVAL, LPF_EUNSUPPORTED, LPF_ECUDA.
+ */
+int s2_counts(const uint8_t *img_dev, int32_t H, int32_t W, int64_t *counts_dev, lpf_stream_t stream);
+
+/*
+ * Changes of the S2 counts and of the S2 error for K candidate exchanges of
+ * the image img_dev (not modified), the S2 analogue of lpf_delta_swap.
+ *   pairs_dev    int32 [K][2] pixel indices y*W + x; a pair of equal phases
+ *                (or a == b) is the identity (all changes 0).
+ *   dcounts_dev  int32 [K][H][W] or NULL: counts after minus before for
+ *                every offset, exact; not written for a pair with an index
+ *                out of range.
+ *   target_dev   float [H][W]: the target S2 of phase 1 at each offset of the
+ *                cell (needed with de_dev); counts_dev int64 [H][W]: the
+ *                image's current counts (from s2_counts).
+ *   de_dev       float [K] or NULL: e(after) - e(before) with e = sum over all
+ *                H*W offsets of (target - counts/(H*W))^2 (Eq. (LSE) on S2),
+ *                float32, summed in a fixed order (bitwise reproducible);
+ *                NaN for a pair with an index out of range or when a bounded
+ *                wait for the staging copy gave up.
+ * The periodically extended cell (W + 2 ceil(W/2)) x (H + 2 ceil(H/2)) bytes
+ * must fit in shared memory (about 227 KB), else LPF_EUNSUPPORTED.  Work
+ * areas are allocated on `stream` (stream-ordered).
+ * Errors: LPF_EINVAL, LPF_EUNSUPPORTED, LPF_ECUDA.
+ */
+int s2_delta_swap(const uint8_t *img_dev, int32_t H, int32_t W, const int32_t *pairs_dev, int32_t K,
+                  int32_t *dcounts_dev, const float *target_dev, const int64_t *counts_dev, float *de_dev,
+                  lpf_stream_t stream);
+
+/*
+ * Start an annealing run (Alg. 3) whose objective is the S2 error above
+ * instead of the lineal path error: the S2-based compression of Sec. 6
+ * (Tab. mutual).  target_dev float [H][W]: the target S2 of phase 1 per
+ * offset of the cell (e.g. an original's S2 cut to the cell's centred offset
+ * window); counts_dev int64 [H][W]: filled with the cell's counts
+ * (s2_counts) and kept current.  Everything else -- proposals, Metropolis
+ * test, schedule, batches, graphs -- is that of lpf_sa_create, and the
+ * handle is driven and released by lpf_sa_run / lpf_sa_read /
+ * lpf_sa_recompute_error / lpf_sa_propose / lpf_sa_set_proposer /
+ * lpf_sa_free.  Cell limits: H, W >= 2, H*W <= 2^20 and the extended cell of
+ * s2_delta_swap in shared memory.
+ * Errors: LPF_EINVAL, LPF_EUNSUPPORTED, LPF_ENOMEM, LPF_ECUDA.
+ */
+int s2_sa_create(uint8_t *cell_dev, int32_t H, int32_t W, const float *target_dev, int64_t *counts_dev,
+                 const lpf_sa_params *params, lpf_stream_t stream, lpf_sa **out);
 
 /* ---- Learned swap proposer (no counterpart in the paper) ---- */
 

@@ -20,7 +20,7 @@ __all__ = [
     "lpf_paths_stats", "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer",
     "lpf_delta_swap", "lpf_full_mc", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror",
     "SaParams", "SaStats", "Annealer", "lpf_sa_create", "lpf_sa_run", "lpf_sa_read", "lpf_sa_recompute_error",
-    "lpf_sa_propose", "s2_fft", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
+    "lpf_sa_propose", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
     "lpf_cnn_forward", "lpf_cnn_gradients", "lpf_cnn_train_step", "lpf_sa_set_proposer", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune", "lpf_batch_status",
 ]
 
@@ -32,7 +32,7 @@ class SaParams(ctypes.Structure):
     """lpf_sa_params of include/lpf.h."""
     _fields_ = [("n_step", ctypes.c_int64), ("c_max", ctypes.c_int64), ("s_max", ctypes.c_int64),
                 ("t_max", ctypes.c_double), ("t_min_ratio", ctypes.c_double), ("k_max", ctypes.c_int32),
-                ("k_min", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("k_min", ctypes.c_int32), ("seed", ctypes.c_uint64), ("phases", ctypes.c_int32)]
 
 
 class SaStats(ctypes.Structure):
@@ -84,6 +84,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_full_noalloc": (ctypes.c_int, [p, i32, i32, p, p, p]),
         "lpf_full_mc": (ctypes.c_int, [p, i32, i32, p, p, p, p]),
         "s2_fft": (ctypes.c_int, [p, i32, i32, i32, p, p]),
+        "s2_counts": (ctypes.c_int, [p, i32, i32, p, p]),
+        "s2_delta_swap": (ctypes.c_int, [p, i32, i32, p, i32, p, p, p, p, p]),
+        "s2_sa_create": (ctypes.c_int, [p, i32, i32, p, p, ctypes.POINTER(SaParams), p, ctypes.POINTER(p)]),
         "lpf_cnn_create": (ctypes.c_int, [i32, i32, ctypes.c_uint64, ctypes.POINTER(p)]),
         "lpf_cnn_num_params": (ctypes.c_int64, [p]),
         "lpf_cnn_set_params": (ctypes.c_int, [p, p, i64]),
@@ -336,16 +339,21 @@ class Annealer:
             self.handle = None
 
 
+def _sa_params(n_step, c_max, s_max, t_max, t_min_ratio, k_max, k_min, seed, phases) -> SaParams:
+    return SaParams(int(n_step), int(c_max if c_max is not None else max(1, n_step // 10)),
+                    int(s_max if s_max is not None else max(1, n_step // 100)), float(t_max), float(t_min_ratio),
+                    int(k_max), int(k_min), int(seed), int(phases))
+
+
 def lpf_sa_create(cell, paths: Paths, target, counts=None, n_step=1_000_000, c_max=None, s_max=None,
-                  t_max=0.0, t_min_ratio=0.01, k_max=4096, k_min=1, seed=1, stream=None) -> Annealer:
-    """Start an annealing run on the CUDA uint8 cell (modified in place)."""
+                  t_max=0.0, t_min_ratio=0.01, k_max=4096, k_min=1, seed=1, phases=3, stream=None) -> Annealer:
+    """Start an annealing run on the CUDA uint8 cell (modified in place).
+    phases: bit mask of the phases in the lineal-path error (3 both, 2 phase 1, 1 phase 0)."""
     import torch
     H, W = cell.shape
     if counts is None:
         counts = torch.empty((2, paths.n_full), dtype=torch.int64, device=cell.device)
-    prm = SaParams(int(n_step), int(c_max if c_max is not None else max(1, n_step // 10)),
-                   int(s_max if s_max is not None else max(1, n_step // 100)), float(t_max), float(t_min_ratio),
-                   int(k_max), int(k_min), int(seed))
+    prm = _sa_params(n_step, c_max, s_max, t_max, t_min_ratio, k_max, k_min, seed, phases)
     h = ctypes.c_void_p()
     _check(load().lpf_sa_create(_dev_ptr(cell, "uint8", "cell"), H, W, paths.handle,
                                 _dev_ptr(target, "float32", "target"), _dev_ptr(counts, "int64", "counts"),
@@ -387,6 +395,53 @@ def s2_fft(img, phase: int, out=None, stream=None):
     _check(load().s2_fft(_dev_ptr(img, "uint8", "img"), H, W, int(phase), _dev_ptr(out, "float32", "s2"),
                          _stream_ptr(stream)), "s2_fft")
     return out
+
+
+def s2_counts(img, out=None, stream=None):
+    """Exact phase-1 autocorrelation counts (W*H * S2): int64 CUDA tensor [H][W]."""
+    import torch
+    H, W = img.shape
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.int64, device=img.device)
+    _check(load().s2_counts(_dev_ptr(img, "uint8", "img"), H, W, _dev_ptr(out, "int64", "counts"),
+                            _stream_ptr(stream)), "s2_counts")
+    return out
+
+
+def s2_delta_swap(img, pairs, target=None, counts=None, want_dcounts: bool = True, want_de: bool = False,
+                  dcounts=None, de=None, stream=None):
+    """S2 count changes (int32 [K][H][W]) and/or S2 error changes (float32 [K])
+    for candidate exchanges pairs (int32 CUDA tensor [K][2])."""
+    import torch
+    H, W = img.shape
+    K = int(pairs.shape[0])
+    if want_dcounts and dcounts is None:
+        dcounts = torch.empty((K, H, W), dtype=torch.int32, device=img.device)
+    if want_de and de is None:
+        de = torch.empty(K, dtype=torch.float32, device=img.device)
+    _check(load().s2_delta_swap(
+        _dev_ptr(img, "uint8", "img"), H, W, _dev_ptr(pairs, "int32", "pairs"), K,
+        _dev_ptr(dcounts, "int32", "dcounts") if dcounts is not None else None,
+        _dev_ptr(target, "float32", "target") if target is not None else None,
+        _dev_ptr(counts, "int64", "counts") if counts is not None else None,
+        _dev_ptr(de, "float32", "de") if de is not None else None,
+        _stream_ptr(stream)), "s2_delta_swap")
+    return dcounts, de
+
+
+def s2_sa_create(cell, target, counts=None, n_step=1_000_000, c_max=None, s_max=None, t_max=0.0, t_min_ratio=0.01,
+                 k_max=4096, k_min=1, seed=1, stream=None) -> Annealer:
+    """Start an annealing run on the S2 error (target float32 [H][W] per cell offset)."""
+    import torch
+    H, W = cell.shape
+    if counts is None:
+        counts = torch.empty((H, W), dtype=torch.int64, device=cell.device)
+    prm = _sa_params(n_step, c_max, s_max, t_max, t_min_ratio, k_max, k_min, seed, 0)
+    h = ctypes.c_void_p()
+    _check(load().s2_sa_create(_dev_ptr(cell, "uint8", "cell"), H, W, _dev_ptr(target, "float32", "target"),
+                               _dev_ptr(counts, "int64", "counts"), ctypes.byref(prm), _stream_ptr(stream),
+                               ctypes.byref(h)), "s2_sa_create")
+    return Annealer(h.value, cell, None, target, counts)
 
 
 class Cnn:

@@ -130,7 +130,7 @@ static int bake_delta(lpf_paths* p, int W, DeltaTables& t) {
   for (int64_t c = 0; c < h.n_canon; ++c) { const double l = (double)(ptr[c + 1] - ptr[c]); total += l * l; }
   // many chunks: a single candidate spreads over many blocks (the annealer
   // evaluates batches of a few candidates when its acceptance rate is high)
-  const int want = (int)std::max<int64_t>(1, std::min<int64_t>(1024, h.n_canon / 8));
+  const int want = (int)std::max<int64_t>(1, std::min<int64_t>(512, h.n_canon / 16));
   std::vector<int32_t> chunk{0};
   double accw = 0;
   for (int64_t c = 0; c < h.n_canon; ++c) {
@@ -171,6 +171,7 @@ int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g) {
   g.base = p->host.base;
   g.target = nullptr;
   g.counts = nullptr;
+  g.phase_mask = 3;
   return LPF_OK;
 }
 
@@ -214,14 +215,12 @@ int delta_prepare(lpf_paths* p, int H, int W, int K) {
 // Blocks per vector chunk: enough candidate strides to fill every SM a few times.
 int delta_stride(int n_chunks, int K) {
   const int sms = g_sms > 0 ? g_sms : 152;
-  return std::max(1, std::min(K, (sms * 8 + n_chunks - 1) / n_chunks));
+  return std::max(1, std::min(K, (sms * 4 + n_chunks - 1) / n_chunks));
 }
 
-}  // namespace lpf
-
-extern "C" int lpf_delta_swap(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths,
-                              const int32_t* pairs_dev, int32_t K, int32_t* dcounts_dev, const float* target_dev,
-                              const int64_t* counts_dev, float* de_dev, lpf_stream_t stream) {
+int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, const int32_t* pairs_dev,
+                   int32_t K, int32_t* dcounts_dev, const float* target_dev, const int64_t* counts_dev, float* de_dev,
+                   int phase_mask, cudaStream_t s) {
   if (!paths || !img_dev || K < 0) return LPF_EINVAL;
   if (K == 0) return LPF_OK;
   if (!pairs_dev) return LPF_EINVAL;
@@ -229,26 +228,35 @@ extern "C" int lpf_delta_swap(const uint8_t* img_dev, int32_t H, int32_t W, lpf_
   if (paths->host.rx >= W || paths->host.ry >= H) return LPF_EINVAL;
   if (de_dev && (!target_dev || !counts_dev)) return LPF_EINVAL;
   if (!de_dev && !dcounts_dev) return LPF_EINVAL;  // nothing to compute
-  int rc = lpf::delta_prepare(paths, H, W, K);
+  int rc = delta_prepare(paths, H, W, K);
   if (rc) return rc;
   (void)cudaGetLastError();
-  cudaStream_t s = (cudaStream_t)stream;
-  lpf::DeltaArgs g;
-  lpf::delta_geometry(paths, H, W, g);
+  DeltaArgs g;
+  delta_geometry(paths, H, W, g);
   g.target = de_dev ? target_dev : nullptr;
   g.counts = de_dev ? counts_dev : nullptr;
+  g.phase_mask = phase_mask;
   {
     const int blocks = (int)std::min<int64_t>((g.ext_bytes + 255) / 256, 4096);
-    lpf::build_ext_kernel<<<blocks, 256, 0, s>>>(img_dev, H, W, g.rx, g.ry, g.We, g.He, g.ext_bytes, paths->d_ext);
+    build_ext_kernel<<<blocks, 256, 0, s>>>(img_dev, H, W, g.rx, g.ry, g.We, g.He, g.ext_bytes, paths->d_ext);
   }
-  const dim3 grid(g.n_chunks, lpf::delta_stride(g.n_chunks, K));
+  const dim3 grid(g.n_chunks, delta_stride(g.n_chunks, K));
   if (paths->ev_start) cudaEventRecord(paths->ev_start, s);
-  lpf::delta_kernel<<<grid, lpf::kDeltaThreads, g.ext_bytes, s>>>(img_dev, paths->d_ext, g, pairs_dev, K, dcounts_dev,
+  delta_kernel<<<grid, kDeltaThreads, g.ext_bytes, s>>>(img_dev, paths->d_ext, g, pairs_dev, K, dcounts_dev,
                                                                   de_dev ? paths->d_partial : nullptr, paths->d_status);
   if (paths->ev_stop) cudaEventRecord(paths->ev_stop, s);
   if (de_dev) {
     const int blocks = std::min((K + 255) / 256, 1024);
-    lpf::delta_reduce_kernel<<<blocks, 256, 0, s>>>(paths->d_partial, g.n_chunks, K, de_dev);
+    delta_reduce_kernel<<<blocks, 256, 0, s>>>(paths->d_partial, g.n_chunks, K, de_dev);
   }
-  return lpf::set_cuda_error(cudaGetLastError());
+  return set_cuda_error(cudaGetLastError());
+}
+
+}  // namespace lpf
+
+extern "C" int lpf_delta_swap(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths,
+                              const int32_t* pairs_dev, int32_t K, int32_t* dcounts_dev, const float* target_dev,
+                              const int64_t* counts_dev, float* de_dev, lpf_stream_t stream) {
+  return lpf::delta_swap_run(img_dev, H, W, paths, pairs_dev, K, dcounts_dev, target_dev, counts_dev, de_dev, 3,
+                             (cudaStream_t)stream);
 }

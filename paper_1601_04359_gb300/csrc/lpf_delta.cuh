@@ -13,7 +13,7 @@ namespace lpf {
 
 constexpr uint8_t kMarkA = 4;  // phase 1 before the exchange, 0 after
 constexpr uint8_t kMarkB = 3;  // phase 0 before the exchange, 1 after
-constexpr int kDeltaThreads = 256;
+constexpr int kDeltaThreads = 512;  // 16 warps: 3 blocks of 64 KB fill 48 of 64 warp slots
 constexpr int kDeltaWarps = kDeltaThreads / 32;
 
 struct DeltaArgs {
@@ -26,6 +26,7 @@ struct DeltaArgs {
   int64_t n_canon, n_full, base;
   const float* target;          // [2][n_full] or null
   const int64_t* counts;        // [2][n_full] or null
+  int phase_mask;               // phases in the error: bit p = phase p (3 = both)
 };
 
 __device__ __forceinline__ int delta_ext_pos(int c, int W, int We, int rx, int ry) {
@@ -55,7 +56,8 @@ __device__ __forceinline__ bool delta_stage(uint8_t* sm, const uint8_t* ext, uin
 // (phase 1) and b (phase 0), both already marked in `sm`; the calling warp
 // handles v = v0 + warp, v0 + warp + kDeltaWarps, ...  Lane 0 writes the
 // changes (if dcounts) and returns the float32 error change of its vectors
-// (if the target is given), accumulated in vector order.
+// over the phases in g.phase_mask (if the target is given), accumulated in
+// vector order.
 __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const DeltaArgs& g, int a, int b, int v0,
                                                     int v1, int warp, int lane, int32_t* dcounts_k) {
   float acc = 0.0f;
@@ -105,12 +107,12 @@ __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const Del
       }
       if (g.target && (d0 | d1)) {
         // (d - D/N)^2 - d^2 = (D/N) * (D/N - 2 d), with d = target - count/N
-        if (d0) {
+        if (d0 && (g.phase_mask & 1)) {
           const float dd = g.target[g.base + v] - (float)g.counts[g.base + v] * invN;
           const float x = (float)d0 * invN;
           acc += x * (x - 2.0f * dd);
         }
-        if (d1) {
+        if (d1 && (g.phase_mask & 2)) {
           const float dd = g.target[g.n_full + g.base + v] - (float)g.counts[g.n_full + g.base + v] * invN;
           const float x = (float)d1 * invN;
           acc += x * (x - 2.0f * dd);

@@ -36,101 +36,10 @@
 #include <vector>
 
 #include "../../include/lpf.h"
-#include "lpf_delta.cuh"
+#include "lpf_sa.cuh"
 #include "lpf_state.hpp"
 
 namespace lpf {
-
-// ---- Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -------------------
-struct U4 { uint32_t x, y, z, w; };
-
-__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
-  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
-    const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
-    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
-    k0 += W0;
-    k1 += W1;
-  }
-  return c;
-}
-
-constexpr int kMaxTries = 1 << 16;  // rejection-sampling attempts before giving up (identity)
-
-struct SaDev {
-  double T, T_mult, e;
-  long long n_eval, n_accept, n_batches, n_cand, c_stage, s_stage;
-  long long n_step, c_max, s_max;
-  double p_est;
-  int k_eff, k_min, k_max, done;
-  int acc_pair[2];
-  float acc_de;
-  unsigned int key0, key1;
-  unsigned int ticket;   // blocks of the current batch that finished
-  // learned proposer (see lpf_sa_set_proposer)
-  int use_model;
-  float eps;
-  const float* cdf1;     // inclusive prefix sums of the phase-1 sampling weights [H*W]
-  const float* cdf0;
-  float tot1, tot0;
-};
-
-// Pixel value (0/1) of cell index c from an extended cell.
-__device__ __forceinline__ int ext_pixel(const uint8_t* e, int c, const DeltaArgs& g) {
-  return e[delta_ext_pos(c, g.W, g.We, g.rx, g.ry)];
-}
-
-__device__ __forceinline__ bool interfacial(const uint8_t* e, int c, const DeltaArgs& g) {
-  const int y = c / g.W, x = c - y * g.W;
-  const int v = e[(y + g.ry) * g.We + x + g.rx];
-  const int l = e[(y + g.ry) * g.We + (x == 0 ? g.W - 1 : x - 1) + g.rx];
-  const int r = e[(y + g.ry) * g.We + (x == g.W - 1 ? 0 : x + 1) + g.rx];
-  const int t = e[((y == 0 ? g.H - 1 : y - 1) + g.ry) * g.We + x + g.rx];
-  const int b = e[((y == g.H - 1 ? 0 : y + 1) + g.ry) * g.We + x + g.rx];
-  return (l != v) | (r != v) | (t != v) | (b != v);
-}
-
-// Smallest pixel index p with cdf[p] > t (t < cdf[npix-1]).
-__device__ __forceinline__ int cdf_search(const float* __restrict__ cdf, int npix, float t) {
-  int lo = 0, hi = npix - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(cdf + mid) > t) hi = mid; else lo = mid + 1;
-  }
-  return lo;
-}
-
-// Candidate n of the run: (a, b, U); a == b == 0 when no pair was found.
-// With a model (use_model and the draw's word 3 >= epsilon), each pixel is
-// drawn from the model's sampling weights instead of uniformly.
-__device__ void draw_candidate(const uint8_t* e, const DeltaArgs& g, unsigned long long n, uint32_t k0, uint32_t k1,
-                               int& a, int& b, float& u, const SaDev* st = nullptr) {
-  const unsigned npix = (unsigned)(g.H * g.W);
-  a = -1;
-  b = -1;
-  bool model = false;
-  for (uint32_t j = 0; j < (uint32_t)kMaxTries && (a < 0 || b < 0); ++j) {
-    const U4 r = philox4x32_10(U4{(uint32_t)n, (uint32_t)(n >> 32), j, 0u}, k0, k1);
-    if (j == 0) {
-      u = ((float)(r.z >> 8) + 0.5f) * (1.0f / 16777216.0f);
-      model = st && st->use_model && st->tot1 > 0.0f && st->tot0 > 0.0f &&
-              ((float)(r.w >> 8) + 0.5f) * (1.0f / 16777216.0f) >= st->eps;
-    }
-    if (a < 0) {
-      const int c = model ? cdf_search(st->cdf1, (int)npix, ((float)(r.x >> 8) + 0.5f) * (1.0f / 16777216.0f) * st->tot1)
-                          : (int)(((unsigned long long)r.x * npix) >> 32);
-      if (ext_pixel(e, c, g) == 1 && interfacial(e, c, g)) a = c;
-    }
-    if (b < 0) {
-      const int c = model ? cdf_search(st->cdf0, (int)npix, ((float)(r.y >> 8) + 0.5f) * (1.0f / 16777216.0f) * st->tot0)
-                          : (int)(((unsigned long long)r.y * npix) >> 32);
-      if (ext_pixel(e, c, g) == 0 && interfacial(e, c, g)) b = c;
-    }
-  }
-  if (a < 0 || b < 0) { a = 0; b = 0; }
-}
 
 // Sampling tables of the model: w_p = exp((s_p - max s) / tau) over the
 // interfacial pixels of each phase (0 elsewhere), inclusive prefix sums in
@@ -219,7 +128,7 @@ __global__ void __launch_bounds__(kDeltaThreads) sa_batch_kernel(
   extern __shared__ __align__(16) uint8_t sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ float warp_acc[kDeltaWarps];
-  __shared__ int s_a, s_b, s_last, s_kstar;
+  __shared__ int s_a, s_b;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ch = blockIdx.x;
   const int Keff = st->done ? 0 : st->k_eff;
@@ -261,45 +170,11 @@ __global__ void __launch_bounds__(kDeltaThreads) sa_batch_kernel(
   }
 
   // ---- last block: accept the first passing candidate and apply it ----
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned total = gridDim.x * gridDim.y;
-    s_last = (atomicAdd(&st->ticket, 1u) == total - 1) ? 1 : 0;
-    s_kstar = 0x7fffffff;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-
-  const long long c0 = st->c_stage, cmax = st->c_max;
-  const double T0 = st->T, Tm = st->T_mult;
+  if (!sa_last_block(st)) return;
   const long long left = st->n_step - st->n_eval;
   const int Kv = (int)min((long long)Keff, max(0LL, left));
-  // error change of candidate k: its chunk partials summed by one warp in a
-  // fixed order (lane-strided partial sums, then a fixed shuffle tree)
-  __shared__ float s_de[32];
-  for (int k0 = 0; k0 < Kv; k0 += kDeltaWarps) {
-    const int k = k0 + warp;
-    float de = 0.0f;
-    if (k < Kv) {
-      const float* pk = partial + (int64_t)k * g.n_chunks;
-      for (int c = lane; c < g.n_chunks; c += 32) de += __ldcg(pk + c);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) de += __shfl_xor_sync(0xffffffffu, de, o);
-      if (lane == 0) {
-        const double Tk = T0 * pow(Tm, (double)((c0 + k) / cmax));
-        const bool acc = de <= 0.0f || __ldcg(u + k) < expf(-de / (float)Tk);
-        if (acc) atomicMin(&s_kstar, k);
-        if (k - k0 < 32) s_de[k - k0] = de;
-      }
-    }
-    __syncthreads();
-    if (s_kstar != 0x7fffffff) break;  // the first accepted candidate is known
-    __syncthreads();
-  }
-  __syncthreads();
-  const int kstar = s_kstar == 0x7fffffff ? -1 : s_kstar;
+  float de_star;
+  const int kstar = sa_first_accept(st, Kv, partial, g.n_chunks, u, &de_star);
   if (kstar >= 0) {
     const int a = __ldcg(pairs + 2 * kstar), b = __ldcg(pairs + 2 * kstar + 1);
     if (a != b) {
@@ -322,58 +197,19 @@ __global__ void __launch_bounds__(kDeltaThreads) sa_batch_kernel(
       }
     }
   }
-  if (threadIdx.x == 0) {
-    const float de_star = kstar >= 0 ? s_de[kstar % kDeltaWarps] : 0.0f;
-    const long long consumed = kstar >= 0 ? kstar + 1 : Kv;
-    const long long rej = kstar >= 0 ? kstar : Kv;
-    long long c = c0 + rej, s = st->s_stage;
-    double T = T0;
-    const long long wraps = c / cmax;
-    if (wraps > 0) s = 0;
-    c -= wraps * cmax;
-    T *= pow(Tm, (double)wraps);
-    if (kstar >= 0) {
-      c += 1;
-      s += 1;
-      if (c >= cmax || s >= st->s_max) { c = 0; s = 0; T *= Tm; }
-      st->acc_pair[0] = __ldcg(pairs + 2 * kstar);
-      st->acc_pair[1] = __ldcg(pairs + 2 * kstar + 1);
-      st->acc_de = de_star;
-      st->e += (double)de_star;
-      st->n_accept += 1;
-    } else {
-      st->acc_pair[0] = 0;
-      st->acc_pair[1] = 0;
-      st->acc_de = 0.0f;
-    }
-    st->c_stage = c;
-    st->s_stage = s;
-    st->T = T;
-    st->n_eval += consumed;
-    st->n_cand += Keff;
-    if (Keff > 0) st->n_batches += 1;
-    if (consumed > 0) {
-      const double obs = (kstar >= 0 ? 1.0 : 0.0) / (double)consumed;
-      st->p_est = 0.8 * st->p_est + 0.2 * obs;
-    }
-    // next batch size: a batch costs a fixed latency plus a share per
-    // candidate and yields (1 - (1-p)^K) / p evaluations; with the measured
-    // costs that ratio is best near K = 1/(2p)
-    const double want = ceil(0.5 / fmax(st->p_est, 1e-9));
-    st->k_eff = (int)fmin((double)st->k_max, fmax((double)st->k_min, want));
-    if (st->n_eval >= st->n_step) st->done = 1;
-    st->ticket = 0u;
-  }
+  if (threadIdx.x == 0) sa_advance(st, Keff, Kv, kstar, de_star, pairs);
 }
 
-// e = sum over both phases and the canonical half of (target - counts/N)^2, in double.
+// e = sum over the phases p in phase_mask and base <= k < n_full of
+// (target[p][k] - counts[p][k] / N)^2, in double (one block of 256 threads).
 __global__ void sa_error_kernel(const float* __restrict__ target, const int64_t* __restrict__ counts, int64_t n_full,
-                                int64_t base, double invN, double* __restrict__ out) {
+                                int64_t base, int phase_mask, double invN, double* __restrict__ out) {
   __shared__ double sh[256];
   double acc = 0.0;
   const int64_t n = n_full - base;
   for (int64_t i = threadIdx.x; i < 2 * n; i += blockDim.x) {
     const int64_t p = i / n, k = base + i - p * n;
+    if (!(phase_mask & (1 << p))) continue;
     const double d = (double)target[p * n_full + k] - (double)counts[p * n_full + k] * invN;
     acc += d * d;
   }
@@ -404,33 +240,6 @@ __global__ void build_ext_sa_kernel(const uint8_t* __restrict__ img, DeltaArgs g
 
 }  // namespace lpf
 
-struct lpf_sa {
-  lpf_paths* paths = nullptr;
-  uint8_t* cell = nullptr;
-  int H = 0, W = 0;
-  const float* target = nullptr;
-  int64_t* counts = nullptr;
-  lpf_sa_params prm{};
-  lpf::DeltaArgs g{};
-  dim3 grid;
-  lpf::SaDev* d_st = nullptr;
-  uint8_t* d_ext = nullptr;
-  int32_t* d_pairs = nullptr;   // [k_max][2]
-  float* d_u = nullptr;         // [k_max]
-  float* d_de = nullptr;        // [k_max]
-  float* d_partial = nullptr;   // [k_max][n_chunks]
-  int32_t* d_dc = nullptr;      // [k_max][2][n_canon]
-  double* d_e = nullptr;
-  int* d_status = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  int graph_batches = 0;
-  lpf_cnn* cnn = nullptr;       // learned proposer (optional)
-  float tau = 1.0f;
-  int refresh = 16;
-  float* d_cdf = nullptr;       // [2][H*W] sampling tables
-};
-
 namespace lpf {
 
 static int g_sa_attr = 0;
@@ -445,13 +254,108 @@ static void enqueue_refresh(lpf_sa* sa, cudaStream_t s) {
 }
 
 static void enqueue_batch(lpf_sa* sa, cudaStream_t s) {
+  if (sa->objective == kSaObjectiveS2) {
+    s2_enqueue_batch(sa, s);
+    return;
+  }
   sa_batch_kernel<<<sa->grid, kDeltaThreads, sa->g.ext_bytes, s>>>(
       sa->d_st, sa->cell, sa->d_ext, sa->g, sa->d_pairs, sa->d_u, sa->d_dc, sa->d_partial,
       reinterpret_cast<unsigned long long*>(sa->counts), sa->d_status);
 }
 
+void sa_enqueue_error(lpf_sa* sa, cudaStream_t s) {
+  sa_error_kernel<<<1, 256, 0, s>>>(sa->target, sa->counts, sa->err_n_full, sa->err_base, sa->phase_mask,
+                                    1.0 / ((double)sa->H * (double)sa->W), sa->d_e);
+}
+
 static int sa_device_state(lpf_sa* sa, SaDev& st, cudaStream_t s) {
   cudaError_t e = cudaMemcpyAsync(&st, sa->d_st, sizeof(st), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return set_cuda_error(e);
+}
+
+int sa_check_params(const lpf_sa_params* prm) {
+  if (prm->k_max < 1 || prm->k_max > (1 << 16) || prm->k_min < 1 || prm->k_min > prm->k_max) return LPF_EINVAL;
+  if (prm->n_step < 1 || prm->c_max < 1 || prm->s_max < 1 || !(prm->t_min_ratio > 0.0)) return LPF_EINVAL;
+  if (prm->phases < 0 || prm->phases > 3) return LPF_EINVAL;
+  return LPF_OK;
+}
+
+// Second half of both create calls, once sa's geometry (g, grid, objective,
+// error layout) is set: work buffers, the extended cell, the initial error,
+// the initial temperature and the device state.
+int sa_start(lpf_sa* sa, cudaStream_t s) {
+  const lpf_sa_params* prm = &sa->prm;
+  const int nch = sa->g.n_chunks;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_st, sizeof(SaDev));
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_ext, sa->g.ext_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_pairs, 2 * (size_t)prm->k_max * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_u, (size_t)prm->k_max * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_de, (size_t)prm->k_max * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_partial, (size_t)prm->k_max * nch * sizeof(float));
+  if (e == cudaSuccess && sa->objective == kSaObjectiveLineal)
+    e = cudaMalloc(&sa->d_dc, (size_t)prm->k_max * 2 * (size_t)sa->paths->host.n_canon * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_e, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(sa->d_status, 0, sizeof(int), s);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  {
+    const int blocks = (int)std::min<int64_t>((sa->g.ext_bytes + 255) / 256, 4096);
+    build_ext_sa_kernel<<<blocks, 256, 0, s>>>(sa->cell, sa->g, sa->d_ext);
+  }
+  sa_enqueue_error(sa, s);  // initial error from the exact counts
+  double e0 = 0.0;
+  e = cudaMemcpyAsync(&e0, sa->d_e, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_cuda_error(e);
+
+  SaDev st{};
+  st.T = prm->t_max;
+  st.T_mult = std::pow(prm->t_min_ratio, (double)prm->s_max / (double)prm->n_step);
+  st.e = e0;
+  st.n_step = prm->n_step;
+  st.c_max = prm->c_max;
+  st.s_max = prm->s_max;
+  st.p_est = 0.5;
+  st.k_min = prm->k_min;
+  st.k_max = prm->k_max;
+  st.k_eff = prm->k_min;
+  st.key0 = (unsigned)(prm->seed & 0xffffffffu);
+  st.key1 = (unsigned)(prm->seed >> 32);
+
+  if (!(prm->t_max > 0.0)) {
+    // T_max so that an uphill move of average size is accepted with
+    // probability 1/2 at the start: k_max candidates of the initial state,
+    // T_max = -mean(positive Delta e) / ln(0.5).
+    const int K = prm->k_max;
+    sa_draw_kernel<<<(K + 127) / 128, 128, 0, s>>>(sa->d_ext, sa->g, 0ull, K, st.key0, st.key1, sa->d_pairs,
+                                                   sa->d_u, nullptr);
+    int rc;
+    if (sa->objective == kSaObjectiveS2) {
+      rc = s2_delta_run(sa->cell, sa->H, sa->W, sa->d_ext, sa->d_pairs, K, nullptr, sa->target, sa->counts, sa->d_de,
+                        sa->d_partial, s);
+    } else {
+      rc = delta_prepare(sa->paths, sa->H, sa->W, K);
+      if (!rc)
+        rc = delta_swap_run(sa->cell, sa->H, sa->W, sa->paths, sa->d_pairs, K, nullptr, sa->target, sa->counts,
+                            sa->d_de, sa->phase_mask, s);
+    }
+    std::vector<float> de(K);
+    if (!rc) {
+      e = cudaMemcpyAsync(de.data(), sa->d_de, de.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) rc = set_cuda_error(e);
+    }
+    if (rc) return rc;
+    double sum = 0.0;
+    int npos = 0;
+    for (float d : de)
+      if (d > 0.0f) { sum += d; ++npos; }
+    st.T = npos ? -(sum / npos) / std::log(0.5) : 1e-12;
+    sa->prm.t_max = st.T;
+  }
+  e = cudaMemcpyAsync(sa->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return set_cuda_error(e);
 }
@@ -465,8 +369,7 @@ int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, con
   if (!out) return LPF_EINVAL;
   *out = nullptr;
   if (!cell_dev || !paths || !target_dev || !counts_dev || !prm) return LPF_EINVAL;
-  if (prm->k_max < 1 || prm->k_max > (1 << 16) || prm->k_min < 1 || prm->k_min > prm->k_max) return LPF_EINVAL;
-  if (prm->n_step < 1 || prm->c_max < 1 || prm->s_max < 1 || !(prm->t_min_ratio > 0.0)) return LPF_EINVAL;
+  if (int rc = lpf::sa_check_params(prm)) return rc;
   if ((int64_t)H * W > (1 << 24)) return LPF_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   int rc = lpf_full(cell_dev, H, W, paths, counts_dev, stream);
@@ -494,76 +397,18 @@ int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, con
   sa->target = target_dev;
   sa->counts = counts_dev;
   sa->prm = *prm;
+  sa->objective = kSaObjectiveLineal;
+  sa->phase_mask = prm->phases ? prm->phases : 3;
+  sa->err_n_full = paths->host.n_full;
+  sa->err_base = paths->host.base;
+  sa->threads = lpf::kDeltaThreads;
   lpf::delta_geometry(paths, H, W, sa->g);
   sa->g.target = target_dev;
   sa->g.counts = counts_dev;
-  const int nch = sa->g.n_chunks;
-  sa->grid = dim3(nch, lpf::delta_stride(nch, prm->k_max));
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_st, sizeof(lpf::SaDev));
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_ext, sa->g.ext_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_pairs, 2 * (size_t)prm->k_max * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_u, (size_t)prm->k_max * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_de, (size_t)prm->k_max * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_partial, (size_t)prm->k_max * nch * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_dc, (size_t)prm->k_max * 2 * (size_t)paths->host.n_canon * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_e, sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemsetAsync(sa->d_status, 0, sizeof(int), s);
-  if (e != cudaSuccess) { lpf_sa_free(sa); return lpf::set_cuda_error(e); }
-  {
-    const int blocks = (int)std::min<int64_t>((sa->g.ext_bytes + 255) / 256, 4096);
-    lpf::build_ext_sa_kernel<<<blocks, 256, 0, s>>>(cell_dev, sa->g, sa->d_ext);
-  }
-  // initial error from the exact counts
-  lpf::sa_error_kernel<<<1, 256, 0, s>>>(target_dev, counts_dev, paths->host.n_full, paths->host.base,
-                                         1.0 / ((double)H * (double)W), sa->d_e);
-  double e0 = 0.0;
-  e = cudaMemcpyAsync(&e0, sa->d_e, sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) { lpf_sa_free(sa); return lpf::set_cuda_error(e); }
-
-  lpf::SaDev st{};
-  st.T = prm->t_max;
-  st.T_mult = std::pow(prm->t_min_ratio, (double)prm->s_max / (double)prm->n_step);
-  st.e = e0;
-  st.n_step = prm->n_step;
-  st.c_max = prm->c_max;
-  st.s_max = prm->s_max;
-  st.p_est = 0.5;
-  st.k_min = prm->k_min;
-  st.k_max = prm->k_max;
-  st.k_eff = prm->k_min;
-  st.key0 = (unsigned)(prm->seed & 0xffffffffu);
-  st.key1 = (unsigned)(prm->seed >> 32);
-
-  if (!(prm->t_max > 0.0)) {
-    // T_max so that an uphill move of average size is accepted with
-    // probability 1/2 at the start: k_max candidates of the initial state,
-    // T_max = -mean(positive Delta e) / ln(0.5).
-    const int K = prm->k_max;
-    lpf::sa_draw_kernel<<<(K + 127) / 128, 128, 0, s>>>(sa->d_ext, sa->g, 0ull, K, st.key0, st.key1, sa->d_pairs,
-                                                        sa->d_u, nullptr);
-    rc = lpf::delta_prepare(paths, H, W, K);
-    if (!rc) rc = lpf_delta_swap(cell_dev, H, W, paths, sa->d_pairs, K, nullptr, target_dev, counts_dev, sa->d_de,
-                                 stream);
-    std::vector<float> de(K);
-    if (!rc) {
-      e = cudaMemcpyAsync(de.data(), sa->d_de, de.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) rc = lpf::set_cuda_error(e);
-    }
-    if (rc) { lpf_sa_free(sa); return rc; }
-    double sum = 0.0;
-    int npos = 0;
-    for (float d : de)
-      if (d > 0.0f) { sum += d; ++npos; }
-    st.T = npos ? -(sum / npos) / std::log(0.5) : 1e-12;
-    sa->prm.t_max = st.T;
-  }
-  e = cudaMemcpyAsync(sa->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) { lpf_sa_free(sa); return lpf::set_cuda_error(e); }
+  sa->g.phase_mask = sa->phase_mask;
+  sa->grid = dim3(sa->g.n_chunks, lpf::delta_stride(sa->g.n_chunks, prm->k_max));
+  rc = lpf::sa_start(sa, s);
+  if (rc) { lpf_sa_free(sa); return rc; }
   *out = sa;
   return LPF_OK;
 }
@@ -657,8 +502,7 @@ int lpf_sa_read(lpf_sa* sa, lpf_sa_stats* out, lpf_stream_t stream) {
 int lpf_sa_recompute_error(lpf_sa* sa, double* e_out, lpf_stream_t stream) {
   if (!sa) return LPF_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  lpf::sa_error_kernel<<<1, 256, 0, s>>>(sa->target, sa->counts, sa->paths->host.n_full, sa->paths->host.base,
-                                         1.0 / ((double)sa->H * (double)sa->W), sa->d_e);
+  lpf::sa_enqueue_error(sa, s);
   lpf::sa_set_error_kernel<<<1, 1, 0, s>>>(sa->d_st, sa->d_e);
   double e = 0.0;
   cudaError_t err = cudaMemcpyAsync(&e, sa->d_e, sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -1,0 +1,262 @@
+// Annealer state and device pieces shared by its objectives (lineal path
+// counts in lpf_sa.cu, the two-point probability in lpf_s2sa.cu).
+#pragma once
+#include <climits>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lpf.h"
+#include "lpf_delta.cuh"
+
+namespace lpf {
+
+// ---- Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+    const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    k0 += W0;
+    k1 += W1;
+  }
+  return c;
+}
+
+constexpr int kMaxTries = 1 << 16;  // rejection-sampling attempts before giving up (identity)
+
+struct SaDev {
+  double T, T_mult, e;
+  long long n_eval, n_accept, n_batches, n_cand, c_stage, s_stage;
+  long long n_step, c_max, s_max;
+  double p_est;
+  int k_eff, k_min, k_max, done;
+  int acc_pair[2];
+  float acc_de;
+  unsigned int key0, key1;
+  unsigned int ticket;   // blocks of the current batch that finished
+  // learned proposer (see lpf_sa_set_proposer)
+  int use_model;
+  float eps;
+  const float* cdf1;     // inclusive prefix sums of the phase-1 sampling weights [H*W]
+  const float* cdf0;
+  float tot1, tot0;
+};
+
+// Pixel value (0/1) of cell index c from an extended cell.
+__device__ __forceinline__ int ext_pixel(const uint8_t* e, int c, const DeltaArgs& g) {
+  return e[delta_ext_pos(c, g.W, g.We, g.rx, g.ry)];
+}
+
+__device__ __forceinline__ bool interfacial(const uint8_t* e, int c, const DeltaArgs& g) {
+  const int y = c / g.W, x = c - y * g.W;
+  const int v = e[(y + g.ry) * g.We + x + g.rx];
+  const int l = e[(y + g.ry) * g.We + (x == 0 ? g.W - 1 : x - 1) + g.rx];
+  const int r = e[(y + g.ry) * g.We + (x == g.W - 1 ? 0 : x + 1) + g.rx];
+  const int t = e[((y == 0 ? g.H - 1 : y - 1) + g.ry) * g.We + x + g.rx];
+  const int b = e[((y == g.H - 1 ? 0 : y + 1) + g.ry) * g.We + x + g.rx];
+  return (l != v) | (r != v) | (t != v) | (b != v);
+}
+
+// Smallest pixel index p with cdf[p] > t (t < cdf[npix-1]).
+__device__ __forceinline__ int cdf_search(const float* __restrict__ cdf, int npix, float t) {
+  int lo = 0, hi = npix - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(cdf + mid) > t) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Candidate n of the run: (a, b, U); a == b == 0 when no pair was found.
+// With a model (use_model and the draw's word 3 >= epsilon), each pixel is
+// drawn from the model's sampling weights instead of uniformly.
+static __device__ void draw_candidate(const uint8_t* e, const DeltaArgs& g, unsigned long long n, uint32_t k0, uint32_t k1,
+                               int& a, int& b, float& u, const SaDev* st = nullptr) {
+  const unsigned npix = (unsigned)(g.H * g.W);
+  a = -1;
+  b = -1;
+  bool model = false;
+  for (uint32_t j = 0; j < (uint32_t)kMaxTries && (a < 0 || b < 0); ++j) {
+    const U4 r = philox4x32_10(U4{(uint32_t)n, (uint32_t)(n >> 32), j, 0u}, k0, k1);
+    if (j == 0) {
+      u = ((float)(r.z >> 8) + 0.5f) * (1.0f / 16777216.0f);
+      model = st && st->use_model && st->tot1 > 0.0f && st->tot0 > 0.0f &&
+              ((float)(r.w >> 8) + 0.5f) * (1.0f / 16777216.0f) >= st->eps;
+    }
+    if (a < 0) {
+      const int c = model ? cdf_search(st->cdf1, (int)npix, ((float)(r.x >> 8) + 0.5f) * (1.0f / 16777216.0f) * st->tot1)
+                          : (int)(((unsigned long long)r.x * npix) >> 32);
+      if (ext_pixel(e, c, g) == 1 && interfacial(e, c, g)) a = c;
+    }
+    if (b < 0) {
+      const int c = model ? cdf_search(st->cdf0, (int)npix, ((float)(r.y >> 8) + 0.5f) * (1.0f / 16777216.0f) * st->tot0)
+                          : (int)(((unsigned long long)r.y * npix) >> 32);
+      if (ext_pixel(e, c, g) == 0 && interfacial(e, c, g)) b = c;
+    }
+  }
+  if (a < 0 || b < 0) { a = 0; b = 0; }
+}
+
+// ---- end of a batch (last block) -----------------------------------------
+
+// The first candidate k < Kv that passes the Metropolis test (Delta e <= 0 or
+// U < exp(-Delta e / T_k), T_k the temperature candidate k would see after k
+// rejections), -1 if none; *de_star gets its error change.  A candidate's
+// change is the sum of its n_chunks partials, added by one warp in a fixed
+// order (lane-strided sums, then a fixed shuffle tree).  Every thread of the
+// block calls this.
+__device__ __forceinline__ int sa_first_accept(const SaDev* st, int Kv, const float* partial, int n_chunks,
+                                               const float* u, float* de_star) {
+  __shared__ float s_de[32];
+  __shared__ int s_kstar;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_kstar = INT_MAX;
+  __syncthreads();
+  const long long c0 = st->c_stage, cmax = st->c_max;
+  const double T0 = st->T, Tm = st->T_mult;
+  int k0 = 0;
+  for (; k0 < Kv; k0 += nw) {
+    const int k = k0 + warp;
+    if (k < Kv) {
+      float de = 0.0f;
+      const float* pk = partial + (int64_t)k * n_chunks;
+      for (int c = lane; c < n_chunks; c += 32) de += __ldcg(pk + c);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) de += __shfl_xor_sync(0xffffffffu, de, o);
+      if (lane == 0) {
+        const double Tk = T0 * pow(Tm, (double)((c0 + k) / cmax));
+        const bool acc = de <= 0.0f || __ldcg(u + k) < expf(-de / (float)Tk);
+        if (acc) atomicMin(&s_kstar, k);
+        s_de[warp] = de;
+      }
+    }
+    __syncthreads();
+    if (s_kstar != INT_MAX) break;  // the first accepted candidate is known
+    __syncthreads();
+  }
+  __syncthreads();
+  const int kstar = s_kstar == INT_MAX ? -1 : s_kstar;
+  *de_star = kstar >= 0 ? s_de[kstar - k0] : 0.0f;
+  return kstar;
+}
+
+// Advance the run past a batch of Keff candidates of which Kv count (the
+// rest lie beyond n_step) and kstar (or -1) was accepted: stage counters,
+// temperature, error, statistics and the next batch size.  Thread 0 only.
+__device__ __forceinline__ void sa_advance(SaDev* st, int Keff, int Kv, int kstar, float de_star,
+                                           const int32_t* pairs) {
+  const long long c0 = st->c_stage, cmax = st->c_max;
+  const double Tm = st->T_mult;
+  const long long consumed = kstar >= 0 ? kstar + 1 : Kv;
+  const long long rej = kstar >= 0 ? kstar : Kv;
+  long long c = c0 + rej, s = st->s_stage;
+  double T = st->T;
+  const long long wraps = c / cmax;
+  if (wraps > 0) s = 0;
+  c -= wraps * cmax;
+  T *= pow(Tm, (double)wraps);
+  if (kstar >= 0) {
+    c += 1;
+    s += 1;
+    if (c >= cmax || s >= st->s_max) { c = 0; s = 0; T *= Tm; }
+    st->acc_pair[0] = __ldcg(pairs + 2 * kstar);
+    st->acc_pair[1] = __ldcg(pairs + 2 * kstar + 1);
+    st->acc_de = de_star;
+    st->e += (double)de_star;
+    st->n_accept += 1;
+  } else {
+    st->acc_pair[0] = 0;
+    st->acc_pair[1] = 0;
+    st->acc_de = 0.0f;
+  }
+  st->c_stage = c;
+  st->s_stage = s;
+  st->T = T;
+  st->n_eval += consumed;
+  st->n_cand += Keff;
+  if (Keff > 0) st->n_batches += 1;
+  if (consumed > 0) {
+    const double obs = (kstar >= 0 ? 1.0 : 0.0) / (double)consumed;
+    st->p_est = 0.8 * st->p_est + 0.2 * obs;
+  }
+  // next batch size: a batch costs a fixed latency plus a share per
+  // candidate and yields (1 - (1-p)^K) / p evaluations; with the measured
+  // costs that ratio is best near K = 1/(2p)
+  const double want = ceil(0.5 / fmax(st->p_est, 1e-9));
+  st->k_eff = (int)fmin((double)st->k_max, fmax((double)st->k_min, want));
+  if (st->n_eval >= st->n_step) st->done = 1;
+  st->ticket = 0u;
+}
+
+// Atomic ticket: true in the last block of the grid to get here (after a
+// fence, so that it sees every other block's writes).  Every thread calls it.
+__device__ __forceinline__ bool sa_last_block(SaDev* st) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned total = gridDim.x * gridDim.y;
+    s_last = (atomicAdd(&st->ticket, 1u) == total - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+}  // namespace lpf
+
+enum { kSaObjectiveLineal = 0, kSaObjectiveS2 = 1 };
+
+struct lpf_sa {
+  lpf_paths* paths = nullptr;
+  uint8_t* cell = nullptr;
+  int H = 0, W = 0;
+  const float* target = nullptr;
+  int64_t* counts = nullptr;
+  lpf_sa_params prm{};
+  lpf::DeltaArgs g{};
+  dim3 grid;
+  lpf::SaDev* d_st = nullptr;
+  uint8_t* d_ext = nullptr;
+  int32_t* d_pairs = nullptr;   // [k_max][2]
+  float* d_u = nullptr;         // [k_max]
+  float* d_de = nullptr;        // [k_max]
+  float* d_partial = nullptr;   // [k_max][n_chunks]
+  int32_t* d_dc = nullptr;      // [k_max][2][n_canon]
+  double* d_e = nullptr;
+  int* d_status = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_batches = 0;
+  lpf_cnn* cnn = nullptr;       // learned proposer (optional)
+  float tau = 1.0f;
+  int refresh = 16;
+  float* d_cdf = nullptr;       // [2][H*W] sampling tables
+  int objective = kSaObjectiveLineal;
+  int phase_mask = 3;           // phases in the lineal-path error
+  int64_t err_n_full = 0, err_base = 0;  // error layout: [phase][err_n_full], summed from err_base
+  int threads = 0;              // batch kernel block size
+};
+
+namespace lpf {
+// Enqueue one batch of the two-point-probability objective (lpf_s2sa.cu).
+void s2_enqueue_batch(lpf_sa* sa, cudaStream_t s);
+// Enqueue the recomputation of the run's error from its exact counts into
+// sa->d_e, in double (lpf_sa.cu).
+void sa_enqueue_error(lpf_sa* sa, cudaStream_t s);
+// LPF_OK if the run parameters are valid (lpf_sa.cu).
+int sa_check_params(const lpf_sa_params* prm);
+// Second half of both create calls once sa's geometry, objective and error
+// layout are set: work buffers, extended cell, initial error and temperature,
+// device state (lpf_sa.cu).
+int sa_start(lpf_sa* sa, cudaStream_t s);
+// S2 error changes (and count changes [K][H*W] if dcounts) of K candidate
+// exchanges; ext/partial may be null (then allocated on the stream) (lpf_s2sa.cu).
+int s2_delta_run(const uint8_t* img, int H, int W, const uint8_t* ext, const int32_t* pairs, int K, int32_t* dcounts,
+                 const float* target, const int64_t* counts, float* de, float* partial, cudaStream_t s);
+}  // namespace lpf
+

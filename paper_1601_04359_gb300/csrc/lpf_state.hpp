@@ -92,6 +92,10 @@ int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g);
 // Candidate strides per vector chunk for K candidates.
 int delta_stride(int n_chunks, int K);
 int delta_max_smem();
+// lpf_delta_swap with the error restricted to the phases in phase_mask.
+int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, const int32_t* pairs_dev,
+                   int32_t K, int32_t* dcounts_dev, const float* target_dev, const int64_t* counts_dev, float* de_dev,
+                   int phase_mask, cudaStream_t s);
 // Learned proposer internals used by the annealer.
 void cnn_forward(lpf_cnn* c, const uint8_t* cell, cudaStream_t s);
 const float* cnn_scores(const lpf_cnn* c);   // [H][W][2] of the last forward

@@ -106,14 +106,14 @@ def train(net, cells, pairs, ys, epochs: int = 4, batch: int = 8, lr: float = 1e
 
 
 def run_until(paths, target, cell0, n_step: int, seed: int, t_max: float, net=None, eps: float = 0.1,
-              tau: float = 1.0, target_error: float | None = None, chunk: int = 64):
+              tau: float = 1.0, target_error: float | None = None, chunk: int = 64, refresh: int = 16):
     """Anneal; return (evaluations when the error first reached target_error
     (or None), final stats, seconds)."""
     import torch
     d_cell = torch.from_numpy(cell0).cuda()
     ann = lpf.lpf_sa_create(d_cell, paths, target, n_step=n_step, t_max=t_max, seed=seed)
     if net is not None:
-        lpf.lpf_sa_set_proposer(ann, net, epsilon=eps, tau=tau, refresh=16)
+        lpf.lpf_sa_set_proposer(ann, net, epsilon=eps, tau=tau, refresh=refresh)
     hit = None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -131,7 +131,7 @@ def run_until(paths, target, cell0, n_step: int, seed: int, t_max: float, net=No
 
 def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22, 23), snapshots: int = 256,
              n: int = 64, epochs: int = 8, taus=(0.5,), epss=(0.2,), on_policy: bool = False,
-             spacing: str = "early"):
+             spacing: str = "early", refreshes=(16,)):
     """Swaps-to-target gain of the learned proposer (median over eval seeds)."""
     import torch
 
@@ -168,24 +168,27 @@ def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22,
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     runs = []
-    for tau in taus:
-        for eps in epss:
-            per_seed = []
-            for s in eval_seeds:
-                e_u = ref[s][0]
-                hit, st_m, dt_m = run_until(paths, target, cells0[s], n_step, s, t_max=t_max, net=net, eps=eps,
-                                            tau=tau, target_error=e_u)
-                per_seed.append({"seed": s, "uniform_error": e_u, "model_evals": hit,
-                                 "ratio": (n_step / hit) if hit else None, "model_seconds": dt_m})
-            ratios = sorted(r["ratio"] or 0.0 for r in per_seed)
-            runs.append({"tau": tau, "epsilon": eps, "median_ratio": ratios[len(ratios) // 2], "per_seed": per_seed})
+    for refresh in refreshes:
+        for tau in taus:
+            for eps in epss:
+                per_seed = []
+                for s in eval_seeds:
+                    e_u = ref[s][0]
+                    hit, st_m, dt_m = run_until(paths, target, cells0[s], n_step, s, t_max=t_max, net=net, eps=eps,
+                                                tau=tau, target_error=e_u, refresh=refresh)
+                    per_seed.append({"seed": s, "uniform_error": e_u, "model_evals": hit,
+                                     "ratio": (n_step / hit) if hit else None, "model_seconds": dt_m})
+                ratios = sorted(r["ratio"] or 0.0 for r in per_seed)
+                runs.append({"refresh": refresh, "tau": tau, "epsilon": eps, "median_ratio": ratios[len(ratios) // 2],
+                             "per_seed": per_seed})
     best = max(runs, key=lambda r: r["median_ratio"])
     return {
         "workload": "128x128 cell, |v|<=64, target from 512x512 clustered disks (f=0.3)",
         "n_step_uniform": n_step, "uniform": {str(s): {"error": v[0], "seconds": v[1], "evals_per_s": v[2]}
                                               for s, v in ref.items()},
         "train_seeds": list(train_seeds), "eval_seeds": list(eval_seeds), "rounds": rounds, "spacing": spacing,
-        "runs": runs, "best": {"tau": best["tau"], "epsilon": best["epsilon"], "median_ratio": best["median_ratio"]},
+        "runs": runs, "best": {"refresh": best["refresh"], "tau": best["tau"], "epsilon": best["epsilon"],
+                               "median_ratio": best["median_ratio"]},
         "train_snapshots": int(cells.shape[0]), "train_candidates_per_snapshot": n, "epochs": epochs,
         "train_and_collect_seconds": t_train, "loss_first": losses[0] if losses else None,
         "loss_last": float(np.mean(losses[-8:])) if losses else None, "t_max": t_max,
@@ -204,12 +207,14 @@ def main():
     ap.add_argument("--eps", type=float, nargs="+", default=[0.2])
     ap.add_argument("--on-policy", action="store_true")
     ap.add_argument("--spacing", choices=["evals", "early"], default="early")
+    ap.add_argument("--refresh", type=int, nargs="+", default=[16])
     a = ap.parse_args()
     lpf.load()
     if a.evaluate:
         print(json.dumps(evaluate(n_step=a.n_step, train_seeds=tuple(a.train_seeds), eval_seeds=tuple(a.eval_seeds),
                                   snapshots=a.snapshots, epochs=a.epochs, taus=tuple(a.tau), epss=tuple(a.eps),
-                                  on_policy=a.on_policy, spacing=a.spacing)), flush=True)
+                                  on_policy=a.on_policy, spacing=a.spacing, refreshes=tuple(a.refresh))),
+              flush=True)
 
 
 if __name__ == "__main__":
