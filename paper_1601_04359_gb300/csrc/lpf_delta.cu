@@ -49,7 +49,7 @@ __global__ void build_ext_kernel(const uint8_t* __restrict__ img, int H, int W, 
   }
 }
 
-__global__ void __launch_bounds__(kDeltaThreads) delta_kernel(const uint8_t* __restrict__ img,
+__global__ void __launch_bounds__(kDeltaThreads, 3) delta_kernel(const uint8_t* __restrict__ img,
                                                                const uint8_t* __restrict__ ext, DeltaArgs g,
                                                                const int32_t* __restrict__ pairs, int K,
                                                                int32_t* __restrict__ dcounts,
@@ -113,9 +113,9 @@ __global__ void delta_reduce_kernel(const float* __restrict__ partial, int n_chu
 // Device tables for one cell width: CSR of the canonical segments with each
 // offset converted to an extended-cell displacement sy*We + sx, and vector
 // chunks of similar walk work.
-static int bake_delta(lpf_paths* p, int W, DeltaTables& t) {
+static int bake_delta(lpf_paths* p, int W, int want_chunks, DeltaTables& t) {
   const int We = W + 2 * p->host.rx;
-  if (t.d_doff && t.We == We) return LPF_OK;
+  if (t.d_doff && t.We == We && t.want == want_chunks) return LPF_OK;
   if (t.d_doff) {
     cudaDeviceSynchronize();
     cudaFree(t.d_doff); cudaFree(t.d_dptr); cudaFree(t.d_chunk);
@@ -128,9 +128,11 @@ static int bake_delta(lpf_paths* p, int W, DeltaTables& t) {
   // chunks balanced by sum of (L+1)^2 (walks per vector times their length bound)
   double total = 0;
   for (int64_t c = 0; c < h.n_canon; ++c) { const double l = (double)(ptr[c + 1] - ptr[c]); total += l * l; }
-  // many chunks: a single candidate spreads over many blocks (the annealer
-  // evaluates batches of a few candidates when its acceptance rate is high)
-  const int want = (int)std::max<int64_t>(1, std::min<int64_t>(512, h.n_canon / 16));
+  // as many chunks as blocks fit on the GPU at once (but at least 16 vectors
+  // each): a single candidate then runs in one wave over every SM (the
+  // annealer evaluates batches of one or a few candidates while its
+  // acceptance rate is high)
+  const int want = (int)std::max<int64_t>(1, std::min<int64_t>(want_chunks, h.n_canon / 16));
   std::vector<int32_t> chunk{0};
   double accw = 0;
   for (int64_t c = 0; c < h.n_canon; ++c) {
@@ -147,6 +149,7 @@ static int bake_delta(lpf_paths* p, int W, DeltaTables& t) {
   if ((e = cudaMemcpy(t.d_dptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return set_cuda_error(e);
   if ((e = cudaMemcpy(t.d_chunk, chunk.data(), chunk.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return set_cuda_error(e);
   t.We = We;
+  t.want = want_chunks;
   t.n_chunks = (int)chunk.size() - 1;
   return LPF_OK;
 }
@@ -184,20 +187,32 @@ int delta_prepare(lpf_paths* p, int H, int W, int K) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncAttributes fa;
+    // the swap-delta kernel and the annealing batch kernel stage the same
+    // extended cell: allow both the opt-in maximum, and limit the cell by the
+    // larger of their static shared memory
+    cudaFuncAttributes fa, fs;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, delta_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fs, sa_batch_kernel_entry());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(delta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(sa_batch_kernel_entry(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   optin - (int)fs.sharedSizeBytes);
     if (e != cudaSuccess) return set_cuda_error(e);
-    g_delta_max_smem = optin - (int)fa.sharedSizeBytes - 64;  // leave room for the annealer kernel's statics
+    g_delta_max_smem = optin - (int)std::max(fa.sharedSizeBytes, fs.sharedSizeBytes);
   }
   const size_t ext = (((size_t)(W + 2 * p->host.rx) * (H + 2 * p->host.ry)) + 15) & ~size_t(15);
   if ((int64_t)ext > g_delta_max_smem) return LPF_EUNSUPPORTED;
   int rc = ensure_device(p, 0);
   if (rc) return rc;
-  rc = bake_delta(p, W, p->delta);
+  // one wave: SMs x resident blocks of the delta and annealing kernels for
+  // this extended cell
+  int occ_d = 0, occ_s = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, delta_kernel, kDeltaThreads, (size_t)ext);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, sa_batch_kernel_entry(), kDeltaThreads,
+                                                                         (size_t)ext);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  rc = bake_delta(p, W, std::max(1, std::min(occ_d, occ_s)) * g_sms, p->delta);
   if (rc) return rc;
-  cudaError_t e;
   if (ext > p->ext_cap) {
     if (p->d_ext) { cudaDeviceSynchronize(); cudaFree(p->d_ext); p->d_ext = nullptr; p->ext_cap = 0; }
     if ((e = cudaMalloc(&p->d_ext, ext)) != cudaSuccess) return set_cuda_error(e);

@@ -15,6 +15,7 @@ constexpr uint8_t kMarkA = 4;  // phase 1 before the exchange, 0 after
 constexpr uint8_t kMarkB = 3;  // phase 0 before the exchange, 1 after
 constexpr int kDeltaThreads = 512;  // 16 warps: 3 blocks of 64 KB fill 48 of 64 warp slots
 constexpr int kDeltaWarps = kDeltaThreads / 32;
+constexpr int kWalkUnroll = 4;  // segment pixels loaded per round of a walk
 
 struct DeltaArgs {
   int H, W, rx, ry, We, He;
@@ -77,14 +78,27 @@ __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const Del
         bool alive = t < tasks;
         const int pos = (is_a ? pa : pb) - (alive ? __ldg(g.doff + o0 + i) : 0);
         int q = -1;
-        for (int j = 0; j < L1; ++j) {
+        // kWalkUnroll pixels per round: their offsets (the same in every
+        // lane) and then their bytes are loaded independently, so a round
+        // costs about one load latency instead of one per pixel; pixels are
+        // then judged in segment order, exactly as a pixel-by-pixel walk.
+        for (int j0 = 0; j0 < L1; j0 += kWalkUnroll) {
           if (!__any_sync(0xffffffffu, alive)) break;
-          const int oj = __ldg(g.doff + o0 + j);
-          if (alive && j != i) {
-            const int val = sm[pos + oj];
+          int oj[kWalkUnroll], val[kWalkUnroll];
+#pragma unroll
+          for (int u = 0; u < kWalkUnroll; ++u) oj[u] = j0 + u < L1 ? __ldg(g.doff + o0 + j0 + u) : 0;
+#pragma unroll
+          for (int u = 0; u < kWalkUnroll; ++u) {
+            const int j = j0 + u;
+            val[u] = (alive && j < L1 && j != i) ? (int)sm[pos + oj[u]] : -1;
+          }
+#pragma unroll
+          for (int u = 0; u < kWalkUnroll; ++u) {
+            const int v = val[u];
+            if (v < 0 || !alive) continue;  // beyond the segment, the anchor itself, or already ended
             if (q < 0) {
-              if (val > 1) alive = false; else q = val;
-            } else if (val != q) {
+              if (v > 1) alive = false; else q = v;
+            } else if (v != q) {
               alive = false;
             }
           }

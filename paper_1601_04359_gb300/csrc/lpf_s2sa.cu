@@ -188,13 +188,16 @@ __global__ void __launch_bounds__(kS2Threads) s2_batch_kernel(SaDev* __restrict_
     } else {
       const int y0 = (int)((int64_t)ch * g.H / g.n_chunks), y1 = (int)((int64_t)(ch + 1) * g.H / g.n_chunks);
       for (int k = blockIdx.y; k < Keff; k += gridDim.y) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
           int a, b;
           float uu;
-          draw_candidate(sm, g, n0 + (unsigned long long)k, st->key0, st->key1, a, b, uu, st);
-          if (ch == 0) { pairs[2 * k] = a; pairs[2 * k + 1] = b; u[k] = uu; }
-          s_a = a;
-          s_b = b;
+          draw_candidate_warp(sm, g, n0 + (unsigned long long)k, st->key0, st->key1, a, b, uu, st,
+                              (int)threadIdx.x);
+          if (threadIdx.x == 0) {
+            if (ch == 0) { pairs[2 * k] = a; pairs[2 * k + 1] = b; u[k] = uu; }
+            s_a = a;
+            s_b = b;
+          }
         }
         __syncthreads();
         const float acc = s_a != s_b ? s2_delta_rows(sm, g, s2_pair(g, s_a, s_b), y0, y1, nullptr) : 0.0f;
@@ -206,10 +209,12 @@ __global__ void __launch_bounds__(kS2Threads) s2_batch_kernel(SaDev* __restrict_
   }
 
   if (!sa_last_block(st)) return;
-  const long long left = st->n_step - st->n_eval;
+  __shared__ SaDev s_state;
+  sa_state_load(&s_state, st);
+  const long long left = s_state.n_step - s_state.n_eval;
   const int Kv = (int)min((long long)Keff, max(0LL, left));
   float de_star;
-  const int kstar = sa_first_accept(st, Kv, partial, g.n_chunks, u, &de_star);
+  const int kstar = sa_first_accept(&s_state, Kv, partial, g.n_chunks, u, &de_star);
   if (kstar >= 0) {
     const int a = __ldcg(pairs + 2 * kstar), b = __ldcg(pairs + 2 * kstar + 1);
     if (a != b) {
@@ -230,7 +235,8 @@ __global__ void __launch_bounds__(kS2Threads) s2_batch_kernel(SaDev* __restrict_
       }
     }
   }
-  if (threadIdx.x == 0) sa_advance(st, Keff, Kv, kstar, de_star, pairs);
+  if (threadIdx.x == 0) sa_advance(&s_state, Keff, Kv, kstar, de_star, pairs);
+  sa_state_store(st, &s_state);
 }
 
 // ---- direct counts ----------------------------------------------------------

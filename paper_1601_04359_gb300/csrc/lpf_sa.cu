@@ -121,7 +121,7 @@ __global__ void sa_draw_kernel(const uint8_t* __restrict__ ext, DeltaArgs g, uns
 }
 
 // One annealing batch (see the file comment).
-__global__ void __launch_bounds__(kDeltaThreads) sa_batch_kernel(
+__global__ void __launch_bounds__(kDeltaThreads, 3) sa_batch_kernel(
     SaDev* __restrict__ st, uint8_t* __restrict__ cell, uint8_t* __restrict__ ext, DeltaArgs g,
     int32_t* __restrict__ pairs, float* __restrict__ u, int32_t* __restrict__ dcounts, float* __restrict__ partial,
     unsigned long long* __restrict__ counts, int* __restrict__ status) {
@@ -135,20 +135,22 @@ __global__ void __launch_bounds__(kDeltaThreads) sa_batch_kernel(
   const unsigned long long n0 = (unsigned long long)st->n_eval;
 
   if ((int)blockIdx.y < Keff) {
-    if (!delta_stage(sm, ext, g.ext_bytes, &bar)) {
+      if (!delta_stage(sm, ext, g.ext_bytes, &bar)) {
       if (threadIdx.x == 0) atomicOr(status, 1);
       (void)mbar_wait(&bar, 0);
     } else {
       const int v0 = g.chunk[ch], v1 = g.chunk[ch + 1];
       for (int k = blockIdx.y; k < Keff; k += gridDim.y) {
-        if (threadIdx.x == 0) {
+        if (warp == 0) {
           int a, b;
           float uu;
-          draw_candidate(sm, g, n0 + (unsigned long long)k, st->key0, st->key1, a, b, uu, st);
-          if (ch == 0) { pairs[2 * k] = a; pairs[2 * k + 1] = b; u[k] = uu; }
-          s_a = a;
-          s_b = b;
-          if (a != b) { delta_mark(sm, a, kMarkA, g); delta_mark(sm, b, kMarkB, g); }
+          draw_candidate_warp(sm, g, n0 + (unsigned long long)k, st->key0, st->key1, a, b, uu, st, lane);
+          if (lane == 0) {
+            if (ch == 0) { pairs[2 * k] = a; pairs[2 * k + 1] = b; u[k] = uu; }
+            s_a = a;
+            s_b = b;
+            if (a != b) { delta_mark(sm, a, kMarkA, g); delta_mark(sm, b, kMarkB, g); }
+          }
         }
         __syncthreads();
         const int a = s_a, b = s_b;
@@ -171,22 +173,36 @@ __global__ void __launch_bounds__(kDeltaThreads) sa_batch_kernel(
 
   // ---- last block: accept the first passing candidate and apply it ----
   if (!sa_last_block(st)) return;
-  const long long left = st->n_step - st->n_eval;
+  __shared__ SaDev s_state;
+  sa_state_load(&s_state, st);
+  const long long left = s_state.n_step - s_state.n_eval;
   const int Kv = (int)min((long long)Keff, max(0LL, left));
   float de_star;
-  const int kstar = sa_first_accept(st, Kv, partial, g.n_chunks, u, &de_star);
+  const int kstar = sa_first_accept(&s_state, Kv, partial, g.n_chunks, u, &de_star);
   if (kstar >= 0) {
     const int a = __ldcg(pairs + 2 * kstar), b = __ldcg(pairs + 2 * kstar + 1);
     if (a != b) {
+      // count changes of the accepted candidate: 8 independent loads per
+      // round, then fire-and-forget atomic adds (this block alone writes the
+      // counts now, so the adds only avoid waiting for each read)
       const int32_t* dk = dcounts + (int64_t)kstar * 2 * g.n_canon;
       const int64_t n2 = 2 * g.n_canon;
-#pragma unroll 4
-      for (int64_t i = threadIdx.x; i < n2; i += blockDim.x) {
-        const long long d = __ldcg(dk + i);
-        if (d == 0) continue;
-        const int64_t p = i / g.n_canon, v = i - p * g.n_canon;
-        counts[p * g.n_full + g.base + v] += (unsigned long long)d;
-        if (v > 0) counts[p * g.n_full + (g.n_full - 1 - (g.base + v))] += (unsigned long long)d;
+      for (int64_t i0 = threadIdx.x; i0 < n2; i0 += 8 * (int64_t)blockDim.x) {
+        int d[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int64_t i = i0 + r * (int64_t)blockDim.x;
+          d[r] = i < n2 ? __ldcg(dk + i) : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          if (d[r] == 0) continue;
+          const int64_t i = i0 + r * (int64_t)blockDim.x;
+          const int64_t p = i / g.n_canon, v = i - p * g.n_canon;
+          const unsigned long long dd = (unsigned long long)(long long)d[r];
+          atomicAdd(counts + p * g.n_full + g.base + v, dd);
+          if (v > 0) atomicAdd(counts + p * g.n_full + (g.n_full - 1 - (g.base + v)), dd);
+        }
       }
       if (threadIdx.x == 0) {
         const uint8_t va = cell[a];
@@ -197,7 +213,8 @@ __global__ void __launch_bounds__(kDeltaThreads) sa_batch_kernel(
       }
     }
   }
-  if (threadIdx.x == 0) sa_advance(st, Keff, Kv, kstar, de_star, pairs);
+  if (threadIdx.x == 0) sa_advance(&s_state, Keff, Kv, kstar, de_star, pairs);
+  sa_state_store(st, &s_state);
 }
 
 // e = sum over the phases p in phase_mask and base <= k < n_full of
@@ -242,7 +259,7 @@ __global__ void build_ext_sa_kernel(const uint8_t* __restrict__ img, DeltaArgs g
 
 namespace lpf {
 
-static int g_sa_attr = 0;
+const void* sa_batch_kernel_entry() { return reinterpret_cast<const void*>(&sa_batch_kernel); }
 
 // Score the current cell with the network and rebuild the sampling tables.
 static void enqueue_refresh(lpf_sa* sa, cudaStream_t s) {
@@ -376,18 +393,6 @@ int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, con
   if (rc) return rc;
   rc = lpf::delta_prepare(paths, H, W, 1);
   if (rc) return rc;
-  if (!lpf::g_sa_attr) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, lpf::sa_batch_kernel);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(lpf::sa_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               optin - (int)fa.sharedSizeBytes);
-    if (e != cudaSuccess) return lpf::set_cuda_error(e);
-    lpf::g_sa_attr = 1;
-  }
   lpf_sa* sa = new (std::nothrow) lpf_sa();
   if (!sa) return LPF_ENOMEM;
   sa->paths = paths;

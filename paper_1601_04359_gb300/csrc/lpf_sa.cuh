@@ -101,6 +101,45 @@ static __device__ void draw_candidate(const uint8_t* e, const DeltaArgs& g, unsi
   if (a < 0 || b < 0) { a = 0; b = 0; }
 }
 
+// draw_candidate evaluated by a whole warp: lane j tries attempt j0 + j of
+// the rejection sampling, and a ballot picks the lowest attempt that found a
+// valid phase-1 pixel (and, independently, phase-0 pixel) -- the attempts the
+// sequential loop would have kept.  Attempt 0 (lane 0 of the first round)
+// gives U and the model choice.  Every lane returns the same (a, b, u).
+__device__ __forceinline__ void draw_candidate_warp(const uint8_t* e, const DeltaArgs& g, unsigned long long n,
+                                                    uint32_t k0, uint32_t k1, int& a, int& b, float& u,
+                                                    const SaDev* st, int lane) {
+  const unsigned npix = (unsigned)(g.H * g.W);
+  a = -1;
+  b = -1;
+  bool model = false;
+  for (uint32_t j0 = 0; j0 < (uint32_t)kMaxTries && (a < 0 || b < 0); j0 += 32) {
+    const U4 r = philox4x32_10(U4{(uint32_t)n, (uint32_t)(n >> 32), j0 + (uint32_t)lane, 0u}, k0, k1);
+    if (j0 == 0) {
+      const float u0 = ((float)(r.z >> 8) + 0.5f) * (1.0f / 16777216.0f);
+      const int m0 = st && st->use_model && st->tot1 > 0.0f && st->tot0 > 0.0f &&
+                     ((float)(r.w >> 8) + 0.5f) * (1.0f / 16777216.0f) >= st->eps;
+      u = __shfl_sync(0xffffffffu, u0, 0);
+      model = __shfl_sync(0xffffffffu, m0, 0) != 0;
+    }
+    int ca = -1, cb = -1;
+    if (a < 0) {
+      ca = model ? cdf_search(st->cdf1, (int)npix, ((float)(r.x >> 8) + 0.5f) * (1.0f / 16777216.0f) * st->tot1)
+                 : (int)(((unsigned long long)r.x * npix) >> 32);
+      if (!(ext_pixel(e, ca, g) == 1 && interfacial(e, ca, g))) ca = -1;
+    }
+    if (b < 0) {
+      cb = model ? cdf_search(st->cdf0, (int)npix, ((float)(r.y >> 8) + 0.5f) * (1.0f / 16777216.0f) * st->tot0)
+                 : (int)(((unsigned long long)r.y * npix) >> 32);
+      if (!(ext_pixel(e, cb, g) == 0 && interfacial(e, cb, g))) cb = -1;
+    }
+    const unsigned ba = __ballot_sync(0xffffffffu, ca >= 0), bb = __ballot_sync(0xffffffffu, cb >= 0);
+    if (a < 0 && ba) a = __shfl_sync(0xffffffffu, ca, __ffs(ba) - 1);
+    if (b < 0 && bb) b = __shfl_sync(0xffffffffu, cb, __ffs(bb) - 1);
+  }
+  if (a < 0 || b < 0) { a = 0; b = 0; }
+}
+
 // ---- end of a batch (last block) -----------------------------------------
 
 // The first candidate k < Kv that passes the Metropolis test (Delta e <= 0 or
@@ -122,13 +161,22 @@ __device__ __forceinline__ int sa_first_accept(const SaDev* st, int Kv, const fl
   for (; k0 < Kv; k0 += nw) {
     const int k = k0 + warp;
     if (k < Kv) {
-      float de = 0.0f;
+      // lane-strided sum in chunk order; the first 16 rounds are loaded
+      // before they are added so that their latencies overlap
       const float* pk = partial + (int64_t)k * n_chunks;
-      for (int c = lane; c < n_chunks; c += 32) de += __ldcg(pk + c);
+      float v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = lane + 32 * r < n_chunks ? __ldcg(pk + lane + 32 * r) : 0.0f;
+      float de = 0.0f;
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        if (lane + 32 * r < n_chunks) de += v[r];
+      for (int c = lane + 32 * 16; c < n_chunks; c += 32) de += __ldcg(pk + c);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) de += __shfl_xor_sync(0xffffffffu, de, o);
       if (lane == 0) {
-        const double Tk = T0 * pow(Tm, (double)((c0 + k) / cmax));
+        const long long wk = (c0 + k) / cmax;  // stage ends before candidate k
+        const double Tk = wk ? T0 * pow(Tm, (double)wk) : T0;
         const bool acc = de <= 0.0f || __ldcg(u + k) < expf(-de / (float)Tk);
         if (acc) atomicMin(&s_kstar, k);
         s_de[warp] = de;
@@ -156,9 +204,11 @@ __device__ __forceinline__ void sa_advance(SaDev* st, int Keff, int Kv, int ksta
   long long c = c0 + rej, s = st->s_stage;
   double T = st->T;
   const long long wraps = c / cmax;
-  if (wraps > 0) s = 0;
+  if (wraps > 0) {
+    s = 0;
+    T *= pow(Tm, (double)wraps);
+  }
   c -= wraps * cmax;
-  T *= pow(Tm, (double)wraps);
   if (kstar >= 0) {
     c += 1;
     s += 1;
@@ -190,6 +240,25 @@ __device__ __forceinline__ void sa_advance(SaDev* st, int Keff, int Kv, int ksta
   st->k_eff = (int)fmin((double)st->k_max, fmax((double)st->k_min, want));
   if (st->n_eval >= st->n_step) st->done = 1;
   st->ticket = 0u;
+}
+
+// The serial end of a batch works on a copy of the run state in shared
+// memory: loaded and stored back with one 8-byte word per thread, so that
+// its many small reads and updates do not each wait for L2.
+static_assert(sizeof(SaDev) % 8 == 0, "run state is copied in 8-byte words");
+constexpr int kSaStateWords = (int)(sizeof(SaDev) / 8);
+
+__device__ __forceinline__ void sa_state_load(SaDev* sh, const SaDev* st) {
+  if ((int)threadIdx.x < kSaStateWords)
+    reinterpret_cast<unsigned long long*>(sh)[threadIdx.x] =
+        __ldcg(reinterpret_cast<const unsigned long long*>(st) + threadIdx.x);
+  __syncthreads();
+}
+
+__device__ __forceinline__ void sa_state_store(SaDev* st, const SaDev* sh) {
+  __syncthreads();
+  if ((int)threadIdx.x < kSaStateWords)
+    reinterpret_cast<unsigned long long*>(st)[threadIdx.x] = reinterpret_cast<const unsigned long long*>(sh)[threadIdx.x];
 }
 
 // Atomic ticket: true in the last block of the grid to get here (after a

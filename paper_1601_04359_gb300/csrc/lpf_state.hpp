@@ -49,6 +49,7 @@ struct Baked {
 // Tables of the swap-delta kernel for one extended cell width.
 struct DeltaTables {
   int We = -1;
+  int want = -1;               // vector chunks asked for (one wave of blocks)
   int32_t* d_doff = nullptr;   // per segment pixel: sy*We + sx
   int32_t* d_dptr = nullptr;   // CSR pointers [n_canon + 1]
   int32_t* d_chunk = nullptr;  // vector chunk bounds [n_chunks + 1]
@@ -92,6 +93,9 @@ int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g);
 // Candidate strides per vector chunk for K candidates.
 int delta_stride(int n_chunks, int K);
 int delta_max_smem();
+// The annealing batch kernel of the lineal-path objective (lpf_sa.cu), for
+// attribute and occupancy queries.
+const void* sa_batch_kernel_entry();
 // lpf_delta_swap with the error restricted to the phases in phase_mask.
 int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, const int32_t* pairs_dev,
                    int32_t K, int32_t* dcounts_dev, const float* target_dev, const int64_t* counts_dev, float* de_dev,
