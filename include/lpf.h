@@ -358,21 +358,25 @@ int lpf_sa_create(uint8_t *cell_dev, int32_t H, int32_t W, lpf_paths *paths,
 
 /*
  * Enqueue n_batches annealing batches on `stream` without synchronising.
- * Each batch is one kernel launch: it draws the next k candidates,
- * evaluates all of them as lpf_delta_swap does, and its last block accepts
- * the first that passes the Metropolis test (Delta e <= 0 or
- * U < exp(-Delta e / T)), applies it to the cell and the counts and updates
- * the temperature stage; k adapts to the acceptance rate p (running
- * estimate) as ceil(1/(2p)), clamped to [k_min, k_max].  Batches after the
- * run is done do nothing.  The first call with n_batches >= 16 (or >= the
- * proposer's refresh interval when a proposer is set) captures that many
- * batches as a CUDA graph, replayed afterwards.
- * Errors: LPF_EINVAL, LPF_ECUDA.
+ * A batch draws the next k candidates, evaluates all of them as
+ * lpf_delta_swap does, accepts the first that passes the Metropolis test
+ * (Delta e <= 0 or U < exp(-Delta e / T)), applies it to the cell and the
+ * counts and updates the temperature stage; k adapts to the acceptance rate
+ * p (running estimate) as ceil(1/(2p)), clamped to [k_min, k_max].  Batches
+ * after the run is done do nothing.
+ * Lineal-path runs use one cooperative launch of a persistent kernel for up
+ * to 4096 batches (or the proposer's refresh interval), whose resident
+ * blocks keep the cell on chip and meet at a bounded grid barrier once per
+ * batch.  S2 runs (and devices without cooperative launch) use one kernel
+ * launch per batch, the first call with n_batches >= 16 (or >= the refresh
+ * interval) capturing that many as a CUDA graph that is replayed afterwards.
+ * Both give the same run.  Errors: LPF_EINVAL, LPF_ECUDA.
  */
 int lpf_sa_run(lpf_sa *sa, int32_t n_batches, lpf_stream_t stream);
 
 /* Synchronise `stream` and copy the run's counters to *out; LPF_ETIMEOUT
- * (counters still copied) if a bounded wait in a batch kernel gave up. */
+ * (counters still copied, state not to be trusted) if a bounded wait in a
+ * batch kernel gave up (staging copy or grid barrier). */
 int lpf_sa_read(lpf_sa *sa, lpf_sa_stats *out, lpf_stream_t stream);
 
 /* Recompute the error from the exact counts in double precision, store it

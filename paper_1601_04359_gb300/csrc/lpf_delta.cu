@@ -190,15 +190,19 @@ int delta_prepare(lpf_paths* p, int H, int W, int K) {
     // the swap-delta kernel and the annealing batch kernel stage the same
     // extended cell: allow both the opt-in maximum, and limit the cell by the
     // larger of their static shared memory
-    cudaFuncAttributes fa, fs;
+    cudaFuncAttributes fa, fs, fp;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, delta_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fs, sa_batch_kernel_entry());
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fp, sa_persistent_kernel_entry());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(delta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    optin - (int)fa.sharedSizeBytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(sa_batch_kernel_entry(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    optin - (int)fs.sharedSizeBytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(sa_persistent_kernel_entry(),
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   optin - (int)fp.sharedSizeBytes);
     if (e != cudaSuccess) return set_cuda_error(e);
-    g_delta_max_smem = optin - (int)std::max(fa.sharedSizeBytes, fs.sharedSizeBytes);
+    g_delta_max_smem = optin - (int)std::max(std::max(fa.sharedSizeBytes, fs.sharedSizeBytes), fp.sharedSizeBytes);
   }
   const size_t ext = (((size_t)(W + 2 * p->host.rx) * (H + 2 * p->host.ry)) + 15) & ~size_t(15);
   if ((int64_t)ext > g_delta_max_smem) return LPF_EUNSUPPORTED;
@@ -206,12 +210,15 @@ int delta_prepare(lpf_paths* p, int H, int W, int K) {
   if (rc) return rc;
   // one wave: SMs x resident blocks of the delta and annealing kernels for
   // this extended cell
-  int occ_d = 0, occ_s = 0;
+  // (the persistent annealer needs every chunk's block resident at once)
+  int occ_d = 0, occ_s = 0, occ_p = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, delta_kernel, kDeltaThreads, (size_t)ext);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, sa_batch_kernel_entry(), kDeltaThreads,
                                                                          (size_t)ext);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, sa_persistent_kernel_entry(), kDeltaThreads, (size_t)ext);
   if (e != cudaSuccess) return set_cuda_error(e);
-  rc = bake_delta(p, W, std::max(1, std::min(occ_d, occ_s)) * g_sms, p->delta);
+  rc = bake_delta(p, W, std::max(1, std::min(std::min(occ_d, occ_s), occ_p)) * g_sms, p->delta);
   if (rc) return rc;
   if (ext > p->ext_cap) {
     if (p->d_ext) { cudaDeviceSynchronize(); cudaFree(p->d_ext); p->d_ext = nullptr; p->ext_cap = 0; }

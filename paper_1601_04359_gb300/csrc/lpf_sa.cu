@@ -217,6 +217,135 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_batch_kernel(
   sa_state_store(st, &s_state);
 }
 
+// ---- persistent annealer ----------------------------------------------------
+//
+// The same sequence of batches as sa_batch_kernel, run by one cooperative
+// launch whose blocks stay resident for n_batches batches: block c owns
+// vector chunk c (the grid is exactly the chunk count, all blocks co-resident)
+// and keeps its extended cell and a copy of the run state in shared memory.
+// Per batch every block draws the batch's candidates, walks its chunk for
+// each and writes its partial error changes; after one grid barrier every
+// block sums the partials of each candidate in the same fixed order, so all
+// blocks find the same first accepted candidate, apply it to their own cell
+// copy and to the counts of their own vectors, and advance their identical
+// copies of the run state.  Partials, pairs and uniforms alternate between
+// two buffers by batch parity: batch b + 2 may overwrite batch b's only after
+// the barrier of batch b + 1, which no block reaches before it has read them.
+
+constexpr uint32_t kBarrierPolls = 1u << 22;  // polls of a grid barrier before giving up (seconds)
+
+// Grid barrier on a counter that only grows: block arrivals up to the end of
+// batch b are (b + 1) * gridDim.x.  False (and status bit 4) if the other
+// blocks did not arrive within kBarrierPolls polls.
+__device__ __forceinline__ bool sa_grid_barrier(unsigned int* count, unsigned int target, int* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    int ok = 0;
+    for (uint32_t it = 0; it < kBarrierPolls; ++it) {
+      if (*reinterpret_cast<volatile unsigned int*>(count) >= target) { ok = 1; break; }
+      __nanosleep(64);
+    }
+    if (!ok) atomicOr(status, 4);
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
+    SaDev* __restrict__ st, uint8_t* __restrict__ cell, uint8_t* __restrict__ ext, DeltaArgs g,
+    int32_t* __restrict__ pairs2, float* __restrict__ u2, int32_t* __restrict__ dcounts, float* __restrict__ partial2,
+    unsigned long long* __restrict__ counts, int* __restrict__ status, unsigned int* __restrict__ bar, int n_batches,
+    int k_max) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ SaDev s_state;
+  __shared__ float warp_acc[kDeltaWarps];
+  __shared__ int s_a, s_b;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ch = blockIdx.x;
+  const int v0 = g.chunk[ch], v1 = g.chunk[ch + 1];
+  sa_state_load(&s_state, st);
+  if (!delta_stage(sm, ext, g.ext_bytes, &mbar)) {
+    if (threadIdx.x == 0) atomicOr(status, 1);
+    (void)mbar_wait(&mbar, 0);
+  }
+  for (int bi = 0; bi < n_batches && !s_state.done; ++bi) {
+    const int Keff = s_state.k_eff;
+    const unsigned long long n0 = (unsigned long long)s_state.n_eval;
+    int32_t* pairs = pairs2 + (size_t)(bi & 1) * 2 * k_max;
+    float* u = u2 + (size_t)(bi & 1) * k_max;
+    float* partial = partial2 + (size_t)(bi & 1) * k_max * g.n_chunks;
+    for (int k = 0; k < Keff; ++k) {
+      if (warp == 0) {
+        int a, b;
+        float uu;
+        draw_candidate_warp(sm, g, n0 + (unsigned long long)k, s_state.key0, s_state.key1, a, b, uu, &s_state, lane);
+        if (lane == 0) {
+          if (ch == 0) { pairs[2 * k] = a; pairs[2 * k + 1] = b; u[k] = uu; }
+          s_a = a;
+          s_b = b;
+          if (a != b) { delta_mark(sm, a, kMarkA, g); delta_mark(sm, b, kMarkB, g); }
+        }
+      }
+      __syncthreads();
+      const int a = s_a, b = s_b;
+      int32_t* dk = dcounts + (int64_t)k * 2 * g.n_canon;
+      float acc = 0.0f;
+      if (a == b) delta_zero_vectors(g, v0, v1, dk);
+      else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk);
+      if (lane == 0) warp_acc[warp] = acc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float sum = 0.0f;
+        for (int w = 0; w < kDeltaWarps; ++w) sum += warp_acc[w];
+        partial[(int64_t)k * g.n_chunks + ch] = sum;
+        if (a != b) { delta_mark(sm, a, 1, g); delta_mark(sm, b, 0, g); }
+      }
+      __syncthreads();
+    }
+    if (!sa_grid_barrier(bar, (unsigned int)(bi + 1) * gridDim.x, status)) break;
+
+    const long long left = s_state.n_step - s_state.n_eval;
+    const int Kv = (int)min((long long)Keff, max(0LL, left));
+    float de_star;
+    const int kstar = sa_first_accept(&s_state, Kv, partial, g.n_chunks, u, &de_star);
+    if (kstar >= 0) {
+      const int a = __ldcg(pairs + 2 * kstar), b = __ldcg(pairs + 2 * kstar + 1);
+      if (a != b) {
+        // this block's vectors: apply the accepted candidate's changes
+        const int32_t* dk = dcounts + (int64_t)kstar * 2 * g.n_canon;
+        for (int v = v0 + (int)threadIdx.x; v < v1; v += blockDim.x) {
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            const long long d = dk[(int64_t)p * g.n_canon + v];
+            if (d == 0) continue;
+            counts[p * g.n_full + g.base + v] += (unsigned long long)d;
+            if (v > 0) counts[p * g.n_full + (g.n_full - 1 - (g.base + v))] += (unsigned long long)d;
+          }
+        }
+        if (threadIdx.x == 0) {
+          delta_mark(sm, a, 0, g);
+          delta_mark(sm, b, 1, g);
+          if (ch == 0) {
+            cell[a] = 0;
+            cell[b] = 1;
+            delta_mark(ext, a, 0, g);
+            delta_mark(ext, b, 1, g);
+          }
+        }
+      }
+    }
+    if (threadIdx.x == 0) sa_advance(&s_state, Keff, Kv, kstar, de_star, pairs);
+    __syncthreads();
+  }
+  if (ch == 0) sa_state_store(st, &s_state);
+}
+
 // e = sum over the phases p in phase_mask and base <= k < n_full of
 // (target[p][k] - counts[p][k] / N)^2, in double (one block of 256 threads).
 __global__ void sa_error_kernel(const float* __restrict__ target, const int64_t* __restrict__ counts, int64_t n_full,
@@ -260,6 +389,23 @@ __global__ void build_ext_sa_kernel(const uint8_t* __restrict__ img, DeltaArgs g
 namespace lpf {
 
 const void* sa_batch_kernel_entry() { return reinterpret_cast<const void*>(&sa_batch_kernel); }
+const void* sa_persistent_kernel_entry() { return reinterpret_cast<const void*>(&sa_persistent_kernel); }
+
+constexpr int kPersistentBatches = 4096;  // batches per persistent launch (bounds one launch's duration)
+
+// Launch the persistent annealer for nb batches (cooperative launch: every
+// block is resident, which its grid barrier relies on).
+static int launch_persistent(lpf_sa* sa, int nb, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sa->d_bar, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  unsigned long long* counts = reinterpret_cast<unsigned long long*>(sa->counts);
+  int k_max = sa->prm.k_max;
+  void* args[] = {&sa->d_st, &sa->cell, &sa->d_ext, &sa->g, &sa->d_pairs, &sa->d_u, &sa->d_dc, &sa->d_partial,
+                  &counts, &sa->d_status, &sa->d_bar, &nb, &k_max};
+  e = cudaLaunchCooperativeKernel(sa_persistent_kernel_entry(), dim3(sa->g.n_chunks), dim3(kDeltaThreads), args,
+                                  sa->g.ext_bytes, s);
+  return set_cuda_error(e);
+}
 
 // Score the current cell with the network and rebuild the sampling tables.
 static void enqueue_refresh(lpf_sa* sa, cudaStream_t s) {
@@ -307,10 +453,13 @@ int sa_start(lpf_sa* sa, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&sa->d_st, sizeof(SaDev));
   if (e == cudaSuccess) e = cudaMalloc(&sa->d_ext, sa->g.ext_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_pairs, 2 * (size_t)prm->k_max * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_u, (size_t)prm->k_max * sizeof(float));
+  // pairs, uniforms and partials: two buffers each (the persistent kernel
+  // alternates between them by batch parity; the batch kernel uses the first)
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_pairs, 2 * 2 * (size_t)prm->k_max * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_u, 2 * (size_t)prm->k_max * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&sa->d_de, (size_t)prm->k_max * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&sa->d_partial, (size_t)prm->k_max * nch * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_partial, 2 * (size_t)prm->k_max * nch * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&sa->d_bar, sizeof(unsigned int));
   if (e == cudaSuccess && sa->objective == kSaObjectiveLineal)
     e = cudaMalloc(&sa->d_dc, (size_t)prm->k_max * 2 * (size_t)sa->paths->host.n_canon * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&sa->d_e, sizeof(double));
@@ -412,6 +561,19 @@ int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, con
   sa->g.counts = counts_dev;
   sa->g.phase_mask = sa->phase_mask;
   sa->grid = dim3(sa->g.n_chunks, lpf::delta_stride(sa->g.n_chunks, prm->k_max));
+  {
+    // persistent batches when the device launches cooperatively and every
+    // chunk's block fits at once (the chunk count is sized for that)
+    int dev = 0, coop = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lpf::sa_persistent_kernel_entry(), lpf::kDeltaThreads,
+                                                        sa->g.ext_bytes);
+    if (e != cudaSuccess) { lpf_sa_free(sa); return lpf::set_cuda_error(e); }
+    sa->persistent = (coop && sa->g.n_chunks <= occ * sms) ? 1 : 0;
+  }
   rc = lpf::sa_start(sa, s);
   if (rc) { lpf_sa_free(sa); return rc; }
   *out = sa;
@@ -423,6 +585,17 @@ int lpf_sa_run(lpf_sa* sa, int32_t n_batches, lpf_stream_t stream) {
   if (n_batches == 0) return LPF_OK;
   cudaStream_t s = (cudaStream_t)stream;
   (void)cudaGetLastError();
+  if (sa->persistent) {
+    // a proposer is re-scored every `refresh` batches, between launches
+    for (int left = n_batches; left > 0;) {
+      const int nb = std::min(left, sa->cnn ? sa->refresh : lpf::kPersistentBatches);
+      lpf::enqueue_refresh(sa, s);
+      const int rc = lpf::launch_persistent(sa, nb, s);
+      if (rc) return rc;
+      left -= nb;
+    }
+    return lpf::set_cuda_error(cudaGetLastError());
+  }
   // One captured graph holds kGraphBatches batches; replay it, then enqueue
   // the remainder directly.
   const int kGraphBatches = sa->cnn ? sa->refresh : 16;
@@ -544,6 +717,7 @@ void lpf_sa_free(lpf_sa* sa) {
   cudaFree(sa->d_e);
   cudaFree(sa->d_status);
   cudaFree(sa->d_cdf);
+  cudaFree(sa->d_bar);
   delete sa;
 }
 

@@ -309,6 +309,8 @@ struct lpf_sa {
   int phase_mask = 3;           // phases in the lineal-path error
   int64_t err_n_full = 0, err_base = 0;  // error layout: [phase][err_n_full], summed from err_base
   int threads = 0;              // batch kernel block size
+  int persistent = 0;           // batches run by the cooperative persistent kernel
+  unsigned int* d_bar = nullptr;  // its grid-barrier counter
 };
 
 namespace lpf {

@@ -96,6 +96,7 @@ int delta_max_smem();
 // The annealing batch kernel of the lineal-path objective (lpf_sa.cu), for
 // attribute and occupancy queries.
 const void* sa_batch_kernel_entry();
+const void* sa_persistent_kernel_entry();
 // lpf_delta_swap with the error restricted to the phases in phase_mask.
 int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, const int32_t* pairs_dev,
                    int32_t K, int32_t* dcounts_dev, const float* target_dev, const int64_t* counts_dev, float* de_dev,
