@@ -225,7 +225,8 @@ int lpf_full_standard(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *p
  *                integer changes; summed in a fixed order (bitwise
  *                reproducible).
  * At least one of dcounts_dev, de_dev must be non-NULL.  Cell limits: the
- * periodically extended cell (W+2rx)*(H+2ry) bytes must fit in shared memory
+ * periodically extended cell (W+2rx, padded to an odd number of 4-byte
+ * words) x (H+2ry) bytes must fit in shared memory
  * (about 227 KB), else LPF_EUNSUPPORTED.  The first call for a cell width, or
  * with a larger K than before, allocates the handle's tables / work area.
  * Errors: LPF_EINVAL, LPF_EUNSUPPORTED, LPF_ENOMEM, LPF_ECUDA.
@@ -388,6 +389,19 @@ int lpf_sa_recompute_error(lpf_sa *sa, double *e, lpf_stream_t stream);
  * Metropolis uniforms), without advancing the run.  k <= k_max.
  * Synchronises.  For inspection and tests. */
 int lpf_sa_propose(lpf_sa *sa, int32_t k, int32_t *pairs_dev, float *u_dev, lpf_stream_t stream);
+
+/*
+ * Check of the annealer's failure detection (no counterpart in the paper):
+ * runs one batch of the persistent kernel whose grid barrier waits for one
+ * block arrival more than the grid makes, so that every block's bounded wait
+ * runs out (about a second or two), and returns LPF_OK when the kernel
+ * reported the timeout through the status word and left the run state
+ * unchanged; the status is cleared afterwards, so the run continues as if
+ * the call had not happened.  Synchronises.  LPF_EUNSUPPORTED when the run
+ * does not use the persistent kernel; LPF_ETIMEOUT if an earlier wait had
+ * already failed; LPF_ECUDA if the timeout was not reported.
+ */
+int lpf_sa_selftest_timeout(lpf_sa *sa, lpf_stream_t stream);
 
 /* Release a run (NULL is ignored); synchronises the device. */
 void lpf_sa_free(lpf_sa *sa);

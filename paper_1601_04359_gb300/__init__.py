@@ -20,7 +20,7 @@ __all__ = [
     "lpf_paths_stats", "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer",
     "lpf_delta_swap", "lpf_full_mc", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror",
     "SaParams", "SaStats", "Annealer", "lpf_sa_create", "lpf_sa_run", "lpf_sa_read", "lpf_sa_recompute_error",
-    "lpf_sa_propose", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
+    "lpf_sa_propose", "lpf_sa_selftest_timeout", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
     "lpf_cnn_forward", "lpf_cnn_gradients", "lpf_cnn_train_step", "lpf_sa_set_proposer", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune", "lpf_batch_status",
 ]
 
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_full_mc": (ctypes.c_int, [p, i32, i32, p, p, p, p]),
         "s2_fft": (ctypes.c_int, [p, i32, i32, i32, p, p]),
         "s2_counts": (ctypes.c_int, [p, i32, i32, p, p]),
+        "lpf_sa_selftest_timeout": (ctypes.c_int, [p, p]),
         "s2_delta_swap": (ctypes.c_int, [p, i32, i32, p, i32, p, p, p, p, p]),
         "s2_sa_create": (ctypes.c_int, [p, i32, i32, p, p, ctypes.POINTER(SaParams), p, ctypes.POINTER(p)]),
         "lpf_cnn_create": (ctypes.c_int, [i32, i32, ctypes.c_uint64, ctypes.POINTER(p)]),
@@ -375,6 +376,12 @@ def lpf_sa_recompute_error(sa: Annealer, stream=None) -> float:
     e = ctypes.c_double()
     _check(load().lpf_sa_recompute_error(sa.handle, ctypes.byref(e), _stream_ptr(stream)), "lpf_sa_recompute_error")
     return e.value
+
+
+def lpf_sa_selftest_timeout(sa: Annealer, stream=None) -> int:
+    """Status code of the annealer's timeout check (0: the bounded grid-barrier
+    wait ran out, was reported, and left the run unchanged)."""
+    return int(load().lpf_sa_selftest_timeout(sa.handle, _stream_ptr(stream)))
 
 
 def lpf_sa_propose(sa: Annealer, k: int, stream=None):

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) delta_kernel(const uint8_t* 
     int32_t* dk = dcounts ? dcounts + (int64_t)k * 2 * g.n_canon : nullptr;
     float acc = 0.0f;
     if (skip) delta_zero_vectors(g, v0, v1, dk);
-    else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk);
+    else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk, delta_terms_global(g));
     if (lane == 0) warp_acc[warp] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -114,7 +114,7 @@ __global__ void delta_reduce_kernel(const float* __restrict__ partial, int n_chu
 // offset converted to an extended-cell displacement sy*We + sx, and vector
 // chunks of similar walk work.
 static int bake_delta(lpf_paths* p, int W, int want_chunks, DeltaTables& t) {
-  const int We = W + 2 * p->host.rx;
+  const int We = delta_row_stride(W, p->host.rx);
   if (t.d_doff && t.We == We && t.want == want_chunks) return LPF_OK;
   if (t.d_doff) {
     cudaDeviceSynchronize();
@@ -151,6 +151,8 @@ static int bake_delta(lpf_paths* p, int W, int want_chunks, DeltaTables& t) {
   t.We = We;
   t.want = want_chunks;
   t.n_chunks = (int)chunk.size() - 1;
+  t.max_chunk_vecs = 0;
+  for (size_t c = 0; c + 1 < chunk.size(); ++c) t.max_chunk_vecs = std::max(t.max_chunk_vecs, chunk[c + 1] - chunk[c]);
   return LPF_OK;
 }
 
@@ -162,7 +164,7 @@ int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g) {
   g.W = W;
   g.rx = p->host.rx;
   g.ry = p->host.ry;
-  g.We = W + 2 * g.rx;
+  g.We = delta_row_stride(W, g.rx);
   g.He = H + 2 * g.ry;
   g.ext_bytes = (uint32_t)((((size_t)g.We * g.He) + 15) & ~size_t(15));
   g.dptr = p->delta.d_dptr;
@@ -175,6 +177,7 @@ int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g) {
   g.target = nullptr;
   g.counts = nullptr;
   g.phase_mask = 3;
+  g.max_chunk_vecs = p->delta.max_chunk_vecs;
   return LPF_OK;
 }
 
@@ -204,7 +207,7 @@ int delta_prepare(lpf_paths* p, int H, int W, int K) {
     if (e != cudaSuccess) return set_cuda_error(e);
     g_delta_max_smem = optin - (int)std::max(std::max(fa.sharedSizeBytes, fs.sharedSizeBytes), fp.sharedSizeBytes);
   }
-  const size_t ext = (((size_t)(W + 2 * p->host.rx) * (H + 2 * p->host.ry)) + 15) & ~size_t(15);
+  const size_t ext = (((size_t)delta_row_stride(W, p->host.rx) * (H + 2 * p->host.ry)) + 15) & ~size_t(15);
   if ((int64_t)ext > g_delta_max_smem) return LPF_EUNSUPPORTED;
   int rc = ensure_device(p, 0);
   if (rc) return rc;
@@ -218,8 +221,23 @@ int delta_prepare(lpf_paths* p, int H, int W, int K) {
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, sa_persistent_kernel_entry(), kDeltaThreads, (size_t)ext);
   if (e != cudaSuccess) return set_cuda_error(e);
-  rc = bake_delta(p, W, std::max(1, std::min(std::min(occ_d, occ_s), occ_p)) * g_sms, p->delta);
+  const int occ = std::max(1, std::min(std::min(occ_d, occ_s), occ_p));
+  rc = bake_delta(p, W, occ * g_sms, p->delta);
   if (rc) return rc;
+  {
+    // the persistent kernel also keeps its chunk's counts and targets: check
+    // the chunking once more with the size it produced
+    const size_t persist = ext + (size_t)p->delta.max_chunk_vecs * 2 * (sizeof(long long) + sizeof(float));
+    int occ2 = 0;
+    if ((int64_t)persist <= g_delta_max_smem &&
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, sa_persistent_kernel_entry(), kDeltaThreads,
+                                                           persist)) != cudaSuccess)
+      return set_cuda_error(e);
+    if (occ2 > 0 && occ2 < occ) {
+      rc = bake_delta(p, W, occ2 * g_sms, p->delta);
+      if (rc) return rc;
+    }
+  }
   if (ext > p->ext_cap) {
     if (p->d_ext) { cudaDeviceSynchronize(); cudaFree(p->d_ext); p->d_ext = nullptr; p->ext_cap = 0; }
     if ((e = cudaMalloc(&p->d_ext, ext)) != cudaSuccess) return set_cuda_error(e);

@@ -1,9 +1,10 @@
 // Device pieces of the swap-delta evaluation shared by lpf_delta_swap and the
 // annealer (see lpf_delta.cu for the method).
 //
-// Extended cell: bytes, (W + 2rx) x (H + 2ry), entry (ey, ex) = pixel
-// ((ey - ry) mod H, (ex - rx) mod W), so a walk of any segment through a
-// pixel never wraps.  A block stages it in shared memory with one bulk copy.
+// Extended cell: bytes, H + 2ry rows of W + 2rx pixels (row stride
+// delta_row_stride), entry (ey, ex) = pixel ((ey - ry) mod H, (ex - rx) mod
+// W), so a walk of any segment through a pixel never wraps.  A block stages
+// it in shared memory with one bulk copy.
 #pragma once
 #include <cstdint>
 
@@ -28,7 +29,39 @@ struct DeltaArgs {
   const float* target;          // [2][n_full] or null
   const int64_t* counts;        // [2][n_full] or null
   int phase_mask;               // phases in the error: bit p = phase p (3 = both)
+  int max_chunk_vecs;           // vectors in the largest chunk
 };
+
+// Where a walk finds the target and the current count of vector v for the
+// error change: entry v - vbase of t[p] and c[p] (phase p).  Either the
+// global arrays (vbase 0, pointers offset by the canonical base) or a
+// block's copy of its chunk in shared memory (vbase = first vector).
+struct DeltaTerms {
+  const float* t[2];
+  const long long* c[2];
+  int vbase;
+};
+
+__device__ __forceinline__ DeltaTerms delta_terms_global(const DeltaArgs& g) {
+  DeltaTerms d;
+  d.t[0] = g.target ? g.target + g.base : nullptr;
+  d.t[1] = g.target ? g.target + g.n_full + g.base : nullptr;
+  d.c[0] = g.counts ? reinterpret_cast<const long long*>(g.counts) + g.base : nullptr;
+  d.c[1] = g.counts ? reinterpret_cast<const long long*>(g.counts) + g.n_full + g.base : nullptr;
+  d.vbase = 0;
+  return d;
+}
+
+// Row stride (bytes) of the extended cell: at least W + 2 rx, and an odd
+// number of 4-byte words, so that 32 lanes reading one byte each from 32
+// consecutive rows (the walks of a near-vertical segment) hit 32 different
+// shared-memory banks.  The padding columns are never read.
+__host__ __device__ inline int delta_row_stride(int W, int rx) {
+  int we = W + 2 * rx;
+  we = (we + 3) & ~3;
+  if ((we >> 2) % 2 == 0) we += 4;
+  return we;
+}
 
 __device__ __forceinline__ int delta_ext_pos(int c, int W, int We, int rx, int ry) {
   const int cy = c / W, cx = c - cy * W;
@@ -60,7 +93,8 @@ __device__ __forceinline__ bool delta_stage(uint8_t* sm, const uint8_t* ext, uin
 // over the phases in g.phase_mask (if the target is given), accumulated in
 // vector order.
 __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const DeltaArgs& g, int a, int b, int v0,
-                                                    int v1, int warp, int lane, int32_t* dcounts_k) {
+                                                    int v1, int warp, int lane, int32_t* dcounts_k,
+                                                    const DeltaTerms& dt) {
   float acc = 0.0f;
   const float invN = 1.0f / ((float)g.H * (float)g.W);
   const int pa = delta_ext_pos(a, g.W, g.We, g.rx, g.ry);
@@ -121,13 +155,14 @@ __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const Del
       }
       if (g.target && (d0 | d1)) {
         // (d - D/N)^2 - d^2 = (D/N) * (D/N - 2 d), with d = target - count/N
+        const int iv = v - dt.vbase;
         if (d0 && (g.phase_mask & 1)) {
-          const float dd = g.target[g.base + v] - (float)g.counts[g.base + v] * invN;
+          const float dd = dt.t[0][iv] - (float)dt.c[0][iv] * invN;
           const float x = (float)d0 * invN;
           acc += x * (x - 2.0f * dd);
         }
         if (d1 && (g.phase_mask & 2)) {
-          const float dd = g.target[g.n_full + g.base + v] - (float)g.counts[g.n_full + g.base + v] * invN;
+          const float dd = dt.t[1][iv] - (float)dt.c[1][iv] * invN;
           const float x = (float)d1 * invN;
           acc += x * (x - 2.0f * dd);
         }

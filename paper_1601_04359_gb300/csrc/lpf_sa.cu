@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_batch_kernel(
         int32_t* dk = dcounts + (int64_t)k * 2 * g.n_canon;
         float acc = 0.0f;
         if (a == b) delta_zero_vectors(g, v0, v1, dk);
-        else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk);
+        else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk, delta_terms_global(g));
         if (lane == 0) warp_acc[warp] = acc;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
     SaDev* __restrict__ st, uint8_t* __restrict__ cell, uint8_t* __restrict__ ext, DeltaArgs g,
     int32_t* __restrict__ pairs2, float* __restrict__ u2, int32_t* __restrict__ dcounts, float* __restrict__ partial2,
     unsigned long long* __restrict__ counts, int* __restrict__ status, unsigned int* __restrict__ bar, int n_batches,
-    int k_max) {
+    int k_max, unsigned int bar_extra) {
   extern __shared__ __align__(16) uint8_t sm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ SaDev s_state;
@@ -268,12 +268,31 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
   __shared__ int s_a, s_b;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ch = blockIdx.x;
-  const int v0 = g.chunk[ch], v1 = g.chunk[ch + 1];
+  const int v0 = g.chunk[ch], v1 = g.chunk[ch + 1], nv = v1 - v0;
   sa_state_load(&s_state, st);
   if (!delta_stage(sm, ext, g.ext_bytes, &mbar)) {
     if (threadIdx.x == 0) atomicOr(status, 1);
     (void)mbar_wait(&mbar, 0);
   }
+  // this chunk's targets and counts stay in shared memory after the cell
+  // for the whole launch; the counts are kept exact there and written through
+  const int mv = g.max_chunk_vecs;
+  long long* s_cnt = reinterpret_cast<long long*>(sm + g.ext_bytes);  // [2][mv]
+  float* s_tgt = reinterpret_cast<float*>(s_cnt + 2 * mv);            // [2][mv]
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      s_tgt[p * mv + i] = g.target[p * g.n_full + g.base + v0 + i];
+      s_cnt[p * mv + i] = (long long)counts[p * g.n_full + g.base + v0 + i];
+    }
+  }
+  __syncthreads();
+  DeltaTerms dt;
+  dt.t[0] = s_tgt;
+  dt.t[1] = s_tgt + mv;
+  dt.c[0] = s_cnt;
+  dt.c[1] = s_cnt + mv;
+  dt.vbase = v0;
   for (int bi = 0; bi < n_batches && !s_state.done; ++bi) {
     const int Keff = s_state.k_eff;
     const unsigned long long n0 = (unsigned long long)s_state.n_eval;
@@ -297,7 +316,7 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
       int32_t* dk = dcounts + (int64_t)k * 2 * g.n_canon;
       float acc = 0.0f;
       if (a == b) delta_zero_vectors(g, v0, v1, dk);
-      else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk);
+      else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk, dt);
       if (lane == 0) warp_acc[warp] = acc;
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -308,7 +327,8 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
       }
       __syncthreads();
     }
-    if (!sa_grid_barrier(bar, (unsigned int)(bi + 1) * gridDim.x, status)) break;
+    // (bar_extra > 0 only in lpf_sa_selftest_timeout: a target no block reaches)
+    if (!sa_grid_barrier(bar, (unsigned int)(bi + 1) * gridDim.x + bar_extra, status)) break;
 
     const long long left = s_state.n_step - s_state.n_eval;
     const int Kv = (int)min((long long)Keff, max(0LL, left));
@@ -319,13 +339,17 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
       if (a != b) {
         // this block's vectors: apply the accepted candidate's changes
         const int32_t* dk = dcounts + (int64_t)kstar * 2 * g.n_canon;
-        for (int v = v0 + (int)threadIdx.x; v < v1; v += blockDim.x) {
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+          const int v = v0 + i;
+          const int d0 = dk[v], d1 = dk[(int64_t)g.n_canon + v];
 #pragma unroll
           for (int p = 0; p < 2; ++p) {
-            const long long d = dk[(int64_t)p * g.n_canon + v];
+            const int d = p ? d1 : d0;
             if (d == 0) continue;
-            counts[p * g.n_full + g.base + v] += (unsigned long long)d;
-            if (v > 0) counts[p * g.n_full + (g.n_full - 1 - (g.base + v))] += (unsigned long long)d;
+            const long long c = s_cnt[p * mv + i] + d;
+            s_cnt[p * mv + i] = c;
+            counts[p * g.n_full + g.base + v] = (unsigned long long)c;
+            if (v > 0) counts[p * g.n_full + (g.n_full - 1 - (g.base + v))] = (unsigned long long)c;
           }
         }
         if (threadIdx.x == 0) {
@@ -393,17 +417,23 @@ const void* sa_persistent_kernel_entry() { return reinterpret_cast<const void*>(
 
 constexpr int kPersistentBatches = 4096;  // batches per persistent launch (bounds one launch's duration)
 
+// Dynamic shared memory of the persistent kernel: the extended cell, then
+// counts (int64) and targets (float) of the largest chunk, both phases.
+static size_t persistent_smem(const DeltaArgs& g) {
+  return (size_t)g.ext_bytes + (size_t)g.max_chunk_vecs * 2 * (sizeof(long long) + sizeof(float));
+}
+
 // Launch the persistent annealer for nb batches (cooperative launch: every
 // block is resident, which its grid barrier relies on).
-static int launch_persistent(lpf_sa* sa, int nb, cudaStream_t s) {
+static int launch_persistent(lpf_sa* sa, int nb, cudaStream_t s, unsigned int bar_extra = 0) {
   cudaError_t e = cudaMemsetAsync(sa->d_bar, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return set_cuda_error(e);
   unsigned long long* counts = reinterpret_cast<unsigned long long*>(sa->counts);
   int k_max = sa->prm.k_max;
   void* args[] = {&sa->d_st, &sa->cell, &sa->d_ext, &sa->g, &sa->d_pairs, &sa->d_u, &sa->d_dc, &sa->d_partial,
-                  &counts, &sa->d_status, &sa->d_bar, &nb, &k_max};
+                  &counts, &sa->d_status, &sa->d_bar, &nb, &k_max, &bar_extra};
   e = cudaLaunchCooperativeKernel(sa_persistent_kernel_entry(), dim3(sa->g.n_chunks), dim3(kDeltaThreads), args,
-                                  sa->g.ext_bytes, s);
+                                  persistent_smem(sa->g), s);
   return set_cuda_error(e);
 }
 
@@ -568,11 +598,12 @@ int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, con
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
+    const size_t smem = lpf::persistent_smem(sa->g);
+    if (e == cudaSuccess && (int64_t)smem <= lpf::delta_max_smem())
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lpf::sa_persistent_kernel_entry(), lpf::kDeltaThreads,
-                                                        sa->g.ext_bytes);
+                                                        smem);
     if (e != cudaSuccess) { lpf_sa_free(sa); return lpf::set_cuda_error(e); }
-    sa->persistent = (coop && sa->g.n_chunks <= occ * sms) ? 1 : 0;
+    sa->persistent = (coop && occ > 0 && sa->g.n_chunks <= occ * sms) ? 1 : 0;
   }
   rc = lpf::sa_start(sa, s);
   if (rc) { lpf_sa_free(sa); return rc; }
@@ -624,6 +655,32 @@ int lpf_sa_run(lpf_sa* sa, int32_t n_batches, lpf_stream_t stream) {
   if (left > 0) lpf::enqueue_refresh(sa, s);
   for (; left > 0; --left) lpf::enqueue_batch(sa, s);
   return lpf::set_cuda_error(cudaGetLastError());
+}
+
+int lpf_sa_selftest_timeout(lpf_sa* sa, lpf_stream_t stream) {
+  if (!sa) return LPF_EINVAL;
+  if (!sa->persistent) return LPF_EUNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  lpf::SaDev before, after;
+  int rc = lpf::sa_device_state(sa, before, s);
+  if (rc) return rc;
+  int status = 0;
+  cudaError_t e = cudaMemcpy(&status, sa->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return lpf::set_cuda_error(e);
+  if (status) return LPF_ETIMEOUT;  // an earlier wait already failed
+  rc = lpf::launch_persistent(sa, 1, s, 1u);  // one arrival short of every target
+  if (rc) return rc;
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(&status, sa->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return lpf::set_cuda_error(e);
+  rc = lpf::sa_device_state(sa, after, s);
+  if (rc) return rc;
+  e = cudaMemsetAsync(sa->d_status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return lpf::set_cuda_error(e);
+  const bool unchanged = after.n_eval == before.n_eval && after.n_accept == before.n_accept &&
+                         after.n_batches == before.n_batches && after.T == before.T && after.e == before.e;
+  return ((status & 4) && unchanged) ? LPF_OK : LPF_ECUDA;
 }
 
 int lpf_sa_set_proposer(lpf_sa* sa, lpf_cnn* cnn, float epsilon, float tau, int32_t refresh) {

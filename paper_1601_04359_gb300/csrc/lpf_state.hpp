@@ -50,6 +50,7 @@ struct Baked {
 struct DeltaTables {
   int We = -1;
   int want = -1;               // vector chunks asked for (one wave of blocks)
+  int max_chunk_vecs = 0;      // vectors in the largest chunk
   int32_t* d_doff = nullptr;   // per segment pixel: sy*We + sx
   int32_t* d_dptr = nullptr;   // CSR pointers [n_canon + 1]
   int32_t* d_chunk = nullptr;  // vector chunk bounds [n_chunks + 1]
