@@ -97,15 +97,17 @@ def propose(cell: np.ndarray, n_eval: int, k: int, seed: int):
 
 def anneal(cell: np.ndarray, target: np.ndarray, counts: np.ndarray, rx: int, ry: int, n_step: int,
            c_max: int, s_max: int, t_max: float, t_min_ratio: float, seed: int, phases: int = 3,
-           objective: str = "l2"):
+           objective: str = "l2", sel=None):
     """Sequential Alg. 3 with the readings above; Delta e from the oracle's
     recount (double precision, rounded to float32 as the error change of a
     candidate).  objective "l2": Eq. (LSE) on the lineal path counts of the
     phases in the bit mask `phases` (counts int64 [2][n_full], target
-    [2][n_full]); "s2": Eq. (LSE) on the phase-1 two-point probability over
-    all W*H offsets of the cell (target [H*W]; counts and rx, ry unused).
-    Returns (final cell, n_accept, final T)."""
-    from . import delta_objective, s2_delta_objective
+    [2][n_full]); with `sel` (uint8 [H][W], the N sampled translations) the
+    counts are those of the Monte-Carlo variant (Sec. 3 opening) and the
+    descriptor is count / N; "s2": Eq. (LSE) on the phase-1 two-point
+    probability over all W*H offsets of the cell (target [H*W]; counts and
+    rx, ry unused).  Returns (final cell, n_accept, final T)."""
+    from . import delta_objective, lpf_full_selected, s2_delta_objective
     cell = np.array(cell, np.uint8)
     counts = np.array(counts, np.int64)
     H, W = cell.shape
@@ -119,6 +121,13 @@ def anneal(cell: np.ndarray, target: np.ndarray, counts: np.ndarray, rx: int, ry
         pairs, u = propose(cell, n, 1, seed)
         if objective == "s2":
             de = np.float32(s2_delta_objective(cell, target, pairs)[0])
+        elif sel is not None:
+            a, b = pairs[0]
+            after = cell.copy().reshape(-1)
+            after[a], after[b] = after[b], after[a]
+            d = (lpf_full_selected(after.reshape(H, W), rx, ry, sel) - counts)[:, base:][None]
+            # normalisation by N: the oracle's objective divides by H*W, so pass N x 1
+            de = np.float32(delta_objective(target, counts, d, rx, ry, int(np.count_nonzero(sel)), 1, phases)[0])
         else:
             d = delta_swap(cell, rx, ry, pairs)
             de = np.float32(delta_objective(target, counts, d, rx, ry, H, W, phases)[0])

@@ -88,3 +88,19 @@ def test_anneal_reduces_error():
     e1 = oracle.objective(target, oracle.lpf_full(out, rx, ry), rx, ry, 24, 24)
     assert n_acc > 0 and e1 < e0
     assert out.sum() == cell.sum()  # exchanges keep the volume fraction
+
+
+def test_monte_carlo_annealing_with_every_translation_is_the_exact_one():
+    # Sec. 3 opening: with N = W*H sampled positions the Monte-Carlo descriptor
+    # is the exact one, so the annealing runs coincide step for step.
+    H = W = 10
+    rx = ry = 3
+    cell = synth.exact_fraction_shuffle(H, W, 35, seed=2)
+    orig = synth.clustered_disks(20, 20, 0.35, seed=3)
+    target = (oracle.lpf_full(orig, rx, ry) / float(orig.size)).astype(np.float32)
+    counts = oracle.lpf_full(cell, rx, ry)
+    kw = dict(n_step=120, c_max=20, s_max=4, t_max=1e-3, t_min_ratio=0.01, seed=5)
+    a = sa.anneal(cell, target, counts, rx, ry, **kw)
+    b = sa.anneal(cell, target, counts, rx, ry, sel=np.ones((H, W), np.uint8), **kw)
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[1] == b[1] and a[1] > 0
