@@ -237,6 +237,30 @@ int lpf_delta_swap(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *path
                    lpf_stream_t stream);
 
 /*
+ * Sum of the lpf_full counts of n_img images of equal size H x W stored one
+ * after another in imgs_dev (uint8 [n_img][H][W]), e.g. the parallel cuts of
+ * a volume: the ensemble average over cuts of Sec. 6.3 is counts / (n_img *
+ * H * W).  counts_dev: int64 [2][n_vec_full] as in lpf_full.  The images are
+ * evaluated one after another on `stream` (each one pack and walk launch).
+ * Errors: as lpf_full; n_img < 1 is LPF_EINVAL.
+ */
+int lpf_full_ensemble(const uint8_t *imgs_dev, int32_t n_img, int32_t H, int32_t W, lpf_paths *paths,
+                      int64_t *counts_dev, lpf_stream_t stream);
+
+/*
+ * lpf_delta_swap for the Monte-Carlo lineal path function (Sec. 3 opening):
+ * only translations x with sel_dev[x] != 0 (H*W uint8, the sampled
+ * positions, N = their number) are counted, as in lpf_full_mc, and the
+ * descriptor is count / N.  counts_dev are then the cell's lpf_full_mc counts
+ * for the same selection; dcounts_dev and de_dev as in lpf_delta_swap.
+ * Copies the selection to the host to count it (synchronises); N = 0 is
+ * LPF_EINVAL.  Errors: as lpf_delta_swap.
+ */
+int lpf_delta_swap_mc(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths, const uint8_t *sel_dev,
+                      const int32_t *pairs_dev, int32_t K, int32_t *dcounts_dev, const float *target_dev,
+                      const int64_t *counts_dev, float *de_dev, lpf_stream_t stream);
+
+/*
  * Two-point probability function of phase `phase` (Sec. 2.1), the baseline
  * descriptor: s2_dev[y][x] = 1/(W*H) * IDFT(DFT(chi) * conj(DFT(chi)))(x, y),
  * chi the indicator of the phase, which equals the direct periodic sum of
@@ -356,6 +380,19 @@ typedef struct {
 int lpf_sa_create(uint8_t *cell_dev, int32_t H, int32_t W, lpf_paths *paths,
                   const float *target_dev, int64_t *counts_dev, const lpf_sa_params *params,
                   lpf_stream_t stream, lpf_sa **out);
+
+/*
+ * lpf_sa_create driven by the Monte-Carlo lineal path function (the
+ * reconstructions of Fig. ComMicRec): the cell's descriptor counts only the
+ * translations sampled in sel_dev (H*W uint8, fixed for the run, N of them)
+ * and is count / N; target_dev is the original's (Monte-Carlo) descriptor,
+ * counts_dev receives the cell's lpf_full_mc counts and is kept current.
+ * Everything else as lpf_sa_create.  Errors: as lpf_sa_create; N = 0 is
+ * LPF_EINVAL.
+ */
+int lpf_sa_create_mc(uint8_t *cell_dev, int32_t H, int32_t W, lpf_paths *paths, const uint8_t *sel_dev,
+                     const float *target_dev, int64_t *counts_dev, const lpf_sa_params *params,
+                     lpf_stream_t stream, lpf_sa **out);
 
 /*
  * Enqueue n_batches annealing batches on `stream` without synchronising.

@@ -20,7 +20,7 @@ __all__ = [
     "lpf_paths_stats", "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer",
     "lpf_delta_swap", "lpf_full_mc", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror",
     "SaParams", "SaStats", "Annealer", "lpf_sa_create", "lpf_sa_run", "lpf_sa_read", "lpf_sa_recompute_error",
-    "lpf_sa_propose", "lpf_sa_selftest_timeout", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
+    "lpf_sa_propose", "lpf_sa_selftest_timeout", "lpf_delta_swap_mc", "lpf_sa_create_mc", "lpf_full_ensemble", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
     "lpf_cnn_forward", "lpf_cnn_gradients", "lpf_cnn_train_step", "lpf_sa_set_proposer", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune", "lpf_batch_status",
 ]
 
@@ -85,6 +85,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_full_mc": (ctypes.c_int, [p, i32, i32, p, p, p, p]),
         "s2_fft": (ctypes.c_int, [p, i32, i32, i32, p, p]),
         "s2_counts": (ctypes.c_int, [p, i32, i32, p, p]),
+        "lpf_full_ensemble": (ctypes.c_int, [p, i32, i32, i32, p, p, p]),
+        "lpf_delta_swap_mc": (ctypes.c_int, [p, i32, i32, p, p, p, i32, p, p, p, p, p]),
+        "lpf_sa_create_mc": (ctypes.c_int, [p, i32, i32, p, p, p, p, ctypes.POINTER(SaParams), p, ctypes.POINTER(p)]),
         "lpf_sa_selftest_timeout": (ctypes.c_int, [p, p]),
         "s2_delta_swap": (ctypes.c_int, [p, i32, i32, p, i32, p, p, p, p, p]),
         "s2_sa_create": (ctypes.c_int, [p, i32, i32, p, p, ctypes.POINTER(SaParams), p, ctypes.POINTER(p)]),
@@ -230,6 +233,17 @@ def lpf_set_launch_shape(paths: Paths, H: int, W: int, T: int, BB: int):
     _check(load().lpf_set_launch_shape(paths.handle, int(H), int(W), int(T), int(BB)), "lpf_set_launch_shape")
 
 
+def lpf_full_ensemble(imgs, paths: Paths, counts=None, stream=None):
+    """Summed counts of the images imgs (uint8 CUDA [n][H][W]); divide by n*H*W for the ensemble average."""
+    import torch
+    n, H, W = imgs.shape
+    if counts is None:
+        counts = torch.empty((2, paths.n_full), dtype=torch.int64, device=imgs.device)
+    _check(load().lpf_full_ensemble(_dev_ptr(imgs, "uint8", "imgs"), n, H, W, paths.handle,
+                                    _dev_ptr(counts, "int64", "counts"), _stream_ptr(stream)), "lpf_full_ensemble")
+    return counts
+
+
 def lpf_full_standard(img, paths: Paths, counts=None, stream=None):
     import torch
     H, W = img.shape
@@ -259,6 +273,25 @@ def lpf_delta_swap(img, paths: Paths, pairs, dcounts=None, target=None, counts=N
         _dev_ptr(counts, "int64", "counts") if counts is not None else None,
         _dev_ptr(de, "float32", "de") if de is not None else None,
         _stream_ptr(stream)), "lpf_delta_swap")
+    return dcounts, de
+
+
+def lpf_delta_swap_mc(img, paths: Paths, sel, pairs, target=None, counts=None, want_dcounts: bool = True,
+                      want_de: bool = False, stream=None):
+    """lpf_delta_swap restricted to the translations sampled in sel (uint8 CUDA [H][W])."""
+    import torch
+    H, W = img.shape
+    K = int(pairs.shape[0])
+    dcounts = torch.empty((K, 2, paths.n_canon), dtype=torch.int32, device=img.device) if want_dcounts else None
+    de = torch.empty(K, dtype=torch.float32, device=img.device) if want_de else None
+    _check(load().lpf_delta_swap_mc(
+        _dev_ptr(img, "uint8", "img"), H, W, paths.handle, _dev_ptr(sel, "uint8", "sel"),
+        _dev_ptr(pairs, "int32", "pairs"), K,
+        _dev_ptr(dcounts, "int32", "dcounts") if dcounts is not None else None,
+        _dev_ptr(target, "float32", "target") if target is not None else None,
+        _dev_ptr(counts, "int64", "counts") if counts is not None else None,
+        _dev_ptr(de, "float32", "de") if de is not None else None,
+        _stream_ptr(stream)), "lpf_delta_swap_mc")
     return dcounts, de
 
 
@@ -402,6 +435,23 @@ def s2_fft(img, phase: int, out=None, stream=None):
     _check(load().s2_fft(_dev_ptr(img, "uint8", "img"), H, W, int(phase), _dev_ptr(out, "float32", "s2"),
                          _stream_ptr(stream)), "s2_fft")
     return out
+
+
+def lpf_sa_create_mc(cell, paths: Paths, sel, target, counts=None, n_step=1_000_000, c_max=None, s_max=None,
+                     t_max=0.0, t_min_ratio=0.01, k_max=4096, k_min=1, seed=1, phases=3, stream=None) -> Annealer:
+    """Annealing run on the Monte-Carlo lineal path function of the translations sampled in sel."""
+    import torch
+    H, W = cell.shape
+    if counts is None:
+        counts = torch.empty((2, paths.n_full), dtype=torch.int64, device=cell.device)
+    prm = _sa_params(n_step, c_max, s_max, t_max, t_min_ratio, k_max, k_min, seed, phases)
+    h = ctypes.c_void_p()
+    _check(load().lpf_sa_create_mc(_dev_ptr(cell, "uint8", "cell"), H, W, paths.handle, _dev_ptr(sel, "uint8", "sel"),
+                                   _dev_ptr(target, "float32", "target"), _dev_ptr(counts, "int64", "counts"),
+                                   ctypes.byref(prm), _stream_ptr(stream), ctypes.byref(h)), "lpf_sa_create_mc")
+    ann = Annealer(h.value, cell, paths, target, counts)
+    ann.sel = sel
+    return ann
 
 
 def s2_counts(img, out=None, stream=None):

@@ -17,7 +17,9 @@
 // and for the anchor b (walks that also contain a are counted from a):
 //   q = 1 -> dcount_1 += 1,  q = 0 -> dcount_0 -= 1.
 // Segments containing both a and b change in neither phase and are ended by
-// the marker.  The zero vector never changes.
+// the marker.  The zero vector (the anchor alone) loses the anchor's old
+// phase and gains its new one: over all translations the two exchanged
+// pixels cancel, over a sample of translations they need not.
 //
 // Work split: blocks = (vector chunk) x (candidate stride); each block stages
 // the extended cell once (one bulk copy of a copy built per call in global
@@ -178,6 +180,8 @@ int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g) {
   g.counts = nullptr;
   g.phase_mask = 3;
   g.max_chunk_vecs = p->delta.max_chunk_vecs;
+  g.sel_ext = nullptr;
+  g.inv_norm = 1.0f / ((float)H * (float)W);
   return LPF_OK;
 }
 
@@ -260,7 +264,7 @@ int delta_stride(int n_chunks, int K) {
 
 int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, const int32_t* pairs_dev,
                    int32_t K, int32_t* dcounts_dev, const float* target_dev, const int64_t* counts_dev, float* de_dev,
-                   int phase_mask, cudaStream_t s) {
+                   int phase_mask, cudaStream_t s, const uint8_t* sel_ext, float inv_norm) {
   if (!paths || !img_dev || K < 0) return LPF_EINVAL;
   if (K == 0) return LPF_OK;
   if (!pairs_dev) return LPF_EINVAL;
@@ -276,6 +280,8 @@ int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* path
   g.target = de_dev ? target_dev : nullptr;
   g.counts = de_dev ? counts_dev : nullptr;
   g.phase_mask = phase_mask;
+  g.sel_ext = sel_ext;
+  if (inv_norm > 0.0f) g.inv_norm = inv_norm;
   {
     const int blocks = (int)std::min<int64_t>((g.ext_bytes + 255) / 256, 4096);
     build_ext_kernel<<<blocks, 256, 0, s>>>(img_dev, H, W, g.rx, g.ry, g.We, g.He, g.ext_bytes, paths->d_ext);
@@ -298,5 +304,59 @@ extern "C" int lpf_delta_swap(const uint8_t* img_dev, int32_t H, int32_t W, lpf_
                               const int32_t* pairs_dev, int32_t K, int32_t* dcounts_dev, const float* target_dev,
                               const int64_t* counts_dev, float* de_dev, lpf_stream_t stream) {
   return lpf::delta_swap_run(img_dev, H, W, paths, pairs_dev, K, dcounts_dev, target_dev, counts_dev, de_dev, 3,
-                             (cudaStream_t)stream);
+                             (cudaStream_t)stream, nullptr, 0.0f);
+}
+
+namespace lpf {
+
+// Number of selected translations (host copy of the mask; synchronises).
+int count_selected(const uint8_t* sel_dev, int H, int W, cudaStream_t s, int64_t* n) {
+  std::vector<uint8_t> h((size_t)H * W);
+  cudaError_t e = cudaMemcpyAsync(h.data(), sel_dev, h.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  int64_t c = 0;
+  for (uint8_t v : h) c += v != 0;
+  *n = c;
+  return LPF_OK;
+}
+
+// The selection mask in the extended-cell layout of the delta kernels, in a
+// new device buffer (stream-ordered).
+int build_sel_ext(const uint8_t* sel_dev, int H, int W, const lpf_paths* paths, cudaStream_t s, uint8_t** out) {
+  DeltaArgs g;
+  g.H = H;
+  g.W = W;
+  g.rx = paths->host.rx;
+  g.ry = paths->host.ry;
+  g.We = delta_row_stride(W, g.rx);
+  g.He = H + 2 * g.ry;
+  g.ext_bytes = (uint32_t)((((size_t)g.We * g.He) + 15) & ~size_t(15));
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(out), g.ext_bytes, s);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  const int blocks = (int)std::min<int64_t>((g.ext_bytes + 255) / 256, 4096);
+  build_ext_kernel<<<blocks, 256, 0, s>>>(sel_dev, H, W, g.rx, g.ry, g.We, g.He, g.ext_bytes, *out);
+  return set_cuda_error(cudaGetLastError());
+}
+
+}  // namespace lpf
+
+extern "C" int lpf_delta_swap_mc(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths,
+                                 const uint8_t* sel_dev, const int32_t* pairs_dev, int32_t K, int32_t* dcounts_dev,
+                                 const float* target_dev, const int64_t* counts_dev, float* de_dev,
+                                 lpf_stream_t stream) {
+  if (!paths || !img_dev || !sel_dev || K < 0 || H < 1 || W < 1) return LPF_EINVAL;
+  if (K == 0) return LPF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t n = 0;
+  int rc = lpf::count_selected(sel_dev, H, W, s, &n);
+  if (rc) return rc;
+  if (n == 0) return LPF_EINVAL;
+  uint8_t* sel_ext = nullptr;
+  rc = lpf::build_sel_ext(sel_dev, H, W, paths, s, &sel_ext);
+  if (!rc)
+    rc = lpf::delta_swap_run(img_dev, H, W, paths, pairs_dev, K, dcounts_dev, target_dev, counts_dev, de_dev, 3, s,
+                             sel_ext, 1.0f / (float)n);
+  if (sel_ext) cudaFreeAsync(sel_ext, s);
+  return rc;
 }

@@ -30,6 +30,8 @@ struct DeltaArgs {
   const int64_t* counts;        // [2][n_full] or null
   int phase_mask;               // phases in the error: bit p = phase p (3 = both)
   int max_chunk_vecs;           // vectors in the largest chunk
+  const uint8_t* sel_ext;       // selected start translations, extended layout (null: all)
+  float inv_norm;               // descriptor = count * inv_norm (1/(H W), or 1/N selected)
 };
 
 // Where a walk finds the target and the current count of vector v for the
@@ -96,14 +98,14 @@ __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const Del
                                                     int v1, int warp, int lane, int32_t* dcounts_k,
                                                     const DeltaTerms& dt) {
   float acc = 0.0f;
-  const float invN = 1.0f / ((float)g.H * (float)g.W);
+  const float invN = g.inv_norm;
   const int pa = delta_ext_pos(a, g.W, g.We, g.rx, g.ry);
   const int pb = delta_ext_pos(b, g.W, g.We, g.rx, g.ry);
   for (int v = v0 + warp; v < v1; v += kDeltaWarps) {
     const int o0 = __ldg(g.dptr + v);
     const int L1 = __ldg(g.dptr + v + 1) - o0;  // pixels of the segment
     int d0 = 0, d1 = 0;
-    if (L1 > 1) {
+    {
       const int tasks = 2 * L1;
       for (int t0 = 0; t0 < tasks; t0 += 32) {
         const int t = t0 + lane;
@@ -111,6 +113,7 @@ __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const Del
         const int i = is_a ? t : t - L1;
         bool alive = t < tasks;
         const int pos = (is_a ? pa : pb) - (alive ? __ldg(g.doff + o0 + i) : 0);
+        if (alive && g.sel_ext && !__ldg(g.sel_ext + pos)) alive = false;  // start not among the sampled
         int q = -1;
         // kWalkUnroll pixels per round: their offsets (the same in every
         // lane) and then their bytes are loaded independently, so a round
@@ -138,8 +141,10 @@ __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const Del
           }
         }
         if (alive) {
-          if (is_a) { if (q == 1) d1 -= 1; else d0 += 1; }
-          else      { if (q == 1) d1 += 1; else d0 -= 1; }
+          // q < 0: the segment is the anchor alone (zero vector), uniform in
+          // its phase before and in the other one after
+          if (is_a) { if (q != 0) d1 -= 1; if (q != 1) d0 += 1; }
+          else      { if (q != 0) d1 += 1; if (q != 1) d0 -= 1; }
         }
       }
 #pragma unroll

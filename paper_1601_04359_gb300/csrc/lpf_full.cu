@@ -384,9 +384,10 @@ static void launch_walk(const Geometry& g, const Baked& b, lpf_paths* p, unsigne
       p->host.n_full, p->host.base, p->d_status, p->d_sel_active);
 }
 
-// Enqueue one full evaluation with launch shape (T, BB) (<= 0: tuned or default).
+// Enqueue one full evaluation with launch shape (T, BB) (<= 0: tuned or
+// default); `accumulate` adds to the counts instead of replacing them.
 static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* counts, cudaStream_t s,
-                    bool standard, int T = 0, int BB = 0, const uint8_t* sel = nullptr) {
+                    bool standard, int T = 0, int BB = 0, const uint8_t* sel = nullptr, bool accumulate = false) {
   if (!p || !img || !counts) return LPF_EINVAL;
   if (H < 1 || W < 1 || H > 8192 || W > 8192) return LPF_EINVAL;
   if (p->host.rx >= W || p->host.ry >= H) return LPF_EINVAL;
@@ -424,7 +425,7 @@ static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* cou
   (void)cudaGetLastError();  // clear a stale error left by earlier, unrelated calls
 
   const int64_t n_full = p->host.n_full, base = p->host.base;
-  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * n_full, s);
+  cudaError_t e = accumulate ? cudaSuccess : cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * n_full, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status + 1, 0, sizeof(int), s);  // work counter
   if (e != cudaSuccess) return set_cuda_error(e);
   {
@@ -727,6 +728,19 @@ int lpf_full_mc(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, 
                 int64_t* counts_dev, lpf_stream_t stream) {
   if (!sel_dev) return LPF_EINVAL;
   return lpf::run_full(img_dev, H, W, paths, counts_dev, (cudaStream_t)stream, false, 0, 0, sel_dev);
+}
+
+int lpf_full_ensemble(const uint8_t* imgs_dev, int32_t n_img, int32_t H, int32_t W, lpf_paths* paths,
+                      int64_t* counts_dev, lpf_stream_t stream) {
+  if (!imgs_dev || n_img < 1) return LPF_EINVAL;
+  for (int32_t i = 0; i < n_img; ++i) {
+    // the non-canonical half is rewritten from the accumulated canonical
+    // half after every image, so the sum stays exact
+    const int rc = lpf::run_full(imgs_dev + (size_t)i * H * W, H, W, paths, counts_dev, (cudaStream_t)stream, false,
+                                 0, 0, nullptr, i > 0);
+    if (rc) return rc;
+  }
+  return LPF_OK;
 }
 
 int lpf_full_standard(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, int64_t* counts_dev,

@@ -458,7 +458,8 @@ static void enqueue_batch(lpf_sa* sa, cudaStream_t s) {
 
 void sa_enqueue_error(lpf_sa* sa, cudaStream_t s) {
   sa_error_kernel<<<1, 256, 0, s>>>(sa->target, sa->counts, sa->err_n_full, sa->err_base, sa->phase_mask,
-                                    1.0 / ((double)sa->H * (double)sa->W), sa->d_e);
+                                    sa->inv_norm > 0.0 ? sa->inv_norm : 1.0 / ((double)sa->H * (double)sa->W),
+                                    sa->d_e);
 }
 
 static int sa_device_state(lpf_sa* sa, SaDev& st, cudaStream_t s) {
@@ -535,7 +536,7 @@ int sa_start(lpf_sa* sa, cudaStream_t s) {
       rc = delta_prepare(sa->paths, sa->H, sa->W, K);
       if (!rc)
         rc = delta_swap_run(sa->cell, sa->H, sa->W, sa->paths, sa->d_pairs, K, nullptr, sa->target, sa->counts,
-                            sa->d_de, sa->phase_mask, s);
+                            sa->d_de, sa->phase_mask, s, sa->d_sel_ext, (float)sa->inv_norm);
     }
     std::vector<float> de(K);
     if (!rc) {
@@ -560,20 +561,39 @@ int sa_start(lpf_sa* sa, cudaStream_t s) {
 
 extern "C" {
 
-int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, const float* target_dev,
-                  int64_t* counts_dev, const lpf_sa_params* prm, lpf_stream_t stream, lpf_sa** out) {
+}  // extern "C"
+
+namespace lpf {
+
+// Lineal-path annealer on all translations (sel_dev null) or on the sampled
+// ones (Monte-Carlo variant).
+static int sa_create_lineal(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, const float* target_dev,
+                            int64_t* counts_dev, const uint8_t* sel_dev, const lpf_sa_params* prm,
+                            lpf_stream_t stream, lpf_sa** out) {
   if (!out) return LPF_EINVAL;
   *out = nullptr;
   if (!cell_dev || !paths || !target_dev || !counts_dev || !prm) return LPF_EINVAL;
-  if (int rc = lpf::sa_check_params(prm)) return rc;
+  if (int rc = sa_check_params(prm)) return rc;
   if ((int64_t)H * W > (1 << 24)) return LPF_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = lpf_full(cell_dev, H, W, paths, counts_dev, stream);
+  int64_t n_sel = 0;
+  if (sel_dev) {
+    int rc = count_selected(sel_dev, H, W, s, &n_sel);
+    if (rc) return rc;
+    if (n_sel == 0) return LPF_EINVAL;
+  }
+  int rc = sel_dev ? lpf_full_mc(cell_dev, H, W, paths, sel_dev, counts_dev, stream)
+                   : lpf_full(cell_dev, H, W, paths, counts_dev, stream);
   if (rc) return rc;
-  rc = lpf::delta_prepare(paths, H, W, 1);
+  rc = delta_prepare(paths, H, W, 1);
   if (rc) return rc;
   lpf_sa* sa = new (std::nothrow) lpf_sa();
   if (!sa) return LPF_ENOMEM;
+  if (sel_dev) {
+    rc = build_sel_ext(sel_dev, H, W, paths, s, &sa->d_sel_ext);
+    if (rc) { lpf_sa_free(sa); return rc; }
+    sa->inv_norm = 1.0 / (double)n_sel;
+  }
   sa->paths = paths;
   sa->cell = cell_dev;
   sa->H = H;
@@ -590,6 +610,8 @@ int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, con
   sa->g.target = target_dev;
   sa->g.counts = counts_dev;
   sa->g.phase_mask = sa->phase_mask;
+  sa->g.sel_ext = sa->d_sel_ext;
+  if (sa->inv_norm > 0.0) sa->g.inv_norm = (float)sa->inv_norm;
   sa->grid = dim3(sa->g.n_chunks, lpf::delta_stride(sa->g.n_chunks, prm->k_max));
   {
     // persistent batches when the device launches cooperatively and every
@@ -609,6 +631,22 @@ int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, con
   if (rc) { lpf_sa_free(sa); return rc; }
   *out = sa;
   return LPF_OK;
+}
+
+}  // namespace lpf
+
+extern "C" {
+
+int lpf_sa_create(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, const float* target_dev,
+                  int64_t* counts_dev, const lpf_sa_params* prm, lpf_stream_t stream, lpf_sa** out) {
+  return lpf::sa_create_lineal(cell_dev, H, W, paths, target_dev, counts_dev, nullptr, prm, stream, out);
+}
+
+int lpf_sa_create_mc(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* paths, const uint8_t* sel_dev,
+                     const float* target_dev, int64_t* counts_dev, const lpf_sa_params* prm, lpf_stream_t stream,
+                     lpf_sa** out) {
+  if (!sel_dev) return LPF_EINVAL;
+  return lpf::sa_create_lineal(cell_dev, H, W, paths, target_dev, counts_dev, sel_dev, prm, stream, out);
 }
 
 int lpf_sa_run(lpf_sa* sa, int32_t n_batches, lpf_stream_t stream) {
@@ -775,6 +813,7 @@ void lpf_sa_free(lpf_sa* sa) {
   cudaFree(sa->d_status);
   cudaFree(sa->d_cdf);
   cudaFree(sa->d_bar);
+  cudaFree(sa->d_sel_ext);
   delete sa;
 }
 

@@ -311,6 +311,8 @@ struct lpf_sa {
   int threads = 0;              // batch kernel block size
   int persistent = 0;           // batches run by the cooperative persistent kernel
   unsigned int* d_bar = nullptr;  // its grid-barrier counter
+  uint8_t* d_sel_ext = nullptr; // Monte-Carlo runs: sampled translations, extended layout
+  double inv_norm = 0.0;        // descriptor = count * inv_norm
 };
 
 namespace lpf {

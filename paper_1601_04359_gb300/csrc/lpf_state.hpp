@@ -98,10 +98,15 @@ int delta_max_smem();
 // attribute and occupancy queries.
 const void* sa_batch_kernel_entry();
 const void* sa_persistent_kernel_entry();
-// lpf_delta_swap with the error restricted to the phases in phase_mask.
+// lpf_delta_swap with the error restricted to the phases in phase_mask and,
+// optionally, the walks restricted to selected start translations (sel_ext:
+// extended layout, from build_sel_ext) with descriptor = count * inv_norm
+// (inv_norm <= 0: 1/(H W)).
 int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, const int32_t* pairs_dev,
                    int32_t K, int32_t* dcounts_dev, const float* target_dev, const int64_t* counts_dev, float* de_dev,
-                   int phase_mask, cudaStream_t s);
+                   int phase_mask, cudaStream_t s, const uint8_t* sel_ext, float inv_norm);
+int count_selected(const uint8_t* sel_dev, int H, int W, cudaStream_t s, int64_t* n);
+int build_sel_ext(const uint8_t* sel_dev, int H, int W, const lpf_paths* paths, cudaStream_t s, uint8_t** out);
 // Learned proposer internals used by the annealer.
 void cnn_forward(lpf_cnn* c, const uint8_t* cell, cudaStream_t s);
 const float* cnn_scores(const lpf_cnn* c);   // [H][W][2] of the last forward

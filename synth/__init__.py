@@ -53,6 +53,22 @@ def boolean_disks(H: int, W: int, R: float, n: int, seed: int) -> np.ndarray:
     return disks_fixed(H, W, R, centres)
 
 
+def boolean_spheres(D: int, H: int, W: int, R: float, n: int, seed: int) -> np.ndarray:
+    """Volume [D][H][W] of n balls of radius R, centres uniform on the 3-torus
+    (Boolean model): a stand-in for a CT volume whose parallel cuts are
+    averaged (Sec. 6.3).  Voxel (x, y, z) is phase 1 when its centre lies in a ball."""
+    rng = np.random.default_rng(seed)
+    c = np.stack([rng.uniform(0, W, n), rng.uniform(0, H, n), rng.uniform(0, D, n)], axis=1)
+    z, y, x = np.mgrid[0:D, 0:H, 0:W].astype(np.float64) + 0.5
+    vol = np.zeros((D, H, W), bool)
+    for cx, cy, cz in c:
+        dx = _torus_delta(x - cx, W)
+        dy = _torus_delta(y - cy, H)
+        dz = _torus_delta(z - cz, D)
+        vol |= dx * dx + dy * dy + dz * dz <= R * R
+    return vol.astype(np.uint8)
+
+
 def disks_for_fraction(H: int, W: int, R: float, fraction: float) -> int:
     """Number of Boolean disks whose expected covered fraction is `fraction`."""
     return int(round(-math.log(1.0 - fraction) * W * H / (math.pi * R * R)))
