@@ -57,14 +57,14 @@ def delta_128(repeat):
 
 
 def sa_128(repeat):
-    """Annealing batches on the 128x128 compression workload (one kernel per batch)."""
+    """Annealing batches on the 128x128 compression workload (one persistent launch of the batches)."""
     orig = synth.config3_original()
     p = lpf.lpf_build_paths(64, 64)
     c = lpf.lpf_full(torch.from_numpy(orig).cuda(), p)
     target = (c.double() / float(orig.size)).float()
     cell = torch.from_numpy(synth.exact_fraction_shuffle(128, 128, int(round(orig.mean() * 128 * 128)), seed=5)).cuda()
     ann = lpf.lpf_sa_create(cell, p, target, n_step=10 ** 6, seed=1)
-    lpf.lpf_sa_run(ann, 8 + repeat)  # below the graph size: one launch per batch
+    lpf.lpf_sa_run(ann, 8 + repeat)
     torch.cuda.synchronize()
 
 
