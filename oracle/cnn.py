@@ -6,15 +6,13 @@ learned part; this is the reference the library's CUDA kernels for the
 proposer are checked against.
 
 Network (every layer a 3x3 convolution with circular padding, i.e. the
-periodic medium's wrap, followed by ReLU except the last; layer l's taps are
-DILATIONS[l] pixels apart):
+periodic medium's wrap, followed by ReLU except the last):
   input  [2][H][W]  channel 0 = cell (0/1), channel 1 = interfacial mask (0/1)
   conv 2 -> 32, conv 32 -> 64, conv 64 -> 48, conv 48 -> 32, conv 32 -> 2
   output [2][H][W]  channel 0 = score of phase-0 pixels (the "b" of a swap),
                     channel 1 = score of phase-1 pixels (the "a" of a swap)
 Weights W_l[tap][cin][cout] with tap = (dy+1)*3 + (dx+1), dy, dx in {-1,0,1};
-out[y][x][co] = b[co] + sum_tap sum_ci in[(y+d*dy)%H][(x+d*dx)%W][ci] * W[tap][ci][co],
-d the layer's dilation.
+out[y][x][co] = b[co] + sum_tap sum_ci in[(y+dy)%H][(x+dx)%W][ci] * W[tap][ci][co].
 
 Loss of one snapshot with logged candidates (a_i, b_i, y_i), i = 1..n:
   L = 1/(2n) * sum_i (s1[a_i] + s0[b_i] - y_i)^2.
@@ -24,7 +22,6 @@ from __future__ import annotations
 import numpy as np
 
 CHANNELS = (2, 32, 64, 48, 32, 2)
-DILATIONS = (1, 2, 4, 8, 1)
 
 
 def init_params(seed: int):
@@ -56,11 +53,11 @@ def _shift(x, dy, dx):
     return np.roll(x, shift=(-dy, -dx), axis=(0, 1))
 
 
-def conv(x, w, b, dil: int = 1):
+def conv(x, w, b):
     out = np.zeros(x.shape[:2] + (w.shape[2],))
     for tap in range(9):
         dy, dx = tap // 3 - 1, tap % 3 - 1
-        out += _shift(x, dil * dy, dil * dx) @ w[tap]
+        out += _shift(x, dy, dx) @ w[tap]
     return out + b
 
 
@@ -69,7 +66,7 @@ def forward(params, x):
     acts = [x]
     h = x
     for li, (w, b) in enumerate(params):
-        h = conv(h, w, b, DILATIONS[li])
+        h = conv(h, w, b)
         if li < len(params) - 1:
             h = np.maximum(h, 0.0)
         acts.append(h)
@@ -105,11 +102,10 @@ def backward(params, acts, gout):
         x = acts[li]
         if li < len(params) - 1:
             g = g * (acts[li + 1] > 0)       # ReLU: act > 0 exactly where its input was > 0
-        d = DILATIONS[li]
         dw = np.zeros_like(w)
         for tap in range(9):
             dy, dx = tap // 3 - 1, tap % 3 - 1
-            xs = _shift(x, d * dy, d * dx)
+            xs = _shift(x, dy, dx)
             dw[tap] = xs.reshape(-1, xs.shape[2]).T @ g.reshape(-1, g.shape[2])
         db = g.sum(axis=(0, 1))
         grads[li] = (dw, db)
@@ -117,6 +113,6 @@ def backward(params, acts, gout):
             gx = np.zeros_like(x)
             for tap in range(9):
                 dy, dx = tap // 3 - 1, tap % 3 - 1
-                gx += _shift(g @ w[tap].T, -d * dy, -d * dx)
+                gx += _shift(g @ w[tap].T, -dy, -dx)
             g = gx
     return grads
