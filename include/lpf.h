@@ -417,6 +417,33 @@ int lpf_sa_run(lpf_sa *sa, int32_t n_batches, lpf_stream_t stream);
  * batch kernel gave up (staging copy or grid barrier). */
 int lpf_sa_read(lpf_sa *sa, lpf_sa_stats *out, lpf_stream_t stream);
 
+/*
+ * Checkpoint of an annealing run's progress (no counterpart in the paper,
+ * whose runs "lasted days" without one): with the cell at that moment, it
+ * resumes the run exactly -- create an annealer on the saved cell with the
+ * same parameters and t_max = the saved t_max, then lpf_sa_import_progress.
+ * Candidate draws depend only on the seed, the evaluation counter and the
+ * cell, and counts are exact integers, so the resumed run equals the
+ * uninterrupted one step for step.
+ */
+typedef struct {
+  int64_t n_eval, n_accept, n_batches, n_candidates;
+  int64_t c_stage, s_stage;  /* attempts and acceptances in the current temperature stage */
+  double temperature, error, p_est, t_max;
+  int32_t next_batch, done;
+  uint64_t seed;             /* checked on import */
+  int64_t n_step, c_max, s_max;  /* checked on import */
+  double t_min_ratio;        /* checked on import */
+} lpf_sa_progress;
+
+/* Copy the run's progress to *out (synchronises `stream`). */
+int lpf_sa_export_progress(lpf_sa *sa, lpf_sa_progress *out, lpf_stream_t stream);
+
+/* Set the run's progress from *in (synchronises).  LPF_EINVAL if the run was
+ * created with another seed, n_step, c_max, s_max or t_min_ratio.  A learned
+ * proposer is not part of the progress: set it again after the import. */
+int lpf_sa_import_progress(lpf_sa *sa, const lpf_sa_progress *in, lpf_stream_t stream);
+
 /* Recompute the error from the exact counts in double precision, store it
  * as the run's current error and return it in *e (may be NULL). Synchronises. */
 int lpf_sa_recompute_error(lpf_sa *sa, double *e, lpf_stream_t stream);

@@ -20,7 +20,8 @@ __all__ = [
     "lpf_paths_stats", "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer",
     "lpf_delta_swap", "lpf_full_mc", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror",
     "SaParams", "SaStats", "Annealer", "lpf_sa_create", "lpf_sa_run", "lpf_sa_read", "lpf_sa_recompute_error",
-    "lpf_sa_propose", "lpf_sa_selftest_timeout", "lpf_delta_swap_mc", "lpf_sa_create_mc", "lpf_full_ensemble", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
+    "lpf_sa_propose", "lpf_sa_selftest_timeout", "lpf_delta_swap_mc", "lpf_sa_create_mc", "lpf_full_ensemble", "SaProgress", "lpf_sa_export_progress", "lpf_sa_import_progress",
+    "save_checkpoint", "load_checkpoint", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
     "lpf_cnn_forward", "lpf_cnn_gradients", "lpf_cnn_train_step", "lpf_sa_set_proposer", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune", "lpf_batch_status",
 ]
 
@@ -40,6 +41,19 @@ class SaStats(ctypes.Structure):
     _fields_ = [("n_eval", ctypes.c_int64), ("n_accept", ctypes.c_int64), ("n_batches", ctypes.c_int64),
                 ("n_candidates", ctypes.c_int64), ("temperature", ctypes.c_double), ("error", ctypes.c_double),
                 ("t_max", ctypes.c_double), ("next_batch", ctypes.c_int32), ("done", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SaProgress(ctypes.Structure):
+    """lpf_sa_progress of include/lpf.h."""
+    _fields_ = [("n_eval", ctypes.c_int64), ("n_accept", ctypes.c_int64), ("n_batches", ctypes.c_int64),
+                ("n_candidates", ctypes.c_int64), ("c_stage", ctypes.c_int64), ("s_stage", ctypes.c_int64),
+                ("temperature", ctypes.c_double), ("error", ctypes.c_double), ("p_est", ctypes.c_double),
+                ("t_max", ctypes.c_double), ("next_batch", ctypes.c_int32), ("done", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("n_step", ctypes.c_int64), ("c_max", ctypes.c_int64),
+                ("s_max", ctypes.c_int64), ("t_min_ratio", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -85,6 +99,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_full_mc": (ctypes.c_int, [p, i32, i32, p, p, p, p]),
         "s2_fft": (ctypes.c_int, [p, i32, i32, i32, p, p]),
         "s2_counts": (ctypes.c_int, [p, i32, i32, p, p]),
+        "lpf_sa_export_progress": (ctypes.c_int, [p, ctypes.POINTER(SaProgress), p]),
+        "lpf_sa_import_progress": (ctypes.c_int, [p, ctypes.POINTER(SaProgress), p]),
         "lpf_full_ensemble": (ctypes.c_int, [p, i32, i32, i32, p, p, p]),
         "lpf_delta_swap_mc": (ctypes.c_int, [p, i32, i32, p, p, p, i32, p, p, p, p, p]),
         "lpf_sa_create_mc": (ctypes.c_int, [p, i32, i32, p, p, p, p, ctypes.POINTER(SaParams), p, ctypes.POINTER(p)]),
@@ -409,6 +425,40 @@ def lpf_sa_recompute_error(sa: Annealer, stream=None) -> float:
     e = ctypes.c_double()
     _check(load().lpf_sa_recompute_error(sa.handle, ctypes.byref(e), _stream_ptr(stream)), "lpf_sa_recompute_error")
     return e.value
+
+
+def lpf_sa_export_progress(sa: Annealer, stream=None) -> dict:
+    pr = SaProgress()
+    _check(load().lpf_sa_export_progress(sa.handle, ctypes.byref(pr), _stream_ptr(stream)), "lpf_sa_export_progress")
+    return pr.as_dict()
+
+
+def lpf_sa_import_progress(sa: Annealer, progress: dict, stream=None):
+    pr = SaProgress(**{k: progress[k] for k, _ in SaProgress._fields_})
+    _check(load().lpf_sa_import_progress(sa.handle, ctypes.byref(pr), _stream_ptr(stream)), "lpf_sa_import_progress")
+
+
+def save_checkpoint(sa: Annealer, path: str, stream=None):
+    """Write the run's cell and progress to an .npz file (the counts follow
+    from the cell and are recomputed on resume)."""
+    import numpy as np
+    pr = lpf_sa_export_progress(sa, stream)
+    np.savez(path, cell=sa.cell.cpu().numpy(), **{k: np.asarray(v) for k, v in pr.items()})
+
+
+def load_checkpoint(path: str, paths: Paths, target, k_max=4096, k_min=1, phases=3, stream=None) -> Annealer:
+    """Resume a lineal-path run from save_checkpoint's file: an annealer on
+    the saved cell with the saved parameters and progress."""
+    import numpy as np
+    import torch
+    z = np.load(path)
+    pr = {k: z[k].item() for k, _ in SaProgress._fields_}
+    cell = torch.from_numpy(z["cell"]).to(target.device)
+    ann = lpf_sa_create(cell, paths, target, n_step=pr["n_step"], c_max=pr["c_max"], s_max=pr["s_max"],
+                        t_max=pr["t_max"], t_min_ratio=pr["t_min_ratio"], k_max=k_max, k_min=k_min, seed=pr["seed"],
+                        phases=phases, stream=stream)
+    lpf_sa_import_progress(ann, pr, stream)
+    return ann
 
 
 def lpf_sa_selftest_timeout(sa: Annealer, stream=None) -> int:

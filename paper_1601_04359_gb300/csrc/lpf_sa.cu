@@ -772,6 +772,57 @@ int lpf_sa_read(lpf_sa* sa, lpf_sa_stats* out, lpf_stream_t stream) {
   return status ? LPF_ETIMEOUT : LPF_OK;
 }
 
+int lpf_sa_export_progress(lpf_sa* sa, lpf_sa_progress* out, lpf_stream_t stream) {
+  if (!sa || !out) return LPF_EINVAL;
+  lpf::SaDev st;
+  const int rc = lpf::sa_device_state(sa, st, (cudaStream_t)stream);
+  if (rc) return rc;
+  out->n_eval = st.n_eval;
+  out->n_accept = st.n_accept;
+  out->n_batches = st.n_batches;
+  out->n_candidates = st.n_cand;
+  out->c_stage = st.c_stage;
+  out->s_stage = st.s_stage;
+  out->temperature = st.T;
+  out->error = st.e;
+  out->p_est = st.p_est;
+  out->t_max = sa->prm.t_max;
+  out->next_batch = st.k_eff;
+  out->done = st.done;
+  out->seed = sa->prm.seed;
+  out->n_step = st.n_step;
+  out->c_max = st.c_max;
+  out->s_max = st.s_max;
+  out->t_min_ratio = sa->prm.t_min_ratio;
+  return LPF_OK;
+}
+
+int lpf_sa_import_progress(lpf_sa* sa, const lpf_sa_progress* in, lpf_stream_t stream) {
+  if (!sa || !in) return LPF_EINVAL;
+  if (in->seed != sa->prm.seed || in->n_step != sa->prm.n_step || in->c_max != sa->prm.c_max ||
+      in->s_max != sa->prm.s_max || in->t_min_ratio != sa->prm.t_min_ratio || in->next_batch < sa->prm.k_min ||
+      in->next_batch > sa->prm.k_max)
+    return LPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  lpf::SaDev st;
+  int rc = lpf::sa_device_state(sa, st, s);
+  if (rc) return rc;
+  st.n_eval = in->n_eval;
+  st.n_accept = in->n_accept;
+  st.n_batches = in->n_batches;
+  st.n_cand = in->n_candidates;
+  st.c_stage = in->c_stage;
+  st.s_stage = in->s_stage;
+  st.T = in->temperature;
+  st.e = in->error;
+  st.p_est = in->p_est;
+  st.k_eff = in->next_batch;
+  st.done = in->done;
+  cudaError_t e = cudaMemcpyAsync(sa->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return lpf::set_cuda_error(e);
+}
+
 int lpf_sa_recompute_error(lpf_sa* sa, double* e_out, lpf_stream_t stream) {
   if (!sa) return LPF_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
