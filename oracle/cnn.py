@@ -15,7 +15,9 @@ Weights W_l[tap][cin][cout] with tap = (dy+1)*3 + (dx+1), dy, dx in {-1,0,1};
 out[y][x][co] = b[co] + sum_tap sum_ci in[(y+dy)%H][(x+dx)%W][ci] * W[tap][ci][co].
 
 Loss of one snapshot with logged candidates (a_i, b_i, y_i), i = 1..n:
-  L = 1/(2n) * sum_i (s1[a_i] + s0[b_i] - y_i)^2.
+  L = 1/(2n) * sum_i (s1[a_i] + s0[b_i] - y_i)^2, or (listwise) the
+  cross-entropy -sum_i q_i log p_i with q = softmax(y / beta) and
+  p = softmax(s1[a] + s0[b]) over the snapshot's candidates.
 """
 from __future__ import annotations
 
@@ -90,6 +92,32 @@ def loss_grad_out(out, a_idx, b_idx, y):
     for i in range(n):
         g[a_idx[i] // W, a_idx[i] % W, 1] += r[i] / n
         g[b_idx[i] // W, b_idx[i] % W, 0] += r[i] / n
+    return g
+
+
+def listwise_loss(out, a_idx, b_idx, y, beta: float):
+    """Cross-entropy between the candidates' target distribution
+    q = softmax(y / beta) and the model's p = softmax(s1[a] + s0[b])."""
+    W = out.shape[1]
+    s = out[a_idx // W, a_idx % W, 1] + out[b_idx // W, b_idx % W, 0]
+    q = np.exp(y / beta - np.max(y / beta))
+    q /= q.sum()
+    ls = np.max(s) + np.log(np.sum(np.exp(s - np.max(s))))
+    return float(ls - np.sum(q * s))
+
+
+def listwise_grad_out(out, a_idx, b_idx, y, beta: float):
+    """dL/d out of listwise_loss: p_i - q_i on both pixels of candidate i."""
+    W = out.shape[1]
+    s = out[a_idx // W, a_idx % W, 1] + out[b_idx // W, b_idx % W, 0]
+    p = np.exp(s - np.max(s))
+    p /= p.sum()
+    q = np.exp(y / beta - np.max(y / beta))
+    q /= q.sum()
+    g = np.zeros_like(out)
+    for i in range(len(y)):
+        g[a_idx[i] // W, a_idx[i] % W, 1] += p[i] - q[i]
+        g[b_idx[i] // W, b_idx[i] % W, 0] += p[i] - q[i]
     return g
 
 

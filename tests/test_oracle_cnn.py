@@ -2,6 +2,7 @@
 circular convolution against a direct loop, and every gradient against
 central finite differences of the loss."""
 import numpy as np
+import pytest
 
 import synth
 from oracle import cnn
@@ -54,3 +55,25 @@ def test_gradients_by_central_differences():
                 flat[j] = old
                 fd = (lp - lm) / (2 * eps)
                 assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (li, j, fd, gflat[j])
+
+
+def test_listwise_gradient_by_central_differences():
+    # d/ds of logsumexp(s) - sum q s is p - q; checked numerically through
+    # the scores of the output map
+    rng = np.random.default_rng(4)
+    out = rng.normal(size=(6, 7, 2))
+    a_idx = np.array([0, 9, 20, 33])
+    b_idx = np.array([4, 9, 21, 40])
+    y = np.array([1.0, -0.5, 2.0, 0.0])
+    g = cnn.listwise_grad_out(out, a_idx, b_idx, y, 0.7)
+    eps = 1e-6
+    for idx in [(0, 0, 1), (1, 2, 1), (0, 4, 0), (1, 2, 0), (5, 5, 0), (3, 2, 1)]:
+        o1, o2 = out.copy(), out.copy()
+        o1[idx] += eps
+        o2[idx] -= eps
+        num = (cnn.listwise_loss(o1, a_idx, b_idx, y, 0.7) - cnn.listwise_loss(o2, a_idx, b_idx, y, 0.7)) / (2 * eps)
+        assert abs(num - g[idx]) < 1e-8
+    # equal scores and equal targets: zero gradient; the loss is then log n
+    z = np.zeros_like(out)
+    assert np.abs(cnn.listwise_grad_out(z, a_idx, b_idx, np.zeros(4), 1.0)).max() < 1e-15
+    assert cnn.listwise_loss(z, a_idx, b_idx, np.zeros(4), 1.0) == pytest.approx(np.log(4))
