@@ -547,6 +547,15 @@ typedef struct lpf_cnn lpf_cnn; /* opaque network, owned by the library */
  * network's device memory for H x W cells.  Errors: LPF_EINVAL, LPF_ENOMEM.
  */
 int lpf_cnn_create(int32_t H, int32_t W, uint64_t seed, lpf_cnn **out);
+
+/*
+ * Training loss of lpf_cnn_gradients / lpf_cnn_train_step.  kind 0 (the
+ * default): L = 1/(2n) sum_i (s1[a_i] + s0[b_i] - y_i)^2.  kind 1 (listwise):
+ * L = -sum_i q_i log p_i with q = softmax(y / beta) and p = softmax(s1[a] +
+ * s0[b]) over the snapshot's candidates (the annealer draws pixels with
+ * probability proportional to exp(score / tau)).  Errors: LPF_EINVAL.
+ */
+int lpf_cnn_set_loss(lpf_cnn *cnn, int32_t kind, float beta);
 int64_t lpf_cnn_num_params(const lpf_cnn *cnn);
 int lpf_cnn_set_params(lpf_cnn *cnn, const float *params_host, int64_t n);      /* synchronous */
 int lpf_cnn_get_params(const lpf_cnn *cnn, float *params_host, int64_t n);      /* synchronous */

@@ -21,7 +21,7 @@ __all__ = [
     "lpf_delta_swap", "lpf_full_mc", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror",
     "SaParams", "SaStats", "Annealer", "lpf_sa_create", "lpf_sa_run", "lpf_sa_read", "lpf_sa_recompute_error",
     "lpf_sa_propose", "lpf_sa_selftest_timeout", "lpf_delta_swap_mc", "lpf_sa_create_mc", "lpf_full_ensemble", "SaProgress", "lpf_sa_export_progress", "lpf_sa_import_progress",
-    "save_checkpoint", "load_checkpoint", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
+    "save_checkpoint", "load_checkpoint", "lpf_cnn_set_loss", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
     "lpf_cnn_forward", "lpf_cnn_gradients", "lpf_cnn_train_step", "lpf_sa_set_proposer", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune", "lpf_batch_status",
 ]
 
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_full_mc": (ctypes.c_int, [p, i32, i32, p, p, p, p]),
         "s2_fft": (ctypes.c_int, [p, i32, i32, i32, p, p]),
         "s2_counts": (ctypes.c_int, [p, i32, i32, p, p]),
+        "lpf_cnn_set_loss": (ctypes.c_int, [p, i32, ctypes.c_float]),
         "lpf_sa_export_progress": (ctypes.c_int, [p, ctypes.POINTER(SaProgress), p]),
         "lpf_sa_import_progress": (ctypes.c_int, [p, ctypes.POINTER(SaProgress), p]),
         "lpf_full_ensemble": (ctypes.c_int, [p, i32, i32, i32, p, p, p]),
@@ -425,6 +426,11 @@ def lpf_sa_recompute_error(sa: Annealer, stream=None) -> float:
     e = ctypes.c_double()
     _check(load().lpf_sa_recompute_error(sa.handle, ctypes.byref(e), _stream_ptr(stream)), "lpf_sa_recompute_error")
     return e.value
+
+
+def lpf_cnn_set_loss(net, kind: str = "squared", beta: float = 1.0):
+    """Training loss of the network: "squared" (default) or "listwise"."""
+    _check(load().lpf_cnn_set_loss(net.handle, {"squared": 0, "listwise": 1}[kind], float(beta)), "lpf_cnn_set_loss")
 
 
 def lpf_sa_export_progress(sa: Annealer, stream=None) -> dict:

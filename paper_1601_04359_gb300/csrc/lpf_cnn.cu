@@ -175,6 +175,35 @@ __global__ void cnn_loss_kernel(const float* __restrict__ out, int W, const int3
   if (loss) *loss += l / n * scale;
 }
 
+// Listwise loss of one snapshot: L = logsumexp(s) - sum_i q_i s_i with
+// s_i = s1[a_i] + s0[b_i] and q = softmax(y / beta); dL/ds_i = p_i - q_i on
+// both pixels of candidate i.  One thread, candidate order (deterministic).
+__global__ void cnn_listwise_kernel(const float* __restrict__ out, const int32_t* __restrict__ pairs,
+                                    const float* __restrict__ y, int n, float beta, float* __restrict__ g,
+                                    float* __restrict__ loss, float scale) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  float smax = -3.0e38f, ymax = -3.0e38f;
+  for (int i = 0; i < n; ++i) {
+    smax = fmaxf(smax, out[2 * pairs[2 * i] + 1] + out[2 * pairs[2 * i + 1]]);
+    ymax = fmaxf(ymax, y[i] / beta);
+  }
+  float zs = 0.0f, zq = 0.0f;
+  for (int i = 0; i < n; ++i) {
+    zs += expf(out[2 * pairs[2 * i] + 1] + out[2 * pairs[2 * i + 1]] - smax);
+    zq += expf(y[i] / beta - ymax);
+  }
+  float l = smax + logf(zs);
+  for (int i = 0; i < n; ++i) {
+    const int a = pairs[2 * i], b = pairs[2 * i + 1];
+    const float si = out[2 * a + 1] + out[2 * b];
+    const float pi = expf(si - smax) / zs, qi = expf(y[i] / beta - ymax) / zq;
+    l -= qi * si;
+    g[2 * a + 1] += pi - qi;
+    g[2 * b] += pi - qi;
+  }
+  if (loss) *loss += l * scale;
+}
+
 __global__ void cnn_to_bf16_kernel(const float* __restrict__ m, int n, __nv_bfloat16* __restrict__ w) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w[i] = __float2bfloat16(m[i]);
 }
@@ -212,6 +241,8 @@ struct lpf_cnn {
   float* d_gact = nullptr;    // gradient buffers (two, ping-pong)
   float* d_gact2 = nullptr;
   int64_t step = 0;
+  int loss_kind = 0;          // 0: squared error, 1: listwise cross-entropy
+  float beta = 1.0f;          // listwise target temperature
 };
 
 namespace lpf {
@@ -288,7 +319,10 @@ static void cnn_fwd_bwd(lpf_cnn* c, const uint8_t* cell, const int32_t* pairs, c
   float* g = c->d_gact;
   float* g2 = c->d_gact2;
   cudaMemsetAsync(g, 0, (size_t)npix * kCh[kLayers] * 4, s);
-  cnn_loss_kernel<<<1, 32, 0, s>>>(c->d_act[kLayers], W, pairs, y, n, g, loss_dev, loss_scale);
+  if (c->loss_kind == 1)
+    cnn_listwise_kernel<<<1, 32, 0, s>>>(c->d_act[kLayers], pairs, y, n, c->beta, g, loss_dev, loss_scale);
+  else
+    cnn_loss_kernel<<<1, 32, 0, s>>>(c->d_act[kLayers], W, pairs, y, n, g, loss_dev, loss_scale);
   for (int l = kLayers - 1; l >= 0; --l) {
     const int cin = kCh[l], cout = kCh[l + 1];
     // g = dL/d(pre-activation output of layer l) here (ReLU mask already applied)
@@ -309,6 +343,13 @@ bool cnn_matches(const lpf_cnn* c, int H, int W) { return c && c->H == H && c->W
 }  // namespace lpf
 
 extern "C" {
+
+int lpf_cnn_set_loss(lpf_cnn* cnn, int32_t kind, float beta) {
+  if (!cnn || (kind != 0 && kind != 1) || !(beta > 0.0f)) return LPF_EINVAL;
+  cnn->loss_kind = kind;
+  cnn->beta = beta;
+  return LPF_OK;
+}
 
 int lpf_cnn_create(int32_t H, int32_t W, uint64_t seed, lpf_cnn** out) {
   if (!out) return LPF_EINVAL;

@@ -131,7 +131,7 @@ def run_until(paths, target, cell0, n_step: int, seed: int, t_max: float, net=No
 
 def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22, 23), snapshots: int = 256,
              n: int = 64, epochs: int = 8, taus=(0.5,), epss=(0.2,), on_policy: bool = False,
-             spacing: str = "early", refreshes=(16,)):
+             spacing: str = "early", refreshes=(16,), loss: str = "squared", beta: float = 1.0):
     """Swaps-to-target gain of the learned proposer (median over eval seeds)."""
     import torch
 
@@ -147,6 +147,7 @@ def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22,
         t_max = t_max or st_u["t_max"]
         ref[s] = (st_u["error"], dt_u, st_u["n_eval"] / dt_u)
     net = lpf.lpf_cnn_create(128, 128, seed=3)
+    lpf.lpf_cnn_set_loss(net, loss, beta)
     t0 = time.perf_counter()
     data = [collect(paths, target, synth.exact_fraction_shuffle(128, 128, n1, seed=s), n_step, s, snapshots, n,
                     t_max=t_max, spacing=spacing) for s in train_seeds]
@@ -190,6 +191,7 @@ def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22,
         "runs": runs, "best": {"refresh": best["refresh"], "tau": best["tau"], "epsilon": best["epsilon"],
                                "median_ratio": best["median_ratio"]},
         "train_snapshots": int(cells.shape[0]), "train_candidates_per_snapshot": n, "epochs": epochs,
+        "loss": loss, "beta": beta,
         "train_and_collect_seconds": t_train, "loss_first": losses[0] if losses else None,
         "loss_last": float(np.mean(losses[-8:])) if losses else None, "t_max": t_max,
     }
@@ -208,12 +210,15 @@ def main():
     ap.add_argument("--on-policy", action="store_true")
     ap.add_argument("--spacing", choices=["evals", "early"], default="early")
     ap.add_argument("--refresh", type=int, nargs="+", default=[16])
+    ap.add_argument("--loss", choices=["squared", "listwise"], default="squared")
+    ap.add_argument("--beta", type=float, default=1.0, help="listwise target temperature")
     a = ap.parse_args()
     lpf.load()
     if a.evaluate:
         print(json.dumps(evaluate(n_step=a.n_step, train_seeds=tuple(a.train_seeds), eval_seeds=tuple(a.eval_seeds),
                                   snapshots=a.snapshots, epochs=a.epochs, taus=tuple(a.tau), epss=tuple(a.eps),
-                                  on_policy=a.on_policy, spacing=a.spacing, refreshes=tuple(a.refresh))),
+                                  on_policy=a.on_policy, spacing=a.spacing, refreshes=tuple(a.refresh),
+                                  loss=a.loss, beta=a.beta)),
               flush=True)
 
 

@@ -100,3 +100,31 @@ def test_training_reduces_loss(gpu_lib):
     for _ in range(200):
         last = gpu_lib.lpf_cnn_train_step(net, c, p, t, 1e-3).item()
     assert last < 0.2 * first
+
+
+@pytest.mark.parametrize("beta", [0.5, 2.0])
+def test_listwise_gradients_match_reference(gpu_lib, beta):
+    H = W = 24
+    net, ref_params = _setup(gpu_lib, H, W, 8)
+    gpu_lib.lpf_cnn_set_loss(net, "listwise", beta)
+    cell = synth.clustered_disks(H, W, 0.4, seed=9)
+    rng = np.random.default_rng(10)
+    flat = cell.reshape(-1)
+    a = rng.choice(np.flatnonzero(flat == 1), 16).astype(np.int32)
+    b = rng.choice(np.flatnonzero(flat == 0), 16).astype(np.int32)
+    y = rng.normal(size=16).astype(np.float32)
+    pairs = np.stack([a, b], axis=1)
+    g, loss = gpu_lib.lpf_cnn_gradients(net, torch.from_numpy(cell).cuda(), torch.from_numpy(pairs).cuda(),
+                                        torch.from_numpy(y).cuda())
+    out, acts = ocnn.forward(ref_params, ocnn.features(cell))
+    yd = y.astype(np.float64)
+    grads = ocnn.backward(ref_params, acts, ocnn.listwise_grad_out(out, a, b, yd, beta))
+    assert abs(loss.item() - ocnn.listwise_loss(out, a, b, yd, beta)) <= 1e-4 * max(1.0, abs(loss.item()))
+    ref = np.concatenate([np.concatenate([dw.reshape(-1), db]) for dw, db in grads])
+    got = g.cpu().numpy().astype(np.float64)
+    off = 0
+    for (dw, db) in grads:
+        n = dw.size + db.size
+        seg_ref, seg_got = ref[off:off + n], got[off:off + n]
+        assert np.abs(seg_got - seg_ref).max() <= 2e-3 * np.abs(seg_ref).max() + 1e-7
+        off += n
