@@ -119,8 +119,11 @@ void lpf_paths_free(lpf_paths *paths);
  * image width uploads the handle's program for that width and may allocate
  * the handle's device work area (make that first call before any stream
  * capture); later calls with the same or smaller sizes allocate nothing.
- * Errors: LPF_EINVAL, LPF_EUNSUPPORTED (image band too large for shared
- * memory), LPF_ENOMEM, LPF_ECUDA.
+ * Size envelope: a thread block stages a band of 32 translation rows plus ry
+ * halo rows, each about (W + 2 rx) / 32 + 2 words, in shared memory (at most
+ * about 227 KB), and W <= 4096; e.g. the full domain (rx = W-1, ry = H-1) fits
+ * up to about 700 x 700, a window of 256 up to W = 4096.  Outside it:
+ * LPF_EUNSUPPORTED.  Errors: LPF_EINVAL, LPF_EUNSUPPORTED, LPF_ENOMEM, LPF_ECUDA.
  */
 int lpf_full(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
              int64_t *counts_dev, lpf_stream_t stream);
