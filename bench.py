@@ -142,7 +142,7 @@ def extra_delta(lpf, reps: int = 5):
     import torch
 
     import synth
-    cell = synth.config3_original()[:128, :128].copy()
+    cell = synth.clustered_512()[:128, :128].copy()
     paths = lpf.lpf_build_paths(64, 64)
     d = torch.from_numpy(cell).cuda()
     counts = lpf.lpf_full(d, paths)
@@ -174,7 +174,7 @@ def extra_sa(lpf, seconds: float = 240.0):
     import torch
 
     import synth
-    orig = synth.config3_original()
+    orig = synth.clustered_512()
     paths = lpf.lpf_build_paths(64, 64)
     c = lpf.lpf_full(torch.from_numpy(orig).cuda(), paths)
     target = (c.double() / float(orig.size)).float()
@@ -201,7 +201,7 @@ def extra_batch(lpf):
     import torch
 
     import synth
-    imgs = synth.config4_images(256, seed=4)
+    imgs = synth.mixed_sizes_batch(256, seed=4)
     paths = [lpf.lpf_build_paths(W // 2, H // 2) for H, W in (i.shape for i in imgs)]
     d = [torch.from_numpy(i).cuda() for i in imgs]
     b = lpf.lpf_batch_create(d, paths)
@@ -236,7 +236,7 @@ def extra_s2(lpf, reps: int = 20):
     import torch
 
     import synth
-    d = torch.from_numpy(synth.config2_image()).cuda()
+    d = torch.from_numpy(synth.ellipses_512()).cuda()
     out = lpf.s2_fft(d, 1)
     a, b = _events()
     torch.cuda.synchronize()
@@ -273,7 +273,7 @@ def run_reference(args, ws, rank):
         return
     import synth
     import oracle
-    img = synth.config2_image()
+    img = synth.ellipses_512()
     per_step = max(1.0, 30.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         cpu_baseline_sample(img, seconds=min(per_step, 2.0))
@@ -328,7 +328,7 @@ def main():
         dist.init_process_group("nccl")
     lpf.load()
 
-    img = synth.config2_image()
+    img = synth.ellipses_512()
     paths = lpf.lpf_build_paths(RX, RY)
     stats = lpf.lpf_paths_stats(paths)
     d_img = torch.from_numpy(img).cuda()

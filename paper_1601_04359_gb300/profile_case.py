@@ -21,7 +21,7 @@ import synth  # noqa: E402
 
 
 def lpf_full_512(repeat):
-    img = torch.from_numpy(synth.config2_image()).cuda()
+    img = torch.from_numpy(synth.ellipses_512()).cuda()
     p = lpf.lpf_build_paths(256, 256)
     c = lpf.lpf_full(img, p)
     for _ in range(repeat):
@@ -31,7 +31,7 @@ def lpf_full_512(repeat):
 
 
 def lpf_full_512_standard(repeat):
-    img = torch.from_numpy(synth.config2_image()).cuda()
+    img = torch.from_numpy(synth.ellipses_512()).cuda()
     p = lpf.lpf_build_paths(256, 256)
     c = lpf.lpf_full_standard(img, p)
     for _ in range(repeat):
@@ -42,7 +42,7 @@ def lpf_full_512_standard(repeat):
 def delta_128(repeat):
     """lpf_delta_swap, 128x128 clustered cell, |v| <= 64, 4096 candidates, error changes."""
     import numpy as np
-    cell = synth.config3_original()[:128, :128].copy()
+    cell = synth.clustered_512()[:128, :128].copy()
     p = lpf.lpf_build_paths(64, 64)
     d = torch.from_numpy(cell).cuda()
     counts = lpf.lpf_full(d, p)
@@ -58,7 +58,7 @@ def delta_128(repeat):
 
 def sa_128(repeat):
     """Annealing batches on the 128x128 compression workload (one persistent launch of the batches)."""
-    orig = synth.config3_original()
+    orig = synth.clustered_512()
     p = lpf.lpf_build_paths(64, 64)
     c = lpf.lpf_full(torch.from_numpy(orig).cuda(), p)
     target = (c.double() / float(orig.size)).float()

@@ -43,7 +43,7 @@ def annealing_problem(r: int = 64, cell_size: int = 128, seed: int = 5):
     import torch
 
     import synth
-    orig = synth.config3_original()
+    orig = synth.clustered_512()
     paths = lpf.lpf_build_paths(r, r)
     c = lpf.lpf_full(torch.from_numpy(orig).cuda(), paths)
     target = (c.double() / float(orig.size)).float()

@@ -155,22 +155,22 @@ def exact_fraction_shuffle(H: int, W: int, n_ones: int, seed: int) -> np.ndarray
 
 # ---- the named workloads ---------------------------------------------------
 
-def config1_image() -> np.ndarray:
+def disks_64() -> np.ndarray:
     """64x64 Boolean disks R=5, expected phase-1 fraction 0.4 (27 disks), seed 1."""
     return boolean_disks(64, 64, 5.0, disks_for_fraction(64, 64, 5.0, 0.4), seed=1)
 
 
-def config2_image() -> np.ndarray:
+def ellipses_512() -> np.ndarray:
     """512x512 overlapping ellipses, semi-axes 6-20 px, fraction 0.35, seed 2."""
     return ellipses(512, 512, 0.35, seed=2)
 
 
-def config3_original() -> np.ndarray:
+def clustered_512() -> np.ndarray:
     """512x512 clustered disks (Thomas process, R=5), fraction 0.30, seed 3."""
     return clustered_disks(512, 512, 0.30, seed=3)
 
 
-def config4_images(n: int = 256, seed: int = 4):
+def mixed_sizes_batch(n: int = 256, seed: int = 4):
     """n images, H, W ~ U{48..256} independently, morphology cycling
     disks / ellipses / clustered disks, fraction ~ U[0.2, 0.6]."""
     rng = np.random.default_rng(seed)

@@ -53,10 +53,10 @@ def test_batch_every_words_per_thread_choice(gpu_lib):
             np.testing.assert_array_equal(c.cpu().numpy(), r)
 
 
-def test_config4_batch_equals_per_image_and_sampled_oracle(gpu_lib):
+def test_mixed_sizes_batch_equals_per_image_and_sampled_oracle(gpu_lib):
     # 256 images, 48..256 px, windows r = size/2; autotuned; every image equal
     # to its own lpf_full; a few vectors per image checked by the oracle.
-    imgs = synth.config4_images(256, seed=4)
+    imgs = synth.mixed_sizes_batch(256, seed=4)
     paths = [gpu_lib.lpf_build_paths(W // 2, H // 2) for H, W in (i.shape for i in imgs)]
     d = [torch.from_numpy(i).cuda() for i in imgs]
     b = gpu_lib.lpf_batch_create(d, paths)

@@ -50,7 +50,7 @@ CASES = [
     ("cell 32x32 r8", lambda: synth.random_binary(32, 32, 0.3, 1), 8, 8),
     ("ragged 45x37 rx20 ry15", lambda: synth.clustered_disks(37, 45, 0.3, seed=2), 20, 15),
     ("full domain 9x8", lambda: synth.random_binary(8, 9, 0.5, 3), 8, 7),
-    ("disks 64x64 r32", lambda: synth.config1_image(), 32, 32),
+    ("disks 64x64 r32", lambda: synth.disks_64(), 32, 32),
 ]
 
 
@@ -94,7 +94,7 @@ def test_error_only_and_determinism(gpu_lib):
     assert torch.equal(de1, de2) and torch.equal(de1, de3)  # bitwise reproducible
 
 
-def test_config3_cell_full_batch_sampled(gpu_lib):
+def test_clustered_128_cell_full_batch_sampled(gpu_lib):
     # 128x128 cell, |v| <= 64, K = 4096 candidates in one launch (the annealing
     # workload); a sample of candidates is recounted by the oracle.
     cell = synth.random_binary(128, 128, 0.3, 33)
@@ -107,7 +107,7 @@ def test_config3_cell_full_batch_sampled(gpu_lib):
     p = gpu_lib.lpf_build_paths(rx, ry)
     d_img = torch.from_numpy(cell).cuda()
     counts = gpu_lib.lpf_full(d_img, p)
-    orig = synth.config3_original()
+    orig = synth.clustered_512()
     target = (oracle.lpf_full(orig[:160, :160], rx, ry) / float(160 * 160)).astype(np.float32)
     dc, de = gpu_lib.lpf_delta_swap(d_img, p, torch.from_numpy(pairs).cuda(),
                                     target=torch.from_numpy(target).cuda(), counts=counts, want_de=True)

@@ -25,7 +25,7 @@ def _run(lpf, img, rx, ry, standard=False):
 
 
 CASES = [
-    ("config1 64x64 r32", lambda: synth.config1_image(), 32, 32),
+    ("disks 64x64 r32", lambda: synth.disks_64(), 32, 32),
     ("ragged 37x45", lambda: synth.random_binary(37, 45, 0.6, 1), 20, 11),
     ("tiny 5x7 full domain", lambda: synth.random_binary(5, 7, 0.5, 2), 6, 4),
     ("tall 70x33 rx=32 ry=69", lambda: synth.random_binary(70, 33, 0.55, 3), 32, 69),
@@ -48,10 +48,10 @@ def test_full_matches_oracle(gpu_lib, name, make, rx, ry, standard):
     np.testing.assert_array_equal(got, ref)
 
 
-def test_config2_512_sampled_and_properties(gpu_lib):
+def test_ellipses_512_sampled_and_properties(gpu_lib):
     # Full size (512x512, |dx|,|dy| <= 256), in the launch configuration the
     # benchmark times: sampled vectors checked one by one against the oracle.
-    img = synth.config2_image()
+    img = synth.ellipses_512()
     got, p = _run(gpu_lib, img, 256, 256)
     n_full, _, base = oracle.window_sizes(256, 256)
     rng = np.random.default_rng(0)
@@ -69,7 +69,7 @@ def test_config2_512_sampled_and_properties(gpu_lib):
 
 
 def test_tree_equals_standard_at_full_size(gpu_lib):
-    img = synth.config2_image()
+    img = synth.ellipses_512()
     a, _ = _run(gpu_lib, img, 256, 256, standard=False)
     b, _ = _run(gpu_lib, img, 256, 256, standard=True)
     np.testing.assert_array_equal(a, b)
@@ -111,7 +111,7 @@ def test_every_launch_shape(gpu_lib):
 
 
 def test_autotune_then_full(gpu_lib):
-    img = synth.config1_image()
+    img = synth.disks_64()
     p = gpu_lib.lpf_build_paths(32, 32)
     d = torch.from_numpy(img).cuda()
     T, BB = gpu_lib.lpf_autotune_full(d, p)

@@ -29,7 +29,7 @@ def test_selected_counts_match_oracle(gpu_lib, H, W, rx, ry, frac, seed):
 
 
 def test_all_selected_equals_exact(gpu_lib):
-    img = synth.config1_image()
+    img = synth.disks_64()
     p = gpu_lib.lpf_build_paths(32, 32)
     d = torch.from_numpy(img).cuda()
     a = gpu_lib.lpf_full_mc(d, p, torch.ones_like(d))

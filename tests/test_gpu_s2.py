@@ -24,7 +24,7 @@ def test_s2_matches_direct_sum(gpu_lib, H, W, seed):
 
 
 def test_s2_properties_512(gpu_lib):
-    img = synth.config2_image()
+    img = synth.ellipses_512()
     d = torch.from_numpy(img).cuda()
     s1 = gpu_lib.s2_fft(d, 1).cpu().numpy().astype(np.float64)
     s0 = gpu_lib.s2_fft(d, 0).cpu().numpy().astype(np.float64)

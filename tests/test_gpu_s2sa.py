@@ -193,7 +193,7 @@ def test_single_phase_lineal_trajectory(gpu_lib, phases):
 def test_s2_annealing_128_reduces_error_and_auto_temperature(gpu_lib):
     # 128x128 cell against the S2 of the 512x512 clustered-disk original, cut
     # to the cell's centred offsets; automatic T_max.
-    orig = synth.config3_original()
+    orig = synth.clustered_512()
     s2o = gpu_lib.s2_fft(torch.from_numpy(orig).cuda(), 1).cpu().numpy()
     target = torch.from_numpy(_cut(s2o, 128, 128)).cuda()
     cell0 = synth.exact_fraction_shuffle(128, 128, int(round(orig.mean() * 128 * 128)), seed=5)

@@ -79,7 +79,7 @@ def test_trajectory_equals_sequential_oracle(gpu_lib, kmin, kmax):
 def test_annealing_128_cell_reduces_error_and_is_deterministic(gpu_lib):
     # The compression workload at reduced length: 128x128 cell, |v| <= 64,
     # target from a 512x512 clustered-disk original.
-    orig = synth.config3_original()
+    orig = synth.clustered_512()
     r = 64
     p = gpu_lib.lpf_build_paths(r, r)
     d_orig = torch.from_numpy(orig).cuda()

@@ -25,7 +25,7 @@ def test_brute_force_rectangular():
 def test_zero_vector_is_volume_fraction():
     # Eq. (l2zero): L(0) = phi, i.e. count_p(0) = number of pixels of phase p,
     # and the two phases add up to W*H.
-    img = synth.config1_image()
+    img = synth.disks_64()
     n_full, _, base = oracle.window_sizes(6, 6)
     c = oracle.lpf_full(img, 6, 6)
     assert c[1, base] == int(img.sum())
@@ -35,7 +35,7 @@ def test_zero_vector_is_volume_fraction():
 @pytest.mark.parametrize("z", [1, 2, 3, 5, 8, 13, 21, 31])
 def test_axis_aligned_by_run_lengths(z):
     # Axis-aligned segments: count from an independent run-length tally.
-    img = synth.config1_image()
+    img = synth.disks_64()
     got = oracle.count_list(img, [(z, 0), (0, z), (-z, 0), (0, -z)])
     for p in (0, 1):
         assert got[0, p] == axis_count_by_runs(img, z, p, axis=1)
@@ -59,7 +59,7 @@ def test_chess_closed_form(s):
 
 def test_point_symmetry_exact():
     # Eq. (symmetry): L(v) = L(-v); the oracle evaluates both halves directly.
-    img = synth.config1_image()
+    img = synth.disks_64()
     c = oracle.lpf_full(img, 20, 14)
     np.testing.assert_array_equal(c, c[:, ::-1])
 
@@ -73,7 +73,7 @@ def test_complement_swaps_phases():
 
 
 def test_translation_invariance():
-    img = synth.config1_image()
+    img = synth.disks_64()
     a = oracle.lpf_full(img, 10, 10)
     b = oracle.lpf_full(np.roll(img, (7, -19), axis=(0, 1)), 10, 10)
     np.testing.assert_array_equal(a, b)
@@ -82,7 +82,7 @@ def test_translation_invariance():
 def test_monotone_along_nested_segments():
     # Sec. 3.2: a segment containing a shorter one can only have a smaller
     # count (the basis of the enhanced evaluation's zero test).
-    img = synth.config1_image()
+    img = synth.disks_64()
     for ux, uy in [(1, 0), (0, 1), (1, 1), (2, 1), (-3, 2), (1, 4)]:
         c = oracle.count_list(img, [(k * ux, k * uy) for k in range(0, 10)])
         assert (np.diff(c, axis=0) <= 0).all()
@@ -90,8 +90,8 @@ def test_monotone_along_nested_segments():
 
 def test_counts_bounded_and_vanish():
     # Eq. (l2lim): the lineal path vanishes for long segments in a medium
-    # without long-range order; on config 1 both phases are far below phi at |v|=32.
-    img = synth.config1_image()
+    # without long-range order; on the 64x64 disks image both phases are far below phi at |v|=32.
+    img = synth.disks_64()
     c = oracle.count_list(img, [(32, 0), (0, 32), (32, 32), (-32, 17)])
     assert (c[:, 1] < 0.05 * img.sum()).all()
 

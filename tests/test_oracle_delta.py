@@ -40,7 +40,7 @@ def test_delta_matches_independent_recount():
 
 
 def test_same_phase_pair_is_identity_and_inverse_cancels():
-    img = synth.config1_image()[:32, :32].copy()
+    img = synth.disks_64()[:32, :32].copy()
     rx = ry = 8
     pairs = _pairs(img, 5, 2)
     d = oracle.delta_swap(img, rx, ry, pairs)

@@ -19,7 +19,7 @@ def test_direct_sum_equals_fft_form(H, W, seed):
 
 
 def test_asymptotics_and_two_phase_relation():
-    img = synth.config1_image()
+    img = synth.disks_64()
     H, W = img.shape
     phi1 = img.mean()
     phi0 = 1 - phi1

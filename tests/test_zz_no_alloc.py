@@ -30,7 +30,7 @@ def test_noalloc_matches_lpf_full_on_two_calls(gpu_lib):
     lib = gpu_lib.load()
     r = 256
     paths = gpu_lib.lpf_build_paths(r, r)
-    a = torch.from_numpy(synth.config2_image()).cuda()
+    a = torch.from_numpy(synth.ellipses_512()).cuda()
     b = torch.from_numpy(synth.clustered_disks(512, 512, 0.3, seed=21)).cuda()
     ref_a = gpu_lib.lpf_full(a, paths)   # existing entry point; also puts the program on the device
     ref_b = gpu_lib.lpf_full(b, paths)
@@ -49,7 +49,7 @@ def test_noalloc_matches_lpf_full_on_two_calls(gpu_lib):
 
 def test_noalloc_rejects_what_it_cannot_do(gpu_lib):
     lib = gpu_lib.load()
-    small = torch.from_numpy(synth.config1_image()).cuda()
+    small = torch.from_numpy(synth.disks_64()).cuda()
     fresh = gpu_lib.lpf_build_paths(32, 32)
     out = torch.empty((2, fresh.n_full), dtype=torch.int64, device="cuda")
     # the program for this size was never put on the device: refused, not allocated
