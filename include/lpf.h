@@ -53,7 +53,7 @@ extern "C" {
 #define LPF_ENOMEM (-2)      /* host or device allocation failed */
 #define LPF_ECUDA (-3)       /* a CUDA runtime call failed (no device, launch error) */
 #define LPF_ETIMEOUT (-4)    /* a device-side bounded wait gave up (see lpf_paths_status) */
-#define LPF_EUNSUPPORTED (-5) /* size beyond what this build supports */
+#define LPF_EUNSUPPORTED (-5) /* size beyond what the kernels support (shared memory, width) */
 
 typedef struct CUstream_st *lpf_stream_t; /* same type as cudaStream_t */
 typedef struct lpf_paths lpf_paths;        /* opaque, owned by the library */
