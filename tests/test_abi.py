@@ -20,14 +20,14 @@ def _declared():
             continue
         txt = open(os.path.join(ROOT, "include", f)).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-        names |= set(re.findall(r"\b(lpf_[a-z0-9_]+)\s*\(", txt))
+        names |= set(re.findall(r"\b((?:lpf|s2)_[a-z0-9_]+)\s*\(", txt))
     return names
 
 
 def test_library_exports_every_declared_symbol():
     lib = lpf.load()
     names = _declared()
-    assert "lpf_full" in names and "lpf_build_paths" in names
+    assert {"lpf_full", "lpf_build_paths", "s2_fft", "s2_sa_create", "lpf_sa_create_mc"} <= names
     for n in sorted(names):
         assert hasattr(lib, n), n
 
@@ -66,3 +66,22 @@ def test_invalid_arguments_rejected_on_host():
     assert lib.lpf_full(ctypes.c_void_p(16), 8, 4, p.handle, ctypes.c_void_p(16), None) == -1
     assert lib.lpf_full(ctypes.c_void_p(16), 0, 8, p.handle, ctypes.c_void_p(16), None) == -1
     assert lpf.lpf_strerror(-1) == "invalid argument"
+
+
+def test_newer_entry_points_reject_bad_arguments_on_host():
+    lib = lpf.load()
+    p = lpf.lpf_build_paths(4, 4)
+    v = ctypes.c_void_p(16)
+    h = ctypes.c_void_p()
+    prm = lpf.SaParams(100, 10, 1, 1e-3, 0.01, 64, 1, 1, 3)
+    assert lib.s2_counts(None, 8, 8, v, None) == -1
+    assert lib.s2_delta_swap(v, 8, 8, v, -1, None, None, None, None, None) == -1
+    assert lib.s2_sa_create(v, 1, 8, v, v, ctypes.byref(prm), None, ctypes.byref(h)) == -1   # H < 2
+    assert lib.lpf_full_ensemble(None, 2, 8, 8, p.handle, v, None) == -1
+    assert lib.lpf_full_ensemble(v, 0, 8, 8, p.handle, v, None) == -1
+    assert lib.lpf_sa_create_mc(v, 8, 8, p.handle, None, v, v, ctypes.byref(prm), None, ctypes.byref(h)) == -1
+    assert lib.lpf_sa_import_progress(None, None, None) == -1
+    assert lib.lpf_sa_export_progress(None, None, None) == -1
+    assert lib.lpf_sa_selftest_timeout(None, None) == -1
+    bad = lpf.SaParams(100, 10, 1, 1e-3, 0.01, 64, 1, 1, 7)   # phases outside {0..3}
+    assert lib.lpf_sa_create(v, 8, 8, p.handle, v, v, ctypes.byref(bad), None, ctypes.byref(h)) == -1
