@@ -618,7 +618,7 @@ def lpf_cnn_train_step(cnn: Cnn, cells, pairs, y, lr: float, stream=None):
     return loss
 
 
-def lpf_sa_set_proposer(sa: "Annealer", cnn, epsilon: float = 0.1, tau: float = 1.0, refresh: int = 16):
+def lpf_sa_set_proposer(sa: "Annealer", cnn, epsilon: float = 0.4, tau: float = 0.35, refresh: int = 16):
     _check(load().lpf_sa_set_proposer(sa.handle, cnn.handle if cnn is not None else None, float(epsilon),
                                       float(tau), int(refresh)), "lpf_sa_set_proposer")
     sa.cnn = cnn
