@@ -16,13 +16,16 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "load", "LpfError", "Paths", "lpf_build_paths", "lpf_paths_info", "lpf_paths_export",
-    "lpf_paths_stats", "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer",
-    "lpf_delta_swap", "lpf_full_mc", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror",
-    "SaParams", "SaStats", "Annealer", "lpf_sa_create", "lpf_sa_run", "lpf_sa_read", "lpf_sa_recompute_error",
-    "lpf_sa_propose", "lpf_sa_selftest_timeout", "lpf_delta_swap_mc", "lpf_sa_create_mc", "lpf_full_ensemble", "SaProgress", "lpf_sa_export_progress", "lpf_sa_import_progress",
-    "save_checkpoint", "load_checkpoint", "lpf_cnn_set_loss", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create", "lpf_cnn_set_params", "lpf_cnn_get_params",
-    "lpf_cnn_forward", "lpf_cnn_gradients", "lpf_cnn_train_step", "lpf_sa_set_proposer", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune", "lpf_batch_status",
+    "load", "LpfError", "Paths", "lpf_build_paths", "lpf_paths_info", "lpf_paths_export", "lpf_paths_stats",
+    "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer", "lpf_delta_swap",
+    "lpf_full_mc", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror", "SaParams", "SaStats",
+    "Annealer", "lpf_sa_create", "lpf_sa_run", "lpf_sa_read", "lpf_sa_recompute_error", "lpf_sa_propose",
+    "lpf_sa_selftest_timeout", "lpf_delta_swap_mc", "lpf_sa_create_mc", "lpf_full_ensemble", "SaProgress",
+    "lpf_sa_export_progress", "lpf_sa_import_progress", "save_checkpoint", "load_checkpoint",
+    "lpf_cnn_set_loss", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create",
+    "lpf_cnn_set_params", "lpf_cnn_get_params", "lpf_cnn_forward", "lpf_cnn_gradients", "lpf_cnn_train_step",
+    "lpf_sa_set_proposer", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune",
+    "lpf_batch_status",
 ]
 
 _lib = None

@@ -129,7 +129,7 @@ def run_until(paths, target, cell0, n_step: int, seed: int, t_max: float, net=No
     return hit, st, dt
 
 
-def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22, 23), snapshots: int = 256,
+def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22, 23, 24, 25), snapshots: int = 256,
              n: int = 64, epochs: int = 8, taus=(0.35,), epss=(0.4,), on_policy: bool = False,
              spacing: str = "early", refreshes=(16,), loss: str = "squared", beta: float = 1.0):
     """Swaps-to-target gain of the learned proposer (median over eval seeds)."""
@@ -204,7 +204,7 @@ def main():
     ap.add_argument("--snapshots", type=int, default=256)
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--train-seeds", type=int, nargs="+", default=[11, 12, 13])
-    ap.add_argument("--eval-seeds", type=int, nargs="+", default=[21, 22, 23])
+    ap.add_argument("--eval-seeds", type=int, nargs="+", default=[21, 22, 23, 24, 25])
     ap.add_argument("--tau", type=float, nargs="+", default=[0.35])
     ap.add_argument("--eps", type=float, nargs="+", default=[0.4])
     ap.add_argument("--on-policy", action="store_true")
