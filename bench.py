@@ -395,7 +395,10 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
     words = H * ((W + 31) // 32)
-    alu_ops = 2.0 * stats["n_tree_nodes"] * words  # 1 funnel shift + 1 LOP3 per (tree node, word)
+    executed, nominal = lpf.lpf_paths_work(paths)  # of the last evaluation (same image every step)
+    done = executed / nominal if nominal else 1.0
+    # 1 funnel shift + 1 LOP3 per (tree node, word) the warps walked (subtrees with zero counts skipped)
+    alu_ops = 2.0 * stats["n_tree_nodes"] * words * done
     achieved = alu_ops / (walk_ms / 1000.0)
     peak = n_sm * ALU_LANES_PER_SM * sm_max * 1e6
     traffic = _traffic_record()
@@ -420,7 +423,9 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "walk_kernel", "kernel_ms": walk_ms,
                      "peak_basis": f"{n_sm} SMs x {ALU_LANES_PER_SM} LOP3/SHF lanes/clk x {sm_max:.0f} MHz (max clock)",
-                     "work_basis": f"{stats['n_tree_nodes']} prefix-tree nodes x {words} translation words x 2 ops"},
+                     "work_basis": f"{stats['n_tree_nodes']} prefix-tree nodes x {words} translation words x 2 ops"
+                                   f" x {done:.4f} (share of the walk not skipped as zero-count subtrees)",
+                     "walked_share": done},
         "e2e": {"value": ws * tests_per_step / (e2e_ms / 1000.0), "unit": "tests/s",
                 "h2d_bytes_per_step": int(img.nbytes), "d2h_bytes_per_step": int(2 * paths.n_full * 8)},
         "gpu_launches": 3 * K,

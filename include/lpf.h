@@ -98,12 +98,29 @@ int lpf_paths_export(const lpf_paths *paths, int16_t *vec_dxdy_host, int64_t *pt
 
 /*
  * Work statistics: n_tree_nodes = pixels the prefix-sharing program visits
- * per translation word, stack_depth = masks it keeps at once, n_pieces =
+ * per translation word at most (subtrees whose count is zero for all
+ * translations a warp holds are skipped: lpf_paths_work reports what a call
+ * did), stack_depth = masks it keeps at once, n_pieces =
  * independent program pieces the kernels spread over thread blocks.
  * Any output pointer may be NULL.
  */
 int lpf_paths_stats(const lpf_paths *paths, int64_t *n_tree_nodes, int32_t *stack_depth,
                     int32_t *n_pieces);
+
+/*
+ * Work of the last lpf_full, lpf_full_standard, lpf_full_mc or
+ * lpf_full_ensemble evaluation enqueued with this handle (for an ensemble:
+ * its last cut; not the allocation-free variant), counted in pixel words
+ * ANDed by a warp (one word for each of the warp's 32 translation rows x T
+ * words), summed over warps:
+ *   executed  what the warps did, after skipping the subtrees of the
+ *             prefix tree whose count is zero for all the warp's translations
+ *             (the zero-count skip of the "enhanced" evaluation, Sec. 3.2);
+ *   nominal   what they would do without that skip.
+ * Host pointers, both required.  Synchronises with the device (a blocking
+ * copy).  Before any evaluation both are 0.  Errors: LPF_EINVAL, LPF_ECUDA.
+ */
+int lpf_paths_work(const lpf_paths *paths, int64_t *executed, int64_t *nominal);
 
 /* Release a handle and its device memory (NULL is ignored).  Synchronises
  * the device before freeing device tables. */
@@ -114,7 +131,9 @@ void lpf_paths_free(lpf_paths *paths);
  * window (Sec. 2.2; Alg. 1/Alg. 2 of Sec. 3.1 with the prefix sharing of
  * Sec. 3.2).  img_dev: H*W uint8 (0/1), counts_dev: int64 full layout
  * [2][n_vec_full], overwritten.  Vectors outside D are filled by the point
- * symmetry of Eq. (symmetry).
+ * symmetry of Eq. (symmetry).  A warp that finds a count zero for all its
+ * translations skips the segments that extend that one (their counts are
+ * zero there too), so the time depends on the image.
  * Requires rx < W, ry < H, 1 <= H, W <= 8192.  The first call with a new
  * image width uploads the handle's program for that width and may allocate
  * the handle's device work area (make that first call before any stream

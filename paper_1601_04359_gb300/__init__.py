@@ -17,6 +17,7 @@ from . import build as _build
 
 __all__ = [
     "load", "LpfError", "Paths", "lpf_build_paths", "lpf_paths_info", "lpf_paths_export", "lpf_paths_stats",
+    "lpf_paths_work",
     "lpf_full", "lpf_full_standard", "lpf_paths_status", "lpf_paths_set_timer", "lpf_delta_swap",
     "lpf_full_mc", "lpf_autotune_full", "lpf_set_launch_shape", "lpf_strerror", "SaParams", "SaStats",
     "Annealer", "lpf_sa_create", "lpf_sa_run", "lpf_sa_read", "lpf_sa_recompute_error", "lpf_sa_propose",
@@ -90,6 +91,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_paths_info": (ctypes.c_int, [p, P64, P64, P64]),
         "lpf_paths_export": (ctypes.c_int, [p, p, p, p]),
         "lpf_paths_stats": (ctypes.c_int, [p, P64, P32, P32]),
+        "lpf_paths_work": (ctypes.c_int, [p, P64, P64]),
         "lpf_paths_free": (None, [p]),
         "lpf_full": (ctypes.c_int, [p, i32, i32, p, p, p]),
         "lpf_full_standard": (ctypes.c_int, [p, i32, i32, p, p, p]),
@@ -212,6 +214,14 @@ def lpf_paths_stats(paths: Paths):
     _check(load().lpf_paths_stats(paths.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "lpf_paths_stats")
     return {"n_tree_nodes": a.value, "stack_depth": b.value, "n_pieces": c.value}
+
+
+def lpf_paths_work(paths: Paths):
+    """(executed, nominal) pixel words ANDed by the walk warps in the last
+    full evaluation with this handle, with and without the zero-count skip."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().lpf_paths_work(paths.handle, ctypes.byref(a), ctypes.byref(b)), "lpf_paths_work")
+    return a.value, b.value
 
 
 def lpf_full(img, paths: Paths, counts=None, stream=None):

@@ -205,7 +205,9 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
 
     int64_t pc = piece[pi];
     const int64_t end = piece[pi + 1];
+    uint32_t executed = 0;  // pixel words this warp ANDs in this item
     while (pc < end) {
+      const int64_t rec = pc;
       const uint32_t hdr = __ldg(prog + pc++);
       if (hdr & kReset) {
 #pragma unroll
@@ -217,9 +219,15 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
         for (int t = 0; t < T; ++t) { m1[t] = st1[l][t]; m0[t] = st0[l][t]; }
       }
       int vec = -1;
-      if (hdr & kEmit) vec = (int)__ldg(prog + pc++);
+      uint32_t skip = 0;
+      if (hdr & kEmit) {
+        vec = (int)__ldg(prog + pc);
+        skip = __ldg(prog + pc + 1);
+        pc += 2;
+      }
       pc = (pc + 3) & ~int64_t(3);
       const int n = (int)(hdr & kNpixMask);
+      executed += (uint32_t)n;
       const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
       const int n4 = n >> 2;
       if (n4 > 0) {
@@ -236,7 +244,11 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
         uint32_t c = 0;
 #pragma unroll
         for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
-        c = warp_sum(c);
+        c = warp_sum(c);  // the same total in every lane
+        if (c == 0 && skip != 0) {  // empty for the whole warp: so is every count below this node
+          pc = rec + skip;
+          continue;
+        }
         if (lane == 0) {
           const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
           if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);
@@ -249,6 +261,7 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
         for (int t = 0; t < T; ++t) { st1[l][t] = m1[t]; st0[l][t] = m0[t]; }
       }
     }
+    if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(ctl + 2), (unsigned long long)executed);
     __syncthreads();  // every warp is done with the staged band before it may be replaced
   }
   if (s_abort) {
@@ -311,7 +324,10 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
   for (size_t i = 0; i < w.size();) {
     const uint32_t h = w[i];
     out[i++] = h;
-    if (h & kEmit) { out[i] = w[i]; ++i; }
+    if (h & kEmit) {  // vector id and skip word
+      out[i] = w[i]; ++i;
+      out[i] = w[i]; ++i;
+    }
     while (i % 4) { out[i] = w[i]; ++i; }  // alignment padding
     const uint32_t n = h & kNpixMask;
     for (uint32_t k = 0; k < n; ++k, ++i) {
@@ -426,7 +442,7 @@ static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* cou
 
   const int64_t n_full = p->host.n_full, base = p->host.base;
   cudaError_t e = accumulate ? cudaSuccess : cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * n_full, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status + 1, 0, sizeof(int), s);  // work counter
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status + 1, 0, 3 * sizeof(int), s);  // work counters
   if (e != cudaSuccess) return set_cuda_error(e);
   {
     const int64_t total = (int64_t)g.rows * g.S;
@@ -446,6 +462,7 @@ static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* cou
     p->d_sel_active = p->d_sel;
   }
   unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
+  p->nominal_pixels = prog.n_pixel_words * g.nbg * g.G * g.BB;  // every warp walks every piece
   if (p->ev_start) cudaEventRecord(p->ev_start, s);
   switch (g.T) {
     case 1: launch_walk<1>(g, b, p, c, blocks, s); break;
@@ -692,6 +709,17 @@ int lpf_paths_stats(const lpf_paths* p, int64_t* n_tree_nodes, int32_t* stack_de
   if (n_tree_nodes) *n_tree_nodes = p->host.n_nodes();
   if (stack_depth) *stack_depth = p->host.tree.stack_depth;
   if (n_pieces) *n_pieces = (int32_t)p->host.tree.piece_pixels.size();
+  return LPF_OK;
+}
+
+int lpf_paths_work(const lpf_paths* p, int64_t* executed, int64_t* nominal) {
+  if (!p || !executed || !nominal) return LPF_EINVAL;
+  *executed = 0;
+  *nominal = p->nominal_pixels;
+  if (!p->d_status) return LPF_OK;
+  unsigned long long h = 0;
+  if (cudaMemcpy(&h, p->d_status + 2, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return LPF_ECUDA;
+  *executed = (int64_t)h;
   return LPF_OK;
 }
 

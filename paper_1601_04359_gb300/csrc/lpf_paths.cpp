@@ -60,6 +60,7 @@ struct Trie {
 
 struct Event {            // one step of the depth-first walk
   enum Kind : uint8_t { kRestoreEv, kPixEv, kEmitEv, kPushEv } kind;
+  int8_t lv;              // pixel events: stack level of the walk invocation
   int32_t a;              // level, node or vector id
 };
 
@@ -74,16 +75,16 @@ struct Walker {
   void node(int32_t n, int level) {
     // Mask of n's parent is current; AND n's pixel, count, then branch.
     for (;;) {
-      ev.push_back({Event::kPixEv, n});
-      if (t.vec[n] >= 0) ev.push_back({Event::kEmitEv, t.vec[n]});
+      ev.push_back({Event::kPixEv, (int8_t)level, n});
+      if (t.vec[n] >= 0) ev.push_back({Event::kEmitEv, 0, t.vec[n]});
       const int32_t c0 = cstart[n], c1 = cstart[n + 1];
       const int nc = c1 - c0;
       if (nc == 0) return;
       if (nc == 1) { n = clist[c0]; continue; }
-      ev.push_back({Event::kPushEv, level});
+      ev.push_back({Event::kPushEv, 0, level});
       max_level = std::max(max_level, level + 1);
       for (int i = 0; i < nc; ++i) {
-        if (i > 0) ev.push_back({Event::kRestoreEv, level});
+        if (i > 0) ev.push_back({Event::kRestoreEv, 0, level});
         if (i < nc - 1) node(clist[c0 + i], level + 1);
       }
       // last (heaviest) child reuses this level: tail position
@@ -127,16 +128,19 @@ static void emit_records(const std::vector<Event>& ev, Program& prog,
     const size_t hdr_pos = w.size();
     w.push_back(0);  // header placeholder
     uint32_t npix = 0;
+    int level = 0;
     pixels.clear();
     while (i < ev.size() && ev[i].kind == Event::kPixEv) {
       pixels.push_back((uint32_t)ev[i].a);  // trie node id until baked
       cur = ev[i].a;
+      level = ev[i].lv;
       ++npix;
       ++i;
     }
     if (i < ev.size() && ev[i].kind == Event::kEmitEv) {
       hdr |= kEmit;
       w.push_back((uint32_t)ev[i].a);
+      w.push_back((uint32_t)level);  // skip word: the walk level until resolve_skips
       ++i;
     }
     if (i < ev.size() && ev[i].kind == Event::kPushEv) {
@@ -313,6 +317,7 @@ int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err
       }
       plain.words.push_back(kReset | kEmit | (uint32_t)chain.size());
       plain.words.push_back((uint32_t)c);
+      plain.words.push_back(0u);  // skip word (resolved to the next record)
       for (int32_t x : chain) plain.words.push_back((uint32_t)x);
       plain.n_pixel_words += (int64_t)chain.size();
     }
@@ -320,6 +325,8 @@ int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err
   split_program(p, plain, n_pieces);
   align_program(tree);
   align_program(plain);
+  resolve_skips(tree);
+  resolve_skips(plain);
 
   p.node_parent = std::move(t.parent);
   p.node_pix = std::move(t.pix);
@@ -341,7 +348,10 @@ void align_program(Program& prog) {
     while (pi < prog.piece_begin.size() && prog.piece_begin[pi] == (int64_t)i) new_begin[pi++] = (int64_t)out.size();
     const uint32_t h = prog.words[i++];
     out.push_back(h);
-    if (h & kEmit) out.push_back(prog.words[i++]);
+    if (h & kEmit) {
+      out.push_back(prog.words[i++]);
+      out.push_back(prog.words[i++]);
+    }
     while (out.size() % 4) out.push_back(0);
     const uint32_t n = h & kNpixMask;
     for (uint32_t k = 0; k < n; ++k) out.push_back(prog.words[i++]);
@@ -349,6 +359,44 @@ void align_program(Program& prog) {
   while (pi < prog.piece_begin.size()) new_begin[pi++] = (int64_t)out.size();
   prog.words.swap(out);
   prog.piece_begin.swap(new_begin);
+}
+
+// Replace the walk level held in each emitting record's skip word by the
+// distance to its skip target.  The records of the subtree below the last node
+// of a record are those that follow it up to the first record that restores a
+// stack level below the level of the walk invocation holding that node (the
+// invocation's own branches restore its level or deeper ones, and once it
+// returns its parent restores one level up) or that resets the mask.
+void resolve_skips(Program& prog) {
+  std::vector<int64_t> starts;
+  for (size_t q = 0; q + 1 < prog.piece_begin.size(); ++q) {
+    const int64_t b = prog.piece_begin[q], e = prog.piece_begin[q + 1];
+    starts.clear();
+    for (int64_t w = b; w < e;) {
+      starts.push_back(w);
+      const uint32_t h = prog.words[w];
+      const int64_t k = (w + 1 + ((h & kEmit) ? 2 : 0) + 3) & ~int64_t(3);
+      w = k + (h & kNpixMask);
+    }
+    // nr[L]: start of the nearest later record that resets or restores a level < L
+    int64_t nr[kMaxStack + 2];
+    for (int64_t& x : nr) x = e;
+    for (size_t r = starts.size(); r-- > 0;) {
+      const int64_t w = starts[r];
+      const uint32_t h = prog.words[w];
+      if (h & kEmit) {
+        const uint32_t lv = std::min<uint32_t>(prog.words[w + 2], kMaxStack + 1);
+        const int64_t d = nr[lv] - w;
+        prog.words[w + 2] = d < (int64_t(1) << 32) ? (uint32_t)d : 0u;  // 0: never skip
+      }
+      if (h & kReset) {
+        for (int64_t& x : nr) x = w;
+      } else if (h & kRestore) {
+        const int l = (int)((h >> kRlevelShift) & kLevelMask);
+        for (int L = l + 1; L <= kMaxStack + 1; ++L) nr[L] = w;
+      }
+    }
+  }
 }
 
 void split_program(const Paths&, Program& prog, int n_pieces) {
@@ -362,7 +410,7 @@ void split_program(const Paths&, Program& prog, int n_pieces) {
     pixc.push_back(pix);
     const int64_t np = h & kNpixMask;
     pix += np;
-    w += 1 + ((h & kEmit) ? 1 : 0) + np;
+    w += 1 + ((h & kEmit) ? 2 : 0) + np;
   }
   starts.push_back((int64_t)prog.words.size());
   pixc.push_back(pix);

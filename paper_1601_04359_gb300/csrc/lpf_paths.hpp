@@ -16,10 +16,19 @@
 
 namespace lpf {
 
-// Record header word (int32) of a program; an optional vector id follows it,
-// then zero padding up to the next multiple of 4 words, then the pixel words.
+// Record header word (int32) of a program; for an emitting record a vector
+// id and a skip word follow it, then zero padding up to the next multiple of
+// 4 words, then the pixel words.
 //   bits  0..13  number of pixel words that follow (n_pix)
-//   bit   14     emit: count the mask into vector `vec` (next word)
+//   bit   14     emit: count the mask into vector `vec` (next word); the word
+//                after it is the distance in words from this header to the
+//                first later record of the piece that lies outside the
+//                subtree of the record's last node (or to the piece end).
+//                Counts only shrink down the tree, so when the mask is empty
+//                for every translation a warp holds, every count in that
+//                subtree is zero there and the warp may continue at the skip
+//                target (the zero-count skip of the "enhanced" evaluation,
+//                Sec. 3.2, applied to whole subtrees).
 //   bit   15     restore: mask <- stack[rlevel] before the pixels
 //   bit   16     push: stack[plevel] <- mask after the pixels (and emit)
 //   bits 17..23  rlevel
@@ -75,5 +84,7 @@ int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err
 void split_program(const Paths& p, Program& prog, int n_pieces);
 // Pad records so that pixel lists start on 16-byte boundaries.
 void align_program(Program& prog);
+// Fill the skip words of an aligned, split program.
+void resolve_skips(Program& prog);
 
 }  // namespace lpf

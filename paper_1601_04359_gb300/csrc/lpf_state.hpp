@@ -65,7 +65,9 @@ struct lpf_paths {
   lpf::Baked tree, plain;
   uint32_t* d_packed = nullptr;  // work area: packed image (one at a time)
   size_t packed_cap = 0;         // words
-  int* d_status = nullptr;       // [0] status flags since the last check, [1] work counter
+  int* d_status = nullptr;       // [0] status flags since the last check, [1] work counter,
+                                 // [2..3] pixel words the walk warps ANDed (uint64)
+  int64_t nominal_pixels = 0;    // the same without the zero-count skip, for the last walk
   std::vector<lpf::Tuned> tuned; // autotuned walk launch shapes
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;  // optional kernel timer
   lpf::DeltaTables delta;

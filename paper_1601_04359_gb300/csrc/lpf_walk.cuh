@@ -63,6 +63,7 @@ __device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, in
 #pragma unroll
   for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
   while (pc < end) {
+    const int64_t rec = pc;
     const uint32_t hdr = __ldg(prog + pc++);
     if (hdr & kReset) {
 #pragma unroll
@@ -74,7 +75,12 @@ __device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, in
       for (int t = 0; t < T; ++t) { m1[t] = st1[l][t]; m0[t] = st0[l][t]; }
     }
     int vec = -1;
-    if (hdr & kEmit) vec = (int)__ldg(prog + pc++);
+    uint32_t skip = 0;
+    if (hdr & kEmit) {
+      vec = (int)__ldg(prog + pc);
+      skip = __ldg(prog + pc + 1);
+      pc += 2;
+    }
     pc = (pc + 3) & ~int64_t(3);
     const int n = (int)(hdr & kNpixMask);
     const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
@@ -93,7 +99,11 @@ __device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, in
       uint32_t c = 0;
 #pragma unroll
       for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
-      c = warp_sum(c);
+      c = warp_sum(c);  // the same total in every lane
+      if (c == 0 && skip != 0) {  // empty for the whole warp: so is every count below this node
+        pc = rec + skip;
+        continue;
+      }
       if (lane == 0) {
         const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
         if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);

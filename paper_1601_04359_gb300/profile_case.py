@@ -1,6 +1,6 @@
 """Run one named workload a few times, for capture under a profiler.
 
-    python -m paper_1601_04359_gb300.profile_case lpf_full_512 [--repeat N]
+    python -m paper_1601_04359_gb300.profile_case lpf_full_512 [--repeat N] [--shape T BB]
 
 Each workload does one warm-up call (which also uploads tables) and then
 `repeat` calls, so a profiler can skip the first launch of a kernel and
@@ -20,9 +20,11 @@ import paper_1601_04359_gb300 as lpf  # noqa: E402
 import synth  # noqa: E402
 
 
-def lpf_full_512(repeat):
+def lpf_full_512(repeat, shape=None):
     img = torch.from_numpy(synth.ellipses_512()).cuda()
     p = lpf.lpf_build_paths(256, 256)
+    if shape:
+        lpf.lpf_set_launch_shape(p, 512, 512, shape[0], shape[1])
     c = lpf.lpf_full(img, p)
     for _ in range(repeat):
         lpf.lpf_full(img, p, c)
@@ -30,7 +32,7 @@ def lpf_full_512(repeat):
     assert lpf.lpf_paths_status(p) == 0
 
 
-def lpf_full_512_standard(repeat):
+def lpf_full_512_standard(repeat, shape=None):
     img = torch.from_numpy(synth.ellipses_512()).cuda()
     p = lpf.lpf_build_paths(256, 256)
     c = lpf.lpf_full_standard(img, p)
@@ -39,7 +41,7 @@ def lpf_full_512_standard(repeat):
     torch.cuda.synchronize()
 
 
-def delta_128(repeat):
+def delta_128(repeat, shape=None):
     """lpf_delta_swap, 128x128 clustered cell, |v| <= 64, 4096 candidates, error changes."""
     import numpy as np
     cell = synth.clustered_512()[:128, :128].copy()
@@ -56,7 +58,7 @@ def delta_128(repeat):
     torch.cuda.synchronize()
 
 
-def sa_128(repeat):
+def sa_128(repeat, shape=None):
     """Annealing batches on the 128x128 compression workload (one persistent launch of the batches)."""
     orig = synth.clustered_512()
     p = lpf.lpf_build_paths(64, 64)
@@ -76,9 +78,11 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("workload", choices=sorted(WORKLOADS))
     ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--shape", type=int, nargs=2, metavar=("T", "BB"),
+                    help="walk-kernel launch shape (lpf_full workloads; default: the built-in choice)")
     a = ap.parse_args()
     lpf.load()
-    WORKLOADS[a.workload](a.repeat)
+    WORKLOADS[a.workload](a.repeat, a.shape)
 
 
 if __name__ == "__main__":

@@ -138,6 +138,41 @@ def squares(H: int, W: int, s: int, fraction: float, seed: int) -> np.ndarray:
     return img
 
 
+def _disks_radii(H: int, W: int, R: np.ndarray, centres: np.ndarray) -> np.ndarray:
+    """Union of disks with per-disk radii R[i] and continuous centres[i]."""
+    img = np.zeros((H, W), np.uint8)
+    r = int(math.ceil(float(R.max()))) + 1
+    bx = np.floor(centres[:, 0]).astype(np.int64)
+    by = np.floor(centres[:, 1]).astype(np.int64)
+    for oy in range(-r, r + 1):
+        py = by + oy
+        dy = _torus_delta((py + 0.5) - centres[:, 1], H)
+        for ox in range(-r, r + 1):
+            px = bx + ox
+            dx = _torus_delta((px + 0.5) - centres[:, 0], W)
+            hit = dx * dx + dy * dy <= R * R
+            img[(py[hit] % H), (px[hit] % W)] = 1
+    return img
+
+
+def foam(H: int, W: int, porosity: float, seed: int, radii=(2.0, 8.0)) -> np.ndarray:
+    """Foam-like medium: phase 1 is the solid left between pores, the pores
+    being disks of radius uniform in `radii` at uniform centres, added in
+    draw order until the pore fraction reaches `porosity` (a stand-in for the
+    metal-foam image of Tab. comptime, third microstructure, which is not
+    available)."""
+    rng = np.random.default_rng(seed)
+    pores = np.zeros((H, W), np.uint8)
+    target = porosity * H * W
+    while pores.sum(dtype=np.int64) < target:
+        # a round of k pores while far from the target, one at a time near it
+        k = 64 if (target - pores.sum(dtype=np.int64)) > 64 * math.pi * radii[1] ** 2 else 1
+        R = rng.uniform(radii[0], radii[1], k)
+        c = np.stack([rng.uniform(0, W, k), rng.uniform(0, H, k)], axis=1)
+        pores |= _disks_radii(H, W, R, c)
+    return (1 - pores).astype(np.uint8)
+
+
 def random_binary(H: int, W: int, fraction: float, seed: int) -> np.ndarray:
     """Independent pixels, phase 1 with probability `fraction`."""
     rng = np.random.default_rng(seed)

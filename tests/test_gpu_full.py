@@ -36,6 +36,11 @@ CASES = [
     ("all ones", lambda: np.ones((33, 65), np.uint8), 17, 9),
     ("all zeros", lambda: np.zeros((33, 65), np.uint8), 17, 9),
     ("ellipses 96x130", lambda: synth.ellipses(96, 130, 0.35, seed=7), 48, 40),
+    # media of Tab. comptime on the full domain, where warps skip whole subtrees of zero counts
+    ("chess 64 full domain", lambda: synth.chess(64, 64, 10), 63, 63),
+    ("chess 33x200 rx=120", lambda: synth.chess(33, 200, 10), 120, 32),
+    ("squares 4x4 60x70 full domain", lambda: synth.squares(60, 70, 4, 0.2, seed=7), 69, 59),
+    ("foam 50 full domain", lambda: synth.foam(50, 50, 0.75, seed=5), 49, 49),
 ]
 
 

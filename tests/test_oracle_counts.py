@@ -57,6 +57,25 @@ def test_chess_closed_form(s):
         assert c[0, 0] == c[0, 1] == c[1, 0] == c[1, 1] == expect
 
 
+@pytest.mark.parametrize("s", [3, 10])
+def test_chess_diagonals_closed_form(s):
+    # Along (k, k) the segment is the exact diagonal: from (x, y) both
+    # coordinates cross a square edge at the same steps (the colour is kept)
+    # exactly when x = y (mod s); along (-k, k) exactly when
+    # x mod s + y mod s = s - 1.  Either way N/s starts, for every k >= s.
+    n = 10 * s
+    img = synth.chess(n, n, s)
+    vecs = [(k, k) for k in (s, s + 1, 2 * s + 3, n - 1)] + [(-k, k) for k in (s, 2 * s - 1, n - 1)]
+    c = oracle.count_list(img, vecs)
+    np.testing.assert_array_equal(c.sum(axis=1), np.full(len(vecs), n * n // s))
+    # Shorter diagonals (k < s): with a = x mod s, b = y mod s the colour is
+    # kept when neither coordinate reaches an edge within k steps ((s - k)^2
+    # residue pairs) or both reach it at the same step (a = b >= s - k: k
+    # pairs), so the two phases together count N ((s - k)^2 + k) / s^2.
+    for k in range(1, s):
+        assert oracle.count_list(img, [(k, k)]).sum() == n * n * ((s - k) ** 2 + k) // (s * s), k
+
+
 def test_point_symmetry_exact():
     # Eq. (symmetry): L(v) = L(-v); the oracle evaluates both halves directly.
     img = synth.disks_64()
