@@ -32,6 +32,12 @@ namespace lpf {
 
 constexpr int kDevStack = 24;   // deepest prefix-tree stack the kernels hold
 constexpr int kMaxSmem = 227 * 1024;
+// Control words of a walk: [0] status flags, [2..3] pixel words walked
+// (uint64), [kCtlUnits + bg] the unit counter of band group bg.
+constexpr int kCtlExecuted = 2;
+constexpr int kCtlUnits = 4;
+constexpr int kMaxBandGroups = (8192 + 31) / 32;
+constexpr int kCtlWords = kCtlUnits + kMaxBandGroups;
 
 int make_geometry(int H, int W, int rx, int ry, int T, int BB, Geometry& g) {
   g.H = H; g.W = W; g.rx = rx; g.ry = ry;
@@ -62,11 +68,17 @@ int make_geometry(int H, int W, int rx, int ry, int T, int BB, Geometry& g) {
 // Kernels
 
 // packed[y][k]: bit b is the pixel at row y mod H, column (32k + b - r32) mod W.
+// Also zeroes the walk's n_zero64 counts and n_zero32 control words (which
+// would otherwise take two more launches).
 __global__ void pack_rows_kernel(const uint8_t* __restrict__ img, int H, int W, int r32, int S, int rows,
-                                 uint32_t* __restrict__ packed) {
+                                 uint32_t* __restrict__ packed, unsigned long long* __restrict__ zero64,
+                                 int64_t n_zero64, int* __restrict__ zero32, int n_zero32) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t i = i0; i < n_zero64; i += stride) zero64[i] = 0ull;
+  for (int64_t i = i0; i < n_zero32; i += stride) zero32[i] = 0;
   const int64_t total = (int64_t)rows * S;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = i0; i < total; i += stride) {
     const int y = (int)(i / S), k = (int)(i % S);
     const uint8_t* row = img + (int64_t)(y % H) * W;
     int x = (32 * k - r32) % W;
@@ -136,13 +148,18 @@ __device__ __forceinline__ void and1(const uint32_t* lane_base, uint32_t p, uint
   }
 }
 
-// Persistent walk kernel.  Work items are (block-band group, program piece)
-// pairs taken from an atomic counter in band-major order, so a block usually
-// keeps its staged band across consecutive items and re-stages it (one bulk
-// copy) only when the band changes.  The launch bounds cap a thread at 64
-// registers (two 512-thread blocks per SM): at T = 8 that doubles the
-// resident warps (32 instead of 16 per SM with 96 registers), which hides the
-// latency of the shared-memory word loads (8.6 % faster at 512², window 256).
+// Persistent walk kernel.  A block stages the image rows of one band group
+// (BB bands of 32 translation rows, plus the ry halo rows) and its warps pull
+// work units from that band group's counter in global memory: unit u is
+// program piece u / n_tiles on tile u % n_tiles (tile = one band and one group
+// of T words, i.e. 32 rows x 32T translations).  Warps never wait for one
+// another inside a band group, so warps whose tiles skip zero-count subtrees
+// (and finish early) simply take more units.  A block starts on band group
+// blockIdx.x mod n_bg and, once that counter is exhausted, moves on to the
+// next band group that still has units (one bulk copy and one block barrier
+// per move).  The launch bounds cap a thread at 64 registers (two 512-thread
+// blocks per SM), which keeps 32 warps resident per SM to hide the latency of
+// the shared-memory word loads.
 template <int T>
 __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict__ packed, int H, int W, int S,
                                                   int nw, int G, int BB, uint32_t band_bytes, int n_bg,
@@ -153,117 +170,134 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
                                                   const uint32_t* __restrict__ sel) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ __align__(8) uint64_t bar;
-  __shared__ int s_item, s_abort;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int bl = warp / G, grp = warp - (warp / G) * G;
+  __shared__ int s_abort, s_done;
+  const int lane = threadIdx.x & 31;
+  const int n_tiles = G * BB;
+  const int units = n_tiles * n_pieces;
+  int* unit_ctr = ctl + kCtlUnits;
   if (threadIdx.x == 0) { mbar_init(&bar, 1); s_abort = 0; }
   __syncthreads();
   uint32_t parity = 0;
-  int cur_bg = -1;
-  const int n_items = n_bg * n_pieces;
-  const uint32_t* lane_base = sm + (bl * 32 + lane) * S + grp * T;
   bool copy_pending = false;
+  unsigned long long executed = 0;  // pixel words this warp ANDs
 
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(ctl + 1, 1);
+  for (int k = 0; k < n_bg; ++k) {
+    const int bg = (int)((blockIdx.x + (unsigned)k) % (unsigned)n_bg);
+    if (threadIdx.x == 0) s_done = *reinterpret_cast<volatile int*>(unit_ctr + bg) >= units;
     __syncthreads();
-    const int item = s_item;
-    if (item >= n_items) break;
-    const int bg = item / n_pieces, pi = item - (item / n_pieces) * n_pieces;
-    if (bg != cur_bg) {
-      if (threadIdx.x == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&bar, band_bytes);
-        bulk_g2s(sm, packed + (size_t)bg * 32 * BB * S, band_bytes, &bar);
-      }
-      copy_pending = true;
-      if (mbar_wait(&bar, parity)) copy_pending = false;
-      else s_abort = 1;
-      parity ^= 1u;
-      cur_bg = bg;
-      __syncthreads();
-      if (s_abort) break;
+    if (s_done) {
+      __syncthreads();  // s_done is rewritten next round
+      continue;
     }
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&bar, band_bytes);
+      bulk_g2s(sm, packed + (size_t)bg * 32 * BB * S, band_bytes, &bar);
+    }
+    copy_pending = true;
+    if (mbar_wait(&bar, parity)) copy_pending = false;
+    else s_abort = 1;
+    parity ^= 1u;
+    __syncthreads();
+    if (s_abort) break;
 
-    const int y = (bg * BB + bl) * 32 + lane;
-    uint32_t valid[T];
+    for (;;) {
+      int u = 0;
+      if (lane == 0) u = atomicAdd(unit_ctr + bg, 1);
+      u = __shfl_sync(0xffffffffu, u, 0);
+      if (u >= units) break;
+      const int tile = u % n_tiles, pi = u / n_tiles;
+      const int bl = tile / G, grp = tile - (tile / G) * G;
+      const uint32_t* lane_base = sm + (bl * 32 + lane) * S + grp * T;
+      const int y = (bg * BB + bl) * 32 + lane;
+      uint32_t valid[T];
 #pragma unroll
-    for (int t = 0; t < T; ++t) {
-      const int j = grp * T + t;
-      uint32_t v = 0;
-      if (y < H && j < nw) {
-        const int rem = W - 32 * j;
-        v = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
-        if (sel) v &= sel[(size_t)y * nw + j];  // only the selected translations
+      for (int t = 0; t < T; ++t) {
+        const int j = grp * T + t;
+        uint32_t v = 0;
+        if (y < H && j < nw) {
+          const int rem = W - 32 * j;
+          v = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+          if (sel) v &= sel[(size_t)y * nw + j];  // only the selected translations
+        }
+        valid[t] = v;
       }
-      valid[t] = v;
-    }
-    uint32_t m1[T], m0[T];
-    uint32_t st1[kDevStack][T], st0[kDevStack][T];
+      uint32_t m1[T], m0[T];
+      uint32_t st1[kDevStack][T], st0[kDevStack][T];
 #pragma unroll
-    for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
+      for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
 
-    int64_t pc = piece[pi];
-    const int64_t end = piece[pi + 1];
-    uint32_t executed = 0;  // pixel words this warp ANDs in this item
-    while (pc < end) {
-      const int64_t rec = pc;
-      const uint32_t hdr = __ldg(prog + pc++);
-      if (hdr & kReset) {
+      int64_t pc = piece[pi];
+      const int64_t end = piece[pi + 1];
+      uint32_t hdr_next = pc < end ? __ldg(prog + pc) : 0u;
+      while (pc < end) {
+        const int64_t rec = pc++;
+        const uint32_t hdr = hdr_next;
+        if (hdr & kReset) {
 #pragma unroll
-        for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
-      }
-      if (hdr & kRestore) {
-        const int l = (hdr >> kRlevelShift) & kLevelMask;
-#pragma unroll
-        for (int t = 0; t < T; ++t) { m1[t] = st1[l][t]; m0[t] = st0[l][t]; }
-      }
-      int vec = -1;
-      uint32_t skip = 0;
-      if (hdr & kEmit) {
-        vec = (int)__ldg(prog + pc);
-        skip = __ldg(prog + pc + 1);
-        pc += 2;
-      }
-      pc = (pc + 3) & ~int64_t(3);
-      const int n = (int)(hdr & kNpixMask);
-      executed += (uint32_t)n;
-      const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
-      const int n4 = n >> 2;
-      if (n4 > 0) {
-        uint4 nxt = __ldg(q4);
-        for (int q = 0; q < n4; ++q) {
-          const uint4 cur = nxt;
-          if (q + 1 < n4) nxt = __ldg(q4 + q + 1);
-          and4<T>(lane_base, cur, m1, m0);
+          for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
         }
-      }
-      for (int i = n4 * 4; i < n; ++i) and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
-      pc += n;
-      if (vec >= 0) {
-        uint32_t c = 0;
+        if (hdr & kRestore) {
+          const int l = (hdr >> kRlevelShift) & kLevelMask;
 #pragma unroll
-        for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
-        c = warp_sum(c);  // the same total in every lane
-        if (c == 0 && skip != 0) {  // empty for the whole warp: so is every count below this node
-          pc = rec + skip;
-          continue;
+          for (int t = 0; t < T; ++t) { m1[t] = st1[l][t]; m0[t] = st0[l][t]; }
         }
-        if (lane == 0) {
-          const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
-          if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);
-          if (c1) atomicAdd(counts + n_full + base + vec, (unsigned long long)c1);
+        int vec = -1;
+        uint32_t skip = 0;
+        if (hdr & kEmit) vec = (int)__ldg(prog + pc++);
+        if (hdr & (kEmit | kPush)) skip = __ldg(prog + pc++);
+        pc = (pc + 3) & ~int64_t(3);
+        const int n = (int)(hdr & kNpixMask);
+        executed += (unsigned)n;
+        // the next record's header, fetched while this record's pixels are ANDed
+        hdr_next = pc + n < end ? __ldg(prog + pc + n) : 0u;
+        const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
+        const int n4 = n >> 2;
+        if (n4 > 0) {
+          uint4 nxt = __ldg(q4);
+          for (int q = 0; q < n4; ++q) {
+            const uint4 cur = nxt;
+            if (q + 1 < n4) nxt = __ldg(q4 + q + 1);
+            and4<T>(lane_base, cur, m1, m0);
+          }
         }
-      }
-      if (hdr & kPush) {
-        const int l = (hdr >> kPlevelShift) & kLevelMask;
+        for (int i = n4 * 4; i < n; ++i) and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
+        pc += n;
+        if (vec >= 0) {
+          uint32_t c = 0;
 #pragma unroll
-        for (int t = 0; t < T; ++t) { st1[l][t] = m1[t]; st0[l][t] = m0[t]; }
+          for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
+          c = warp_sum(c);  // the same total in every lane
+          if (c == 0 && skip != 0) {  // empty for the whole warp: so is every count below this node
+            pc = rec + skip;
+            hdr_next = pc < end ? __ldg(prog + pc) : 0u;
+            continue;
+          }
+          if (lane == 0) {
+            const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
+            if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);
+            if (c1) atomicAdd(counts + n_full + base + vec, (unsigned long long)c1);
+          }
+        } else if (hdr & kPush) {  // a branching node that ends no vector: same test by a vote
+          uint32_t any = 0;
+#pragma unroll
+          for (int t = 0; t < T; ++t) any |= m1[t] | m0[t];
+          if (!__any_sync(0xffffffffu, any != 0) && skip != 0) {
+            pc = rec + skip;
+            hdr_next = pc < end ? __ldg(prog + pc) : 0u;
+            continue;
+          }
+        }
+        if (hdr & kPush) {
+          const int l = (hdr >> kPlevelShift) & kLevelMask;
+#pragma unroll
+          for (int t = 0; t < T; ++t) { st1[l][t] = m1[t]; st0[l][t] = m0[t]; }
+        }
       }
     }
-    if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(ctl + 2), (unsigned long long)executed);
     __syncthreads();  // every warp is done with the staged band before it may be replaced
   }
+  if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(ctl + kCtlExecuted), executed);
   if (s_abort) {
     atomicOr(ctl, 1);
     if (copy_pending) (void)mbar_wait(&bar, parity ^ 1u);  // let an outstanding copy land
@@ -293,8 +327,8 @@ int ensure_device(lpf_paths* p, size_t packed_words) {
     return LPF_EINVAL;  // handle is bound to another device
   }
   if (!p->d_status) {
-    if ((e = cudaMalloc(&p->d_status, 4 * sizeof(int))) != cudaSuccess) return set_cuda_error(e);
-    if ((e = cudaMemset(p->d_status, 0, 4 * sizeof(int))) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMalloc(&p->d_status, kCtlWords * sizeof(int))) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemset(p->d_status, 0, kCtlWords * sizeof(int))) != cudaSuccess) return set_cuda_error(e);
   }
   if (packed_words > p->packed_cap) {
     if (p->d_packed) {
@@ -324,10 +358,7 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
   for (size_t i = 0; i < w.size();) {
     const uint32_t h = w[i];
     out[i++] = h;
-    if (h & kEmit) {  // vector id and skip word
-      out[i] = w[i]; ++i;
-      out[i] = w[i]; ++i;
-    }
+    for (int k = record_extra_words(h); k > 0; --k) { out[i] = w[i]; ++i; }  // vector id, skip word
     while (i % 4) { out[i] = w[i]; ++i; }  // alignment padding
     const uint32_t n = h & kNpixMask;
     for (uint32_t k = 0; k < n; ++k, ++i) {
@@ -441,13 +472,16 @@ static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* cou
   (void)cudaGetLastError();  // clear a stale error left by earlier, unrelated calls
 
   const int64_t n_full = p->host.n_full, base = p->host.base;
-  cudaError_t e = accumulate ? cudaSuccess : cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * n_full, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status + 1, 0, 3 * sizeof(int), s);  // work counters
-  if (e != cudaSuccess) return set_cuda_error(e);
+  cudaError_t e = cudaSuccess;
   {
-    const int64_t total = (int64_t)g.rows * g.S;
+    // pack the rows; zero the counts (unless accumulating) and the work
+    // counters (not the status flags)
+    const int64_t n_zero = accumulate ? 0 : 2 * n_full;
+    const int64_t total = std::max<int64_t>((int64_t)g.rows * g.S, n_zero);
     const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-    pack_rows_kernel<<<pblocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, p->d_packed);
+    pack_rows_kernel<<<pblocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, p->d_packed,
+                                             reinterpret_cast<unsigned long long*>(counts), n_zero,
+                                             p->d_status + 1, kCtlUnits - 1 + g.nbg);
   }
   p->d_sel_active = nullptr;
   if (sel) {
@@ -541,7 +575,7 @@ static int autotune_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t
 // allocating routine.
 constexpr size_t kNoAllocPackedWords = size_t(1) << 18;  // 1 MiB of packed image rows
 static __device__ __align__(256) uint32_t g_noalloc_packed[kNoAllocPackedWords];
-static __device__ __align__(256) int g_noalloc_ctl[4];   // [0] status flags, [1] work counter
+static __device__ __align__(256) int g_noalloc_ctl[kCtlWords];  // control words of the walk
 
 namespace {
 struct NoAllocSlot {
@@ -613,13 +647,13 @@ static int run_full_noalloc(const uint8_t* img, int H, int W, lpf_paths* p, int6
   (void)cudaGetLastError();
 
   const int64_t n_full = p->host.n_full, base = p->host.base;
-  e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * 2 * n_full, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(slot.ctl, 0, 4 * sizeof(int), s);  // status and work counter start at 0
-  if (e != cudaSuccess) return set_cuda_error(e);
   {
-    const int64_t total = (int64_t)g.rows * g.S;
+    // pack the rows; the counts, the status and the work counters start at 0
+    const int64_t total = std::max<int64_t>((int64_t)g.rows * g.S, 2 * n_full);
     const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-    pack_rows_kernel<<<pblocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, slot.packed);
+    pack_rows_kernel<<<pblocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, slot.packed,
+                                             reinterpret_cast<unsigned long long*>(counts), 2 * n_full, slot.ctl,
+                                             kCtlUnits + g.nbg);
   }
   unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
   const dim3 block(32 * g.G * g.BB);
@@ -670,13 +704,9 @@ int lpf_build_paths(int32_t rx, int32_t ry, lpf_paths** out) {
   lpf_paths* p = new (std::nothrow) lpf_paths();
   if (!p) return LPF_ENOMEM;
   std::string err;
-  // Enough pieces for ~8 waves of blocks over 152 SMs on large windows,
-  // fewer on small ones (each piece repeats a prologue of one segment).
-  const int64_t n_canon = (int64_t)ry * (2 * rx + 1) + rx + 1;
-  const int pieces = (int)std::max<int64_t>(1, std::min<int64_t>(256, n_canon / 256));
   int rc;
   try {
-    rc = lpf::build_paths(rx, ry, pieces, p->host, err);
+    rc = lpf::build_paths(rx, ry, 0, p->host, err);  // pieces sized by the tree
   } catch (const std::bad_alloc&) {
     rc = LPF_ENOMEM;
   }
@@ -718,7 +748,8 @@ int lpf_paths_work(const lpf_paths* p, int64_t* executed, int64_t* nominal) {
   *nominal = p->nominal_pixels;
   if (!p->d_status) return LPF_OK;
   unsigned long long h = 0;
-  if (cudaMemcpy(&h, p->d_status + 2, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return LPF_ECUDA;
+  if (cudaMemcpy(&h, p->d_status + lpf::kCtlExecuted, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LPF_ECUDA;
   *executed = (int64_t)h;
   return LPF_OK;
 }

@@ -140,7 +140,6 @@ static void emit_records(const std::vector<Event>& ev, Program& prog,
     if (i < ev.size() && ev[i].kind == Event::kEmitEv) {
       hdr |= kEmit;
       w.push_back((uint32_t)ev[i].a);
-      w.push_back((uint32_t)level);  // skip word: the walk level until resolve_skips
       ++i;
     }
     if (i < ev.size() && ev[i].kind == Event::kPushEv) {
@@ -149,6 +148,7 @@ static void emit_records(const std::vector<Event>& ev, Program& prog,
       top = ev[i].a + 1;
       ++i;
     }
+    if (hdr & (kEmit | kPush)) w.push_back((uint32_t)level);  // skip word: the walk level until resolve_skips
     hdr |= npix;
     w[hdr_pos] = hdr;
     for (uint32_t q : pixels) w.push_back(q);
@@ -231,11 +231,28 @@ int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err
   // rebuilds its starting state from the root (no emits).
   const int64_t nrec = (int64_t)rec_word.size() - 1;
   const int64_t total = rec_pix.back();
-  if (n_pieces < 1) n_pieces = 1;
+  if (n_pieces < 1) {  // automatic: pieces of 2 segment lengths of tree nodes (at least 64), at most kMaxPieces
+    const int64_t piece_nodes = std::max<int64_t>(64, 2 * ((int64_t)std::max(rx, ry) + 1));
+    n_pieces = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxPieces, nn / piece_nodes));
+  }
+  // Each cut sits near its share of the pixels, at the record (within a
+  // quarter piece either way) whose starting node is shallowest: the
+  // piece's prologue re-walks that node's segment prefix.
   std::vector<int64_t> cuts{0};
+  const int64_t slack = std::min<int64_t>(4096, nrec / (4 * (int64_t)n_pieces));
   for (int q = 1; q < n_pieces; ++q) {
     const int64_t target = total * q / n_pieces;
-    int64_t r = std::lower_bound(rec_pix.begin(), rec_pix.end() - 1, target) - rec_pix.begin();
+    const int64_t r0 = std::lower_bound(rec_pix.begin(), rec_pix.end() - 1, target) - rec_pix.begin();
+    const int64_t lo = std::max<int64_t>(cuts.back() + 1, r0 - slack);
+    const int64_t hi = std::min<int64_t>(nrec - 1, r0 + slack);
+    int64_t r = r0;
+    if (lo <= hi) {
+      r = lo;
+      for (int64_t c = lo + 1; c <= hi; ++c) {
+        const int32_t dc = t.depth[rec_cur[c]], dr = t.depth[rec_cur[r]];
+        if (dc < dr || (dc == dr && std::llabs(c - r0) < std::llabs(r - r0))) r = c;
+      }
+    }
     if (r <= cuts.back()) continue;
     if (r >= nrec) break;
     cuts.push_back(r);
@@ -268,8 +285,12 @@ int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err
         const bool is_push = li < live.size() && live[li] == chain[ci];
         if (is_push || ci + 1 == chain.size()) {
           uint32_t hdr = (uint32_t)run.size() | (first ? kReset : 0u);
-          if (is_push) { hdr |= kPush | ((uint32_t)li << kPlevelShift); ++li; }
           tree.words.push_back(hdr);
+          if (is_push) {  // the node pushed at level li belongs to a walk invocation of level li
+            tree.words.back() |= kPush | ((uint32_t)li << kPlevelShift);
+            tree.words.push_back((uint32_t)li);  // skip word
+            ++li;
+          }
           for (uint32_t n : run) tree.words.push_back(n);
           pix += (int64_t)run.size();
           run.clear();
@@ -348,10 +369,7 @@ void align_program(Program& prog) {
     while (pi < prog.piece_begin.size() && prog.piece_begin[pi] == (int64_t)i) new_begin[pi++] = (int64_t)out.size();
     const uint32_t h = prog.words[i++];
     out.push_back(h);
-    if (h & kEmit) {
-      out.push_back(prog.words[i++]);
-      out.push_back(prog.words[i++]);
-    }
+    for (int k = record_extra_words(h); k > 0; --k) out.push_back(prog.words[i++]);
     while (out.size() % 4) out.push_back(0);
     const uint32_t n = h & kNpixMask;
     for (uint32_t k = 0; k < n; ++k) out.push_back(prog.words[i++]);
@@ -361,8 +379,8 @@ void align_program(Program& prog) {
   prog.piece_begin.swap(new_begin);
 }
 
-// Replace the walk level held in each emitting record's skip word by the
-// distance to its skip target.  The records of the subtree below the last node
+// Replace the walk level held in each skip word by the distance to its skip
+// target.  The records of the subtree below the last node
 // of a record are those that follow it up to the first record that restores a
 // stack level below the level of the walk invocation holding that node (the
 // invocation's own branches restore its level or deeper ones, and once it
@@ -375,7 +393,7 @@ void resolve_skips(Program& prog) {
     for (int64_t w = b; w < e;) {
       starts.push_back(w);
       const uint32_t h = prog.words[w];
-      const int64_t k = (w + 1 + ((h & kEmit) ? 2 : 0) + 3) & ~int64_t(3);
+      const int64_t k = (w + 1 + record_extra_words(h) + 3) & ~int64_t(3);
       w = k + (h & kNpixMask);
     }
     // nr[L]: start of the nearest later record that resets or restores a level < L
@@ -384,10 +402,11 @@ void resolve_skips(Program& prog) {
     for (size_t r = starts.size(); r-- > 0;) {
       const int64_t w = starts[r];
       const uint32_t h = prog.words[w];
-      if (h & kEmit) {
-        const uint32_t lv = std::min<uint32_t>(prog.words[w + 2], kMaxStack + 1);
+      if (h & (kEmit | kPush)) {
+        const int64_t at = w + record_extra_words(h);  // the skip word is the last extra word
+        const uint32_t lv = std::min<uint32_t>(prog.words[at], kMaxStack + 1);
         const int64_t d = nr[lv] - w;
-        prog.words[w + 2] = d < (int64_t(1) << 32) ? (uint32_t)d : 0u;  // 0: never skip
+        prog.words[at] = d < (int64_t(1) << 32) ? (uint32_t)d : 0u;  // 0: never skip
       }
       if (h & kReset) {
         for (int64_t& x : nr) x = w;
@@ -410,7 +429,7 @@ void split_program(const Paths&, Program& prog, int n_pieces) {
     pixc.push_back(pix);
     const int64_t np = h & kNpixMask;
     pix += np;
-    w += 1 + ((h & kEmit) ? 2 : 0) + np;
+    w += 1 + record_extra_words(h) + np;
   }
   starts.push_back((int64_t)prog.words.size());
   pixc.push_back(pix);

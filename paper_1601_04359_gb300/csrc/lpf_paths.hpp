@@ -16,21 +16,20 @@
 
 namespace lpf {
 
-// Record header word (int32) of a program; for an emitting record a vector
-// id and a skip word follow it, then zero padding up to the next multiple of
-// 4 words, then the pixel words.
+// Record header word (int32) of a program, then a vector id (emitting
+// records), then a skip word (emitting or pushing records), then zero
+// padding up to the next multiple of 4 words, then the pixel words.
 //   bits  0..13  number of pixel words that follow (n_pix)
-//   bit   14     emit: count the mask into vector `vec` (next word); the word
-//                after it is the distance in words from this header to the
-//                first later record of the piece that lies outside the
-//                subtree of the record's last node (or to the piece end).
-//                Counts only shrink down the tree, so when the mask is empty
-//                for every translation a warp holds, every count in that
-//                subtree is zero there and the warp may continue at the skip
-//                target (the zero-count skip of the "enhanced" evaluation,
-//                Sec. 3.2, applied to whole subtrees).
+//   bit   14     emit: count the mask into vector `vec`
 //   bit   15     restore: mask <- stack[rlevel] before the pixels
 //   bit   16     push: stack[plevel] <- mask after the pixels (and emit)
+// The skip word is the distance in words from the header to the first later
+// record of the piece that lies outside the subtree of the record's last node
+// (or to the piece end; 0: none).  Masks only shrink down the tree, so when
+// the mask is empty for every translation a warp holds, every count in that
+// subtree is zero there and the warp may continue at the skip target (the
+// zero-count skip of the "enhanced" evaluation, Sec. 3.2, applied to whole
+// subtrees).
 //   bits 17..23  rlevel
 //   bits 24..30  plevel
 //   bit   31     reset: mask <- all valid translations before the pixels
@@ -43,6 +42,16 @@ constexpr int kPlevelShift = 24;
 constexpr uint32_t kLevelMask = 0x7Fu;
 constexpr uint32_t kReset = 1u << 31;
 constexpr int kMaxStack = 32;
+
+#ifdef __CUDACC__
+#define LPF_HOST_DEVICE __host__ __device__
+#else
+#define LPF_HOST_DEVICE
+#endif
+// Words between a record's header and its padding (vector id, skip word).
+LPF_HOST_DEVICE inline int record_extra_words(uint32_t hdr) {
+  return ((hdr & kEmit) ? 1 : 0) + ((hdr & (kEmit | kPush)) ? 1 : 0);
+}
 
 struct Program {
   // Words: headers, vec ids and pixel words.  Pixel words hold an index into
@@ -77,7 +86,13 @@ inline bool is_canonical(int dx, int dy) { return dy > 0 || (dy == 0 && dx >= 0)
 // Pixel offsets of the segment (0,0) -> (dx,dy), for canonical (dx,dy).
 void segment_canonical(int dx, int dy, std::vector<int16_t>& out_xy);
 
-// Build tables and both programs.  Returns 0 or a negative status.
+// Build tables and both programs, split into n_pieces pieces (n_pieces < 1:
+// one piece per 2 longest-segment lengths of tree nodes, at least 64, and at
+// most kMaxPieces pieces).  A piece repeats a prologue of at most one
+// segment, cut where the tree is shallow (a few % of the work), and more
+// pieces let more warps share a small tree, whose walk is latency-bound.
+// Returns 0 or a negative status.
+constexpr int64_t kMaxPieces = 1024;
 int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err);
 
 // Split a program into pieces of similar pixel count; fills piece tables.

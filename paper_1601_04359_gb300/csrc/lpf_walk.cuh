@@ -76,11 +76,8 @@ __device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, in
     }
     int vec = -1;
     uint32_t skip = 0;
-    if (hdr & kEmit) {
-      vec = (int)__ldg(prog + pc);
-      skip = __ldg(prog + pc + 1);
-      pc += 2;
-    }
+    if (hdr & kEmit) vec = (int)__ldg(prog + pc++);
+    if (hdr & (kEmit | kPush)) skip = __ldg(prog + pc++);
     pc = (pc + 3) & ~int64_t(3);
     const int n = (int)(hdr & kNpixMask);
     const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
@@ -108,6 +105,14 @@ __device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, in
         const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
         if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);
         if (c1) atomicAdd(counts + n_full + base + vec, (unsigned long long)c1);
+      }
+    } else if (hdr & kPush) {  // a branching node that ends no vector: same test by a vote
+      uint32_t any = 0;
+#pragma unroll
+      for (int t = 0; t < T; ++t) any |= m1[t] | m0[t];
+      if (!__any_sync(0xffffffffu, any != 0) && skip != 0) {
+        pc = rec + skip;
+        continue;
       }
     }
     if (hdr & kPush) {
