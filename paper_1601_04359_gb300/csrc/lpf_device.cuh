@@ -50,6 +50,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// The staged word a baked pixel word refers to.  A pixel word is
+// (word offset << 7) | funnel shift, i.e. (byte offset << 5) | shift with a
+// shift below 32, so the byte offset is a plain right shift by 5 (one add
+// with a shifted operand, no masking).
+__device__ __forceinline__ const uint32_t* lane_word(const uint32_t* lane_base, uint32_t pix) {
+  return reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(lane_base) + (pix >> 5));
+}
+
 __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

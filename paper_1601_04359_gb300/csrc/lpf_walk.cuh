@@ -18,10 +18,10 @@ constexpr int kWalkStack = 24;
 
 template <int T>
 __device__ __forceinline__ void walk_and4(const uint32_t* lane_base, uint4 P, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
-  const uint32_t* sa = lane_base + (P.x >> 7);
-  const uint32_t* sb = lane_base + (P.y >> 7);
-  const uint32_t* sc = lane_base + (P.z >> 7);
-  const uint32_t* sd = lane_base + (P.w >> 7);
+  const uint32_t* sa = lane_word(lane_base, P.x);
+  const uint32_t* sb = lane_word(lane_base, P.y);
+  const uint32_t* sc = lane_word(lane_base, P.z);
+  const uint32_t* sd = lane_word(lane_base, P.w);
   uint32_t wa[T + 1], wb[T + 1], wc[T + 1], wd[T + 1];
 #pragma unroll
   for (int t = 0; t <= T; ++t) { wa[t] = sa[t]; wb[t] = sb[t]; wc[t] = sc[t]; wd[t] = sd[t]; }
@@ -38,7 +38,7 @@ __device__ __forceinline__ void walk_and4(const uint32_t* lane_base, uint4 P, ui
 
 template <int T>
 __device__ __forceinline__ void walk_and1(const uint32_t* lane_base, uint32_t p, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
-  const uint32_t* sa = lane_base + (p >> 7);
+  const uint32_t* sa = lane_word(lane_base, p);
   uint32_t wa[T + 1];
 #pragma unroll
   for (int t = 0; t <= T; ++t) wa[t] = sa[t];
@@ -92,27 +92,25 @@ __device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, in
     }
     for (int i = n4 * 4; i < n; ++i) walk_and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
     pc += n;
-    if (vec >= 0) {
-      uint32_t c = 0;
-#pragma unroll
-      for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
-      c = warp_sum(c);  // the same total in every lane
-      if (c == 0 && skip != 0) {  // empty for the whole warp: so is every count below this node
-        pc = rec + skip;
-        continue;
-      }
-      if (lane == 0) {
-        const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
-        if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);
-        if (c1) atomicAdd(counts + n_full + base + vec, (unsigned long long)c1);
-      }
-    } else if (hdr & kPush) {  // a branching node that ends no vector: same test by a vote
+    if (hdr & (kEmit | kPush)) {
+      // Empty for the whole warp (one vote): so is every count below this node.
       uint32_t any = 0;
 #pragma unroll
       for (int t = 0; t < T; ++t) any |= m1[t] | m0[t];
       if (!__any_sync(0xffffffffu, any != 0) && skip != 0) {
         pc = rec + skip;
         continue;
+      }
+      if (vec >= 0) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
+        c = warp_sum(c);
+        if (lane == 0) {
+          const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
+          if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);
+          if (c1) atomicAdd(counts + n_full + base + vec, (unsigned long long)c1);
+        }
       }
     }
     if (hdr & kPush) {
