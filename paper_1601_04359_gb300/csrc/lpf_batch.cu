@@ -7,12 +7,16 @@
 // table of per-image descriptors written); a run is then four launches with
 // no host-device copies -- zero the counts, pack every image into bit rows,
 // one persistent walk kernel, fill the mirrored halves -- and can be replayed
-// as a CUDA graph.  The walk kernel pulls work items (image, band group,
-// program piece) from an atomic counter; all blocks have 8 warps, and each
-// image gets its own split of those warps into word groups x bands (G x BB,
-// G*BB = 8) and its own words per thread T, chosen by a waste/load cost model
-// or by the batch autotuner.  A block re-stages its rows (one bulk copy) only
-// when the image or band group changes.
+// as a CUDA graph.  All blocks have 8 warps, and each image gets its own
+// split of those warps into word groups x bands (G x BB, G*BB = 8 tiles of 32
+// rows x 32T translations) and its own words per thread T, chosen by a
+// waste/load cost model or by the batch autotuner.  The walk kernel visits a
+// host-built list of band-group slots (every band group of every image gets
+// slots in proportion to its work, heaviest first) at the grid stride; for
+// each it stages the band group's rows (one bulk copy, skipped if already
+// staged) and its warps pull units (tile, program piece) from that band
+// group's counter until none are left, so warps whose tiles skip zero-count
+// subtrees take more units instead of waiting for the others.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -28,15 +32,21 @@ namespace lpf {
 constexpr int kBatchWarps = 8;
 constexpr int kBatchThreads = 32 * kBatchWarps;
 
+constexpr int kBatchCtlUnits = 4;  // control words: [0] status, [kBatchCtlUnits + g] unit counter of band group g
+
 struct BatchDesc {
   const uint8_t* img;
   unsigned long long* counts;
   uint32_t* packed;
   const uint32_t* prog;
   const int64_t* piece;
-  int64_t n_full, base, item0;
-  int H, W, S, nw, G, BB, T, r32, rows, nbg, n_pieces;
+  int64_t n_full, base;
+  int H, W, S, nw, G, BB, T, r32, rows, nbg, n_pieces, bg0;
   uint32_t band_bytes;
+};
+
+struct BatchSlot {
+  int img, bg, g;  // image, its band group, global band-group index (counter)
 };
 
 __global__ void batch_zero_kernel(const BatchDesc* __restrict__ d) {
@@ -73,9 +83,9 @@ __global__ void batch_mirror_kernel(const BatchDesc* __restrict__ d) {
 }
 
 template <int T>
-__device__ __forceinline__ void batch_item(const BatchDesc& b, int bg, int pi, const uint32_t* sm, int warp, int lane) {
-  const int bl = warp / b.G, grp = warp - (warp / b.G) * b.G;
-  if (bl >= b.BB) return;
+__device__ __forceinline__ void batch_unit(const BatchDesc& b, int bg, int tile, int pi, const uint32_t* sm,
+                                           int lane) {
+  const int bl = tile / b.G, grp = tile - (tile / b.G) * b.G;
   const int y = (bg * b.BB + bl) * 32 + lane;
   uint32_t valid[T];
 #pragma unroll
@@ -92,58 +102,59 @@ __device__ __forceinline__ void batch_item(const BatchDesc& b, int bg, int pi, c
   walk_piece<T>(b.prog, b.piece[pi], b.piece[pi + 1], lane_base, valid, lane, b.counts, b.n_full, b.base);
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 2) batch_walk_kernel(const BatchDesc* __restrict__ d, int n_img,
-                                                                   int64_t total_items, int* __restrict__ ctl) {
+__global__ void __launch_bounds__(kBatchThreads, 4) batch_walk_kernel(const BatchDesc* __restrict__ d,
+                                                                   const BatchSlot* __restrict__ slots,
+                                                                   int n_slots, int* __restrict__ ctl) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ __align__(8) uint64_t bar;
-  __shared__ int64_t s_item;
-  __shared__ int s_img, s_abort;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ int s_abort, s_done;
+  const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) { mbar_init(&bar, 1); s_abort = 0; }
   __syncthreads();
   uint32_t parity = 0;
   int cur_img = -1, cur_bg = -1;
   bool copy_pending = false;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const int64_t item = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(ctl + 2), 1ull);
-      int lo = 0, hi = n_img;  // last image with item0 <= item
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (d[mid].item0 <= item) lo = mid; else hi = mid;
-      }
-      s_item = item;
-      s_img = lo;
-    }
+  for (int k = blockIdx.x; k < n_slots; k += gridDim.x) {
+    const BatchSlot sl = slots[k];
+    const BatchDesc& b = d[sl.img];
+    const int n_tiles = b.G * b.BB;
+    const int units = n_tiles * b.n_pieces;
+    int* ctr = ctl + kBatchCtlUnits + sl.g;
+    if (threadIdx.x == 0) s_done = *reinterpret_cast<volatile int*>(ctr) >= units;
     __syncthreads();
-    const int64_t item = s_item;
-    if (item >= total_items) break;
-    const int im = s_img;
-    const BatchDesc& b = d[im];
-    const int64_t local = item - b.item0;
-    const int bg = (int)(local / b.n_pieces), pi = (int)(local - (int64_t)bg * b.n_pieces);
-    if (im != cur_img || bg != cur_bg) {
+    if (s_done) {
+      __syncthreads();  // s_done is rewritten next round
+      continue;
+    }
+    if (sl.img != cur_img || sl.bg != cur_bg) {
       if (threadIdx.x == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bar, b.band_bytes);
-        bulk_g2s(sm, b.packed + (size_t)bg * 32 * b.BB * b.S, b.band_bytes, &bar);
+        bulk_g2s(sm, b.packed + (size_t)sl.bg * 32 * b.BB * b.S, b.band_bytes, &bar);
       }
       copy_pending = true;
       if (mbar_wait(&bar, parity)) copy_pending = false;
       else s_abort = 1;
       parity ^= 1u;
-      cur_img = im;
-      cur_bg = bg;
+      cur_img = sl.img;
+      cur_bg = sl.bg;
       __syncthreads();
       if (s_abort) break;
     }
-    switch (b.T) {
-      case 1: batch_item<1>(b, bg, pi, sm, warp, lane); break;
-      case 2: batch_item<2>(b, bg, pi, sm, warp, lane); break;
-      case 4: batch_item<4>(b, bg, pi, sm, warp, lane); break;
-      default: batch_item<8>(b, bg, pi, sm, warp, lane); break;
+    for (;;) {
+      int u = 0;
+      if (lane == 0) u = atomicAdd(ctr, 1);
+      u = __shfl_sync(0xffffffffu, u, 0);
+      if (u >= units) break;
+      const int tile = u % n_tiles, pi = u / n_tiles;
+      switch (b.T) {
+        case 1: batch_unit<1>(b, sl.bg, tile, pi, sm, lane); break;
+        case 2: batch_unit<2>(b, sl.bg, tile, pi, sm, lane); break;
+        case 4: batch_unit<4>(b, sl.bg, tile, pi, sm, lane); break;
+        default: batch_unit<8>(b, sl.bg, tile, pi, sm, lane); break;
+      }
     }
-    __syncthreads();
+    __syncthreads();  // every warp is done with the staged band before it may be replaced
   }
   if (s_abort) {
     atomicOr(ctl, 1);
@@ -173,8 +184,15 @@ struct lpf_batch {
   std::vector<lpf::BatchDesc> desc;
   lpf::BatchDesc* d_desc = nullptr;
   uint32_t* d_packed = nullptr;
-  int* d_ctl = nullptr;          // [0] status, [2..3] 64-bit work counter
-  int64_t total_items = 0;
+  int* d_ctl = nullptr;          // [0] status, [kBatchCtlUnits + g] unit counter of band group g
+  int ctl_words = 0, ctl_cap = 0;
+  lpf::BatchSlot* d_slots = nullptr;
+  int n_slots = 0;
+  // The batch's own copies of the programs (one per handle and row stride):
+  // evaluating a handle on its own afterwards (another launch shape) re-bakes
+  // the handle's program and must not move the batch's.
+  std::vector<const lpf_paths*> baked_for;
+  std::vector<lpf::Baked> baked;
   uint32_t max_band = 0;
   int blocks = 0;
   int max_pack = 0, max_full = 0;
@@ -190,7 +208,9 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
   size_t packed_total = 0;
   std::vector<size_t> offs(bt->n);
   bt->desc.assign(bt->n, BatchDesc{});
-  int64_t items = 0;
+  std::vector<char> used(bt->baked.size(), 0);
+  int total_bg = 0;
+  std::vector<double> bg_work(bt->n);  // nominal work of one band group of each image
   bt->max_band = 0;
   for (int i = 0; i < bt->n; ++i) {
     lpf_paths* p = bt->paths[i];
@@ -222,26 +242,43 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
     g.packed_words = (size_t)g.rows * g.S + 4;
     rc = ensure_device(p, 0);
     if (rc) return rc;
-    rc = bake(p, p->host.tree, g, p->tree);
+    size_t k = 0;  // this handle's copy for this row stride, else a new slot
+    while (k < bt->baked.size() && !(bt->baked_for[k] == p && bt->baked[k].S == g.S)) ++k;
+    if (k == bt->baked.size()) {
+      bt->baked_for.push_back(p);
+      bt->baked.emplace_back();
+      used.push_back(0);
+    }
+    used[k] = 1;
+    rc = bake(p, p->host.tree, g, bt->baked[k]);
     if (rc) return rc;
     BatchDesc& d = bt->desc[i];
     d.img = imgs[i];
     d.counts = reinterpret_cast<unsigned long long*>(counts[i]);
-    d.prog = p->tree.d_words;
-    d.piece = p->tree.d_piece;
+    d.prog = bt->baked[k].d_words;
+    d.piece = bt->baked[k].d_piece;
     d.n_full = p->host.n_full;
     d.base = p->host.base;
-    d.item0 = items;
+    d.bg0 = total_bg;
     d.H = g.H; d.W = g.W; d.S = g.S; d.nw = g.nw; d.G = g.G; d.BB = g.BB; d.T = g.T; d.r32 = g.r32;
-    d.rows = g.rows; d.nbg = g.nbg; d.n_pieces = p->tree.n_pieces; d.band_bytes = g.band_bytes;
-    items += (int64_t)g.nbg * d.n_pieces;
+    d.rows = g.rows; d.nbg = g.nbg; d.n_pieces = bt->baked[k].n_pieces; d.band_bytes = g.band_bytes;
+    total_bg += g.nbg;
+    bg_work[i] = (double)p->host.tree.n_pixel_words * g.G * g.BB * (g.T + 1);
     offs[i] = packed_total;
     packed_total += (g.packed_words + 3) & ~size_t(3);  // keep every image 16-byte aligned
     bt->max_band = std::max(bt->max_band, g.band_bytes);
     bt->max_pack = std::max<int>(bt->max_pack, (int)std::min<int64_t>(((int64_t)g.rows * g.S + 255) / 256, 64));
     bt->max_full = std::max<int>(bt->max_full, (int)std::min<int64_t>((2 * d.n_full + 255) / 256, 64));
   }
-  bt->total_items = items;
+  // drop the copies no image of this build uses (earlier launch shapes)
+  for (size_t k = bt->baked.size(); k-- > 0;)
+    if (!used[k]) {
+      cudaDeviceSynchronize();
+      cudaFree(bt->baked[k].d_words);
+      cudaFree(bt->baked[k].d_piece);
+      bt->baked.erase(bt->baked.begin() + (std::ptrdiff_t)k);
+      bt->baked_for.erase(bt->baked_for.begin() + (std::ptrdiff_t)k);
+    }
   cudaError_t e;
   if (bt->d_packed) { cudaFree(bt->d_packed); bt->d_packed = nullptr; }
   if ((e = cudaMalloc(&bt->d_packed, std::max<size_t>(16, packed_total * 4))) != cudaSuccess) return set_cuda_error(e);
@@ -249,10 +286,13 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
   if (!bt->d_desc && (e = cudaMalloc(&bt->d_desc, sizeof(BatchDesc) * bt->n)) != cudaSuccess) return set_cuda_error(e);
   if ((e = cudaMemcpy(bt->d_desc, bt->desc.data(), sizeof(BatchDesc) * bt->n, cudaMemcpyHostToDevice)) != cudaSuccess)
     return set_cuda_error(e);
-  if (!bt->d_ctl) {
-    if ((e = cudaMalloc(&bt->d_ctl, 4 * sizeof(int))) != cudaSuccess) return set_cuda_error(e);
-    if ((e = cudaMemset(bt->d_ctl, 0, 4 * sizeof(int))) != cudaSuccess) return set_cuda_error(e);
+  bt->ctl_words = kBatchCtlUnits + total_bg;
+  if (bt->ctl_words > bt->ctl_cap) {
+    if (bt->d_ctl) { cudaFree(bt->d_ctl); bt->d_ctl = nullptr; }
+    if ((e = cudaMalloc(&bt->d_ctl, bt->ctl_words * sizeof(int))) != cudaSuccess) return set_cuda_error(e);
+    bt->ctl_cap = bt->ctl_words;
   }
+  if ((e = cudaMemset(bt->d_ctl, 0, bt->ctl_words * sizeof(int))) != cudaSuccess) return set_cuda_error(e);
   int dev = 0, optin = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -267,17 +307,40 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_walk_kernel, kBatchThreads, bt->max_band)) !=
       cudaSuccess)
     return set_cuda_error(e);
-  bt->blocks = (int)std::min<int64_t>((int64_t)std::max(1, per_sm) * sms, std::max<int64_t>(1, items));
+  const int resident = std::max(1, per_sm) * sms;
+  // Slots: every band group at least one, more in proportion to its work
+  // (about three slots per resident block in all), heaviest band groups first.
+  {
+    std::vector<int> order(bt->n);
+    for (int i = 0; i < bt->n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return bg_work[a] > bg_work[b]; });
+    double total = 0;
+    for (int i = 0; i < bt->n; ++i) total += bg_work[i] * bt->desc[i].nbg;
+    const double per_slot = total / (3.0 * resident);
+    std::vector<BatchSlot> slots;
+    for (int i : order)
+      for (int bg = 0; bg < bt->desc[i].nbg; ++bg) {
+        const int n = std::max(1, (int)std::lround(bg_work[i] / per_slot));
+        for (int c = 0; c < n; ++c) slots.push_back({i, bg, bt->desc[i].bg0 + bg});
+      }
+    bt->n_slots = (int)slots.size();
+    if (bt->d_slots) { cudaFree(bt->d_slots); bt->d_slots = nullptr; }
+    if ((e = cudaMalloc(&bt->d_slots, sizeof(BatchSlot) * slots.size())) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemcpy(bt->d_slots, slots.data(), sizeof(BatchSlot) * slots.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return set_cuda_error(e);
+  }
+  bt->blocks = std::min(resident, bt->n_slots);
   if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
   if (bt->graph) { cudaGraphDestroy(bt->graph); bt->graph = nullptr; }
   return LPF_OK;
 }
 
 static void batch_enqueue(lpf_batch* bt, cudaStream_t s) {
-  cudaMemsetAsync(bt->d_ctl, 0, 4 * sizeof(int), s);
+  cudaMemsetAsync(bt->d_ctl, 0, bt->ctl_words * sizeof(int), s);  // status of this run, unit counters
   batch_zero_kernel<<<dim3(bt->max_full, bt->n), 256, 0, s>>>(bt->d_desc);
   batch_pack_kernel<<<dim3(bt->max_pack, bt->n), 256, 0, s>>>(bt->d_desc);
-  batch_walk_kernel<<<bt->blocks, kBatchThreads, bt->max_band, s>>>(bt->d_desc, bt->n, bt->total_items, bt->d_ctl);
+  batch_walk_kernel<<<bt->blocks, kBatchThreads, bt->max_band, s>>>(bt->d_desc, bt->d_slots, bt->n_slots, bt->d_ctl);
   batch_mirror_kernel<<<dim3(bt->max_full, bt->n), 256, 0, s>>>(bt->d_desc);
 }
 
@@ -405,6 +468,11 @@ void lpf_batch_free(lpf_batch* bt) {
   cudaFree(bt->d_desc);
   cudaFree(bt->d_packed);
   cudaFree(bt->d_ctl);
+  cudaFree(bt->d_slots);
+  for (lpf::Baked& b : bt->baked) {
+    cudaFree(b.d_words);
+    cudaFree(b.d_piece);
+  }
   delete bt;
 }
 

@@ -76,3 +76,24 @@ def test_mixed_sizes_batch_equals_per_image_and_sampled_oracle(gpu_lib):
             for (dx, dy), r in zip(vecs, ref):
                 kk = oracle.full_index(dx, dy, p.rx, p.ry)
                 assert cc[0, kk] == r[0] and cc[1, kk] == r[1]
+
+
+def test_batch_keeps_its_programs_when_the_handles_are_used_alone(gpu_lib):
+    # Evaluating a batch's handles on their own in another launch shape
+    # uploads the handles' programs for another row stride; the batch keeps
+    # its own copies and still gives the oracle's counts.
+    imgs = [synth.ellipses(40, 96, 0.35, seed=1), synth.clustered_disks(64, 64, 0.3, seed=2)]
+    paths = [gpu_lib.lpf_build_paths(W // 2, H // 2) for H, W in (i.shape for i in imgs)]
+    d = [torch.from_numpy(i).cuda() for i in imgs]
+    refs = [oracle.lpf_full(i, p.rx, p.ry) for i, p in zip(imgs, paths)]
+    b = gpu_lib.lpf_batch_create(d, paths, words_per_thread=[8, 1])  # 8 and 2 staged words per row
+    for img, p, dd, r in zip(imgs, paths, d, refs):
+        H, W = img.shape
+        gpu_lib.lpf_set_launch_shape(p, H, W, 4, 1)  # 4 staged words per row: another row stride
+        np.testing.assert_array_equal(gpu_lib.lpf_full(dd, p).cpu().numpy(), r)
+    for use_graph in (False, True):
+        counts = gpu_lib.lpf_batch_run(b, use_graph=use_graph)
+        torch.cuda.synchronize()
+        assert gpu_lib.lpf_batch_status(b) == 0
+        for c, r in zip(counts, refs):
+            np.testing.assert_array_equal(c.cpu().numpy(), r)
