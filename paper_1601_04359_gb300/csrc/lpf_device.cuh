@@ -58,6 +58,12 @@ __device__ __forceinline__ const uint32_t* lane_word(const uint32_t* lane_base, 
   return reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(lane_base) + (pix >> 5));
 }
 
+// The staged word window of a baked pair word ((byte offset << 10) | (shift1
+// << 5) | shift2): one shifted add as well.
+__device__ __forceinline__ const uint32_t* pair_word(const uint32_t* lane_base, uint32_t pair) {
+  return reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(lane_base) + (pair >> 10));
+}
+
 __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

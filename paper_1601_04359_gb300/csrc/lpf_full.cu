@@ -27,10 +27,11 @@
 
 #include "lpf_device.cuh"
 #include "lpf_state.hpp"
+#include "lpf_walk.cuh"
 
 namespace lpf {
 
-constexpr int kDevStack = 24;   // deepest prefix-tree stack the kernels hold
+constexpr int kDevStack = kWalkStack;  // deepest prefix-tree stack the kernels hold
 constexpr int kMaxSmem = 227 * 1024;
 // Control words of a walk: [0] status flags, [2..3] pixel words walked
 // (uint64), [kCtlUnits + bg] the unit counter of band group bg.
@@ -103,7 +104,6 @@ __global__ void mirror_kernel(unsigned long long* __restrict__ counts, int64_t n
   }
 }
 
-// AND of one funnel-shifted image word into both phase masks, for 4 pixels.
 // sel_bits[y][j]: bit b set when translation (32j + b, y) is selected.
 __global__ void pack_sel_kernel(const uint8_t* __restrict__ sel, int H, int W, int nw, uint32_t* __restrict__ bits) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < H * nw; i += gridDim.x * blockDim.x) {
@@ -111,40 +111,6 @@ __global__ void pack_sel_kernel(const uint8_t* __restrict__ sel, int H, int W, i
     uint32_t v = 0;
     for (int b = 0; b < 32 && 32 * j + b < W; ++b) v |= (uint32_t)(sel[(size_t)y * W + 32 * j + b] != 0) << b;
     bits[i] = v;
-  }
-}
-
-template <int T>
-__device__ __forceinline__ void and4(const uint32_t* lane_base, uint4 P, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
-  const uint32_t* sa = lane_word(lane_base, P.x);
-  const uint32_t* sb = lane_word(lane_base, P.y);
-  const uint32_t* sc = lane_word(lane_base, P.z);
-  const uint32_t* sd = lane_word(lane_base, P.w);
-  uint32_t wa[T + 1], wb[T + 1], wc[T + 1], wd[T + 1];
-#pragma unroll
-  for (int t = 0; t <= T; ++t) { wa[t] = sa[t]; wb[t] = sb[t]; wc[t] = sc[t]; wd[t] = sd[t]; }
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], P.x);
-    const uint32_t b = __funnelshift_r(wb[t], wb[t + 1], P.y);
-    const uint32_t c = __funnelshift_r(wc[t], wc[t + 1], P.z);
-    const uint32_t d = __funnelshift_r(wd[t], wd[t + 1], P.w);
-    m1[t] = (m1[t] & a & b) & (c & d);
-    m0[t] = (m0[t] & ~(a | b)) & ~(c | d);
-  }
-}
-
-template <int T>
-__device__ __forceinline__ void and1(const uint32_t* lane_base, uint32_t p, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
-  const uint32_t* sa = lane_word(lane_base, p);
-  uint32_t wa[T + 1];
-#pragma unroll
-  for (int t = 0; t <= T; ++t) wa[t] = sa[t];
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], p);
-    m1[t] &= a;
-    m0[t] &= ~a;
   }
 }
 
@@ -246,23 +212,30 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
         uint32_t skip = 0;
         if (hdr & kEmit) vec = (int)__ldg(prog + pc++);
         if (hdr & (kEmit | kPush)) skip = __ldg(prog + pc++);
+        const int np = (int)__ldg(prog + pc++);  // pixel pairs sharing a staged word window
         pc = (pc + 3) & ~int64_t(3);
         const int n = (int)(hdr & kNpixMask);
         executed += (unsigned)n;
+        const int ns = n - 2 * np;  // np is a multiple of 4
         // the next record's header, fetched while this record's pixels are ANDed
-        hdr_next = pc + n < end ? __ldg(prog + pc + n) : 0u;
+        hdr_next = pc + np + ns < end ? __ldg(prog + pc + np + ns) : 0u;
+        {
+          const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
+          for (int q = 0; q < (np >> 2); ++q) walk_pair4<T>(lane_base, __ldg(q4 + q), m1, m0);
+          pc += np;
+        }
         const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
-        const int n4 = n >> 2;
+        const int n4 = ns >> 2;
         if (n4 > 0) {
           uint4 nxt = __ldg(q4);
           for (int q = 0; q < n4; ++q) {
             const uint4 cur = nxt;
             if (q + 1 < n4) nxt = __ldg(q4 + q + 1);
-            and4<T>(lane_base, cur, m1, m0);
+            walk_and4<T>(lane_base, cur, m1, m0);
           }
         }
-        for (int i = n4 * 4; i < n; ++i) and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
-        pc += n;
+        for (int i = n4 * 4; i < ns; ++i) walk_and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
+        pc += ns;
         if (hdr & (kEmit | kPush)) {
           // Empty for the whole warp (one vote): so is every count below this node.
           uint32_t any = 0;
@@ -349,29 +322,15 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
     b.d_words = nullptr;
     b.d_piece = nullptr;
   }
-  const std::vector<uint32_t>& w = prog.words;
-  std::vector<uint32_t> out(w.size());
-  const std::vector<int16_t>& np = p->host.node_pix;
-  for (size_t i = 0; i < w.size();) {
-    const uint32_t h = w[i];
-    out[i++] = h;
-    for (int k = record_extra_words(h); k > 0; --k) { out[i] = w[i]; ++i; }  // vector id, skip word
-    while (i % 4) { out[i] = w[i]; ++i; }  // alignment padding
-    const uint32_t n = h & kNpixMask;
-    for (uint32_t k = 0; k < n; ++k, ++i) {
-      const int node = (int)w[i];
-      const int sx = np[2 * node], sy = np[2 * node + 1];
-      const int sxp = sx + g.r32;              // >= 0
-      const uint32_t off = (uint32_t)(sy * g.S + (sxp >> 5));
-      out[i] = (off << 7) | (uint32_t)(sxp & 31);  // word offset << 7 | funnel shift
-    }
-  }
+  std::vector<uint32_t> out;
+  std::vector<int64_t> piece;
+  bake_words(p->host, prog, g.S, g.r32, out, piece);
   cudaError_t e;
   if ((e = cudaMalloc(&b.d_words, out.size() * 4)) != cudaSuccess) return set_cuda_error(e);
-  if ((e = cudaMalloc(&b.d_piece, prog.piece_begin.size() * 8)) != cudaSuccess) return set_cuda_error(e);
+  if ((e = cudaMalloc(&b.d_piece, piece.size() * 8)) != cudaSuccess) return set_cuda_error(e);
   if ((e = cudaMemcpy(b.d_words, out.data(), out.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
     return set_cuda_error(e);
-  if ((e = cudaMemcpy(b.d_piece, prog.piece_begin.data(), prog.piece_begin.size() * 8, cudaMemcpyHostToDevice)) !=
+  if ((e = cudaMemcpy(b.d_piece, piece.data(), piece.size() * 8, cudaMemcpyHostToDevice)) !=
       cudaSuccess)
     return set_cuda_error(e);
   b.W = g.W;

@@ -149,6 +149,7 @@ static void emit_records(const std::vector<Event>& ev, Program& prog,
       ++i;
     }
     if (hdr & (kEmit | kPush)) w.push_back((uint32_t)level);  // skip word: the walk level until resolve_skips
+    w.push_back(0u);                                            // pair count (formed when baked)
     hdr |= npix;
     w[hdr_pos] = hdr;
     for (uint32_t q : pixels) w.push_back(q);
@@ -291,6 +292,7 @@ int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err
             tree.words.push_back((uint32_t)li);  // skip word
             ++li;
           }
+          tree.words.push_back(0u);  // pair count
           for (uint32_t n : run) tree.words.push_back(n);
           pix += (int64_t)run.size();
           run.clear();
@@ -339,6 +341,7 @@ int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err
       plain.words.push_back(kReset | kEmit | (uint32_t)chain.size());
       plain.words.push_back((uint32_t)c);
       plain.words.push_back(0u);  // skip word (resolved to the next record)
+      plain.words.push_back(0u);  // pair count
       for (int32_t x : chain) plain.words.push_back((uint32_t)x);
       plain.n_pixel_words += (int64_t)chain.size();
     }
@@ -403,7 +406,7 @@ void resolve_skips(Program& prog) {
       const int64_t w = starts[r];
       const uint32_t h = prog.words[w];
       if (h & (kEmit | kPush)) {
-        const int64_t at = w + record_extra_words(h);  // the skip word is the last extra word
+        const int64_t at = w + record_skip_at(h);
         const uint32_t lv = std::min<uint32_t>(prog.words[at], kMaxStack + 1);
         const int64_t d = nr[lv] - w;
         prog.words[at] = d < (int64_t(1) << 32) ? (uint32_t)d : 0u;  // 0: never skip
@@ -416,6 +419,75 @@ void resolve_skips(Program& prog) {
       }
     }
   }
+}
+
+void bake_words(const Paths& p, const Program& prog, int S, int r32, std::vector<uint32_t>& out,
+                std::vector<int64_t>& piece_out) {
+  const std::vector<uint32_t>& w = prog.words;
+  out.clear();
+  out.reserve(w.size() + w.size() / 16);
+  std::vector<int64_t> old_start, new_start;  // record starts
+  std::vector<std::pair<uint32_t, uint32_t>> pix;  // (byte offset, shift)
+  std::vector<uint32_t> singles;
+  for (size_t i = 0; i < w.size();) {
+    old_start.push_back((int64_t)i);
+    new_start.push_back((int64_t)out.size());
+    const uint32_t h = w[i];
+    const int extra = record_extra_words(h);
+    for (int k = 0; k <= extra; ++k) out.push_back(w[i + k]);  // header, vector id, skip, pair count
+    i += 1 + extra;
+    while (i % 4) ++i;
+    while (out.size() % 4) out.push_back(0u);
+    const uint32_t n = h & kNpixMask;
+    pix.clear();
+    for (uint32_t k = 0; k < n; ++k) {
+      const int node = (int)w[i + k];
+      const int sxp = p.node_pix[2 * node] + r32;  // >= 0
+      const int sy = p.node_pix[2 * node + 1];
+      pix.push_back({(uint32_t)(sy * S + (sxp >> 5)) * 4u, (uint32_t)(sxp & 31)});
+    }
+    i += n;
+    std::stable_sort(pix.begin(), pix.end(),
+                     [](const std::pair<uint32_t, uint32_t>& a, const std::pair<uint32_t, uint32_t>& b) {
+                       return a.first < b.first;
+                     });
+    // pairs in whole groups of 4 (the kernels take them 4 at a time); the
+    // pixels of the pairs left over stay single
+    uint32_t avail = 0;
+    for (size_t k = 0; k + 1 < pix.size();) {
+      if (pix[k].first == pix[k + 1].first) { ++avail; k += 2; } else { k += 1; }
+    }
+    uint32_t n_pairs = 0;
+    const uint32_t want = avail & ~3u;
+    singles.clear();
+    for (size_t k = 0; k < pix.size();) {
+      if (n_pairs < want && k + 1 < pix.size() && pix[k].first == pix[k + 1].first) {
+        out.push_back((pix[k].first << 10) | (pix[k].second << 5) | pix[k + 1].second);
+        ++n_pairs;
+        k += 2;
+      } else {
+        singles.push_back((pix[k].first << 5) | pix[k].second);
+        k += 1;
+      }
+    }
+    out[(size_t)new_start.back() + (size_t)extra] = n_pairs;
+    out.insert(out.end(), singles.begin(), singles.end());
+  }
+  auto relocate = [&](int64_t old_pos) -> int64_t {  // a record start or the program end
+    if (old_pos >= (int64_t)w.size()) return (int64_t)out.size();
+    const auto it = std::lower_bound(old_start.begin(), old_start.end(), old_pos);
+    return new_start[it - old_start.begin()];
+  };
+  for (size_t r = 0; r < old_start.size(); ++r) {
+    const uint32_t h = w[(size_t)old_start[r]];
+    if (!(h & (kEmit | kPush))) continue;
+    const uint32_t d = w[(size_t)old_start[r] + (size_t)record_skip_at(h)];
+    if (d == 0) continue;
+    const int64_t nd = relocate(old_start[r] + d) - new_start[r];
+    out[(size_t)new_start[r] + (size_t)record_skip_at(h)] = nd < (int64_t(1) << 32) ? (uint32_t)nd : 0u;
+  }
+  piece_out.resize(prog.piece_begin.size());
+  for (size_t q = 0; q < prog.piece_begin.size(); ++q) piece_out[q] = relocate(prog.piece_begin[q]);
 }
 
 void split_program(const Paths&, Program& prog, int n_pieces) {

@@ -17,8 +17,15 @@
 namespace lpf {
 
 // Record header word (int32) of a program, then a vector id (emitting
-// records), then a skip word (emitting or pushing records), then zero
-// padding up to the next multiple of 4 words, then the pixel words.
+// records), then a skip word (emitting or pushing records), then a pair
+// count, then zero padding up to the next multiple of 4 words, then the pixel
+// words.  In a program as built the pair count is 0 and the pixel words are
+// prefix-tree node ids; a program baked for an image layout (bake_words)
+// holds first n_pairs pair words (a multiple of 4) -- two pixels of the
+// record that read the same staged word window, (byte offset << 10) |
+// (shift1 << 5) | shift2 -- then the other pixels as single words,
+// (byte offset << 5) | shift.  The ANDs of a record commute, so the order of
+// its pixels is free.
 //   bits  0..13  number of pixel words that follow (n_pix)
 //   bit   14     emit: count the mask into vector `vec`
 //   bit   15     restore: mask <- stack[rlevel] before the pixels
@@ -48,9 +55,15 @@ constexpr int kMaxStack = 32;
 #else
 #define LPF_HOST_DEVICE
 #endif
-// Words between a record's header and its padding (vector id, skip word).
+// Words between a record's header and its padding (vector id, skip word,
+// pair count), and the position of the skip word after the header.
 LPF_HOST_DEVICE inline int record_extra_words(uint32_t hdr) {
-  return ((hdr & kEmit) ? 1 : 0) + ((hdr & (kEmit | kPush)) ? 1 : 0);
+  return 1 + ((hdr & kEmit) ? 1 : 0) + ((hdr & (kEmit | kPush)) ? 1 : 0);
+}
+LPF_HOST_DEVICE inline int record_skip_at(uint32_t hdr) { return 1 + ((hdr & kEmit) ? 1 : 0); }
+// Pixel words of a baked record with n_pix pixels of which 2 n_pairs are paired.
+LPF_HOST_DEVICE inline uint32_t record_pixel_words(uint32_t n_pix, uint32_t n_pairs) {
+  return n_pix - n_pairs;
 }
 
 struct Program {
@@ -101,5 +114,10 @@ void split_program(const Paths& p, Program& prog, int n_pieces);
 void align_program(Program& prog);
 // Fill the skip words of an aligned, split program.
 void resolve_skips(Program& prog);
+// Bake a program for staged rows of S words whose bit e is the pixel at
+// column e - r32: pixel words as above (pairs formed per record), skip words
+// and piece starts remapped to the new layout.
+void bake_words(const Paths& p, const Program& prog, int S, int r32, std::vector<uint32_t>& out,
+                std::vector<int64_t>& piece_out);
 
 }  // namespace lpf

@@ -2,9 +2,9 @@
 // shared by the single-image and the batched walk kernels).
 //
 // The program is a depth-first walk of the prefix tree of the canonical
-// segments (see lpf_paths.hpp for the record format): every pixel word ANDs
-// one funnel-shifted image word into the phase-1 mask and its complement into
-// the phase-0 mask; emit records count both masks (popc, warp sum, one atomic
+// segments (see lpf_paths.hpp for the record format): every pixel ANDs one
+// funnel-shifted image word into the phase-1 mask and its complement into the
+// phase-0 mask (two pixels of a pair word share one staged word window); emit records count both masks (popc, warp sum, one atomic
 // per phase); push/restore records keep branch masks on a small stack.
 #pragma once
 #include <cstdint>
@@ -50,9 +50,28 @@ __device__ __forceinline__ void walk_and1(const uint32_t* lane_base, uint32_t p,
   }
 }
 
-// Walk program words [pc, end) for this warp's T words.  lane_base points at
-// the lane's first staged word (row = lane's translation row); valid[t] masks
-// the translations that exist (x < W, row < H).
+// AND of the two pixels of each of 4 pair words (one staged word window per
+// pair, two funnel shifts) into both phase masks.
+template <int T>
+__device__ __forceinline__ void walk_pair4(const uint32_t* lane_base, uint4 P, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
+  const uint32_t* sa = pair_word(lane_base, P.x);
+  const uint32_t* sb = pair_word(lane_base, P.y);
+  const uint32_t* sc = pair_word(lane_base, P.z);
+  const uint32_t* sd = pair_word(lane_base, P.w);
+  uint32_t wa[T + 1], wb[T + 1], wc[T + 1], wd[T + 1];
+#pragma unroll
+  for (int t = 0; t <= T; ++t) { wa[t] = sa[t]; wb[t] = sb[t]; wc[t] = sc[t]; wd[t] = sd[t]; }
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const uint32_t a1 = __funnelshift_r(wa[t], wa[t + 1], P.x >> 5), a2 = __funnelshift_r(wa[t], wa[t + 1], P.x);
+    const uint32_t b1 = __funnelshift_r(wb[t], wb[t + 1], P.y >> 5), b2 = __funnelshift_r(wb[t], wb[t + 1], P.y);
+    const uint32_t c1 = __funnelshift_r(wc[t], wc[t + 1], P.z >> 5), c2 = __funnelshift_r(wc[t], wc[t + 1], P.z);
+    const uint32_t d1 = __funnelshift_r(wd[t], wd[t + 1], P.w >> 5), d2 = __funnelshift_r(wd[t], wd[t + 1], P.w);
+    m1[t] = (((m1[t] & a1 & a2) & b1 & b2) & c1 & c2) & d1 & d2;
+    m0[t] = (((m0[t] & ~(a1 | a2)) & ~(b1 | b2)) & ~(c1 | c2)) & ~(d1 | d2);
+  }
+}
+
 template <int T>
 __device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, int64_t pc, int64_t end,
                                            const uint32_t* lane_base, const uint32_t (&valid)[T], int lane,
@@ -78,10 +97,16 @@ __device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, in
     uint32_t skip = 0;
     if (hdr & kEmit) vec = (int)__ldg(prog + pc++);
     if (hdr & (kEmit | kPush)) skip = __ldg(prog + pc++);
+    const int np = (int)__ldg(prog + pc++);  // pixel pairs sharing a staged word window
     pc = (pc + 3) & ~int64_t(3);
-    const int n = (int)(hdr & kNpixMask);
+    const int ns = (int)(hdr & kNpixMask) - 2 * np;
+    {  // np is a multiple of 4
+      const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
+      for (int q = 0; q < (np >> 2); ++q) walk_pair4<T>(lane_base, __ldg(q4 + q), m1, m0);
+      pc += np;
+    }
     const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
-    const int n4 = n >> 2;
+    const int n4 = ns >> 2;
     if (n4 > 0) {
       uint4 nxt = __ldg(q4);
       for (int q = 0; q < n4; ++q) {
@@ -90,8 +115,8 @@ __device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, in
         walk_and4<T>(lane_base, cur, m1, m0);
       }
     }
-    for (int i = n4 * 4; i < n; ++i) walk_and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
-    pc += n;
+    for (int i = n4 * 4; i < ns; ++i) walk_and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
+    pc += ns;
     if (hdr & (kEmit | kPush)) {
       // Empty for the whole warp (one vote): so is every count below this node.
       uint32_t any = 0;
