@@ -112,20 +112,36 @@ def _peaks():
         return {}
 
 
-def _source_sha(path: str) -> str:
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+# Sources that decide what the walk kernel executes: the kernel, its shared
+# walk helpers and device utilities, and the program builder / baker.
+WALK_SOURCES = ("lpf_full.cu", "lpf_walk.cuh", "lpf_device.cuh", "lpf_paths.hpp", "lpf_paths.cpp")
+
+
+def _source_sha(paths) -> str:
+    """Hash of the code of the given files, line comments and blank lines
+    removed (comment edits leave a captured kernel's counters valid)."""
+    h = hashlib.sha256()
+    for path in paths:
+        for line in open(path, encoding="utf-8"):
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
+    return h.hexdigest()[:16]
+
+
+def _walk_source_sha() -> str:
+    return _source_sha([os.path.join(ROOT, "paper_1601_04359_gb300", "csrc", f) for f in WALK_SOURCES])
 
 
 def _traffic_record():
     """DRAM bytes per launch of the walk kernel from a committed ncu summary,
-    valid only while the kernel source is unchanged."""
+    valid only while the code the kernel is built from is unchanged."""
     f = os.path.join(ROOT, "profiles", "walk_kernel_512_traffic.json")
     try:
         rec = json.load(open(f))
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_1601_04359_gb300", "csrc", "lpf_full.cu")
-    if rec.get("source_sha") != _source_sha(src):
+    if rec.get("source_sha") != _walk_source_sha():
         return None
     return rec.get("dram_bytes_per_launch")
 

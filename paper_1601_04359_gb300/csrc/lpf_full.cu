@@ -9,15 +9,18 @@
 // row; one funnel-shifted image word serves both phases (the phase-0 mask
 // ANDs its complement).
 //
-// Work split.  A block owns one band of 32 translation rows (lane = row, so
-// the 32 lanes of a warp read 32 different rows: an odd row stride in words
-// puts them in 32 different shared-memory banks) and all words of the row
-// (warp g owns words g*T .. g*T+T-1).  The band's image rows are staged in
-// shared memory with one TMA bulk copy.  Every warp then runs one piece of
-// the evaluation program: a depth-first walk of the prefix tree of all
-// canonical segments, ANDing one shifted image word per tree node and
-// counting (popc + warp sum + one atomic per phase) where a node ends a
-// canonical vector.  Masks of branching nodes are kept on a per-thread stack.
+// Work split.  A tile is 32 translation rows (lane = row, so the 32 lanes of
+// a warp read 32 different rows: an odd row stride in words puts them in 32
+// different shared-memory banks) by T words of translations.  A block stages
+// the image rows of a band group (BB bands of 32 rows, all words of the row)
+// in shared memory with one bulk copy; its warps then take units, one piece
+// of the evaluation program on one tile, from the band group's counter.  The
+// program is a depth-first walk of the prefix tree of all canonical
+// segments: each tree node ANDs one shifted image word (two nodes of a pair
+// share the staged words), a node that ends a canonical vector is counted
+// (popc + warp sum + one atomic per phase), masks of branching nodes are kept
+// on a per-thread stack, and a subtree whose count is zero for the whole tile
+// is skipped.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>

@@ -53,3 +53,24 @@ def test_reference_arm_prints_one_json_line():
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["unit"] == "tests/s" and rec["value"] > 0
     assert rec["cpu_baseline"]["kind"] == "oracle" and rec["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_walk_source_hash_ignores_comments_only(tmp_path):
+    # The committed DRAM-traffic record stays valid across comment edits of the
+    # walk sources and is dropped by any code edit.
+    sys.path.insert(0, ROOT)
+    import bench
+    a, b, c = tmp_path / "a.cu", tmp_path / "b.cu", tmp_path / "c.cu"
+    a.write_text("int f(int x) {\n  return x + 1;  // add one\n}\n")
+    b.write_text("// a new header comment\nint f(int x) {\n\n  return x + 1;  // plus one\n}\n")
+    c.write_text("int f(int x) {\n  return x + 2;  // add one\n}\n")
+    assert bench._source_sha([str(a)]) == bench._source_sha([str(b)])
+    assert bench._source_sha([str(a)]) != bench._source_sha([str(c)])
+
+
+def test_committed_traffic_record_matches_the_walk_sources():
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = json.load(open(os.path.join(ROOT, "profiles", "walk_kernel_512_traffic.json")))
+    assert rec["source_sha"] == bench._walk_source_sha()
+    assert bench._traffic_record() == rec["dram_bytes_per_launch"] > 0
