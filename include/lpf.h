@@ -131,9 +131,10 @@ void lpf_paths_free(lpf_paths *paths);
  * window (Sec. 2.2; Alg. 1/Alg. 2 of Sec. 3.1 with the prefix sharing of
  * Sec. 3.2).  img_dev: H*W uint8 (0/1), counts_dev: int64 full layout
  * [2][n_vec_full], overwritten.  Vectors outside D are filled by the point
- * symmetry of Eq. (symmetry).  A warp that finds a count zero for all its
- * translations skips the segments that extend that one (their counts are
- * zero there too), so the time depends on the image.
+ * symmetry of Eq. (symmetry).  A warp that finds no translation left (at the
+ * end of a prefix, or every 8 pixels inside one) skips the rest of that
+ * prefix and the segments that extend it (their counts are zero there too),
+ * so the time depends on the image.
  * Requires rx < W, ry < H, 1 <= H, W <= 8192.  The first call with a new
  * image width uploads the handle's program for that width and may allocate
  * the handle's device work area (make that first call before any stream
@@ -217,7 +218,9 @@ int lpf_set_launch_shape(lpf_paths *paths, int32_t H, int32_t W, int32_t T, int3
 /*
  * Same as lpf_full but evaluates every segment from scratch, one vector after
  * another (the "standard" evaluation of Sec. 3.2, i.e. Alg. 1 order without
- * any shared work).  Same arguments, layout and errors; for comparison runs.
+ * any shared work; a warp stops a segment once none of its translations is
+ * left, Alg. 1's early break).  Same arguments, layout and errors; for
+ * comparison runs.
  */
 int lpf_full_standard(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
                       int64_t *counts_dev, lpf_stream_t stream);

@@ -222,29 +222,48 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
         const int ns = n - 2 * np;  // np is a multiple of 4
         // the next record's header, fetched while this record's pixels are ANDed
         hdr_next = pc + np + ns < end ? __ldg(prog + pc + np + ns) : 0u;
+        // Every 8 pixels the warp votes: once its tile is empty, the rest of
+        // the record and the subtree below it are zero there (the record's
+        // skip target is the first record after that subtree).
+        bool dead = false;
         {
           const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
-          for (int q = 0; q < (np >> 2); ++q) walk_pair4<T>(lane_base, __ldg(q4 + q), m1, m0);
+          for (int q = 0; q < (np >> 2); ++q) {
+            walk_pair4<T>(lane_base, __ldg(q4 + q), m1, m0);
+            if (skip != 0 && warp_empty<T>(m1, m0)) {
+              dead = true;
+              executed -= (unsigned)(n - 8 * (q + 1));  // pixels not walked
+              break;
+            }
+          }
           pc += np;
         }
         const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
-        const int n4 = ns >> 2;
+        const int n4 = dead ? 0 : ns >> 2;
         if (n4 > 0) {
           uint4 nxt = __ldg(q4);
           for (int q = 0; q < n4; ++q) {
             const uint4 cur = nxt;
             if (q + 1 < n4) nxt = __ldg(q4 + q + 1);
             walk_and4<T>(lane_base, cur, m1, m0);
+            if ((q & 1) && skip != 0 && warp_empty<T>(m1, m0)) {
+              dead = true;
+              executed -= (unsigned)(ns - 4 * (q + 1));  // pixels not walked
+              break;
+            }
           }
         }
-        for (int i = n4 * 4; i < ns; ++i) walk_and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
+        if (!dead)
+          for (int i = n4 * 4; i < ns; ++i) walk_and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
         pc += ns;
+        if (dead) {
+          pc = rec + skip;
+          hdr_next = pc < end ? __ldg(prog + pc) : 0u;
+          continue;
+        }
         if (hdr & (kEmit | kPush)) {
           // Empty for the whole warp (one vote): so is every count below this node.
-          uint32_t any = 0;
-#pragma unroll
-          for (int t = 0; t < T; ++t) any |= m1[t] | m0[t];
-          if (!__any_sync(0xffffffffu, any != 0) && skip != 0) {
+          if (skip != 0 && warp_empty<T>(m1, m0)) {
             pc = rec + skip;
             hdr_next = pc < end ? __ldg(prog + pc) : 0u;
             continue;

@@ -72,6 +72,18 @@ __device__ __forceinline__ void walk_pair4(const uint32_t* lane_base, uint4 P, u
   }
 }
 
+// True when no translation of the warp's tile is left in either phase (one vote).
+template <int T>
+__device__ __forceinline__ bool warp_empty(const uint32_t (&m1)[T], const uint32_t (&m0)[T]) {
+  uint32_t any = 0;
+#pragma unroll
+  for (int t = 0; t < T; ++t) any |= m1[t] | m0[t];
+  return !__any_sync(0xffffffffu, any != 0);
+}
+
+// Walk program words [pc, end) for this warp's T words.  lane_base points at
+// the lane's first staged word (row = lane's translation row); valid[t] masks
+// the translations that exist (x < W, row < H).
 template <int T>
 __device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, int64_t pc, int64_t end,
                                            const uint32_t* lane_base, const uint32_t (&valid)[T], int lane,

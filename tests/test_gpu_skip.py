@@ -31,10 +31,11 @@ def test_work_counter(gpu_lib):
     ex, nom = gpu_lib.lpf_paths_work(p)
     assert 0 < ex < 0.8 * nom
     np.testing.assert_array_equal(c, oracle.lpf_full(synth.chess(48, 48, 10), 47, 47))
-    # the standard program has no shared work: its records are never skipped
+    # the standard program shares no work (more nominal work); a segment stops
+    # once no translation of the tile is left (Alg. 1's early break, per warp)
     cs = _full(gpu_lib, synth.chess(48, 48, 10), p, standard=True)
     ex_s, nom_s = gpu_lib.lpf_paths_work(p)
-    assert ex_s == nom_s > nom
+    assert 0 < ex_s < nom_s and nom_s > nom
     np.testing.assert_array_equal(cs, c)
 
 
