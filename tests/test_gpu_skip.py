@@ -82,3 +82,25 @@ def test_batch_with_skips(gpu_lib):
     assert gpu_lib.lpf_batch_status(b) == 0
     for img, p, c in zip(imgs, paths, counts):
         np.testing.assert_array_equal(c.cpu().numpy(), oracle.lpf_full(img, p.rx, p.ry))
+
+
+def test_skip_with_a_selection_and_an_ensemble(gpu_lib):
+    # The skip tests the tile's selected translations only (Monte-Carlo
+    # variant), and each cut of an ensemble skips on its own.
+    img = synth.chess(64, 96, 10)
+    p = gpu_lib.lpf_build_paths(95, 63)
+    sel = (np.random.default_rng(3).random(img.shape) < 0.1).astype(np.uint8)
+    c = gpu_lib.lpf_full_mc(torch.from_numpy(img).cuda(), p, torch.from_numpy(sel).cuda())
+    torch.cuda.synchronize()
+    assert gpu_lib.lpf_paths_status(p) == 0
+    # with a selection L(v) and L(-v) count different starts: the canonical half
+    # is computed, the other half mirrors it
+    base = p.base
+    np.testing.assert_array_equal(c.cpu().numpy()[:, base:], oracle.lpf_full_selected(img, 95, 63, sel)[:, base:])
+    ex, nom = gpu_lib.lpf_paths_work(p)
+    assert 0 < ex < nom
+    vol = np.stack([synth.chess(64, 96, 10), synth.squares(64, 96, 4, 0.2, seed=7), synth.foam(64, 96, 0.75, seed=5)])
+    e = gpu_lib.lpf_full_ensemble(torch.from_numpy(vol).cuda(), p)
+    torch.cuda.synchronize()
+    ref = sum(oracle.lpf_full(v, 95, 63) for v in vol)
+    np.testing.assert_array_equal(e.cpu().numpy(), ref)
