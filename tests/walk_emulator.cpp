@@ -1,0 +1,150 @@
+// Test infrastructure: a CPU emulation of the walk kernels' semantics on the
+// programs the library builds and bakes (build_paths, bake_words of
+// lpf_paths.cpp), so that -m "not gpu" tests can check the host side -- the
+// prefix-tree program, its pieces and prologues, the skip words and the baked
+// pixel pairs -- against the oracle without a GPU.
+//
+// A "warp" here is 32 translation rows x T words of 32 translations, as in
+// the device kernels: a unit is one program piece on one such tile; masks are
+// ANDed pixel by pixel, counts are added at emitting records, and the walk
+// jumps to a record's skip target when no translation of the tile is left (at
+// the end of an emitting or branching record, or after every 8 pixels inside
+// a record).
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../paper_1601_04359_gb300/csrc/lpf_paths.hpp"
+
+using namespace lpf;
+
+namespace {
+
+inline uint32_t funnel_r(uint32_t lo, uint32_t hi, uint32_t s) {
+  return (uint32_t)(((((uint64_t)hi) << 32) | lo) >> (s & 31u));
+}
+
+}  // namespace
+
+// counts: int64 [2][n_full] (phase 0 first), stats: int64 [4] = {pixels
+// walked, nominal pixels, skips taken, pairs baked}.  Returns 0 or -1.
+extern "C" int emulate_walk(const uint8_t* img, int H, int W, int rx, int ry, int standard, int T,
+                            int64_t* counts, int64_t* stats) {
+  Paths p;
+  std::string err;
+  if (build_paths(rx, ry, 0, p, err)) return -1;
+  const Program& prog = standard ? p.plain : p.tree;
+  const int nw = (W + 31) / 32, G = (nw + T - 1) / T, r32 = ((rx + 31) / 32) * 32;
+  int S = G * T + ((r32 + rx) >> 5) + 1;
+  if (!(S & 1)) ++S;
+  const int nb = (H + 31) / 32, rows = 32 * nb + ry;
+  // packed rows: bit b of word k of row y = pixel (y mod H, (32k + b - r32) mod W)
+  std::vector<uint32_t> packed((size_t)rows * S + 4, 0);
+  for (int y = 0; y < rows; ++y)
+    for (int k = 0; k < S; ++k) {
+      uint32_t bits = 0;
+      for (int b = 0; b < 32; ++b) {
+        const int x = ((32 * k + b - r32) % W + W) % W;
+        bits |= (uint32_t)(img[(y % H) * W + x] != 0) << b;
+      }
+      packed[(size_t)y * S + k] = bits;
+    }
+  std::vector<uint32_t> w;
+  std::vector<int64_t> piece;
+  bake_words(p, prog, S, r32, w, piece);
+  const int64_t nf = p.n_full, base = p.base;
+  std::memset(counts, 0, sizeof(int64_t) * 2 * nf);
+  int64_t walked = 0, skips = 0, pairs = 0;
+  const int L = 32 * T;
+  std::vector<uint32_t> valid(L), m1(L), m0(L), st1((kMaxStack + 1) * L), st0((kMaxStack + 1) * L);
+  auto empty = [&]() {
+    for (int i = 0; i < L; ++i)
+      if (m1[i] | m0[i]) return false;
+    return true;
+  };
+  for (int band = 0; band < nb; ++band)
+    for (size_t pi = 0; pi + 1 < piece.size(); ++pi)
+      for (int g = 0; g < G; ++g) {
+        for (int lane = 0; lane < 32; ++lane)
+          for (int t = 0; t < T; ++t) {
+            const int y = band * 32 + lane, j = g * T + t;
+            uint32_t v = 0;
+            if (y < H && j < nw) {
+              const int rem = W - 32 * j;
+              v = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+            }
+            valid[lane * T + t] = m1[lane * T + t] = m0[lane * T + t] = v;
+          }
+        auto and_pixel = [&](uint32_t word, bool pair) {
+          for (int lane = 0; lane < 32; ++lane) {
+            const uint32_t* lb = packed.data() + (size_t)(band * 32 + lane) * S + g * T;
+            const uint32_t* sa = lb + ((pair ? (word >> 10) : (word >> 5)) >> 2);  // byte offset -> word
+            for (int t = 0; t < T; ++t) {
+              const uint32_t a1 = funnel_r(sa[t], sa[t + 1], pair ? (word >> 5) : word);
+              const uint32_t a2 = pair ? funnel_r(sa[t], sa[t + 1], word) : a1;
+              m1[lane * T + t] &= a1 & a2;
+              m0[lane * T + t] &= ~(a1 | a2);
+            }
+          }
+        };
+        int64_t pc = piece[pi];
+        const int64_t end = piece[pi + 1];
+        while (pc < end) {
+          const int64_t rec = pc;
+          const uint32_t h = w[pc++];
+          if (h & kReset) { m1 = valid; m0 = valid; }
+          if (h & kRestore) {
+            const int l = (h >> kRlevelShift) & kLevelMask;
+            for (int i = 0; i < L; ++i) { m1[i] = st1[l * L + i]; m0[i] = st0[l * L + i]; }
+          }
+          int vec = -1;
+          uint32_t skip = 0;
+          if (h & kEmit) vec = (int)w[pc++];
+          if (h & (kEmit | kPush)) skip = w[pc++];
+          const int np = (int)w[pc++];
+          pc = (pc + 3) & ~int64_t(3);
+          const int n = (int)(h & kNpixMask), ns = n - 2 * np;
+          pairs += np;
+          bool dead = false;
+          int done = 0;
+          for (int q = 0; q < np / 4 && !dead; ++q) {
+            for (int k = 0; k < 4; ++k) and_pixel(w[pc + 4 * q + k], true);
+            done += 8;
+            if (skip && empty()) dead = true;
+          }
+          const int64_t ps = pc + np;
+          const int n4 = dead ? 0 : ns / 4;
+          for (int q = 0; q < n4 && !dead; ++q) {
+            for (int k = 0; k < 4; ++k) and_pixel(w[ps + 4 * q + k], false);
+            done += 4;
+            if ((q & 1) && skip && empty()) dead = true;
+          }
+          if (!dead)
+            for (int i = n4 * 4; i < ns; ++i) { and_pixel(w[ps + i], false); ++done; }
+          walked += done;
+          pc = ps + ns;
+          if (dead) { pc = rec + skip; ++skips; continue; }
+          if (h & (kEmit | kPush)) {
+            if (skip && empty()) { pc = rec + skip; ++skips; continue; }
+            if (vec >= 0) {
+              int64_t c0 = 0, c1 = 0;
+              for (int i = 0; i < L; ++i) { c0 += __builtin_popcount(m0[i]); c1 += __builtin_popcount(m1[i]); }
+              counts[base + vec] += c0;
+              counts[nf + base + vec] += c1;
+            }
+          }
+          if (h & kPush) {
+            const int l = (h >> kPlevelShift) & kLevelMask;
+            for (int i = 0; i < L; ++i) { st1[l * L + i] = m1[i]; st0[l * L + i] = m0[i]; }
+          }
+        }
+      }
+  for (int64_t j = base + 1; j < nf; ++j)
+    for (int q = 0; q < 2; ++q) counts[q * nf + nf - 1 - j] = counts[q * nf + j];
+  stats[0] = walked;
+  stats[1] = prog.n_pixel_words * (int64_t)nb * G;
+  stats[2] = skips;
+  stats[3] = pairs;
+  return 0;
+}
