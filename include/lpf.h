@@ -155,10 +155,10 @@ int lpf_full(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
  * and give libraries fixed budgets, and real-time or pipelined loops where a
  * cudaMalloc -- which can synchronise the whole device -- is not allowed.
  * Same arguments, layout and results as lpf_full; this call performs no
- * cudaMalloc, cudaFree or other allocation.  Its work area (packed image rows
- * and a work counter) is a fixed array of 1 MiB (2^18 words of packed rows)
- * compiled into the library, which every GPU that loads the library holds
- * until the process exits.
+ * cudaMalloc, cudaFree or other allocation.  Its work area (packed image
+ * rows and the walk's control words) is a fixed array of 1 MiB (2^18 words
+ * of packed rows) compiled into the library, which every GPU that loads the
+ * library holds until the process exits.
  *   - Size limit: the packed, periodically extended image must fit in 2^18
  *     words; it takes roughly (H + ry) * (W + 2*rx) / 32 words plus a few
  *     rows and columns of padding (512x512 with |v| <= 256: 25,348 words).
@@ -170,7 +170,7 @@ int lpf_full(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
  *     (once per device, with that device current); make that first call
  *     before any stream capture.
  *   - Sharing: every call on a device uses the same fixed array and leaves
- *     its contents behind (each call clears the work counter it needs).
+ *     its contents behind (each call clears the control words it needs).
  *     Calls whose work overlaps on the GPU -- on different streams, or from
  *     different host threads without ordering -- race on that array and give
  *     wrong counts; order them on one stream.

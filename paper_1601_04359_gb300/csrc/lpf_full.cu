@@ -542,7 +542,8 @@ static int autotune_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t
 // Full evaluation without allocating.
 //
 // lpf_full keeps its per-call work area (the packed image rows and the
-// counter of the persistent work queue) in device memory that the handle
+// walk's control words: status, walked-work and unit counters) in device
+// memory that the handle
 // allocates on first use.  Some callers cannot let a library allocate at the
 // time they evaluate: a host application that owns every device allocation
 // and hands out fixed budgets, a real-time loop where cudaMalloc (which can
