@@ -75,3 +75,13 @@ def test_skips_and_pairs_are_exercised(emulator):
     assert pairs > 0
     _, stats = _walk(emulator, np.ones((20, 33), np.uint8), 19, 19, standard=False, T=2)
     assert stats[0] == stats[1] and stats[2] == 0  # nothing to skip when every segment fits
+
+
+def test_wide_tiles(emulator):
+    # 4 and 8 words per thread: wider staged rows, other pixel pairs
+    img = synth.ellipses(40, 200, 0.35, seed=5)
+    ref = oracle.lpf_full(img, 70, 25)
+    for T in (4, 8):
+        got, stats = _walk(emulator, img, 70, 25, standard=False, T=T)
+        np.testing.assert_array_equal(got, ref, err_msg=f"T={T}")
+        assert stats[3] > 0
