@@ -7,9 +7,14 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  *  Image     uint8, H rows x W columns, row-major: pixel (x, y) is img[y*W + x]
- *            (x = column, y = row).  Values must be 0 or 1; "phase p" is the
+ *            (x = column, y = row).  Values are 0 or 1; "phase p" is the
  *            set of pixels with value p.  The medium is periodic: coordinates
  *            wrap modulo W and H (the "%" convention of Eq. (S2dis), Sec. 2.1).
+ *            Other byte values: by default (unchecked) every nonzero byte is
+ *            read as phase 1; in checked mode (lpf_set_checked) a kernel that
+ *            reads the image also raises a status flag that lpf_paths_status
+ *            reports as LPF_EPIXEL, and the results of that call are not to
+ *            be used.
  *  Vectors   v = (dx, dy), dx a column offset, dy a row offset, in the window
  *            |dx| <= rx, |dy| <= ry with 0 <= rx < W and 0 <= ry < H.  The
  *            paper's full domain is rx = W-1, ry = H-1 (Eq. (segments), Sec. 2.2).
@@ -54,6 +59,7 @@ extern "C" {
 #define LPF_ECUDA (-3)       /* a CUDA runtime call failed (no device, launch error) */
 #define LPF_ETIMEOUT (-4)    /* a device-side bounded wait gave up (see lpf_paths_status) */
 #define LPF_EUNSUPPORTED (-5) /* size beyond what the kernels support (shared memory, width) */
+#define LPF_EPIXEL (-6)      /* a pixel other than 0 or 1 was read in checked mode (see lpf_set_checked) */
 
 typedef struct CUstream_st *lpf_stream_t; /* same type as cudaStream_t */
 typedef struct lpf_paths lpf_paths;        /* opaque, owned by the library */
@@ -127,6 +133,20 @@ int lpf_paths_work(const lpf_paths *paths, int64_t *executed, int64_t *nominal);
 void lpf_paths_free(lpf_paths *paths);
 
 /*
+ * Checked mode of a handle (default off).  on = 1: every later device call
+ * with this handle that reads an image (lpf_full, lpf_full_noalloc,
+ * lpf_full_mc, lpf_full_standard, lpf_full_ensemble, lpf_delta_swap,
+ * lpf_delta_swap_mc, and the count set-up of lpf_sa_create /
+ * lpf_sa_create_mc) also checks that every pixel byte is 0 or 1; a byte
+ * outside {0, 1} sets a device status flag that the next lpf_paths_status
+ * returns as LPF_EPIXEL (the Sec. 2.2 definition covers two-phase images
+ * only, so such a call's results are not to be used).  The check costs one
+ * compare per staged byte in kernels that read the image anyway.  on = 0:
+ * no check; nonzero bytes are phase 1.  Host-only.  Errors: LPF_EINVAL.
+ */
+int lpf_set_checked(lpf_paths *paths, int32_t on);
+
+/*
  * Full lineal path counts of both phases for every vector of the handle's
  * window (Sec. 2.2; Alg. 1/Alg. 2 of Sec. 3.1 with the prefix sharing of
  * Sec. 3.2).  img_dev: H*W uint8 (0/1), counts_dev: int64 full layout
@@ -158,14 +178,19 @@ int lpf_full(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
  * cudaMalloc, cudaFree or other allocation.  Its work area (packed image
  * rows and the walk's control words) is a fixed array of 1 MiB (2^18 words
  * of packed rows) compiled into the library, which every GPU that loads the
- * library holds until the process exits.
+ * library holds until the process exits.  Checked mode (lpf_set_checked)
+ * applies as for lpf_full.
  *   - Size limit: the packed, periodically extended image must fit in 2^18
  *     words; it takes roughly (H + ry) * (W + 2*rx) / 32 words plus a few
  *     rows and columns of padding (512x512 with |v| <= 256: 25,348 words).
  *     Larger images return LPF_EUNSUPPORTED.
  *   - Set-up: the handle's program for this image size must already be on the
  *     current device -- call lpf_full (or lpf_autotune_full) once for this
- *     H, W during set-up; otherwise LPF_EINVAL.  The first call of this
+ *     H, W during set-up; otherwise LPF_EINVAL.  The walk runs in the launch
+ *     shape lpf_full would use (tuned or set), or, where that shape needs
+ *     another row layout than the program on the device was prepared for
+ *     (e.g. lpf_set_launch_shape after the set-up call), in the shape it was
+ *     prepared for.  The first call of this
  *     function on a device looks up the device address of the fixed array
  *     (once per device, with that device current); make that first call
  *     before any stream capture.
@@ -174,8 +199,10 @@ int lpf_full(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
  *     Calls whose work overlaps on the GPU -- on different streams, or from
  *     different host threads without ordering -- race on that array and give
  *     wrong counts; order them on one stream.
- *   - A device-side wait timeout is not reported by lpf_paths_status for
- *     this variant.
+ *   - Status: a bounded wait that gave up, or a pixel outside {0, 1} in
+ *     checked mode, sets a flag in the fixed array's status word; the next
+ *     lpf_paths_status on this device, with any handle, reports it
+ *     (LPF_ETIMEOUT, LPF_EPIXEL) and clears it.
  * Errors: LPF_EINVAL, LPF_EUNSUPPORTED, LPF_ECUDA.
  */
 int lpf_full_noalloc(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
@@ -205,6 +232,18 @@ int lpf_full_mc(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths, 
  */
 int lpf_autotune_full(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *paths,
                       int64_t *counts_dev, lpf_stream_t stream, int32_t *best_T, int32_t *best_BB);
+
+/*
+ * Failure-detection self-test of the walk kernel (no counterpart in the
+ * paper).  on = 1: later lpf_full / lpf_full_noalloc calls with this handle
+ * make each block's wait for its staging copy expect 16 bytes more than the
+ * copy delivers and give up after 2^16 try_wait rounds (instead of 2^24), so
+ * every wait runs out (milliseconds to seconds); the kernel then records the
+ * timeout and returns, the counts are incomplete, and lpf_paths_status
+ * reports LPF_ETIMEOUT.  on = 0 restores normal waits.  Faults nothing; for
+ * tests only.  Host-only.  Errors: LPF_EINVAL.
+ */
+int lpf_paths_set_selftest(lpf_paths *paths, int32_t on);
 
 /*
  * Fix the walk-kernel launch shape used by lpf_full for images of size H x W
@@ -441,9 +480,12 @@ int lpf_sa_create_mc(uint8_t *cell_dev, int32_t H, int32_t W, lpf_paths *paths, 
  */
 int lpf_sa_run(lpf_sa *sa, int32_t n_batches, lpf_stream_t stream);
 
-/* Synchronise `stream` and copy the run's counters to *out; LPF_ETIMEOUT
- * (counters still copied, state not to be trusted) if a bounded wait in a
- * batch kernel gave up (staging copy or grid barrier). */
+/* Synchronise `stream` and copy the run's counters to *out.  LPF_ETIMEOUT if
+ * a bounded wait in a batch kernel gave up (staging copy or grid barrier)
+ * since the last read: the library has then already made the state
+ * consistent again -- counts recomputed from the cell, the error from the
+ * counts, the run's counters those of the cell's last applied batch -- so
+ * the run can continue; the flag is cleared (reported once). */
 int lpf_sa_read(lpf_sa *sa, lpf_sa_stats *out, lpf_stream_t stream);
 
 /*
@@ -486,15 +528,20 @@ int lpf_sa_propose(lpf_sa *sa, int32_t k, int32_t *pairs_dev, float *u_dev, lpf_
 /*
  * Check of the annealer's failure detection (no counterpart in the paper):
  * runs one batch of the persistent kernel whose grid barrier waits for one
- * block arrival more than the grid makes, so that every block's bounded wait
- * runs out (about a second or two), and returns LPF_OK when the kernel
- * reported the timeout through the status word and left the run state
- * unchanged; the status is cleared afterwards, so the run continues as if
- * the call had not happened.  Synchronises.  LPF_EUNSUPPORTED when the run
- * does not use the persistent kernel; LPF_ETIMEOUT if an earlier wait had
+ * block arrival more than the grid makes -- in every block (block = -1) or in
+ * block `block` only (0 <= block < the kernel's grid, the others pass and
+ * apply the batch's decision to their vector chunks) -- so that those
+ * blocks' bounded waits run out (about a second or two).  Then it restores a
+ * consistent state as lpf_sa_read does (counts recomputed from the cell) and
+ * clears the status.  Returns LPF_OK when the kernel reported the timeout
+ * and the run state is that of before the batch (block = -1 or 0: block 0,
+ * which keeps the state, gave up) or that after it (another block gave up);
+ * the run continues as the sequential annealer would from that cell.
+ * Synchronises.  LPF_EUNSUPPORTED when the run does not use the persistent
+ * kernel; LPF_EINVAL for a bad block; LPF_ETIMEOUT if an earlier wait had
  * already failed; LPF_ECUDA if the timeout was not reported.
  */
-int lpf_sa_selftest_timeout(lpf_sa *sa, lpf_stream_t stream);
+int lpf_sa_selftest_timeout(lpf_sa *sa, int32_t block, lpf_stream_t stream);
 
 /* Release a run (NULL is ignored); synchronises the device. */
 void lpf_sa_free(lpf_sa *sa);
@@ -635,10 +682,12 @@ int lpf_sa_set_proposer(lpf_sa *sa, lpf_cnn *cnn, float epsilon, float tau, int3
 int lpf_paths_set_timer(lpf_paths *paths, void *ev_start, void *ev_stop);
 
 /*
- * Device-side status of the handle's last calls: synchronises `stream`,
- * returns LPF_ETIMEOUT if a bounded wait inside a kernel gave up, LPF_EINVAL
- * if a kernel met an out-of-range pixel index, since the last check (and
- * clears the flags), LPF_OK otherwise.
+ * Device-side status of the handle's last calls (and of lpf_full_noalloc
+ * calls on the current device): synchronises `stream`, returns LPF_ETIMEOUT
+ * if a bounded wait inside a kernel gave up, else LPF_EPIXEL if a kernel read
+ * a pixel other than 0 or 1 in checked mode, else LPF_EINVAL if a kernel met
+ * an out-of-range pixel index, since the last check (and clears the flags),
+ * LPF_OK otherwise.  Errors: LPF_EINVAL (paths == NULL), LPF_ECUDA.
  */
 int lpf_paths_status(lpf_paths *paths, lpf_stream_t stream);
 

@@ -39,6 +39,7 @@ def _load():
         lib = ctypes.CDLL(path)
         i32, i64, p = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
         lib.lpfo_num_threads.restype = i32
+        lib.lpfo_set_num_threads.argtypes = [i32]
         lib.lpfo_segment.argtypes = [i32, i32, p, p]
         lib.lpfo_segment.restype = i32
         lib.lpfo_count.argtypes = [p, i32, i32, i32, i32, i32]
@@ -64,6 +65,11 @@ def _ptr(a: np.ndarray) -> int:
 def num_threads() -> int:
     """Threads the oracle's OpenMP loops use."""
     return int(_load().lpfo_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's later OpenMP loops (for timing it on one core)."""
+    _load().lpfo_set_num_threads(int(n))
 
 
 def window_sizes(rx: int, ry: int):

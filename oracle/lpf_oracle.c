@@ -34,6 +34,15 @@
 static int imod(int a, int m) { int r = a % m; return r < 0 ? r + m : r; }
 static int iabs(int a) { return a < 0 ? -a : a; }
 
+/* Threads of later OpenMP loops (n >= 1); for timing the oracle on one core. */
+void lpfo_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int lpfo_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

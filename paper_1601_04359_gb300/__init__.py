@@ -26,8 +26,11 @@ __all__ = [
     "lpf_cnn_set_loss", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create",
     "lpf_cnn_set_params", "lpf_cnn_get_params", "lpf_cnn_forward", "lpf_cnn_gradients", "lpf_cnn_train_step",
     "lpf_sa_set_proposer", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune",
-    "lpf_batch_status",
+    "lpf_batch_status", "lpf_set_checked", "lpf_paths_set_selftest", "LPF_EPIXEL", "LPF_ETIMEOUT",
 ]
+
+LPF_ETIMEOUT = -4
+LPF_EPIXEL = -6
 
 _lib = None
 LIB_PATH = _build.LIB
@@ -110,7 +113,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_full_ensemble": (ctypes.c_int, [p, i32, i32, i32, p, p, p]),
         "lpf_delta_swap_mc": (ctypes.c_int, [p, i32, i32, p, p, p, i32, p, p, p, p, p]),
         "lpf_sa_create_mc": (ctypes.c_int, [p, i32, i32, p, p, p, p, ctypes.POINTER(SaParams), p, ctypes.POINTER(p)]),
-        "lpf_sa_selftest_timeout": (ctypes.c_int, [p, p]),
+        "lpf_sa_selftest_timeout": (ctypes.c_int, [p, i32, p]),
+        "lpf_set_checked": (ctypes.c_int, [p, i32]),
+        "lpf_paths_set_selftest": (ctypes.c_int, [p, i32]),
         "s2_delta_swap": (ctypes.c_int, [p, i32, i32, p, i32, p, p, p, p, p]),
         "s2_sa_create": (ctypes.c_int, [p, i32, i32, p, p, ctypes.POINTER(SaParams), p, ctypes.POINTER(p)]),
         "lpf_cnn_create": (ctypes.c_int, [i32, i32, ctypes.c_uint64, ctypes.POINTER(p)]),
@@ -261,6 +266,16 @@ def lpf_autotune_full(img, paths: Paths, counts=None, stream=None):
 
 def lpf_set_launch_shape(paths: Paths, H: int, W: int, T: int, BB: int):
     _check(load().lpf_set_launch_shape(paths.handle, int(H), int(W), int(T), int(BB)), "lpf_set_launch_shape")
+
+
+def lpf_set_checked(paths: Paths, on: bool = True):
+    """Checked mode: kernels that read an image flag pixels other than 0/1 (lpf_paths_status -> LPF_EPIXEL)."""
+    _check(load().lpf_set_checked(paths.handle, int(bool(on))), "lpf_set_checked")
+
+
+def lpf_paths_set_selftest(paths: Paths, on: bool = True):
+    """Failure-detection self-test of the walk kernel's staging wait (tests only)."""
+    _check(load().lpf_paths_set_selftest(paths.handle, int(bool(on))), "lpf_paths_set_selftest")
 
 
 def lpf_full_ensemble(imgs, paths: Paths, counts=None, stream=None):
@@ -480,10 +495,11 @@ def load_checkpoint(path: str, paths: Paths, target, k_max=4096, k_min=1, phases
     return ann
 
 
-def lpf_sa_selftest_timeout(sa: Annealer, stream=None) -> int:
+def lpf_sa_selftest_timeout(sa: Annealer, block: int = -1, stream=None) -> int:
     """Status code of the annealer's timeout check (0: the bounded grid-barrier
-    wait ran out, was reported, and left the run unchanged)."""
-    return int(load().lpf_sa_selftest_timeout(sa.handle, _stream_ptr(stream)))
+    wait of every block (block=-1) or of one block ran out, was reported, and
+    the run state was made consistent again)."""
+    return int(load().lpf_sa_selftest_timeout(sa.handle, int(block), _stream_ptr(stream)))
 
 
 def lpf_sa_propose(sa: Annealer, k: int, stream=None):

@@ -35,20 +35,26 @@
 
 namespace lpf {
 
-// ext[ey][ex] = img[(ey - ry) mod H][(ex - rx) mod W]; zero padding to `bytes`.
+// ext[ey][ex] = (img[(ey - ry) mod H][(ex - rx) mod W] != 0); zero padding to
+// `bytes`.  pix_flag != null (checked mode): a byte other than 0 or 1 sets
+// status bit 8 in *pix_flag.
 __global__ void build_ext_kernel(const uint8_t* __restrict__ img, int H, int W, int rx, int ry, int We, int He,
-                                 uint32_t bytes, uint8_t* __restrict__ ext) {
+                                 uint32_t bytes, uint8_t* __restrict__ ext, int* __restrict__ pix_flag) {
   const int total = We * He;
+  uint32_t high = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)bytes; i += gridDim.x * blockDim.x) {
     uint8_t v = 0;
     if (i < total) {
       const int ey = i / We, ex = i - ey * We;
       int y = (ey - ry) % H; if (y < 0) y += H;
       int x = (ex - rx) % W; if (x < 0) x += W;
-      v = img[y * W + x];
+      const uint32_t raw = img[y * W + x];
+      high |= raw >> 1;
+      v = raw != 0;
     }
     ext[i] = v;
   }
+  if (pix_flag && high) atomicOr(pix_flag, 8);
 }
 
 __global__ void __launch_bounds__(kDeltaThreads, 3) delta_kernel(const uint8_t* __restrict__ img,
@@ -75,7 +81,7 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) delta_kernel(const uint8_t* 
       int a = pairs[2 * k], b = pairs[2 * k + 1];
       int skip = 0;
       if (a < 0 || b < 0 || a >= npix || b >= npix) { skip = 1; atomicOr(status, 2); }
-      else if (img[a] == img[b]) skip = 1;                       // same phase (or a == b): identity
+      else if ((img[a] != 0) == (img[b] != 0)) skip = 1;         // same phase (or a == b): identity
       else if (img[a] == 0) { const int t = a; a = b; b = t; }   // a holds phase 1
       s_a = a; s_b = b; s_skip = skip;
       if (!skip) { delta_mark(sm, a, kMarkA, g); delta_mark(sm, b, kMarkB, g); }
@@ -284,7 +290,8 @@ int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* path
   if (inv_norm > 0.0f) g.inv_norm = inv_norm;
   {
     const int blocks = (int)std::min<int64_t>((g.ext_bytes + 255) / 256, 4096);
-    build_ext_kernel<<<blocks, 256, 0, s>>>(img_dev, H, W, g.rx, g.ry, g.We, g.He, g.ext_bytes, paths->d_ext);
+    build_ext_kernel<<<blocks, 256, 0, s>>>(img_dev, H, W, g.rx, g.ry, g.We, g.He, g.ext_bytes, paths->d_ext,
+                                            paths->checked ? paths->d_status : nullptr);
   }
   const dim3 grid(g.n_chunks, delta_stride(g.n_chunks, K));
   if (paths->ev_start) cudaEventRecord(paths->ev_start, s);
@@ -335,7 +342,7 @@ int build_sel_ext(const uint8_t* sel_dev, int H, int W, const lpf_paths* paths, 
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(out), g.ext_bytes, s);
   if (e != cudaSuccess) return set_cuda_error(e);
   const int blocks = (int)std::min<int64_t>((g.ext_bytes + 255) / 256, 4096);
-  build_ext_kernel<<<blocks, 256, 0, s>>>(sel_dev, H, W, g.rx, g.ry, g.We, g.He, g.ext_bytes, *out);
+  build_ext_kernel<<<blocks, 256, 0, s>>>(sel_dev, H, W, g.rx, g.ry, g.We, g.He, g.ext_bytes, *out, nullptr);
   return set_cuda_error(cudaGetLastError());
 }
 

@@ -34,9 +34,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Wait for phase `parity` of `bar`; false when the bounded wait gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kWaitRounds; ++it) {
+// Wait for phase `parity` of `bar`; false when the bounded wait (`rounds`
+// try_wait rounds) gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t rounds = kWaitRounds) {
+  for (uint32_t it = 0; it < rounds; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"

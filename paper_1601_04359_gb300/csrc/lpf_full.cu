@@ -39,6 +39,10 @@ constexpr int kMaxSmem = 227 * 1024;
 // Control words of a walk: [0] status flags, [2..3] pixel words walked
 // (uint64), [kCtlUnits + bg] the unit counter of band group bg.
 constexpr int kCtlExecuted = 2;
+// Bits of the status word ctl[0]: a bounded wait gave up (1), an index out of
+// range (2, swap deltas), a pixel other than 0 or 1 in checked mode (8).
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusPixel = 8;
 constexpr int kCtlUnits = 4;
 constexpr int kMaxBandGroups = (8192 + 31) / 32;
 constexpr int kCtlWords = kCtlUnits + kMaxBandGroups;
@@ -71,17 +75,21 @@ int make_geometry(int H, int W, int rx, int ry, int T, int BB, Geometry& g) {
 // ---------------------------------------------------------------------------
 // Kernels
 
-// packed[y][k]: bit b is the pixel at row y mod H, column (32k + b - r32) mod W.
-// Also zeroes the walk's n_zero64 counts and n_zero32 control words (which
-// would otherwise take two more launches).
+// packed[y][k]: bit b is the pixel at row y mod H, column (32k + b - r32) mod W
+// (any nonzero byte is phase 1).  Also zeroes the walk's n_zero64 counts and
+// n_zero32 control words (which would otherwise take two more launches).
+// pix_flag != null (checked mode): a byte other than 0 or 1 sets kStatusPixel
+// in *pix_flag.
 __global__ void pack_rows_kernel(const uint8_t* __restrict__ img, int H, int W, int r32, int S, int rows,
                                  uint32_t* __restrict__ packed, unsigned long long* __restrict__ zero64,
-                                 int64_t n_zero64, int* __restrict__ zero32, int n_zero32) {
+                                 int64_t n_zero64, int* __restrict__ zero32, int n_zero32,
+                                 int* __restrict__ pix_flag) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   for (int64_t i = i0; i < n_zero64; i += stride) zero64[i] = 0ull;
   for (int64_t i = i0; i < n_zero32; i += stride) zero32[i] = 0;
   const int64_t total = (int64_t)rows * S;
+  uint32_t high = 0;  // OR of the bytes' bits above bit 0
   for (int64_t i = i0; i < total; i += stride) {
     const int y = (int)(i / S), k = (int)(i % S);
     const uint8_t* row = img + (int64_t)(y % H) * W;
@@ -90,11 +98,14 @@ __global__ void pack_rows_kernel(const uint8_t* __restrict__ img, int H, int W, 
     uint32_t bits = 0;
 #pragma unroll 4
     for (int b = 0; b < 32; ++b) {
-      bits |= (uint32_t)(row[x] != 0) << b;
+      const uint32_t v = row[x];
+      bits |= (uint32_t)(v != 0) << b;
+      high |= v >> 1;
       if (++x == W) x = 0;
     }
     packed[i] = bits;
   }
+  if (pix_flag && high) atomicOr(pix_flag, kStatusPixel);
 }
 
 // counts[p][n_full-1-i] = counts[p][i] for the canonical entries i > base
@@ -136,7 +147,8 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
                                                   const int64_t* __restrict__ piece,
                                                   unsigned long long* __restrict__ counts, int64_t n_full,
                                                   int64_t base, int* __restrict__ ctl,
-                                                  const uint32_t* __restrict__ sel) {
+                                                  const uint32_t* __restrict__ sel, uint32_t extra_tx,
+                                                  uint32_t wait_rounds) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_abort, s_done;
@@ -160,11 +172,12 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
     }
     if (threadIdx.x == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(&bar, band_bytes);
+      // (extra_tx > 0 only in the failure-detection self-test: bytes no copy delivers)
+      mbar_expect_tx(&bar, band_bytes + extra_tx);
       bulk_g2s(sm, packed + (size_t)bg * 32 * BB * S, band_bytes, &bar);
     }
     copy_pending = true;
-    if (mbar_wait(&bar, parity)) copy_pending = false;
+    if (mbar_wait(&bar, parity, wait_rounds)) copy_pending = false;
     else s_abort = 1;
     parity ^= 1u;
     __syncthreads();
@@ -291,8 +304,8 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
   }
   if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(ctl + kCtlExecuted), executed);
   if (s_abort) {
-    atomicOr(ctl, 1);
-    if (copy_pending) (void)mbar_wait(&bar, parity ^ 1u);  // let an outstanding copy land
+    atomicOr(ctl, kStatusTimeout);
+    if (copy_pending) (void)mbar_wait(&bar, parity ^ 1u, wait_rounds);  // let an outstanding copy land
   }
 }
 
@@ -336,7 +349,11 @@ int ensure_device(lpf_paths* p, size_t packed_words) {
 }
 
 int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
-  if (b.d_words && b.W == g.W && b.S == g.S && b.r32 == g.r32) return LPF_OK;
+  if (b.d_words && b.W == g.W && b.S == g.S && b.r32 == g.r32) {
+    b.T = g.T;
+    b.BB = g.BB;
+    return LPF_OK;
+  }
   if (b.d_words) {
     cudaDeviceSynchronize();
     cudaFree(b.d_words);
@@ -358,6 +375,8 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
   b.W = g.W;
   b.S = g.S;
   b.r32 = g.r32;
+  b.T = g.T;
+  b.BB = g.BB;
   b.n_pieces = (int)prog.piece_begin.size() - 1;
   return LPF_OK;
 }
@@ -401,12 +420,18 @@ static int walk_blocks(const Geometry& g) {
   return std::max(1, per_sm) * g_num_sms;
 }
 
+// Failure-detection self-test (lpf_paths_set_selftest): the staging wait
+// expects 16 bytes more than the copy delivers and gives up after 2^16
+// try_wait rounds instead of 2^24.
+static uint32_t selftest_extra_tx(const lpf_paths* p) { return p->selftest ? 16u : 0u; }
+static uint32_t selftest_wait_rounds(const lpf_paths* p) { return p->selftest ? (1u << 16) : kWaitRounds; }
+
 template <int T>
 static void launch_walk(const Geometry& g, const Baked& b, lpf_paths* p, unsigned long long* c, int blocks,
                         cudaStream_t s) {
   walk_kernel<T><<<blocks, 32 * g.G * g.BB, g.band_bytes, s>>>(
       p->d_packed, g.H, g.W, g.S, g.nw, g.G, g.BB, g.band_bytes, g.nbg, b.n_pieces, b.d_words, b.d_piece, c,
-      p->host.n_full, p->host.base, p->d_status, p->d_sel_active);
+      p->host.n_full, p->host.base, p->d_status, p->d_sel_active, selftest_extra_tx(p), selftest_wait_rounds(p));
 }
 
 // Enqueue one full evaluation with launch shape (T, BB) (<= 0: tuned or
@@ -459,7 +484,8 @@ static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* cou
     const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
     pack_rows_kernel<<<pblocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, p->d_packed,
                                              reinterpret_cast<unsigned long long*>(counts), n_zero,
-                                             p->d_status + 1, kCtlUnits - 1 + g.nbg);
+                                             p->d_status + 1, kCtlUnits - 1 + g.nbg,
+                                             p->checked ? p->d_status : nullptr);
   }
   p->d_sel_active = nullptr;
   if (sel) {
@@ -530,6 +556,14 @@ static int autotune_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t
   cudaEventDestroy(e1);
   if (rc) return rc;
   if (bt == 0) return LPF_EUNSUPPORTED;
+  {
+    // leave the program on the device laid out for the winning shape (the
+    // trials re-baked it for each shape they ran)
+    Geometry g;
+    rc = make_geometry(H, W, p->host.rx, p->host.ry, bt, bb, g);
+    if (!rc) rc = bake(p, p->host.tree, g, p->tree);
+    if (rc) return rc;
+  }
   for (Tuned& t : p->tuned)
     if (t.H == H && t.W == W) { t.T = bt; t.BB = bb; bt = -bt; break; }
   if (bt > 0) p->tuned.push_back({H, W, bt, bb});
@@ -586,6 +620,13 @@ int noalloc_slot(int dev, NoAllocSlot& out) {
 }
 }  // namespace
 
+// The fixed status word on device dev if an allocation-free call has run there.
+int* noalloc_ctl_if_ready(int dev) {
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  return g_noalloc_slot[dev].ready ? g_noalloc_slot[dev].ctl : nullptr;
+}
+
 static int run_full_noalloc(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* counts, cudaStream_t s) {
   if (!p || !img || !counts) return LPF_EINVAL;
   if (H < 1 || W < 1 || H > 8192 || W > 8192) return LPF_EINVAL;
@@ -605,7 +646,15 @@ static int run_full_noalloc(const uint8_t* img, int H, int W, lpf_paths* p, int6
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_cuda_error(e);
   const Baked& b = p->tree;
-  // the program for this width must already be on this device (an earlier lpf_full call put it there)
+  // The program for this width must already be on this device (an earlier
+  // lpf_full call put it there).  When the tuned shape needs another row
+  // layout than the one it was baked for (lpf_set_launch_shape after that
+  // call), the walk runs in the shape it was baked for instead.
+  if (b.d_words && b.W == g.W && (b.S != g.S || b.r32 != g.r32) && b.T > 0) {
+    rc = make_geometry(H, W, p->host.rx, p->host.ry, b.T, b.BB, g);
+    if (rc) return rc;
+    if ((int)g.band_bytes > g_max_dyn_smem || g.packed_words > kNoAllocPackedWords) return LPF_EUNSUPPORTED;
+  }
   if (p->device != dev || !b.d_words || b.W != g.W || b.S != g.S || b.r32 != g.r32) return LPF_EINVAL;
   NoAllocSlot slot;
   rc = noalloc_slot(dev, slot);
@@ -627,19 +676,21 @@ static int run_full_noalloc(const uint8_t* img, int H, int W, lpf_paths* p, int6
 
   const int64_t n_full = p->host.n_full, base = p->host.base;
   {
-    // pack the rows; the counts, the status and the work counters start at 0
+    // pack the rows; the counts and the work counters start at 0 (the status
+    // word keeps its flags until lpf_paths_status reads and clears them)
     const int64_t total = std::max<int64_t>((int64_t)g.rows * g.S, 2 * n_full);
     const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
     pack_rows_kernel<<<pblocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, slot.packed,
-                                             reinterpret_cast<unsigned long long*>(counts), 2 * n_full, slot.ctl,
-                                             kCtlUnits + g.nbg);
+                                             reinterpret_cast<unsigned long long*>(counts), 2 * n_full, slot.ctl + 1,
+                                             kCtlUnits - 1 + g.nbg, p->checked ? slot.ctl : nullptr);
   }
   unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
   const dim3 block(32 * g.G * g.BB);
 #define LPF_NOALLOC_WALK(TT)                                                                                   \
   walk_kernel<TT><<<blocks, block, g.band_bytes, s>>>(slot.packed, g.H, g.W, g.S, g.nw, g.G, g.BB, g.band_bytes, \
                                                       g.nbg, b.n_pieces, b.d_words, b.d_piece, c, n_full, base,   \
-                                                      slot.ctl, nullptr)
+                                                      slot.ctl, nullptr, selftest_extra_tx(p),                  \
+                                                      selftest_wait_rounds(p))
   switch (g.T) {
     case 1: LPF_NOALLOC_WALK(1); break;
     case 2: LPF_NOALLOC_WALK(2); break;
@@ -672,6 +723,7 @@ const char* lpf_strerror(int code) {
     case LPF_ECUDA: return "CUDA runtime error";
     case LPF_ETIMEOUT: return "device-side wait timed out";
     case LPF_EUNSUPPORTED: return "size not supported";
+    case LPF_EPIXEL: return "pixel value other than 0 or 1 (checked mode)";
     default: return "unknown status";
   }
 }
@@ -825,14 +877,36 @@ int lpf_paths_set_timer(lpf_paths* p, void* ev_start, void* ev_stop) {
 
 int lpf_paths_status(lpf_paths* p, lpf_stream_t stream) {
   if (!p) return LPF_EINVAL;
-  if (!p->d_status) return LPF_OK;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return LPF_ECUDA;
   int h = 0;
-  if (cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LPF_ECUDA;
-  if (h) {
-    cudaMemset(p->d_status, 0, sizeof(int));
-    return (h & 1) ? LPF_ETIMEOUT : LPF_EINVAL;
+  if (p->d_status) {
+    if (cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LPF_ECUDA;
+    if (h && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return LPF_ECUDA;
   }
+  // the status word of lpf_full_noalloc's fixed work area on this device
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LPF_ECUDA;
+  int* ctl = lpf::noalloc_ctl_if_ready(dev);
+  if (ctl) {
+    int n = 0;
+    if (cudaMemcpy(&n, ctl, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LPF_ECUDA;
+    if (n && cudaMemset(ctl, 0, sizeof(int)) != cudaSuccess) return LPF_ECUDA;
+    h |= n;
+  }
+  if (h & lpf::kStatusTimeout) return LPF_ETIMEOUT;
+  if (h & lpf::kStatusPixel) return LPF_EPIXEL;
+  return h ? LPF_EINVAL : LPF_OK;
+}
+
+int lpf_set_checked(lpf_paths* p, int32_t on) {
+  if (!p || (on != 0 && on != 1)) return LPF_EINVAL;
+  p->checked = on;
+  return LPF_OK;
+}
+
+int lpf_paths_set_selftest(lpf_paths* p, int32_t on) {
+  if (!p || (on != 0 && on != 1)) return LPF_EINVAL;
+  p->selftest = on;
   return LPF_OK;
 }
 

@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
     SaDev* __restrict__ st, uint8_t* __restrict__ cell, uint8_t* __restrict__ ext, DeltaArgs g,
     int32_t* __restrict__ pairs2, float* __restrict__ u2, int32_t* __restrict__ dcounts, float* __restrict__ partial2,
     unsigned long long* __restrict__ counts, int* __restrict__ status, unsigned int* __restrict__ bar, int n_batches,
-    int k_max, unsigned int bar_extra) {
+    int k_max, unsigned int bar_extra, int bar_block) {
   extern __shared__ __align__(16) uint8_t sm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ SaDev s_state;
@@ -327,8 +327,10 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
       }
       __syncthreads();
     }
-    // (bar_extra > 0 only in lpf_sa_selftest_timeout: a target no block reaches)
-    if (!sa_grid_barrier(bar, (unsigned int)(bi + 1) * gridDim.x + bar_extra, status)) break;
+    // (bar_extra > 0 only in lpf_sa_selftest_timeout: a target that block
+    // bar_block, or every block if bar_block < 0, never reaches)
+    const unsigned int extra = (bar_block < 0 || (int)blockIdx.x == bar_block) ? bar_extra : 0u;
+    if (!sa_grid_barrier(bar, (unsigned int)(bi + 1) * gridDim.x + extra, status)) break;
 
     const long long left = s_state.n_step - s_state.n_eval;
     const int Kv = (int)min((long long)Keff, max(0LL, left));
@@ -402,7 +404,7 @@ __global__ void build_ext_sa_kernel(const uint8_t* __restrict__ img, DeltaArgs g
       const int ey = i / g.We, ex = i - ey * g.We;
       int y = (ey - g.ry) % g.H; if (y < 0) y += g.H;
       int x = (ex - g.rx) % g.W; if (x < 0) x += g.W;
-      v = img[y * g.W + x];
+      v = img[y * g.W + x] != 0;
     }
     ext[i] = v;
   }
@@ -425,13 +427,13 @@ static size_t persistent_smem(const DeltaArgs& g) {
 
 // Launch the persistent annealer for nb batches (cooperative launch: every
 // block is resident, which its grid barrier relies on).
-static int launch_persistent(lpf_sa* sa, int nb, cudaStream_t s, unsigned int bar_extra = 0) {
+static int launch_persistent(lpf_sa* sa, int nb, cudaStream_t s, unsigned int bar_extra = 0, int bar_block = -1) {
   cudaError_t e = cudaMemsetAsync(sa->d_bar, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return set_cuda_error(e);
   unsigned long long* counts = reinterpret_cast<unsigned long long*>(sa->counts);
   int k_max = sa->prm.k_max;
   void* args[] = {&sa->d_st, &sa->cell, &sa->d_ext, &sa->g, &sa->d_pairs, &sa->d_u, &sa->d_dc, &sa->d_partial,
-                  &counts, &sa->d_status, &sa->d_bar, &nb, &k_max, &bar_extra};
+                  &counts, &sa->d_status, &sa->d_bar, &nb, &k_max, &bar_extra, &bar_block};
   e = cudaLaunchCooperativeKernel(sa_persistent_kernel_entry(), dim3(sa->g.n_chunks), dim3(kDeltaThreads), args,
                                   persistent_smem(sa->g), s);
   return set_cuda_error(e);
@@ -465,6 +467,28 @@ void sa_enqueue_error(lpf_sa* sa, cudaStream_t s) {
 static int sa_device_state(lpf_sa* sa, SaDev& st, cudaStream_t s) {
   cudaError_t e = cudaMemcpyAsync(&st, sa->d_st, sizeof(st), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return set_cuda_error(e);
+}
+
+// Make the run state consistent again after a bounded wait gave up.  The
+// cell, its extended copy in global memory and the run state are written by
+// one block only (block 0 of the persistent kernel, the last block of a batch
+// kernel), so they always agree; the counts are written per vector chunk by
+// every block, and after a grid barrier that timed out in some blocks only,
+// some chunks hold the counts after a swap that the cell does not show.  So
+// the counts are recomputed from the cell (exact integers) and the error from
+// the counts, and the run continues from the cell's state.
+int sa_recover(lpf_sa* sa, cudaStream_t s) {
+  int rc;
+  if (sa->objective == kSaObjectiveS2) rc = s2_counts(sa->cell, sa->H, sa->W, sa->counts, s);
+  else if (sa->d_sel) rc = lpf_full_mc(sa->cell, sa->H, sa->W, sa->paths, sa->d_sel, sa->counts, s);
+  else rc = lpf_full(sa->cell, sa->H, sa->W, sa->paths, sa->counts, s);
+  if (rc) return rc;
+  sa_enqueue_error(sa, s);
+  sa_set_error_kernel<<<1, 1, 0, s>>>(sa->d_st, sa->d_e);
+  cudaError_t e = cudaMemsetAsync(sa->d_status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
   return set_cuda_error(e);
 }
 
@@ -593,6 +617,10 @@ static int sa_create_lineal(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* 
     rc = build_sel_ext(sel_dev, H, W, paths, s, &sa->d_sel_ext);
     if (rc) { lpf_sa_free(sa); return rc; }
     sa->inv_norm = 1.0 / (double)n_sel;
+    // the run's own copy of the selection (counts are recomputed from it after a failed wait)
+    cudaError_t e = cudaMalloc(&sa->d_sel, (size_t)H * W);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sa->d_sel, sel_dev, (size_t)H * W, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) { lpf_sa_free(sa); return lpf::set_cuda_error(e); }
   }
   sa->paths = paths;
   sa->cell = cell_dev;
@@ -695,9 +723,10 @@ int lpf_sa_run(lpf_sa* sa, int32_t n_batches, lpf_stream_t stream) {
   return lpf::set_cuda_error(cudaGetLastError());
 }
 
-int lpf_sa_selftest_timeout(lpf_sa* sa, lpf_stream_t stream) {
+int lpf_sa_selftest_timeout(lpf_sa* sa, int32_t block, lpf_stream_t stream) {
   if (!sa) return LPF_EINVAL;
   if (!sa->persistent) return LPF_EUNSUPPORTED;
+  if (block < -1 || block >= sa->g.n_chunks) return LPF_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   lpf::SaDev before, after;
   int rc = lpf::sa_device_state(sa, before, s);
@@ -706,19 +735,22 @@ int lpf_sa_selftest_timeout(lpf_sa* sa, lpf_stream_t stream) {
   cudaError_t e = cudaMemcpy(&status, sa->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return lpf::set_cuda_error(e);
   if (status) return LPF_ETIMEOUT;  // an earlier wait already failed
-  rc = lpf::launch_persistent(sa, 1, s, 1u);  // one arrival short of every target
+  rc = lpf::launch_persistent(sa, 1, s, 1u, block);  // one arrival short of the chosen targets
   if (rc) return rc;
   e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaMemcpy(&status, sa->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return lpf::set_cuda_error(e);
   rc = lpf::sa_device_state(sa, after, s);
   if (rc) return rc;
-  e = cudaMemsetAsync(sa->d_status, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return lpf::set_cuda_error(e);
+  // Every block timed out, or block 0 did: block 0 kept the state of before
+  // the batch.  Another block timed out: block 0 took the batch's decision.
   const bool unchanged = after.n_eval == before.n_eval && after.n_accept == before.n_accept &&
                          after.n_batches == before.n_batches && after.T == before.T && after.e == before.e;
-  return ((status & 4) && unchanged) ? LPF_OK : LPF_ECUDA;
+  const bool advanced = after.n_batches == before.n_batches + 1;
+  rc = lpf::sa_recover(sa, s);  // recount from the cell, clear the status
+  if (rc) return rc;
+  const bool state_ok = (block <= 0) ? unchanged : advanced;
+  return ((status & 4) && state_ok) ? LPF_OK : LPF_ECUDA;
 }
 
 int lpf_sa_set_proposer(lpf_sa* sa, lpf_cnn* cnn, float epsilon, float tau, int32_t refresh) {
@@ -769,7 +801,14 @@ int lpf_sa_read(lpf_sa* sa, lpf_sa_stats* out, lpf_stream_t stream) {
   out->t_max = sa->prm.t_max;
   out->next_batch = st.k_eff;
   out->done = st.done;
-  return status ? LPF_ETIMEOUT : LPF_OK;
+  if (!status) return LPF_OK;
+  // a bounded wait gave up: restore consistent counts and error, then report it once
+  rc = lpf::sa_recover(sa, (cudaStream_t)stream);
+  if (rc) return rc;
+  rc = lpf::sa_device_state(sa, st, (cudaStream_t)stream);
+  if (rc) return rc;
+  out->error = st.e;
+  return LPF_ETIMEOUT;
 }
 
 int lpf_sa_export_progress(lpf_sa* sa, lpf_sa_progress* out, lpf_stream_t stream) {
@@ -862,6 +901,7 @@ void lpf_sa_free(lpf_sa* sa) {
   cudaFree(sa->d_dc);
   cudaFree(sa->d_e);
   cudaFree(sa->d_status);
+  cudaFree(sa->d_sel);
   cudaFree(sa->d_cdf);
   cudaFree(sa->d_bar);
   cudaFree(sa->d_sel_ext);

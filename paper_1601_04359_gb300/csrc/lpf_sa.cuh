@@ -312,6 +312,7 @@ struct lpf_sa {
   int persistent = 0;           // batches run by the cooperative persistent kernel
   unsigned int* d_bar = nullptr;  // its grid-barrier counter
   uint8_t* d_sel_ext = nullptr; // Monte-Carlo runs: sampled translations, extended layout
+  uint8_t* d_sel = nullptr;     // Monte-Carlo runs: the run's copy of the selection, H*W
   double inv_norm = 0.0;        // descriptor = count * inv_norm
 };
 
@@ -323,6 +324,9 @@ void s2_enqueue_batch(lpf_sa* sa, cudaStream_t s);
 void sa_enqueue_error(lpf_sa* sa, cudaStream_t s);
 // LPF_OK if the run parameters are valid (lpf_sa.cu).
 int sa_check_params(const lpf_sa_params* prm);
+// Recompute counts (from the cell) and error (from the counts) after a
+// bounded wait gave up, and clear the run's status word (lpf_sa.cu).
+int sa_recover(lpf_sa* sa, cudaStream_t s);
 // Second half of both create calls once sa's geometry, objective and error
 // layout are set: work buffers, extended cell, initial error and temperature,
 // device state (lpf_sa.cu).

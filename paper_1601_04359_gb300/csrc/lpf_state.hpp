@@ -41,6 +41,7 @@ struct Tuned {
 // A program with its pixel words converted to packed offsets for one width.
 struct Baked {
   int W = -1, S = -1, r32 = -1;
+  int T = 0, BB = 0;  // a launch shape whose row layout the program was baked for
   uint32_t* d_words = nullptr;
   int64_t* d_piece = nullptr;
   int n_pieces = 0;
@@ -78,6 +79,8 @@ struct lpf_paths {
   uint32_t* d_sel = nullptr;     // work area: packed translation selection (Monte-Carlo variant)
   size_t sel_cap = 0;            // words
   const uint32_t* d_sel_active = nullptr;  // selection of the walk being enqueued (or null)
+  int checked = 0;               // 1: kernels that read the image flag pixels other than 0 or 1
+  int selftest = 0;              // 1: walks wait for bytes no copy delivers (failure-detection test)
 };
 
 namespace lpf {

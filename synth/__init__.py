@@ -224,3 +224,20 @@ def mixed_sizes_batch(n: int = 256, seed: int = 4):
             img = clustered_disks(H, W, f, seed=s)
         out.append(img)
     return out
+
+
+def swap_candidates(cell: np.ndarray, K: int, seed: int = 0) -> np.ndarray:
+    """int32 [K][2] candidate exchanges of a two-phase cell: column 0 a
+    phase-1 pixel, column 1 a phase-0 pixel (linear indices y*W + x), each
+    uniform over its phase, independently (the candidate batch of the
+    swap-delta workload)."""
+    rng = np.random.default_rng(seed)
+    flat = cell.reshape(-1)
+    ones = np.flatnonzero(flat == 1)
+    zeros = np.flatnonzero(flat == 0)
+    return np.stack([rng.choice(ones, K), rng.choice(zeros, K)], axis=1).astype(np.int32)
+
+
+def clustered_cell_128() -> np.ndarray:
+    """128x128 crop of the 512x512 clustered-disk image (the swap-delta workload's cell)."""
+    return clustered_512()[:128, :128].copy()

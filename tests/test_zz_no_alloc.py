@@ -63,3 +63,47 @@ def test_noalloc_rejects_what_it_cannot_do(gpu_lib):
     big = torch.zeros((4096, 2048), dtype=torch.uint8, device="cuda")
     big_out = torch.empty((2, fresh.n_full), dtype=torch.int64, device="cuda")
     assert _call(lib, big, fresh, big_out) == -5
+
+
+def test_noalloc_after_autotune_and_shape_changes(gpu_lib):
+    # 200 x 200, window 40: launch shapes with 1 and 8 words per thread lay
+    # the packed rows out with different strides (11 and 13 words).  After the
+    # autotuner, and after a launch shape set later, the call still finds a
+    # usable program and gives lpf_full's counts.
+    lib = gpu_lib.load()
+    img = torch.from_numpy(synth.ellipses(200, 200, 0.35, seed=8)).cuda()
+    paths = gpu_lib.lpf_build_paths(40, 40)
+    ref = gpu_lib.lpf_full(img, paths).clone()
+    gpu_lib.lpf_autotune_full(img, paths)
+    out = torch.full((2, paths.n_full), -1, dtype=torch.int64, device="cuda")
+    assert _call(lib, img, paths, out) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    for T in (1, 8):
+        gpu_lib.lpf_set_launch_shape(paths, 200, 200, T, 1)
+        out.fill_(-1)
+        assert _call(lib, img, paths, out) == 0
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    assert gpu_lib.lpf_paths_status(paths) == 0
+
+
+def test_noalloc_equals_the_oracle_and_reports_a_timeout(gpu_lib):
+    import oracle
+    lib = gpu_lib.load()
+    img = synth.clustered_disks(72, 90, 0.3, seed=12)
+    d = torch.from_numpy(img).cuda()
+    paths = gpu_lib.lpf_build_paths(30, 20)
+    gpu_lib.lpf_full(d, paths)   # set-up
+    out = torch.empty((2, paths.n_full), dtype=torch.int64, device="cuda")
+    assert _call(lib, d, paths, out) == 0
+    assert gpu_lib.lpf_paths_status(paths) == 0
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.lpf_full(img, 30, 20))
+    # a staging wait made to run out is reported through lpf_paths_status
+    gpu_lib.lpf_paths_set_selftest(paths, True)
+    assert _call(lib, d, paths, out) == 0
+    assert gpu_lib.lpf_paths_status(paths) == gpu_lib.LPF_ETIMEOUT
+    gpu_lib.lpf_paths_set_selftest(paths, False)
+    assert _call(lib, d, paths, out) == 0
+    assert gpu_lib.lpf_paths_status(paths) == 0
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.lpf_full(img, 30, 20))
