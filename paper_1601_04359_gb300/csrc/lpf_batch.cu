@@ -38,8 +38,8 @@ struct BatchDesc {
   const uint8_t* img;
   unsigned long long* counts;
   uint32_t* packed;
-  const uint32_t* prog;
-  const int64_t* piece;
+  const uint4* prog;        // baked program, 16-byte groups
+  const uint32_t* piece;    // piece starts in groups
   int64_t n_full, base;
   int H, W, S, nw, G, BB, T, r32, rows, nbg, n_pieces, bg0;
   uint32_t band_bytes;
@@ -87,19 +87,9 @@ __device__ __forceinline__ void batch_unit(const BatchDesc& b, int bg, int tile,
                                            int lane) {
   const int bl = tile / b.G, grp = tile - (tile / b.G) * b.G;
   const int y = (bg * b.BB + bl) * 32 + lane;
-  uint32_t valid[T];
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int j = grp * T + t;
-    uint32_t v = 0;
-    if (y < b.H && j < b.nw) {
-      const int rem = b.W - 32 * j;
-      v = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
-    }
-    valid[t] = v;
-  }
   const uint32_t* lane_base = sm + (bl * 32 + lane) * b.S + grp * T;
-  walk_piece<T>(b.prog, b.piece[pi], b.piece[pi + 1], lane_base, valid, lane, b.counts, b.n_full, b.base);
+  (void)walk_unit<T>(b.prog, b.piece[pi], b.piece[pi + 1], lane_base, y, b.H, b.W, b.nw, grp * T, nullptr, lane,
+                     b.counts, b.n_full, b.base);
 }
 
 __global__ void __launch_bounds__(kBatchThreads, 4) batch_walk_kernel(const BatchDesc* __restrict__ d,
@@ -255,7 +245,7 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
     BatchDesc& d = bt->desc[i];
     d.img = imgs[i];
     d.counts = reinterpret_cast<unsigned long long*>(counts[i]);
-    d.prog = bt->baked[k].d_words;
+    d.prog = reinterpret_cast<const uint4*>(bt->baked[k].d_words);
     d.piece = bt->baked[k].d_piece;
     d.n_full = p->host.n_full;
     d.base = p->host.base;

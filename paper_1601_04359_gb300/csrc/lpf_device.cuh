@@ -51,18 +51,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
   return false;
 }
 
-// The staged word a baked pixel word refers to.  A pixel word is
-// (word offset << 7) | funnel shift, i.e. (byte offset << 5) | shift with a
-// shift below 32, so the byte offset is a plain right shift by 5 (one add
-// with a shifted operand, no masking).
+// The staged word a baked pixel word refers to.  A pixel word (and the first
+// word of a pair) is (byte offset << 5) | funnel shift with a shift below 32,
+// so the byte offset is a plain right shift by 5 (one add with a shifted
+// operand, no masking), and the funnel shift reads the low 5 bits directly.
 __device__ __forceinline__ const uint32_t* lane_word(const uint32_t* lane_base, uint32_t pix) {
   return reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(lane_base) + (pix >> 5));
-}
-
-// The staged word window of a baked pair word ((byte offset << 10) | (shift1
-// << 5) | shift2): one shifted add as well.
-__device__ __forceinline__ const uint32_t* pair_word(const uint32_t* lane_base, uint32_t pair) {
-  return reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(lane_base) + (pair >> 10));
 }
 
 __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {

@@ -143,8 +143,8 @@ __global__ void pack_sel_kernel(const uint8_t* __restrict__ sel, int H, int W, i
 template <int T>
 __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict__ packed, int H, int W, int S,
                                                   int nw, int G, int BB, uint32_t band_bytes, int n_bg,
-                                                  int n_pieces, const uint32_t* __restrict__ prog,
-                                                  const int64_t* __restrict__ piece,
+                                                  int n_pieces, const uint4* __restrict__ prog,
+                                                  const uint32_t* __restrict__ piece,
                                                   unsigned long long* __restrict__ counts, int64_t n_full,
                                                   int64_t base, int* __restrict__ ctl,
                                                   const uint32_t* __restrict__ sel, uint32_t extra_tx,
@@ -192,113 +192,8 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
       const int bl = tile / G, grp = tile - (tile / G) * G;
       const uint32_t* lane_base = sm + (bl * 32 + lane) * S + grp * T;
       const int y = (bg * BB + bl) * 32 + lane;
-      uint32_t valid[T];
-#pragma unroll
-      for (int t = 0; t < T; ++t) {
-        const int j = grp * T + t;
-        uint32_t v = 0;
-        if (y < H && j < nw) {
-          const int rem = W - 32 * j;
-          v = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
-          if (sel) v &= sel[(size_t)y * nw + j];  // only the selected translations
-        }
-        valid[t] = v;
-      }
-      uint32_t m1[T], m0[T];
-      uint32_t st1[kDevStack][T], st0[kDevStack][T];
-#pragma unroll
-      for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
-
-      int64_t pc = piece[pi];
-      const int64_t end = piece[pi + 1];
-      uint32_t hdr_next = pc < end ? __ldg(prog + pc) : 0u;
-      while (pc < end) {
-        const int64_t rec = pc++;
-        const uint32_t hdr = hdr_next;
-        if (hdr & kReset) {
-#pragma unroll
-          for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
-        }
-        if (hdr & kRestore) {
-          const int l = (hdr >> kRlevelShift) & kLevelMask;
-#pragma unroll
-          for (int t = 0; t < T; ++t) { m1[t] = st1[l][t]; m0[t] = st0[l][t]; }
-        }
-        int vec = -1;
-        uint32_t skip = 0;
-        if (hdr & kEmit) vec = (int)__ldg(prog + pc++);
-        if (hdr & (kEmit | kPush)) skip = __ldg(prog + pc++);
-        const int np = (int)__ldg(prog + pc++);  // pixel pairs sharing a staged word window
-        pc = (pc + 3) & ~int64_t(3);
-        const int n = (int)(hdr & kNpixMask);
-        executed += (unsigned)n;
-        const int ns = n - 2 * np;  // np is a multiple of 4
-        // the next record's header, fetched while this record's pixels are ANDed
-        hdr_next = pc + np + ns < end ? __ldg(prog + pc + np + ns) : 0u;
-        // Every 8 pixels the warp votes: once its tile is empty, the rest of
-        // the record and the subtree below it are zero there (the record's
-        // skip target is the first record after that subtree).
-        bool dead = false;
-        {
-          const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
-          for (int q = 0; q < (np >> 2); ++q) {
-            walk_pair4<T>(lane_base, __ldg(q4 + q), m1, m0);
-            if (skip != 0 && warp_empty<T>(m1, m0)) {
-              dead = true;
-              executed -= (unsigned)(n - 8 * (q + 1));  // pixels not walked
-              break;
-            }
-          }
-          pc += np;
-        }
-        const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
-        const int n4 = dead ? 0 : ns >> 2;
-        if (n4 > 0) {
-          uint4 nxt = __ldg(q4);
-          for (int q = 0; q < n4; ++q) {
-            const uint4 cur = nxt;
-            if (q + 1 < n4) nxt = __ldg(q4 + q + 1);
-            walk_and4<T>(lane_base, cur, m1, m0);
-            if ((q & 1) && skip != 0 && warp_empty<T>(m1, m0)) {
-              dead = true;
-              executed -= (unsigned)(ns - 4 * (q + 1));  // pixels not walked
-              break;
-            }
-          }
-        }
-        if (!dead)
-          for (int i = n4 * 4; i < ns; ++i) walk_and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
-        pc += ns;
-        if (dead) {
-          pc = rec + skip;
-          hdr_next = pc < end ? __ldg(prog + pc) : 0u;
-          continue;
-        }
-        if (hdr & (kEmit | kPush)) {
-          // Empty for the whole warp (one vote): so is every count below this node.
-          if (skip != 0 && warp_empty<T>(m1, m0)) {
-            pc = rec + skip;
-            hdr_next = pc < end ? __ldg(prog + pc) : 0u;
-            continue;
-          }
-          if (vec >= 0) {
-            uint32_t c = 0;
-#pragma unroll
-            for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
-            c = warp_sum(c);
-            if (lane == 0) {
-              const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
-              if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);
-              if (c1) atomicAdd(counts + n_full + base + vec, (unsigned long long)c1);
-            }
-          }
-        }
-        if (hdr & kPush) {
-          const int l = (hdr >> kPlevelShift) & kLevelMask;
-#pragma unroll
-          for (int t = 0; t < T; ++t) { st1[l][t] = m1[t]; st0[l][t] = m0[t]; }
-        }
-      }
+      executed += walk_unit<T>(prog, piece[pi], piece[pi + 1], lane_base, y, H, W, nw, grp * T, sel, lane, counts,
+                               n_full, base);
     }
     __syncthreads();  // every warp is done with the staged band before it may be replaced
   }
@@ -364,12 +259,14 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
   std::vector<uint32_t> out;
   std::vector<int64_t> piece;
   bake_words(p->host, prog, g.S, g.r32, out, piece);
+  if (out.size() / 4 >= (size_t(1) << 32)) return LPF_EUNSUPPORTED;  // group offsets are 32-bit
+  std::vector<uint32_t> piece32(piece.begin(), piece.end());
   cudaError_t e;
   if ((e = cudaMalloc(&b.d_words, out.size() * 4)) != cudaSuccess) return set_cuda_error(e);
-  if ((e = cudaMalloc(&b.d_piece, piece.size() * 8)) != cudaSuccess) return set_cuda_error(e);
+  if ((e = cudaMalloc(&b.d_piece, piece32.size() * 4)) != cudaSuccess) return set_cuda_error(e);
   if ((e = cudaMemcpy(b.d_words, out.data(), out.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
     return set_cuda_error(e);
-  if ((e = cudaMemcpy(b.d_piece, piece.data(), piece.size() * 8, cudaMemcpyHostToDevice)) !=
+  if ((e = cudaMemcpy(b.d_piece, piece32.data(), piece32.size() * 4, cudaMemcpyHostToDevice)) !=
       cudaSuccess)
     return set_cuda_error(e);
   b.W = g.W;
@@ -430,7 +327,8 @@ template <int T>
 static void launch_walk(const Geometry& g, const Baked& b, lpf_paths* p, unsigned long long* c, int blocks,
                         cudaStream_t s) {
   walk_kernel<T><<<blocks, 32 * g.G * g.BB, g.band_bytes, s>>>(
-      p->d_packed, g.H, g.W, g.S, g.nw, g.G, g.BB, g.band_bytes, g.nbg, b.n_pieces, b.d_words, b.d_piece, c,
+      p->d_packed, g.H, g.W, g.S, g.nw, g.G, g.BB, g.band_bytes, g.nbg, b.n_pieces,
+      reinterpret_cast<const uint4*>(b.d_words), b.d_piece, c,
       p->host.n_full, p->host.base, p->d_status, p->d_sel_active, selftest_extra_tx(p), selftest_wait_rounds(p));
 }
 
@@ -688,7 +586,8 @@ static int run_full_noalloc(const uint8_t* img, int H, int W, lpf_paths* p, int6
   const dim3 block(32 * g.G * g.BB);
 #define LPF_NOALLOC_WALK(TT)                                                                                   \
   walk_kernel<TT><<<blocks, block, g.band_bytes, s>>>(slot.packed, g.H, g.W, g.S, g.nw, g.G, g.BB, g.band_bytes, \
-                                                      g.nbg, b.n_pieces, b.d_words, b.d_piece, c, n_full, base,   \
+                                                      g.nbg, b.n_pieces, reinterpret_cast<const uint4*>(b.d_words), \
+                                                      b.d_piece, c, n_full, base,                              \
                                                       slot.ctl, nullptr, selftest_extra_tx(p),                  \
                                                       selftest_wait_rounds(p))
   switch (g.T) {

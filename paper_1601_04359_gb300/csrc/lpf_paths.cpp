@@ -425,19 +425,19 @@ void bake_words(const Paths& p, const Program& prog, int S, int r32, std::vector
                 std::vector<int64_t>& piece_out) {
   const std::vector<uint32_t>& w = prog.words;
   out.clear();
-  out.reserve(w.size() + w.size() / 16);
-  std::vector<int64_t> old_start, new_start;  // record starts
+  out.reserve(w.size() + w.size() / 8);
+  std::vector<int64_t> old_start, new_start;  // record starts (old: words, new: groups)
   std::vector<std::pair<uint32_t, uint32_t>> pix;  // (byte offset, shift)
   std::vector<uint32_t> singles;
   for (size_t i = 0; i < w.size();) {
     old_start.push_back((int64_t)i);
-    new_start.push_back((int64_t)out.size());
+    new_start.push_back((int64_t)(out.size() / 4));
     const uint32_t h = w[i];
     const int extra = record_extra_words(h);
-    for (int k = 0; k <= extra; ++k) out.push_back(w[i + k]);  // header, vector id, skip, pair count
+    const uint32_t vec = (h & kEmit) ? w[i + 1] : 0u;
+    const uint32_t skip = (h & (kEmit | kPush)) ? w[i + (size_t)record_skip_at(h)] : 0u;  // resolved below
     i += 1 + extra;
     while (i % 4) ++i;
-    while (out.size() % 4) out.push_back(0u);
     const uint32_t n = h & kNpixMask;
     pix.clear();
     for (uint32_t k = 0; k < n; ++k) {
@@ -451,40 +451,51 @@ void bake_words(const Paths& p, const Program& prog, int S, int r32, std::vector
                      [](const std::pair<uint32_t, uint32_t>& a, const std::pair<uint32_t, uint32_t>& b) {
                        return a.first < b.first;
                      });
-    // pairs in whole groups of 4 (the kernels take them 4 at a time); the
-    // pixels of the pairs left over stay single
-    uint32_t avail = 0;
-    for (size_t k = 0; k + 1 < pix.size();) {
-      if (pix[k].first == pix[k + 1].first) { ++avail; k += 2; } else { k += 1; }
-    }
-    uint32_t n_pairs = 0;
-    const uint32_t want = avail & ~3u;
+    // pairs of pixels in one word window, two pairs per group; a pair left
+    // over and the unpaired pixels are singles
+    std::vector<uint32_t> pairs;
     singles.clear();
     for (size_t k = 0; k < pix.size();) {
-      if (n_pairs < want && k + 1 < pix.size() && pix[k].first == pix[k + 1].first) {
-        out.push_back((pix[k].first << 10) | (pix[k].second << 5) | pix[k + 1].second);
-        ++n_pairs;
+      if (k + 1 < pix.size() && pix[k].first == pix[k + 1].first) {
+        pairs.push_back((pix[k].first << 5) | pix[k].second);
+        pairs.push_back(pix[k + 1].second);
         k += 2;
       } else {
         singles.push_back((pix[k].first << 5) | pix[k].second);
         k += 1;
       }
     }
-    out[(size_t)new_start.back() + (size_t)extra] = n_pairs;
+    if ((pairs.size() / 2) & 1) {  // odd number of pairs: the last one becomes two singles
+      const uint32_t s2 = pairs.back();
+      pairs.pop_back();
+      const uint32_t s1 = pairs.back();
+      pairs.pop_back();
+      singles.push_back(s1);
+      singles.push_back((s1 & ~31u) | s2);
+    }
+    if (singles.size() & 1) singles.push_back(singles.back());  // ANDing a pixel twice changes nothing
+    const uint32_t n_pg = (uint32_t)(pairs.size() / 4);
+    const uint32_t n_sg = (uint32_t)(singles.size() / 4);
+    const uint32_t half = (uint32_t)(singles.size() % 4 != 0);
+    out.push_back(h);
+    out.push_back(vec);
+    out.push_back(skip);
+    out.push_back(n_pg | (n_sg << kCntBits) | (half << (2 * kCntBits)));
+    out.insert(out.end(), pairs.begin(), pairs.end());
     out.insert(out.end(), singles.begin(), singles.end());
+    while (out.size() % 4) out.push_back(0u);
   }
-  auto relocate = [&](int64_t old_pos) -> int64_t {  // a record start or the program end
-    if (old_pos >= (int64_t)w.size()) return (int64_t)out.size();
+  auto relocate = [&](int64_t old_pos) -> int64_t {  // a record start or the program end, in groups
+    if (old_pos >= (int64_t)w.size()) return (int64_t)(out.size() / 4);
     const auto it = std::lower_bound(old_start.begin(), old_start.end(), old_pos);
     return new_start[it - old_start.begin()];
   };
   for (size_t r = 0; r < old_start.size(); ++r) {
     const uint32_t h = w[(size_t)old_start[r]];
-    if (!(h & (kEmit | kPush))) continue;
-    const uint32_t d = w[(size_t)old_start[r] + (size_t)record_skip_at(h)];
-    if (d == 0) continue;
-    const int64_t nd = relocate(old_start[r] + d) - new_start[r];
-    out[(size_t)new_start[r] + (size_t)record_skip_at(h)] = nd < (int64_t(1) << 32) ? (uint32_t)nd : 0u;
+    uint32_t& sk = out[4 * (size_t)new_start[r] + 2];
+    if (!(h & (kEmit | kPush)) || sk == 0) { sk = 0; continue; }
+    const int64_t nd = relocate(old_start[r] + sk) - new_start[r];
+    sk = nd < (int64_t(1) << 32) ? (uint32_t)nd : 0u;
   }
   piece_out.resize(prog.piece_begin.size());
   for (size_t q = 0; q < prog.piece_begin.size(); ++q) piece_out[q] = relocate(prog.piece_begin[q]);

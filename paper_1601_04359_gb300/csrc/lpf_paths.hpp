@@ -20,12 +20,20 @@ namespace lpf {
 // records), then a skip word (emitting or pushing records), then a pair
 // count, then zero padding up to the next multiple of 4 words, then the pixel
 // words.  In a program as built the pair count is 0 and the pixel words are
-// prefix-tree node ids; a program baked for an image layout (bake_words)
-// holds first n_pairs pair words (a multiple of 4) -- two pixels of the
-// record that read the same staged word window, (byte offset << 10) |
-// (shift1 << 5) | shift2 -- then the other pixels as single words,
-// (byte offset << 5) | shift.  The ANDs of a record commute, so the order of
-// its pixels is free.
+// prefix-tree node ids.
+//
+// A program baked for an image layout (bake_words) is a sequence of 16-byte
+// groups (uint4); every record is
+//   header group   {hdr, vec (emitting records, else 0), skip (in groups,
+//                   0: none), cnt = n_pg | n_sg << 13 | half << 26}
+//   n_pg pair groups   two pairs {(byte offset << 5) | shift1, shift2} of
+//                      pixels that read the same staged word window
+//   n_sg single groups four pixels (byte offset << 5) | shift
+//   half (0 or 1)      one group holding two single pixels and two zeros
+// with hdr as below (n_pix the record's true pixel count).  The ANDs of a
+// record commute and are idempotent, so its pixels are sorted by word window
+// and an odd single left over is written twice (so that singles come in
+// twos and fours).  Piece starts and skip distances count groups.
 //   bits  0..13  number of pixel words that follow (n_pix)
 //   bit   14     emit: count the mask into vector `vec`
 //   bit   15     restore: mask <- stack[rlevel] before the pixels
@@ -115,8 +123,11 @@ void align_program(Program& prog);
 // Fill the skip words of an aligned, split program.
 void resolve_skips(Program& prog);
 // Bake a program for staged rows of S words whose bit e is the pixel at
-// column e - r32: pixel words as above (pairs formed per record), skip words
-// and piece starts remapped to the new layout.
+// column e - r32, in the group layout above (pairs formed per record), skip
+// distances and piece starts counted in 16-byte groups.  out holds 4 words
+// per group.
+constexpr uint32_t kCntBits = 13;
+constexpr uint32_t kCntMask = (1u << kCntBits) - 1u;
 void bake_words(const Paths& p, const Program& prog, int S, int r32, std::vector<uint32_t>& out,
                 std::vector<int64_t>& piece_out);
 

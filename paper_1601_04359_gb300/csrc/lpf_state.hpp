@@ -42,8 +42,8 @@ struct Tuned {
 struct Baked {
   int W = -1, S = -1, r32 = -1;
   int T = 0, BB = 0;  // a launch shape whose row layout the program was baked for
-  uint32_t* d_words = nullptr;
-  int64_t* d_piece = nullptr;
+  uint32_t* d_words = nullptr;   // 16-byte groups (4 words each)
+  uint32_t* d_piece = nullptr;   // piece starts, in groups [n_pieces + 1]
   int n_pieces = 0;
 };
 

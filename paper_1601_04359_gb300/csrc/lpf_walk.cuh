@@ -1,11 +1,19 @@
-// One warp's walk of one program piece over its translation words (the body
-// shared by the single-image and the batched walk kernels).
+// One warp's walk of one program piece over its tile of translations (the
+// body shared by the single-image and the batched walk kernels).
 //
 // The program is a depth-first walk of the prefix tree of the canonical
-// segments (see lpf_paths.hpp for the record format): every pixel ANDs one
-// funnel-shifted image word into the phase-1 mask and its complement into the
-// phase-0 mask (two pixels of a pair word share one staged word window); emit records count both masks (popc, warp sum, one atomic
-// per phase); push/restore records keep branch masks on a small stack.
+// segments, baked into 16-byte groups (see lpf_paths.hpp): a record is a
+// header group, then groups of four pixels (two pairs of pixels that read the
+// same staged word window, or four single pixels), then at most one group
+// with two single pixels.  Every pixel ANDs one funnel-shifted image word
+// into the phase-1 mask and its complement into the phase-0 mask; emitting
+// records count both masks (popc, warp sum, one atomic per phase);
+// push/restore records keep branch masks on a small per-thread stack.  After
+// every 8 pixels inside a record and at the end of an emitting or branching
+// record the warp votes: once no translation of its tile is left in either
+// phase, every count of the subtree below is zero there too, and the warp
+// jumps to the record's skip target (the zero-count skip of Sec. 3.2,
+// applied to whole subtrees).
 #pragma once
 #include <cstdint>
 
@@ -16,59 +24,84 @@ namespace lpf {
 
 constexpr int kWalkStack = 24;
 
+// The T + 1 staged words of a pixel word's window.
 template <int T>
-__device__ __forceinline__ void walk_and4(const uint32_t* lane_base, uint4 P, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
-  const uint32_t* sa = lane_word(lane_base, P.x);
-  const uint32_t* sb = lane_word(lane_base, P.y);
-  const uint32_t* sc = lane_word(lane_base, P.z);
-  const uint32_t* sd = lane_word(lane_base, P.w);
-  uint32_t wa[T + 1], wb[T + 1], wc[T + 1], wd[T + 1];
+__device__ __forceinline__ void load_window(const uint32_t* lane_base, uint32_t pix, uint32_t (&w)[T + 1]) {
+  const uint32_t* s = lane_word(lane_base, pix);
 #pragma unroll
-  for (int t = 0; t <= T; ++t) { wa[t] = sa[t]; wb[t] = sb[t]; wc[t] = sc[t]; wd[t] = sd[t]; }
+  for (int t = 0; t <= T; ++t) w[t] = s[t];
+}
+
+// Four single pixels (one group).
+template <int T>
+__device__ __forceinline__ void walk_singles4(const uint32_t* lane_base, uint4 P, uint32_t (&m1)[T],
+                                              uint32_t (&m0)[T]) {
+  if (T <= 4) {
+    uint32_t wa[T + 1], wb[T + 1], wc[T + 1], wd[T + 1];
+    load_window<T>(lane_base, P.x, wa);
+    load_window<T>(lane_base, P.y, wb);
+    load_window<T>(lane_base, P.z, wc);
+    load_window<T>(lane_base, P.w, wd);
 #pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], P.x);
-    const uint32_t b = __funnelshift_r(wb[t], wb[t + 1], P.y);
-    const uint32_t c = __funnelshift_r(wc[t], wc[t + 1], P.z);
-    const uint32_t d = __funnelshift_r(wd[t], wd[t + 1], P.w);
-    m1[t] = (m1[t] & a & b) & (c & d);
-    m0[t] = (m0[t] & ~(a | b)) & ~(c | d);
+    for (int t = 0; t < T; ++t) {
+      const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], P.x);
+      const uint32_t b = __funnelshift_r(wb[t], wb[t + 1], P.y);
+      const uint32_t c = __funnelshift_r(wc[t], wc[t + 1], P.z);
+      const uint32_t d = __funnelshift_r(wd[t], wd[t + 1], P.w);
+      m1[t] = (m1[t] & a & b) & c & d;
+      m0[t] = (m0[t] & ~a & ~b) & ~c & ~d;
+    }
+  } else {  // two pixels at a time (registers)
+    uint32_t wa[T + 1], wb[T + 1];
+    load_window<T>(lane_base, P.x, wa);
+    load_window<T>(lane_base, P.y, wb);
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], P.x);
+      const uint32_t b = __funnelshift_r(wb[t], wb[t + 1], P.y);
+      m1[t] = m1[t] & a & b;
+      m0[t] = m0[t] & ~a & ~b;
+    }
+    load_window<T>(lane_base, P.z, wa);
+    load_window<T>(lane_base, P.w, wb);
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], P.z);
+      const uint32_t b = __funnelshift_r(wb[t], wb[t + 1], P.w);
+      m1[t] = m1[t] & a & b;
+      m0[t] = m0[t] & ~a & ~b;
+    }
   }
 }
 
+// Two single pixels.
 template <int T>
-__device__ __forceinline__ void walk_and1(const uint32_t* lane_base, uint32_t p, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
-  const uint32_t* sa = lane_word(lane_base, p);
-  uint32_t wa[T + 1];
-#pragma unroll
-  for (int t = 0; t <= T; ++t) wa[t] = sa[t];
+__device__ __forceinline__ void walk_singles2(const uint32_t* lane_base, uint32_t p, uint32_t q, uint32_t (&m1)[T],
+                                              uint32_t (&m0)[T]) {
+  uint32_t wa[T + 1], wb[T + 1];
+  load_window<T>(lane_base, p, wa);
+  load_window<T>(lane_base, q, wb);
 #pragma unroll
   for (int t = 0; t < T; ++t) {
     const uint32_t a = __funnelshift_r(wa[t], wa[t + 1], p);
-    m1[t] &= a;
-    m0[t] &= ~a;
+    const uint32_t b = __funnelshift_r(wb[t], wb[t + 1], q);
+    m1[t] = m1[t] & a & b;
+    m0[t] = m0[t] & ~a & ~b;
   }
 }
 
-// AND of the two pixels of each of 4 pair words (one staged word window per
-// pair, two funnel shifts) into both phase masks.
+// Two pairs {window|shift1, shift2} (one group): one window per pair.
 template <int T>
-__device__ __forceinline__ void walk_pair4(const uint32_t* lane_base, uint4 P, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
-  const uint32_t* sa = pair_word(lane_base, P.x);
-  const uint32_t* sb = pair_word(lane_base, P.y);
-  const uint32_t* sc = pair_word(lane_base, P.z);
-  const uint32_t* sd = pair_word(lane_base, P.w);
-  uint32_t wa[T + 1], wb[T + 1], wc[T + 1], wd[T + 1];
-#pragma unroll
-  for (int t = 0; t <= T; ++t) { wa[t] = sa[t]; wb[t] = sb[t]; wc[t] = sc[t]; wd[t] = sd[t]; }
+__device__ __forceinline__ void walk_pairs2(const uint32_t* lane_base, uint4 P, uint32_t (&m1)[T], uint32_t (&m0)[T]) {
+  uint32_t wa[T + 1], wb[T + 1];
+  load_window<T>(lane_base, P.x, wa);
+  load_window<T>(lane_base, P.z, wb);
 #pragma unroll
   for (int t = 0; t < T; ++t) {
-    const uint32_t a1 = __funnelshift_r(wa[t], wa[t + 1], P.x >> 5), a2 = __funnelshift_r(wa[t], wa[t + 1], P.x);
-    const uint32_t b1 = __funnelshift_r(wb[t], wb[t + 1], P.y >> 5), b2 = __funnelshift_r(wb[t], wb[t + 1], P.y);
-    const uint32_t c1 = __funnelshift_r(wc[t], wc[t + 1], P.z >> 5), c2 = __funnelshift_r(wc[t], wc[t + 1], P.z);
-    const uint32_t d1 = __funnelshift_r(wd[t], wd[t + 1], P.w >> 5), d2 = __funnelshift_r(wd[t], wd[t + 1], P.w);
-    m1[t] = (((m1[t] & a1 & a2) & b1 & b2) & c1 & c2) & d1 & d2;
-    m0[t] = (((m0[t] & ~(a1 | a2)) & ~(b1 | b2)) & ~(c1 | c2)) & ~(d1 | d2);
+    const uint32_t a1 = __funnelshift_r(wa[t], wa[t + 1], P.x), a2 = __funnelshift_r(wa[t], wa[t + 1], P.y);
+    const uint32_t b1 = __funnelshift_r(wb[t], wb[t + 1], P.z), b2 = __funnelshift_r(wb[t], wb[t + 1], P.w);
+    m1[t] = (m1[t] & a1 & a2) & b1 & b2;
+    m0[t] = (m0[t] & ~a1 & ~a2) & ~b1 & ~b2;
   }
 }
 
@@ -81,64 +114,100 @@ __device__ __forceinline__ bool warp_empty(const uint32_t (&m1)[T], const uint32
   return !__any_sync(0xffffffffu, any != 0);
 }
 
-// Walk program words [pc, end) for this warp's T words.  lane_base points at
-// the lane's first staged word (row = lane's translation row); valid[t] masks
-// the translations that exist (x < W, row < H).
+// Valid translations of a tile: word t of the lane's row holds translations
+// x = 32 (j0 + t) + bit; those with x < W in a row y < H exist (and, with a
+// selection, only the selected ones).
 template <int T>
-__device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, int64_t pc, int64_t end,
-                                           const uint32_t* lane_base, const uint32_t (&valid)[T], int lane,
-                                           unsigned long long* __restrict__ counts, int64_t n_full,
-                                           int64_t base) {
+__device__ __forceinline__ void tile_valid(int y, int H, int W, int nw, int j0, const uint32_t* __restrict__ sel,
+                                           uint32_t (&v)[T]) {
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int j = j0 + t;
+    uint32_t m = 0;
+    if (y < H && j < nw) {
+      const int rem = W - 32 * j;
+      m = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+      if (sel) m &= sel[(size_t)y * nw + j];
+    }
+    v[t] = m;
+  }
+}
+
+// Walk program groups [pc, end) for this warp's tile.  lane_base points at
+// the lane's first staged word (row = the lane's translation row).  Counts
+// go to counts[base + vec] (phase 0) and counts[n_full + base + vec] (phase
+// 1).  Returns the pixels this warp walked (for the work statistics).
+template <int T>
+__device__ __forceinline__ uint32_t walk_unit(const uint4* __restrict__ prog, uint32_t pc, uint32_t end,
+                                              const uint32_t* lane_base, int y, int H, int W, int nw, int j0,
+                                              const uint32_t* __restrict__ sel, int lane,
+                                              unsigned long long* __restrict__ counts, int64_t n_full,
+                                              int64_t base) {
   uint32_t m1[T], m0[T];
   uint32_t st1[kWalkStack][T], st0[kWalkStack][T];
+  tile_valid<T>(y, H, W, nw, j0, sel, m1);
 #pragma unroll
-  for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
+  for (int t = 0; t < T; ++t) m0[t] = m1[t];
+  uint32_t walked = 0;
+  uint4 hd = pc < end ? __ldg(prog + pc) : make_uint4(0u, 0u, 0u, 0u);
   while (pc < end) {
-    const int64_t rec = pc;
-    const uint32_t hdr = __ldg(prog + pc++);
+    const uint32_t rec = pc;
+    const uint32_t hdr = hd.x, skip = hd.z, cnt = hd.w;
+    const uint32_t n_pg = cnt & kCntMask, n_sg = (cnt >> kCntBits) & kCntMask, half = cnt >> (2 * kCntBits);
+    const uint32_t next = rec + 1u + n_pg + n_sg + half;
+    const int vec = (int)hd.y;
+    hd = next < end ? __ldg(prog + next) : make_uint4(0u, 0u, 0u, 0u);  // fetched while this record runs
     if (hdr & kReset) {
+      tile_valid<T>(y, H, W, nw, j0, sel, m1);
 #pragma unroll
-      for (int t = 0; t < T; ++t) { m1[t] = valid[t]; m0[t] = valid[t]; }
+      for (int t = 0; t < T; ++t) m0[t] = m1[t];
     }
     if (hdr & kRestore) {
       const int l = (hdr >> kRlevelShift) & kLevelMask;
 #pragma unroll
       for (int t = 0; t < T; ++t) { m1[t] = st1[l][t]; m0[t] = st0[l][t]; }
     }
-    int vec = -1;
-    uint32_t skip = 0;
-    if (hdr & kEmit) vec = (int)__ldg(prog + pc++);
-    if (hdr & (kEmit | kPush)) skip = __ldg(prog + pc++);
-    const int np = (int)__ldg(prog + pc++);  // pixel pairs sharing a staged word window
-    pc = (pc + 3) & ~int64_t(3);
-    const int ns = (int)(hdr & kNpixMask) - 2 * np;
-    {  // np is a multiple of 4
-      const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
-      for (int q = 0; q < (np >> 2); ++q) walk_pair4<T>(lane_base, __ldg(q4 + q), m1, m0);
-      pc += np;
-    }
-    const uint4* q4 = reinterpret_cast<const uint4*>(prog + pc);
-    const int n4 = ns >> 2;
-    if (n4 > 0) {
-      uint4 nxt = __ldg(q4);
-      for (int q = 0; q < n4; ++q) {
-        const uint4 cur = nxt;
-        if (q + 1 < n4) nxt = __ldg(q4 + q + 1);
-        walk_and4<T>(lane_base, cur, m1, m0);
+    const uint32_t n = hdr & kNpixMask;
+    walked += n;
+    bool dead = false;
+    const uint4* g = prog + rec + 1u;
+    for (uint32_t q = 0; q < n_pg; ++q) {
+      walk_pairs2<T>(lane_base, __ldg(g + q), m1, m0);
+      if ((q & 1u) && skip != 0u && warp_empty<T>(m1, m0)) {
+        dead = true;
+        walked -= n - 4u * (q + 1u);  // pixels not walked (pair groups hold four pixels of the record)
+        break;
       }
     }
-    for (int i = n4 * 4; i < ns; ++i) walk_and1<T>(lane_base, __ldg(prog + pc + i), m1, m0);
-    pc += ns;
+    if (!dead) {
+      g += n_pg;
+      for (uint32_t q = 0; q < n_sg; ++q) {
+        walk_singles4<T>(lane_base, __ldg(g + q), m1, m0);
+        if ((q & 1u) && skip != 0u && warp_empty<T>(m1, m0)) {
+          dead = true;
+          const uint32_t done = 4u * (n_pg + q + 1u);
+          walked -= n > done ? n - done : 0u;
+          break;
+        }
+      }
+      if (!dead && half) {
+        const uint4 P = __ldg(g + n_sg);
+        walk_singles2<T>(lane_base, P.x, P.y, m1, m0);
+      }
+    }
+    if (dead) {
+      pc = rec + skip;
+      hd = pc < end ? __ldg(prog + pc) : make_uint4(0u, 0u, 0u, 0u);
+      continue;
+    }
     if (hdr & (kEmit | kPush)) {
       // Empty for the whole warp (one vote): so is every count below this node.
-      uint32_t any = 0;
-#pragma unroll
-      for (int t = 0; t < T; ++t) any |= m1[t] | m0[t];
-      if (!__any_sync(0xffffffffu, any != 0) && skip != 0) {
+      if (skip != 0u && warp_empty<T>(m1, m0)) {
         pc = rec + skip;
+        hd = pc < end ? __ldg(prog + pc) : make_uint4(0u, 0u, 0u, 0u);
         continue;
       }
-      if (vec >= 0) {
+      if (hdr & kEmit) {
         uint32_t c = 0;
 #pragma unroll
         for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
@@ -155,7 +224,9 @@ __device__ __forceinline__ void walk_piece(const uint32_t* __restrict__ prog, in
 #pragma unroll
       for (int t = 0; t < T; ++t) { st1[l][t] = m1[t]; st0[l][t] = m0[t]; }
     }
+    pc = next;
   }
+  return walked;
 }
 
 }  // namespace lpf

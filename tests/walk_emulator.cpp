@@ -10,6 +10,7 @@
 // jumps to a record's skip target when no translation of the tile is left (at
 // the end of an emitting or branching record, or after every 8 pixels inside
 // a record).
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -76,54 +77,57 @@ extern "C" int emulate_walk(const uint8_t* img, int H, int W, int rx, int ry, in
             }
             valid[lane * T + t] = m1[lane * T + t] = m0[lane * T + t] = v;
           }
-        auto and_pixel = [&](uint32_t word, bool pair) {
+        // AND pixel `word` ((byte offset << 5) | shift) into the masks; a
+        // pair reads the window of `word` with a second shift `shift2`.
+        auto and_pixel = [&](uint32_t word, uint32_t shift) {
           for (int lane = 0; lane < 32; ++lane) {
             const uint32_t* lb = packed.data() + (size_t)(band * 32 + lane) * S + g * T;
-            const uint32_t* sa = lb + ((pair ? (word >> 10) : (word >> 5)) >> 2);  // byte offset -> word
+            const uint32_t* sa = lb + ((word >> 5) >> 2);  // byte offset -> word
             for (int t = 0; t < T; ++t) {
-              const uint32_t a1 = funnel_r(sa[t], sa[t + 1], pair ? (word >> 5) : word);
-              const uint32_t a2 = pair ? funnel_r(sa[t], sa[t + 1], word) : a1;
-              m1[lane * T + t] &= a1 & a2;
-              m0[lane * T + t] &= ~(a1 | a2);
+              const uint32_t a = funnel_r(sa[t], sa[t + 1], shift);
+              m1[lane * T + t] &= a;
+              m0[lane * T + t] &= ~a;
             }
           }
         };
-        int64_t pc = piece[pi];
+        int64_t pc = piece[pi];  // in 16-byte groups
         const int64_t end = piece[pi + 1];
         while (pc < end) {
           const int64_t rec = pc;
-          const uint32_t h = w[pc++];
+          const uint32_t* hg = &w[4 * (size_t)pc];
+          const uint32_t h = hg[0], vecw = hg[1], skip = hg[2], cnt = hg[3];
+          const uint32_t n_pg = cnt & kCntMask, n_sg = (cnt >> kCntBits) & kCntMask, half = cnt >> (2 * kCntBits);
           if (h & kReset) { m1 = valid; m0 = valid; }
           if (h & kRestore) {
             const int l = (h >> kRlevelShift) & kLevelMask;
             for (int i = 0; i < L; ++i) { m1[i] = st1[l * L + i]; m0[i] = st0[l * L + i]; }
           }
-          int vec = -1;
-          uint32_t skip = 0;
-          if (h & kEmit) vec = (int)w[pc++];
-          if (h & (kEmit | kPush)) skip = w[pc++];
-          const int np = (int)w[pc++];
-          pc = (pc + 3) & ~int64_t(3);
-          const int n = (int)(h & kNpixMask), ns = n - 2 * np;
-          pairs += np;
+          const int vec = (h & kEmit) ? (int)vecw : -1;
+          const int n = (int)(h & kNpixMask);
+          pairs += 2 * n_pg;
           bool dead = false;
-          int done = 0;
-          for (int q = 0; q < np / 4 && !dead; ++q) {
-            for (int k = 0; k < 4; ++k) and_pixel(w[pc + 4 * q + k], true);
-            done += 8;
-            if (skip && empty()) dead = true;
-          }
-          const int64_t ps = pc + np;
-          const int n4 = dead ? 0 : ns / 4;
-          for (int q = 0; q < n4 && !dead; ++q) {
-            for (int k = 0; k < 4; ++k) and_pixel(w[ps + 4 * q + k], false);
+          int64_t done = 0;
+          const uint32_t* gp = hg + 4;
+          for (uint32_t q = 0; q < n_pg && !dead; ++q, gp += 4) {
+            and_pixel(gp[0], gp[0]);
+            and_pixel(gp[0], gp[1]);
+            and_pixel(gp[2], gp[2]);
+            and_pixel(gp[2], gp[3]);
             done += 4;
             if ((q & 1) && skip && empty()) dead = true;
           }
-          if (!dead)
-            for (int i = n4 * 4; i < ns; ++i) { and_pixel(w[ps + i], false); ++done; }
-          walked += done;
-          pc = ps + ns;
+          for (uint32_t q = 0; q < n_sg && !dead; ++q, gp += 4) {
+            for (int k = 0; k < 4; ++k) and_pixel(gp[k], gp[k]);
+            done += 4;
+            if ((q & 1) && skip && empty()) dead = true;
+          }
+          if (!dead && half) {
+            and_pixel(gp[0], gp[0]);
+            and_pixel(gp[1], gp[1]);
+            done += 2;
+          }
+          walked += std::min<int64_t>(done, n);
+          pc = rec + 1 + n_pg + n_sg + half;
           if (dead) { pc = rec + skip; ++skips; continue; }
           if (h & (kEmit | kPush)) {
             if (skip && empty()) { pc = rec + skip; ++skips; continue; }
