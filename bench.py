@@ -260,6 +260,55 @@ def extra_s2(lpf, reps: int = 20):
     return {"workload": "s2_fft 512x512, one phase, double-precision FFT", "ms_per_call": a.elapsed_time(b) / reps}
 
 
+def extra_proposer(lpf):
+    """Learned proposer (config 5): swaps to reach the uniform run's error.
+    128x128 cell, |v| <= 64, target from the 512x512 clustered-disk original;
+    uniform runs of N = 10^5 evaluations (the budget of this measurement) on 5
+    evaluation seeds; network trained on snapshots logged by uniform runs with
+    3 other seeds; ratio = N / evaluations of the network's run until it first
+    reaches the uniform run's final error; median over the seeds."""
+    from paper_1601_04359_gb300 import proposer
+    t0 = time.perf_counter()
+    res = proposer.evaluate(n_step=100000)
+    run = res["runs"][0]
+    return {"workload": "learned proposer, 128x128 cell |v|<=64, N=1e5 uniform evaluations per seed",
+            "median_ratio": run["median_ratio"], "target_ratio": 3.0,
+            "ratios": [s["ratio"] for s in run["per_seed"]], "eval_seeds": res["eval_seeds"],
+            "train_seeds": res["train_seeds"], "tau": run["tau"], "epsilon": run["epsilon"],
+            "train_and_collect_seconds": res["train_and_collect_seconds"],
+            "seconds": time.perf_counter() - t0}
+
+
+def extra_cnn_train(lpf, reps: int = 20):
+    """One Adam step of the proposal network on 8 snapshots of a 128x128 cell
+    (8 forward + backward passes on the tensor cores)."""
+    import numpy as np
+    import torch
+
+    import synth
+    H = W = 128
+    net = lpf.lpf_cnn_create(H, W, 3)
+    B, n = 8, 64
+    rng = np.random.default_rng(0)
+    cells = np.stack([synth.clustered_disks(H, W, 0.3, seed=10 + i) for i in range(B)])
+    pairs = np.stack([synth.swap_candidates(c, n, seed=i) for i, c in enumerate(cells)])
+    y = rng.normal(size=(B, n)).astype(np.float32)
+    c, p, t = (torch.from_numpy(v).cuda() for v in (cells, pairs, y))
+    for _ in range(3):
+        lpf.lpf_cnn_train_step(net, c, p, t, 1e-3)
+    a, b = _events()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        lpf.lpf_cnn_train_step(net, c, p, t, 1e-3)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    flop = 3 * 2 * H * W * 9 * sum(ci * co for ci, co in zip((2, 32, 64, 48, 32), (32, 64, 48, 32, 2))) * B
+    return {"workload": "proposal network, Adam step on 8 snapshots of 128x128 (forward + backward)",
+            "ms_per_step": ms, "tflops": flop / (ms / 1000.0) / 1e12}
+
+
 def cpu_model() -> str:
     """Name of the host CPU (lscpu, else /proc/cpuinfo, else the platform)."""
     import platform
@@ -566,7 +615,7 @@ def main():
     if not args.no_extras and ws == 1:
         extras = {}
         for name, fn in (("delta_swap", extra_delta), ("annealing", extra_sa), ("batched", extra_batch),
-                         ("s2_fft", extra_s2)):
+                         ("s2_fft", extra_s2), ("cnn_train", extra_cnn_train), ("proposer", extra_proposer)):
             try:
                 extras[name] = fn(lpf)
             except Exception as exc:  # report, do not hide, a failing extra

@@ -14,6 +14,15 @@ periodic medium's wrap, followed by ReLU except the last):
 Weights W_l[tap][cin][cout] with tap = (dy+1)*3 + (dx+1), dy, dx in {-1,0,1};
 out[y][x][co] = b[co] + sum_tap sum_ci in[(y+dy)%H][(x+dx)%W][ci] * W[tap][ci][co].
 
+Operand rounding (optional): the network's arithmetic contract is bfloat16
+weights and activations with float32 accumulation (gradients enter products
+as two bfloat16 terms, close to float32).  Callers pass bfloat16-rounded
+weights; `rnd`, when given, is applied to the layer inputs where they enter
+a product (the forward convolutions and the weight-gradient products), so
+that a comparison with the library isolates the order of float32
+accumulation.  Gradients, bias gradients and ReLU masks are not rounded.
+With rnd = None everything stays float64.
+
 Loss of one snapshot with logged candidates (a_i, b_i, y_i), i = 1..n:
   L = 1/(2n) * sum_i (s1[a_i] + s0[b_i] - y_i)^2, or (listwise) the
   cross-entropy -sum_i q_i log p_i with q = softmax(y / beta) and
@@ -63,12 +72,17 @@ def conv(x, w, b):
     return out + b
 
 
-def forward(params, x):
+def _id(a):
+    return a
+
+
+def forward(params, x, rnd=None):
     """Returns the output [H][W][2] and the list of layer inputs (for backward)."""
+    r = rnd or _id
     acts = [x]
     h = x
     for li, (w, b) in enumerate(params):
-        h = conv(h, w, b)
+        h = conv(r(h), w, b)
         if li < len(params) - 1:
             h = np.maximum(h, 0.0)
         acts.append(h)
@@ -121,26 +135,28 @@ def listwise_grad_out(out, a_idx, b_idx, y, beta: float):
     return g
 
 
-def backward(params, acts, gout):
+def backward(params, acts, gout, rnd=None):
     """Gradients [(dW, db), ...] of the loss given dL/d out."""
+    r = rnd or _id
     grads = [None] * len(params)
     g = gout
     for li in range(len(params) - 1, -1, -1):
         w, b = params[li]
-        x = acts[li]
+        x = r(acts[li])
         if li < len(params) - 1:
             g = g * (acts[li + 1] > 0)       # ReLU: act > 0 exactly where its input was > 0
+        gr = g
         dw = np.zeros_like(w)
         for tap in range(9):
             dy, dx = tap // 3 - 1, tap % 3 - 1
             xs = _shift(x, dy, dx)
-            dw[tap] = xs.reshape(-1, xs.shape[2]).T @ g.reshape(-1, g.shape[2])
+            dw[tap] = xs.reshape(-1, xs.shape[2]).T @ gr.reshape(-1, gr.shape[2])
         db = g.sum(axis=(0, 1))
         grads[li] = (dw, db)
         if li > 0:
             gx = np.zeros_like(x)
             for tap in range(9):
                 dy, dx = tap // 3 - 1, tap % 3 - 1
-                gx += _shift(g @ w[tap].T, -dy, -dx)
+                gx += _shift(gr @ w[tap].T, -dy, -dx)
             g = gx
     return grads

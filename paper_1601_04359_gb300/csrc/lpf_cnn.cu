@@ -10,7 +10,12 @@
 // periodic), ReLU between them: 2 -> 32 -> 64 -> 48 -> 32 -> 2 channels,
 // 61,234 parameters.  Input channels: cell value, interfacial mask.
 // Weights: float32 master copies updated by Adam, bfloat16 copies used by the
-// forward and backward passes; activations and accumulation in float32.
+// forward and backward passes.  The convolutions (forward, input gradient,
+// weight gradient) are implicit GEMMs on the tensor cores (mma.sync,
+// bfloat16 operands, float32 accumulation): activations are kept in float32
+// and rounded to bfloat16 where they enter a product; gradients enter as two
+// bfloat16 terms (high and low part, about 16 significant bits), because
+// their sums over pixels cancel and a single rounding loses too much.
 //
 // Layouts: activations [H][W][C] (channels innermost); weights [9][Cin][Cout]
 // with tap = (dy+1)*3 + (dx+1); parameter vector = for each layer W then b.
@@ -29,8 +34,6 @@ namespace lpf {
 
 constexpr int kLayers = 5;
 constexpr int kCh[kLayers + 1] = {2, 32, 64, 48, 32, 2};
-constexpr int kTile = 16;        // output tile 16 x 16 pixels per block
-constexpr int kCinChunk = 8;     // input channels staged per step
 
 inline int layer_w_size(int l) { return 9 * kCh[l] * kCh[l + 1]; }
 
@@ -48,160 +51,365 @@ __global__ void cnn_features_kernel(const uint8_t* __restrict__ cell, int H, int
   }
 }
 
-// out[p][co] = bias[co] + sum_tap sum_ci in[p + off(tap)][ci] * w[tap][ci][co],
-// circular; optional ReLU; optional mask: out *= (mask[p][co] > 0).
-// `flip` reads the weights as w[8 - tap][co][ci] (the transposed convolution
-// used for input gradients; then CIN/COUT are the layer's Cout/Cin).
-template <int COUT>
-__global__ void __launch_bounds__(kTile* kTile) cnn_conv_kernel(const float* __restrict__ in, int H, int W, int CIN,
-                                                               const __nv_bfloat16* __restrict__ w, int flip,
-                                                               const float* __restrict__ bias, int relu,
-                                                               const float* __restrict__ mask,
-                                                               float* __restrict__ out) {
-  __shared__ float s_in[(kTile + 2) * (kTile + 2) * kCinChunk];
-  __shared__ float s_w[9 * kCinChunk * COUT];
-  const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
-  const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
-  const int px = x0 + tx, py = y0 + ty;
-  float acc[COUT];
-#pragma unroll
-  for (int c = 0; c < COUT; ++c) acc[c] = bias ? bias[c] : 0.0f;
-  for (int c0 = 0; c0 < CIN; c0 += kCinChunk) {
-    const int cn = min(kCinChunk, CIN - c0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < (kTile + 2) * (kTile + 2) * kCinChunk; i += blockDim.x) {
-      const int ci = i % kCinChunk, q = i / kCinChunk;
-      const int ly = q / (kTile + 2), lx = q - ly * (kTile + 2);
-      int gy = (y0 + ly - 1) % H; if (gy < 0) gy += H;
-      int gx = (x0 + lx - 1) % W; if (gx < 0) gx += W;
-      s_in[i] = ci < cn ? in[((int64_t)gy * W + gx) * CIN + c0 + ci] : 0.0f;
+// ---- convolutions as implicit GEMMs on the tensor cores ------------------
+//
+// Operands are bfloat16 (weights as stored; activations and gradients
+// rounded to nearest even when staged), products accumulate in float32 with
+// mma.sync.m16n8k16.  A block owns a tile of kTH x kTW output pixels; the
+// input tile with its one-pixel circular halo is staged in shared memory as
+// [pixel][channel] rows (channel counts padded to multiples of 16, rows
+// padded by 8 bf16 so that the fragment loads of 8 consecutive pixels hit
+// distinct banks).
+
+constexpr int kTH = 8, kTW = 16;                 // output tile: 8 rows of 16 pixels (one M fragment per row)
+constexpr int kHalo = (kTH + 2) * (kTW + 2);     // staged input pixels
+constexpr int kConvThreads = 32 * kTH;           // a warp per tile row
+constexpr int kDwThreads = 32 * 9;               // a warp per tap
+
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldmatrix_x4_trans(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
+                                                  uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void ldmatrix_x2_trans(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// Stage the block's input tile with its circular halo: s[(ly*(kTW+2) + lx)][k]
+// = bf16(in[(y0+ly-1) % H][(x0+lx-1) % W][k]) for k < C, 0 up to KC.
+// With lo != null (split operand) also lo[...] = bf16(v - hi): the value as
+// two bfloat16 terms, hi + lo, about 16 significant bits.
+template <int KC>
+__device__ __forceinline__ void stage_halo(const float* __restrict__ in, int H, int W, int C, int x0, int y0,
+                                           __nv_bfloat16* s, __nv_bfloat16* lo = nullptr) {
+  constexpr int KS = KC + 8;
+  constexpr int KP = KC / 2;  // channel pairs
+  for (int i = threadIdx.x; i < kHalo * KP; i += blockDim.x) {
+    const int q = i / KP, k = 2 * (i - q * KP);
+    const int ly = q / (kTW + 2), lx = q - ly * (kTW + 2);
+    int gy = (y0 + ly - 1) % H; if (gy < 0) gy += H;
+    int gx = (x0 + lx - 1) % W; if (gx < 0) gx += W;
+    const float* src = in + ((int64_t)gy * W + gx) * C;
+    const float v0 = k < C ? src[k] : 0.0f, v1 = k + 1 < C ? src[k + 1] : 0.0f;
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+    *reinterpret_cast<__nv_bfloat162*>(s + q * KS + k) = h;
+    if (lo) {
+      const float2 hf = __bfloat1622float2(h);
+      *reinterpret_cast<__nv_bfloat162*>(lo + q * KS + k) = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
     }
-    for (int i = threadIdx.x; i < 9 * kCinChunk * COUT; i += blockDim.x) {
-      const int co = i % COUT, r = i / COUT;
-      const int ci = r % kCinChunk, tap = r / kCinChunk;
-      float v = 0.0f;
-      if (ci < cn) {
-        const int cig = c0 + ci;
-        v = flip ? __bfloat162float(w[((int64_t)(8 - tap) * COUT + co) * CIN + cig])
-                 : __bfloat162float(w[((int64_t)tap * CIN + cig) * COUT + co]);
+  }
+}
+
+// out[p][n] = bias[n] + sum_tap sum_k in[p + off(tap)][k] * B[tap][k][n], circular.
+// Forward (flip = 0): k = ci, n = co, B[tap][k][n] = w[tap][k][n] (w of shape
+// [9][K][N]).  Input gradient (flip = 1, the transposed convolution): k = the
+// layer's output channel, n = its input channel, B[tap][k][n] = w[8 - tap][n][k]
+// (w of shape [9][N][K]).  Optional ReLU; optional mask: out = 0 where
+// mask[p][n] <= 0 (the ReLU derivative of the layer input).  K <= KC, N <= NC.
+template <int KC, int NC, bool SPLIT>
+__global__ void __launch_bounds__(kConvThreads) cnn_conv_mma_kernel(const float* __restrict__ in, int H, int W,
+                                                                    int K, int N, const __nv_bfloat16* __restrict__ w,
+                                                                    int flip, const float* __restrict__ bias,
+                                                                    int relu, const float* __restrict__ mask,
+                                                                    float* __restrict__ out) {
+  constexpr int KS = KC + 8;
+  extern __shared__ __align__(16) __nv_bfloat16 csm[];
+  __nv_bfloat16* s_in = csm;                 // [kHalo][KS]
+  __nv_bfloat16* s_w = csm + kHalo * KS;     // [9][NC][KS]  (n rows, k contiguous)
+  __nv_bfloat16* s_lo = s_w + 9 * NC * KS;   // SPLIT: [kHalo][KS], the input's low bfloat16 terms
+  const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+  stage_halo<KC>(in, H, W, K, x0, y0, s_in, SPLIT ? s_lo : nullptr);
+  for (int i = threadIdx.x; i < 9 * NC * KC; i += blockDim.x) {
+    const int k = i % KC, r = i / KC;
+    const int n = r % NC, tap = r / NC;
+    float v = 0.0f;
+    if (k < K && n < N)
+      v = flip ? __bfloat162float(w[((int64_t)(8 - tap) * N + n) * K + k])
+               : __bfloat162float(w[((int64_t)tap * K + k) * N + n]);
+    s_w[r * KS + k] = __float2bfloat16(v);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gid = lane >> 2, tig = lane & 3;
+  float acc[NC / 8][4];
+#pragma unroll
+  for (int f = 0; f < NC / 8; ++f) {
+    const int n = f * 8 + tig * 2;
+    const float b0 = (bias && n < N) ? bias[n] : 0.0f, b1 = (bias && n + 1 < N) ? bias[n + 1] : 0.0f;
+    acc[f][0] = b0; acc[f][1] = b1; acc[f][2] = b0; acc[f][3] = b1;
+  }
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    const int dy = tap / 3, dx = tap - dy * 3;
+    // A rows: the 16 output pixels of tile row `warp`, shifted by the tap
+    const __nv_bfloat16* arow = s_in + ((warp + dy) * (kTW + 2) + dx) * KS;
+    const __nv_bfloat16* brow = s_w + tap * NC * KS;
+#pragma unroll
+    for (int kk = 0; kk < KC / 16; ++kk) {
+      const int kc = kk * 16 + tig * 2;
+      const uint32_t a0 = *reinterpret_cast<const uint32_t*>(arow + gid * KS + kc);
+      const uint32_t a1 = *reinterpret_cast<const uint32_t*>(arow + (gid + 8) * KS + kc);
+      const uint32_t a2 = *reinterpret_cast<const uint32_t*>(arow + gid * KS + kc + 8);
+      const uint32_t a3 = *reinterpret_cast<const uint32_t*>(arow + (gid + 8) * KS + kc + 8);
+      uint32_t l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+      if constexpr (SPLIT) {
+        const __nv_bfloat16* lrow = arow - s_in + s_lo;
+        l0 = *reinterpret_cast<const uint32_t*>(lrow + gid * KS + kc);
+        l1 = *reinterpret_cast<const uint32_t*>(lrow + (gid + 8) * KS + kc);
+        l2 = *reinterpret_cast<const uint32_t*>(lrow + gid * KS + kc + 8);
+        l3 = *reinterpret_cast<const uint32_t*>(lrow + (gid + 8) * KS + kc + 8);
       }
-      s_w[i] = v;
-    }
-    __syncthreads();
-    if (px < W && py < H) {
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
-        const float* xi = s_in + ((ty + dy) * (kTile + 2) + (tx + dx)) * kCinChunk;
-        const float* wi = s_w + tap * kCinChunk * COUT;
-        for (int ci = 0; ci < cn; ++ci) {
-          const float xv = xi[ci];
-#pragma unroll
-          for (int c = 0; c < COUT; ++c) acc[c] = fmaf(xv, wi[ci * COUT + c], acc[c]);
-        }
+      for (int f = 0; f < NC / 8; ++f) {
+        const __nv_bfloat16* bn = brow + (f * 8 + gid) * KS + kc;
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bn), b1 = *reinterpret_cast<const uint32_t*>(bn + 8);
+        mma_bf16(acc[f], a0, a1, a2, a3, b0, b1);
+        if constexpr (SPLIT) mma_bf16(acc[f], l0, l1, l2, l3, b0, b1);
       }
     }
   }
-  if (px < W && py < H) {
+  const int py = y0 + warp;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int px = x0 + gid + 8 * h;
+    if (py >= H || px >= W) continue;
     const int64_t p = (int64_t)py * W + px;
 #pragma unroll
-    for (int c = 0; c < COUT; ++c) {
-      float v = acc[c];
-      if (relu) v = fmaxf(v, 0.0f);
-      if (mask && !(mask[p * COUT + c] > 0.0f)) v = 0.0f;
-      out[p * COUT + c] = v;
-    }
+    for (int f = 0; f < NC / 8; ++f)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int n = f * 8 + tig * 2 + e;
+        if (n >= N) continue;
+        float v = acc[f][2 * h + e];
+        if (relu) v = fmaxf(v, 0.0f);
+        if (mask && !(mask[p * N + n] > 0.0f)) v = 0.0f;
+        out[p * N + n] = v;
+      }
   }
 }
 
-// dw[tap][ci][co] (+)= sum_p in[p + off(tap)][ci] * g[p][co]; one block per
-// (tap, ci), threads = co x 4 row quarters, quarters summed in order.
-__global__ void cnn_dw_kernel(const float* __restrict__ in, const float* __restrict__ g, int H, int W, int CIN,
-                              int COUT, float* __restrict__ dw, int accumulate) {
-  extern __shared__ float s_part[];
-  const int tap = blockIdx.x / CIN, ci = blockIdx.x - tap * CIN;
-  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-  const int co = threadIdx.x % COUT, quarter = threadIdx.x / COUT;
-  const int y0 = quarter * ((H + 3) / 4), y1 = min(H, y0 + (H + 3) / 4);
-  float acc = 0.0f;
-  for (int y = y0; y < y1; ++y) {
-    int sy = y + dy; sy = sy < 0 ? sy + H : (sy >= H ? sy - H : sy);
-    const float* irow = in + (int64_t)sy * W * CIN + ci;
-    const float* grow = g + (int64_t)y * W * COUT + co;
-    for (int x = 0; x < W; ++x) {
-      int sx = x + dx; sx = sx < 0 ? sx + W : (sx >= W ? sx - W : sx);
-      acc = fmaf(irow[(int64_t)sx * CIN], grow[(int64_t)x * COUT], acc);
+// Weight and bias gradients of one layer, per block (partial sums over the
+// block's output tile): part[blk][tap][ci][co] = sum_p in[p + off(tap)][ci] *
+// g[p][co] and part_b[blk][co] = sum_p g[p][co].  GEMM per tap with M = ci,
+// N = co, K = the tile's pixels; warp t computes tap t.  Pixels outside the
+// image contribute nothing (their gradient rows are staged as zeros).
+template <int KC, int NC>
+__global__ void __launch_bounds__(kDwThreads) cnn_dw_mma_kernel(const float* __restrict__ in,
+                                                                const float* __restrict__ g, int H, int W, int CIN,
+                                                                int COUT, float* __restrict__ part,
+                                                                float* __restrict__ part_b) {
+  constexpr int KS = KC + 8, NS = NC + 8;
+  extern __shared__ __align__(16) __nv_bfloat16 csm[];
+  __nv_bfloat16* s_in = csm;                          // [kHalo][KS]
+  __nv_bfloat16* s_g = csm + kHalo * KS;              // [kTH * kTW][NS], gradient high terms
+  __nv_bfloat16* s_gl = s_g + kTH * kTW * NS;         // and low terms (the gradient as hi + lo)
+  const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+  const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+  stage_halo<KC>(in, H, W, CIN, x0, y0, s_in);
+  for (int i = threadIdx.x; i < kTH * kTW * (NC / 2); i += blockDim.x) {
+    const int q = i / (NC / 2), n = 2 * (i - q * (NC / 2));
+    const int py = y0 + q / kTW, px = x0 + q % kTW;
+    float v0 = 0.0f, v1 = 0.0f;
+    if (py < H && px < W) {
+      const float* src = g + ((int64_t)py * W + px) * COUT;
+      v0 = n < COUT ? src[n] : 0.0f;
+      v1 = n + 1 < COUT ? src[n + 1] : 0.0f;
+    }
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+    const float2 hf = __bfloat1622float2(h);
+    *reinterpret_cast<__nv_bfloat162*>(s_g + q * NS + n) = h;
+    *reinterpret_cast<__nv_bfloat162*>(s_gl + q * NS + n) = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+  }
+  // bias partial: fixed order over the tile's pixels (float32, no rounding)
+  if ((int)threadIdx.x < COUT) {
+    float sb = 0.0f;
+    for (int q = 0; q < kTH * kTW; ++q) {
+      const int py = y0 + q / kTW, px = x0 + q % kTW;
+      if (py < H && px < W) sb += g[((int64_t)py * W + px) * COUT + threadIdx.x];
+    }
+    part_b[(int64_t)blk * COUT + threadIdx.x] = sb;
+  }
+  __syncthreads();
+  const int tap = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int dy = tap / 3, dx = tap - dy * 3;
+  float acc[KC / 16][NC / 8][4];
+#pragma unroll
+  for (int m = 0; m < KC / 16; ++m)
+#pragma unroll
+    for (int f = 0; f < NC / 8; ++f)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[m][f][e] = 0.0f;
+  // ldmatrix row addresses: lane L serves matrix L/8, row L%8
+  const int mat = lane >> 3, row = lane & 7;
+#pragma unroll 1
+  for (int r = 0; r < kTH; ++r) {  // K step: the 16 pixels of tile row r
+    const __nv_bfloat16* arow = s_in + ((r + dy) * (kTW + 2) + dx) * KS;  // pixel k of the step -> arow + k*KS
+    const __nv_bfloat16* grow = s_g + (r * kTW) * NS;
+    const __nv_bfloat16* glow = s_gl + (r * kTW) * NS;
+    uint32_t b[NC / 8][2], bl[NC / 8][2];
+    if constexpr (NC >= 16) {
+#pragma unroll
+      for (int f = 0; f < NC / 8; f += 2) {
+        // matrices: (k 0-7, n f), (k 8-15, n f), (k 0-7, n f+1), (k 8-15, n f+1)
+        const int k = row + ((mat & 1) ? 8 : 0), n = (f + (mat >> 1)) * 8;
+        ldmatrix_x4_trans(smem_addr(grow + k * NS + n), b[f][0], b[f][1], b[f + 1][0], b[f + 1][1]);
+        ldmatrix_x4_trans(smem_addr(glow + k * NS + n), bl[f][0], bl[f][1], bl[f + 1][0], bl[f + 1][1]);
+      }
+    } else {
+      const int k = row + ((mat & 1) ? 8 : 0);
+      ldmatrix_x2_trans(smem_addr(grow + k * NS), b[0][0], b[0][1]);
+      ldmatrix_x2_trans(smem_addr(glow + k * NS), bl[0][0], bl[0][1]);
+    }
+#pragma unroll
+    for (int m = 0; m < KC / 16; ++m) {
+      // A[m = ci][k = pixel] from s_in[pixel][ci]: matrices (ci 0-7, k 0-7),
+      // (ci 8-15, k 0-7), (ci 0-7, k 8-15), (ci 8-15, k 8-15)
+      const int k = row + ((mat >> 1) ? 8 : 0), c = m * 16 + ((mat & 1) ? 8 : 0);
+      uint32_t a0, a1, a2, a3;
+      ldmatrix_x4_trans(smem_addr(arow + k * KS + c), a0, a1, a2, a3);
+#pragma unroll
+      for (int f = 0; f < NC / 8; ++f) {
+        mma_bf16(acc[m][f], a0, a1, a2, a3, b[f][0], b[f][1]);
+        mma_bf16(acc[m][f], a0, a1, a2, a3, bl[f][0], bl[f][1]);
+      }
     }
   }
-  s_part[threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.x < COUT) {
-    const float s = ((s_part[co] + s_part[COUT + co]) + s_part[2 * COUT + co]) + s_part[3 * COUT + co];
-    const int64_t i = ((int64_t)tap * CIN + ci) * COUT + co;
-    dw[i] = accumulate ? dw[i] + s : s;
-  }
+  const int gid = lane >> 2, tig = lane & 3;
+  float* dst = part + ((int64_t)blk * 9 + tap) * CIN * COUT;
+#pragma unroll
+  for (int m = 0; m < KC / 16; ++m)
+#pragma unroll
+    for (int f = 0; f < NC / 8; ++f)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int ci = m * 16 + gid + (e >= 2 ? 8 : 0), co = f * 8 + tig * 2 + (e & 1);
+        if (ci < CIN && co < COUT) dst[ci * COUT + co] = acc[m][f][e];
+      }
 }
 
-// db[co] (+)= sum_p g[p][co], one block of COUT x 8 threads, parts summed in order.
-__global__ void cnn_db_kernel(const float* __restrict__ g, int npix, int COUT, float* __restrict__ db, int accumulate) {
-  extern __shared__ float s_part[];
-  const int co = threadIdx.x % COUT, part = threadIdx.x / COUT;
-  float acc = 0.0f;
-  if (part < 8)
-    for (int p = part; p < npix; p += 8) acc += g[(int64_t)p * COUT + co];
-  s_part[threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.x < COUT) {
+// dst[i] (+)= sum over blocks b of part[b][i], blocks in order (deterministic).
+__global__ void cnn_reduce_parts_kernel(const float* __restrict__ part, int n_blk, int n, float* __restrict__ dst,
+                                        int accumulate) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float s = 0.0f;
-    for (int q = 0; q < 8; ++q) s += s_part[q * COUT + co];
-    db[co] = accumulate ? db[co] + s : s;
+    for (int b = 0; b < n_blk; ++b) s += part[(int64_t)b * n + i];
+    dst[i] = accumulate ? dst[i] + s : s;
   }
 }
 
-// Loss of one snapshot and dL/d out (two pixels per candidate), in candidate
-// order by one thread (deterministic).  g must be zeroed beforehand.
+// g[idx] += v for one contribution per lane, deterministically: lanes with the
+// same index are combined by their lowest lane, in lane order.
+__device__ __forceinline__ void warp_scatter_add(float* __restrict__ g, int idx, float v, bool active) {
+  const unsigned act = __ballot_sync(0xffffffffu, active);
+  const unsigned peers = __match_any_sync(0xffffffffu, active ? idx : -1) & act;
+  const int lane = threadIdx.x & 31;
+  float sum = 0.0f;
+  for (unsigned m = peers; m; m &= m - 1) {
+    const int src = __ffs(m) - 1;
+    sum += __shfl_sync(peers, v, src);
+  }
+  if (active && lane == __ffs(peers) - 1) g[idx] += sum;
+  __syncwarp();
+}
+
+// Warp sum in a fixed tree order.
+__device__ __forceinline__ float warp_fsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_fmax(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Loss of one snapshot and dL/d out (two pixels per candidate), one warp:
+// candidates in chunks of 32 (lane = candidate), chunks in order
+// (deterministic).  g must be zeroed beforehand.
 __global__ void cnn_loss_kernel(const float* __restrict__ out, int W, const int32_t* __restrict__ pairs,
                                 const float* __restrict__ y, int n, float* __restrict__ g, float* __restrict__ loss,
                                 float scale) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
   float l = 0.0f;
-  for (int i = 0; i < n; ++i) {
-    const int a = pairs[2 * i], b = pairs[2 * i + 1];
-    const float r = out[2 * a + 1] + out[2 * b] - y[i];
-    l += 0.5f * r * r;
-    g[2 * a + 1] += r / n;
-    g[2 * b] += r / n;
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    const bool on = i < n;
+    int a = 0, b = 0;
+    float r = 0.0f;
+    if (on) {
+      a = pairs[2 * i];
+      b = pairs[2 * i + 1];
+      r = out[2 * a + 1] + out[2 * b] - y[i];
+    }
+    l += warp_fsum(on ? 0.5f * r * r : 0.0f);
+    warp_scatter_add(g, 2 * a + 1, r / n, on);
+    warp_scatter_add(g, 2 * b, r / n, on);
   }
-  if (loss) *loss += l / n * scale;
+  if (lane == 0 && loss) *loss += l / n * scale;
 }
 
 // Listwise loss of one snapshot: L = logsumexp(s) - sum_i q_i s_i with
 // s_i = s1[a_i] + s0[b_i] and q = softmax(y / beta); dL/ds_i = p_i - q_i on
-// both pixels of candidate i.  One thread, candidate order (deterministic).
+// both pixels of candidate i.  One warp, fixed reduction order (deterministic).
 __global__ void cnn_listwise_kernel(const float* __restrict__ out, const int32_t* __restrict__ pairs,
                                     const float* __restrict__ y, int n, float beta, float* __restrict__ g,
                                     float* __restrict__ loss, float scale) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
   float smax = -3.0e38f, ymax = -3.0e38f;
-  for (int i = 0; i < n; ++i) {
+  for (int i = lane; i < n; i += 32) {
     smax = fmaxf(smax, out[2 * pairs[2 * i] + 1] + out[2 * pairs[2 * i + 1]]);
     ymax = fmaxf(ymax, y[i] / beta);
   }
+  smax = warp_fmax(smax);
+  ymax = warp_fmax(ymax);
   float zs = 0.0f, zq = 0.0f;
-  for (int i = 0; i < n; ++i) {
+  for (int i = lane; i < n; i += 32) {
     zs += expf(out[2 * pairs[2 * i] + 1] + out[2 * pairs[2 * i + 1]] - smax);
     zq += expf(y[i] / beta - ymax);
   }
-  float l = smax + logf(zs);
-  for (int i = 0; i < n; ++i) {
-    const int a = pairs[2 * i], b = pairs[2 * i + 1];
-    const float si = out[2 * a + 1] + out[2 * b];
-    const float pi = expf(si - smax) / zs, qi = expf(y[i] / beta - ymax) / zq;
-    l -= qi * si;
-    g[2 * a + 1] += pi - qi;
-    g[2 * b] += pi - qi;
+  zs = warp_fsum(zs);
+  zq = warp_fsum(zq);
+  float lq = 0.0f;
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    const bool on = i < n;
+    int a = 0, b = 0;
+    float d = 0.0f;
+    if (on) {
+      a = pairs[2 * i];
+      b = pairs[2 * i + 1];
+      const float si = out[2 * a + 1] + out[2 * b];
+      const float pi = expf(si - smax) / zs, qi = expf(y[i] / beta - ymax) / zq;
+      lq += qi * si;
+      d = pi - qi;
+    }
+    warp_scatter_add(g, 2 * a + 1, d, on);
+    warp_scatter_add(g, 2 * b, d, on);
   }
-  if (loss) *loss += l * scale;
+  lq = warp_fsum(lq);
+  if (lane == 0 && loss) *loss += (smax + logf(zs) - lq) * scale;
 }
 
 __global__ void cnn_to_bf16_kernel(const float* __restrict__ m, int n, __nv_bfloat16* __restrict__ w) {
@@ -240,6 +448,9 @@ struct lpf_cnn {
   float* d_act[lpf::kLayers + 1] = {};
   float* d_gact = nullptr;    // gradient buffers (two, ping-pong)
   float* d_gact2 = nullptr;
+  float* d_part = nullptr;    // per-block weight-gradient partials [blocks][9 * 64 * 64]
+  float* d_part_b = nullptr;  // per-block bias-gradient partials [blocks][64]
+  int n_blk = 0;              // output tiles (blocks) of a convolution
   int64_t step = 0;
   int loss_kind = 0;          // 0: squared error, 1: listwise cross-entropy
   float beta = 1.0f;          // listwise target temperature
@@ -270,6 +481,9 @@ static int cnn_alloc(lpf_cnn* c) {
   for (int l = 0; l <= kLayers && e == cudaSuccess; ++l) e = cudaMalloc(&c->d_act[l], npix * kCh[l] * 4);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_gact, npix * 64 * 4);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_gact2, npix * 64 * 4);
+  c->n_blk = ((c->W + kTW - 1) / kTW) * ((c->H + kTH - 1) / kTH);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_part, (size_t)c->n_blk * 9 * 64 * 64 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_part_b, (size_t)c->n_blk * 64 * 4);
   if (e == cudaSuccess) e = cudaMemset(c->d_m, 0, np * 4);
   if (e == cudaSuccess) e = cudaMemset(c->d_v, 0, np * 4);
   if (e != cudaSuccess) return set_cuda_error(e);
@@ -285,20 +499,77 @@ static void cnn_sync_bf16(lpf_cnn* c, cudaStream_t s) {
     cnn_to_bf16_kernel<<<64, 256, 0, s>>>(c->d_p + c->w_off[l], layer_w_size(l), c->d_wbf + c->wb_off[l]);
 }
 
-template <int COUT>
-static void conv_launch(const float* in, int H, int W, int CIN, const __nv_bfloat16* w, int flip, const float* bias,
-                        int relu, const float* mask, float* out, cudaStream_t s) {
-  const dim3 grid((W + kTile - 1) / kTile, (H + kTile - 1) / kTile);
-  cnn_conv_kernel<COUT><<<grid, kTile * kTile, 0, s>>>(in, H, W, CIN, w, flip, bias, relu, mask, out);
+template <int KC, int NC, bool SPLIT>
+static size_t conv_smem() { return (size_t)((SPLIT ? 2 : 1) * kHalo * (KC + 8) + 9 * NC * (KC + 8)) * 2; }
+template <int KC, int NC>
+static size_t dw_smem() { return (size_t)(kHalo * (KC + 8) + 2 * kTH * kTW * (NC + 8)) * 2; }
+
+// flip = 1 (the input gradient) carries the incoming gradient as two bfloat16 terms.
+template <int KC, int NC>
+static void conv_mma(const float* in, int H, int W, int K, int N, const __nv_bfloat16* w, int flip,
+                     const float* bias, int relu, const float* mask, float* out, cudaStream_t s) {
+  const dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
+  static bool attr[2] = {false, false};  // dynamic shared memory above 48 KB must be allowed once per kernel
+  if (flip) {
+    const size_t smem = conv_smem<KC, NC, true>();
+    if (!attr[1]) {
+      cudaFuncSetAttribute(cnn_conv_mma_kernel<KC, NC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr[1] = true;
+    }
+    cnn_conv_mma_kernel<KC, NC, true><<<grid, kConvThreads, smem, s>>>(in, H, W, K, N, w, flip, bias, relu, mask,
+                                                                        out);
+  } else {
+    const size_t smem = conv_smem<KC, NC, false>();
+    if (!attr[0]) {
+      cudaFuncSetAttribute(cnn_conv_mma_kernel<KC, NC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      attr[0] = true;
+    }
+    cnn_conv_mma_kernel<KC, NC, false><<<grid, kConvThreads, smem, s>>>(in, H, W, K, N, w, flip, bias, relu, mask,
+                                                                         out);
+  }
 }
 
-static void conv_any(int COUT, const float* in, int H, int W, int CIN, const __nv_bfloat16* w, int flip,
+// Convolution with K input and N output channels of the GEMM (see the kernel).
+static void conv_any(int K, int N, const float* in, int H, int W, const __nv_bfloat16* w, int flip,
                      const float* bias, int relu, const float* mask, float* out, cudaStream_t s) {
-  switch (COUT) {
-    case 2: conv_launch<2>(in, H, W, CIN, w, flip, bias, relu, mask, out, s); break;
-    case 32: conv_launch<32>(in, H, W, CIN, w, flip, bias, relu, mask, out, s); break;
-    case 48: conv_launch<48>(in, H, W, CIN, w, flip, bias, relu, mask, out, s); break;
-    default: conv_launch<64>(in, H, W, CIN, w, flip, bias, relu, mask, out, s); break;
+  const int key = K * 1000 + N;
+  switch (key) {
+    // forward layers
+    case 2 * 1000 + 32: conv_mma<16, 32>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
+    case 32 * 1000 + 64: conv_mma<32, 64>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
+    case 64 * 1000 + 48: conv_mma<64, 48>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
+    case 48 * 1000 + 32: conv_mma<48, 32>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
+    case 32 * 1000 + 2: conv_mma<32, 8>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
+    // transposed (input gradients of layers 1..4)
+    case 64 * 1000 + 32: conv_mma<64, 32>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
+    case 48 * 1000 + 64: conv_mma<48, 64>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
+    case 32 * 1000 + 48: conv_mma<32, 48>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
+    default: conv_mma<16, 32>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;  // 2 -> 32
+  }
+}
+
+template <int KC, int NC>
+static void dw_mma(const float* in, const float* g, int H, int W, int CIN, int COUT, float* part, float* part_b,
+                   cudaStream_t s) {
+  const size_t smem = dw_smem<KC, NC>();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(cnn_dw_mma_kernel<KC, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  const dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
+  cnn_dw_mma_kernel<KC, NC><<<grid, kDwThreads, smem, s>>>(in, g, H, W, CIN, COUT, part, part_b);
+}
+
+static void dw_any(int CIN, int COUT, const float* in, const float* g, int H, int W, float* part, float* part_b,
+                   cudaStream_t s) {
+  switch (CIN * 1000 + COUT) {
+    case 2 * 1000 + 32: dw_mma<16, 32>(in, g, H, W, CIN, COUT, part, part_b, s); break;
+    case 32 * 1000 + 64: dw_mma<32, 64>(in, g, H, W, CIN, COUT, part, part_b, s); break;
+    case 64 * 1000 + 48: dw_mma<64, 48>(in, g, H, W, CIN, COUT, part, part_b, s); break;
+    case 48 * 1000 + 32: dw_mma<48, 32>(in, g, H, W, CIN, COUT, part, part_b, s); break;
+    default: dw_mma<32, 8>(in, g, H, W, CIN, COUT, part, part_b, s); break;  // 32 -> 2
   }
 }
 
@@ -306,7 +577,7 @@ void cnn_forward(lpf_cnn* c, const uint8_t* cell, cudaStream_t s) {
   const int npix = c->H * c->W;
   cnn_features_kernel<<<(npix + 255) / 256, 256, 0, s>>>(cell, c->H, c->W, c->d_act[0]);
   for (int l = 0; l < kLayers; ++l)
-    conv_any(kCh[l + 1], c->d_act[l], c->H, c->W, kCh[l], c->d_wbf + c->wb_off[l], 0, c->d_p + c->b_off[l],
+    conv_any(kCh[l], kCh[l + 1], c->d_act[l], c->H, c->W, c->d_wbf + c->wb_off[l], 0, c->d_p + c->b_off[l],
              l < kLayers - 1, nullptr, c->d_act[l + 1], s);
 }
 
@@ -326,12 +597,14 @@ static void cnn_fwd_bwd(lpf_cnn* c, const uint8_t* cell, const int32_t* pairs, c
   for (int l = kLayers - 1; l >= 0; --l) {
     const int cin = kCh[l], cout = kCh[l + 1];
     // g = dL/d(pre-activation output of layer l) here (ReLU mask already applied)
-    cnn_dw_kernel<<<9 * cin, 4 * cout, 4 * cout * sizeof(float), s>>>(c->d_act[l], g, H, W, cin, cout,
-                                                                       c->d_g + c->w_off[l], accumulate);
-    cnn_db_kernel<<<1, 8 * cout, 8 * cout * sizeof(float), s>>>(g, npix, cout, c->d_g + c->b_off[l], accumulate);
+    dw_any(cin, cout, c->d_act[l], g, H, W, c->d_part, c->d_part_b, s);
+    const int nw_l = 9 * cin * cout;
+    cnn_reduce_parts_kernel<<<(nw_l + 255) / 256, 256, 0, s>>>(c->d_part, c->n_blk, nw_l, c->d_g + c->w_off[l],
+                                                                accumulate);
+    cnn_reduce_parts_kernel<<<1, 64, 0, s>>>(c->d_part_b, c->n_blk, cout, c->d_g + c->b_off[l], accumulate);
     if (l > 0) {
       // dL/d act[l] = transposed conv of g, then times the ReLU mask of act[l]
-      conv_any(cin, g, H, W, cout, c->d_wbf + c->wb_off[l], 1, nullptr, 0, c->d_act[l], g2, s);
+      conv_any(cout, cin, g, H, W, c->d_wbf + c->wb_off[l], 1, nullptr, 0, c->d_act[l], g2, s);
       std::swap(g, g2);
     }
   }
@@ -442,6 +715,8 @@ void lpf_cnn_free(lpf_cnn* c) {
   for (int l = 0; l <= lpf::kLayers; ++l) cudaFree(c->d_act[l]);
   cudaFree(c->d_gact);
   cudaFree(c->d_gact2);
+  cudaFree(c->d_part);
+  cudaFree(c->d_part_b);
   delete c;
 }
 

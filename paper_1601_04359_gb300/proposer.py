@@ -37,13 +37,14 @@ if ROOT not in sys.path:
 import paper_1601_04359_gb300 as lpf  # noqa: E402
 
 
-def annealing_problem(r: int = 64, cell_size: int = 128, seed: int = 5):
+def annealing_problem(r: int = 64, cell_size: int = 128, seed: int = 5, orig_size: int = 512):
     """The compression workload: target = lineal path function (|v| <= r) of a
-    512x512 clustered-disk original; random initial cell with its fraction."""
+    clustered-disk original (the 512x512 one of the annealing workload, or
+    an orig_size^2 one with fraction 0.3); random initial cell with its fraction."""
     import torch
 
     import synth
-    orig = synth.clustered_512()
+    orig = synth.clustered_512() if orig_size == 512 else synth.clustered_disks(orig_size, orig_size, 0.3, seed=9)
     paths = lpf.lpf_build_paths(r, r)
     c = lpf.lpf_full(torch.from_numpy(orig).cuda(), paths)
     target = (c.double() / float(orig.size)).float()
@@ -131,14 +132,16 @@ def run_until(paths, target, cell0, n_step: int, seed: int, t_max: float, net=No
 
 def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22, 23, 24, 25), snapshots: int = 256,
              n: int = 64, epochs: int = 8, taus=(0.35,), epss=(0.4,), on_policy: bool = False,
-             spacing: str = "early", refreshes=(16,), loss: str = "squared", beta: float = 1.0):
+             spacing: str = "early", refreshes=(16,), loss: str = "squared", beta: float = 1.0,
+             r: int = 64, cell_size: int = 128, orig_size: int = 512, net_seed: int = 3):
     """Swaps-to-target gain of the learned proposer (median over eval seeds)."""
     import torch
 
     import synth
-    paths, target, cell0 = annealing_problem()
+    C = cell_size
+    paths, target, cell0 = annealing_problem(r=r, cell_size=C, orig_size=orig_size)
     n1 = int(cell0.sum())
-    cells0 = {s: synth.exact_fraction_shuffle(128, 128, n1, seed=1000 + s) for s in eval_seeds}
+    cells0 = {s: synth.exact_fraction_shuffle(C, C, n1, seed=1000 + s) for s in eval_seeds}
     # uniform reference runs
     ref = {}
     t_max = None
@@ -146,10 +149,10 @@ def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22,
         _, st_u, dt_u = run_until(paths, target, cells0[s], n_step, s, t_max=t_max or 0.0)
         t_max = t_max or st_u["t_max"]
         ref[s] = (st_u["error"], dt_u, st_u["n_eval"] / dt_u)
-    net = lpf.lpf_cnn_create(128, 128, seed=3)
+    net = lpf.lpf_cnn_create(C, C, seed=net_seed)
     lpf.lpf_cnn_set_loss(net, loss, beta)
     t0 = time.perf_counter()
-    data = [collect(paths, target, synth.exact_fraction_shuffle(128, 128, n1, seed=s), n_step, s, snapshots, n,
+    data = [collect(paths, target, synth.exact_fraction_shuffle(C, C, n1, seed=s), n_step, s, snapshots, n,
                     t_max=t_max, spacing=spacing) for s in train_seeds]
     cells = torch.cat([d[0] for d in data])
     pairs = torch.cat([d[1] for d in data])
@@ -158,7 +161,7 @@ def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22,
     rounds = 1
     if on_policy:
         # second round: candidates drawn by the annealer while it uses the network
-        data2 = [collect(paths, target, synth.exact_fraction_shuffle(128, 128, n1, seed=s + 100), n_step, s + 100,
+        data2 = [collect(paths, target, synth.exact_fraction_shuffle(C, C, n1, seed=s + 100), n_step, s + 100,
                          snapshots, n, t_max=t_max, net=net, eps=epss[0], tau=taus[0], spacing=spacing)
                  for s in train_seeds]
         cells = torch.cat([cells] + [d[0] for d in data2])
@@ -184,7 +187,7 @@ def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22,
                              "per_seed": per_seed})
     best = max(runs, key=lambda r: r["median_ratio"])
     return {
-        "workload": "128x128 cell, |v|<=64, target from 512x512 clustered disks (f=0.3)",
+        "workload": f"{C}x{C} cell, |v|<=%d, target from {orig_size}x{orig_size} clustered disks (f=0.3)" % r,
         "n_step_uniform": n_step, "uniform": {str(s): {"error": v[0], "seconds": v[1], "evals_per_s": v[2]}
                                               for s, v in ref.items()},
         "train_seeds": list(train_seeds), "eval_seeds": list(eval_seeds), "rounds": rounds, "spacing": spacing,
@@ -212,13 +215,16 @@ def main():
     ap.add_argument("--refresh", type=int, nargs="+", default=[16])
     ap.add_argument("--loss", choices=["squared", "listwise"], default="squared")
     ap.add_argument("--beta", type=float, default=1.0, help="listwise target temperature")
+    ap.add_argument("--r", type=int, default=64, help="window radius")
+    ap.add_argument("--cell", type=int, default=128, help="cell size")
+    ap.add_argument("--orig", type=int, default=512, help="original size (512: the annealing workload's image)")
     a = ap.parse_args()
     lpf.load()
     if a.evaluate:
         print(json.dumps(evaluate(n_step=a.n_step, train_seeds=tuple(a.train_seeds), eval_seeds=tuple(a.eval_seeds),
                                   snapshots=a.snapshots, epochs=a.epochs, taus=tuple(a.tau), epss=tuple(a.eps),
                                   on_policy=a.on_policy, spacing=a.spacing, refreshes=tuple(a.refresh),
-                                  loss=a.loss, beta=a.beta)),
+                                  loss=a.loss, beta=a.beta, r=a.r, cell_size=a.cell, orig_size=a.orig)),
               flush=True)
 
 

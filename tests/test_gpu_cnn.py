@@ -1,10 +1,26 @@
 """GPU proposer network against its float64 CPU reference.
 
-The GPU uses bfloat16 copies of the weights; the reference is given the same
-bfloat16-rounded values (in float64), so the remaining difference is float32
-accumulation: a forward layer sums 9*Cin <= 576 products, so relative errors
-stay at a few 1e-6 of the summed magnitudes; the tolerance below is 1e-4 of
-the largest magnitude of each compared array.
+The GPU convolutions run on tensor cores with bfloat16 operands and float32
+accumulation: weights are stored as bfloat16, activations are rounded to
+bfloat16 where they enter a product, gradients enter as two bfloat16 terms
+(high and low part).  Two comparisons:
+
+- against the reference given the same roundings (weights rounded, and the
+  oracle's operand-rounding hook set to the same round-to-nearest-even for
+  layer inputs): what remains is float32 accumulation order, the low-term
+  residue of the gradients (2^-16 relative), and the rare activation whose
+  float32 and float64 values round to neighbouring bfloat16 values (one
+  bfloat16 ulp, 2^-8 relative, of one operand); tolerance 3e-3 of the
+  largest magnitude (forward);
+- the forward pass also against the plain float64 reference (only the
+  weights rounded): the bfloat16 rounding of activations, BF16-scale
+  tolerance 1e-2 of the largest magnitude.
+
+Gradients are compared with the rounded reference only, at the BF16-scale
+1e-2 of each layer's largest gradient: they are the gradients of the network
+the library evaluates (bfloat16 activations).  Against the unrounded network
+the first layer's gradients differ by a few percent, because the loss's
+residuals s1[a] + s0[b] - y cancel and amplify the forward rounding.
 """
 import numpy as np
 import pytest
@@ -39,6 +55,18 @@ def _setup(gpu_lib, H, W, seed):
     return net, _params_for_reference(params)
 
 
+def _per_layer_close(grads, ref, got, tol):
+    """Each layer's gradients within tol of that layer's largest reference gradient."""
+    off = 0
+    for li, (dw, db) in enumerate(grads):
+        n = dw.size + db.size
+        seg_ref, seg_got = ref[off:off + n], got[off:off + n]
+        err = np.abs(seg_got - seg_ref).max() / (np.abs(seg_ref).max() + 1e-30)
+        print(f"layer {li}: rel grad err {err:.2e} (tol {tol:.0e})")
+        assert err <= tol
+        off += n
+
+
 def test_param_roundtrip(gpu_lib):
     net = gpu_lib.lpf_cnn_create(16, 16, 3)
     assert net.n_params == ocnn.n_params() == 61234
@@ -52,8 +80,13 @@ def test_forward_matches_reference(gpu_lib, H, W):
     net, ref_params = _setup(gpu_lib, H, W, 1)
     cell = synth.clustered_disks(H, W, 0.35, seed=2)
     got = gpu_lib.lpf_cnn_forward(net, torch.from_numpy(cell).cuda()).cpu().numpy().astype(np.float64)
-    ref, _ = ocnn.forward(ref_params, ocnn.features(cell))
-    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+    ref, _ = ocnn.forward(ref_params, ocnn.features(cell), rnd=_bf16_round)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    plain, _ = ocnn.forward(ref_params, ocnn.features(cell))
+    err_plain = np.abs(got - plain).max() / np.abs(plain).max()
+    print(f"forward {H}x{W}: rel err {err:.2e} (rounded reference), {err_plain:.2e} (float64)")
+    assert err <= 3e-3
+    assert err_plain <= 1e-2
 
 
 @pytest.mark.parametrize("H,W", [(16, 16), (40, 28)])
@@ -69,18 +102,13 @@ def test_gradients_match_reference(gpu_lib, H, W):
     g, loss = gpu_lib.lpf_cnn_gradients(net, torch.from_numpy(cell).cuda(), torch.from_numpy(pairs).cuda(),
                                         torch.from_numpy(y).cuda())
     x = ocnn.features(cell)
-    out, acts = ocnn.forward(ref_params, x)
-    grads = ocnn.backward(ref_params, acts, ocnn.loss_grad_out(out, a, b, y.astype(np.float64)))
-    ref = np.concatenate([np.concatenate([dw.reshape(-1), db]) for dw, db in grads])
     got = g.cpu().numpy().astype(np.float64)
-    assert abs(loss.item() - ocnn.loss(out, a, b, y.astype(np.float64))) <= 1e-4 * max(1.0, loss.item())
-    # per layer: relative to that layer's largest gradient
-    off = 0
-    for (dw, db) in grads:
-        n = dw.size + db.size
-        seg_ref, seg_got = ref[off:off + n], got[off:off + n]
-        assert np.abs(seg_got - seg_ref).max() <= 2e-3 * np.abs(seg_ref).max() + 1e-7
-        off += n
+    for rnd, tol in ((_bf16_round, 1e-2),):
+        out, acts = ocnn.forward(ref_params, x, rnd=rnd)
+        grads = ocnn.backward(ref_params, acts, ocnn.loss_grad_out(out, a, b, y.astype(np.float64)), rnd=rnd)
+        ref = np.concatenate([np.concatenate([dw.reshape(-1), db]) for dw, db in grads])
+        assert abs(loss.item() - ocnn.loss(out, a, b, y.astype(np.float64))) <= tol * max(1.0, loss.item())
+        _per_layer_close(grads, ref, got, tol)
 
 
 def test_training_reduces_loss(gpu_lib):
@@ -116,15 +144,11 @@ def test_listwise_gradients_match_reference(gpu_lib, beta):
     pairs = np.stack([a, b], axis=1)
     g, loss = gpu_lib.lpf_cnn_gradients(net, torch.from_numpy(cell).cuda(), torch.from_numpy(pairs).cuda(),
                                         torch.from_numpy(y).cuda())
-    out, acts = ocnn.forward(ref_params, ocnn.features(cell))
     yd = y.astype(np.float64)
-    grads = ocnn.backward(ref_params, acts, ocnn.listwise_grad_out(out, a, b, yd, beta))
-    assert abs(loss.item() - ocnn.listwise_loss(out, a, b, yd, beta)) <= 1e-4 * max(1.0, abs(loss.item()))
-    ref = np.concatenate([np.concatenate([dw.reshape(-1), db]) for dw, db in grads])
     got = g.cpu().numpy().astype(np.float64)
-    off = 0
-    for (dw, db) in grads:
-        n = dw.size + db.size
-        seg_ref, seg_got = ref[off:off + n], got[off:off + n]
-        assert np.abs(seg_got - seg_ref).max() <= 2e-3 * np.abs(seg_ref).max() + 1e-7
-        off += n
+    for rnd, tol in ((_bf16_round, 1e-2),):
+        out, acts = ocnn.forward(ref_params, ocnn.features(cell), rnd=rnd)
+        grads = ocnn.backward(ref_params, acts, ocnn.listwise_grad_out(out, a, b, yd, beta), rnd=rnd)
+        assert abs(loss.item() - ocnn.listwise_loss(out, a, b, yd, beta)) <= tol * max(1.0, abs(loss.item()))
+        ref = np.concatenate([np.concatenate([dw.reshape(-1), db]) for dw, db in grads])
+        _per_layer_close(grads, ref, got, tol)

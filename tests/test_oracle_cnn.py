@@ -77,3 +77,27 @@ def test_listwise_gradient_by_central_differences():
     z = np.zeros_like(out)
     assert np.abs(cnn.listwise_grad_out(z, a_idx, b_idx, np.zeros(4), 1.0)).max() < 1e-15
     assert cnn.listwise_loss(z, a_idx, b_idx, np.zeros(4), 1.0) == pytest.approx(np.log(4))
+
+
+def test_operand_rounding_hook():
+    # The optional rounding hook is applied to the layer inputs only: the
+    # identity gives the plain float64 network, and a rounding of the inputs
+    # changes the output no more than the rounding's size allows.
+    import numpy as np
+
+    from oracle import cnn as ocnn
+    params = ocnn.init_params(2)
+    rng = np.random.default_rng(3)
+    cell = (rng.random((12, 10)) < 0.4).astype(np.uint8)
+    x = ocnn.features(cell)
+    plain, _ = ocnn.forward(params, x)
+    same, _ = ocnn.forward(params, x, rnd=lambda a: a)
+    np.testing.assert_array_equal(plain, same)
+    coarse, acts = ocnn.forward(params, x, rnd=lambda a: np.round(a * 256.0) / 256.0)
+    assert 0 < np.abs(coarse - plain).max() < 0.05 * np.abs(plain).max()
+    g = ocnn.loss_grad_out(coarse, np.array([3]), np.array([7]), np.array([0.5]))
+    a = ocnn.backward(params, acts, g, rnd=lambda v: v)
+    b = ocnn.backward(params, acts, g)
+    for (wa, ba), (wb, bb) in zip(a, b):
+        np.testing.assert_array_equal(wa, wb)
+        np.testing.assert_array_equal(ba, bb)
