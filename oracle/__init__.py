@@ -19,6 +19,8 @@ Functions and the passages they follow:
   s2_direct(img, phase)            Eq. (S2dis), direct double sum
   lpf_full_selected(img, rx, ry, sel)   Sec. 3 Monte-Carlo variant (selected translations)
   s2_counts(img), s2_delta_objective(img, target, pairs)   Eq. (S2dis) counts; Eq. (LSE) on S2, by recount
+  segment3(dx, dy, dz), lpf_full3(vol, rx, ry, rz), count3(vol, dx, dy, dz, phase)
+                             3D extension (Sec. 2 remark, Sec. 6.3): the 2D tie rule per minor axis
 Parity status: every function above is pinned by ``tests/test_oracle_*.py``.
 """
 from __future__ import annotations
@@ -54,6 +56,11 @@ def _load():
         lib.lpfo_lpf_full_sel.argtypes = [p, i32, i32, i32, i32, p, p]
         lib.lpfo_s2_counts.argtypes = [p, i32, i32, p]
         lib.lpfo_s2_delta_objective.argtypes = [p, i32, i32, p, p, i32, p]
+        lib.lpfo_segment3.argtypes = [i32, i32, i32, p, p, p]
+        lib.lpfo_segment3.restype = i32
+        lib.lpfo_count3.argtypes = [p, i32, i32, i32, i32, i32, i32, i32]
+        lib.lpfo_count3.restype = i64
+        lib.lpfo_lpf_full3.argtypes = [p, i32, i32, i32, i32, i32, i32, p]
         _lib = lib
     return _lib
 
@@ -195,4 +202,48 @@ def s2_direct(img, phase: int) -> np.ndarray:
     H, W = a.shape
     out = np.zeros((H, W), np.float64)
     _load().lpfo_s2_direct(_ptr(a), H, W, int(phase), _ptr(out))
+    return out
+
+
+def window_sizes3(rx: int, ry: int, rz: int):
+    """(n_full, n_canon, base) of the 3D window |dx|<=rx, |dy|<=ry, |dz|<=rz."""
+    n_full = (2 * rx + 1) * (2 * ry + 1) * (2 * rz + 1)
+    base = (n_full - 1) // 2
+    return n_full, n_full - base, base
+
+
+def full_index3(dx: int, dy: int, dz: int, rx: int, ry: int, rz: int) -> int:
+    return ((dz + rz) * (2 * ry + 1) + (dy + ry)) * (2 * rx + 1) + (dx + rx)
+
+
+def segment3(dx: int, dy: int, dz: int) -> np.ndarray:
+    """Voxel offsets [(sx, sy, sz), ...] of the 3D segment (0,0,0) -> (dx, dy, dz)."""
+    n = max(abs(dx), abs(dy), abs(dz)) + 1
+    out = np.zeros((3, n), np.int32)
+    m = _load().lpfo_segment3(int(dx), int(dy), int(dz), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]))
+    assert m == n
+    return np.ascontiguousarray(out.T)
+
+
+def _vol(vol) -> np.ndarray:
+    a = np.ascontiguousarray(vol, dtype=np.uint8)
+    assert a.ndim == 3
+    return a
+
+
+def count3(vol, dx: int, dy: int, dz: int, phase: int) -> int:
+    a = _vol(vol)
+    D, H, W = a.shape
+    return int(_load().lpfo_count3(_ptr(a), D, H, W, int(dx), int(dy), int(dz), int(phase)))
+
+
+def lpf_full3(vol, rx: int, ry: int, rz: int) -> np.ndarray:
+    """int64 [2][(2rz+1)(2ry+1)(2rx+1)] counts of a periodic volume vol[z][y][x]."""
+    a = _vol(vol)
+    D, H, W = a.shape
+    if not (0 <= rx < W and 0 <= ry < H and 0 <= rz < D):
+        raise ValueError("window must satisfy 0 <= rx < W, 0 <= ry < H, 0 <= rz < D")
+    n_full, _, _ = window_sizes3(rx, ry, rz)
+    out = np.zeros((2, n_full), np.int64)
+    _load().lpfo_lpf_full3(_ptr(a), D, H, W, rx, ry, rz, _ptr(out))
     return out

@@ -354,3 +354,78 @@ void lpfo_s2_direct(const uint8_t *img, int H, int W, int phase, double *s2) {
             s2[(int64_t)y * W + x] = (double)acc * inv;
         }
 }
+
+/* ---- Three-dimensional extension (Sec. 2, remark on 3D media; Sec. 6.3) ----
+ *
+ * The paper states that the lineal path function extends to 3D media but
+ * defines no 3D segment.  Reading: the same Bresenham rule per minor axis.
+ * For v = (dx, dy, dz) with a = max(|dx|, |dy|, |dz|), step i = 0..a moves
+ * sgn(d_j) * round(i |d_j| / a) along every axis j (the major axis exactly
+ * i), an exact half rounding away from the start; |S(v)| = a + 1.  The
+ * half-domain D3 is dz > 0, or dz = 0 and (dy, dx) in the 2D half-domain;
+ * outside D3, S(v) = v + S(-v) as in 2D.  Volumes are vol[z][y][x], periodic
+ * in all three coordinates.
+ */
+static int lpfo_is_canonical3(int dx, int dy, int dz) {
+    return dz > 0 || (dz == 0 && lpfo_is_canonical(dx, dy));
+}
+
+int lpfo_segment3(int dx, int dy, int dz, int32_t *sx, int32_t *sy, int32_t *sz) {
+    if (!lpfo_is_canonical3(dx, dy, dz)) {
+        int n = lpfo_segment3(-dx, -dy, -dz, sx, sy, sz);
+        for (int i = 0; i < n; ++i) { sx[i] += dx; sy[i] += dy; sz[i] += dz; }
+        return n;
+    }
+    int ad[3] = {iabs(dx), iabs(dy), iabs(dz)};
+    int g[3] = {dx < 0 ? -1 : 1, dy < 0 ? -1 : 1, dz < 0 ? -1 : 1};
+    int a = ad[0];
+    if (ad[1] > a) a = ad[1];
+    if (ad[2] > a) a = ad[2];
+    for (int i = 0; i <= a; ++i) {
+        int c[3];
+        for (int j = 0; j < 3; ++j) c[j] = (a == 0) ? 0 : g[j] * ((2 * i * ad[j] + a) / (2 * a));
+        sx[i] = c[0]; sy[i] = c[1]; sz[i] = c[2];
+    }
+    return a + 1;
+}
+
+/* Alg. 1 in 3D for one segment: every translation of the periodic volume,
+ * early break at the first voxel outside the phase. */
+int64_t lpfo_count3(const uint8_t *vol, int D, int H, int W, int dx, int dy, int dz, int phase) {
+    int ax = iabs(dx), ay = iabs(dy), az = iabs(dz);
+    int n = (ax > ay ? ax : ay);
+    n = (n > az ? n : az) + 1;
+    int32_t *sx = (int32_t *)malloc(sizeof(int32_t) * 3 * n);
+    int32_t *sy = sx + n, *sz = sx + 2 * n;
+    lpfo_segment3(dx, dy, dz, sx, sy, sz);
+    int64_t L = 0;
+    for (int z = 0; z < D; ++z)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                int k;
+                for (k = 0; k < n; ++k) {
+                    int vz = ((z + sz[k]) % D + D) % D;
+                    int vy = ((y + sy[k]) % H + H) % H;
+                    int vx = ((x + sx[k]) % W + W) % W;
+                    if (vol[((int64_t)vz * H + vy) * W + vx] != phase) break;
+                }
+                if (k == n) ++L;
+            }
+    free(sx);
+    return L;
+}
+
+/* Counts of both phases for every vector of |dx| <= rx, |dy| <= ry,
+ * |dz| <= rz in the full layout counts[p][((dz+rz)(2ry+1) + dy+ry)(2rx+1) + dx+rx];
+ * every vector evaluated directly. */
+void lpfo_lpf_full3(const uint8_t *vol, int D, int H, int W, int rx, int ry, int rz, int64_t *counts) {
+    int nx = 2 * rx + 1, ny = 2 * ry + 1, nz = 2 * rz + 1;
+    int64_t nfull = (int64_t)nx * ny * nz;
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nfull; ++k) {
+        int dz = (int)(k / ((int64_t)nx * ny)) - rz;
+        int rem = (int)(k % ((int64_t)nx * ny));
+        int dy = rem / nx - ry, dx = rem % nx - rx;
+        for (int p = 0; p < 2; ++p) counts[p * nfull + k] = lpfo_count3(vol, D, H, W, dx, dy, dz, p);
+    }
+}
