@@ -96,8 +96,9 @@ int lpf_paths_info(const lpf_paths *paths, int64_t *n_vec_full, int64_t *n_vec_c
  * vec_dxdy_host [n_vec_canon][2] (dx, dy) in canonical order,
  * ptr_host [n_vec_canon + 1] (segment c is offsets ptr[c] .. ptr[c+1]-1),
  * off_dxdy_host [n_offsets][2] (sx, sy) pixel offsets from the start pixel,
- * start pixel first.  Any output pointer may be NULL.
- * Errors: LPF_EINVAL (paths == NULL).
+ * start pixel first.  For a volume's handle (lpf_build_paths_3d) the vector
+ * and offset arrays hold triples (dx, dy, dz) and (sx, sy, sz) instead.  Any
+ * output pointer may be NULL.  Errors: LPF_EINVAL (paths == NULL).
  */
 int lpf_paths_export(const lpf_paths *paths, int16_t *vec_dxdy_host, int64_t *ptr_host,
                      int16_t *off_dxdy_host);
@@ -337,6 +338,42 @@ int lpf_delta_swap_mc(const uint8_t *img_dev, int32_t H, int32_t W, lpf_paths *p
  */
 int s2_fft(const uint8_t *img_dev, int32_t H, int32_t W, int32_t phase, float *s2_dev,
            lpf_stream_t stream);
+
+/* ---- Volumes (3D extension; Sec. 2 remark on 3D media, Sec. 6.3) ---- */
+
+/*
+ * Segments of every vector |dx| <= rx, |dy| <= ry, |dz| <= rz of a volume
+ * and the prefix-tree program over them.  The paper mentions the 3D
+ * extension without defining 3D segments; this library takes the 2D rule
+ * on every minor axis: for v = (dx, dy, dz), a = max(|dx|, |dy|, |dz|), step
+ * i = 0..a moves round(i |d_j| / a) along every axis j (exact halves away
+ * from the start), |S(v)| = a + 1; the half-domain is dz > 0, or dz = 0 and
+ * (dx, dy) in the 2D half-domain, and S(v) = v + S(-v) outside it.
+ * Host-only.  rx, ry, rz in [0, 1023].  The handle serves lpf_full_3d,
+ * lpf_paths_info / _export / _stats / _work / _status, lpf_set_checked and
+ * lpf_paths_free; image calls (lpf_full, lpf_delta_swap, batches,
+ * annealers) refuse it with LPF_EINVAL.
+ * Errors: LPF_EINVAL, LPF_ENOMEM, LPF_EUNSUPPORTED.
+ */
+int lpf_build_paths_3d(int32_t rx, int32_t ry, int32_t rz, lpf_paths **out);
+
+/*
+ * Full lineal path counts of both phases of a periodic volume: vol_dev
+ * uint8 [D][H][W] (0/1), voxel (x, y, z) = vol[z][y][x], coordinates
+ * wrapping modulo W, H, D; count_p(v) = #{x : vol[(x + s) mod (W,H,D)] == p
+ * for all s in S(v)}.  counts_dev int64 [2][(2rz+1)(2ry+1)(2rx+1)], entry
+ * ((dz+rz)(2ry+1) + dy+ry)(2rx+1) + dx+rx, phase 0 first; the other half of
+ * the window filled by point symmetry.  The same bit-parallel prefix-tree
+ * walk as lpf_full: slices packed as bit rows extended periodically by ry
+ * rows and, as slices, by rz; a block stages the rows of its 32-row bands
+ * plus the halo rows of the next rz slices.  Requires rx < W, ry < H,
+ * rz < D, sizes up to 4096, at most 8192 bands of 32 rows over all slices,
+ * and (rz (H + 2ry) + 32 + 2ry) rows of about (W + 2rx)/32 + 2 words in
+ * shared memory (about 227 KB), else LPF_EUNSUPPORTED.  First call per size allocates as lpf_full does.
+ * Errors: LPF_EINVAL, LPF_EUNSUPPORTED, LPF_ENOMEM, LPF_ECUDA.
+ */
+int lpf_full_3d(const uint8_t *vol_dev, int32_t D, int32_t H, int32_t W, lpf_paths *paths,
+                int64_t *counts_dev, lpf_stream_t stream);
 
 /* ---- Many independent images in one persistent launch ---- */
 

@@ -27,6 +27,7 @@ __all__ = [
     "lpf_cnn_set_params", "lpf_cnn_get_params", "lpf_cnn_forward", "lpf_cnn_gradients", "lpf_cnn_train_step",
     "lpf_sa_set_proposer", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune",
     "lpf_batch_status", "lpf_set_checked", "lpf_paths_set_selftest", "LPF_EPIXEL", "LPF_ETIMEOUT",
+    "lpf_build_paths_3d", "lpf_full_3d",
 ]
 
 LPF_ETIMEOUT = -4
@@ -115,6 +116,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_sa_create_mc": (ctypes.c_int, [p, i32, i32, p, p, p, p, ctypes.POINTER(SaParams), p, ctypes.POINTER(p)]),
         "lpf_sa_selftest_timeout": (ctypes.c_int, [p, i32, p]),
         "lpf_set_checked": (ctypes.c_int, [p, i32]),
+        "lpf_build_paths_3d": (ctypes.c_int, [i32, i32, i32, ctypes.POINTER(p)]),
+        "lpf_full_3d": (ctypes.c_int, [p, i32, i32, i32, p, p, p]),
         "lpf_paths_set_selftest": (ctypes.c_int, [p, i32]),
         "s2_delta_swap": (ctypes.c_int, [p, i32, i32, p, i32, p, p, p, p, p]),
         "s2_sa_create": (ctypes.c_int, [p, i32, i32, p, p, ctypes.POINTER(SaParams), p, ctypes.POINTER(p)]),
@@ -179,9 +182,11 @@ def _dev_ptr(t, dtype_name: str, what: str) -> int:
 class Paths:
     """Owning wrapper of an ``lpf_paths*`` handle (freed on garbage collection)."""
 
-    def __init__(self, handle: int, rx: int, ry: int):
+    def __init__(self, handle: int, rx: int, ry: int, rz: int | None = None):
         self.handle = handle
         self.rx, self.ry = rx, ry
+        self.rz = rz
+        self.dims = 2 if rz is None else 3
         self.n_full, self.n_canon, self.n_offsets = lpf_paths_info(self)
         self.base = (self.n_full - 1) // 2
 
@@ -205,10 +210,10 @@ def lpf_paths_info(paths: Paths):
 
 
 def lpf_paths_export(paths: Paths):
-    """(vec [n_canon][2] int16, ptr [n_canon+1] int64, off [n_offsets][2] int16)."""
-    vec = np.zeros((paths.n_canon, 2), np.int16)
+    """(vec [n_canon][dims] int16, ptr [n_canon+1] int64, off [n_offsets][dims] int16); dims = 2 or 3."""
+    vec = np.zeros((paths.n_canon, paths.dims), np.int16)
     ptr = np.zeros(paths.n_canon + 1, np.int64)
-    off = np.zeros((paths.n_offsets, 2), np.int16)
+    off = np.zeros((paths.n_offsets, paths.dims), np.int16)
     _check(load().lpf_paths_export(paths.handle, vec.ctypes.data, ptr.ctypes.data, off.ctypes.data),
            "lpf_paths_export")
     return vec, ptr, off
@@ -237,6 +242,24 @@ def lpf_full(img, paths: Paths, counts=None, stream=None):
         counts = torch.empty((2, paths.n_full), dtype=torch.int64, device=img.device)
     _check(load().lpf_full(_dev_ptr(img, "uint8", "img"), H, W, paths.handle,
                            _dev_ptr(counts, "int64", "counts"), _stream_ptr(stream)), "lpf_full")
+    return counts
+
+
+def lpf_build_paths_3d(rx: int, ry: int, rz: int) -> Paths:
+    """Segments of every vector |dx|<=rx, |dy|<=ry, |dz|<=rz of a volume (3D extension)."""
+    h = ctypes.c_void_p()
+    _check(load().lpf_build_paths_3d(int(rx), int(ry), int(rz), ctypes.byref(h)), "lpf_build_paths_3d")
+    return Paths(h.value, int(rx), int(ry), int(rz))
+
+
+def lpf_full_3d(vol, paths: Paths, counts=None, stream=None):
+    """Counts of both phases of a periodic volume (uint8 CUDA tensor [D][H][W]) for every vector."""
+    import torch
+    D, H, W = vol.shape
+    if counts is None:
+        counts = torch.empty((2, paths.n_full), dtype=torch.int64, device=vol.device)
+    _check(load().lpf_full_3d(_dev_ptr(vol, "uint8", "vol"), D, H, W, paths.handle,
+                              _dev_ptr(counts, "int64", "counts"), _stream_ptr(stream)), "lpf_full_3d")
     return counts
 
 

@@ -345,6 +345,8 @@ int lpf_batch_create(int32_t n_img, const uint8_t* const* imgs_dev, const int32_
   *out = nullptr;
   if (n_img < 1 || !imgs_dev || !H || !W || !paths || !counts_dev) return LPF_EINVAL;
   for (int i = 0; i < n_img; ++i)
+    if (!paths[i] || paths[i]->host.dims != 2) return LPF_EINVAL;  // images only
+  for (int i = 0; i < n_img; ++i)
     for (int j = 0; j < i; ++j)
       if (paths[i] == paths[j] && (H[i] != H[j] || W[i] != W[j])) return LPF_EINVAL;  // one program per handle
   lpf_batch* bt = new (std::nothrow) lpf_batch();

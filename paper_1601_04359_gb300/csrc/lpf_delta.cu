@@ -195,6 +195,7 @@ int delta_max_smem() { return g_delta_max_smem; }
 int delta_num_sms() { return g_sms; }
 
 int delta_prepare(lpf_paths* p, int H, int W, int K) {
+  if (p->host.dims != 2) return LPF_EINVAL;  // swap deltas of images only
   if (g_delta_max_smem < 0) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);

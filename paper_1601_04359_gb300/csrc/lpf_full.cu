@@ -44,7 +44,7 @@ constexpr int kCtlExecuted = 2;
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusPixel = 8;
 constexpr int kCtlUnits = 4;
-constexpr int kMaxBandGroups = (8192 + 31) / 32;
+constexpr int kMaxBandGroups = 8192;  // images: ceil(H / 32) <= 256; volumes: D * ceil(H / (32 BB))
 constexpr int kCtlWords = kCtlUnits + kMaxBandGroups;
 
 int make_geometry(int H, int W, int rx, int ry, int T, int BB, Geometry& g) {
@@ -68,7 +68,35 @@ int make_geometry(int H, int W, int rx, int ry, int T, int BB, Geometry& g) {
   const size_t band = (size_t)(32 * BB + ry) * g.S * 4;
   g.band_bytes = (uint32_t)((band + 15) & ~size_t(15));
   g.packed_words = (size_t)g.rows * g.S + 4;
+  g.D = 1;
+  g.rz = 0;
+  g.slice_rows = 0;
+  g.nbg_s = g.nbg;
   if (g.G > 16 || band > (size_t)kMaxSmem - 64) return LPF_EUNSUPPORTED;
+  return LPF_OK;
+}
+
+// Volume layout: packed row (z' * slice_rows + y'') holds image row
+// (y'' - ry) mod H of slice z' mod D, z' < D + rz; a block of band group
+// (z, b) stages rows z * slice_rows + 32 BB b onwards: its 32 BB
+// translation rows, ry above and below them, and the rz following slices.
+int make_geometry3(int D, int H, int W, int rx, int ry, int rz, int T, int BB, Geometry& g) {
+  int rc = make_geometry(H, W, rx, ry, T, BB, g);
+  if (rc && rc != LPF_EUNSUPPORTED) return rc;
+  g.D = D;
+  g.rz = rz;
+  g.nbg_s = g.nbg;
+  // A band group's bulk copy starts at row z * slice_rows + 32 BB b, which
+  // must be a 16-byte boundary (cp.async.bulk): S is odd, so slice_rows is a
+  // multiple of 4 (the extra rows hold the periodic continuation).
+  g.slice_rows = (32 * g.BB * g.nbg_s + 2 * ry + 3) & ~3;
+  g.nbg = D * g.nbg_s;
+  g.rows = (D + rz) * g.slice_rows;
+  const size_t band = (size_t)(rz * g.slice_rows + 32 * g.BB + 2 * ry) * g.S * 4;
+  g.band_bytes = (uint32_t)((band + 15) & ~size_t(15));
+  g.packed_words = (size_t)g.rows * g.S + 4;
+  if (g.G > 16 || band > (size_t)kMaxSmem - 64 || g.nbg > kMaxBandGroups) return LPF_EUNSUPPORTED;
+  if (((size_t)g.slice_rows * g.S) % 4 != 0 || ((size_t)32 * g.BB * g.S) % 4 != 0) return LPF_EUNSUPPORTED;
   return LPF_OK;
 }
 
@@ -97,6 +125,40 @@ __global__ void pack_rows_kernel(const uint8_t* __restrict__ img, int H, int W, 
     if (x < 0) x += W;
     uint32_t bits = 0;
 #pragma unroll 4
+    for (int b = 0; b < 32; ++b) {
+      const uint32_t v = row[x];
+      bits |= (uint32_t)(v != 0) << b;
+      high |= v >> 1;
+      if (++x == W) x = 0;
+    }
+    packed[i] = bits;
+  }
+  if (pix_flag && high) atomicOr(pix_flag, kStatusPixel);
+}
+
+// Volume rows: packed[(z' * slice_rows + y'') * S + k] bit b = voxel at
+// slice z' mod D, row (y'' - ry) mod H, column (32k + b - r32) mod W; also
+// zeroes the counts and control words as pack_rows_kernel does.
+__global__ void pack_vol_kernel(const uint8_t* __restrict__ vol, int D, int H, int W, int ry, int r32, int S,
+                                int slice_rows, int rows, uint32_t* __restrict__ packed,
+                                unsigned long long* __restrict__ zero64, int64_t n_zero64, int* __restrict__ zero32,
+                                int n_zero32, int* __restrict__ pix_flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t i = i0; i < n_zero64; i += stride) zero64[i] = 0ull;
+  for (int64_t i = i0; i < n_zero32; i += stride) zero32[i] = 0;
+  const int64_t total = (int64_t)rows * S;
+  uint32_t high = 0;
+  for (int64_t i = i0; i < total; i += stride) {
+    const int64_t r = i / S;
+    const int k = (int)(i % S);
+    const int zp = (int)(r / slice_rows), yp = (int)(r % slice_rows);
+    int y = (yp - ry) % H;
+    if (y < 0) y += H;
+    const uint8_t* row = vol + ((int64_t)(zp % D) * H + y) * W;
+    int x = (32 * k - r32) % W;
+    if (x < 0) x += W;
+    uint32_t bits = 0;
     for (int b = 0; b < 32; ++b) {
       const uint32_t v = row[x];
       bits |= (uint32_t)(v != 0) << b;
@@ -148,7 +210,7 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
                                                   unsigned long long* __restrict__ counts, int64_t n_full,
                                                   int64_t base, int* __restrict__ ctl,
                                                   const uint32_t* __restrict__ sel, uint32_t extra_tx,
-                                                  uint32_t wait_rounds) {
+                                                  uint32_t wait_rounds, int nbg_s, int slice_rows) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_abort, s_done;
@@ -174,7 +236,9 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       // (extra_tx > 0 only in the failure-detection self-test: bytes no copy delivers)
       mbar_expect_tx(&bar, band_bytes + extra_tx);
-      bulk_g2s(sm, packed + (size_t)bg * 32 * BB * S, band_bytes, &bar);
+      // band group bg = slice bg / nbg_s (volumes; images have one slice), band bg % nbg_s
+      const size_t row0 = (size_t)(bg / nbg_s) * slice_rows + (size_t)(bg % nbg_s) * 32 * BB;
+      bulk_g2s(sm, packed + row0 * S, band_bytes, &bar);
     }
     copy_pending = true;
     if (mbar_wait(&bar, parity, wait_rounds)) copy_pending = false;
@@ -191,7 +255,7 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
       const int tile = u % n_tiles, pi = u / n_tiles;
       const int bl = tile / G, grp = tile - (tile / G) * G;
       const uint32_t* lane_base = sm + (bl * 32 + lane) * S + grp * T;
-      const int y = (bg * BB + bl) * 32 + lane;
+      const int y = ((bg % nbg_s) * BB + bl) * 32 + lane;  // translation row within the slice
       executed += walk_unit<T>(prog, piece[pi], piece[pi + 1], lane_base, y, H, W, nw, grp * T, sel, lane, counts,
                                n_full, base);
     }
@@ -244,7 +308,7 @@ int ensure_device(lpf_paths* p, size_t packed_words) {
 }
 
 int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
-  if (b.d_words && b.W == g.W && b.S == g.S && b.r32 == g.r32) {
+  if (b.d_words && b.W == g.W && b.S == g.S && b.r32 == g.r32 && b.slice_rows == g.slice_rows) {
     b.T = g.T;
     b.BB = g.BB;
     return LPF_OK;
@@ -258,7 +322,9 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
   }
   std::vector<uint32_t> out;
   std::vector<int64_t> piece;
-  bake_words(p->host, prog, g.S, g.r32, out, piece);
+  // volumes: a voxel (sx, sy, sz) of a translation on staged row `lane` reads
+  // row lane + sz * slice_rows + sy + ry (sy may be negative in 3D)
+  bake_words(p->host, prog, g.S, g.r32, out, piece, g.slice_rows, g.slice_rows ? g.ry : 0);
   if (out.size() / 4 >= (size_t(1) << 32)) return LPF_EUNSUPPORTED;  // group offsets are 32-bit
   std::vector<uint32_t> piece32(piece.begin(), piece.end());
   cudaError_t e;
@@ -274,6 +340,7 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
   b.r32 = g.r32;
   b.T = g.T;
   b.BB = g.BB;
+  b.slice_rows = g.slice_rows;
   b.n_pieces = (int)prog.piece_begin.size() - 1;
   return LPF_OK;
 }
@@ -329,7 +396,8 @@ static void launch_walk(const Geometry& g, const Baked& b, lpf_paths* p, unsigne
   walk_kernel<T><<<blocks, 32 * g.G * g.BB, g.band_bytes, s>>>(
       p->d_packed, g.H, g.W, g.S, g.nw, g.G, g.BB, g.band_bytes, g.nbg, b.n_pieces,
       reinterpret_cast<const uint4*>(b.d_words), b.d_piece, c,
-      p->host.n_full, p->host.base, p->d_status, p->d_sel_active, selftest_extra_tx(p), selftest_wait_rounds(p));
+      p->host.n_full, p->host.base, p->d_status, p->d_sel_active, selftest_extra_tx(p), selftest_wait_rounds(p),
+      g.nbg_s, g.slice_rows);
 }
 
 // Enqueue one full evaluation with launch shape (T, BB) (<= 0: tuned or
@@ -337,6 +405,7 @@ static void launch_walk(const Geometry& g, const Baked& b, lpf_paths* p, unsigne
 static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* counts, cudaStream_t s,
                     bool standard, int T = 0, int BB = 0, const uint8_t* sel = nullptr, bool accumulate = false) {
   if (!p || !img || !counts) return LPF_EINVAL;
+  if (p->host.dims != 2) return LPF_EINVAL;  // a volume's handle: lpf_full_3d
   if (H < 1 || W < 1 || H > 8192 || W > 8192) return LPF_EINVAL;
   if (p->host.rx >= W || p->host.ry >= H) return LPF_EINVAL;
   const Program& prog = standard ? p->host.plain : p->host.tree;
@@ -470,6 +539,71 @@ static int autotune_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t
   return LPF_OK;
 }
 
+// Full evaluation of a volume (3D handle): pack the slices, walk, mirror.
+static int run_full3(const uint8_t* vol, int D, int H, int W, lpf_paths* p, int64_t* counts, cudaStream_t s) {
+  if (!p || !vol || !counts) return LPF_EINVAL;
+  if (p->host.dims != 3) return LPF_EINVAL;  // an image's handle: lpf_full
+  if (D < 1 || H < 1 || W < 1 || D > 4096 || H > 4096 || W > 4096) return LPF_EINVAL;
+  if (p->host.rx >= W || p->host.ry >= H || p->host.rz >= D) return LPF_EINVAL;
+  const Program& prog = p->host.tree;
+  if (prog.stack_depth > kDevStack) return LPF_EUNSUPPORTED;
+  std::call_once(g_attr_once, set_kernel_attributes);
+  if (g_attr_status) return g_attr_status;
+  int T = 0, BB = 0;
+  for (const Tuned& t : p->tuned)
+    if (t.H == H && t.W == W) { T = t.T; BB = t.BB; }
+  Geometry g;
+  int rc = make_geometry3(D, H, W, p->host.rx, p->host.ry, p->host.rz, T, BB, g);
+  if (rc) return rc;
+  if ((int)g.band_bytes > g_max_dyn_smem) return LPF_EUNSUPPORTED;
+  rc = ensure_device(p, g.packed_words);
+  if (rc) return rc;
+  rc = bake(p, prog, g, p->tree);
+  if (rc) return rc;
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return set_cuda_error(e);
+  }
+  int blocks = 0;
+  switch (g.T) {
+    case 1: blocks = walk_blocks<1>(g); break;
+    case 2: blocks = walk_blocks<2>(g); break;
+    case 4: blocks = walk_blocks<4>(g); break;
+    default: blocks = walk_blocks<8>(g); break;
+  }
+  if (blocks < 0) return -blocks;
+  blocks = std::min(blocks, g.nbg * p->tree.n_pieces);
+  (void)cudaGetLastError();
+  const int64_t n_full = p->host.n_full, base = p->host.base;
+  {
+    const int64_t total = std::max<int64_t>((int64_t)g.rows * g.S, 2 * n_full);
+    const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    pack_vol_kernel<<<pblocks, 256, 0, s>>>(vol, D, H, W, g.ry, g.r32, g.S, g.slice_rows, g.rows, p->d_packed,
+                                            reinterpret_cast<unsigned long long*>(counts), 2 * n_full,
+                                            p->d_status + 1, kCtlUnits - 1 + g.nbg,
+                                            p->checked ? p->d_status : nullptr);
+  }
+  unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
+  p->nominal_pixels = prog.n_pixel_words * g.nbg * g.G * g.BB;
+  p->d_sel_active = nullptr;
+  if (p->ev_start) cudaEventRecord(p->ev_start, s);
+  switch (g.T) {
+    case 1: launch_walk<1>(g, p->tree, p, c, blocks, s); break;
+    case 2: launch_walk<2>(g, p->tree, p, c, blocks, s); break;
+    case 4: launch_walk<4>(g, p->tree, p, c, blocks, s); break;
+    default: launch_walk<8>(g, p->tree, p, c, blocks, s); break;
+  }
+  if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
+  if (n_full > 1) {
+    const int64_t n = 2 * (n_full - base - 1);
+    const int mblocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    mirror_kernel<<<mblocks, 256, 0, s>>>(c, n_full, base);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
 // ---------------------------------------------------------------------------
 // Full evaluation without allocating.
 //
@@ -527,6 +661,7 @@ int* noalloc_ctl_if_ready(int dev) {
 
 static int run_full_noalloc(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* counts, cudaStream_t s) {
   if (!p || !img || !counts) return LPF_EINVAL;
+  if (p->host.dims != 2) return LPF_EINVAL;
   if (H < 1 || W < 1 || H > 8192 || W > 8192) return LPF_EINVAL;
   if (p->host.rx >= W || p->host.ry >= H) return LPF_EINVAL;
   if (p->host.tree.stack_depth > kDevStack) return LPF_EUNSUPPORTED;
@@ -589,7 +724,7 @@ static int run_full_noalloc(const uint8_t* img, int H, int W, lpf_paths* p, int6
                                                       g.nbg, b.n_pieces, reinterpret_cast<const uint4*>(b.d_words), \
                                                       b.d_piece, c, n_full, base,                              \
                                                       slot.ctl, nullptr, selftest_extra_tx(p),                  \
-                                                      selftest_wait_rounds(p))
+                                                      selftest_wait_rounds(p), g.nbg_s, g.slice_rows)
   switch (g.T) {
     case 1: LPF_NOALLOC_WALK(1); break;
     case 2: LPF_NOALLOC_WALK(2); break;
@@ -646,6 +781,32 @@ int lpf_build_paths(int32_t rx, int32_t ry, lpf_paths** out) {
   }
   *out = p;
   return LPF_OK;
+}
+
+int lpf_build_paths_3d(int32_t rx, int32_t ry, int32_t rz, lpf_paths** out) {
+  if (!out) return LPF_EINVAL;
+  *out = nullptr;
+  if (rx < 0 || ry < 0 || rz < 0 || rx > 1023 || ry > 1023 || rz > 1023) return LPF_EINVAL;
+  lpf_paths* p = new (std::nothrow) lpf_paths();
+  if (!p) return LPF_ENOMEM;
+  std::string err;
+  int rc;
+  try {
+    rc = lpf::build_paths_nd(rx, ry, rz, 3, 0, p->host, err);
+  } catch (const std::bad_alloc&) {
+    rc = LPF_ENOMEM;
+  }
+  if (rc != 0) {
+    delete p;
+    return rc == LPF_ENOMEM ? LPF_ENOMEM : LPF_EUNSUPPORTED;
+  }
+  *out = p;
+  return LPF_OK;
+}
+
+int lpf_full_3d(const uint8_t* vol_dev, int32_t D, int32_t H, int32_t W, lpf_paths* paths, int64_t* counts_dev,
+                lpf_stream_t stream) {
+  return lpf::run_full3(vol_dev, D, H, W, paths, counts_dev, (cudaStream_t)stream);
 }
 
 int lpf_paths_info(const lpf_paths* p, int64_t* n_full, int64_t* n_canon, int64_t* n_off) {

@@ -33,27 +33,52 @@ void segment_canonical(int dx, int dy, std::vector<int16_t>& out) {
   }
 }
 
+// 3D segment, the same rule on every minor axis (one error term per axis):
+// the major axis advances one voxel per step, each other axis advances when
+// its error reaches a full voxel, ties going away from the start.
+void segment_canonical3(int dx, int dy, int dz, std::vector<int16_t>& out) {
+  const int ad[3] = {std::abs(dx), std::abs(dy), std::abs(dz)};
+  const int g[3] = {dx < 0 ? -1 : 1, dy < 0 ? -1 : 1, dz < 0 ? -1 : 1};
+  const int a = std::max(ad[0], std::max(ad[1], ad[2]));
+  out.clear();
+  int pos[3] = {0, 0, 0};
+  int err[3] = {a, a, a};
+  for (int i = 0; i <= a; ++i) {
+    if (i > 0)
+      for (int j = 0; j < 3; ++j) {
+        err[j] += 2 * ad[j];
+        if (err[j] >= 2 * a) { err[j] -= 2 * a; ++pos[j]; }
+      }
+    for (int j = 0; j < 3; ++j) out.push_back((int16_t)(g[j] * pos[j]));
+  }
+}
+
 namespace {
 
-// Child slot of a one-pixel move inside a canonical segment: the move is
-// (mx, my) with my in {0, 1} and mx in {-1, 0, 1}, never (0, 0).
+// Child slot of a one-pixel move inside a canonical segment.  2D: the move
+// is (mx, my) with my in {0, 1} and mx in {-1, 0, 1}, never (0, 0) (5
+// slots).  3D: (mx, my, mz) with mz in {0, 1}, mx, my in {-1, 0, 1} (18
+// slots, one of them unused).
 inline int move_slot(int mx, int my) { return my == 0 ? (mx < 0 ? 0 : 1) : 2 + (mx + 1); }
+inline int move_slot3(int mx, int my, int mz) { return mz * 9 + (my + 1) * 3 + (mx + 1); }
 
 struct Trie {
+  int slots = 5;                  // children per node
   std::vector<int32_t> parent;
-  std::vector<int16_t> pix;       // [n][2]
+  std::vector<int16_t> pix;       // [n][3] (x, y, z)
   std::vector<int32_t> vec;
-  std::vector<int32_t> child5;    // [n][5]
+  std::vector<int32_t> child5;    // [n][slots]
   std::vector<int32_t> depth;
 
-  int32_t add(int32_t par, int16_t x, int16_t y, int32_t d) {
+  int32_t add(int32_t par, int16_t x, int16_t y, int16_t z, int32_t d) {
     const int32_t id = (int32_t)parent.size();
     parent.push_back(par);
     pix.push_back(x);
     pix.push_back(y);
+    pix.push_back(z);
     vec.push_back(-1);
     depth.push_back(d);
-    for (int k = 0; k < 5; ++k) child5.push_back(-1);
+    for (int k = 0; k < slots; ++k) child5.push_back(-1);
     return id;
   }
 };
@@ -160,38 +185,60 @@ static void emit_records(const std::vector<Event>& ev, Program& prog,
 }
 
 int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err) {
-  if (rx < 0 || ry < 0 || rx > 4095 || ry > 4095) { err = "window radius out of range [0, 4095]"; return -1; }
+  return build_paths_nd(rx, ry, 0, 2, n_pieces, p, err);
+}
+
+int build_paths_nd(int32_t rx, int32_t ry, int32_t rz, int dims, int n_pieces, Paths& p, std::string& err) {
+  if (rx < 0 || ry < 0 || rz < 0 || rx > 4095 || ry > 4095 || rz > 4095) {
+    err = "window radius out of range [0, 4095]";
+    return -1;
+  }
+  if (dims != 2 && dims != 3) { err = "dims must be 2 or 3"; return -1; }
+  if (dims == 2) rz = 0;
   p = Paths();
   p.rx = rx;
   p.ry = ry;
-  p.n_full = (int64_t)(2 * rx + 1) * (2 * ry + 1);
+  p.rz = rz;
+  p.dims = dims;
+  const int64_t nxy = (int64_t)(2 * rx + 1) * (2 * ry + 1);
+  p.n_full = nxy * (2 * rz + 1);
   p.base = (p.n_full - 1) / 2;
   p.n_canon = p.n_full - p.base;
-  p.vec.resize(2 * p.n_canon);
+  p.vec.resize((size_t)dims * p.n_canon);
   p.ptr.assign(p.n_canon + 1, 0);
   std::vector<int16_t> seg;
   for (int64_t c = 0; c < p.n_canon; ++c) {
     const int64_t k = p.base + c;
-    const int dy = (int)(k / (2 * rx + 1)) - ry, dx = (int)(k % (2 * rx + 1)) - rx;
-    p.vec[2 * c] = (int16_t)dx;
-    p.vec[2 * c + 1] = (int16_t)dy;
-    segment_canonical(dx, dy, seg);
-    p.ptr[c + 1] = p.ptr[c] + (int64_t)seg.size() / 2;
+    const int dz = (int)(k / nxy) - rz;
+    const int64_t rem = k % nxy;
+    const int dy = (int)(rem / (2 * rx + 1)) - ry, dx = (int)(rem % (2 * rx + 1)) - rx;
+    p.vec[(size_t)dims * c] = (int16_t)dx;
+    p.vec[(size_t)dims * c + 1] = (int16_t)dy;
+    if (dims == 3) {
+      p.vec[(size_t)dims * c + 2] = (int16_t)dz;
+      segment_canonical3(dx, dy, dz, seg);
+    } else {
+      segment_canonical(dx, dy, seg);
+    }
+    p.ptr[c + 1] = p.ptr[c] + (int64_t)seg.size() / dims;
     p.off.insert(p.off.end(), seg.begin(), seg.end());
   }
 
-  // Prefix tree of all canonical segments; node 0 is pixel (0,0).
+  // Prefix tree of all canonical segments; node 0 is pixel (0,0[,0]).
   Trie t;
-  t.add(-1, 0, 0, 0);
+  t.slots = dims == 3 ? 18 : 5;
+  const int S5 = t.slots;
+  t.add(-1, 0, 0, 0, 0);
   for (int64_t c = 0; c < p.n_canon; ++c) {
     int32_t n = 0;
     for (int64_t j = p.ptr[c] + 1; j < p.ptr[c + 1]; ++j) {
-      const int16_t x = p.off[2 * j], y = p.off[2 * j + 1];
-      const int slot = move_slot(x - t.pix[2 * n], y - t.pix[2 * n + 1]);
-      int32_t ch = t.child5[5 * (int64_t)n + slot];
+      const int16_t x = p.off[dims * j], y = p.off[dims * j + 1], z = dims == 3 ? p.off[dims * j + 2] : 0;
+      const int mx = x - t.pix[3 * n], my = y - t.pix[3 * n + 1], mz = z - t.pix[3 * n + 2];
+      const int slot = dims == 3 ? move_slot3(mx, my, mz) : move_slot(mx, my);
+      int32_t ch = t.child5[(int64_t)S5 * n + slot];
       if (ch < 0) {
-        ch = t.add(n, x, y, t.depth[n] + 1);
-        t.child5[5 * (int64_t)n + slot] = ch;
+        ch = t.add(n, x, y, z, t.depth[n] + 1);
+        t.child5[(int64_t)S5 * n + slot] = ch;
       }
       n = ch;
     }
@@ -204,9 +251,9 @@ int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err
   std::vector<int32_t> cstart(nn + 1, 0), clist;
   clist.reserve(nn);
   for (int64_t n = 0; n < nn; ++n) {
-    int32_t cs[5];
+    int32_t cs[18];
     int m = 0;
-    for (int k = 0; k < 5; ++k) if (t.child5[5 * n + k] >= 0) cs[m++] = t.child5[5 * n + k];
+    for (int k = 0; k < S5; ++k) if (t.child5[S5 * n + k] >= 0) cs[m++] = t.child5[S5 * n + k];
     std::sort(cs, cs + m, [&](int32_t a, int32_t b) { return sub[a] != sub[b] ? sub[a] < sub[b] : a < b; });
     for (int k = 0; k < m; ++k) clist.push_back(cs[k]);
     cstart[n + 1] = (int32_t)clist.size();
@@ -329,11 +376,11 @@ int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err
       int32_t n = 0;
       chain.push_back(0);
       for (int64_t j = p.ptr[c] + 1; j < p.ptr[c + 1]; ++j) {
-        const int16_t x = p.off[2 * j], y = p.off[2 * j + 1];
+        const int16_t x = p.off[dims * j], y = p.off[dims * j + 1], z = dims == 3 ? p.off[dims * j + 2] : 0;
         int32_t found = -1;
         for (int32_t k = cstart[n]; k < cstart[n + 1]; ++k) {
           const int32_t ch = clist[k];
-          if (t.pix[2 * ch] == x && t.pix[2 * ch + 1] == y) { found = ch; break; }
+          if (t.pix[3 * ch] == x && t.pix[3 * ch + 1] == y && t.pix[3 * ch + 2] == z) { found = ch; break; }
         }
         n = found;
         chain.push_back(n);
@@ -353,7 +400,13 @@ int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err
   resolve_skips(plain);
 
   p.node_parent = std::move(t.parent);
-  p.node_pix = std::move(t.pix);
+  p.node_pix.resize(2 * (size_t)nn);
+  if (dims == 3) p.node_pz.resize((size_t)nn);
+  for (int64_t n = 0; n < nn; ++n) {
+    p.node_pix[2 * n] = t.pix[3 * n];
+    p.node_pix[2 * n + 1] = t.pix[3 * n + 1];
+    if (dims == 3) p.node_pz[n] = t.pix[3 * n + 2];
+  }
   p.node_vec = std::move(t.vec);
   return 0;
 }
@@ -422,7 +475,7 @@ void resolve_skips(Program& prog) {
 }
 
 void bake_words(const Paths& p, const Program& prog, int S, int r32, std::vector<uint32_t>& out,
-                std::vector<int64_t>& piece_out) {
+                std::vector<int64_t>& piece_out, int slice_rows, int row_off) {
   const std::vector<uint32_t>& w = prog.words;
   out.clear();
   out.reserve(w.size() + w.size() / 8);
@@ -443,8 +496,9 @@ void bake_words(const Paths& p, const Program& prog, int S, int r32, std::vector
     for (uint32_t k = 0; k < n; ++k) {
       const int node = (int)w[i + k];
       const int sxp = p.node_pix[2 * node] + r32;  // >= 0
-      const int sy = p.node_pix[2 * node + 1];
-      pix.push_back({(uint32_t)(sy * S + (sxp >> 5)) * 4u, (uint32_t)(sxp & 31)});
+      const int sz = p.node_pz.empty() ? 0 : p.node_pz[node];
+      const int row = sz * slice_rows + p.node_pix[2 * node + 1] + row_off;  // >= 0
+      pix.push_back({(uint32_t)(row * S + (sxp >> 5)) * 4u, (uint32_t)(sxp & 31)});
     }
     i += n;
     std::stable_sort(pix.begin(), pix.end(),

@@ -85,15 +85,17 @@ struct Program {
 };
 
 struct Paths {
-  int32_t rx = 0, ry = 0;
+  int32_t rx = 0, ry = 0, rz = 0;
+  int dims = 2;                      // 2: images; 3: volumes (vectors (dx, dy, dz))
   int64_t n_full = 0, n_canon = 0, base = 0;
   // Canonical vectors in canonical order (canonical index = full index - base).
-  std::vector<int16_t> vec;          // [n_canon][2] (dx, dy)
+  std::vector<int16_t> vec;          // [n_canon][dims] (dx, dy[, dz])
   std::vector<int64_t> ptr;          // [n_canon + 1] CSR into off
-  std::vector<int16_t> off;          // [ptr[n_canon]][2] (sx, sy) pixel offsets
+  std::vector<int16_t> off;          // [ptr[n_canon]][dims] (sx, sy[, sz]) pixel offsets
   // Prefix tree of the canonical segments.
   std::vector<int32_t> node_parent;  // -1 for the root (pixel (0,0))
-  std::vector<int16_t> node_pix;     // [n_nodes][2]
+  std::vector<int16_t> node_pix;     // [n_nodes][2] (x, y)
+  std::vector<int16_t> node_pz;      // [n_nodes] z (3D only, else empty)
   std::vector<int32_t> node_vec;     // canonical index ending here, or -1
   // Programs: tree walk (shared prefixes) and plain (every segment from scratch).
   Program tree;
@@ -106,6 +108,9 @@ inline bool is_canonical(int dx, int dy) { return dy > 0 || (dy == 0 && dx >= 0)
 
 // Pixel offsets of the segment (0,0) -> (dx,dy), for canonical (dx,dy).
 void segment_canonical(int dx, int dy, std::vector<int16_t>& out_xy);
+// Voxel offsets (x, y, z triples) of the 3D segment (0,0,0) -> (dx,dy,dz),
+// for (dx,dy,dz) in the 3D half-domain (dz > 0, or dz = 0 and (dx,dy) in D).
+void segment_canonical3(int dx, int dy, int dz, std::vector<int16_t>& out_xyz);
 
 // Build tables and both programs, split into n_pieces pieces (n_pieces < 1:
 // one piece per 2 longest-segment lengths of tree nodes, at least 64, and at
@@ -115,6 +120,8 @@ void segment_canonical(int dx, int dy, std::vector<int16_t>& out_xy);
 // Returns 0 or a negative status.
 constexpr int64_t kMaxPieces = 1024;
 int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err);
+// The same for dims = 2 (rz ignored) or dims = 3 (vectors |dz| <= rz too).
+int build_paths_nd(int32_t rx, int32_t ry, int32_t rz, int dims, int n_pieces, Paths& p, std::string& err);
 
 // Split a program into pieces of similar pixel count; fills piece tables.
 void split_program(const Paths& p, Program& prog, int n_pieces);
@@ -128,7 +135,9 @@ void resolve_skips(Program& prog);
 // per group.
 constexpr uint32_t kCntBits = 13;
 constexpr uint32_t kCntMask = (1u << kCntBits) - 1u;
+// 3D programs: a voxel at offset (sx, sy, sz) reads staged row
+// sz * slice_rows + sy + row_off (slices of slice_rows packed rows).
 void bake_words(const Paths& p, const Program& prog, int S, int r32, std::vector<uint32_t>& out,
-                std::vector<int64_t>& piece_out);
+                std::vector<int64_t>& piece_out, int slice_rows = 0, int row_off = 0);
 
 }  // namespace lpf

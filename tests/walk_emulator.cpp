@@ -28,32 +28,36 @@ inline uint32_t funnel_r(uint32_t lo, uint32_t hi, uint32_t s) {
 
 }  // namespace
 
-// counts: int64 [2][n_full] (phase 0 first), stats: int64 [4] = {pixels
-// walked, nominal pixels, skips taken, pairs baked}.  Returns 0 or -1.
-extern "C" int emulate_walk(const uint8_t* img, int H, int W, int rx, int ry, int standard, int T,
-                            int64_t* counts, int64_t* stats) {
-  Paths p;
-  std::string err;
-  if (build_paths(rx, ry, 0, p, err)) return -1;
-  const Program& prog = standard ? p.plain : p.tree;
+// Walk every unit of `prog` over the packed layout of the kernels.  Images:
+// one slice, packed row y = image row y mod H.  Volumes: slices of
+// Hs = 32 nb + 2 ry packed rows (image row (y'' - ry) mod H of slice z' mod D),
+// D + rz slices; a translation row of slice z starts at packed row z Hs + y.
+static int emulate_impl(const Paths& p, const Program& prog, const uint8_t* img, int D, int H, int W, int T,
+                        bool volume, int64_t* counts, int64_t* stats) {
+  const int rx = p.rx, ry = p.ry, rz = p.rz;
   const int nw = (W + 31) / 32, G = (nw + T - 1) / T, r32 = ((rx + 31) / 32) * 32;
   int S = G * T + ((r32 + rx) >> 5) + 1;
   if (!(S & 1)) ++S;
-  const int nb = (H + 31) / 32, rows = 32 * nb + ry;
-  // packed rows: bit b of word k of row y = pixel (y mod H, (32k + b - r32) mod W)
+  const int nb = (H + 31) / 32;
+  const int Hs = volume ? (32 * nb + 2 * ry + 3) & ~3 : 0;  // as the kernels: a multiple of 4 rows
+  const int rows = volume ? (D + rz) * Hs : 32 * nb + ry;
+  // packed rows: bit b of word k = pixel at column (32k + b - r32) mod W
   std::vector<uint32_t> packed((size_t)rows * S + 4, 0);
-  for (int y = 0; y < rows; ++y)
+  for (int r = 0; r < rows; ++r) {
+    const int zs = volume ? (r / Hs) % D : 0;
+    const int yi = volume ? (((r % Hs) - ry) % H + H) % H : r % H;
     for (int k = 0; k < S; ++k) {
       uint32_t bits = 0;
       for (int b = 0; b < 32; ++b) {
         const int x = ((32 * k + b - r32) % W + W) % W;
-        bits |= (uint32_t)(img[(y % H) * W + x] != 0) << b;
+        bits |= (uint32_t)(img[((size_t)zs * H + yi) * W + x] != 0) << b;
       }
-      packed[(size_t)y * S + k] = bits;
+      packed[(size_t)r * S + k] = bits;
     }
+  }
   std::vector<uint32_t> w;
   std::vector<int64_t> piece;
-  bake_words(p, prog, S, r32, w, piece);
+  bake_words(p, prog, S, r32, w, piece, Hs, volume ? ry : 0);
   const int64_t nf = p.n_full, base = p.base;
   std::memset(counts, 0, sizeof(int64_t) * 2 * nf);
   int64_t walked = 0, skips = 0, pairs = 0;
@@ -64,6 +68,7 @@ extern "C" int emulate_walk(const uint8_t* img, int H, int W, int rx, int ry, in
       if (m1[i] | m0[i]) return false;
     return true;
   };
+  for (int zs = 0; zs < (volume ? D : 1); ++zs)
   for (int band = 0; band < nb; ++band)
     for (size_t pi = 0; pi + 1 < piece.size(); ++pi)
       for (int g = 0; g < G; ++g) {
@@ -81,7 +86,7 @@ extern "C" int emulate_walk(const uint8_t* img, int H, int W, int rx, int ry, in
         // pair reads the window of `word` with a second shift `shift2`.
         auto and_pixel = [&](uint32_t word, uint32_t shift) {
           for (int lane = 0; lane < 32; ++lane) {
-            const uint32_t* lb = packed.data() + (size_t)(band * 32 + lane) * S + g * T;
+            const uint32_t* lb = packed.data() + (size_t)(zs * Hs + band * 32 + lane) * S + g * T;
             const uint32_t* sa = lb + ((word >> 5) >> 2);  // byte offset -> word
             for (int t = 0; t < T; ++t) {
               const uint32_t a = funnel_r(sa[t], sa[t + 1], shift);
@@ -147,8 +152,27 @@ extern "C" int emulate_walk(const uint8_t* img, int H, int W, int rx, int ry, in
   for (int64_t j = base + 1; j < nf; ++j)
     for (int q = 0; q < 2; ++q) counts[q * nf + nf - 1 - j] = counts[q * nf + j];
   stats[0] = walked;
-  stats[1] = prog.n_pixel_words * (int64_t)nb * G;
+  stats[1] = prog.n_pixel_words * (int64_t)nb * G * (volume ? D : 1);
   stats[2] = skips;
   stats[3] = pairs;
   return 0;
+}
+
+// counts: int64 [2][n_full] (phase 0 first), stats: int64 [4] = {pixels
+// walked, nominal pixels, skips taken, pairs baked}.  Returns 0 or -1.
+extern "C" int emulate_walk(const uint8_t* img, int H, int W, int rx, int ry, int standard, int T,
+                            int64_t* counts, int64_t* stats) {
+  Paths p;
+  std::string err;
+  if (build_paths(rx, ry, 0, p, err)) return -1;
+  return emulate_impl(p, standard ? p.plain : p.tree, img, 1, H, W, T, false, counts, stats);
+}
+
+// The same for a volume vol[z][y][x] (D x H x W) and window (rx, ry, rz).
+extern "C" int emulate_walk3(const uint8_t* vol, int D, int H, int W, int rx, int ry, int rz, int T,
+                             int64_t* counts, int64_t* stats) {
+  Paths p;
+  std::string err;
+  if (build_paths_nd(rx, ry, rz, 3, 0, p, err)) return -1;
+  return emulate_impl(p, p.tree, vol, D, H, W, T, true, counts, stats);
 }
