@@ -1,5 +1,7 @@
 """GPU parity of lpf_delta_swap (count changes and error changes) against the
 CPU oracle's recount-after-minus-before and its double-precision Eq. (LSE)."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -94,30 +96,27 @@ def test_error_only_and_determinism(gpu_lib):
     assert torch.equal(de1, de2) and torch.equal(de1, de3)  # bitwise reproducible
 
 
-def test_clustered_128_cell_full_batch_sampled(gpu_lib):
-    # 128x128 cell, |v| <= 64, K = 4096 candidates in one launch (the annealing
-    # workload); a sample of candidates is recounted by the oracle.
-    cell = synth.random_binary(128, 128, 0.3, 33)
+def test_clustered_128_cell_full_batch_64_candidates(gpu_lib):
+    # The swap-delta workload: the 128x128 clustered cell, |v| <= 64, K = 4096
+    # candidates in one launch; 64 of them (the first, the last, identities,
+    # same-phase and reversed pairs, and random ones) against the oracle's
+    # recount stored by tests/golden/make_lpf_goldens.py.
+    g = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "lpf_delta_clustered_128.npz"))
+    cell = synth.clustered_cell_128()
     rx = ry = 64
-    rng = np.random.default_rng(7)
-    flat = cell.reshape(-1)
-    ones = np.flatnonzero(flat == 1)
-    zeros = np.flatnonzero(flat == 0)
-    pairs = np.stack([rng.choice(ones, 4096), rng.choice(zeros, 4096)], axis=1).astype(np.int32)
+    pairs, sample, ref = g["pairs"], g["sample"], g["dcounts"].astype(np.int64)
     p = gpu_lib.lpf_build_paths(rx, ry)
     d_img = torch.from_numpy(cell).cuda()
     counts = gpu_lib.lpf_full(d_img, p)
-    orig = synth.clustered_512()
-    target = (oracle.lpf_full(orig[:160, :160], rx, ry) / float(160 * 160)).astype(np.float32)
+    counts_h = counts.cpu().numpy()
+    np.testing.assert_array_equal(counts_h, g["counts"])
+    target = (counts_h / float(cell.size) * 0.9).astype(np.float32)
     dc, de = gpu_lib.lpf_delta_swap(d_img, p, torch.from_numpy(pairs).cuda(),
                                     target=torch.from_numpy(target).cuda(), counts=counts, want_de=True)
+    assert gpu_lib.lpf_paths_status(p) == 0
     dc = dc.cpu().numpy()
     de = de.cpu().numpy()
-    sample = [0, 1, 4095, int(rng.integers(0, 4096))]
-    ref = oracle.delta_swap(cell, rx, ry, pairs[sample])
-    for j, k in enumerate(sample):
-        np.testing.assert_array_equal(dc[k], ref[j])
-    counts_h = counts.cpu().numpy()
+    np.testing.assert_array_equal(dc[sample], ref)
     de_ref = oracle.delta_objective(target, counts_h, ref, rx, ry, 128, 128)
     tol = _de_tolerance(target, counts_h, ref, rx, ry, 128, 128)
     assert (np.abs(de[sample] - de_ref) <= tol).all()

@@ -1,9 +1,13 @@
 """GPU parity of lpf_full / lpf_full_standard against the CPU oracle.
 
 Counts are integers: the bar is bit-exact equality with the oracle on every
-entry (small cases) or on sampled vectors evaluated one by one by the oracle
-(full-size cases), plus properties that hold at any size.
+entry -- the small cases against the oracle run now, the full-size 512x512
+workload against the oracle's whole table stored by
+tests/golden/make_lpf_goldens.py -- plus properties that hold at any size.
 """
+import hashlib
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -53,31 +57,43 @@ def test_full_matches_oracle(gpu_lib, name, make, rx, ry, standard):
     np.testing.assert_array_equal(got, ref)
 
 
-def test_ellipses_512_sampled_and_properties(gpu_lib):
-    # Full size (512x512, |dx|,|dy| <= 256), in the launch configuration the
-    # benchmark times: sampled vectors checked one by one against the oracle.
+GOLDEN_512 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "lpf_ellipses_512_r256.npz")
+
+
+def _golden_512():
+    """The oracle's whole [2][513*513] table of the 512x512 ellipses, window
+    256 (written by tests/golden/make_lpf_goldens.py, which calls only the
+    oracle), checked against the digest stored beside it."""
+    g = np.load(GOLDEN_512)
+    counts = g["counts"].astype(np.int64)
+    digest = hashlib.sha256(np.ascontiguousarray(counts, dtype="<i8").tobytes()).hexdigest()
+    assert digest == str(g["sha256"])
+    return counts
+
+
+@pytest.mark.parametrize("shape", ["T4_BB4", "autotuned", "standard"])
+def test_ellipses_512_every_entry_equals_the_oracle(gpu_lib, shape):
+    # Full size (512x512, |dx|,|dy| <= 256), all 2 x 263,169 counts compared
+    # with the oracle's: in the launch shape the benchmark's autotuner picks
+    # on the GB300 (4 words per thread, 4 bands per block), in whatever shape
+    # the autotuner picks now, and with the standard (no prefix sharing)
+    # program.
     img = synth.ellipses_512()
-    got, p = _run(gpu_lib, img, 256, 256)
+    ref = _golden_512()
+    p = gpu_lib.lpf_build_paths(256, 256)
+    d = torch.from_numpy(img).cuda()
+    if shape == "T4_BB4":
+        gpu_lib.lpf_set_launch_shape(p, 512, 512, 4, 4)
+    elif shape == "autotuned":
+        gpu_lib.lpf_autotune_full(d, p)
+    run = gpu_lib.lpf_full_standard if shape == "standard" else gpu_lib.lpf_full
+    got = run(d, p).cpu().numpy()
+    assert gpu_lib.lpf_paths_status(p) == 0
+    bad = np.argwhere(got != ref)
+    assert len(bad) == 0, f"{len(bad)} entries differ, first {bad[:5].tolist()}"
+    # properties that hold at any size
     n_full, _, base = oracle.window_sizes(256, 256)
-    rng = np.random.default_rng(0)
-    vecs = [(0, 0), (1, 0), (256, 0), (-256, 0), (0, 256), (256, 256), (-256, 256), (256, -256),
-            (255, 3), (-7, 200), (17, -129)]
-    vecs += [(int(a), int(b)) for a, b in rng.integers(-256, 257, size=(24, 2))]
-    ref = oracle.count_list(img, vecs)
-    for (dx, dy), r in zip(vecs, ref):
-        k = oracle.full_index(dx, dy, 256, 256)
-        assert got[0, k] == r[0] and got[1, k] == r[1], (dx, dy)
-    # properties at full size
     assert got[1, base] == int(img.sum()) and got[0, base] == img.size - int(img.sum())
-    np.testing.assert_array_equal(got, got[:, ::-1])
-    assert (got >= 0).all()
-
-
-def test_tree_equals_standard_at_full_size(gpu_lib):
-    img = synth.ellipses_512()
-    a, _ = _run(gpu_lib, img, 256, 256, standard=False)
-    b, _ = _run(gpu_lib, img, 256, 256, standard=True)
-    np.testing.assert_array_equal(a, b)
 
 
 def test_repeated_calls_and_width_change(gpu_lib):
