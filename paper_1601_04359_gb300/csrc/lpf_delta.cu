@@ -106,6 +106,73 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) delta_kernel(const uint8_t* 
   }
 }
 
+// z[v][y][x] = number of phase-0 pixels of S(v) + (x, y) for every canonical
+// vector and translation, from the extended cell (0/1 bytes).  Blocks stage
+// the cell once and take vectors at the grid stride; threads take
+// translations.
+__global__ void __launch_bounds__(kDeltaThreads) z_init_kernel(const uint8_t* __restrict__ ext, DeltaArgs g,
+                                                               uint8_t* __restrict__ z, int* __restrict__ status) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ __align__(8) uint64_t bar;
+  if (!delta_stage(sm, ext, g.ext_bytes, &bar)) {
+    if (threadIdx.x == 0) atomicOr(status, 1);
+    (void)mbar_wait(&bar, 0);
+    return;
+  }
+  const int hw = g.H * g.W;
+  for (int v = blockIdx.x; v < (int)g.n_canon; v += gridDim.x) {
+    const int o0 = __ldg(g.dptr + v), L1 = __ldg(g.dptr + v + 1) - o0;
+    uint8_t* zv = z + (int64_t)v * hw;
+    for (int p = threadIdx.x; p < hw; p += blockDim.x) {
+      const int y = p / g.W, x = p - y * g.W;
+      const uint8_t* base = sm + (y + g.ry) * g.We + (x + g.rx);
+      int c = 0;
+      for (int k = 0; k < L1; ++k) c += base[__ldg(g.doff + o0 + k)] == 0;
+      zv[p] = (uint8_t)c;
+    }
+  }
+}
+
+// Count changes (and error changes) of K candidates from the phase-0 counts
+// g.z: no staged cell, no block barriers -- a warp takes one candidate at a
+// time (candidates k = warp index over the grid's y extent, strided) and all
+// vectors of its block's chunk, in vector order, and writes that chunk's
+// partial error change.
+__global__ void __launch_bounds__(kDeltaThreads) delta_lookup_kernel(const uint8_t* __restrict__ img, DeltaArgs g,
+                                                                     const int32_t* __restrict__ pairs, int K,
+                                                                     int32_t* __restrict__ dcounts,
+                                                                     float* __restrict__ partial,
+                                                                     int* __restrict__ status) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ch = blockIdx.x;
+  const int v0 = g.chunk[ch], v1 = g.chunk[ch + 1];
+  const int npix = g.H * g.W;
+  const int stride = gridDim.y * kDeltaWarps;
+  for (int k = blockIdx.y * kDeltaWarps + warp; k < K; k += stride) {
+    int a = pairs[2 * k], b = pairs[2 * k + 1];
+    int skip = 0;
+    if (a < 0 || b < 0 || a >= npix || b >= npix) {
+      skip = 1;
+      if (lane == 0) atomicOr(status, 2);
+    } else if ((img[a] != 0) == (img[b] != 0)) {
+      skip = 1;                                   // same phase (or a == b): identity
+    } else if (img[a] == 0) {
+      const int t = a; a = b; b = t;              // a holds phase 1
+    }
+    int32_t* dk = dcounts ? dcounts + (int64_t)k * 2 * g.n_canon : nullptr;
+    float acc = 0.0f;
+    if (skip) {
+      if (dk)
+        for (int v = v0 + lane; v < v1; v += 32) { dk[v] = 0; dk[g.n_canon + v] = 0; }
+    } else {
+      // the warp's own pass over the chunk: v0, v0 + 1, ... (one warp, so
+      // "warp 0 of 1" in the helper's striding)
+      acc = delta_lookup_vectors_warp(g, a, b, v0, v1, lane, dk, delta_terms_global(g));
+    }
+    if (lane == 0 && partial) partial[(int64_t)k * g.n_chunks + ch] = acc;
+  }
+}
+
 // de[k] = sum over chunks of partial[k][c], in chunk order.
 __global__ void delta_reduce_kernel(const float* __restrict__ partial, int n_chunks, int K, float* __restrict__ de) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
@@ -126,16 +193,24 @@ static int bake_delta(lpf_paths* p, int W, int want_chunks, DeltaTables& t) {
   if (t.d_doff && t.We == We && t.want == want_chunks) return LPF_OK;
   if (t.d_doff) {
     cudaDeviceSynchronize();
-    cudaFree(t.d_doff); cudaFree(t.d_dptr); cudaFree(t.d_chunk);
+    cudaFree(t.d_doff); cudaFree(t.d_dptr); cudaFree(t.d_chunk); cudaFree(t.d_off16);
     t.d_doff = t.d_dptr = t.d_chunk = nullptr;
+    t.d_off16 = nullptr;
   }
   const Paths& h = p->host;
   std::vector<int32_t> off(h.ptr.back()), ptr(h.n_canon + 1);
   for (int64_t c = 0; c <= h.n_canon; ++c) ptr[c] = (int32_t)h.ptr[c];
   for (int64_t j = 0; j < h.ptr.back(); ++j) off[j] = (int32_t)h.off[2 * j + 1] * We + (int32_t)h.off[2 * j];
-  // chunks balanced by sum of (L+1)^2 (walks per vector times their length bound)
+  // chunks balanced by work: 2 (L+1) lookups per vector where count changes
+  // come from the phase-0 counts (segments up to 255 pixels), else 2 (L+1)
+  // walks of up to L+1 pixels
+  const bool lookups = std::max(h.rx, h.ry) + 1 <= 255;
+  auto weight = [&](int64_t c) {
+    const double l = (double)(ptr[c + 1] - ptr[c]);
+    return lookups ? l : l * l;
+  };
   double total = 0;
-  for (int64_t c = 0; c < h.n_canon; ++c) { const double l = (double)(ptr[c + 1] - ptr[c]); total += l * l; }
+  for (int64_t c = 0; c < h.n_canon; ++c) total += weight(c);
   // as many chunks as blocks fit on the GPU at once (but at least 16 vectors
   // each): a single candidate then runs in one wave over every SM (the
   // annealer evaluates batches of one or a few candidates while its
@@ -144,8 +219,7 @@ static int bake_delta(lpf_paths* p, int W, int want_chunks, DeltaTables& t) {
   std::vector<int32_t> chunk{0};
   double accw = 0;
   for (int64_t c = 0; c < h.n_canon; ++c) {
-    const double l = (double)(ptr[c + 1] - ptr[c]);
-    accw += l * l;
+    accw += weight(c);
     if (accw >= total * (double)chunk.size() / want && (int)chunk.size() < want) chunk.push_back((int32_t)c + 1);
   }
   if (chunk.back() != (int32_t)h.n_canon) chunk.push_back((int32_t)h.n_canon);
@@ -156,6 +230,9 @@ static int bake_delta(lpf_paths* p, int W, int want_chunks, DeltaTables& t) {
   if ((e = cudaMemcpy(t.d_doff, off.data(), off.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return set_cuda_error(e);
   if ((e = cudaMemcpy(t.d_dptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return set_cuda_error(e);
   if ((e = cudaMemcpy(t.d_chunk, chunk.data(), chunk.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return set_cuda_error(e);
+  if ((e = cudaMalloc(&t.d_off16, std::max<size_t>(1, h.off.size()) * 2)) != cudaSuccess) return set_cuda_error(e);
+  if ((e = cudaMemcpy(t.d_off16, h.off.data(), h.off.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return set_cuda_error(e);
   t.We = We;
   t.want = want_chunks;
   t.n_chunks = (int)chunk.size() - 1;
@@ -187,6 +264,8 @@ int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g) {
   g.phase_mask = 3;
   g.max_chunk_vecs = p->delta.max_chunk_vecs;
   g.sel_ext = nullptr;
+  g.z = nullptr;
+  g.off16 = p->delta.d_off16;
   g.inv_norm = 1.0f / ((float)H * (float)W);
   return LPF_OK;
 }
@@ -210,6 +289,10 @@ int delta_prepare(lpf_paths* p, int H, int W, int K) {
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fp, sa_persistent_kernel_entry());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(delta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    optin - (int)fa.sharedSizeBytes);
+    cudaFuncAttributes fz;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fz, z_init_kernel);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(z_init_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   optin - (int)fz.sharedSizeBytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(sa_batch_kernel_entry(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    optin - (int)fs.sharedSizeBytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(sa_persistent_kernel_entry(),
@@ -269,6 +352,33 @@ int delta_stride(int n_chunks, int K) {
   return std::max(1, std::min(K, (sms * 4 + n_chunks - 1) / n_chunks));
 }
 
+// Bytes of the phase-0 counts z for an H x W cell (one byte per canonical
+// vector and translation, plus word padding for the update atomics), or 0
+// when they do not apply: segments longer than 255 pixels (a byte count) or
+// more than kZBudget bytes.
+constexpr size_t kZBudget = size_t(2) << 30;
+size_t delta_z_bytes(const lpf_paths* p, int H, int W) {
+  if (std::max(p->host.rx, p->host.ry) + 1 > 255) return 0;
+  const size_t b = (size_t)p->host.n_canon * H * W + 4;
+  return b <= kZBudget ? b : 0;
+}
+
+int delta_z_prepare(lpf_paths* p, int H, int W) {
+  const size_t need = delta_z_bytes(p, H, W);
+  if (need > p->z_cap) {
+    if (p->d_z) { cudaDeviceSynchronize(); cudaFree(p->d_z); p->d_z = nullptr; p->z_cap = 0; }
+    cudaError_t e = cudaMalloc(&p->d_z, need);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    p->z_cap = need;
+  }
+  return LPF_OK;
+}
+
+void z_init_launch(const uint8_t* ext, const DeltaArgs& g, uint8_t* z, int* status, cudaStream_t s) {
+  z_init_kernel<<<std::min<int64_t>(g.n_canon, 2 * (int64_t)(g_sms > 0 ? g_sms : 152)), kDeltaThreads, g.ext_bytes,
+                  s>>>(ext, g, z, status);
+}
+
 int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, const int32_t* pairs_dev,
                    int32_t K, int32_t* dcounts_dev, const float* target_dev, const int64_t* counts_dev, float* de_dev,
                    int phase_mask, cudaStream_t s, const uint8_t* sel_ext, float inv_norm) {
@@ -294,11 +404,28 @@ int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* path
     build_ext_kernel<<<blocks, 256, 0, s>>>(img_dev, H, W, g.rx, g.ry, g.We, g.He, g.ext_bytes, paths->d_ext,
                                             paths->checked ? paths->d_status : nullptr);
   }
-  const dim3 grid(g.n_chunks, delta_stride(g.n_chunks, K));
-  if (paths->ev_start) cudaEventRecord(paths->ev_start, s);
-  delta_kernel<<<grid, kDeltaThreads, g.ext_bytes, s>>>(img_dev, paths->d_ext, g, pairs_dev, K, dcounts_dev,
-                                                                  de_dev ? paths->d_partial : nullptr, paths->d_status);
-  if (paths->ev_stop) cudaEventRecord(paths->ev_stop, s);
+  dim3 grid(g.n_chunks, delta_stride(g.n_chunks, K));
+  // Phase-0 counts of every (vector, translation) when they fit the budget:
+  // count changes by lookups; otherwise by walks.
+  if (delta_z_bytes(paths, H, W) > 0) {
+    rc = delta_z_prepare(paths, H, W);
+    if (rc) return rc;
+    g.z = paths->d_z;
+    z_init_kernel<<<std::min<int64_t>(g.n_canon, 2 * (int64_t)(g_sms > 0 ? g_sms : 152)), kDeltaThreads, g.ext_bytes,
+                    s>>>(paths->d_ext, g, g.z, paths->d_status);
+    if (paths->ev_start) cudaEventRecord(paths->ev_start, s);
+    // a warp per candidate: enough candidate groups of 16 for a few warps per SM slot
+    grid.y = (unsigned)std::max(1, std::min((K + kDeltaWarps - 1) / kDeltaWarps,
+                                            (8 * (g_sms > 0 ? g_sms : 152) + g.n_chunks - 1) / g.n_chunks));
+    delta_lookup_kernel<<<grid, kDeltaThreads, 0, s>>>(img_dev, g, pairs_dev, K, dcounts_dev,
+                                                       de_dev ? paths->d_partial : nullptr, paths->d_status);
+    if (paths->ev_stop) cudaEventRecord(paths->ev_stop, s);
+  } else {
+    if (paths->ev_start) cudaEventRecord(paths->ev_start, s);
+    delta_kernel<<<grid, kDeltaThreads, g.ext_bytes, s>>>(img_dev, paths->d_ext, g, pairs_dev, K, dcounts_dev,
+                                                          de_dev ? paths->d_partial : nullptr, paths->d_status);
+    if (paths->ev_stop) cudaEventRecord(paths->ev_stop, s);
+  }
   if (de_dev) {
     const int blocks = std::min((K + 255) / 256, 1024);
     delta_reduce_kernel<<<blocks, 256, 0, s>>>(paths->d_partial, g.n_chunks, K, de_dev);

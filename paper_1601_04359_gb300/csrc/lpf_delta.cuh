@@ -32,6 +32,12 @@ struct DeltaArgs {
   int max_chunk_vecs;           // vectors in the largest chunk
   const uint8_t* sel_ext;       // selected start translations, extended layout (null: all)
   float inv_norm;               // descriptor = count * inv_norm (1/(H W), or 1/N selected)
+  // Phase-0 counts (see delta_lookup_vectors): z[v][y][x] = number of phase-0
+  // pixels of S(v) + (x, y), one byte per canonical vector and translation;
+  // null: count changes by walks.  off16: the segments' pixel offsets
+  // (sx, sy) as int16 pairs, CSR by dptr.
+  uint8_t* z;
+  const int16_t* off16;
 };
 
 // Where a walk finds the target and the current count of vector v for the
@@ -175,6 +181,169 @@ __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const Del
     }
   }
   return acc;
+}
+
+// ---- count changes by lookups of per-translation phase-0 counts -----------
+//
+// With z_v(x) = number of phase-0 pixels of S(v) + x (L1 = |S(v)| pixels), a
+// translation x through a (phase 1 before, 0 after) and not through b lies
+// in phase 1 before iff z = 0 (lost by phase 1) and in phase 0 after iff
+// z = L1 - 1 (gained by phase 0); through b (0 before, 1 after) and not
+// through a, it lies in phase 1 after iff z = 1 (gained) and in phase 0
+// before iff z = L1 (lost); a translation through both changes neither
+// phase.  These are the same count changes as the walks' (the definition of
+// Sec. 2.2 restricted to the translations the exchange touches), read from
+// one byte per translation instead of walking the segment.
+
+// Canonical vector of canonical index v (window rx, ry).
+__device__ __forceinline__ void delta_vector(const DeltaArgs& g, int v, int& dx, int& dy) {
+  const int64_t k = g.base + v;
+  dy = (int)(k / (2 * g.rx + 1)) - g.ry;
+  dx = (int)(k % (2 * g.rx + 1)) - g.rx;
+}
+
+// True when pixel (qx, qy) lies on S(v) placed at translation (x, y), on the
+// torus (the segment spans fewer than W columns and H rows, so at most one
+// period of (qx, qy) is in its bounding box).
+__device__ __forceinline__ bool delta_on_segment(const DeltaArgs& g, int o0, int dx, int dy, int x, int y, int qx,
+                                                 int qy) {
+  int uy = (qy - y) % g.H;
+  if (uy < 0) uy += g.H;
+  if (uy > dy) return false;                // canonical: 0 <= sy <= dy
+  const int xlo = dx < 0 ? dx : 0, xhi = dx < 0 ? 0 : dx;
+  int ux = (qx - x - xlo) % g.W;
+  if (ux < 0) ux += g.W;
+  ux += xlo;
+  if (ux > xhi) return false;
+  const int adx = dx < 0 ? -dx : dx;
+  if (adx >= dy) {                          // x-major: pixel k at sx = sign(dx) k
+    const int k = dx < 0 ? -ux : ux;
+    return g.off16[2 * (o0 + k) + 1] == uy;
+  }
+  return g.off16[2 * (o0 + uy)] == ux;      // y-major: pixel k at sy = k
+}
+
+// Same contract as delta_walk_vectors (a phase 1, b phase 0; the warp's
+// vectors v = v0 + warp, v0 + warp + kDeltaWarps, ...; lane 0 writes and
+// returns), from the phase-0 counts g.z.
+__device__ __forceinline__ float delta_lookup_vectors_strided(const DeltaArgs& g, int a, int b, int v0, int v1,
+                                                              int vstep, int lane, int32_t* dcounts_k,
+                                                              const DeltaTerms& dt);
+
+__device__ __forceinline__ float delta_lookup_vectors(const DeltaArgs& g, int a, int b, int v0, int v1, int warp,
+                                                      int lane, int32_t* dcounts_k, const DeltaTerms& dt) {
+  return delta_lookup_vectors_strided(g, a, b, v0 + warp, v1, kDeltaWarps, lane, dcounts_k, dt);
+}
+
+// One warp over all vectors v0 <= v < v1 (in order); lane 0 returns.
+__device__ __forceinline__ float delta_lookup_vectors_warp(const DeltaArgs& g, int a, int b, int v0, int v1,
+                                                           int lane, int32_t* dcounts_k, const DeltaTerms& dt) {
+  return delta_lookup_vectors_strided(g, a, b, v0, v1, 1, lane, dcounts_k, dt);
+}
+
+// Vectors v = v0, v0 + vstep, ... < v1.
+__device__ __forceinline__ float delta_lookup_vectors_strided(const DeltaArgs& g, int a, int b, int v0, int v1,
+                                                              int vstep, int lane, int32_t* dcounts_k,
+                                                              const DeltaTerms& dt) {
+  float acc = 0.0f;
+  const float invN = g.inv_norm;
+  const int W = g.W, H = g.H;
+  const int ay = a / W, ax = a - ay * W, by = b / W, bx = b - by * W;
+  const int64_t hw = (int64_t)H * W;
+  for (int v = v0; v < v1; v += vstep) {
+    const int o0 = __ldg(g.dptr + v);
+    const int L1 = __ldg(g.dptr + v + 1) - o0;
+    int dx, dy;
+    delta_vector(g, v, dx, dy);
+    const uint8_t* zv = g.z + (int64_t)v * hw;
+    int d0 = 0, d1 = 0;
+    // four lookups per lane in flight: offsets, then counts, then the tests
+    for (int t0 = 0; t0 < 2 * L1; t0 += 128) {
+      int xs[4], ys[4], zs[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + 32 * u + lane;
+        const int side = t >= L1;
+        const int i = t < 2 * L1 ? (side ? t - L1 : t) : 0;
+        const short2 s2 = reinterpret_cast<const short2*>(g.off16)[o0 + i];
+        int x = (side ? bx : ax) - s2.x, y = (side ? by : ay) - s2.y;
+        xs[u] = x < 0 ? x + W : (x >= W ? x - W : x);
+        ys[u] = y < 0 ? y + H : (y >= H ? y - H : y);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)  // read at L2 (the annealer updates z with atomics, which bypass L1)
+        zs[u] = t0 + 32 * u + lane < 2 * L1 ? __ldcg(zv + (int64_t)ys[u] * W + xs[u]) : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + 32 * u + lane;
+        if (t >= 2 * L1) continue;
+        const int x = xs[u], y = ys[u], z = zs[u];
+        if (g.sel_ext && !g.sel_ext[(y + g.ry) * g.We + (x + g.rx)]) continue;  // start not sampled
+        if (t < L1) {
+          if (z == 0) d1 -= 1;
+          if (z == L1 - 1 && !delta_on_segment(g, o0, dx, dy, x, y, bx, by)) d0 += 1;
+        } else {
+          if (z == L1) d0 -= 1;
+          if (z == 1 && !delta_on_segment(g, o0, dx, dy, x, y, ax, ay)) d1 += 1;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+      d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+    }
+    if (lane == 0) {
+      if (dcounts_k) {
+        dcounts_k[v] = d0;
+        dcounts_k[g.n_canon + v] = d1;
+      }
+      if (g.target && (d0 | d1)) {
+        const int iv = v - dt.vbase;
+        if (d0 && (g.phase_mask & 1)) {
+          const float dd = dt.t[0][iv] - (float)dt.c[0][iv] * invN;
+          const float x = (float)d0 * invN;
+          acc += x * (x - 2.0f * dd);
+        }
+        if (d1 && (g.phase_mask & 2)) {
+          const float dd = dt.t[1][iv] - (float)dt.c[1][iv] * invN;
+          const float x = (float)d1 * invN;
+          acc += x * (x - 2.0f * dd);
+        }
+      }
+    }
+  }
+  return acc;
+}
+
+// After exchanging a (now phase 0) and b (now phase 1): z_v += 1 on the
+// translations through a and -= 1 on those through b, for the warp's
+// vectors of [v0, v1).  A translation through both gets both, which nets 0;
+// the byte never wraps in between (it counts b, so it is >= 1 before the
+// decrement, and < L1 before the increment), so the two updates may land
+// in either order: one 32-bit atomic add per byte.
+__device__ __forceinline__ void delta_lookup_update(const DeltaArgs& g, int a, int b, int v0, int v1, int warp,
+                                                   int lane) {
+  const int W = g.W, H = g.H;
+  const int ay = a / W, ax = a - ay * W, by = b / W, bx = b - by * W;
+  const int64_t hw = (int64_t)H * W;
+  for (int v = v0 + warp; v < v1; v += kDeltaWarps) {
+    const int o0 = __ldg(g.dptr + v);
+    const int L1 = __ldg(g.dptr + v + 1) - o0;
+    uint8_t* zv = g.z + (int64_t)v * hw;
+    for (int t = lane; t < 2 * L1; t += 32) {
+      const int side = t >= L1;
+      const int i = side ? t - L1 : t;
+      int x = (side ? bx : ax) - g.off16[2 * (o0 + i)], y = (side ? by : ay) - g.off16[2 * (o0 + i) + 1];
+      x = x < 0 ? x + W : (x >= W ? x - W : x);
+      y = y < 0 ? y + H : (y >= H ? y - H : y);
+      const int64_t e = (int64_t)y * W + x;
+      uint8_t* byte = zv + e;
+      unsigned int* word = reinterpret_cast<unsigned int*>(reinterpret_cast<uintptr_t>(byte) & ~uintptr_t(3));
+      const unsigned int sh = 8u * (unsigned)(reinterpret_cast<uintptr_t>(byte) & 3);
+      atomicAdd(word, side ? (0u - (1u << sh)) : (1u << sh));
+    }
+  }
 }
 
 // Write zero changes for vectors v0 <= v < v1 (identity candidates).

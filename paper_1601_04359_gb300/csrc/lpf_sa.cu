@@ -316,6 +316,7 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
       int32_t* dk = dcounts + (int64_t)k * 2 * g.n_canon;
       float acc = 0.0f;
       if (a == b) delta_zero_vectors(g, v0, v1, dk);
+      else if (g.z) acc = delta_lookup_vectors(g, a, b, v0, v1, warp, lane, dk, dt);
       else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk, dt);
       if (lane == 0) warp_acc[warp] = acc;
       __syncthreads();
@@ -354,6 +355,8 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
             if (v > 0) counts[p * g.n_full + (g.n_full - 1 - (g.base + v))] = (unsigned long long)c;
           }
         }
+        // this block's vectors: the phase-0 counts follow the exchange
+        if (g.z) delta_lookup_update(g, a, b, v0, v1, warp, lane);
         if (threadIdx.x == 0) {
           delta_mark(sm, a, 0, g);
           delta_mark(sm, b, 1, g);
@@ -484,6 +487,7 @@ int sa_recover(lpf_sa* sa, cudaStream_t s) {
   else if (sa->d_sel) rc = lpf_full_mc(sa->cell, sa->H, sa->W, sa->paths, sa->d_sel, sa->counts, s);
   else rc = lpf_full(sa->cell, sa->H, sa->W, sa->paths, sa->counts, s);
   if (rc) return rc;
+  if (sa->d_z) z_init_launch(sa->d_ext, sa->g, sa->d_z, sa->d_status, s);  // the counts per translation too
   sa_enqueue_error(sa, s);
   sa_set_error_kernel<<<1, 1, 0, s>>>(sa->d_st, sa->d_e);
   cudaError_t e = cudaMemsetAsync(sa->d_status, 0, sizeof(int), s);
@@ -524,6 +528,17 @@ int sa_start(lpf_sa* sa, cudaStream_t s) {
   {
     const int blocks = (int)std::min<int64_t>((sa->g.ext_bytes + 255) / 256, 4096);
     build_ext_sa_kernel<<<blocks, 256, 0, s>>>(sa->cell, sa->g, sa->d_ext);
+  }
+  if (sa->objective == kSaObjectiveLineal && sa->persistent) {
+    // count changes by lookups of the run's own phase-0 counts, kept current
+    // by the persistent kernel after every accepted exchange
+    const size_t zb = delta_z_bytes(sa->paths, sa->H, sa->W);
+    if (zb > 0) {
+      e = cudaMalloc(&sa->d_z, zb);
+      if (e != cudaSuccess) return set_cuda_error(e);
+      sa->g.z = sa->d_z;
+      z_init_launch(sa->d_ext, sa->g, sa->d_z, sa->d_status, s);
+    }
   }
   sa_enqueue_error(sa, s);  // initial error from the exact counts
   double e0 = 0.0;
@@ -902,6 +917,7 @@ void lpf_sa_free(lpf_sa* sa) {
   cudaFree(sa->d_e);
   cudaFree(sa->d_status);
   cudaFree(sa->d_sel);
+  cudaFree(sa->d_z);
   cudaFree(sa->d_cdf);
   cudaFree(sa->d_bar);
   cudaFree(sa->d_sel_ext);

@@ -313,6 +313,7 @@ struct lpf_sa {
   unsigned int* d_bar = nullptr;  // its grid-barrier counter
   uint8_t* d_sel_ext = nullptr; // Monte-Carlo runs: sampled translations, extended layout
   uint8_t* d_sel = nullptr;     // Monte-Carlo runs: the run's copy of the selection, H*W
+  uint8_t* d_z = nullptr;       // phase-0 counts per (vector, translation), kept current by the run
   double inv_norm = 0.0;        // descriptor = count * inv_norm
 };
 

@@ -63,6 +63,7 @@ struct DeltaTables {
   int32_t* d_dptr = nullptr;   // CSR pointers [n_canon + 1]
   int32_t* d_chunk = nullptr;  // vector chunk bounds [n_chunks + 1]
   int n_chunks = 0;
+  int16_t* d_off16 = nullptr;  // per segment pixel: (sx, sy)
 };
 
 }  // namespace lpf
@@ -86,6 +87,8 @@ struct lpf_paths {
   uint32_t* d_sel = nullptr;     // work area: packed translation selection (Monte-Carlo variant)
   size_t sel_cap = 0;            // words
   const uint32_t* d_sel_active = nullptr;  // selection of the walk being enqueued (or null)
+  uint8_t* d_z = nullptr;        // work area: phase-0 counts per (vector, translation) of swap deltas
+  size_t z_cap = 0;              // bytes
   int checked = 0;               // 1: kernels that read the image flag pixels other than 0 or 1
   int selftest = 0;              // 1: walks wait for bytes no copy delivers (failure-detection test)
 };
@@ -106,6 +109,12 @@ int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g);
 // Candidate strides per vector chunk for K candidates.
 int delta_stride(int n_chunks, int K);
 int delta_max_smem();
+// Phase-0 counts for swap deltas by lookup: bytes for an H x W cell (0: not
+// used -- too long segments or too much memory), allocation in the handle,
+// and the kernel that fills them from an extended cell.
+size_t delta_z_bytes(const lpf_paths* p, int H, int W);
+int delta_z_prepare(lpf_paths* p, int H, int W);
+void z_init_launch(const uint8_t* ext, const DeltaArgs& g, uint8_t* z, int* status, cudaStream_t s);
 // The annealing batch kernel of the lineal-path objective (lpf_sa.cu), for
 // attribute and occupancy queries.
 const void* sa_batch_kernel_entry();
