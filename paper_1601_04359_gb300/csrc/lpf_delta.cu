@@ -193,9 +193,9 @@ static int bake_delta(lpf_paths* p, int W, int want_chunks, DeltaTables& t) {
   if (t.d_doff && t.We == We && t.want == want_chunks) return LPF_OK;
   if (t.d_doff) {
     cudaDeviceSynchronize();
-    cudaFree(t.d_doff); cudaFree(t.d_dptr); cudaFree(t.d_chunk); cudaFree(t.d_off16);
+    cudaFree(t.d_doff); cudaFree(t.d_dptr); cudaFree(t.d_chunk); cudaFree(t.d_off16); cudaFree(t.d_vec16);
     t.d_doff = t.d_dptr = t.d_chunk = nullptr;
-    t.d_off16 = nullptr;
+    t.d_off16 = t.d_vec16 = nullptr;
   }
   const Paths& h = p->host;
   std::vector<int32_t> off(h.ptr.back()), ptr(h.n_canon + 1);
@@ -233,6 +233,9 @@ static int bake_delta(lpf_paths* p, int W, int want_chunks, DeltaTables& t) {
   if ((e = cudaMalloc(&t.d_off16, std::max<size_t>(1, h.off.size()) * 2)) != cudaSuccess) return set_cuda_error(e);
   if ((e = cudaMemcpy(t.d_off16, h.off.data(), h.off.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
     return set_cuda_error(e);
+  if ((e = cudaMalloc(&t.d_vec16, std::max<size_t>(1, h.vec.size()) * 2)) != cudaSuccess) return set_cuda_error(e);
+  if ((e = cudaMemcpy(t.d_vec16, h.vec.data(), h.vec.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return set_cuda_error(e);
   t.We = We;
   t.want = want_chunks;
   t.n_chunks = (int)chunk.size() - 1;
@@ -266,6 +269,7 @@ int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g) {
   g.sel_ext = nullptr;
   g.z = nullptr;
   g.off16 = p->delta.d_off16;
+  g.vec16 = p->delta.d_vec16;
   g.inv_norm = 1.0f / ((float)H * (float)W);
   return LPF_OK;
 }

@@ -38,6 +38,7 @@ struct DeltaArgs {
   // (sx, sy) as int16 pairs, CSR by dptr.
   uint8_t* z;
   const int16_t* off16;
+  const int16_t* vec16;         // canonical vectors (dx, dy) as int16 pairs
 };
 
 // Where a walk finds the target and the current count of vector v for the
@@ -195,11 +196,11 @@ __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const Del
 // Sec. 2.2 restricted to the translations the exchange touches), read from
 // one byte per translation instead of walking the segment.
 
-// Canonical vector of canonical index v (window rx, ry).
+// Canonical vector of canonical index v.
 __device__ __forceinline__ void delta_vector(const DeltaArgs& g, int v, int& dx, int& dy) {
-  const int64_t k = g.base + v;
-  dy = (int)(k / (2 * g.rx + 1)) - g.ry;
-  dx = (int)(k % (2 * g.rx + 1)) - g.rx;
+  const short2 d = __ldg(reinterpret_cast<const short2*>(g.vec16) + v);
+  dx = d.x;
+  dy = d.y;
 }
 
 // True when pixel (qx, qy) lies on S(v) placed at translation (x, y), on the
@@ -288,11 +289,12 @@ __device__ __forceinline__ float delta_lookup_vectors_strided(const DeltaArgs& g
         }
       }
     }
+    // one reduction for both phases: |d0|, |d1| <= 2 L1 < 2^15 per vector
+    int dp = d0 + d1 * 65536;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      d0 += __shfl_xor_sync(0xffffffffu, d0, o);
-      d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-    }
+    for (int o = 16; o > 0; o >>= 1) dp += __shfl_xor_sync(0xffffffffu, dp, o);
+    d0 = (int)(short)(dp & 0xffff);
+    d1 = (dp - d0) / 65536;
     if (lane == 0) {
       if (dcounts_k) {
         dcounts_k[v] = d0;

@@ -64,6 +64,7 @@ struct DeltaTables {
   int32_t* d_chunk = nullptr;  // vector chunk bounds [n_chunks + 1]
   int n_chunks = 0;
   int16_t* d_off16 = nullptr;  // per segment pixel: (sx, sy)
+  int16_t* d_vec16 = nullptr;  // per canonical vector: (dx, dy)
 };
 
 }  // namespace lpf
