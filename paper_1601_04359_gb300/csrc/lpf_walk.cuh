@@ -171,28 +171,39 @@ __device__ __forceinline__ uint32_t walk_unit(const uint4* __restrict__ prog, ui
     walked += n;
     bool dead = false;
     const uint4* g = prog + rec + 1u;
-    for (uint32_t q = 0; q < n_pg; ++q) {
-      walk_pairs2<T>(lane_base, __ldg(g + q), m1, m0);
-      if ((q & 1u) && skip != 0u && warp_empty<T>(m1, m0)) {
+    // two groups (8 pixels) per iteration: both program loads issued
+    // together, one vote after them
+    uint32_t q = 0;
+    for (; q + 2u <= n_pg; q += 2u) {
+      const uint4 P0 = __ldg(g + q), P1 = __ldg(g + q + 1u);
+      walk_pairs2<T>(lane_base, P0, m1, m0);
+      walk_pairs2<T>(lane_base, P1, m1, m0);
+      if (skip != 0u && warp_empty<T>(m1, m0)) {
         dead = true;
-        walked -= n - 4u * (q + 1u);  // pixels not walked (pair groups hold four pixels of the record)
+        walked -= n - 4u * (q + 2u);  // pixels not walked (pair groups hold four pixels of the record)
         break;
       }
     }
+    if (!dead && q < n_pg) walk_pairs2<T>(lane_base, __ldg(g + q), m1, m0);
     if (!dead) {
       g += n_pg;
-      for (uint32_t q = 0; q < n_sg; ++q) {
-        walk_singles4<T>(lane_base, __ldg(g + q), m1, m0);
-        if ((q & 1u) && skip != 0u && warp_empty<T>(m1, m0)) {
+      for (q = 0; q + 2u <= n_sg; q += 2u) {
+        const uint4 P0 = __ldg(g + q), P1 = __ldg(g + q + 1u);
+        walk_singles4<T>(lane_base, P0, m1, m0);
+        walk_singles4<T>(lane_base, P1, m1, m0);
+        if (skip != 0u && warp_empty<T>(m1, m0)) {
           dead = true;
-          const uint32_t done = 4u * (n_pg + q + 1u);
+          const uint32_t done = 4u * (n_pg + q + 2u);
           walked -= n > done ? n - done : 0u;
           break;
         }
       }
-      if (!dead && half) {
-        const uint4 P = __ldg(g + n_sg);
-        walk_singles2<T>(lane_base, P.x, P.y, m1, m0);
+      if (!dead) {
+        if (q < n_sg) walk_singles4<T>(lane_base, __ldg(g + q), m1, m0);
+        if (half) {
+          const uint4 P = __ldg(g + n_sg);
+          walk_singles2<T>(lane_base, P.x, P.y, m1, m0);
+        }
       }
     }
     if (dead) {
