@@ -122,9 +122,15 @@ __global__ void __launch_bounds__(kDeltaThreads) z_init_kernel(const uint8_t* __
   const int hw = g.H * g.W;
   for (int v = blockIdx.x; v < (int)g.n_canon; v += gridDim.x) {
     const int o0 = __ldg(g.dptr + v), L1 = __ldg(g.dptr + v + 1) - o0;
+    int dx, dy;
+    delta_vector(g, v, dx, dy);
+    const bool ymajor = dy > (dx < 0 ? -dx : dx);
     uint8_t* zv = z + (int64_t)v * hw;
     for (int p = threadIdx.x; p < hw; p += blockDim.x) {
-      const int y = p / g.W, x = p - y * g.W;
+      // p runs over the vector's layout (column-major for y-major vectors)
+      int x, y;
+      if (ymajor) { x = p / g.H; y = p - x * g.H; }
+      else        { y = p / g.W; x = p - y * g.W; }
       const uint8_t* base = sm + (y + g.ry) * g.We + (x + g.rx);
       int c = 0;
       for (int k = 0; k < L1; ++k) c += base[__ldg(g.doff + o0 + k)] == 0;

@@ -196,6 +196,13 @@ __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const Del
 // Sec. 2.2 restricted to the translations the exchange touches), read from
 // one byte per translation instead of walking the segment.
 
+// Index of translation (x, y) in z_v: row-major for x-major vectors,
+// column-major for y-major ones (dy > |dx|), so that the translations
+// through one pixel along the segment are mostly consecutive bytes.
+__device__ __forceinline__ int delta_z_index(const DeltaArgs& g, int dx, int dy, int x, int y) {
+  return dy > (dx < 0 ? -dx : dx) ? x * g.H + y : y * g.W + x;
+}
+
 // Canonical vector of canonical index v.
 __device__ __forceinline__ void delta_vector(const DeltaArgs& g, int v, int& dx, int& dy) {
   const short2 d = __ldg(reinterpret_cast<const short2*>(g.vec16) + v);
@@ -208,12 +215,13 @@ __device__ __forceinline__ void delta_vector(const DeltaArgs& g, int v, int& dx,
 // period of (qx, qy) is in its bounding box).
 __device__ __forceinline__ bool delta_on_segment(const DeltaArgs& g, int o0, int dx, int dy, int x, int y, int qx,
                                                  int qy) {
-  int uy = (qy - y) % g.H;
+  int uy = qy - y;                          // in (-H, H)
   if (uy < 0) uy += g.H;
   if (uy > dy) return false;                // canonical: 0 <= sy <= dy
   const int xlo = dx < 0 ? dx : 0, xhi = dx < 0 ? 0 : dx;
-  int ux = (qx - x - xlo) % g.W;
+  int ux = qx - x - xlo;                    // in (-W, W + rx), rx < W
   if (ux < 0) ux += g.W;
+  else if (ux >= g.W) ux -= g.W;
   ux += xlo;
   if (ux > xhi) return false;
   const int adx = dx < 0 ? -dx : dx;
@@ -273,7 +281,7 @@ __device__ __forceinline__ float delta_lookup_vectors_strided(const DeltaArgs& g
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)  // read at L2 (the annealer updates z with atomics, which bypass L1)
-        zs[u] = t0 + 32 * u + lane < 2 * L1 ? __ldcg(zv + (int64_t)ys[u] * W + xs[u]) : -1;
+        zs[u] = t0 + 32 * u + lane < 2 * L1 ? __ldcg(zv + delta_z_index(g, dx, dy, xs[u], ys[u])) : -1;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int t = t0 + 32 * u + lane;
@@ -332,6 +340,8 @@ __device__ __forceinline__ void delta_lookup_update(const DeltaArgs& g, int a, i
   for (int v = v0 + warp; v < v1; v += kDeltaWarps) {
     const int o0 = __ldg(g.dptr + v);
     const int L1 = __ldg(g.dptr + v + 1) - o0;
+    int dx, dy;
+    delta_vector(g, v, dx, dy);
     uint8_t* zv = g.z + (int64_t)v * hw;
     for (int t = lane; t < 2 * L1; t += 32) {
       const int side = t >= L1;
@@ -339,8 +349,7 @@ __device__ __forceinline__ void delta_lookup_update(const DeltaArgs& g, int a, i
       int x = (side ? bx : ax) - g.off16[2 * (o0 + i)], y = (side ? by : ay) - g.off16[2 * (o0 + i) + 1];
       x = x < 0 ? x + W : (x >= W ? x - W : x);
       y = y < 0 ? y + H : (y >= H ? y - H : y);
-      const int64_t e = (int64_t)y * W + x;
-      uint8_t* byte = zv + e;
+      uint8_t* byte = zv + delta_z_index(g, dx, dy, x, y);
       unsigned int* word = reinterpret_cast<unsigned int*>(reinterpret_cast<uintptr_t>(byte) & ~uintptr_t(3));
       const unsigned int sh = 8u * (unsigned)(reinterpret_cast<uintptr_t>(byte) & 3);
       atomicAdd(word, side ? (0u - (1u << sh)) : (1u << sh));
