@@ -429,7 +429,24 @@ def _only_batch_256(lpf, repeat, shape):
     assert lpf.lpf_batch_status(b) == 0
 
 
+def _only_cnn_train(lpf, repeat, shape):
+    import numpy as np
+    import torch
+
+    import synth
+    H = W = 128
+    net = lpf.lpf_cnn_create(H, W, 3)
+    cells = np.stack([synth.clustered_disks(H, W, 0.3, seed=10 + i) for i in range(8)])
+    pairs = np.stack([synth.swap_candidates(c, 64, seed=i) for i, c in enumerate(cells)])
+    y = np.random.default_rng(0).normal(size=(8, 64)).astype(np.float32)
+    c, p, t = (torch.from_numpy(v).cuda() for v in (cells, pairs, y))
+    for _ in range(1 + repeat):
+        lpf.lpf_cnn_train_step(net, c, p, t, 1e-3)
+    torch.cuda.synchronize()
+
+
 PROFILE_WORKLOADS = {
+    "cnn_train": _only_cnn_train,
     "lpf_full_512": _only_lpf_full_512,
     "lpf_full_512_standard": lambda lpf, r, s: _only_lpf_full_512(lpf, r, s, standard=True),
     "delta_128": _only_delta_128,
