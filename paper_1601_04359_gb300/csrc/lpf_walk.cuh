@@ -222,7 +222,7 @@ __device__ __forceinline__ uint32_t walk_unit(const uint4* __restrict__ prog, ui
         uint32_t c = 0;
 #pragma unroll
         for (int t = 0; t < T; ++t) c += (uint32_t)__popc(m1[t]) + ((uint32_t)__popc(m0[t]) << 16);
-        c = warp_sum(c);
+        c = __reduce_add_sync(0xffffffffu, c);  // one warp-reduce instruction
         if (lane == 0) {
           const uint32_t c1 = c & 0xffffu, c0 = c >> 16;
           if (c0) atomicAdd(counts + base + vec, (unsigned long long)c0);
