@@ -75,7 +75,12 @@ const char *lpf_last_error_message(void);
  * Build the discretised segments of every vector of the window |dx| <= rx,
  * |dy| <= ry (Sec. 2.2 segments; Sec. 3.1 step 1, done once) and the
  * evaluation program that shares the work of common segment prefixes (the
- * enhanced evaluation of Sec. 3.2, generalised to all shared prefixes).
+ * enhanced evaluation of Sec. 3.2, generalised to all shared prefixes).  The
+ * program has two prefix trees: the segments of the x-major vectors
+ * (|dx| >= |dy|), walked over the image, and those of the y-major vectors,
+ * transposed, walked over the transposed image, so that every segment
+ * advances one pixel along a packed row per step (the count of a vector is
+ * the same over the transposed image for the transposed segment).
  * Host-only; touches no GPU.  rx, ry in [0, 4095].  *out receives a handle
  * to release with lpf_paths_free().  Device tables are uploaded lazily by the
  * first device call that uses the handle (see lpf_full).

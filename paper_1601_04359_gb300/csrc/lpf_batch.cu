@@ -34,6 +34,10 @@ constexpr int kBatchThreads = 32 * kBatchWarps;
 
 constexpr int kBatchCtlUnits = 4;  // control words: [0] status, [kBatchCtlUnits + g] unit counter of band group g
 
+// One side of one image (the image with the x-major vectors' program, or
+// its transpose with the y-major vectors' program; both add to the image's
+// counts).  H, W are the side's: the transpose's pixel (r, c) is the image's
+// (c, r).
 struct BatchDesc {
   const uint8_t* img;
   unsigned long long* counts;
@@ -42,6 +46,9 @@ struct BatchDesc {
   const uint32_t* piece;    // piece starts in groups
   int64_t n_full, base;
   int H, W, S, nw, G, BB, T, r32, rows, nbg, n_pieces, bg0;
+  int rs, cs;               // the side's pixel (r, c) is img[r rs + c cs]
+  int up;                   // packed row y holds the side's row (y - up) mod H
+  int primary;              // 1: side 0 (zeroes and mirrors the image's counts)
   uint32_t band_bytes;
 };
 
@@ -51,30 +58,37 @@ struct BatchSlot {
 
 __global__ void batch_zero_kernel(const BatchDesc* __restrict__ d) {
   const BatchDesc& b = d[blockIdx.y];
+  if (!b.primary) return;
   const int64_t n = 2 * b.n_full;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b.counts[i] = 0ull;
 }
 
+// Packed rows of every side: bit b of word k of row y is the side's pixel at
+// row (y - up) mod H, column (32k + b - r32) mod W.  A transposed side runs over its
+// words column by column, so that a warp reads consecutive image bytes.
 __global__ void batch_pack_kernel(const BatchDesc* __restrict__ d) {
   const BatchDesc& b = d[blockIdx.y];
   const int64_t total = (int64_t)b.rows * b.S;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int y = (int)(i / b.S), k = (int)(i % b.S);
-    const uint8_t* row = b.img + (int64_t)(y % b.H) * b.W;
+    int y, k;
+    if (b.primary) { y = (int)(i / b.S); k = (int)(i % b.S); }
+    else { k = (int)(i / b.rows); y = (int)(i % b.rows); }
+    const uint8_t* row = b.img + (int64_t)((y + b.H - b.up % b.H) % b.H) * b.rs;
     int x = (32 * k - b.r32) % b.W;
     if (x < 0) x += b.W;
     uint32_t bits = 0;
     for (int bit = 0; bit < 32; ++bit) {
-      bits |= (uint32_t)(row[x] != 0) << bit;
+      bits |= (uint32_t)(row[(int64_t)x * b.cs] != 0) << bit;
       if (++x == b.W) x = 0;
     }
-    b.packed[i] = bits;
+    b.packed[(int64_t)y * b.S + k] = bits;
   }
 }
 
 __global__ void batch_mirror_kernel(const BatchDesc* __restrict__ d) {
   const BatchDesc& b = d[blockIdx.y];
+  if (!b.primary) return;
   const int64_t n = b.n_full - b.base - 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = i / n, j = b.base + 1 + i % n;
@@ -171,7 +185,8 @@ static double shape_cost(int H, int W, int T) {
 struct lpf_batch {
   int n = 0;
   std::vector<lpf_paths*> paths;
-  std::vector<lpf::BatchDesc> desc;
+  std::vector<lpf::BatchDesc> desc;  // per side of every image
+  std::vector<int> img_desc;         // an image's first descriptor (its side 0)
   lpf::BatchDesc* d_desc = nullptr;
   uint32_t* d_packed = nullptr;
   int* d_ctl = nullptr;          // [0] status, [kBatchCtlUnits + g] unit counter of band group g
@@ -182,7 +197,9 @@ struct lpf_batch {
   // evaluating a handle on its own afterwards (another launch shape) re-bakes
   // the handle's program and must not move the batch's.
   std::vector<const lpf_paths*> baked_for;
+  std::vector<int> baked_side;   // 0: the image's program, 1: the transpose's
   std::vector<lpf::Baked> baked;
+  int desc_cap = 0;
   uint32_t max_band = 0;
   int blocks = 0;
   int max_pack = 0, max_full = 0;
@@ -192,74 +209,104 @@ struct lpf_batch {
 
 namespace lpf {
 
+// The words per thread of a side from the cost model (0: none admissible).
+static int best_T(int H, int W) {
+  double best = 1e30;
+  int T = 0;
+  for (int t : {1, 2, 4, 8}) {
+    const double c = shape_cost(H, W, t);
+    if (c < best) { best = c; T = t; }
+  }
+  return T;
+}
+
+static bool admissible(int W, int T) {
+  const int G = ((W + 31) / 32 + T - 1) / T;
+  return G <= kBatchWarps && kBatchWarps % G == 0;
+}
+
 static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t* H, const int32_t* W,
                        int64_t* const* counts, const int32_t* T_choice) {
-  // geometry, programs on the device, work-area layout
+  // geometry, programs on the device, work-area layout; one descriptor per
+  // side of every image
   size_t packed_total = 0;
-  std::vector<size_t> offs(bt->n);
-  bt->desc.assign(bt->n, BatchDesc{});
+  std::vector<size_t> offs;
+  bt->desc.clear();
+  bt->img_desc.assign(bt->n, 0);
   std::vector<char> used(bt->baked.size(), 0);
   int total_bg = 0;
-  std::vector<double> bg_work(bt->n);  // nominal work of one band group of each image
+  std::vector<double> bg_work;  // nominal work of one band group of each side
   bt->max_band = 0;
+  bt->max_pack = bt->max_full = 0;
   for (int i = 0; i < bt->n; ++i) {
     lpf_paths* p = bt->paths[i];
     if (!p || !imgs[i] || !counts[i]) return LPF_EINVAL;
     if (H[i] < 1 || W[i] < 1 || H[i] > 8192 || W[i] > 8192) return LPF_EINVAL;
     if (p->host.rx >= W[i] || p->host.ry >= H[i]) return LPF_EINVAL;
-    if (p->host.tree.stack_depth > kWalkStack) return LPF_EUNSUPPORTED;
-    int T = T_choice ? T_choice[i] : 0;
-    if (T <= 0) {
-      double best = 1e30;
-      for (int t : {1, 2, 4, 8}) {
-        const double c = shape_cost(H[i], W[i], t);
-        if (c < best) { best = c; T = t; }
+    if (std::max(p->host.tree.stack_depth, p->host.tree_t.stack_depth) > kWalkStack) return LPF_EUNSUPPORTED;
+    int rc = ensure_device(p, 0);
+    if (rc) return rc;
+    const int n_sides = p->host.root_t >= 0 ? 2 : 1;
+    bt->img_desc[i] = (int)bt->desc.size();
+    for (int side = 0; side < n_sides; ++side) {
+      // side 1: the transposed image with the y-major vectors' program
+      const int Hs = side ? W[i] : H[i], Ws = side ? H[i] : W[i];
+      const int rxs = side ? p->host.ry : p->host.rx;
+      // row offsets: side 0 0 .. min(rx, ry); side 1 -h .. h, h = min(rx, ry - 1)
+      const int rys = side ? std::min(p->host.rx, p->host.ry - 1) : std::min(p->host.rx, p->host.ry);
+      const int up = side ? rys : 0;
+      int T = T_choice ? T_choice[i] : 0;
+      if (T <= 0 || (side && !admissible(Ws, T))) T = best_T(Hs, Ws);
+      if (T <= 0 || !admissible(Ws, T)) return LPF_EUNSUPPORTED;
+      const int G = ((Ws + 31) / 32 + T - 1) / T;
+      Geometry g;
+      // keep G*BB = 8 even if the side has fewer bands (the extra warps idle)
+      rc = layout_side(Hs, Ws, rxs, rys, T, kBatchWarps / G, g, up);
+      if (rc) return rc;
+      g.BB = kBatchWarps / G;
+      g.nbg = (g.nbands + g.BB - 1) / g.BB;
+      g.rows = 32 * g.BB * g.nbg + g.ry + up;
+      const size_t band = (size_t)(32 * g.BB + g.ry + up) * g.S * 4;
+      g.band_bytes = (uint32_t)((band + 15) & ~size_t(15));
+      g.packed_words = (size_t)g.rows * g.S + 4;
+      size_t k = 0;  // this handle's copy of this side's program for this row stride, else a new slot
+      while (k < bt->baked.size() &&
+             !(bt->baked_for[k] == p && bt->baked_side[k] == side && bt->baked[k].S == g.S)) ++k;
+      if (k == bt->baked.size()) {
+        bt->baked_for.push_back(p);
+        bt->baked_side.push_back(side);
+        bt->baked.emplace_back();
+        used.push_back(0);
       }
+      used[k] = 1;
+      const Program& prog = side ? p->host.tree_t : p->host.tree;
+      rc = bake(p, prog, g, nullptr, nullptr, bt->baked[k]);
+      if (rc) return rc;
+      BatchDesc d{};
+      d.img = imgs[i];
+      d.counts = reinterpret_cast<unsigned long long*>(counts[i]);
+      d.prog = reinterpret_cast<const uint4*>(bt->baked[k].d_words);
+      d.piece = bt->baked[k].d_piece;
+      d.n_full = p->host.n_full;
+      d.base = p->host.base;
+      d.bg0 = total_bg;
+      d.H = g.H; d.W = g.W; d.S = g.S; d.nw = g.nw; d.G = g.G; d.BB = g.BB; d.T = g.T; d.r32 = g.r32;
+      d.rows = g.rows; d.nbg = g.nbg; d.n_pieces = bt->baked[k].n_pieces; d.band_bytes = g.band_bytes;
+      d.up = up;
+      d.rs = side ? 1 : W[i];
+      d.cs = side ? W[i] : 1;
+      d.primary = side == 0;
+      bt->desc.push_back(d);
+      total_bg += g.nbg;
+      bg_work.push_back((double)prog.n_pixel_words * g.G * g.BB * (g.T + 1));
+      offs.push_back(packed_total);
+      packed_total += (g.packed_words + 3) & ~size_t(3);  // keep every side 16-byte aligned
+      bt->max_band = std::max(bt->max_band, g.band_bytes);
+      bt->max_pack = std::max<int>(bt->max_pack, (int)std::min<int64_t>(((int64_t)g.rows * g.S + 255) / 256, 64));
+      bt->max_full = std::max<int>(bt->max_full, (int)std::min<int64_t>((2 * d.n_full + 255) / 256, 64));
     }
-    const int nw = (W[i] + 31) / 32;
-    const int G = (nw + T - 1) / T;
-    if (G > kBatchWarps || kBatchWarps % G) return LPF_EUNSUPPORTED;
-    Geometry g;
-    int rc = make_geometry(H[i], W[i], p->host.rx, p->host.ry, T, kBatchWarps / G, g);
-    if (rc) return rc;
-    if (g.T != T || g.G != G) return LPF_EUNSUPPORTED;
-    // keep G*BB = 8 even if the image has fewer bands (the extra warps idle)
-    g.BB = kBatchWarps / G;
-    g.nbg = (g.nbands + g.BB - 1) / g.BB;
-    g.rows = 32 * g.BB * g.nbg + g.ry;
-    const size_t band = (size_t)(32 * g.BB + g.ry) * g.S * 4;
-    g.band_bytes = (uint32_t)((band + 15) & ~size_t(15));
-    g.packed_words = (size_t)g.rows * g.S + 4;
-    rc = ensure_device(p, 0);
-    if (rc) return rc;
-    size_t k = 0;  // this handle's copy for this row stride, else a new slot
-    while (k < bt->baked.size() && !(bt->baked_for[k] == p && bt->baked[k].S == g.S)) ++k;
-    if (k == bt->baked.size()) {
-      bt->baked_for.push_back(p);
-      bt->baked.emplace_back();
-      used.push_back(0);
-    }
-    used[k] = 1;
-    rc = bake(p, p->host.tree, g, bt->baked[k]);
-    if (rc) return rc;
-    BatchDesc& d = bt->desc[i];
-    d.img = imgs[i];
-    d.counts = reinterpret_cast<unsigned long long*>(counts[i]);
-    d.prog = reinterpret_cast<const uint4*>(bt->baked[k].d_words);
-    d.piece = bt->baked[k].d_piece;
-    d.n_full = p->host.n_full;
-    d.base = p->host.base;
-    d.bg0 = total_bg;
-    d.H = g.H; d.W = g.W; d.S = g.S; d.nw = g.nw; d.G = g.G; d.BB = g.BB; d.T = g.T; d.r32 = g.r32;
-    d.rows = g.rows; d.nbg = g.nbg; d.n_pieces = bt->baked[k].n_pieces; d.band_bytes = g.band_bytes;
-    total_bg += g.nbg;
-    bg_work[i] = (double)p->host.tree.n_pixel_words * g.G * g.BB * (g.T + 1);
-    offs[i] = packed_total;
-    packed_total += (g.packed_words + 3) & ~size_t(3);  // keep every image 16-byte aligned
-    bt->max_band = std::max(bt->max_band, g.band_bytes);
-    bt->max_pack = std::max<int>(bt->max_pack, (int)std::min<int64_t>(((int64_t)g.rows * g.S + 255) / 256, 64));
-    bt->max_full = std::max<int>(bt->max_full, (int)std::min<int64_t>((2 * d.n_full + 255) / 256, 64));
   }
+  const int n_desc = (int)bt->desc.size();
   // drop the copies no image of this build uses (earlier launch shapes)
   for (size_t k = bt->baked.size(); k-- > 0;)
     if (!used[k]) {
@@ -268,13 +315,18 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
       cudaFree(bt->baked[k].d_piece);
       bt->baked.erase(bt->baked.begin() + (std::ptrdiff_t)k);
       bt->baked_for.erase(bt->baked_for.begin() + (std::ptrdiff_t)k);
+      bt->baked_side.erase(bt->baked_side.begin() + (std::ptrdiff_t)k);
     }
   cudaError_t e;
   if (bt->d_packed) { cudaFree(bt->d_packed); bt->d_packed = nullptr; }
   if ((e = cudaMalloc(&bt->d_packed, std::max<size_t>(16, packed_total * 4))) != cudaSuccess) return set_cuda_error(e);
-  for (int i = 0; i < bt->n; ++i) bt->desc[i].packed = bt->d_packed + offs[i];
-  if (!bt->d_desc && (e = cudaMalloc(&bt->d_desc, sizeof(BatchDesc) * bt->n)) != cudaSuccess) return set_cuda_error(e);
-  if ((e = cudaMemcpy(bt->d_desc, bt->desc.data(), sizeof(BatchDesc) * bt->n, cudaMemcpyHostToDevice)) != cudaSuccess)
+  for (int i = 0; i < n_desc; ++i) bt->desc[i].packed = bt->d_packed + offs[i];
+  if (n_desc > bt->desc_cap) {
+    if (bt->d_desc) { cudaFree(bt->d_desc); bt->d_desc = nullptr; }
+    if ((e = cudaMalloc(&bt->d_desc, sizeof(BatchDesc) * n_desc)) != cudaSuccess) return set_cuda_error(e);
+    bt->desc_cap = n_desc;
+  }
+  if ((e = cudaMemcpy(bt->d_desc, bt->desc.data(), sizeof(BatchDesc) * n_desc, cudaMemcpyHostToDevice)) != cudaSuccess)
     return set_cuda_error(e);
   bt->ctl_words = kBatchCtlUnits + total_bg;
   if (bt->ctl_words > bt->ctl_cap) {
@@ -301,11 +353,11 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
   // Slots: every band group at least one, more in proportion to its work
   // (about three slots per resident block in all), heaviest band groups first.
   {
-    std::vector<int> order(bt->n);
-    for (int i = 0; i < bt->n; ++i) order[i] = i;
+    std::vector<int> order(n_desc);
+    for (int i = 0; i < n_desc; ++i) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return bg_work[a] > bg_work[b]; });
     double total = 0;
-    for (int i = 0; i < bt->n; ++i) total += bg_work[i] * bt->desc[i].nbg;
+    for (int i = 0; i < n_desc; ++i) total += bg_work[i] * bt->desc[i].nbg;
     const double per_slot = total / (3.0 * resident);
     std::vector<BatchSlot> slots;
     for (int i : order)
@@ -328,10 +380,11 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
 
 static void batch_enqueue(lpf_batch* bt, cudaStream_t s) {
   cudaMemsetAsync(bt->d_ctl, 0, bt->ctl_words * sizeof(int), s);  // status of this run, unit counters
-  batch_zero_kernel<<<dim3(bt->max_full, bt->n), 256, 0, s>>>(bt->d_desc);
-  batch_pack_kernel<<<dim3(bt->max_pack, bt->n), 256, 0, s>>>(bt->d_desc);
+  const int n_desc = (int)bt->desc.size();
+  batch_zero_kernel<<<dim3(bt->max_full, n_desc), 256, 0, s>>>(bt->d_desc);
+  batch_pack_kernel<<<dim3(bt->max_pack, n_desc), 256, 0, s>>>(bt->d_desc);
   batch_walk_kernel<<<bt->blocks, kBatchThreads, bt->max_band, s>>>(bt->d_desc, bt->d_slots, bt->n_slots, bt->d_ctl);
-  batch_mirror_kernel<<<dim3(bt->max_full, bt->n), 256, 0, s>>>(bt->d_desc);
+  batch_mirror_kernel<<<dim3(bt->max_full, n_desc), 256, 0, s>>>(bt->d_desc);
 }
 
 }  // namespace lpf
@@ -402,7 +455,7 @@ int lpf_batch_autotune(lpf_batch* bt, const uint8_t* const* imgs_dev, const int3
   if (!bt || !imgs_dev || !H || !W || !counts_dev) return LPF_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<int32_t> T(bt->n);
-  for (int i = 0; i < bt->n; ++i) T[i] = bt->desc[i].T;
+  for (int i = 0; i < bt->n; ++i) T[i] = bt->desc[bt->img_desc[i]].T;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);

@@ -47,32 +47,63 @@ constexpr int kCtlUnits = 4;
 constexpr int kMaxBandGroups = 8192;  // images: ceil(H / 32) <= 256; volumes: D * ceil(H / (32 BB))
 constexpr int kCtlWords = kCtlUnits + kMaxBandGroups;
 
-int make_geometry(int H, int W, int rx, int ry, int T, int BB, Geometry& g) {
-  g.H = H; g.W = W; g.rx = rx; g.ry = ry;
+int layout_side(int H, int W, int rx, int ry, int T, int BB, Geometry& g, int up) {
+  g.H = H; g.W = W; g.rx = rx; g.ry = ry; g.up = up;
   g.nw = (W + 31) / 32;
-  if (T <= 0) T = g.nw >= 6 ? 8 : (g.nw >= 3 ? 4 : (g.nw >= 2 ? 2 : 1));
-  while ((g.nw + T - 1) / T > 16 && T < 8) T *= 2;  // at most 16 warps per band
   g.T = T;
   g.G = (g.nw + T - 1) / T;
   g.nbands = (H + 31) / 32;
-  if (BB <= 0) BB = std::max(1, std::min(4, 8 / g.G));
-  BB = std::max(1, std::min(BB, g.nbands));
-  while (BB > 1 && g.G * BB > 16) --BB;              // at most 512 threads per block
-  g.BB = BB;
-  g.nbg = (g.nbands + BB - 1) / BB;
+  g.BB = std::max(1, std::min(BB, g.nbands));
+  g.nbg = (g.nbands + g.BB - 1) / g.BB;
   g.r32 = ((rx + 31) / 32) * 32;
   const int nwp = g.G * T;
   g.S = nwp + ((g.r32 + rx) >> 5) + 1;
   if ((g.S & 1) == 0) g.S += 1;
-  g.rows = 32 * BB * g.nbg + ry;
-  const size_t band = (size_t)(32 * BB + ry) * g.S * 4;
+  g.rows = 32 * g.BB * g.nbg + ry + up;
+  const size_t band = (size_t)(32 * g.BB + ry + up) * g.S * 4;
   g.band_bytes = (uint32_t)((band + 15) & ~size_t(15));
   g.packed_words = (size_t)g.rows * g.S + 4;
   g.D = 1;
   g.rz = 0;
   g.slice_rows = 0;
   g.nbg_s = g.nbg;
-  if (g.G > 16 || band > (size_t)kMaxSmem - 64) return LPF_EUNSUPPORTED;
+  if (band > (size_t)kMaxSmem - 64) return LPF_EUNSUPPORTED;
+  return LPF_OK;
+}
+
+int make_geometry(int H, int W, int rx, int ry, int T, int BB, Geometry& g) {
+  const int nw = (W + 31) / 32;
+  if (T <= 0) T = nw >= 6 ? 8 : (nw >= 3 ? 4 : (nw >= 2 ? 2 : 1));
+  while ((nw + T - 1) / T > 16 && T < 8) T *= 2;  // at most 16 warps per band
+  const int G = (nw + T - 1) / T;
+  const int nbands = (H + 31) / 32;
+  if (BB <= 0) BB = std::max(1, std::min(4, 8 / G));
+  BB = std::max(1, std::min(BB, nbands));
+  while (BB > 1 && G * BB > 16) --BB;              // at most 512 threads per block
+  return layout_side(H, W, rx, ry, T, BB, g);
+}
+
+int make_sides(const Paths& paths, int H, int W, int T, int BB, Sides& s) {
+  const int rx = paths.rx, ry = paths.ry;
+  int rc = make_geometry(H, W, rx, std::min(rx, ry), T, BB, s.g[0]);
+  if (rc) return rc;
+  s.n = paths.root_t >= 0 ? 2 : 1;
+  s.off1 = (s.g[0].packed_words + 3) & ~size_t(3);
+  s.packed_words = s.g[0].packed_words;
+  s.band_bytes = s.g[0].band_bytes;
+  s.nbg = s.g[0].nbg;
+  int tiles = s.g[0].G * s.g[0].BB;
+  if (s.n == 2) {
+    const int h = std::min(rx, ry - 1);  // transposed segments: row offsets -h .. h
+    rc = layout_side(W, H, ry, h, s.g[0].T, s.g[0].BB, s.g[1], h);
+    if (rc) return rc;
+    s.packed_words = s.off1 + s.g[1].packed_words;
+    s.band_bytes = std::max(s.band_bytes, s.g[1].band_bytes);
+    s.nbg += s.g[1].nbg;
+    tiles = std::max(tiles, s.g[1].G * s.g[1].BB);
+  }
+  s.threads = 32 * std::min(16, tiles);
+  if (s.nbg > kMaxBandGroups) return LPF_EUNSUPPORTED;
   return LPF_OK;
 }
 
@@ -95,7 +126,7 @@ int make_geometry3(int D, int H, int W, int rx, int ry, int rz, int T, int BB, G
   const size_t band = (size_t)(rz * g.slice_rows + 32 * g.BB + 2 * ry) * g.S * 4;
   g.band_bytes = (uint32_t)((band + 15) & ~size_t(15));
   g.packed_words = (size_t)g.rows * g.S + 4;
-  if (g.G > 16 || band > (size_t)kMaxSmem - 64 || g.nbg > kMaxBandGroups) return LPF_EUNSUPPORTED;
+  if (band > (size_t)kMaxSmem - 64 || g.nbg > kMaxBandGroups) return LPF_EUNSUPPORTED;
   if (((size_t)g.slice_rows * g.S) % 4 != 0 || ((size_t)32 * g.BB * g.S) % 4 != 0) return LPF_EUNSUPPORTED;
   return LPF_OK;
 }
@@ -103,35 +134,50 @@ int make_geometry3(int D, int H, int W, int rx, int ry, int rz, int T, int BB, G
 // ---------------------------------------------------------------------------
 // Kernels
 
-// packed[y][k]: bit b is the pixel at row y mod H, column (32k + b - r32) mod W
-// (any nonzero byte is phase 1).  Also zeroes the walk's n_zero64 counts and
-// n_zero32 control words (which would otherwise take two more launches).
-// pix_flag != null (checked mode): a byte other than 0 or 1 sets kStatusPixel
-// in *pix_flag.
-__global__ void pack_rows_kernel(const uint8_t* __restrict__ img, int H, int W, int r32, int S, int rows,
-                                 uint32_t* __restrict__ packed, unsigned long long* __restrict__ zero64,
-                                 int64_t n_zero64, int* __restrict__ zero32, int n_zero32,
-                                 int* __restrict__ pix_flag) {
+// One side's packed rows: packed[y][k] bit b is the pixel at row
+// (y - up) mod Ho, column (32k + b - r32) mod Wo of the side's image, whose
+// pixel (r, c) is img[r rs + c cs] (side 0: the image, rs = W, cs = 1,
+// up = 0; side 1: its transpose, rs = 1, cs = W, up = its halo above).  Any
+// nonzero byte is phase 1.
+struct PackSide {
+  uint32_t* packed;
+  int Ho, Wo, r32, S, rows, rs, cs, up;
+};
+
+// Packs side blockIdx.y.  Side 1 runs over its words column by column, so
+// that the threads of a warp read consecutive bytes of an image row.  Side
+// 0's blocks also zero the walk's n_zero64 counts and n_zero32 control words
+// (which would otherwise take two more launches).  pix_flag != null (checked
+// mode): a byte other than 0 or 1 sets kStatusPixel in *pix_flag.
+__global__ void pack_rows_kernel(const uint8_t* __restrict__ img, PackSide s0, PackSide s1,
+                                 unsigned long long* __restrict__ zero64, int64_t n_zero64, int* __restrict__ zero32,
+                                 int n_zero32, int* __restrict__ pix_flag) {
+  const bool side1 = blockIdx.y != 0;
+  const PackSide ps = side1 ? s1 : s0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (int64_t i = i0; i < n_zero64; i += stride) zero64[i] = 0ull;
-  for (int64_t i = i0; i < n_zero32; i += stride) zero32[i] = 0;
-  const int64_t total = (int64_t)rows * S;
+  if (!side1) {
+    for (int64_t i = i0; i < n_zero64; i += stride) zero64[i] = 0ull;
+    for (int64_t i = i0; i < n_zero32; i += stride) zero32[i] = 0;
+  }
+  const int64_t total = (int64_t)ps.rows * ps.S;
   uint32_t high = 0;  // OR of the bytes' bits above bit 0
   for (int64_t i = i0; i < total; i += stride) {
-    const int y = (int)(i / S), k = (int)(i % S);
-    const uint8_t* row = img + (int64_t)(y % H) * W;
-    int x = (32 * k - r32) % W;
-    if (x < 0) x += W;
+    int y, k;
+    if (side1) { k = (int)(i / ps.rows); y = (int)(i % ps.rows); }
+    else { y = (int)(i / ps.S); k = (int)(i % ps.S); }
+    const uint8_t* row = img + (int64_t)((y + ps.Ho - ps.up % ps.Ho) % ps.Ho) * ps.rs;
+    int x = (32 * k - ps.r32) % ps.Wo;
+    if (x < 0) x += ps.Wo;
     uint32_t bits = 0;
 #pragma unroll 4
     for (int b = 0; b < 32; ++b) {
-      const uint32_t v = row[x];
+      const uint32_t v = row[(int64_t)x * ps.cs];
       bits |= (uint32_t)(v != 0) << b;
       high |= v >> 1;
-      if (++x == W) x = 0;
+      if (++x == ps.Wo) x = 0;
     }
-    packed[i] = bits;
+    ps.packed[(int64_t)y * ps.S + k] = bits;
   }
   if (pix_flag && high) atomicOr(pix_flag, kStatusPixel);
 }
@@ -180,43 +226,83 @@ __global__ void mirror_kernel(unsigned long long* __restrict__ counts, int64_t n
   }
 }
 
-// sel_bits[y][j]: bit b set when translation (32j + b, y) is selected.
-__global__ void pack_sel_kernel(const uint8_t* __restrict__ sel, int H, int W, int nw, uint32_t* __restrict__ bits) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < H * nw; i += gridDim.x * blockDim.x) {
+// sel_bits[y][j]: bit b set when translation (32j + b, y) of a side is
+// selected; the side's translation (x, y) is sel[y rs + x cs] (side 0: rs =
+// W, cs = 1; side 1, whose translation (x', y') is the image's (y', x'):
+// rs = 1, cs = W).
+__global__ void pack_sel_kernel(const uint8_t* __restrict__ sel, int Ho, int Wo, int nw, int rs, int cs,
+                                uint32_t* __restrict__ bits) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Ho * nw; i += gridDim.x * blockDim.x) {
     const int y = i / nw, j = i - y * nw;
     uint32_t v = 0;
-    for (int b = 0; b < 32 && 32 * j + b < W; ++b) v |= (uint32_t)(sel[(size_t)y * W + 32 * j + b] != 0) << b;
+    for (int b = 0; b < 32 && 32 * j + b < Wo; ++b)
+      v |= (uint32_t)(sel[(size_t)y * rs + (size_t)(32 * j + b) * cs] != 0) << b;
     bits[i] = v;
   }
 }
 
-// Persistent walk kernel.  A block stages the image rows of one band group
-// (BB bands of 32 translation rows, plus the ry halo rows) and its warps pull
-// work units from that band group's counter in global memory: unit u is
-// program piece u / n_tiles on tile u % n_tiles (tile = one band and one group
-// of T words, i.e. 32 rows x 32T translations).  Warps never wait for one
-// another inside a band group, so warps whose tiles skip zero-count subtrees
-// (and finish early) simply take more units.  A block starts on band group
-// blockIdx.x mod n_bg and, once that counter is exhausted, moves on to the
-// next band group that still has units (one bulk copy and one block barrier
-// per move).  The launch bounds cap a thread at 64 registers (two 512-thread
-// blocks per SM), which keeps 32 warps resident per SM to hide the latency of
-// the shared-memory word loads.
+// One side of a walk (the image or its transpose; volumes have one side):
+// its packed rows, translation selection, size, layout and its pieces of the
+// program.
+struct WalkSide {
+  const uint32_t* packed;
+  const uint32_t* sel;  // packed translation selection, or null
+  int H, W, S, nw, G, BB;
+  int nbg, nbg_s, slice_rows;
+  int piece0, n_pieces;
+  uint32_t band_bytes;
+};
+
+// The units of band group lbg of side sd, pulled from its counter ctr until
+// none is left: unit u is the side's program piece u / n_tiles on tile
+// u % n_tiles (tile = one band and one group of T words, i.e. 32 rows x 32T
+// translations).  Returns the pixel words this warp ANDed.
 template <int T>
-__global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict__ packed, int H, int W, int S,
-                                                  int nw, int G, int BB, uint32_t band_bytes, int n_bg,
-                                                  int n_pieces, const uint4* __restrict__ prog,
+__device__ __forceinline__ unsigned long long walk_band(const WalkSide& sd, int lbg, int* ctr, const uint32_t* sm,
+                                                        int lane, const uint4* __restrict__ prog,
+                                                        const uint32_t* __restrict__ piece,
+                                                        unsigned long long* __restrict__ counts, int64_t n_full,
+                                                        int64_t base) {
+  const int n_tiles = sd.G * sd.BB;
+  const int units = n_tiles * sd.n_pieces;
+  unsigned long long executed = 0;
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(ctr, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= units) break;
+    const int tile = u % n_tiles, pi = sd.piece0 + u / n_tiles;
+    const int bl = tile / sd.G, grp = tile - bl * sd.G;
+    const uint32_t* lane_base = sm + (bl * 32 + lane) * sd.S + grp * T;
+    const int y = ((lbg % sd.nbg_s) * sd.BB + bl) * 32 + lane;  // translation row within the slice
+    executed += walk_unit<T>(prog, piece[pi], piece[pi + 1], lane_base, y, sd.H, sd.W, sd.nw, grp * T, sd.sel, lane,
+                             counts, n_full, base);
+  }
+  return executed;
+}
+
+// Persistent walk kernel.  A block stages the packed rows of one band group
+// (BB bands of 32 translation rows, plus the halo rows) and its warps pull
+// work units from that band group's counter in global memory (walk_band).
+// Band groups are numbered side 0 first, then side 1.  Warps never wait for
+// one another inside a band group, so warps whose tiles skip zero-count
+// subtrees (and finish early) simply take more units.  A block starts on
+// band group blockIdx.x mod n_bg and, once that counter is exhausted, moves
+// on to the next band group that still has units (one bulk copy and one
+// block barrier per move).  The launch bounds cap a thread at 64 registers
+// (two 512-thread blocks per SM), which keeps 32 warps resident per SM to
+// hide the latency of the shared-memory word loads.
+template <int T>
+__global__ void __launch_bounds__(512, 2) walk_kernel(WalkSide s0, WalkSide s1, const uint4* __restrict__ prog,
                                                   const uint32_t* __restrict__ piece,
                                                   unsigned long long* __restrict__ counts, int64_t n_full,
-                                                  int64_t base, int* __restrict__ ctl,
-                                                  const uint32_t* __restrict__ sel, uint32_t extra_tx,
-                                                  uint32_t wait_rounds, int nbg_s, int slice_rows) {
+                                                  int64_t base, int* __restrict__ ctl, uint32_t extra_tx,
+                                                  uint32_t wait_rounds) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_abort, s_done;
   const int lane = threadIdx.x & 31;
-  const int n_tiles = G * BB;
-  const int units = n_tiles * n_pieces;
+  const int n_bg = s0.nbg + s1.nbg;
   int* unit_ctr = ctl + kCtlUnits;
   if (threadIdx.x == 0) { mbar_init(&bar, 1); s_abort = 0; }
   __syncthreads();
@@ -226,7 +312,12 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
 
   for (int k = 0; k < n_bg; ++k) {
     const int bg = (int)((blockIdx.x + (unsigned)k) % (unsigned)n_bg);
-    if (threadIdx.x == 0) s_done = *reinterpret_cast<volatile int*>(unit_ctr + bg) >= units;
+    const bool side1 = bg >= s0.nbg;
+    const int lbg = side1 ? bg - s0.nbg : bg;
+    if (threadIdx.x == 0) {
+      const int units = side1 ? s1.G * s1.BB * s1.n_pieces : s0.G * s0.BB * s0.n_pieces;
+      s_done = *reinterpret_cast<volatile int*>(unit_ctr + bg) >= units;
+    }
     __syncthreads();
     if (s_done) {
       __syncthreads();  // s_done is rewritten next round
@@ -234,11 +325,15 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
     }
     if (threadIdx.x == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const uint32_t bytes = side1 ? s1.band_bytes : s0.band_bytes;
       // (extra_tx > 0 only in the failure-detection self-test: bytes no copy delivers)
-      mbar_expect_tx(&bar, band_bytes + extra_tx);
-      // band group bg = slice bg / nbg_s (volumes; images have one slice), band bg % nbg_s
-      const size_t row0 = (size_t)(bg / nbg_s) * slice_rows + (size_t)(bg % nbg_s) * 32 * BB;
-      bulk_g2s(sm, packed + row0 * S, band_bytes, &bar);
+      mbar_expect_tx(&bar, bytes + extra_tx);
+      // band group lbg = slice lbg / nbg_s (volumes; images have one slice), band lbg % nbg_s
+      const int nbg_s = side1 ? s1.nbg_s : s0.nbg_s, BB = side1 ? s1.BB : s0.BB;
+      const size_t row0 = (size_t)(lbg / nbg_s) * (side1 ? s1.slice_rows : s0.slice_rows) +
+                          (size_t)(lbg % nbg_s) * 32 * BB;
+      const uint32_t* src = side1 ? s1.packed + row0 * s1.S : s0.packed + row0 * s0.S;
+      bulk_g2s(sm, src, bytes, &bar);
     }
     copy_pending = true;
     if (mbar_wait(&bar, parity, wait_rounds)) copy_pending = false;
@@ -246,19 +341,8 @@ __global__ void __launch_bounds__(512, 2) walk_kernel(const uint32_t* __restrict
     parity ^= 1u;
     __syncthreads();
     if (s_abort) break;
-
-    for (;;) {
-      int u = 0;
-      if (lane == 0) u = atomicAdd(unit_ctr + bg, 1);
-      u = __shfl_sync(0xffffffffu, u, 0);
-      if (u >= units) break;
-      const int tile = u % n_tiles, pi = u / n_tiles;
-      const int bl = tile / G, grp = tile - (tile / G) * G;
-      const uint32_t* lane_base = sm + (bl * 32 + lane) * S + grp * T;
-      const int y = ((bg % nbg_s) * BB + bl) * 32 + lane;  // translation row within the slice
-      executed += walk_unit<T>(prog, piece[pi], piece[pi + 1], lane_base, y, H, W, nw, grp * T, sel, lane, counts,
-                               n_full, base);
-    }
+    if (side1) executed += walk_band<T>(s1, lbg, unit_ctr + bg, sm, lane, prog, piece, counts, n_full, base);
+    else executed += walk_band<T>(s0, lbg, unit_ctr + bg, sm, lane, prog, piece, counts, n_full, base);
     __syncthreads();  // every warp is done with the staged band before it may be replaced
   }
   if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(ctl + kCtlExecuted), executed);
@@ -307,10 +391,13 @@ int ensure_device(lpf_paths* p, size_t packed_words) {
   return LPF_OK;
 }
 
-int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
-  if (b.d_words && b.W == g.W && b.S == g.S && b.r32 == g.r32 && b.slice_rows == g.slice_rows) {
-    b.T = g.T;
-    b.BB = g.BB;
+int bake(lpf_paths* p, const Program& prog0, const Geometry& g0, const Program* prog1, const Geometry* g1,
+         Baked& b) {
+  const int S1 = prog1 ? g1->S : -1, r32_1 = prog1 ? g1->r32 : -1;
+  if (b.d_words && b.W == g0.W && b.S == g0.S && b.r32 == g0.r32 && b.slice_rows == g0.slice_rows && b.S1 == S1 &&
+      b.r32_1 == r32_1) {
+    b.T = g0.T;
+    b.BB = g0.BB;
     return LPF_OK;
   }
   if (b.d_words) {
@@ -320,12 +407,21 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
     b.d_words = nullptr;
     b.d_piece = nullptr;
   }
-  std::vector<uint32_t> out;
-  std::vector<int64_t> piece;
-  // volumes: a voxel (sx, sy, sz) of a translation on staged row `lane` reads
-  // row lane + sz * slice_rows + sy + ry (sy may be negative in 3D)
-  bake_words(p->host, prog, g.S, g.r32, out, piece, g.slice_rows, g.slice_rows ? g.ry : 0);
+  std::vector<uint32_t> out, out1;
+  std::vector<int64_t> piece, piece1;
+  // a pixel (sx, sy) of a translation on staged row `lane` reads row
+  // lane + sy + up (sy >= -up); volumes: a voxel (sx, sy, sz) reads row
+  // lane + sz * slice_rows + sy + ry (sy may be negative in 3D)
+  bake_words(p->host, prog0, g0.S, g0.r32, out, piece, g0.slice_rows, g0.slice_rows ? g0.ry : g0.up);
+  const int n0 = (int)piece.size() - 1;
+  if (prog1) {
+    bake_words(p->host, *prog1, g1->S, g1->r32, out1, piece1, 0, g1->up);
+    const int64_t at = (int64_t)(out.size() / 4);  // side 1's groups follow side 0's
+    out.insert(out.end(), out1.begin(), out1.end());
+    for (size_t q = 1; q < piece1.size(); ++q) piece.push_back(at + piece1[q]);
+  }
   if (out.size() / 4 >= (size_t(1) << 32)) return LPF_EUNSUPPORTED;  // group offsets are 32-bit
+  if (out.empty()) out.assign(4, 0u);
   std::vector<uint32_t> piece32(piece.begin(), piece.end());
   cudaError_t e;
   if ((e = cudaMalloc(&b.d_words, out.size() * 4)) != cudaSuccess) return set_cuda_error(e);
@@ -335,14 +431,30 @@ int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b) {
   if ((e = cudaMemcpy(b.d_piece, piece32.data(), piece32.size() * 4, cudaMemcpyHostToDevice)) !=
       cudaSuccess)
     return set_cuda_error(e);
-  b.W = g.W;
-  b.S = g.S;
-  b.r32 = g.r32;
-  b.T = g.T;
-  b.BB = g.BB;
-  b.slice_rows = g.slice_rows;
-  b.n_pieces = (int)prog.piece_begin.size() - 1;
+  b.W = g0.W;
+  b.S = g0.S;
+  b.r32 = g0.r32;
+  b.S1 = S1;
+  b.r32_1 = r32_1;
+  b.T = g0.T;
+  b.BB = g0.BB;
+  b.slice_rows = g0.slice_rows;
+  b.n_pieces = (int)piece.size() - 1;
+  b.n_pieces0 = n0;
   return LPF_OK;
+}
+
+// True when b holds the programs laid out for the sides' row layouts.
+static bool baked_for_sides(const Baked& b, const Sides& sd) {
+  return b.d_words && b.W == sd.g[0].W && b.S == sd.g[0].S && b.r32 == sd.g[0].r32 &&
+         b.S1 == (sd.n == 2 ? sd.g[1].S : -1) && b.r32_1 == (sd.n == 2 ? sd.g[1].r32 : -1);
+}
+
+// Bake the image's programs (tree or plain) for the sides.
+static int bake_sides(lpf_paths* p, const Sides& sd, bool standard, Baked& b) {
+  const Program& prog0 = standard ? p->host.plain : p->host.tree;
+  const Program& prog1 = standard ? p->host.plain_t : p->host.tree_t;
+  return bake(p, prog0, sd.g[0], sd.n == 2 ? &prog1 : nullptr, sd.n == 2 ? &sd.g[1] : nullptr, b);
 }
 
 static std::once_flag g_attr_once;
@@ -376,12 +488,30 @@ static void set_kernel_attributes() {
 static int g_num_sms = 0;
 
 template <int T>
-static int walk_blocks(const Geometry& g) {
+static int walk_blocks(const Sides& sd) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<T>, 32 * g.G * g.BB,
-                                                                g.band_bytes);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<T>, sd.threads, sd.band_bytes);
   if (e != cudaSuccess) return -set_cuda_error(e);
   return std::max(1, per_sm) * g_num_sms;
+}
+
+static int walk_blocks_for(const Sides& sd) {
+  switch (sd.g[0].T) {
+    case 1: return walk_blocks<1>(sd);
+    case 2: return walk_blocks<2>(sd);
+    case 4: return walk_blocks<4>(sd);
+    default: return walk_blocks<8>(sd);
+  }
+}
+
+static int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return set_cuda_error(e);
+  }
+  return LPF_OK;
 }
 
 // Failure-detection self-test (lpf_paths_set_selftest): the staging wait
@@ -390,14 +520,49 @@ static int walk_blocks(const Geometry& g) {
 static uint32_t selftest_extra_tx(const lpf_paths* p) { return p->selftest ? 16u : 0u; }
 static uint32_t selftest_wait_rounds(const lpf_paths* p) { return p->selftest ? (1u << 16) : kWaitRounds; }
 
-template <int T>
-static void launch_walk(const Geometry& g, const Baked& b, lpf_paths* p, unsigned long long* c, int blocks,
-                        cudaStream_t s) {
-  walk_kernel<T><<<blocks, 32 * g.G * g.BB, g.band_bytes, s>>>(
-      p->d_packed, g.H, g.W, g.S, g.nw, g.G, g.BB, g.band_bytes, g.nbg, b.n_pieces,
-      reinterpret_cast<const uint4*>(b.d_words), b.d_piece, c,
-      p->host.n_full, p->host.base, p->d_status, p->d_sel_active, selftest_extra_tx(p), selftest_wait_rounds(p),
-      g.nbg_s, g.slice_rows);
+// The walk's view of the sides: packed rows from `packed` (side 1 at
+// sd.off1), selections sel0/sel1 (or null), pieces from b.
+static void walk_sides(const Sides& sd, const Baked& b, const uint32_t* packed, const uint32_t* sel0,
+                       const uint32_t* sel1, WalkSide& w0, WalkSide& w1) {
+  const Geometry& g0 = sd.g[0];
+  w0 = WalkSide{packed, sel0, g0.H, g0.W, g0.S, g0.nw, g0.G, g0.BB, g0.nbg, g0.nbg_s, g0.slice_rows,
+                0, b.n_pieces0, g0.band_bytes};
+  w1 = WalkSide{};
+  if (sd.n == 2) {
+    const Geometry& g1 = sd.g[1];
+    w1 = WalkSide{packed + sd.off1, sel1, g1.H, g1.W, g1.S, g1.nw, g1.G, g1.BB, g1.nbg, g1.nbg_s, g1.slice_rows,
+                  b.n_pieces0, b.n_pieces - b.n_pieces0, g1.band_bytes};
+  }
+}
+
+static void launch_walk(const Sides& sd, const Baked& b, const uint32_t* packed, const uint32_t* sel0,
+                        const uint32_t* sel1, unsigned long long* c, int64_t n_full, int64_t base, int* ctl,
+                        const lpf_paths* p, int blocks, cudaStream_t s) {
+  WalkSide w0, w1;
+  walk_sides(sd, b, packed, sel0, sel1, w0, w1);
+  const uint4* prog = reinterpret_cast<const uint4*>(b.d_words);
+  const uint32_t xt = selftest_extra_tx(p), wr = selftest_wait_rounds(p);
+  switch (sd.g[0].T) {
+    case 1: walk_kernel<1><<<blocks, sd.threads, sd.band_bytes, s>>>(w0, w1, prog, b.d_piece, c, n_full, base, ctl, xt, wr); break;
+    case 2: walk_kernel<2><<<blocks, sd.threads, sd.band_bytes, s>>>(w0, w1, prog, b.d_piece, c, n_full, base, ctl, xt, wr); break;
+    case 4: walk_kernel<4><<<blocks, sd.threads, sd.band_bytes, s>>>(w0, w1, prog, b.d_piece, c, n_full, base, ctl, xt, wr); break;
+    default: walk_kernel<8><<<blocks, sd.threads, sd.band_bytes, s>>>(w0, w1, prog, b.d_piece, c, n_full, base, ctl, xt, wr); break;
+  }
+}
+
+// Pack both sides of an image (one launch, one grid row per side), zeroing
+// n_zero counts and the walk's control words 1.. of the sides' band groups.
+static void launch_pack(const uint8_t* img, const Sides& sd, uint32_t* packed, int64_t* counts, int64_t n_zero,
+                        int* ctl, const lpf_paths* p, cudaStream_t s) {
+  const Geometry& g0 = sd.g[0];
+  const Geometry& g1 = sd.n == 2 ? sd.g[1] : sd.g[0];
+  const PackSide s0{packed, g0.H, g0.W, g0.r32, g0.S, g0.rows, g0.W, 1, 0};
+  const PackSide s1{packed + sd.off1, g1.H, g1.W, g1.r32, g1.S, g1.rows, 1, g0.W, g1.up};
+  const int64_t total = std::max<int64_t>({(int64_t)g0.rows * g0.S, sd.n == 2 ? (int64_t)g1.rows * g1.S : 0, n_zero});
+  const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  pack_rows_kernel<<<dim3(pblocks, sd.n), 256, 0, s>>>(img, s0, s1, reinterpret_cast<unsigned long long*>(counts),
+                                                       n_zero, ctl + 1, kCtlUnits - 1 + sd.nbg,
+                                                       p->checked ? ctl : nullptr);
 }
 
 // Enqueue one full evaluation with launch shape (T, BB) (<= 0: tuned or
@@ -408,75 +573,63 @@ static int run_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t* cou
   if (p->host.dims != 2) return LPF_EINVAL;  // a volume's handle: lpf_full_3d
   if (H < 1 || W < 1 || H > 8192 || W > 8192) return LPF_EINVAL;
   if (p->host.rx >= W || p->host.ry >= H) return LPF_EINVAL;
-  const Program& prog = standard ? p->host.plain : p->host.tree;
-  if (prog.stack_depth > kDevStack) return LPF_EUNSUPPORTED;
+  const Program& prog0 = standard ? p->host.plain : p->host.tree;
+  const Program& prog1 = standard ? p->host.plain_t : p->host.tree_t;
+  if (std::max(prog0.stack_depth, prog1.stack_depth) > kDevStack) return LPF_EUNSUPPORTED;
   std::call_once(g_attr_once, set_kernel_attributes);
   if (g_attr_status) return g_attr_status;
   if (T <= 0)
     for (const Tuned& t : p->tuned)
       if (t.H == H && t.W == W) { T = t.T; BB = t.BB; }
-  Geometry g;
-  int rc = make_geometry(H, W, p->host.rx, p->host.ry, T, BB, g);
+  Sides sd;
+  int rc = make_sides(p->host, H, W, T, BB, sd);
   if (rc) return rc;
-  if ((int)g.band_bytes > g_max_dyn_smem) return LPF_EUNSUPPORTED;
-  rc = ensure_device(p, g.packed_words);
+  if ((int)sd.band_bytes > g_max_dyn_smem) return LPF_EUNSUPPORTED;
+  rc = ensure_device(p, sd.packed_words);
   if (rc) return rc;
   Baked& b = standard ? p->plain : p->tree;
-  rc = bake(p, prog, g, b);
+  rc = bake_sides(p, sd, standard, b);
   if (rc) return rc;
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaError_t e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return set_cuda_error(e);
-  }
-  int blocks = 0;
-  switch (g.T) {
-    case 1: blocks = walk_blocks<1>(g); break;
-    case 2: blocks = walk_blocks<2>(g); break;
-    case 4: blocks = walk_blocks<4>(g); break;
-    default: blocks = walk_blocks<8>(g); break;
-  }
+  if ((rc = num_sms())) return rc;
+  int blocks = walk_blocks_for(sd);
   if (blocks < 0) return -blocks;
-  blocks = std::min(blocks, g.nbg * b.n_pieces);
+  blocks = std::min(blocks, sd.nbg * b.n_pieces);
   (void)cudaGetLastError();  // clear a stale error left by earlier, unrelated calls
 
   const int64_t n_full = p->host.n_full, base = p->host.base;
   cudaError_t e = cudaSuccess;
-  {
-    // pack the rows; zero the counts (unless accumulating) and the work
-    // counters (not the status flags)
-    const int64_t n_zero = accumulate ? 0 : 2 * n_full;
-    const int64_t total = std::max<int64_t>((int64_t)g.rows * g.S, n_zero);
-    const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-    pack_rows_kernel<<<pblocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, p->d_packed,
-                                             reinterpret_cast<unsigned long long*>(counts), n_zero,
-                                             p->d_status + 1, kCtlUnits - 1 + g.nbg,
-                                             p->checked ? p->d_status : nullptr);
-  }
-  p->d_sel_active = nullptr;
+  // pack the rows; zero the counts (unless accumulating) and the work
+  // counters (not the status flags)
+  launch_pack(img, sd, p->d_packed, counts, accumulate ? 0 : 2 * n_full, p->d_status, p, s);
+  const uint32_t* sel0 = nullptr;
+  const uint32_t* sel1 = nullptr;
   if (sel) {
-    const size_t words = (size_t)H * g.nw;
+    const Geometry& g0 = sd.g[0];
+    const size_t words0 = (size_t)g0.H * g0.nw, words = words0 + (sd.n == 2 ? (size_t)sd.g[1].H * sd.g[1].nw : 0);
     if (words > p->sel_cap) {
       if (p->d_sel) { cudaDeviceSynchronize(); cudaFree(p->d_sel); p->d_sel = nullptr; p->sel_cap = 0; }
       e = cudaMalloc(&p->d_sel, words * 4);
       if (e != cudaSuccess) return set_cuda_error(e);
       p->sel_cap = words;
     }
-    pack_sel_kernel<<<(int)std::min<size_t>((words + 255) / 256, 4096), 256, 0, s>>>(sel, H, W, g.nw, p->d_sel);
-    p->d_sel_active = p->d_sel;
+    pack_sel_kernel<<<(int)std::min<size_t>((words0 + 255) / 256, 4096), 256, 0, s>>>(sel, g0.H, g0.W, g0.nw, W, 1,
+                                                                                      p->d_sel);
+    sel0 = p->d_sel;
+    if (sd.n == 2) {
+      const Geometry& g1 = sd.g[1];
+      const size_t words1 = words - words0;
+      pack_sel_kernel<<<(int)std::min<size_t>((words1 + 255) / 256, 4096), 256, 0, s>>>(sel, g1.H, g1.W, g1.nw, 1,
+                                                                                        W, p->d_sel + words0);
+      sel1 = p->d_sel + words0;
+    }
   }
   unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
-  p->nominal_pixels = prog.n_pixel_words * g.nbg * g.G * g.BB;  // every warp walks every piece
+  // every warp walks every piece of its side
+  p->nominal_pixels = prog0.n_pixel_words * sd.g[0].nbg * sd.g[0].G * sd.g[0].BB;
+  if (sd.n == 2) p->nominal_pixels += prog1.n_pixel_words * sd.g[1].nbg * sd.g[1].G * sd.g[1].BB;
   if (p->ev_start) cudaEventRecord(p->ev_start, s);
-  switch (g.T) {
-    case 1: launch_walk<1>(g, b, p, c, blocks, s); break;
-    case 2: launch_walk<2>(g, b, p, c, blocks, s); break;
-    case 4: launch_walk<4>(g, b, p, c, blocks, s); break;
-    default: launch_walk<8>(g, b, p, c, blocks, s); break;
-  }
+  launch_walk(sd, b, p->d_packed, sel0, sel1, c, n_full, base, p->d_status, p, blocks, s);
   if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
-  p->d_sel_active = nullptr;
   if (n_full > 1) {
     const int64_t n = 2 * (n_full - base - 1);
     const int mblocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
@@ -497,10 +650,10 @@ static int autotune_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t
   for (int T : {1, 2, 4, 8}) {
     if (T > 1 && (T / 2) >= nw) continue;          // more words per thread than a row has
     for (int BB : {1, 2, 4, 8}) {
-      Geometry g;
-      if (make_geometry(H, W, p->host.rx, p->host.ry, T, BB, g) != LPF_OK) continue;
-      if (g.T != T || g.BB != BB) continue;         // shape not admissible as asked
-      if ((int)g.band_bytes > g_max_dyn_smem && g_max_dyn_smem > 0) continue;
+      Sides sd;
+      if (make_sides(p->host, H, W, T, BB, sd) != LPF_OK) continue;
+      if (sd.g[0].T != T || sd.g[0].BB != BB) continue;  // shape not admissible as asked
+      if ((int)sd.band_bytes > g_max_dyn_smem && g_max_dyn_smem > 0) continue;
       rc = run_full(img, H, W, p, counts, s, false, T, BB);  // warm-up (uploads tables)
       if (rc) break;
       float t_min = 1e30f;
@@ -526,9 +679,9 @@ static int autotune_full(const uint8_t* img, int H, int W, lpf_paths* p, int64_t
   {
     // leave the program on the device laid out for the winning shape (the
     // trials re-baked it for each shape they ran)
-    Geometry g;
-    rc = make_geometry(H, W, p->host.rx, p->host.ry, bt, bb, g);
-    if (!rc) rc = bake(p, p->host.tree, g, p->tree);
+    Sides sd;
+    rc = make_sides(p->host, H, W, bt, bb, sd);
+    if (!rc) rc = bake_sides(p, sd, false, p->tree);
     if (rc) return rc;
   }
   for (Tuned& t : p->tuned)
@@ -552,27 +705,22 @@ static int run_full3(const uint8_t* vol, int D, int H, int W, lpf_paths* p, int6
   int T = 0, BB = 0;
   for (const Tuned& t : p->tuned)
     if (t.H == H && t.W == W) { T = t.T; BB = t.BB; }
-  Geometry g;
-  int rc = make_geometry3(D, H, W, p->host.rx, p->host.ry, p->host.rz, T, BB, g);
+  Sides sd;  // one side
+  int rc = make_geometry3(D, H, W, p->host.rx, p->host.ry, p->host.rz, T, BB, sd.g[0]);
   if (rc) return rc;
+  const Geometry& g = sd.g[0];
+  sd.n = 1;
+  sd.packed_words = g.packed_words;
+  sd.band_bytes = g.band_bytes;
+  sd.nbg = g.nbg;
+  sd.threads = 32 * std::min(16, g.G * g.BB);
   if ((int)g.band_bytes > g_max_dyn_smem) return LPF_EUNSUPPORTED;
   rc = ensure_device(p, g.packed_words);
   if (rc) return rc;
-  rc = bake(p, prog, g, p->tree);
+  rc = bake(p, prog, g, nullptr, nullptr, p->tree);
   if (rc) return rc;
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaError_t e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return set_cuda_error(e);
-  }
-  int blocks = 0;
-  switch (g.T) {
-    case 1: blocks = walk_blocks<1>(g); break;
-    case 2: blocks = walk_blocks<2>(g); break;
-    case 4: blocks = walk_blocks<4>(g); break;
-    default: blocks = walk_blocks<8>(g); break;
-  }
+  if ((rc = num_sms())) return rc;
+  int blocks = walk_blocks_for(sd);
   if (blocks < 0) return -blocks;
   blocks = std::min(blocks, g.nbg * p->tree.n_pieces);
   (void)cudaGetLastError();
@@ -587,14 +735,8 @@ static int run_full3(const uint8_t* vol, int D, int H, int W, lpf_paths* p, int6
   }
   unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
   p->nominal_pixels = prog.n_pixel_words * g.nbg * g.G * g.BB;
-  p->d_sel_active = nullptr;
   if (p->ev_start) cudaEventRecord(p->ev_start, s);
-  switch (g.T) {
-    case 1: launch_walk<1>(g, p->tree, p, c, blocks, s); break;
-    case 2: launch_walk<2>(g, p->tree, p, c, blocks, s); break;
-    case 4: launch_walk<4>(g, p->tree, p, c, blocks, s); break;
-    default: launch_walk<8>(g, p->tree, p, c, blocks, s); break;
-  }
+  launch_walk(sd, p->tree, p->d_packed, nullptr, nullptr, c, n_full, base, p->d_status, p, blocks, s);
   if (p->ev_stop) cudaEventRecord(p->ev_stop, s);
   if (n_full > 1) {
     const int64_t n = 2 * (n_full - base - 1);
@@ -664,74 +806,45 @@ static int run_full_noalloc(const uint8_t* img, int H, int W, lpf_paths* p, int6
   if (p->host.dims != 2) return LPF_EINVAL;
   if (H < 1 || W < 1 || H > 8192 || W > 8192) return LPF_EINVAL;
   if (p->host.rx >= W || p->host.ry >= H) return LPF_EINVAL;
-  if (p->host.tree.stack_depth > kDevStack) return LPF_EUNSUPPORTED;
+  if (std::max(p->host.tree.stack_depth, p->host.tree_t.stack_depth) > kDevStack) return LPF_EUNSUPPORTED;
   std::call_once(g_attr_once, set_kernel_attributes);
   if (g_attr_status) return g_attr_status;
   int T = 0, BB = 0;
   for (const Tuned& t : p->tuned)
     if (t.H == H && t.W == W) { T = t.T; BB = t.BB; }
-  Geometry g;
-  int rc = make_geometry(H, W, p->host.rx, p->host.ry, T, BB, g);
+  Sides sd;
+  int rc = make_sides(p->host, H, W, T, BB, sd);
   if (rc) return rc;
-  if ((int)g.band_bytes > g_max_dyn_smem) return LPF_EUNSUPPORTED;
-  if (g.packed_words > kNoAllocPackedWords) return LPF_EUNSUPPORTED;  // image too large for the fixed area
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_cuda_error(e);
   const Baked& b = p->tree;
-  // The program for this width must already be on this device (an earlier
-  // lpf_full call put it there).  When the tuned shape needs another row
-  // layout than the one it was baked for (lpf_set_launch_shape after that
-  // call), the walk runs in the shape it was baked for instead.
-  if (b.d_words && b.W == g.W && (b.S != g.S || b.r32 != g.r32) && b.T > 0) {
-    rc = make_geometry(H, W, p->host.rx, p->host.ry, b.T, b.BB, g);
+  // The programs for this size must already be on this device (an earlier
+  // lpf_full call put them there).  When the tuned shape needs other row
+  // layouts than the ones they were baked for (lpf_set_launch_shape after
+  // that call), the walk runs in the shape they were baked for instead.
+  if (b.d_words && b.W == W && !baked_for_sides(b, sd) && b.T > 0) {
+    rc = make_sides(p->host, H, W, b.T, b.BB, sd);
     if (rc) return rc;
-    if ((int)g.band_bytes > g_max_dyn_smem || g.packed_words > kNoAllocPackedWords) return LPF_EUNSUPPORTED;
   }
-  if (p->device != dev || !b.d_words || b.W != g.W || b.S != g.S || b.r32 != g.r32) return LPF_EINVAL;
+  if ((int)sd.band_bytes > g_max_dyn_smem) return LPF_EUNSUPPORTED;
+  if (sd.packed_words > kNoAllocPackedWords) return LPF_EUNSUPPORTED;  // image too large for the fixed area
+  if (p->device != dev || !baked_for_sides(b, sd)) return LPF_EINVAL;
   NoAllocSlot slot;
   rc = noalloc_slot(dev, slot);
   if (rc) return rc;
-  if (g_num_sms == 0) {
-    e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return set_cuda_error(e);
-  }
-  int blocks = 0;
-  switch (g.T) {
-    case 1: blocks = walk_blocks<1>(g); break;
-    case 2: blocks = walk_blocks<2>(g); break;
-    case 4: blocks = walk_blocks<4>(g); break;
-    default: blocks = walk_blocks<8>(g); break;
-  }
+  if ((rc = num_sms())) return rc;
+  int blocks = walk_blocks_for(sd);
   if (blocks < 0) return -blocks;
-  blocks = std::min(blocks, g.nbg * b.n_pieces);
+  blocks = std::min(blocks, sd.nbg * b.n_pieces);
   (void)cudaGetLastError();
 
   const int64_t n_full = p->host.n_full, base = p->host.base;
-  {
-    // pack the rows; the counts and the work counters start at 0 (the status
-    // word keeps its flags until lpf_paths_status reads and clears them)
-    const int64_t total = std::max<int64_t>((int64_t)g.rows * g.S, 2 * n_full);
-    const int pblocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-    pack_rows_kernel<<<pblocks, 256, 0, s>>>(img, H, W, g.r32, g.S, g.rows, slot.packed,
-                                             reinterpret_cast<unsigned long long*>(counts), 2 * n_full, slot.ctl + 1,
-                                             kCtlUnits - 1 + g.nbg, p->checked ? slot.ctl : nullptr);
-  }
+  // pack the rows; the counts and the work counters start at 0 (the status
+  // word keeps its flags until lpf_paths_status reads and clears them)
+  launch_pack(img, sd, slot.packed, counts, 2 * n_full, slot.ctl, p, s);
   unsigned long long* c = reinterpret_cast<unsigned long long*>(counts);
-  const dim3 block(32 * g.G * g.BB);
-#define LPF_NOALLOC_WALK(TT)                                                                                   \
-  walk_kernel<TT><<<blocks, block, g.band_bytes, s>>>(slot.packed, g.H, g.W, g.S, g.nw, g.G, g.BB, g.band_bytes, \
-                                                      g.nbg, b.n_pieces, reinterpret_cast<const uint4*>(b.d_words), \
-                                                      b.d_piece, c, n_full, base,                              \
-                                                      slot.ctl, nullptr, selftest_extra_tx(p),                  \
-                                                      selftest_wait_rounds(p), g.nbg_s, g.slice_rows)
-  switch (g.T) {
-    case 1: LPF_NOALLOC_WALK(1); break;
-    case 2: LPF_NOALLOC_WALK(2); break;
-    case 4: LPF_NOALLOC_WALK(4); break;
-    default: LPF_NOALLOC_WALK(8); break;
-  }
-#undef LPF_NOALLOC_WALK
+  launch_walk(sd, b, slot.packed, nullptr, nullptr, c, n_full, base, slot.ctl, p, blocks, s);
   if (n_full > 1) {
     const int64_t n = 2 * (n_full - base - 1);
     const int mblocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
@@ -828,8 +941,8 @@ int lpf_paths_export(const lpf_paths* p, int16_t* vec, int64_t* ptr, int16_t* of
 int lpf_paths_stats(const lpf_paths* p, int64_t* n_tree_nodes, int32_t* stack_depth, int32_t* n_pieces) {
   if (!p) return LPF_EINVAL;
   if (n_tree_nodes) *n_tree_nodes = p->host.n_nodes();
-  if (stack_depth) *stack_depth = p->host.tree.stack_depth;
-  if (n_pieces) *n_pieces = (int32_t)p->host.tree.piece_pixels.size();
+  if (stack_depth) *stack_depth = std::max(p->host.tree.stack_depth, p->host.tree_t.stack_depth);
+  if (n_pieces) *n_pieces = (int32_t)(p->host.tree.piece_pixels.size() + p->host.tree_t.piece_pixels.size());
   return LPF_OK;
 }
 

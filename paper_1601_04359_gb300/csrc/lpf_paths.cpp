@@ -3,6 +3,7 @@
 #include "lpf_paths.hpp"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 
 namespace lpf {
@@ -55,11 +56,12 @@ void segment_canonical3(int dx, int dy, int dz, std::vector<int16_t>& out) {
 
 namespace {
 
-// Child slot of a one-pixel move inside a canonical segment.  2D: the move
-// is (mx, my) with my in {0, 1} and mx in {-1, 0, 1}, never (0, 0) (5
-// slots).  3D: (mx, my, mz) with mz in {0, 1}, mx, my in {-1, 0, 1} (18
-// slots, one of them unused).
-inline int move_slot(int mx, int my) { return my == 0 ? (mx < 0 ? 0 : 1) : 2 + (mx + 1); }
+// Child slot of a one-pixel move inside an oriented segment.  2D: the move
+// is (mx, my) with my in {0, 1} and mx in {-1, 0, 1}, never (0, 0), or
+// (1, -1) (a transposed segment of a vector with dx < 0) (6 slots).  3D:
+// (mx, my, mz) with mz in {0, 1}, mx, my in {-1, 0, 1} (18 slots, one of
+// them unused).
+inline int move_slot(int mx, int my) { return my < 0 ? 5 : (my == 0 ? (mx < 0 ? 0 : 1) : 2 + (mx + 1)); }
 inline int move_slot3(int mx, int my, int mz) { return mz * 9 + (my + 1) * 3 + (mx + 1); }
 
 struct Trie {
@@ -184,105 +186,19 @@ static void emit_records(const std::vector<Event>& ev, Program& prog,
   rec_pix.push_back(pix_total);
 }
 
-int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err) {
-  return build_paths_nd(rx, ry, 0, 2, n_pieces, p, err);
-}
-
-int build_paths_nd(int32_t rx, int32_t ry, int32_t rz, int dims, int n_pieces, Paths& p, std::string& err) {
-  if (rx < 0 || ry < 0 || rz < 0 || rx > 4095 || ry > 4095 || rz > 4095) {
-    err = "window radius out of range [0, 4095]";
-    return -1;
-  }
-  if (dims != 2 && dims != 3) { err = "dims must be 2 or 3"; return -1; }
-  if (dims == 2) rz = 0;
-  p = Paths();
-  p.rx = rx;
-  p.ry = ry;
-  p.rz = rz;
-  p.dims = dims;
-  const int64_t nxy = (int64_t)(2 * rx + 1) * (2 * ry + 1);
-  p.n_full = nxy * (2 * rz + 1);
-  p.base = (p.n_full - 1) / 2;
-  p.n_canon = p.n_full - p.base;
-  p.vec.resize((size_t)dims * p.n_canon);
-  p.ptr.assign(p.n_canon + 1, 0);
-  std::vector<int16_t> seg;
-  for (int64_t c = 0; c < p.n_canon; ++c) {
-    const int64_t k = p.base + c;
-    const int dz = (int)(k / nxy) - rz;
-    const int64_t rem = k % nxy;
-    const int dy = (int)(rem / (2 * rx + 1)) - ry, dx = (int)(rem % (2 * rx + 1)) - rx;
-    p.vec[(size_t)dims * c] = (int16_t)dx;
-    p.vec[(size_t)dims * c + 1] = (int16_t)dy;
-    if (dims == 3) {
-      p.vec[(size_t)dims * c + 2] = (int16_t)dz;
-      segment_canonical3(dx, dy, dz, seg);
-    } else {
-      segment_canonical(dx, dy, seg);
-    }
-    p.ptr[c + 1] = p.ptr[c] + (int64_t)seg.size() / dims;
-    p.off.insert(p.off.end(), seg.begin(), seg.end());
-  }
-
-  // Prefix tree of all canonical segments; node 0 is pixel (0,0[,0]).
-  Trie t;
-  t.slots = dims == 3 ? 18 : 5;
-  const int S5 = t.slots;
-  t.add(-1, 0, 0, 0, 0);
-  for (int64_t c = 0; c < p.n_canon; ++c) {
-    int32_t n = 0;
-    for (int64_t j = p.ptr[c] + 1; j < p.ptr[c + 1]; ++j) {
-      const int16_t x = p.off[dims * j], y = p.off[dims * j + 1], z = dims == 3 ? p.off[dims * j + 2] : 0;
-      const int mx = x - t.pix[3 * n], my = y - t.pix[3 * n + 1], mz = z - t.pix[3 * n + 2];
-      const int slot = dims == 3 ? move_slot3(mx, my, mz) : move_slot(mx, my);
-      int32_t ch = t.child5[(int64_t)S5 * n + slot];
-      if (ch < 0) {
-        ch = t.add(n, x, y, z, t.depth[n] + 1);
-        t.child5[(int64_t)S5 * n + slot] = ch;
-      }
-      n = ch;
-    }
-    t.vec[n] = (int32_t)c;
-  }
-  const int64_t nn = (int64_t)t.parent.size();
-  // subtree sizes (children have larger ids than parents)
-  std::vector<int64_t> sub(nn, 1);
-  for (int64_t n = nn - 1; n > 0; --n) sub[t.parent[n]] += sub[n];
-  std::vector<int32_t> cstart(nn + 1, 0), clist;
-  clist.reserve(nn);
-  for (int64_t n = 0; n < nn; ++n) {
-    int32_t cs[18];
-    int m = 0;
-    for (int k = 0; k < S5; ++k) if (t.child5[S5 * n + k] >= 0) cs[m++] = t.child5[S5 * n + k];
-    std::sort(cs, cs + m, [&](int32_t a, int32_t b) { return sub[a] != sub[b] ? sub[a] < sub[b] : a < b; });
-    for (int k = 0; k < m; ++k) clist.push_back(cs[k]);
-    cstart[n + 1] = (int32_t)clist.size();
-  }
-  std::vector<int32_t>().swap(t.child5);
-
-  // Depth-first walk -> events -> records.
-  Walker wk{t, sub, cstart, clist, {}, 0};
-  wk.ev.reserve(nn + 3 * p.n_canon);
-  wk.node(0, 0);
-  if (wk.max_level > kMaxStack) { err = "prefix-tree stack deeper than supported"; return -2; }
-
+// The tree program of one prefix tree from its depth-first event list: cut
+// into n_pieces pieces of similar pixel count, each with a prologue that
+// rebuilds its starting state from the tree's root (no emits).
+static void make_tree_program(const Trie& t, const std::vector<Event>& ev, int max_level, int n_pieces,
+                              Program& tree) {
   std::vector<int64_t> rec_word, rec_pix;
   std::vector<int32_t> rec_cur;
   std::vector<std::vector<int32_t>> rec_stack;
   std::vector<uint8_t> rec_restores;
   Program full;
-  emit_records(wk.ev, full, rec_word, rec_pix, rec_cur, rec_stack, rec_restores);
-  full.stack_depth = wk.max_level;
-  full.n_pixel_words = rec_pix.back();
-
-  // Cut into pieces of similar pixel count; each piece gets a prologue that
-  // rebuilds its starting state from the root (no emits).
+  emit_records(ev, full, rec_word, rec_pix, rec_cur, rec_stack, rec_restores);
   const int64_t nrec = (int64_t)rec_word.size() - 1;
   const int64_t total = rec_pix.back();
-  if (n_pieces < 1) {  // automatic: pieces of 2 segment lengths of tree nodes (at least 64), at most kMaxPieces
-    const int64_t piece_nodes = std::max<int64_t>(64, 2 * ((int64_t)std::max(rx, ry) + 1));
-    n_pieces = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxPieces, nn / piece_nodes));
-  }
   // Each cut sits near its share of the pixels, at the record (within a
   // quarter piece either way) whose starting node is shallowest: the
   // piece's prologue re-walks that node's segment prefix.
@@ -306,11 +222,10 @@ int build_paths_nd(int32_t rx, int32_t ry, int32_t rz, int dims, int n_pieces, P
     cuts.push_back(r);
   }
   cuts.push_back(nrec);
-  Program& tree = p.tree;
   tree.words.clear();
   tree.piece_begin.clear();
   tree.piece_pixels.clear();
-  tree.stack_depth = full.stack_depth;
+  tree.stack_depth = max_level;
   tree.n_pixel_words = 0;
   for (size_t q = 0; q + 1 < cuts.size(); ++q) {
     const int64_t r0 = cuts[q], r1 = cuts[q + 1];
@@ -360,44 +275,171 @@ int build_paths_nd(int32_t rx, int32_t ry, int32_t rz, int dims, int n_pieces, P
     tree.n_pixel_words += pix;
   }
   tree.piece_begin.push_back((int64_t)tree.words.size());
+}
 
-  // Plain program: every canonical segment from scratch (Alg. 1 order).
-  Program& plain = p.plain;
+// The plain program of one tree: the segment of every vector of orientation
+// o from scratch, in canonical order; its pixel words are the tree's nodes
+// along the segment (found by walking its oriented pixels down from root).
+static void make_plain_program(const Trie& t, const std::vector<int32_t>& cstart, const std::vector<int32_t>& clist,
+                               const std::vector<int16_t>& oseq, const std::vector<int64_t>& ptr,
+                               const std::vector<uint8_t>& orient, uint8_t o, int32_t root, int dims,
+                               Program& plain) {
   plain.words.clear();
   plain.stack_depth = 0;
   plain.n_pixel_words = 0;
-  // pixel words of the plain program refer to trie nodes as well: walk each
-  // segment down the tree to recover its node chain.
-  {
-    std::vector<int32_t> chain;
-    for (int64_t c = 0; c < p.n_canon; ++c) {
-      // find node of vector c by walking pixels
-      chain.clear();
-      int32_t n = 0;
-      chain.push_back(0);
-      for (int64_t j = p.ptr[c] + 1; j < p.ptr[c + 1]; ++j) {
-        const int16_t x = p.off[dims * j], y = p.off[dims * j + 1], z = dims == 3 ? p.off[dims * j + 2] : 0;
-        int32_t found = -1;
-        for (int32_t k = cstart[n]; k < cstart[n + 1]; ++k) {
-          const int32_t ch = clist[k];
-          if (t.pix[3 * ch] == x && t.pix[3 * ch + 1] == y && t.pix[3 * ch + 2] == z) { found = ch; break; }
-        }
-        n = found;
-        chain.push_back(n);
+  std::vector<int32_t> chain;
+  const int64_t n_canon = (int64_t)ptr.size() - 1;
+  for (int64_t c = 0; c < n_canon; ++c) {
+    if (orient[c] != o) continue;
+    chain.clear();
+    int32_t n = root;
+    chain.push_back(n);
+    for (int64_t j = ptr[c] + 1; j < ptr[c + 1]; ++j) {
+      const int16_t x = oseq[dims * j], y = oseq[dims * j + 1], z = dims == 3 ? oseq[dims * j + 2] : 0;
+      int32_t found = -1;
+      for (int32_t k = cstart[n]; k < cstart[n + 1]; ++k) {
+        const int32_t ch = clist[k];
+        if (t.pix[3 * ch] == x && t.pix[3 * ch + 1] == y && t.pix[3 * ch + 2] == z) { found = ch; break; }
       }
-      plain.words.push_back(kReset | kEmit | (uint32_t)chain.size());
-      plain.words.push_back((uint32_t)c);
-      plain.words.push_back(0u);  // skip word (resolved to the next record)
-      plain.words.push_back(0u);  // pair count
-      for (int32_t x : chain) plain.words.push_back((uint32_t)x);
-      plain.n_pixel_words += (int64_t)chain.size();
+      n = found;
+      chain.push_back(n);
+    }
+    plain.words.push_back(kReset | kEmit | (uint32_t)chain.size());
+    plain.words.push_back((uint32_t)c);
+    plain.words.push_back(0u);  // skip word (resolved to the next record)
+    plain.words.push_back(0u);  // pair count
+    for (int32_t x : chain) plain.words.push_back((uint32_t)x);
+    plain.n_pixel_words += (int64_t)chain.size();
+  }
+}
+
+int build_paths(int32_t rx, int32_t ry, int n_pieces, Paths& p, std::string& err) {
+  return build_paths_nd(rx, ry, 0, 2, n_pieces, p, err);
+}
+
+int build_paths_nd(int32_t rx, int32_t ry, int32_t rz, int dims, int n_pieces, Paths& p, std::string& err) {
+  if (rx < 0 || ry < 0 || rz < 0 || rx > 4095 || ry > 4095 || rz > 4095) {
+    err = "window radius out of range [0, 4095]";
+    return -1;
+  }
+  if (dims != 2 && dims != 3) { err = "dims must be 2 or 3"; return -1; }
+  if (dims == 2) rz = 0;
+  p = Paths();
+  p.rx = rx;
+  p.ry = ry;
+  p.rz = rz;
+  p.dims = dims;
+  const int64_t nxy = (int64_t)(2 * rx + 1) * (2 * ry + 1);
+  p.n_full = nxy * (2 * rz + 1);
+  p.base = (p.n_full - 1) / 2;
+  p.n_canon = p.n_full - p.base;
+  p.vec.resize((size_t)dims * p.n_canon);
+  p.ptr.assign(p.n_canon + 1, 0);
+  std::vector<int16_t> seg;
+  for (int64_t c = 0; c < p.n_canon; ++c) {
+    const int64_t k = p.base + c;
+    const int dz = (int)(k / nxy) - rz;
+    const int64_t rem = k % nxy;
+    const int dy = (int)(rem / (2 * rx + 1)) - ry, dx = (int)(rem % (2 * rx + 1)) - rx;
+    p.vec[(size_t)dims * c] = (int16_t)dx;
+    p.vec[(size_t)dims * c + 1] = (int16_t)dy;
+    if (dims == 3) {
+      p.vec[(size_t)dims * c + 2] = (int16_t)dz;
+      segment_canonical3(dx, dy, dz, seg);
+    } else {
+      segment_canonical(dx, dy, seg);
+    }
+    p.ptr[c + 1] = p.ptr[c] + (int64_t)seg.size() / dims;
+    p.off.insert(p.off.end(), seg.begin(), seg.end());
+  }
+
+  // Oriented segments: an image's y-major vectors go to the transposed tree
+  // (see Paths) as the sequence (x', y') = (sy, sx) of their pixels, which
+  // starts at (0, 0) and steps one pixel along x'.
+  std::vector<uint8_t> orient((size_t)p.n_canon, 0);
+  std::vector<int16_t> oseq(p.off);
+  bool any_t = false;
+  if (dims == 2) {
+    for (int64_t c = 0; c < p.n_canon; ++c) {
+      const int dx = p.vec[2 * c], dy = p.vec[2 * c + 1];
+      if (std::abs(dy) <= std::abs(dx)) continue;
+      orient[c] = 1;
+      any_t = true;
+      for (int64_t j = p.ptr[c]; j < p.ptr[c + 1]; ++j) {
+        oseq[2 * j] = p.off[2 * j + 1];
+        oseq[2 * j + 1] = p.off[2 * j];
+      }
     }
   }
-  split_program(p, plain, n_pieces);
-  align_program(tree);
-  align_program(plain);
-  resolve_skips(tree);
-  resolve_skips(plain);
+
+  // Prefix trees; node 0 is pixel (0,0[,0]) of the image's tree, node 1 the
+  // root of the transposed tree (when there is one).
+  Trie t;
+  t.slots = dims == 3 ? 18 : 6;
+  const int S5 = t.slots;
+  t.add(-1, 0, 0, 0, 0);
+  const int32_t root_t = any_t ? t.add(-1, 0, 0, 0, 0) : -1;
+  for (int64_t c = 0; c < p.n_canon; ++c) {
+    int32_t n = orient[c] ? root_t : 0;
+    for (int64_t j = p.ptr[c] + 1; j < p.ptr[c + 1]; ++j) {
+      const int16_t x = oseq[dims * j], y = oseq[dims * j + 1], z = dims == 3 ? oseq[dims * j + 2] : 0;
+      const int mx = x - t.pix[3 * n], my = y - t.pix[3 * n + 1], mz = z - t.pix[3 * n + 2];
+      const int slot = dims == 3 ? move_slot3(mx, my, mz) : move_slot(mx, my);
+      int32_t ch = t.child5[(int64_t)S5 * n + slot];
+      if (ch < 0) {
+        ch = t.add(n, x, y, z, t.depth[n] + 1);
+        t.child5[(int64_t)S5 * n + slot] = ch;
+      }
+      n = ch;
+    }
+    t.vec[n] = (int32_t)c;
+  }
+  const int64_t nn = (int64_t)t.parent.size();
+  // subtree sizes (children have larger ids than parents)
+  std::vector<int64_t> sub(nn, 1);
+  for (int64_t n = nn - 1; n > 0; --n)
+    if (t.parent[n] >= 0) sub[t.parent[n]] += sub[n];
+  std::vector<int32_t> cstart(nn + 1, 0), clist;
+  clist.reserve(nn);
+  for (int64_t n = 0; n < nn; ++n) {
+    int32_t cs[18];
+    int m = 0;
+    for (int k = 0; k < S5; ++k) if (t.child5[S5 * n + k] >= 0) cs[m++] = t.child5[S5 * n + k];
+    std::sort(cs, cs + m, [&](int32_t a, int32_t b) { return sub[a] != sub[b] ? sub[a] < sub[b] : a < b; });
+    for (int k = 0; k < m; ++k) clist.push_back(cs[k]);
+    cstart[n + 1] = (int32_t)clist.size();
+  }
+  std::vector<int32_t>().swap(t.child5);
+
+  // Pieces per program: automatic (one per 2 segment lengths of tree nodes,
+  // at least 64, at most kMaxPieces) or n_pieces shared in proportion to the
+  // trees' nodes.
+  auto pieces_for = [&](int64_t nodes) -> int {
+    if (n_pieces < 1) {
+      const int64_t piece_nodes = std::max<int64_t>(64, 2 * ((int64_t)std::max(rx, ry) + 1));
+      return (int)std::max<int64_t>(1, std::min<int64_t>(kMaxPieces, nodes / piece_nodes));
+    }
+    return (int)std::max<int64_t>(1, std::llround((double)n_pieces * (double)nodes / (double)nn));
+  };
+  const int n_trees = root_t >= 0 ? 2 : 1;
+  for (int o = 0; o < n_trees; ++o) {
+    const int32_t root = o ? root_t : 0;
+    // Depth-first walk -> events -> records -> pieces.
+    Walker wk{t, sub, cstart, clist, {}, 0};
+    wk.ev.reserve(sub[root] + 3 * p.n_canon / n_trees);
+    wk.node(root, 0);
+    if (wk.max_level > kMaxStack) { err = "prefix-tree stack deeper than supported"; return -2; }
+    make_tree_program(t, wk.ev, wk.max_level, pieces_for(sub[root]), o ? p.tree_t : p.tree);
+    // Plain program: every segment of the tree from scratch (Alg. 1 order).
+    make_plain_program(t, cstart, clist, oseq, p.ptr, orient, (uint8_t)o, root, dims, o ? p.plain_t : p.plain);
+    split_program(p, o ? p.plain_t : p.plain, pieces_for(sub[root]));
+  }
+  for (Program* prog : {&p.tree, &p.tree_t, &p.plain, &p.plain_t}) {
+    if (prog->piece_begin.empty()) prog->piece_begin.push_back(0);  // no tree: no pieces
+    align_program(*prog);
+    resolve_skips(*prog);
+  }
+  p.root_t = root_t;
 
   p.node_parent = std::move(t.parent);
   p.node_pix.resize(2 * (size_t)nn);

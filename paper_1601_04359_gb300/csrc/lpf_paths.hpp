@@ -92,14 +92,23 @@ struct Paths {
   std::vector<int16_t> vec;          // [n_canon][dims] (dx, dy[, dz])
   std::vector<int64_t> ptr;          // [n_canon + 1] CSR into off
   std::vector<int16_t> off;          // [ptr[n_canon]][dims] (sx, sy[, sz]) pixel offsets
-  // Prefix tree of the canonical segments.
-  std::vector<int32_t> node_parent;  // -1 for the root (pixel (0,0))
-  std::vector<int16_t> node_pix;     // [n_nodes][2] (x, y)
+  // Prefix trees of the canonical segments.  Images: the x-major vectors
+  // (|dx| >= |dy|) form the tree rooted at node 0, in image coordinates; the
+  // y-major vectors (|dy| > |dx|) form the tree rooted at node root_t, in the
+  // coordinates of the transposed image (x' = y, y' = x, so y' < 0 for
+  // dx < 0).  Both trees then hold only segments that step one pixel along x
+  // per node, so most nodes share a staged word window with a neighbour in
+  // the same row.  Volumes: one tree of all vectors (root_t = -1).
+  std::vector<int32_t> node_parent;  // -1 for a root (pixel (0,0))
+  std::vector<int16_t> node_pix;     // [n_nodes][2] (x, y) in its tree's coordinates
   std::vector<int16_t> node_pz;      // [n_nodes] z (3D only, else empty)
   std::vector<int32_t> node_vec;     // canonical index ending here, or -1
-  // Programs: tree walk (shared prefixes) and plain (every segment from scratch).
-  Program tree;
-  Program plain;
+  int32_t root_t = -1;               // root of the transposed tree, -1 when there is none
+  // Programs: tree walk (shared prefixes) and plain (every segment from
+  // scratch), for the image (tree, plain) and its transpose (tree_t, plain_t;
+  // empty when root_t < 0).
+  Program tree, tree_t;
+  Program plain, plain_t;
   int64_t n_nodes() const { return (int64_t)node_parent.size(); }
 };
 
@@ -112,9 +121,10 @@ void segment_canonical(int dx, int dy, std::vector<int16_t>& out_xy);
 // for (dx,dy,dz) in the 3D half-domain (dz > 0, or dz = 0 and (dx,dy) in D).
 void segment_canonical3(int dx, int dy, int dz, std::vector<int16_t>& out_xyz);
 
-// Build tables and both programs, split into n_pieces pieces (n_pieces < 1:
-// one piece per 2 longest-segment lengths of tree nodes, at least 64, and at
-// most kMaxPieces pieces).  A piece repeats a prologue of at most one
+// Build tables and all programs, split into n_pieces pieces in all (shared
+// by the image's and the transpose's programs in proportion to their tree
+// nodes; n_pieces < 1: one piece per 2 longest-segment lengths of tree
+// nodes, at least 64, and at most kMaxPieces pieces per program).  A piece repeats a prologue of at most one
 // segment, cut where the tree is shallow (a few % of the work), and more
 // pieces let more warps share a small tree, whose walk is latency-bound.
 // Returns 0 or a negative status.

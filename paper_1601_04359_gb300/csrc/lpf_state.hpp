@@ -25,7 +25,8 @@ struct Geometry {
   int r32 = 0;     // rx rounded up to a multiple of 32
   int S = 0;       // words per packed row (odd, so that 32 rows hit 32 banks)
   int nbands = 0;  // 32-row bands of translations
-  int rows = 0;    // packed rows = 32*BB*nbg + ry
+  int up = 0;      // halo rows above the translation rows (packed row y = image row y - up)
+  int rows = 0;    // packed rows = 32*BB*nbg + ry + up
   uint32_t band_bytes = 0;   // shared memory of one block's rows (multiple of 16)
   size_t packed_words = 0;   // rows*S plus padding for the last band's bulk copy
   // Volumes (3D): D slices, window rz; every slice is slice_rows packed rows
@@ -37,6 +38,27 @@ struct Geometry {
 
 // T, BB <= 0 pick defaults.
 int make_geometry(int H, int W, int rx, int ry, int T, int BB, Geometry& g);
+// The layout of one side for a fixed shape (T words per thread, BB bands per
+// block, clamped to the bands there are).
+int layout_side(int H, int W, int rx, int ry, int T, int BB, Geometry& g, int up = 0);
+
+// The sides of an image evaluation: side 0 walks the image's program (the
+// x-major vectors; column offsets up to rx, row offsets 0 .. min(rx, ry)),
+// side 1 the transpose's program on the transposed image (the y-major
+// vectors; H and W swapped, column offsets up to ry, row offsets -h .. h,
+// h = min(rx, ry - 1), so its packed rows have h halo rows above too).  Both use the same words per thread.  Their packed rows
+// share one work area, side 1 from word off1 (a 16-byte boundary); their
+// band groups are numbered side 0 first.
+struct Sides {
+  Geometry g[2];
+  int n = 1;                 // 1: no y-major vectors (ry = 0) or a volume
+  size_t off1 = 0;           // words
+  size_t packed_words = 0;   // both sides
+  uint32_t band_bytes = 0;   // the larger side's
+  int nbg = 0;               // band groups of both sides
+  int threads = 0;           // walk block: one warp per tile of the larger side, at most 16
+};
+int make_sides(const Paths& paths, int H, int W, int T, int BB, Sides& s);
 // The same for a D x H x W volume and window (rx, ry, rz).
 int make_geometry3(int D, int H, int W, int rx, int ry, int rz, int T, int BB, Geometry& g);
 
@@ -45,13 +67,16 @@ struct Tuned {
   int H = 0, W = 0, T = 0, BB = 0;
 };
 
-// A program with its pixel words converted to packed offsets for one width.
+// The programs of an evaluation with their pixel words converted to packed
+// offsets for one row layout per side: side 0's groups, then side 1's.
 struct Baked {
   int W = -1, S = -1, r32 = -1, slice_rows = 0;
+  int H = -1, S1 = -1, r32_1 = -1;  // side 1 (-1: none)
   int T = 0, BB = 0;  // a launch shape whose row layout the program was baked for
   uint32_t* d_words = nullptr;   // 16-byte groups (4 words each)
   uint32_t* d_piece = nullptr;   // piece starts, in groups [n_pieces + 1]
-  int n_pieces = 0;
+  int n_pieces = 0;              // both sides
+  int n_pieces0 = 0;             // side 0's (pieces n_pieces0.. belong to side 1)
 };
 
 // Tables of the swap-delta kernel for one extended cell width.
@@ -87,7 +112,6 @@ struct lpf_paths {
   size_t ext_cap = 0;
   uint32_t* d_sel = nullptr;     // work area: packed translation selection (Monte-Carlo variant)
   size_t sel_cap = 0;            // words
-  const uint32_t* d_sel_active = nullptr;  // selection of the walk being enqueued (or null)
   uint8_t* d_z = nullptr;        // work area: phase-0 counts per (vector, translation) of swap deltas
   size_t z_cap = 0;              // bytes
   int checked = 0;               // 1: kernels that read the image flag pixels other than 0 or 1
@@ -97,8 +121,10 @@ struct lpf_paths {
 namespace lpf {
 // Record a CUDA error for lpf_last_error_message(); returns the status code.
 int set_cuda_error(cudaError_t e);
-// Upload/convert `prog` for geometry g (no-op if already baked for g.W/S).
-int bake(lpf_paths* p, const Program& prog, const Geometry& g, Baked& b);
+// Upload/convert prog0 for side geometry g0 and, when prog1 is not null,
+// prog1 for g1 (no-op if already baked for these row layouts).
+int bake(lpf_paths* p, const Program& prog0, const Geometry& g0, const Program* prog1, const Geometry* g1,
+         Baked& b);
 // Make sure the handle is bound to the current device and has a status word
 // and a packed-image area of at least `words`.
 int ensure_device(lpf_paths* p, size_t packed_words);

@@ -1,5 +1,6 @@
-"""The size envelope of lpf_full: the largest supported widths and windows
-against sampled oracle counts, and a clean LPF_EUNSUPPORTED beyond them."""
+"""The size envelope of lpf_full: the largest supported widths, heights and
+windows against sampled oracle counts, and a clean LPF_EINVAL or
+LPF_EUNSUPPORTED beyond them."""
 import numpy as np
 import pytest
 import torch
@@ -30,6 +31,13 @@ def test_widest_image(gpu_lib):
     _sampled_check(gpu_lib, img, 200, 12, 24, 2)
 
 
+def test_widest_and_tallest_images_at_the_size_limit(gpu_lib):
+    # 8192 words of translations in a row on one side: the image's (wide) or
+    # the transpose's (tall)
+    _sampled_check(gpu_lib, synth.random_binary(40, 8192, 0.6, 5), 200, 12, 16, 6)
+    _sampled_check(gpu_lib, synth.random_binary(8192, 40, 0.6, 7), 12, 200, 16, 8)
+
+
 def test_full_domain_300(gpu_lib):
     img = synth.clustered_disks(300, 300, 0.35, seed=3)
     _sampled_check(gpu_lib, img, 299, 299, 16, 4)
@@ -37,10 +45,19 @@ def test_full_domain_300(gpu_lib):
 
 def test_beyond_the_envelope_is_refused(gpu_lib):
     p = gpu_lib.lpf_build_paths(8, 4)
+    for shape in ((16, 8193), (8193, 16)):
+        with pytest.raises(gpu_lib.LpfError) as e:
+            gpu_lib.lpf_full(torch.zeros(shape, dtype=torch.uint8, device="cuda"), p)
+        assert e.value.code == -1  # LPF_EINVAL
+    # halo rows of min(rx, ry) = 299 x 277 words of a 8192-wide row: beyond shared memory
+    q = gpu_lib.lpf_build_paths(299, 299)
     with pytest.raises(gpu_lib.LpfError) as e:
-        gpu_lib.lpf_full(torch.zeros((16, 4100), dtype=torch.uint8, device="cuda"), p)
-    assert e.value.code in (-1, -5)  # LPF_EINVAL or LPF_EUNSUPPORTED
-    q = gpu_lib.lpf_build_paths(4, 1500)  # halo rows of 1500 x 130 words: far beyond shared memory
-    with pytest.raises(gpu_lib.LpfError) as e:
-        gpu_lib.lpf_full(torch.zeros((1600, 4096), dtype=torch.uint8, device="cuda"), q)
-    assert e.value.code == -5
+        gpu_lib.lpf_full(torch.zeros((320, 8192), dtype=torch.uint8, device="cuda"), q)
+    assert e.value.code == -5  # LPF_EUNSUPPORTED
+
+
+def test_long_one_sided_windows_fit_on_the_transposed_side(gpu_lib):
+    # a window 4 x 1500: the y-major vectors run along rows of the transposed
+    # image, whose halo is min(rx, ry - 1) = 4 rows, so the image fits
+    img = synth.random_binary(1600, 64, 0.7, 9)
+    _sampled_check(gpu_lib, img, 4, 1500, 12, 10)

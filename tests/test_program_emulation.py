@@ -1,7 +1,8 @@
 """Host side of the walk, checked on the CPU: the programs the library builds
-and bakes (prefix tree of all canonical segments, pieces with prologues, skip
-words, pixel pairs) are walked by a C++ emulation of the kernels' semantics
-(tests/walk_emulator.cpp) and compared with the oracle entry by entry."""
+and bakes (prefix trees of the x-major segments and of the transposed y-major
+segments, pieces with prologues, skip words, pixel pairs) are walked by a C++
+emulation of the kernels' semantics (tests/walk_emulator.cpp) over the image
+and its transpose and compared with the oracle entry by entry."""
 import ctypes
 import os
 import shutil
@@ -28,6 +29,9 @@ def emulator(tmp_path_factory):
     lib.emulate_walk.restype = ctypes.c_int
     lib.emulate_walk.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.emulate_walk_sel.restype = ctypes.c_int
+    lib.emulate_walk_sel.argtypes = [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int] * 5 + [ctypes.c_void_p,
+                                                                                               ctypes.c_void_p]
     lib.emulate_walk3.restype = ctypes.c_int
     lib.emulate_walk3.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 7 + [ctypes.c_void_p, ctypes.c_void_p]
     return lib
@@ -104,3 +108,22 @@ def test_volume_programs_walk_to_the_oracle_counts(emulator, shape, window, T):
     assert emulator.emulate_walk3(v.ctypes.data, D, H, W, rx, ry, rz, T, counts.ctypes.data, stats.ctypes.data) == 0
     np.testing.assert_array_equal(counts, oracle.lpf_full3(vol, rx, ry, rz))
     assert 0 < stats[0] <= stats[1]
+
+
+@pytest.mark.parametrize("H,W,rx,ry,frac,seed", [(40, 50, 20, 15, 0.1, 1), (33, 70, 69, 32, 0.05, 3),
+                                                 (30, 30, 29, 29, 0.3, 4)])
+def test_selected_start_translations(emulator, H, W, rx, ry, frac, seed):
+    # The Monte-Carlo variant counts only selected start pixels: a segment of
+    # the transposed tree must start where the image's segment starts (a
+    # vector with dx < 0 runs to y' < 0 over the transposed image).
+    img = synth.squares(H, W, 4, 0.3, seed=seed)
+    rng = np.random.default_rng(seed)
+    sel = np.zeros(H * W, np.uint8)
+    sel[rng.choice(H * W, max(1, int(frac * H * W)), replace=False)] = 1
+    sel = sel.reshape(H, W)
+    counts = np.zeros((2, (2 * rx + 1) * (2 * ry + 1)), np.int64)
+    stats = np.zeros(4, np.int64)
+    assert emulator.emulate_walk_sel(img.ctypes.data, sel.ctypes.data, H, W, rx, ry, 2, counts.ctypes.data,
+                                     stats.ctypes.data) == 0
+    _, _, base = oracle.window_sizes(rx, ry)
+    np.testing.assert_array_equal(counts[:, base:], oracle.lpf_full_selected(img, rx, ry, sel)[:, base:])

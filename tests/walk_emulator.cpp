@@ -28,24 +28,27 @@ inline uint32_t funnel_r(uint32_t lo, uint32_t hi, uint32_t s) {
 
 }  // namespace
 
-// Walk every unit of `prog` over the packed layout of the kernels.  Images:
-// one slice, packed row y = image row y mod H.  Volumes: slices of
+// Walk every unit of `prog` over the packed layout of the kernels, adding to
+// counts and stats.  rx: the program's column offsets lie in [-rx, rx]; ry:
+// its row offsets in [-up, ry] (images) or [-ry, ry] (volumes).  Images: one
+// slice, packed row y = image row (y - up) mod H.  Volumes: slices of
 // Hs = 32 nb + 2 ry packed rows (image row (y'' - ry) mod H of slice z' mod D),
 // D + rz slices; a translation row of slice z starts at packed row z Hs + y.
-static int emulate_impl(const Paths& p, const Program& prog, const uint8_t* img, int D, int H, int W, int T,
-                        bool volume, int64_t* counts, int64_t* stats) {
-  const int rx = p.rx, ry = p.ry, rz = p.rz;
+static int emulate_side(const Paths& p, const Program& prog, const uint8_t* img, int D, int H, int W, int rx,
+                        int ry, int up, int T, bool volume, int64_t* counts, int64_t* stats,
+                        const uint8_t* sel = nullptr) {
+  const int rz = p.rz;
   const int nw = (W + 31) / 32, G = (nw + T - 1) / T, r32 = ((rx + 31) / 32) * 32;
   int S = G * T + ((r32 + rx) >> 5) + 1;
   if (!(S & 1)) ++S;
   const int nb = (H + 31) / 32;
   const int Hs = volume ? (32 * nb + 2 * ry + 3) & ~3 : 0;  // as the kernels: a multiple of 4 rows
-  const int rows = volume ? (D + rz) * Hs : 32 * nb + ry;
+  const int rows = volume ? (D + rz) * Hs : 32 * nb + ry + up;
   // packed rows: bit b of word k = pixel at column (32k + b - r32) mod W
   std::vector<uint32_t> packed((size_t)rows * S + 4, 0);
   for (int r = 0; r < rows; ++r) {
     const int zs = volume ? (r / Hs) % D : 0;
-    const int yi = volume ? (((r % Hs) - ry) % H + H) % H : r % H;
+    const int yi = volume ? (((r % Hs) - ry) % H + H) % H : ((r - up) % H + H) % H;
     for (int k = 0; k < S; ++k) {
       uint32_t bits = 0;
       for (int b = 0; b < 32; ++b) {
@@ -57,9 +60,8 @@ static int emulate_impl(const Paths& p, const Program& prog, const uint8_t* img,
   }
   std::vector<uint32_t> w;
   std::vector<int64_t> piece;
-  bake_words(p, prog, S, r32, w, piece, Hs, volume ? ry : 0);
+  bake_words(p, prog, S, r32, w, piece, Hs, volume ? ry : up);
   const int64_t nf = p.n_full, base = p.base;
-  std::memset(counts, 0, sizeof(int64_t) * 2 * nf);
   int64_t walked = 0, skips = 0, pairs = 0;
   const int L = 32 * T;
   std::vector<uint32_t> valid(L), m1(L), m0(L), st1((kMaxStack + 1) * L), st0((kMaxStack + 1) * L);
@@ -79,6 +81,9 @@ static int emulate_impl(const Paths& p, const Program& prog, const uint8_t* img,
             if (y < H && j < nw) {
               const int rem = W - 32 * j;
               v = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+              if (sel)  // selected start translations only (Monte-Carlo variant)
+                for (int b = 0; b < 32 && 32 * j + b < W; ++b)
+                  if (!sel[(size_t)y * W + 32 * j + b]) v &= ~(1u << b);
             }
             valid[lane * T + t] = m1[lane * T + t] = m0[lane * T + t] = v;
           }
@@ -149,12 +154,42 @@ static int emulate_impl(const Paths& p, const Program& prog, const uint8_t* img,
           }
         }
       }
+  stats[0] += walked;
+  stats[1] += prog.n_pixel_words * (int64_t)nb * G * (volume ? D : 1);
+  stats[2] += skips;
+  stats[3] += pairs;
+  return 0;
+}
+
+static void mirror(const Paths& p, int64_t* counts) {
+  const int64_t nf = p.n_full, base = p.base;
   for (int64_t j = base + 1; j < nf; ++j)
     for (int q = 0; q < 2; ++q) counts[q * nf + nf - 1 - j] = counts[q * nf + j];
-  stats[0] = walked;
-  stats[1] = prog.n_pixel_words * (int64_t)nb * G * (volume ? D : 1);
-  stats[2] = skips;
-  stats[3] = pairs;
+}
+
+// An image: the image's program on the image (column offsets up to rx, rows
+// 0 .. min(rx, ry)) and the transpose's program on the transposed image
+// (column offsets up to ry, rows -h .. h with h = min(rx, ry - 1)).
+// sel != null: only the selected start translations count (sel[y][x]).
+static int emulate_impl(const Paths& p, bool standard, const uint8_t* img, int H, int W, int T, int64_t* counts,
+                        int64_t* stats, const uint8_t* sel = nullptr) {
+  std::memset(counts, 0, sizeof(int64_t) * 2 * p.n_full);
+  for (int k = 0; k < 4; ++k) stats[k] = 0;
+  emulate_side(p, standard ? p.plain : p.tree, img, 1, H, W, p.rx, std::min(p.rx, p.ry), 0, T, false, counts,
+               stats, sel);
+  if (p.root_t >= 0) {
+    // the transposed image; its translation (x', y') is the image's (y', x')
+    std::vector<uint8_t> imgT((size_t)H * W), selT(sel ? (size_t)H * W : 0);
+    for (int y = 0; y < H; ++y)
+      for (int x = 0; x < W; ++x) {
+        imgT[(size_t)x * H + y] = img[(size_t)y * W + x];
+        if (sel) selT[(size_t)x * H + y] = sel[(size_t)y * W + x];
+      }
+    const int h = std::min(p.rx, p.ry - 1);
+    emulate_side(p, standard ? p.plain_t : p.tree_t, imgT.data(), 1, W, H, p.ry, h, h, T, false, counts, stats,
+                 sel ? selT.data() : nullptr);
+  }
+  mirror(p, counts);
   return 0;
 }
 
@@ -165,7 +200,17 @@ extern "C" int emulate_walk(const uint8_t* img, int H, int W, int rx, int ry, in
   Paths p;
   std::string err;
   if (build_paths(rx, ry, 0, p, err)) return -1;
-  return emulate_impl(p, standard ? p.plain : p.tree, img, 1, H, W, T, false, counts, stats);
+  return emulate_impl(p, standard != 0, img, H, W, T, counts, stats);
+}
+
+// The walk over selected start translations only (sel[y][x] != 0; the
+// Monte-Carlo variant), tree program.
+extern "C" int emulate_walk_sel(const uint8_t* img, const uint8_t* sel, int H, int W, int rx, int ry, int T,
+                                int64_t* counts, int64_t* stats) {
+  Paths p;
+  std::string err;
+  if (build_paths(rx, ry, 0, p, err)) return -1;
+  return emulate_impl(p, false, img, H, W, T, counts, stats, sel);
 }
 
 // The same for a volume vol[z][y][x] (D x H x W) and window (rx, ry, rz).
@@ -174,5 +219,9 @@ extern "C" int emulate_walk3(const uint8_t* vol, int D, int H, int W, int rx, in
   Paths p;
   std::string err;
   if (build_paths_nd(rx, ry, rz, 3, 0, p, err)) return -1;
-  return emulate_impl(p, p.tree, vol, D, H, W, T, true, counts, stats);
+  std::memset(counts, 0, sizeof(int64_t) * 2 * p.n_full);
+  for (int k = 0; k < 4; ++k) stats[k] = 0;
+  emulate_side(p, p.tree, vol, D, H, W, rx, ry, 0, T, true, counts, stats);
+  mirror(p, counts);
+  return 0;
 }
