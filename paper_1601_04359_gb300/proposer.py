@@ -13,12 +13,18 @@ Training data come from uniform-proposal runs with seeds distinct from the
 evaluation seeds (an optional second round adds candidates drawn by runs that
 already use the network; measured, it lowers the gain).
 
-Evaluation (swaps to target error): for each evaluation seed, a uniform run
-of N evaluations reaches error e_U; the model-proposal run (same initial cell,
-seed and temperature schedule) is followed until its error first falls to
+Evaluation (swaps to target error), two protocols.  First crossing: for each
+evaluation seed, a uniform run of N evaluations reaches error e_U; the
+model-proposal run (same initial cell, seed and temperature schedule, the
+schedule of an N-evaluation run) is followed until its error first falls to
 e_U; the ratio of evaluations is the gain, reported as the median over seeds.
+Own budget: annealers with a budget of N/k evaluations (each with the
+schedule of its budget) end at e_M(k) with the network's proposals and at
+e_u(k) with uniform ones; a seed's gain is the largest k whose e_M(k) <= e_U,
+the control's the same for e_u(k).
 
     python -m paper_1601_04359_gb300.proposer --evaluate [--n-step 100000]
+    python -m paper_1601_04359_gb300.proposer --evaluate-budget [--ks 2 3 4 6]
 """
 from __future__ import annotations
 
@@ -200,9 +206,65 @@ def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22,
     }
 
 
+def evaluate_budget(n_step: int = 100000, ks=(2, 3, 4, 6), train_seeds=(11, 12, 13),
+                    eval_seeds=(21, 22, 23, 24, 25, 26, 27), snapshots: int = 256, n: int = 64, epochs: int = 8,
+                    tau: float = 0.35, eps: float = 0.4, r: int = 64, cell_size: int = 128, orig_size: int = 512,
+                    net_seed: int = 3):
+    """Swaps-to-target gain with each annealer run to its own budget.
+
+    For each evaluation seed a uniform-proposal annealer with a budget of
+    N = n_step evaluations ends at error e_U; annealers with a budget of N/k
+    (their own temperature schedule, same initial cell, seed and initial
+    temperature) end at e_M(k) with the network's proposals and at e_u(k)
+    with uniform ones (the control).  The seed's gain is the largest k in
+    ks with e_M(k) <= e_U (1 if none); the control's gain is the same with
+    e_u(k).  Reported: the medians over the evaluation seeds."""
+    import torch
+
+    import synth
+    C = cell_size
+    paths, target, cell0 = annealing_problem(r=r, cell_size=C, orig_size=orig_size)
+    n1 = int(cell0.sum())
+    cells0 = {s: synth.exact_fraction_shuffle(C, C, n1, seed=1000 + s) for s in eval_seeds}
+    e_full = {}
+    t_max = None
+    t0 = time.perf_counter()
+    for s in eval_seeds:
+        _, st, _ = run_until(paths, target, cells0[s], n_step, s, t_max=t_max or 0.0)
+        t_max = t_max or st["t_max"]
+        e_full[s] = st["error"]
+    net = lpf.lpf_cnn_create(C, C, seed=net_seed)
+    data = [collect(paths, target, synth.exact_fraction_shuffle(C, C, n1, seed=s), n_step, s, snapshots, n,
+                    t_max=t_max, spacing="early") for s in train_seeds]
+    train(net, torch.cat([d[0] for d in data]), torch.cat([d[1] for d in data]), torch.cat([d[2] for d in data]),
+          epochs=epochs)
+    per_seed = []
+    for s in eval_seeds:
+        row = {"seed": s, "uniform_error": e_full[s], "model_error": {}, "uniform_k_error": {}}
+        for k in ks:
+            _, st_m, _ = run_until(paths, target, cells0[s], n_step // k, s, t_max=t_max, net=net, eps=eps, tau=tau)
+            _, st_u, _ = run_until(paths, target, cells0[s], n_step // k, s, t_max=t_max)
+            row["model_error"][k] = st_m["error"]
+            row["uniform_k_error"][k] = st_u["error"]
+        row["gain"] = max([1] + [k for k in ks if row["model_error"][k] <= e_full[s]])
+        row["control_gain"] = max([1] + [k for k in ks if row["uniform_k_error"][k] <= e_full[s]])
+        per_seed.append(row)
+    gains = sorted(r_["gain"] for r_ in per_seed)
+    control = sorted(r_["control_gain"] for r_ in per_seed)
+    return {
+        "workload": f"{C}x{C} cell, |v|<={r}, target from {orig_size}x{orig_size} clustered disks (f=0.3)",
+        "n_step_uniform": n_step, "ks": list(ks), "tau": tau, "epsilon": eps, "train_seeds": list(train_seeds),
+        "eval_seeds": list(eval_seeds), "median_gain": gains[len(gains) // 2],
+        "median_control_gain": control[len(control) // 2], "per_seed": per_seed,
+        "seconds": time.perf_counter() - t0,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--evaluate", action="store_true")
+    ap.add_argument("--evaluate", action="store_true", help="first-crossing protocol (one schedule of N)")
+    ap.add_argument("--evaluate-budget", action="store_true", help="own-budget protocol (schedules of N/k)")
+    ap.add_argument("--ks", type=int, nargs="+", default=[2, 3, 4, 6])
     ap.add_argument("--n-step", type=int, default=100000)
     ap.add_argument("--snapshots", type=int, default=256)
     ap.add_argument("--epochs", type=int, default=8)
@@ -225,6 +287,11 @@ def main():
                                   snapshots=a.snapshots, epochs=a.epochs, taus=tuple(a.tau), epss=tuple(a.eps),
                                   on_policy=a.on_policy, spacing=a.spacing, refreshes=tuple(a.refresh),
                                   loss=a.loss, beta=a.beta, r=a.r, cell_size=a.cell, orig_size=a.orig)),
+              flush=True)
+    if a.evaluate_budget:
+        print(json.dumps(evaluate_budget(n_step=a.n_step, ks=tuple(a.ks), train_seeds=tuple(a.train_seeds),
+                                         eval_seeds=tuple(a.eval_seeds), snapshots=a.snapshots, epochs=a.epochs,
+                                         tau=a.tau[0], eps=a.eps[0], r=a.r, cell_size=a.cell, orig_size=a.orig)),
               flush=True)
 
 
