@@ -268,10 +268,10 @@ def extra_proposer(lpf):
     First crossing (5 evaluation seeds): ratio = N / evaluations of the
     network's run (the schedule of an N-evaluation run) until it first
     reaches the uniform run's final error.  Own budget (7 evaluation seeds):
-    the largest k in {2, 3, 4, 6} for which an annealer with the network and
-    a budget of N/k evaluations (its own schedule) ends at or below the
-    uniform N-evaluation run's error; the control is the same for uniform
-    annealers with budget N/k.  Medians over the seeds."""
+    the largest k in {2, 3, 4, 6} for which annealers with the network and a
+    budget of N/j evaluations (their own schedule), every j <= k, end at or
+    below the uniform N-evaluation run's error; the control is the same for
+    uniform annealers.  Medians over the seeds."""
     from paper_1601_04359_gb300 import proposer
     t0 = time.perf_counter()
     res = proposer.evaluate(n_step=100000)

@@ -20,8 +20,8 @@ schedule of an N-evaluation run) is followed until its error first falls to
 e_U; the ratio of evaluations is the gain, reported as the median over seeds.
 Own budget: annealers with a budget of N/k evaluations (each with the
 schedule of its budget) end at e_M(k) with the network's proposals and at
-e_u(k) with uniform ones; a seed's gain is the largest k whose e_M(k) <= e_U,
-the control's the same for e_u(k).
+e_u(k) with uniform ones; a seed's gain is the largest k such that every
+budget N/j, j <= k, reached e_M(j) <= e_U; the control's the same for e_u.
 
     python -m paper_1601_04359_gb300.proposer --evaluate [--n-step 100000]
     python -m paper_1601_04359_gb300.proposer --evaluate-budget [--ks 2 3 4 6]
@@ -206,6 +206,17 @@ def evaluate(n_step: int = 100000, train_seeds=(11, 12, 13), eval_seeds=(21, 22,
     }
 
 
+def _budget_gain(ks, err, e_ref) -> int:
+    """Largest k of ks (ascending) such that the runs with every budget N/j,
+    j <= k in ks, ended at or below e_ref (1 if the smallest k already fails)."""
+    gain = 1
+    for k in sorted(ks):
+        if err[k] > e_ref:
+            break
+        gain = k
+    return gain
+
+
 def evaluate_budget(n_step: int = 100000, ks=(2, 3, 4, 6), train_seeds=(11, 12, 13),
                     eval_seeds=(21, 22, 23, 24, 25, 26, 27), snapshots: int = 256, n: int = 64, epochs: int = 8,
                     tau: float = 0.35, eps: float = 0.4, r: int = 64, cell_size: int = 128, orig_size: int = 512,
@@ -217,8 +228,9 @@ def evaluate_budget(n_step: int = 100000, ks=(2, 3, 4, 6), train_seeds=(11, 12, 
     (their own temperature schedule, same initial cell, seed and initial
     temperature) end at e_M(k) with the network's proposals and at e_u(k)
     with uniform ones (the control).  The seed's gain is the largest k in
-    ks with e_M(k) <= e_U (1 if none); the control's gain is the same with
-    e_u(k).  Reported: the medians over the evaluation seeds."""
+    ks such that e_M(j) <= e_U for every j <= k in ks (1 if none); the
+    control's gain is the same with e_u.  Reported: the medians over the
+    evaluation seeds."""
     import torch
 
     import synth
@@ -246,8 +258,8 @@ def evaluate_budget(n_step: int = 100000, ks=(2, 3, 4, 6), train_seeds=(11, 12, 
             _, st_u, _ = run_until(paths, target, cells0[s], n_step // k, s, t_max=t_max)
             row["model_error"][k] = st_m["error"]
             row["uniform_k_error"][k] = st_u["error"]
-        row["gain"] = max([1] + [k for k in ks if row["model_error"][k] <= e_full[s]])
-        row["control_gain"] = max([1] + [k for k in ks if row["uniform_k_error"][k] <= e_full[s]])
+        row["gain"] = _budget_gain(ks, row["model_error"], e_full[s])
+        row["control_gain"] = _budget_gain(ks, row["uniform_k_error"], e_full[s])
         per_seed.append(row)
     gains = sorted(r_["gain"] for r_ in per_seed)
     control = sorted(r_["control_gain"] for r_ in per_seed)
