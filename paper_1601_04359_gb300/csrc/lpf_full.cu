@@ -15,12 +15,13 @@
 // the image rows of a band group (BB bands of 32 rows, all words of the row)
 // in shared memory with one bulk copy; its warps then take units, one piece
 // of the evaluation program on one tile, from the band group's counter.  The
-// program is a depth-first walk of the prefix tree of all canonical
-// segments: each tree node ANDs one shifted image word (two nodes of a pair
-// share the staged words), a node that ends a canonical vector is counted
-// (popc + warp sum + one atomic per phase), masks of branching nodes are kept
-// on a per-thread stack, and a subtree whose count is zero for the whole tile
-// is skipped.
+// program is a depth-first walk of a prefix tree of canonical segments: each
+// tree node ANDs one shifted image word (two nodes of a pair share the staged
+// words), a node that ends a canonical vector is counted (popc + warp sum +
+// one atomic per phase), masks of branching nodes are kept on a per-thread
+// stack, and a subtree whose count is zero for the whole tile is skipped.
+// Images have two sides: the tree of the x-major vectors over the image and
+// the tree of the y-major vectors, transposed, over the transposed image.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
