@@ -440,6 +440,25 @@ def _only_batch_256(lpf, repeat, shape):
     assert lpf.lpf_batch_status(b) == 0
 
 
+def _only_s2(lpf, repeat, shape):
+    """The S2 baseline: s2_fft of the 512x512 ellipses (phase 1), exact S2
+    counts of the 128x128 clustered cell and the S2 error changes of 1024
+    candidate exchanges there."""
+    import torch
+
+    import synth
+    img = torch.from_numpy(synth.ellipses_512()).cuda()
+    cell = synth.clustered_cell_128()
+    d = torch.from_numpy(cell).cuda()
+    pairs = torch.from_numpy(synth.swap_candidates(cell, 1024, seed=0)).cuda()
+    for _ in range(1 + repeat):
+        lpf.s2_fft(img, 1)
+        counts = lpf.s2_counts(d)
+        target = (counts.double() / cell.size).float() * 0.9
+        lpf.s2_delta_swap(d, pairs, target=target, counts=counts, want_dcounts=False, want_de=True)
+    torch.cuda.synchronize()
+
+
 def _only_cnn_train(lpf, repeat, shape):
     import numpy as np
     import torch
@@ -463,6 +482,7 @@ PROFILE_WORKLOADS = {
     "delta_128": _only_delta_128,
     "sa_128": _only_sa_128,
     "batch_256": _only_batch_256,
+    "s2": _only_s2,
 }
 
 

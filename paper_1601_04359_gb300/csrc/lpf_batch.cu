@@ -12,8 +12,9 @@
 // rows x 32T translations) and its own words per thread T, chosen by a
 // waste/load cost model or by the batch autotuner.  The walk kernel visits a
 // host-built list of band-group slots (every band group of every image gets
-// slots in proportion to its work, heaviest first) at the grid stride; for
-// each it stages the band group's rows (one bulk copy, skipped if already
+// slots in proportion to its work, heaviest first, then one more each), a
+// block claiming the next slot from a counter whenever it is free; for each
+// it stages the band group's rows (one bulk copy, skipped if already
 // staged) and its warps pull units (tile, program piece) from that band
 // group's counter until none are left, so warps whose tiles skip zero-count
 // subtrees take more units instead of waiting for the others.
@@ -32,7 +33,9 @@ namespace lpf {
 constexpr int kBatchWarps = 8;
 constexpr int kBatchThreads = 32 * kBatchWarps;
 
-constexpr int kBatchCtlUnits = 4;  // control words: [0] status, [kBatchCtlUnits + g] unit counter of band group g
+// control words: [0] status, [1] slot counter, [kBatchCtlUnits + g] unit counter of band group g
+constexpr int kBatchCtlSlot = 1;
+constexpr int kBatchCtlUnits = 4;
 
 // One side of one image (the image with the x-major vectors' program, or
 // its transpose with the y-major vectors' program; both add to the image's
@@ -111,14 +114,22 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_walk_kernel(const Batc
                                                                    int n_slots, int* __restrict__ ctl) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ __align__(8) uint64_t bar;
-  __shared__ int s_abort, s_done;
+  __shared__ int s_abort, s_done, s_slot;
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) { mbar_init(&bar, 1); s_abort = 0; }
   __syncthreads();
   uint32_t parity = 0;
   int cur_img = -1, cur_bg = -1;
   bool copy_pending = false;
-  for (int k = blockIdx.x; k < n_slots; k += gridDim.x) {
+  for (;;) {
+    // the next slot, claimed when this block is free (the slot list ends
+    // with one more slot per band group, heaviest first, so that blocks
+    // left without work help the band groups that still have units)
+    if (threadIdx.x == 0) s_slot = atomicAdd(ctl + kBatchCtlSlot, 1);
+    __syncthreads();
+    const int k = s_slot;
+    __syncthreads();  // s_slot is rewritten next round
+    if (k >= n_slots) break;
     const BatchSlot sl = slots[k];
     const BatchDesc& b = d[sl.img];
     const int n_tiles = b.G * b.BB;
@@ -365,6 +376,9 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
         const int n = std::max(1, (int)std::lround(bg_work[i] / per_slot));
         for (int c = 0; c < n; ++c) slots.push_back({i, bg, bt->desc[i].bg0 + bg});
       }
+    // the sweep: every band group once more, heaviest first
+    for (int i : order)
+      for (int bg = 0; bg < bt->desc[i].nbg; ++bg) slots.push_back({i, bg, bt->desc[i].bg0 + bg});
     bt->n_slots = (int)slots.size();
     if (bt->d_slots) { cudaFree(bt->d_slots); bt->d_slots = nullptr; }
     if ((e = cudaMalloc(&bt->d_slots, sizeof(BatchSlot) * slots.size())) != cudaSuccess) return set_cuda_error(e);
