@@ -124,13 +124,12 @@ __global__ void __launch_bounds__(kDeltaThreads) z_init_kernel(const uint8_t* __
     const int o0 = __ldg(g.dptr + v), L1 = __ldg(g.dptr + v + 1) - o0;
     int dx, dy;
     delta_vector(g, v, dx, dy);
-    const bool ymajor = dy > (dx < 0 ? -dx : dx);
+    const int m = delta_shear(dx, dy);
     uint8_t* zv = z + (int64_t)v * hw;
     for (int p = threadIdx.x; p < hw; p += blockDim.x) {
-      // p runs over the vector's layout (column-major for y-major vectors)
+      // p runs over the vector's sheared layout (delta_z_index)
       int x, y;
-      if (ymajor) { x = p / g.H; y = p - x * g.H; }
-      else        { y = p / g.W; x = p - y * g.W; }
+      delta_z_translation(g, dx, dy, m, p, x, y);
       const uint8_t* base = sm + (y + g.ry) * g.We + (x + g.rx);
       int c = 0;
       for (int k = 0; k < L1; ++k) c += base[__ldg(g.doff + o0 + k)] == 0;
@@ -246,7 +245,11 @@ static int bake_delta(lpf_paths* p, int W, int want_chunks, DeltaTables& t) {
   t.want = want_chunks;
   t.n_chunks = (int)chunk.size() - 1;
   t.max_chunk_vecs = 0;
-  for (size_t c = 0; c + 1 < chunk.size(); ++c) t.max_chunk_vecs = std::max(t.max_chunk_vecs, chunk[c + 1] - chunk[c]);
+  t.max_chunk_entries = 0;
+  for (size_t c = 0; c + 1 < chunk.size(); ++c) {
+    t.max_chunk_vecs = std::max(t.max_chunk_vecs, chunk[c + 1] - chunk[c]);
+    t.max_chunk_entries = std::max(t.max_chunk_entries, ptr[chunk[c + 1]] - ptr[chunk[c]]);
+  }
   return LPF_OK;
 }
 
@@ -272,6 +275,7 @@ int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g) {
   g.counts = nullptr;
   g.phase_mask = 3;
   g.max_chunk_vecs = p->delta.max_chunk_vecs;
+  g.max_chunk_entries = p->delta.max_chunk_entries;
   g.sel_ext = nullptr;
   g.z = nullptr;
   g.off16 = p->delta.d_off16;
@@ -329,9 +333,9 @@ int delta_prepare(lpf_paths* p, int H, int W, int K) {
   rc = bake_delta(p, W, occ * g_sms, p->delta);
   if (rc) return rc;
   {
-    // the persistent kernel also keeps its chunk's counts and targets: check
+    // the persistent kernel also keeps its chunk's counts, targets and lookup tables: check
     // the chunking once more with the size it produced
-    const size_t persist = ext + (size_t)p->delta.max_chunk_vecs * 2 * (sizeof(long long) + sizeof(float));
+    const size_t persist = persistent_smem_bytes(ext, p->delta.max_chunk_vecs, p->delta.max_chunk_entries);
     int occ2 = 0;
     if ((int64_t)persist <= g_delta_max_smem &&
         (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, sa_persistent_kernel_entry(), kDeltaThreads,

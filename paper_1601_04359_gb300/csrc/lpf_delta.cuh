@@ -30,11 +30,13 @@ struct DeltaArgs {
   const int64_t* counts;        // [2][n_full] or null
   int phase_mask;               // phases in the error: bit p = phase p (3 = both)
   int max_chunk_vecs;           // vectors in the largest chunk
+  int max_chunk_entries;        // segment pixels of the largest chunk
   const uint8_t* sel_ext;       // selected start translations, extended layout (null: all)
   float inv_norm;               // descriptor = count * inv_norm (1/(H W), or 1/N selected)
-  // Phase-0 counts (see delta_lookup_vectors): z[v][y][x] = number of phase-0
-  // pixels of S(v) + (x, y), one byte per canonical vector and translation;
-  // null: count changes by walks.  off16: the segments' pixel offsets
+  // Phase-0 counts (see delta_lookup_vectors_strided): byte
+  // v H W + delta_z_index(v, x, y) of z = number of phase-0 pixels of
+  // S(v) + (x, y), one byte per canonical vector and translation; null:
+  // count changes by walks.  off16: the segments' pixel offsets
   // (sx, sy) as int16 pairs, CSR by dptr.
   uint8_t* z;
   const int16_t* off16;
@@ -196,11 +198,51 @@ __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const Del
 // Sec. 2.2 restricted to the translations the exchange touches), read from
 // one byte per translation instead of walking the segment.
 
-// Index of translation (x, y) in z_v: row-major for x-major vectors,
-// column-major for y-major ones (dy > |dx|), so that the translations
-// through one pixel along the segment are mostly consecutive bytes.
-__device__ __forceinline__ int delta_z_index(const DeltaArgs& g, int dx, int dy, int x, int y) {
-  return dy > (dx < 0 ? -dx : dx) ? x * g.H + y : y * g.W + x;
+// Layout of z_v.  The translations whose segment contains one pixel q are
+// q - S(v), a digital line along v; z_v is stored sheared along v so that
+// such a line is a run of consecutive bytes in one or two rows (a few
+// 32-byte sectors per warp instead of one per pixel for diagonal vectors).
+// x-major v (|dx| >= dy): translation (x, y) is at row y - sh(x) (mod H),
+// column x, rows of W bytes; y-major v (dy > |dx|): at column x - sh(y)
+// (mod W), row y, columns of H bytes; sh(t) = floor(t m / 2^16) with
+// m = delta_shear(dx, dy), about t dy/dx (x-major) or t dx/dy (y-major).
+// For a fixed column (row) the shear is a rotation, so every layout is a
+// permutation of the translations; any m would be correct, this one makes
+// the lines short.  |sh(t)| < the sheared extent's period along t.
+__host__ __device__ inline int delta_shear(int dx, int dy) {
+  const int adx = dx < 0 ? -dx : dx;
+  if (dy > adx) return (int)(((long long)dx * 65536) / dy);
+  return adx ? (int)(((long long)dy * 65536) / dx) : 0;
+}
+
+__device__ __forceinline__ int delta_shift(int t, int m) { return (int)(((long long)t * m) >> 16); }
+
+// t reduced into [0, n) when t lies in (-n, 2n), else by a full modulo.
+__device__ __forceinline__ int delta_wrap(int t, int n) {
+  if (t < 0) t += n;
+  else if (t >= n) t -= n;
+  if ((unsigned)t >= (unsigned)n) t = ((t % n) + n) % n;
+  return t;
+}
+
+// Index of translation (x, y) in z_v (m = delta_shear of v).
+__device__ __forceinline__ int delta_z_index(const DeltaArgs& g, int dx, int dy, int m, int x, int y) {
+  if (dy > (dx < 0 ? -dx : dx)) return delta_wrap(x - delta_shift(y, m), g.W) * g.H + y;
+  return delta_wrap(y - delta_shift(x, m), g.H) * g.W + x;
+}
+
+// Translation (x, y) stored at index p of z_v: the inverse of delta_z_index.
+__device__ __forceinline__ void delta_z_translation(const DeltaArgs& g, int dx, int dy, int m, int p, int& x,
+                                                    int& y) {
+  if (dy > (dx < 0 ? -dx : dx)) {
+    const int c = p / g.H;
+    y = p - c * g.H;
+    x = delta_wrap(c + delta_shift(y, m), g.W);
+  } else {
+    const int r = p / g.W;
+    x = p - r * g.W;
+    y = delta_wrap(r + delta_shift(x, m), g.H);
+  }
 }
 
 // Canonical vector of canonical index v.
@@ -233,16 +275,11 @@ __device__ __forceinline__ bool delta_on_segment(const DeltaArgs& g, int o0, int
 }
 
 // Same contract as delta_walk_vectors (a phase 1, b phase 0; the warp's
-// vectors v = v0 + warp, v0 + warp + kDeltaWarps, ...; lane 0 writes and
-// returns), from the phase-0 counts g.z.
+// vectors v = v0, v0 + vstep, ...; lane 0 writes and returns), from the
+// phase-0 counts g.z.
 __device__ __forceinline__ float delta_lookup_vectors_strided(const DeltaArgs& g, int a, int b, int v0, int v1,
                                                               int vstep, int lane, int32_t* dcounts_k,
                                                               const DeltaTerms& dt);
-
-__device__ __forceinline__ float delta_lookup_vectors(const DeltaArgs& g, int a, int b, int v0, int v1, int warp,
-                                                      int lane, int32_t* dcounts_k, const DeltaTerms& dt) {
-  return delta_lookup_vectors_strided(g, a, b, v0 + warp, v1, kDeltaWarps, lane, dcounts_k, dt);
-}
 
 // One warp over all vectors v0 <= v < v1 (in order); lane 0 returns.
 __device__ __forceinline__ float delta_lookup_vectors_warp(const DeltaArgs& g, int a, int b, int v0, int v1,
@@ -264,6 +301,7 @@ __device__ __forceinline__ float delta_lookup_vectors_strided(const DeltaArgs& g
     const int L1 = __ldg(g.dptr + v + 1) - o0;
     int dx, dy;
     delta_vector(g, v, dx, dy);
+    const int m = delta_shear(dx, dy);
     const uint8_t* zv = g.z + (int64_t)v * hw;
     int d0 = 0, d1 = 0;
     // four lookups per lane in flight: offsets, then counts, then the tests
@@ -280,8 +318,8 @@ __device__ __forceinline__ float delta_lookup_vectors_strided(const DeltaArgs& g
         ys[u] = y < 0 ? y + H : (y >= H ? y - H : y);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)  // read at L2 (the annealer updates z with atomics, which bypass L1)
-        zs[u] = t0 + 32 * u + lane < 2 * L1 ? __ldcg(zv + delta_z_index(g, dx, dy, xs[u], ys[u])) : -1;
+      for (int u = 0; u < 4; ++u)  // read at L2 (the annealer updates z in place)
+        zs[u] = t0 + 32 * u + lane < 2 * L1 ? __ldcg(zv + delta_z_index(g, dx, dy, m, xs[u], ys[u])) : -1;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int t = t0 + 32 * u + lane;
@@ -326,34 +364,225 @@ __device__ __forceinline__ float delta_lookup_vectors_strided(const DeltaArgs& g
   return acc;
 }
 
-// After exchanging a (now phase 0) and b (now phase 1): z_v += 1 on the
-// translations through a and -= 1 on those through b, for the warp's
-// vectors of [v0, v1).  A translation through both gets both, which nets 0;
-// the byte never wraps in between (it counts b, so it is >= 1 before the
-// decrement, and < L1 before the increment), so the two updates may land
-// in either order: one 32-bit atomic add per byte.
-__device__ __forceinline__ void delta_lookup_update(const DeltaArgs& g, int a, int b, int v0, int v1, int warp,
-                                                   int lane) {
-  const int W = g.W, H = g.H;
+// A block's vector chunk for the block-wide lookups of the persistent
+// annealer.  The segment pixels of the chunk's vectors v0 <= v < v0 + nv are
+// the contiguous entries o_base + [0, pre[nv]) of off16, copied to off;
+// vector v0 + i owns entries [pre[i], pre[i + 1]).  d ([2][mv]) and term
+// ([mv]) are the block's scratch for count changes and error terms.  All
+// arrays are in shared memory.
+struct ChunkTables {
+  const int32_t* pre;   // [nv + 1] entry offsets
+  const short2* vec;    // [nv] the chunk's canonical vectors (dx, dy)
+  const int32_t* shear; // [nv] their delta_shear
+  const short2* off;    // [pre[nv]] the chunk's segment pixels (sx, sy)
+  int32_t* d;           // [2][mv] count changes (phase 0, phase 1)
+  float* term;          // [mv] error terms
+  int nv, mv;
+};
+
+// Entries each thread takes per round of the block-wide lookups.
+constexpr int kChunkUnroll = 4;
+
+// The chunk-relative vector owning entry e: the largest i with pre[i] <= e.
+__device__ __forceinline__ int chunk_vector_of(const int32_t* pre, int nv, int e) {
+  int lo = 0, hi = nv - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= e) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// delta_on_segment for chunk vector i, reading its pixels from the chunk's
+// copy in shared memory.
+__device__ __forceinline__ bool chunk_on_segment(const DeltaArgs& g, const ChunkTables& ct, int i, int dx, int dy,
+                                                 int x, int y, int qx, int qy) {
+  int uy = qy - y;
+  if (uy < 0) uy += g.H;
+  if (uy > dy) return false;
+  const int xlo = dx < 0 ? dx : 0, xhi = dx < 0 ? 0 : dx;
+  int ux = qx - x - xlo;
+  if (ux < 0) ux += g.W;
+  else if (ux >= g.W) ux -= g.W;
+  ux += xlo;
+  if (ux > xhi) return false;
+  const short2* o = ct.off + ct.pre[i];
+  const int adx = dx < 0 ? -dx : dx;
+  if (adx >= dy) return o[dx < 0 ? -ux : ux].y == uy;  // x-major: pixel k at sx = sign(dx) k
+  return o[uy].x == ux;                                // y-major: pixel k at sy = k
+}
+
+// Translation of chunk entry j for the exchange pixel (qx, qy): the start x
+// of the segment whose pixel j is q, wrapped onto the torus, and the byte of
+// z holding its phase-0 count (z has fewer than 2^31 bytes on the lookup
+// path).
+__device__ __forceinline__ void chunk_entry(const DeltaArgs& g, const ChunkTables& ct, int v0, int j, int qx, int qy,
+                                            int& i, int& x, int& y, uint32_t& zi) {
+  i = chunk_vector_of(ct.pre, ct.nv, j);
+  const short2 s2 = ct.off[j];
+  x = qx - s2.x;
+  y = qy - s2.y;
+  x = x < 0 ? x + g.W : (x >= g.W ? x - g.W : x);
+  y = y < 0 ? y + g.H : (y >= g.H ? y - g.H : y);
+  const short2 dv = ct.vec[i];
+  zi = (uint32_t)(v0 + i) * (uint32_t)(g.H * g.W) + (uint32_t)delta_z_index(g, dv.x, dv.y, ct.shear[i], x, y);
+}
+
+// Count changes and error change of the chunk's vectors for the exchange of
+// a (phase 1) and b (phase 0), from the phase-0 counts z, with the chunk's
+// 2 (L + 1) lookups per vector spread evenly over all threads of the block:
+// entry e < E looks at the translation through a of pixel e, entry E + e at
+// the one through b; kChunkUnroll lookups per thread in flight.  The tests
+// are those of delta_lookup_vectors_strided.  When the block has at most
+// kChunkUnroll entries per thread, *held receives the thread's counts as
+// read (one byte each, for delta_chunk_apply_held), else 0.  Every thread
+// calls it; thread 0 returns the chunk's error change, summed over the
+// vectors in a fixed order.
+__device__ __forceinline__ float delta_chunk_lookup(const DeltaArgs& g, int a, int b, int v0,
+                                                    const ChunkTables& ct, int32_t* dcounts_k,
+                                                    const DeltaTerms& dt, uint32_t* held) {
+  const int E = ct.pre[ct.nv];
+  for (int i = threadIdx.x; i < ct.nv; i += blockDim.x) {
+    ct.d[i] = 0;
+    ct.d[ct.mv + i] = 0;
+  }
+  __syncthreads();
+  const int W = g.W;
   const int ay = a / W, ax = a - ay * W, by = b / W, bx = b - by * W;
-  const int64_t hw = (int64_t)H * W;
-  for (int v = v0 + warp; v < v1; v += kDeltaWarps) {
-    const int o0 = __ldg(g.dptr + v);
-    const int L1 = __ldg(g.dptr + v + 1) - o0;
-    int dx, dy;
-    delta_vector(g, v, dx, dy);
-    uint8_t* zv = g.z + (int64_t)v * hw;
-    for (int t = lane; t < 2 * L1; t += 32) {
-      const int side = t >= L1;
-      const int i = side ? t - L1 : t;
-      int x = (side ? bx : ax) - g.off16[2 * (o0 + i)], y = (side ? by : ay) - g.off16[2 * (o0 + i) + 1];
-      x = x < 0 ? x + W : (x >= W ? x - W : x);
-      y = y < 0 ? y + H : (y >= H ? y - H : y);
-      uint8_t* byte = zv + delta_z_index(g, dx, dy, x, y);
-      unsigned int* word = reinterpret_cast<unsigned int*>(reinterpret_cast<uintptr_t>(byte) & ~uintptr_t(3));
-      const unsigned int sh = 8u * (unsigned)(reinterpret_cast<uintptr_t>(byte) & 3);
-      atomicAdd(word, side ? (0u - (1u << sh)) : (1u << sh));
+  const int nthr = blockDim.x;
+  uint32_t h = 0;
+  for (int e0 = 0; e0 < 2 * E; e0 += kChunkUnroll * nthr) {
+    int vi[kChunkUnroll], xs[kChunkUnroll], ys[kChunkUnroll], zs[kChunkUnroll];
+    uint32_t zi[kChunkUnroll];
+#pragma unroll
+    for (int u = 0; u < kChunkUnroll; ++u) {
+      const int e = e0 + u * nthr + (int)threadIdx.x;
+      vi[u] = -1;
+      if (e < 2 * E) {
+        const bool side = e >= E;
+        chunk_entry(g, ct, v0, side ? e - E : e, side ? bx : ax, side ? by : ay, vi[u], xs[u], ys[u], zi[u]);
+      }
     }
+#pragma unroll
+    for (int u = 0; u < kChunkUnroll; ++u)  // read at L2 (other threads of the block update z)
+      zs[u] = vi[u] >= 0 ? (int)__ldcg(g.z + zi[u]) : 0;
+#pragma unroll
+    for (int u = 0; u < kChunkUnroll; ++u) {
+      h |= (uint32_t)zs[u] << (8 * u);
+      if (vi[u] < 0) continue;
+      const int e = e0 + u * nthr + (int)threadIdx.x;
+      const int i = vi[u], x = xs[u], y = ys[u], z = zs[u];
+      if (g.sel_ext && !g.sel_ext[(y + g.ry) * g.We + (x + g.rx)]) continue;  // start not sampled
+      const int L1 = ct.pre[i + 1] - ct.pre[i];
+      const short2 dv = ct.vec[i];
+      if (e < E) {
+        if (z == 0) atomicAdd(ct.d + ct.mv + i, -1);
+        if (z == L1 - 1 && !chunk_on_segment(g, ct, i, dv.x, dv.y, x, y, bx, by)) atomicAdd(ct.d + i, 1);
+      } else {
+        if (z == L1) atomicAdd(ct.d + i, -1);
+        if (z == 1 && !chunk_on_segment(g, ct, i, dv.x, dv.y, x, y, ax, ay)) atomicAdd(ct.d + ct.mv + i, 1);
+      }
+    }
+  }
+  *held = 2 * E <= kChunkUnroll * nthr ? h : 0u;
+  __syncthreads();
+  const float invN = g.inv_norm;
+  for (int i = threadIdx.x; i < ct.nv; i += blockDim.x) {
+    const int d0 = ct.d[i], d1 = ct.d[ct.mv + i];
+    const int v = v0 + i;
+    if (dcounts_k) {
+      dcounts_k[v] = d0;
+      dcounts_k[g.n_canon + v] = d1;
+    }
+    float acc = 0.0f;
+    if (g.target && (d0 | d1)) {
+      const int iv = v - dt.vbase;
+      if (d0 && (g.phase_mask & 1)) {
+        const float dd = dt.t[0][iv] - (float)dt.c[0][iv] * invN;
+        const float xx = (float)d0 * invN;
+        acc += xx * (xx - 2.0f * dd);
+      }
+      if (d1 && (g.phase_mask & 2)) {
+        const float dd = dt.t[1][iv] - (float)dt.c[1][iv] * invN;
+        const float xx = (float)d1 * invN;
+        acc += xx * (xx - 2.0f * dd);
+      }
+    }
+    ct.term[i] = acc;
+  }
+  __syncthreads();
+  float sum = 0.0f;
+  if (threadIdx.x < 32) {  // lane-strided sums in vector order, then a fixed shuffle tree
+    for (int i = threadIdx.x; i < ct.nv; i += 32) sum += ct.term[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  }
+  return sum;
+}
+
+// After exchanging a (now phase 0) and b (now phase 1): z_v += 1 on the
+// translations through a and -= 1 on those through b, for the chunk's
+// vectors, with the counts delta_chunk_lookup read for this same exchange
+// and held by each thread (the block had at most kChunkUnroll entries per
+// thread): plain stores at L2 -- the block owns these bytes.  A
+// translation through both pixels keeps its count (its two entries are
+// one byte, which neither stores); within one side a vector's translations
+// are distinct, so no two threads store the same byte.  Every thread calls
+// it with the same a, b as that lookup.
+__device__ __forceinline__ void delta_chunk_apply_held(const DeltaArgs& g, int a, int b, int v0,
+                                                       const ChunkTables& ct, uint32_t held) {
+  const int E = ct.pre[ct.nv];
+  const int W = g.W;
+  const int ay = a / W, ax = a - ay * W, by = b / W, bx = b - by * W;
+  const int nthr = blockDim.x;
+#pragma unroll
+  for (int u = 0; u < kChunkUnroll; ++u) {
+    const int e = u * nthr + (int)threadIdx.x;
+    if (e >= 2 * E) continue;
+    const bool side = e >= E;
+    int i, x, y;
+    uint32_t zi;
+    chunk_entry(g, ct, v0, side ? e - E : e, side ? bx : ax, side ? by : ay, i, x, y, zi);
+    const short2 dv = ct.vec[i];
+    if (chunk_on_segment(g, ct, i, dv.x, dv.y, x, y, side ? ax : bx, side ? ay : by)) continue;
+    const uint32_t z = (held >> (8 * u)) & 0xffu;
+    __stcg(g.z + zi, (uint8_t)(side ? z - 1u : z + 1u));
+  }
+}
+
+// The same update without held counts: each byte is loaded and stored at
+// L2, first every translation through a, then (after a block barrier) every
+// one through b, so that a translation through both gets both changes in
+// turn.  Every thread calls it.
+__device__ __forceinline__ void delta_chunk_update(const DeltaArgs& g, int a, int b, int v0, const ChunkTables& ct) {
+  const int E = ct.pre[ct.nv];
+  const int W = g.W;
+  const int nthr = blockDim.x;
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    const int q = side ? b : a;
+    const int qy = q / W, qx = q - qy * W;
+    for (int j0 = 0; j0 < E; j0 += kChunkUnroll * nthr) {
+      uint32_t zi[kChunkUnroll], zz[kChunkUnroll];
+      bool ok[kChunkUnroll];
+#pragma unroll
+      for (int u = 0; u < kChunkUnroll; ++u) {
+        const int j = j0 + u * nthr + (int)threadIdx.x;
+        ok[u] = j < E;
+        zi[u] = 0;
+        if (ok[u]) {
+          int i, x, y;
+          chunk_entry(g, ct, v0, j, qx, qy, i, x, y, zi[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kChunkUnroll; ++u) zz[u] = ok[u] ? (uint32_t)__ldcg(g.z + zi[u]) : 0u;
+#pragma unroll
+      for (int u = 0; u < kChunkUnroll; ++u)
+        if (ok[u]) __stcg(g.z + zi[u], (uint8_t)(side ? zz[u] - 1u : zz[u] + 1u));
+    }
+    __syncthreads();
   }
 }
 

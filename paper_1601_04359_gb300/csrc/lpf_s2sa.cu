@@ -235,7 +235,8 @@ __global__ void __launch_bounds__(kS2Threads) s2_batch_kernel(SaDev* __restrict_
       }
     }
   }
-  if (threadIdx.x == 0) sa_advance(&s_state, Keff, Kv, kstar, de_star, pairs);
+  if (threadIdx.x == 0) sa_advance(&s_state, Keff, Kv, kstar, de_star, kstar >= 0 ? __ldcg(pairs + 2 * kstar) : 0,
+                                      kstar >= 0 ? __ldcg(pairs + 2 * kstar + 1) : 0);
   sa_state_store(st, &s_state);
 }
 

@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_batch_kernel(
       }
     }
   }
-  if (threadIdx.x == 0) sa_advance(&s_state, Keff, Kv, kstar, de_star, pairs);
+  if (threadIdx.x == 0) sa_advance(&s_state, Keff, Kv, kstar, de_star, kstar >= 0 ? __ldcg(pairs + 2 * kstar) : 0,
+                                      kstar >= 0 ? __ldcg(pairs + 2 * kstar + 1) : 0);
   sa_state_store(st, &s_state);
 }
 
@@ -223,8 +224,10 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_batch_kernel(
 // launch whose blocks stay resident for n_batches batches: block c owns
 // vector chunk c (the grid is exactly the chunk count, all blocks co-resident)
 // and keeps its extended cell and a copy of the run state in shared memory.
-// Per batch every block draws the batch's candidates, walks its chunk for
-// each and writes its partial error changes; after one grid barrier every
+// Per batch every block draws the batch's candidates, evaluates its chunk
+// for each (with the phase-0 counts: the chunk's lookups spread over all
+// threads of the block, so that every block takes about the same time to
+// reach the barrier; else walks) and writes its partial error changes; after one grid barrier every
 // block sums the partials of each candidate in the same fixed order, so all
 // blocks find the same first accepted candidate, apply it to their own cell
 // copy and to the counts of their own vectors, and advance their identical
@@ -279,6 +282,30 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
   const int mv = g.max_chunk_vecs;
   long long* s_cnt = reinterpret_cast<long long*>(sm + g.ext_bytes);  // [2][mv]
   float* s_tgt = reinterpret_cast<float*>(s_cnt + 2 * mv);            // [2][mv]
+  // the chunk's tables for the block-wide lookups and updates (lookup path)
+  ChunkTables ct;
+  int32_t* s_pre = reinterpret_cast<int32_t*>(s_tgt + 2 * mv);        // [mv + 1]
+  short2* s_vec = reinterpret_cast<short2*>(s_pre + mv + 1);          // [mv]
+  ct.pre = s_pre;
+  ct.vec = s_vec;
+  ct.d = reinterpret_cast<int32_t*>(s_vec + mv);                      // [2][mv]
+  ct.term = reinterpret_cast<float*>(ct.d + 2 * mv);                  // [mv]
+  int32_t* s_shear = reinterpret_cast<int32_t*>(ct.term + mv);       // [mv]
+  short2* s_off = reinterpret_cast<short2*>(s_shear + mv);            // [max_chunk_entries]
+  ct.shear = s_shear;
+  ct.off = s_off;
+  ct.nv = nv;
+  ct.mv = mv;
+  const int o_base = g.dptr[v0], n_ent = g.dptr[v1] - o_base;
+  for (int i = threadIdx.x; i <= nv; i += blockDim.x) {
+    s_pre[i] = g.dptr[v0 + i] - o_base;
+    if (i < nv) {
+      const short2 dv = reinterpret_cast<const short2*>(g.vec16)[v0 + i];
+      s_vec[i] = dv;
+      s_shear[i] = delta_shear(dv.x, dv.y);
+    }
+  }
+  for (int j = threadIdx.x; j < n_ent; j += blockDim.x) s_off[j] = reinterpret_cast<const short2*>(g.off16)[o_base + j];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
@@ -293,6 +320,8 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
   dt.c[0] = s_cnt;
   dt.c[1] = s_cnt + mv;
   dt.vbase = v0;
+  uint32_t held = 0;  // the phase-0 counts this thread read for candidate held_k
+  int held_k = -1;
   for (int bi = 0; bi < n_batches && !s_state.done; ++bi) {
     const int Keff = s_state.k_eff;
     const unsigned long long n0 = (unsigned long long)s_state.n_eval;
@@ -315,14 +344,21 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
       const int a = s_a, b = s_b;
       int32_t* dk = dcounts + (int64_t)k * 2 * g.n_canon;
       float acc = 0.0f;
+      const bool block_sum = a != b && g.z;  // block-wide lookups: thread 0 holds the chunk's sum
+      held_k = -1;
       if (a == b) delta_zero_vectors(g, v0, v1, dk);
-      else if (g.z) acc = delta_lookup_vectors(g, a, b, v0, v1, warp, lane, dk, dt);
+      else if (g.z) {
+        acc = delta_chunk_lookup(g, a, b, v0, ct, dk, dt, &held);
+        if (2 * n_ent <= kChunkUnroll * (int)blockDim.x) held_k = k;  // this candidate's counts stay in registers
+      }
       else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk, dt);
-      if (lane == 0) warp_acc[warp] = acc;
+      if (!block_sum && lane == 0) warp_acc[warp] = acc;
       __syncthreads();
       if (threadIdx.x == 0) {
         float sum = 0.0f;
-        for (int w = 0; w < kDeltaWarps; ++w) sum += warp_acc[w];
+        if (block_sum) sum = acc;
+        else
+          for (int w = 0; w < kDeltaWarps; ++w) sum += warp_acc[w];
         partial[(int64_t)k * g.n_chunks + ch] = sum;
         if (a != b) { delta_mark(sm, a, 1, g); delta_mark(sm, b, 0, g); }
       }
@@ -337,14 +373,21 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
     const int Kv = (int)min((long long)Keff, max(0LL, left));
     float de_star;
     const int kstar = sa_first_accept(&s_state, Kv, partial, g.n_chunks, u, &de_star);
+    int acc_a = 0, acc_b = 0;
     if (kstar >= 0) {
-      const int a = __ldcg(pairs + 2 * kstar), b = __ldcg(pairs + 2 * kstar + 1);
+      // every block drew the candidates itself; the last one drawn is in s_a, s_b
+      const int a = kstar == Keff - 1 ? s_a : __ldcg(pairs + 2 * kstar);
+      const int b = kstar == Keff - 1 ? s_b : __ldcg(pairs + 2 * kstar + 1);
+      acc_a = a;
+      acc_b = b;
       if (a != b) {
         // this block's vectors: apply the accepted candidate's changes
+        // (the block-wide lookups of the last candidate left its changes in ct.d)
+        const bool in_smem = held_k == kstar && held_k >= 0;
         const int32_t* dk = dcounts + (int64_t)kstar * 2 * g.n_canon;
         for (int i = threadIdx.x; i < nv; i += blockDim.x) {
           const int v = v0 + i;
-          const int d0 = dk[v], d1 = dk[(int64_t)g.n_canon + v];
+          const int d0 = in_smem ? ct.d[i] : dk[v], d1 = in_smem ? ct.d[mv + i] : dk[(int64_t)g.n_canon + v];
 #pragma unroll
           for (int p = 0; p < 2; ++p) {
             const int d = p ? d1 : d0;
@@ -356,7 +399,10 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
           }
         }
         // this block's vectors: the phase-0 counts follow the exchange
-        if (g.z) delta_lookup_update(g, a, b, v0, v1, warp, lane);
+        if (g.z) {
+          if (held_k == kstar) delta_chunk_apply_held(g, a, b, v0, ct, held);
+          else delta_chunk_update(g, a, b, v0, ct);
+        }
         if (threadIdx.x == 0) {
           delta_mark(sm, a, 0, g);
           delta_mark(sm, b, 1, g);
@@ -369,7 +415,7 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
         }
       }
     }
-    if (threadIdx.x == 0) sa_advance(&s_state, Keff, Kv, kstar, de_star, pairs);
+    if (threadIdx.x == 0) sa_advance(&s_state, Keff, Kv, kstar, de_star, acc_a, acc_b);
     __syncthreads();
   }
   if (ch == 0) sa_state_store(st, &s_state);
@@ -422,10 +468,8 @@ const void* sa_persistent_kernel_entry() { return reinterpret_cast<const void*>(
 
 constexpr int kPersistentBatches = 4096;  // batches per persistent launch (bounds one launch's duration)
 
-// Dynamic shared memory of the persistent kernel: the extended cell, then
-// counts (int64) and targets (float) of the largest chunk, both phases.
 static size_t persistent_smem(const DeltaArgs& g) {
-  return (size_t)g.ext_bytes + (size_t)g.max_chunk_vecs * 2 * (sizeof(long long) + sizeof(float));
+  return persistent_smem_bytes(g.ext_bytes, g.max_chunk_vecs, g.max_chunk_entries);
 }
 
 // Launch the persistent annealer for nb batches (cooperative launch: every

@@ -195,8 +195,8 @@ __device__ __forceinline__ int sa_first_accept(const SaDev* st, int Kv, const fl
 // Advance the run past a batch of Keff candidates of which Kv count (the
 // rest lie beyond n_step) and kstar (or -1) was accepted: stage counters,
 // temperature, error, statistics and the next batch size.  Thread 0 only.
-__device__ __forceinline__ void sa_advance(SaDev* st, int Keff, int Kv, int kstar, float de_star,
-                                           const int32_t* pairs) {
+__device__ __forceinline__ void sa_advance(SaDev* st, int Keff, int Kv, int kstar, float de_star, int acc_a,
+                                           int acc_b) {
   const long long c0 = st->c_stage, cmax = st->c_max;
   const double Tm = st->T_mult;
   const long long consumed = kstar >= 0 ? kstar + 1 : Kv;
@@ -213,8 +213,8 @@ __device__ __forceinline__ void sa_advance(SaDev* st, int Keff, int Kv, int ksta
     c += 1;
     s += 1;
     if (c >= cmax || s >= st->s_max) { c = 0; s = 0; T *= Tm; }
-    st->acc_pair[0] = __ldcg(pairs + 2 * kstar);
-    st->acc_pair[1] = __ldcg(pairs + 2 * kstar + 1);
+    st->acc_pair[0] = acc_a;
+    st->acc_pair[1] = acc_b;
     st->acc_de = de_star;
     st->e += (double)de_star;
     st->n_accept += 1;

@@ -84,6 +84,7 @@ struct DeltaTables {
   int We = -1;
   int want = -1;               // vector chunks asked for (one wave of blocks)
   int max_chunk_vecs = 0;      // vectors in the largest chunk
+  int max_chunk_entries = 0;   // segment pixels of the largest chunk (by pixels)
   int32_t* d_doff = nullptr;   // per segment pixel: sy*We + sx
   int32_t* d_dptr = nullptr;   // CSR pointers [n_canon + 1]
   int32_t* d_chunk = nullptr;  // vector chunk bounds [n_chunks + 1]
@@ -135,6 +136,17 @@ int delta_prepare(lpf_paths* p, int H, int W, int K);
 int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g);
 // Candidate strides per vector chunk for K candidates.
 int delta_stride(int n_chunks, int K);
+// Dynamic shared memory of the persistent annealer for an extended cell of
+// ext_bytes and chunks of at most mv vectors and me segment pixels: the
+// cell, the chunk's counts (int64) and targets (float) of both phases, then
+// its tables for the block-wide lookups (entry offsets, vectors as int16
+// pairs, count changes of both phases, error terms, shears, the segment
+// pixels as int16 pairs).
+inline size_t persistent_smem_bytes(size_t ext_bytes, int mv, int me) {
+  const size_t m = (size_t)mv;
+  return ext_bytes + m * 2 * (sizeof(long long) + sizeof(float)) + (m + 1) * 4 + m * (4 + 2 * 4 + 4 + 4) +
+         (size_t)me * 4;
+}
 int delta_max_smem();
 // Phase-0 counts for swap deltas by lookup: bytes for an H x W cell (0: not
 // used -- too long segments or too much memory), allocation in the handle,
