@@ -367,12 +367,13 @@ int delta_stride(int n_chunks, int K) {
 }
 
 // Bytes of the phase-0 counts z for an H x W cell (one byte per canonical
-// vector and translation, plus word padding for the update atomics), or 0
-// when they do not apply: segments longer than 255 pixels (a byte count) or
-// more than kZBudget bytes.
+// vector and translation, plus 4 bytes of padding), or 0
+// when they do not apply: segments longer than 255 pixels (a byte count),
+// cells wider or higher than kZMaxSide, or more than kZBudget bytes.
 constexpr size_t kZBudget = size_t(2) << 30;
 size_t delta_z_bytes(const lpf_paths* p, int H, int W) {
   if (std::max(p->host.rx, p->host.ry) + 1 > 255) return 0;
+  if (H > kZMaxSide || W > kZMaxSide) return 0;
   const size_t b = (size_t)p->host.n_canon * H * W + 4;
   return b <= kZBudget ? b : 0;
 }

@@ -209,13 +209,16 @@ __device__ __forceinline__ float delta_walk_vectors(const uint8_t* sm, const Del
 // For a fixed column (row) the shear is a rotation, so every layout is a
 // permutation of the translations; any m would be correct, this one makes
 // the lines short.  |sh(t)| < the sheared extent's period along t.
+constexpr int kZMaxSide = 32767;  // cells wider or higher than this use walks
 __host__ __device__ inline int delta_shear(int dx, int dy) {
   const int adx = dx < 0 ? -dx : dx;
   if (dy > adx) return (int)(((long long)dx * 65536) / dy);
   return adx ? (int)(((long long)dy * 65536) / dx) : 0;
 }
 
-__device__ __forceinline__ int delta_shift(int t, int m) { return (int)(((long long)t * m) >> 16); }
+// floor(t m / 2^16); t < 2^15 and |m| <= 2^16 (cells on the lookup path
+// are narrower and lower than 2^15), so the product fits 32 bits.
+__device__ __forceinline__ int delta_shift(int t, int m) { return (t * m) >> 16; }
 
 // t reduced into [0, n) when t lies in (-n, 2n), else by a full modulo.
 __device__ __forceinline__ int delta_wrap(int t, int n) {
@@ -375,6 +378,7 @@ struct ChunkTables {
   const short2* vec;    // [nv] the chunk's canonical vectors (dx, dy)
   const int32_t* shear; // [nv] their delta_shear
   const short2* off;    // [pre[nv]] the chunk's segment pixels (sx, sy)
+  const uint16_t* vid;  // [pre[nv]] the chunk-relative vector of every entry
   int32_t* d;           // [2][mv] count changes (phase 0, phase 1)
   float* term;          // [mv] error terms
   int nv, mv;
@@ -383,7 +387,8 @@ struct ChunkTables {
 // Entries each thread takes per round of the block-wide lookups.
 constexpr int kChunkUnroll = 4;
 
-// The chunk-relative vector owning entry e: the largest i with pre[i] <= e.
+// The chunk-relative vector owning entry e: the largest i with pre[i] <= e
+// (the tables builder's search; the kernels read ct.vid).
 __device__ __forceinline__ int chunk_vector_of(const int32_t* pre, int nv, int e) {
   int lo = 0, hi = nv - 1;
   while (lo < hi) {
@@ -393,6 +398,11 @@ __device__ __forceinline__ int chunk_vector_of(const int32_t* pre, int nv, int e
   }
   return lo;
 }
+
+// The pixels of an exchange, split into coordinates once.
+struct PixelPair {
+  int ax, ay, bx, by;
+};
 
 // delta_on_segment for chunk vector i, reading its pixels from the chunk's
 // copy in shared memory.
@@ -419,7 +429,7 @@ __device__ __forceinline__ bool chunk_on_segment(const DeltaArgs& g, const Chunk
 // path).
 __device__ __forceinline__ void chunk_entry(const DeltaArgs& g, const ChunkTables& ct, int v0, int j, int qx, int qy,
                                             int& i, int& x, int& y, uint32_t& zi) {
-  i = chunk_vector_of(ct.pre, ct.nv, j);
+  i = ct.vid[j];
   const short2 s2 = ct.off[j];
   x = qx - s2.x;
   y = qy - s2.y;
@@ -439,7 +449,7 @@ __device__ __forceinline__ void chunk_entry(const DeltaArgs& g, const ChunkTable
 // read (one byte each, for delta_chunk_apply_held), else 0.  Every thread
 // calls it; thread 0 returns the chunk's error change, summed over the
 // vectors in a fixed order.
-__device__ __forceinline__ float delta_chunk_lookup(const DeltaArgs& g, int a, int b, int v0,
+__device__ __forceinline__ float delta_chunk_lookup(const DeltaArgs& g, const PixelPair& q, int v0,
                                                     const ChunkTables& ct, int32_t* dcounts_k,
                                                     const DeltaTerms& dt, uint32_t* held) {
   const int E = ct.pre[ct.nv];
@@ -448,8 +458,7 @@ __device__ __forceinline__ float delta_chunk_lookup(const DeltaArgs& g, int a, i
     ct.d[ct.mv + i] = 0;
   }
   __syncthreads();
-  const int W = g.W;
-  const int ay = a / W, ax = a - ay * W, by = b / W, bx = b - by * W;
+  const int ax = q.ax, ay = q.ay, bx = q.bx, by = q.by;
   const int nthr = blockDim.x;
   uint32_t h = 0;
   for (int e0 = 0; e0 < 2 * E; e0 += kChunkUnroll * nthr) {
@@ -521,6 +530,23 @@ __device__ __forceinline__ float delta_chunk_lookup(const DeltaArgs& g, int a, i
   return sum;
 }
 
+// Whether some translation of chunk vector i has both exchanged pixels on
+// its segment, for a torus displacement (ddx, ddy) = b - a taken in
+// [-W/2, W/2) x [-H/2, H/2).  Every pixel (sx, sy) of S(v) lies within a/2
+// of the line along v (|sy dx - sx dy| <= a/2, a = max(|dx|, dy): the
+// rounding of Sec. 2.2's segments), so a difference of two of its pixels
+// lies within a of it and inside the segment's box.  When the box is less
+// than half the cell on both axes only that representative of the
+// displacement can fit, and the test is exact enough to rule pairs out;
+// otherwise it answers "maybe".
+__device__ __forceinline__ bool chunk_maybe_both(const DeltaArgs& g, int dx, int dy, int ddx, int ddy) {
+  const int adx = dx < 0 ? -dx : dx;
+  if (2 * adx >= g.W || 2 * dy >= g.H) return true;
+  if ((ddx < 0 ? -ddx : ddx) > adx || (ddy < 0 ? -ddy : ddy) > dy) return false;
+  const int cross = ddy * dx - ddx * dy;
+  return (cross < 0 ? -cross : cross) <= (adx > dy ? adx : dy);
+}
+
 // After exchanging a (now phase 0) and b (now phase 1): z_v += 1 on the
 // translations through a and -= 1 on those through b, for the chunk's
 // vectors, with the counts delta_chunk_lookup read for this same exchange
@@ -529,13 +555,16 @@ __device__ __forceinline__ float delta_chunk_lookup(const DeltaArgs& g, int a, i
 // translation through both pixels keeps its count (its two entries are
 // one byte, which neither stores); within one side a vector's translations
 // are distinct, so no two threads store the same byte.  Every thread calls
-// it with the same a, b as that lookup.
-__device__ __forceinline__ void delta_chunk_apply_held(const DeltaArgs& g, int a, int b, int v0,
+// it with the same pixels as that lookup.
+__device__ __forceinline__ void delta_chunk_apply_held(const DeltaArgs& g, const PixelPair& q, int v0,
                                                        const ChunkTables& ct, uint32_t held) {
   const int E = ct.pre[ct.nv];
-  const int W = g.W;
-  const int ay = a / W, ax = a - ay * W, by = b / W, bx = b - by * W;
   const int nthr = blockDim.x;
+  int ddx = q.bx - q.ax, ddy = q.by - q.ay;
+  if (2 * ddx >= g.W) ddx -= g.W;
+  else if (2 * ddx < -g.W) ddx += g.W;
+  if (2 * ddy >= g.H) ddy -= g.H;
+  else if (2 * ddy < -g.H) ddy += g.H;
 #pragma unroll
   for (int u = 0; u < kChunkUnroll; ++u) {
     const int e = u * nthr + (int)threadIdx.x;
@@ -543,9 +572,11 @@ __device__ __forceinline__ void delta_chunk_apply_held(const DeltaArgs& g, int a
     const bool side = e >= E;
     int i, x, y;
     uint32_t zi;
-    chunk_entry(g, ct, v0, side ? e - E : e, side ? bx : ax, side ? by : ay, i, x, y, zi);
+    chunk_entry(g, ct, v0, side ? e - E : e, side ? q.bx : q.ax, side ? q.by : q.ay, i, x, y, zi);
     const short2 dv = ct.vec[i];
-    if (chunk_on_segment(g, ct, i, dv.x, dv.y, x, y, side ? ax : bx, side ? ay : by)) continue;
+    if (chunk_maybe_both(g, dv.x, dv.y, ddx, ddy) &&
+        chunk_on_segment(g, ct, i, dv.x, dv.y, x, y, side ? q.ax : q.bx, side ? q.ay : q.by))
+      continue;
     const uint32_t z = (held >> (8 * u)) & 0xffu;
     __stcg(g.z + zi, (uint8_t)(side ? z - 1u : z + 1u));
   }
@@ -555,14 +586,13 @@ __device__ __forceinline__ void delta_chunk_apply_held(const DeltaArgs& g, int a
 // L2, first every translation through a, then (after a block barrier) every
 // one through b, so that a translation through both gets both changes in
 // turn.  Every thread calls it.
-__device__ __forceinline__ void delta_chunk_update(const DeltaArgs& g, int a, int b, int v0, const ChunkTables& ct) {
+__device__ __forceinline__ void delta_chunk_update(const DeltaArgs& g, const PixelPair& q, int v0,
+                                                   const ChunkTables& ct) {
   const int E = ct.pre[ct.nv];
-  const int W = g.W;
   const int nthr = blockDim.x;
 #pragma unroll 1
   for (int side = 0; side < 2; ++side) {
-    const int q = side ? b : a;
-    const int qy = q / W, qx = q - qy * W;
+    const int qx = side ? q.bx : q.ax, qy = side ? q.by : q.ay;
     for (int j0 = 0; j0 < E; j0 += kChunkUnroll * nthr) {
       uint32_t zi[kChunkUnroll], zz[kChunkUnroll];
       bool ok[kChunkUnroll];

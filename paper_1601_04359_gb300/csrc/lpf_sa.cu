@@ -268,7 +268,8 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
   __shared__ __align__(8) uint64_t mbar;
   __shared__ SaDev s_state;
   __shared__ float warp_acc[kDeltaWarps];
-  __shared__ int s_a, s_b;
+  __shared__ int s_a, s_b, s_na, s_nb;
+  __shared__ PixelPair s_q, s_nq;  // the pixels of s_a, s_b and of s_na, s_nb as coordinates
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ch = blockIdx.x;
   const int v0 = g.chunk[ch], v1 = g.chunk[ch + 1], nv = v1 - v0;
@@ -292,8 +293,10 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
   ct.term = reinterpret_cast<float*>(ct.d + 2 * mv);                  // [mv]
   int32_t* s_shear = reinterpret_cast<int32_t*>(ct.term + mv);       // [mv]
   short2* s_off = reinterpret_cast<short2*>(s_shear + mv);            // [max_chunk_entries]
+  uint16_t* s_vid = reinterpret_cast<uint16_t*>(s_off + g.max_chunk_entries);  // [max_chunk_entries]
   ct.shear = s_shear;
   ct.off = s_off;
+  ct.vid = s_vid;
   ct.nv = nv;
   ct.mv = mv;
   const int o_base = g.dptr[v0], n_ent = g.dptr[v1] - o_base;
@@ -305,7 +308,11 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
       s_shear[i] = delta_shear(dv.x, dv.y);
     }
   }
-  for (int j = threadIdx.x; j < n_ent; j += blockDim.x) s_off[j] = reinterpret_cast<const short2*>(g.off16)[o_base + j];
+  __syncthreads();  // s_pre is complete
+  for (int j = threadIdx.x; j < n_ent; j += blockDim.x) {
+    s_off[j] = reinterpret_cast<const short2*>(g.off16)[o_base + j];
+    s_vid[j] = (uint16_t)chunk_vector_of(s_pre, nv, j);
+  }
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
@@ -322,33 +329,55 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
   dt.vbase = v0;
   uint32_t held = 0;  // the phase-0 counts this thread read for candidate held_k
   int held_k = -1;
+  // Candidate k of batch bi (warp 0): drawn from the block's own cell copy,
+  // marked there, kept in *sa / *sb; block 0 also records it for the others.
+  auto draw = [&](int bi, int k, int* sa, int* sb, PixelPair* sq) {
+    int a, b;
+    float uu;
+    draw_candidate_warp(sm, g, (unsigned long long)s_state.n_eval + (unsigned long long)k, s_state.key0,
+                        s_state.key1, a, b, uu, &s_state, lane);
+    if (lane == 0) {
+      if (ch == 0) {
+        pairs2[(size_t)(bi & 1) * 2 * k_max + 2 * k] = a;
+        pairs2[(size_t)(bi & 1) * 2 * k_max + 2 * k + 1] = b;
+        u2[(size_t)(bi & 1) * k_max + k] = uu;
+      }
+      *sa = a;
+      *sb = b;
+      sq->ay = a / g.W;
+      sq->ax = a - sq->ay * g.W;
+      sq->by = b / g.W;
+      sq->bx = b - sq->by * g.W;
+      if (a != b) { delta_mark(sm, a, kMarkA, g); delta_mark(sm, b, kMarkB, g); }
+    }
+  };
+  // The first candidate of every batch is drawn ahead, by warp 0 at the end
+  // of the batch before (while the other warps apply its exchange), into
+  // s_na, s_nb; later candidates of a batch go through s_a, s_b.
+  if (warp == 0 && !s_state.done && n_batches > 0) draw(0, 0, &s_na, &s_nb, &s_nq);
+  __syncthreads();
   for (int bi = 0; bi < n_batches && !s_state.done; ++bi) {
     const int Keff = s_state.k_eff;
-    const unsigned long long n0 = (unsigned long long)s_state.n_eval;
     int32_t* pairs = pairs2 + (size_t)(bi & 1) * 2 * k_max;
     float* u = u2 + (size_t)(bi & 1) * k_max;
     float* partial = partial2 + (size_t)(bi & 1) * k_max * g.n_chunks;
+    int last_a = 0, last_b = 0;  // the batch's last candidate
+    PixelPair last_q = {0, 0, 0, 0};
     for (int k = 0; k < Keff; ++k) {
-      if (warp == 0) {
-        int a, b;
-        float uu;
-        draw_candidate_warp(sm, g, n0 + (unsigned long long)k, s_state.key0, s_state.key1, a, b, uu, &s_state, lane);
-        if (lane == 0) {
-          if (ch == 0) { pairs[2 * k] = a; pairs[2 * k + 1] = b; u[k] = uu; }
-          s_a = a;
-          s_b = b;
-          if (a != b) { delta_mark(sm, a, kMarkA, g); delta_mark(sm, b, kMarkB, g); }
-        }
-      }
+      if (k > 0 && warp == 0) draw(bi, k, &s_a, &s_b, &s_q);
       __syncthreads();
-      const int a = s_a, b = s_b;
+      const int a = k == 0 ? s_na : s_a, b = k == 0 ? s_nb : s_b;
+      const PixelPair q = k == 0 ? s_nq : s_q;
+      last_a = a;
+      last_b = b;
+      last_q = q;
       int32_t* dk = dcounts + (int64_t)k * 2 * g.n_canon;
       float acc = 0.0f;
       const bool block_sum = a != b && g.z;  // block-wide lookups: thread 0 holds the chunk's sum
       held_k = -1;
       if (a == b) delta_zero_vectors(g, v0, v1, dk);
       else if (g.z) {
-        acc = delta_chunk_lookup(g, a, b, v0, ct, dk, dt, &held);
+        acc = delta_chunk_lookup(g, q, v0, ct, dk, dt, &held);
         if (2 * n_ent <= kChunkUnroll * (int)blockDim.x) held_k = k;  // this candidate's counts stay in registers
       }
       else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk, dt);
@@ -375,9 +404,9 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
     const int kstar = sa_first_accept(&s_state, Kv, partial, g.n_chunks, u, &de_star);
     int acc_a = 0, acc_b = 0;
     if (kstar >= 0) {
-      // every block drew the candidates itself; the last one drawn is in s_a, s_b
-      const int a = kstar == Keff - 1 ? s_a : __ldcg(pairs + 2 * kstar);
-      const int b = kstar == Keff - 1 ? s_b : __ldcg(pairs + 2 * kstar + 1);
+      // every block drew the candidates itself and holds the last one
+      const int a = kstar == Keff - 1 ? last_a : __ldcg(pairs + 2 * kstar);
+      const int b = kstar == Keff - 1 ? last_b : __ldcg(pairs + 2 * kstar + 1);
       acc_a = a;
       acc_b = b;
       if (a != b) {
@@ -400,22 +429,34 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
         }
         // this block's vectors: the phase-0 counts follow the exchange
         if (g.z) {
-          if (held_k == kstar) delta_chunk_apply_held(g, a, b, v0, ct, held);
-          else delta_chunk_update(g, a, b, v0, ct);
-        }
-        if (threadIdx.x == 0) {
-          delta_mark(sm, a, 0, g);
-          delta_mark(sm, b, 1, g);
-          if (ch == 0) {
-            cell[a] = 0;
-            cell[b] = 1;
-            delta_mark(ext, a, 0, g);
-            delta_mark(ext, b, 1, g);
+          if (held_k == kstar) {
+            delta_chunk_apply_held(g, last_q, v0, ct, held);
+          } else {
+            const PixelPair qk = {a % g.W, a / g.W, b % g.W, b / g.W};
+            delta_chunk_update(g, qk, v0, ct);
           }
         }
       }
     }
-    if (threadIdx.x == 0) sa_advance(&s_state, Keff, Kv, kstar, de_star, acc_a, acc_b);
+    // warp 0: the exchange on the block's cell copy, the run state, and the
+    // next batch's first candidate (drawn on the updated cell)
+    if (warp == 0) {
+      if (lane == 0) {
+        if (kstar >= 0 && acc_a != acc_b) {
+          delta_mark(sm, acc_a, 0, g);
+          delta_mark(sm, acc_b, 1, g);
+          if (ch == 0) {
+            cell[acc_a] = 0;
+            cell[acc_b] = 1;
+            delta_mark(ext, acc_a, 0, g);
+            delta_mark(ext, acc_b, 1, g);
+          }
+        }
+        sa_advance(&s_state, Keff, Kv, kstar, de_star, acc_a, acc_b);
+      }
+      __syncwarp();
+      if (!s_state.done && bi + 1 < n_batches) draw(bi + 1, 0, &s_na, &s_nb, &s_nq);
+    }
     __syncthreads();
   }
   if (ch == 0) sa_state_store(st, &s_state);
@@ -712,7 +753,8 @@ static int sa_create_lineal(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* 
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lpf::sa_persistent_kernel_entry(), lpf::kDeltaThreads,
                                                         smem);
     if (e != cudaSuccess) { lpf_sa_free(sa); return lpf::set_cuda_error(e); }
-    sa->persistent = (coop && occ > 0 && sa->g.n_chunks <= occ * sms) ? 1 : 0;
+    // (the block-wide lookups number a chunk's vectors in 16 bits)
+    sa->persistent = (coop && occ > 0 && sa->g.n_chunks <= occ * sms && sa->g.max_chunk_vecs <= 65535) ? 1 : 0;
   }
   rc = lpf::sa_start(sa, s);
   if (rc) { lpf_sa_free(sa); return rc; }

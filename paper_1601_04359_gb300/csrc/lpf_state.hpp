@@ -141,11 +141,11 @@ int delta_stride(int n_chunks, int K);
 // cell, the chunk's counts (int64) and targets (float) of both phases, then
 // its tables for the block-wide lookups (entry offsets, vectors as int16
 // pairs, count changes of both phases, error terms, shears, the segment
-// pixels as int16 pairs).
+// pixels as int16 pairs and the vector of every pixel as uint16).
 inline size_t persistent_smem_bytes(size_t ext_bytes, int mv, int me) {
   const size_t m = (size_t)mv;
   return ext_bytes + m * 2 * (sizeof(long long) + sizeof(float)) + (m + 1) * 4 + m * (4 + 2 * 4 + 4 + 4) +
-         (size_t)me * 4;
+         (size_t)me * (4 + 2) + 16;
 }
 int delta_max_smem();
 // Phase-0 counts for swap deltas by lookup: bytes for an H x W cell (0: not
