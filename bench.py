@@ -239,9 +239,28 @@ def extra_batch(lpf):
     e.record()
     torch.cuda.synchronize()
     ms_single = a.elapsed_time(e) / reps
+    # the walked work of the last batched run, counted as for lpf_full's
+    # roofline: 2 ALU ops per (prefix-tree node, 32-translation word) walked,
+    # both sides of each image at the mean of their word counts
+    lpf.lpf_batch_run(b, use_graph=True)
+    executed, nominal = lpf.lpf_batch_work(b)
+    ops = 0.0
+    for img, p, ex, nom in zip(imgs, paths, executed, nominal):
+        H, W = img.shape
+        words = 0.5 * (H * ((W + 31) // 32) + W * ((H + 31) // 32))
+        ops += 2.0 * lpf.lpf_paths_stats(p)["n_tree_nodes"] * words * (ex / nom if nom else 1.0)
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    peak = torch.cuda.get_device_properties(0).multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6
+    achieved = ops / (ms_batch / 1000.0)
     return {"workload": "256 images 48-256 px, r = size/2, both phases", "ms_batched_graph": ms_batch,
             "ms_per_image_launches": ms_single, "tests_per_s_batched": tests / (ms_batch / 1000.0),
-            "speedup": ms_single / ms_batch}
+            "speedup": ms_single / ms_batch,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "ALU op/s",
+                         "frac": achieved / peak, "kernel_ms": ms_batch,
+                         "walked_share": float(executed.sum() / max(1, nominal.sum())),
+                         "work_basis": "2 ops x prefix-tree nodes x translation words x walked share, per image; "
+                                       "time of the whole graph (zero, pack, walk, mirror)"}}
 
 
 def extra_s2(lpf, reps: int = 20):

@@ -430,6 +430,16 @@ int lpf_batch_autotune(lpf_batch *batch, const uint8_t *const *imgs_dev, const i
  * kernel gave up during a run so far, else LPF_OK. */
 int lpf_batch_status(lpf_batch *batch, lpf_stream_t stream);
 
+/*
+ * Work of the last lpf_batch_run, per image (both sides of its walk), in the
+ * units of lpf_paths_work: executed[i] = pixel words the warps ANDed for
+ * image i after the zero-count skip of Sec. 3.2, nominal[i] = the same
+ * without it.  Host arrays of n_img entries, both required.  Synchronises
+ * `stream`, then copies from the device.  Before any run executed is 0.
+ * Errors: LPF_EINVAL, LPF_ECUDA.
+ */
+int lpf_batch_work(lpf_batch *batch, int64_t *executed, int64_t *nominal, lpf_stream_t stream);
+
 /* Release a batch (NULL is ignored); synchronises the device. */
 void lpf_batch_free(lpf_batch *batch);
 

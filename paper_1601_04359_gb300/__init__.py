@@ -26,7 +26,7 @@ __all__ = [
     "lpf_cnn_set_loss", "s2_fft", "s2_counts", "s2_delta_swap", "s2_sa_create", "Cnn", "lpf_cnn_create",
     "lpf_cnn_set_params", "lpf_cnn_get_params", "lpf_cnn_forward", "lpf_cnn_gradients", "lpf_cnn_train_step",
     "lpf_sa_set_proposer", "Batch", "lpf_batch_create", "lpf_batch_run", "lpf_batch_autotune",
-    "lpf_batch_status", "lpf_set_checked", "lpf_paths_set_selftest", "LPF_EPIXEL", "LPF_ETIMEOUT",
+    "lpf_batch_status", "lpf_batch_work", "lpf_set_checked", "lpf_paths_set_selftest", "LPF_EPIXEL", "LPF_ETIMEOUT",
     "lpf_build_paths_3d", "lpf_full_3d",
 ]
 
@@ -134,6 +134,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lpf_batch_run": (ctypes.c_int, [p, i32, p]),
         "lpf_batch_autotune": (ctypes.c_int, [p, p, p, p, p, p, p]),
         "lpf_batch_status": (ctypes.c_int, [p, p]),
+        "lpf_batch_work": (ctypes.c_int, [p, p, p, p]),
         "lpf_batch_free": (None, [p]),
         "lpf_sa_create": (ctypes.c_int, [p, i32, i32, p, p, p, ctypes.POINTER(SaParams), p, ctypes.POINTER(p)]),
         "lpf_sa_run": (ctypes.c_int, [p, i32, p]),
@@ -425,6 +426,17 @@ def lpf_batch_autotune(batch: Batch, stream=None):
 
 def lpf_batch_status(batch: Batch, stream=None) -> int:
     return int(load().lpf_batch_status(batch.handle, _stream_ptr(stream)))
+
+
+def lpf_batch_work(batch: Batch, stream=None):
+    """Per image of the last run: (executed, nominal) pixel words ANDed by the
+    walk warps, with and without the zero-count skip (numpy int64 arrays)."""
+    import numpy as np
+    n = len(batch.imgs)
+    ex, nom = np.zeros(n, np.int64), np.zeros(n, np.int64)
+    _check(load().lpf_batch_work(batch.handle, ex.ctypes.data, nom.ctypes.data, _stream_ptr(stream)),
+           "lpf_batch_work")
+    return ex, nom
 
 
 class Annealer:

@@ -99,22 +99,25 @@ __global__ void batch_mirror_kernel(const BatchDesc* __restrict__ d) {
   }
 }
 
+// One unit; returns the pixels the warp walked.
 template <int T>
-__device__ __forceinline__ void batch_unit(const BatchDesc& b, int bg, int tile, int pi, const uint32_t* sm,
-                                           int lane) {
+__device__ __forceinline__ uint32_t batch_unit(const BatchDesc& b, int bg, int tile, int pi, const uint32_t* sm,
+                                               int lane) {
   const int bl = tile / b.G, grp = tile - (tile / b.G) * b.G;
   const int y = (bg * b.BB + bl) * 32 + lane;
   const uint32_t* lane_base = sm + (bl * 32 + lane) * b.S + grp * T;
-  (void)walk_unit<T>(b.prog, b.piece[pi], b.piece[pi + 1], lane_base, y, b.H, b.W, b.nw, grp * T, nullptr, lane,
-                     b.counts, b.n_full, b.base);
+  return walk_unit<T>(b.prog, b.piece[pi], b.piece[pi + 1], lane_base, y, b.H, b.W, b.nw, grp * T, nullptr, lane,
+                      b.counts, b.n_full, b.base);
 }
 
 __global__ void __launch_bounds__(kBatchThreads, 4) batch_walk_kernel(const BatchDesc* __restrict__ d,
                                                                    const BatchSlot* __restrict__ slots,
-                                                                   int n_slots, int* __restrict__ ctl) {
+                                                                   int n_slots, int* __restrict__ ctl,
+                                                                   unsigned long long* __restrict__ executed) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_abort, s_done, s_slot;
+  __shared__ uint32_t s_walked[kBatchWarps];
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) { mbar_init(&bar, 1); s_abort = 0; }
   __syncthreads();
@@ -156,19 +159,26 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_walk_kernel(const Batc
       __syncthreads();
       if (s_abort) break;
     }
+    // (pixels walked are tallied in shared memory, one word per warp, to keep
+    // registers for the walk)
+    if (lane == 0) s_walked[threadIdx.x >> 5] = 0u;
     for (;;) {
       int u = 0;
       if (lane == 0) u = atomicAdd(ctr, 1);
       u = __shfl_sync(0xffffffffu, u, 0);
       if (u >= units) break;
       const int tile = u % n_tiles, pi = u / n_tiles;
+      uint32_t w;
       switch (b.T) {
-        case 1: batch_unit<1>(b, sl.bg, tile, pi, sm, lane); break;
-        case 2: batch_unit<2>(b, sl.bg, tile, pi, sm, lane); break;
-        case 4: batch_unit<4>(b, sl.bg, tile, pi, sm, lane); break;
-        default: batch_unit<8>(b, sl.bg, tile, pi, sm, lane); break;
+        case 1: w = batch_unit<1>(b, sl.bg, tile, pi, sm, lane); break;
+        case 2: w = batch_unit<2>(b, sl.bg, tile, pi, sm, lane); break;
+        case 4: w = batch_unit<4>(b, sl.bg, tile, pi, sm, lane); break;
+        default: w = batch_unit<8>(b, sl.bg, tile, pi, sm, lane); break;
       }
+      if (lane == 0) s_walked[threadIdx.x >> 5] += w;
     }
+    if (lane == 0 && s_walked[threadIdx.x >> 5])
+      atomicAdd(executed + sl.img, (unsigned long long)s_walked[threadIdx.x >> 5]);
     __syncthreads();  // every warp is done with the staged band before it may be replaced
   }
   if (s_abort) {
@@ -199,6 +209,8 @@ struct lpf_batch {
   std::vector<lpf::BatchDesc> desc;  // per side of every image
   std::vector<int> img_desc;         // an image's first descriptor (its side 0)
   lpf::BatchDesc* d_desc = nullptr;
+  unsigned long long* d_exec = nullptr;  // per descriptor: pixels the warps walked in the last run
+  std::vector<int64_t> nominal;          // per descriptor: the same without the zero-count skip
   uint32_t* d_packed = nullptr;
   int* d_ctl = nullptr;          // [0] status, [kBatchCtlUnits + g] unit counter of band group g
   int ctl_words = 0, ctl_cap = 0;
@@ -243,6 +255,7 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
   size_t packed_total = 0;
   std::vector<size_t> offs;
   bt->desc.clear();
+  bt->nominal.clear();
   bt->img_desc.assign(bt->n, 0);
   std::vector<char> used(bt->baked.size(), 0);
   int total_bg = 0;
@@ -310,6 +323,7 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
       bt->desc.push_back(d);
       total_bg += g.nbg;
       bg_work.push_back((double)prog.n_pixel_words * g.G * g.BB * (g.T + 1));
+      bt->nominal.push_back(prog.n_pixel_words * (int64_t)g.nbg * g.G * g.BB);  // every warp walks every piece
       offs.push_back(packed_total);
       packed_total += (g.packed_words + 3) & ~size_t(3);  // keep every side 16-byte aligned
       bt->max_band = std::max(bt->max_band, g.band_bytes);
@@ -334,9 +348,12 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
   for (int i = 0; i < n_desc; ++i) bt->desc[i].packed = bt->d_packed + offs[i];
   if (n_desc > bt->desc_cap) {
     if (bt->d_desc) { cudaFree(bt->d_desc); bt->d_desc = nullptr; }
+    if (bt->d_exec) { cudaFree(bt->d_exec); bt->d_exec = nullptr; }
     if ((e = cudaMalloc(&bt->d_desc, sizeof(BatchDesc) * n_desc)) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMalloc(&bt->d_exec, sizeof(unsigned long long) * n_desc)) != cudaSuccess) return set_cuda_error(e);
     bt->desc_cap = n_desc;
   }
+  if ((e = cudaMemset(bt->d_exec, 0, sizeof(unsigned long long) * n_desc)) != cudaSuccess) return set_cuda_error(e);
   if ((e = cudaMemcpy(bt->d_desc, bt->desc.data(), sizeof(BatchDesc) * n_desc, cudaMemcpyHostToDevice)) != cudaSuccess)
     return set_cuda_error(e);
   bt->ctl_words = kBatchCtlUnits + total_bg;
@@ -395,9 +412,11 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
 static void batch_enqueue(lpf_batch* bt, cudaStream_t s) {
   cudaMemsetAsync(bt->d_ctl, 0, bt->ctl_words * sizeof(int), s);  // status of this run, unit counters
   const int n_desc = (int)bt->desc.size();
+  cudaMemsetAsync(bt->d_exec, 0, sizeof(unsigned long long) * n_desc, s);
   batch_zero_kernel<<<dim3(bt->max_full, n_desc), 256, 0, s>>>(bt->d_desc);
   batch_pack_kernel<<<dim3(bt->max_pack, n_desc), 256, 0, s>>>(bt->d_desc);
-  batch_walk_kernel<<<bt->blocks, kBatchThreads, bt->max_band, s>>>(bt->d_desc, bt->d_slots, bt->n_slots, bt->d_ctl);
+  batch_walk_kernel<<<bt->blocks, kBatchThreads, bt->max_band, s>>>(bt->d_desc, bt->d_slots, bt->n_slots, bt->d_ctl,
+                                                                    bt->d_exec);
   batch_mirror_kernel<<<dim3(bt->max_full, n_desc), 256, 0, s>>>(bt->d_desc);
 }
 
@@ -460,6 +479,26 @@ int lpf_batch_status(lpf_batch* bt, lpf_stream_t stream) {
   e = cudaMemcpy(&h, bt->d_ctl, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return lpf::set_cuda_error(e);
   return h ? LPF_ETIMEOUT : LPF_OK;
+}
+
+int lpf_batch_work(lpf_batch* bt, int64_t* executed, int64_t* nominal, lpf_stream_t stream) {
+  if (!bt || !executed || !nominal) return LPF_EINVAL;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return lpf::set_cuda_error(e);
+  const int n_desc = (int)bt->desc.size();
+  std::vector<unsigned long long> h(n_desc, 0);
+  if (n_desc && (e = cudaMemcpy(h.data(), bt->d_exec, sizeof(unsigned long long) * n_desc,
+                                cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return lpf::set_cuda_error(e);
+  for (int i = 0; i < bt->n; ++i) {
+    const int d0 = bt->img_desc[i], d1 = i + 1 < bt->n ? bt->img_desc[i + 1] : n_desc;
+    executed[i] = nominal[i] = 0;
+    for (int d = d0; d < d1; ++d) {
+      executed[i] += (int64_t)h[d];
+      nominal[i] += bt->nominal[d];
+    }
+  }
+  return LPF_OK;
 }
 
 int lpf_batch_autotune(lpf_batch* bt, const uint8_t* const* imgs_dev, const int32_t* H, const int32_t* W,
@@ -525,6 +564,7 @@ void lpf_batch_free(lpf_batch* bt) {
   if (bt->exec) cudaGraphExecDestroy(bt->exec);
   if (bt->graph) cudaGraphDestroy(bt->graph);
   cudaFree(bt->d_desc);
+  cudaFree(bt->d_exec);
   cudaFree(bt->d_packed);
   cudaFree(bt->d_ctl);
   cudaFree(bt->d_slots);

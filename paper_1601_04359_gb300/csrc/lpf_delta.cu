@@ -124,12 +124,17 @@ __global__ void __launch_bounds__(kDeltaThreads) z_init_kernel(const uint8_t* __
     const int o0 = __ldg(g.dptr + v), L1 = __ldg(g.dptr + v + 1) - o0;
     int dx, dy;
     delta_vector(g, v, dx, dy);
-    const int m = delta_shear(dx, dy);
+    const int m = g.shear ? __ldg(g.shear + v) : 0;
     uint8_t* zv = z + (int64_t)v * hw;
     for (int p = threadIdx.x; p < hw; p += blockDim.x) {
       // p runs over the vector's sheared layout (delta_z_index)
       int x, y;
-      delta_z_translation(g, dx, dy, m, p, x, y);
+      if (m == 0) {  // unsheared: rows of W bytes (x-major), columns of H bytes (y-major)
+        if (dy > (dx < 0 ? -dx : dx)) { x = p / g.H; y = p - x * g.H; }
+        else { y = p / g.W; x = p - y * g.W; }
+      } else {
+        delta_z_translation(g, dx, dy, m, p, x, y);
+      }
       const uint8_t* base = sm + (y + g.ry) * g.We + (x + g.rx);
       int c = 0;
       for (int k = 0; k < L1; ++k) c += base[__ldg(g.doff + o0 + k)] == 0;
@@ -199,6 +204,8 @@ static int bake_delta(lpf_paths* p, int W, int want_chunks, DeltaTables& t) {
   if (t.d_doff) {
     cudaDeviceSynchronize();
     cudaFree(t.d_doff); cudaFree(t.d_dptr); cudaFree(t.d_chunk); cudaFree(t.d_off16); cudaFree(t.d_vec16);
+    cudaFree(t.d_shear);
+    t.d_shear = nullptr;
     t.d_doff = t.d_dptr = t.d_chunk = nullptr;
     t.d_off16 = t.d_vec16 = nullptr;
   }
@@ -241,6 +248,13 @@ static int bake_delta(lpf_paths* p, int W, int want_chunks, DeltaTables& t) {
   if ((e = cudaMalloc(&t.d_vec16, std::max<size_t>(1, h.vec.size()) * 2)) != cudaSuccess) return set_cuda_error(e);
   if ((e = cudaMemcpy(t.d_vec16, h.vec.data(), h.vec.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
     return set_cuda_error(e);
+  {
+    std::vector<int32_t> shear(std::max<int64_t>(1, h.n_canon));
+    for (int64_t c = 0; c < h.n_canon; ++c) shear[c] = delta_shear(h.vec[2 * c], h.vec[2 * c + 1]);
+    if ((e = cudaMalloc(&t.d_shear, shear.size() * 4)) != cudaSuccess) return set_cuda_error(e);
+    if ((e = cudaMemcpy(t.d_shear, shear.data(), shear.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return set_cuda_error(e);
+  }
   t.We = We;
   t.want = want_chunks;
   t.n_chunks = (int)chunk.size() - 1;
@@ -280,6 +294,7 @@ int delta_geometry(const lpf_paths* p, int H, int W, DeltaArgs& g) {
   g.z = nullptr;
   g.off16 = p->delta.d_off16;
   g.vec16 = p->delta.d_vec16;
+  g.shear = p->delta.d_shear;
   g.inv_norm = 1.0f / ((float)H * (float)W);
   return LPF_OK;
 }
@@ -426,6 +441,11 @@ int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* path
     rc = delta_z_prepare(paths, H, W);
     if (rc) return rc;
     g.z = paths->d_z;
+    // unsheared counts: this call reads every candidate's lookups from an L2
+    // that holds z, and is bound by instruction issue, not by the sectors
+    // each warp touches (the annealer's sheared layout costs it 5 more
+    // instructions per lookup)
+    g.shear = nullptr;
     z_init_kernel<<<std::min<int64_t>(g.n_canon, 2 * (int64_t)(g_sms > 0 ? g_sms : 152)), kDeltaThreads, g.ext_bytes,
                     s>>>(paths->d_ext, g, g.z, paths->d_status);
     if (paths->ev_start) cudaEventRecord(paths->ev_start, s);

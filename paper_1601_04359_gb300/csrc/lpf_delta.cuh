@@ -41,6 +41,7 @@ struct DeltaArgs {
   uint8_t* z;
   const int16_t* off16;
   const int16_t* vec16;         // canonical vectors (dx, dy) as int16 pairs
+  const int32_t* shear;         // their delta_shear, or null: z unsheared
 };
 
 // Where a walk finds the target and the current count of vector v for the
@@ -220,18 +221,21 @@ __host__ __device__ inline int delta_shear(int dx, int dy) {
 // are narrower and lower than 2^15), so the product fits 32 bits.
 __device__ __forceinline__ int delta_shift(int t, int m) { return (t * m) >> 16; }
 
-// t reduced into [0, n) when t lies in (-n, 2n), else by a full modulo.
-__device__ __forceinline__ int delta_wrap(int t, int n) {
-  if (t < 0) t += n;
-  else if (t >= n) t -= n;
-  if ((unsigned)t >= (unsigned)n) t = ((t % n) + n) % n;
-  return t;
+// t reduced into [0, n).  On a square cell |shear| < n, so t lies in
+// (-n, 2n) and one wrap does; otherwise a full modulo.
+__device__ __forceinline__ int delta_wrap(const DeltaArgs& g, int t, int n) {
+  if (g.H == g.W) return t < 0 ? t + n : (t >= n ? t - n : t);
+  return ((t % n) + n) % n;
 }
 
-// Index of translation (x, y) in z_v (m = delta_shear of v).
+// Index of translation (x, y) in z_v (m = delta_shear of v, or 0 for the
+// unsheared layout: rows of W bytes for x-major vectors, columns of H bytes
+// for y-major ones).
 __device__ __forceinline__ int delta_z_index(const DeltaArgs& g, int dx, int dy, int m, int x, int y) {
-  if (dy > (dx < 0 ? -dx : dx)) return delta_wrap(x - delta_shift(y, m), g.W) * g.H + y;
-  return delta_wrap(y - delta_shift(x, m), g.H) * g.W + x;
+  const bool ymajor = dy > (dx < 0 ? -dx : dx);
+  if (m == 0) return ymajor ? x * g.H + y : y * g.W + x;
+  if (ymajor) return delta_wrap(g, x - delta_shift(y, m), g.W) * g.H + y;
+  return delta_wrap(g, y - delta_shift(x, m), g.H) * g.W + x;
 }
 
 // Translation (x, y) stored at index p of z_v: the inverse of delta_z_index.
@@ -240,11 +244,11 @@ __device__ __forceinline__ void delta_z_translation(const DeltaArgs& g, int dx, 
   if (dy > (dx < 0 ? -dx : dx)) {
     const int c = p / g.H;
     y = p - c * g.H;
-    x = delta_wrap(c + delta_shift(y, m), g.W);
+    x = delta_wrap(g, c + delta_shift(y, m), g.W);
   } else {
     const int r = p / g.W;
     x = p - r * g.W;
-    y = delta_wrap(r + delta_shift(x, m), g.H);
+    y = delta_wrap(g, r + delta_shift(x, m), g.H);
   }
 }
 
@@ -304,7 +308,7 @@ __device__ __forceinline__ float delta_lookup_vectors_strided(const DeltaArgs& g
     const int L1 = __ldg(g.dptr + v + 1) - o0;
     int dx, dy;
     delta_vector(g, v, dx, dy);
-    const int m = delta_shear(dx, dy);
+    const int m = g.shear ? __ldg(g.shear + v) : 0;
     const uint8_t* zv = g.z + (int64_t)v * hw;
     int d0 = 0, d1 = 0;
     // four lookups per lane in flight: offsets, then counts, then the tests

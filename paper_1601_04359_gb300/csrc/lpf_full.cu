@@ -977,6 +977,7 @@ void lpf_paths_free(lpf_paths* p) {
     cudaFree(p->delta.d_chunk);
     cudaFree(p->delta.d_off16);
     cudaFree(p->delta.d_vec16);
+    cudaFree(p->delta.d_shear);
     cudaFree(p->d_z);
     cudaFree(p->d_partial);
     cudaFree(p->d_ext);

@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
     if (i < nv) {
       const short2 dv = reinterpret_cast<const short2*>(g.vec16)[v0 + i];
       s_vec[i] = dv;
-      s_shear[i] = delta_shear(dv.x, dv.y);
+      s_shear[i] = g.shear[v0 + i];
     }
   }
   __syncthreads();  // s_pre is complete

@@ -175,7 +175,7 @@ __device__ __forceinline__ int sa_first_accept(const SaDev* st, int Kv, const fl
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) de += __shfl_xor_sync(0xffffffffu, de, o);
       if (lane == 0) {
-        const long long wk = (c0 + k) / cmax;  // stage ends before candidate k
+        const long long wk = c0 + k >= cmax ? (c0 + k) / cmax : 0;  // stage ends before candidate k
         const double Tk = wk ? T0 * pow(Tm, (double)wk) : T0;
         const bool acc = de <= 0.0f || __ldcg(u + k) < expf(-de / (float)Tk);
         if (acc) atomicMin(&s_kstar, k);
@@ -203,7 +203,7 @@ __device__ __forceinline__ void sa_advance(SaDev* st, int Keff, int Kv, int ksta
   const long long rej = kstar >= 0 ? kstar : Kv;
   long long c = c0 + rej, s = st->s_stage;
   double T = st->T;
-  const long long wraps = c / cmax;
+  const long long wraps = c >= cmax ? c / cmax : 0;  // (a 64-bit division only when a stage ends)
   if (wraps > 0) {
     s = 0;
     T *= pow(Tm, (double)wraps);
@@ -236,8 +236,8 @@ __device__ __forceinline__ void sa_advance(SaDev* st, int Keff, int Kv, int ksta
   // next batch size: a batch costs a fixed latency plus a share per
   // candidate and yields (1 - (1-p)^K) / p evaluations; with the measured
   // costs that ratio is best near K = 1/(2p)
-  const double want = ceil(0.5 / fmax(st->p_est, 1e-9));
-  st->k_eff = (int)fmin((double)st->k_max, fmax((double)st->k_min, want));
+  const float want = ceilf(0.5f / fmaxf((float)st->p_est, 1e-9f));
+  st->k_eff = (int)fminf((float)st->k_max, fmaxf((float)st->k_min, want));
   if (st->n_eval >= st->n_step) st->done = 1;
   st->ticket = 0u;
 }

@@ -91,6 +91,7 @@ struct DeltaTables {
   int n_chunks = 0;
   int16_t* d_off16 = nullptr;  // per segment pixel: (sx, sy)
   int16_t* d_vec16 = nullptr;  // per canonical vector: (dx, dy)
+  int32_t* d_shear = nullptr;  // per canonical vector: the shear of its phase-0 counts' layout
 };
 
 }  // namespace lpf

@@ -86,6 +86,7 @@ def test_newer_entry_points_reject_bad_arguments_on_host():
     assert lib.lpf_set_checked(None, 1) == -1
     assert lib.lpf_set_checked(p.handle, 2) == -1
     assert lib.lpf_paths_set_selftest(None, 1) == -1
+    assert lib.lpf_batch_work(None, v, v, None) == -1
     assert lpf.lpf_strerror(-6).startswith("pixel value")
     bad = lpf.SaParams(100, 10, 1, 1e-3, 0.01, 64, 1, 1, 7)   # phases outside {0..3}
     assert lib.lpf_sa_create(v, 8, 8, p.handle, v, v, ctypes.byref(bad), None, ctypes.byref(h)) == -1

@@ -38,6 +38,10 @@ def test_batch_matches_oracle(gpu_lib, use_graph):
         assert gpu_lib.lpf_batch_status(b) == 0
         for img, p, c in zip(imgs, paths, counts):
             np.testing.assert_array_equal(c.cpu().numpy(), oracle.lpf_full(img, p.rx, p.ry))
+        # the walked work of the run: every image walked some of its program, at
+        # most all of it
+        executed, nominal = gpu_lib.lpf_batch_work(b)
+        assert (nominal > 0).all() and (executed > 0).all() and (executed <= nominal).all()
 
 
 def test_batch_every_words_per_thread_choice(gpu_lib):

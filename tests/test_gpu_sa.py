@@ -45,9 +45,10 @@ def test_proposals_match_oracle(gpu_lib):
     np.testing.assert_array_equal(u.cpu().numpy(), ref_u)
 
 
-@pytest.mark.parametrize("kmin,kmax", [(1, 1), (8, 64), (32, 4096)])
-def test_trajectory_equals_sequential_oracle(gpu_lib, kmin, kmax):
-    H = W = 24
+@pytest.mark.parametrize("kmin,kmax,H,W", [(1, 1, 24, 24), (8, 64, 24, 24), (32, 4096, 24, 24), (1, 1, 20, 28),
+                                            (8, 64, 28, 20)])
+def test_trajectory_equals_sequential_oracle(gpu_lib, kmin, kmax, H, W):
+    # (non-square cells take the other branch of the counts' sheared layout)
     r = 6
     cell, target = _setup(H, W, r)
     n_step, c_max, s_max = 600, 60, 6
