@@ -106,10 +106,11 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) delta_kernel(const uint8_t* 
   }
 }
 
-// z[v][y][x] = number of phase-0 pixels of S(v) + (x, y) for every canonical
-// vector and translation, from the extended cell (0/1 bytes).  Blocks stage
-// the cell once and take vectors at the grid stride; threads take
-// translations.
+// Phase-0 count of S(v) + (x, y) for every canonical vector and translation,
+// from the extended cell (0/1 bytes), at delta_z_index in the sheared layout
+// (SHEARED, g.shear set) or the unsheared one.  Blocks stage the cell once
+// and take vectors at the grid stride; threads take translations.
+template <bool SHEARED>
 __global__ void __launch_bounds__(kDeltaThreads) z_init_kernel(const uint8_t* __restrict__ ext, DeltaArgs g,
                                                                uint8_t* __restrict__ z, int* __restrict__ status) {
   extern __shared__ __align__(16) uint8_t sm[];
@@ -124,17 +125,12 @@ __global__ void __launch_bounds__(kDeltaThreads) z_init_kernel(const uint8_t* __
     const int o0 = __ldg(g.dptr + v), L1 = __ldg(g.dptr + v + 1) - o0;
     int dx, dy;
     delta_vector(g, v, dx, dy);
-    const int m = g.shear ? __ldg(g.shear + v) : 0;
+    const int m = SHEARED ? __ldg(g.shear + v) : 0;
     uint8_t* zv = z + (int64_t)v * hw;
     for (int p = threadIdx.x; p < hw; p += blockDim.x) {
-      // p runs over the vector's sheared layout (delta_z_index)
+      // p runs over the vector's layout (delta_z_index)
       int x, y;
-      if (m == 0) {  // unsheared: rows of W bytes (x-major), columns of H bytes (y-major)
-        if (dy > (dx < 0 ? -dx : dx)) { x = p / g.H; y = p - x * g.H; }
-        else { y = p / g.W; x = p - y * g.W; }
-      } else {
-        delta_z_translation(g, dx, dy, m, p, x, y);
-      }
+      delta_z_translation(g, dx, dy, m, p, x, y);
       const uint8_t* base = sm + (y + g.ry) * g.We + (x + g.rx);
       int c = 0;
       for (int k = 0; k < L1; ++k) c += base[__ldg(g.doff + o0 + k)] == 0;
@@ -319,8 +315,11 @@ int delta_prepare(lpf_paths* p, int H, int W, int K) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(delta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    optin - (int)fa.sharedSizeBytes);
     cudaFuncAttributes fz;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fz, z_init_kernel);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(z_init_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fz, z_init_kernel<true>);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(z_init_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   optin - (int)fz.sharedSizeBytes);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fz, z_init_kernel<false>);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(z_init_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    optin - (int)fz.sharedSizeBytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(sa_batch_kernel_entry(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    optin - (int)fs.sharedSizeBytes);
@@ -405,8 +404,9 @@ int delta_z_prepare(lpf_paths* p, int H, int W) {
 }
 
 void z_init_launch(const uint8_t* ext, const DeltaArgs& g, uint8_t* z, int* status, cudaStream_t s) {
-  z_init_kernel<<<std::min<int64_t>(g.n_canon, 2 * (int64_t)(g_sms > 0 ? g_sms : 152)), kDeltaThreads, g.ext_bytes,
-                  s>>>(ext, g, z, status);
+  const int blocks = (int)std::min<int64_t>(g.n_canon, 2 * (int64_t)(g_sms > 0 ? g_sms : 152));
+  if (g.shear) z_init_kernel<true><<<blocks, kDeltaThreads, g.ext_bytes, s>>>(ext, g, z, status);
+  else z_init_kernel<false><<<blocks, kDeltaThreads, g.ext_bytes, s>>>(ext, g, z, status);
 }
 
 int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* paths, const int32_t* pairs_dev,
@@ -446,8 +446,7 @@ int delta_swap_run(const uint8_t* img_dev, int32_t H, int32_t W, lpf_paths* path
     // each warp touches (the annealer's sheared layout costs it 5 more
     // instructions per lookup)
     g.shear = nullptr;
-    z_init_kernel<<<std::min<int64_t>(g.n_canon, 2 * (int64_t)(g_sms > 0 ? g_sms : 152)), kDeltaThreads, g.ext_bytes,
-                    s>>>(paths->d_ext, g, g.z, paths->d_status);
+    z_init_launch(paths->d_ext, g, g.z, paths->d_status, s);
     if (paths->ev_start) cudaEventRecord(paths->ev_start, s);
     // a warp per candidate: enough candidate groups of 16 for a few warps per SM slot
     grid.y = (unsigned)std::max(1, std::min((K + kDeltaWarps - 1) / kDeltaWarps,

@@ -244,11 +244,11 @@ __device__ __forceinline__ void delta_z_translation(const DeltaArgs& g, int dx, 
   if (dy > (dx < 0 ? -dx : dx)) {
     const int c = p / g.H;
     y = p - c * g.H;
-    x = delta_wrap(g, c + delta_shift(y, m), g.W);
+    x = m == 0 ? c : delta_wrap(g, c + delta_shift(y, m), g.W);
   } else {
     const int r = p / g.W;
     x = p - r * g.W;
-    y = delta_wrap(g, r + delta_shift(x, m), g.H);
+    y = m == 0 ? r : delta_wrap(g, r + delta_shift(x, m), g.H);
   }
 }
 
@@ -283,7 +283,7 @@ __device__ __forceinline__ bool delta_on_segment(const DeltaArgs& g, int o0, int
 
 // Same contract as delta_walk_vectors (a phase 1, b phase 0; the warp's
 // vectors v = v0, v0 + vstep, ...; lane 0 writes and returns), from the
-// phase-0 counts g.z.
+// phase-0 counts g.z in the unsheared layout (g.shear null).
 __device__ __forceinline__ float delta_lookup_vectors_strided(const DeltaArgs& g, int a, int b, int v0, int v1,
                                                               int vstep, int lane, int32_t* dcounts_k,
                                                               const DeltaTerms& dt);
@@ -308,7 +308,6 @@ __device__ __forceinline__ float delta_lookup_vectors_strided(const DeltaArgs& g
     const int L1 = __ldg(g.dptr + v + 1) - o0;
     int dx, dy;
     delta_vector(g, v, dx, dy);
-    const int m = g.shear ? __ldg(g.shear + v) : 0;
     const uint8_t* zv = g.z + (int64_t)v * hw;
     int d0 = 0, d1 = 0;
     // four lookups per lane in flight: offsets, then counts, then the tests
@@ -326,7 +325,7 @@ __device__ __forceinline__ float delta_lookup_vectors_strided(const DeltaArgs& g
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)  // read at L2 (the annealer updates z in place)
-        zs[u] = t0 + 32 * u + lane < 2 * L1 ? __ldcg(zv + delta_z_index(g, dx, dy, m, xs[u], ys[u])) : -1;
+        zs[u] = t0 + 32 * u + lane < 2 * L1 ? __ldcg(zv + delta_z_index(g, dx, dy, 0, xs[u], ys[u])) : -1;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int t = t0 + 32 * u + lane;
