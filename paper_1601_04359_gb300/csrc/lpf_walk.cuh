@@ -137,7 +137,9 @@ __device__ __forceinline__ void tile_valid(int y, int H, int W, int nw, int j0, 
 // the lane's first staged word (row = the lane's translation row).  Counts
 // go to counts[base + vec] (phase 0) and counts[n_full + base + vec] (phase
 // 1).  Returns the pixels this warp walked (for the work statistics).
-template <int T>
+// UNROLL4: pair groups four per loop iteration (less loop control, more
+// code: the batched kernel, which inlines every T, keeps two).
+template <int T, bool UNROLL4 = true>
 __device__ __forceinline__ uint32_t walk_unit(const uint4* __restrict__ prog, uint32_t pc, uint32_t end,
                                               const uint32_t* lane_base, int y, int H, int W, int nw, int j0,
                                               const uint32_t* __restrict__ sel, int lane,
@@ -171,16 +173,33 @@ __device__ __forceinline__ uint32_t walk_unit(const uint4* __restrict__ prog, ui
     walked += n;
     bool dead = false;
     const uint4* g = prog + rec + 1u;
-    // two groups (8 pixels) per iteration: both program loads issued
-    // together, one vote after them
+    // four groups (16 pixels) per iteration, their program loads issued
+    // together, a vote after every two (8 pixels); then pairs of groups
     uint32_t q = 0;
-    for (; q + 2u <= n_pg; q += 2u) {
-      const uint4 P0 = __ldg(g + q), P1 = __ldg(g + q + 1u);
+    for (; UNROLL4 && q + 4u <= n_pg; q += 4u) {
+      const uint4 P0 = __ldg(g + q), P1 = __ldg(g + q + 1u), P2 = __ldg(g + q + 2u), P3 = __ldg(g + q + 3u);
       walk_pairs2<T>(lane_base, P0, m1, m0);
       walk_pairs2<T>(lane_base, P1, m1, m0);
       if (skip != 0u && warp_empty<T>(m1, m0)) {
         dead = true;
         walked -= n - 4u * (q + 2u);  // pixels not walked (pair groups hold four pixels of the record)
+        break;
+      }
+      walk_pairs2<T>(lane_base, P2, m1, m0);
+      walk_pairs2<T>(lane_base, P3, m1, m0);
+      if (skip != 0u && warp_empty<T>(m1, m0)) {
+        dead = true;
+        walked -= n - 4u * (q + 4u);
+        break;
+      }
+    }
+    for (; !dead && q + 2u <= n_pg; q += 2u) {
+      const uint4 P0 = __ldg(g + q), P1 = __ldg(g + q + 1u);
+      walk_pairs2<T>(lane_base, P0, m1, m0);
+      walk_pairs2<T>(lane_base, P1, m1, m0);
+      if (skip != 0u && warp_empty<T>(m1, m0)) {
+        dead = true;
+        walked -= n - 4u * (q + 2u);
         break;
       }
     }
