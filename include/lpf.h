@@ -705,6 +705,10 @@ int lpf_cnn_gradients(lpf_cnn *cnn, const uint8_t *cell_dev, const int32_t *pair
  * One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean loss of B
  * snapshots: cells_dev uint8 [B][H][W], pairs_dev int32 [B][n][2], y_dev
  * float [B][n]; loss_dev (may be NULL) receives the mean loss before the step.
+ * Up to 8 snapshots go through the network together (one launch per layer
+ * and pass); the first call that trains on more snapshots than any before
+ * allocates the training buffers and synchronises the device.  The result
+ * does not depend on that grouping.
  */
 int lpf_cnn_train_step(lpf_cnn *cnn, const uint8_t *cells_dev, int32_t B, const int32_t *pairs_dev,
                        const float *y_dev, int32_t n, float lr, float *loss_dev, lpf_stream_t stream);

@@ -37,8 +37,11 @@ constexpr int kCh[kLayers + 1] = {2, 32, 64, 48, 32, 2};
 
 inline int layer_w_size(int l) { return 9 * kCh[l] * kCh[l + 1]; }
 
-// Input features [H][W][2]: cell value and interfacial mask (torus).
+// Input features [H][W][2]: cell value and interfacial mask (torus); cell
+// blockIdx.y of a batch of cells [B][H][W] into x [B][H][W][2].
 __global__ void cnn_features_kernel(const uint8_t* __restrict__ cell, int H, int W, float* __restrict__ x) {
+  cell += (int64_t)blockIdx.y * H * W;
+  x += (int64_t)blockIdx.y * H * W * 2;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < H * W; p += gridDim.x * blockDim.x) {
     const int y = p / W, xx = p - y * W;
     const int v = cell[p] != 0;
@@ -124,13 +127,19 @@ __device__ __forceinline__ void stage_halo(const float* __restrict__ in, int H, 
 // layer's output channel, n = its input channel, B[tap][k][n] = w[8 - tap][n][k]
 // (w of shape [9][N][K]).  Optional ReLU; optional mask: out = 0 where
 // mask[p][n] <= 0 (the ReLU derivative of the layer input).  K <= KC, N <= NC.
+// blockIdx.z selects a snapshot of a batch: in, out and mask advance by
+// in_stride, out_stride and out_stride floats per snapshot.
 template <int KC, int NC, bool SPLIT>
 __global__ void __launch_bounds__(kConvThreads) cnn_conv_mma_kernel(const float* __restrict__ in, int H, int W,
                                                                     int K, int N, const __nv_bfloat16* __restrict__ w,
                                                                     int flip, const float* __restrict__ bias,
                                                                     int relu, const float* __restrict__ mask,
-                                                                    float* __restrict__ out) {
+                                                                    float* __restrict__ out, int64_t in_stride,
+                                                                    int64_t out_stride) {
   constexpr int KS = KC + 8;
+  in += blockIdx.z * in_stride;
+  out += blockIdx.z * out_stride;
+  if (mask) mask += blockIdx.z * out_stride;
   extern __shared__ __align__(16) __nv_bfloat16 csm[];
   __nv_bfloat16* s_in = csm;                 // [kHalo][KS]
   __nv_bfloat16* s_w = csm + kHalo * KS;     // [9][NC][KS]  (n rows, k contiguous)
@@ -211,18 +220,23 @@ __global__ void __launch_bounds__(kConvThreads) cnn_conv_mma_kernel(const float*
 // g[p][co] and part_b[blk][co] = sum_p g[p][co].  GEMM per tap with M = ci,
 // N = co, K = the tile's pixels; warp t computes tap t.  Pixels outside the
 // image contribute nothing (their gradient rows are staged as zeros).
+// blockIdx.z selects a snapshot (in and g advance by in_stride, g_stride
+// floats); its tiles' partials follow those of the snapshots before it.
 template <int KC, int NC>
 __global__ void __launch_bounds__(kDwThreads) cnn_dw_mma_kernel(const float* __restrict__ in,
                                                                 const float* __restrict__ g, int H, int W, int CIN,
                                                                 int COUT, float* __restrict__ part,
-                                                                float* __restrict__ part_b) {
+                                                                float* __restrict__ part_b, int64_t in_stride,
+                                                                int64_t g_stride) {
+  in += blockIdx.z * in_stride;
+  g += blockIdx.z * g_stride;
   constexpr int KS = KC + 8, NS = NC + 8;
   extern __shared__ __align__(16) __nv_bfloat16 csm[];
   __nv_bfloat16* s_in = csm;                          // [kHalo][KS]
   __nv_bfloat16* s_g = csm + kHalo * KS;              // [kTH * kTW][NS], gradient high terms
   __nv_bfloat16* s_gl = s_g + kTH * kTW * NS;         // and low terms (the gradient as hi + lo)
   const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-  const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+  const int blk = ((int)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   stage_halo<KC>(in, H, W, CIN, x0, y0, s_in);
   for (int i = threadIdx.x; i < kTH * kTW * (NC / 2); i += blockDim.x) {
     const int q = i / (NC / 2), n = 2 * (i - q * (NC / 2));
@@ -305,13 +319,20 @@ __global__ void __launch_bounds__(kDwThreads) cnn_dw_mma_kernel(const float* __r
       }
 }
 
-// dst[i] (+)= sum over blocks b of part[b][i], blocks in order (deterministic).
-__global__ void cnn_reduce_parts_kernel(const float* __restrict__ part, int n_blk, int n, float* __restrict__ dst,
-                                        int accumulate) {
+// For each snapshot z in order: s_z = sum over its blocks b of
+// part[z][b][i], blocks in order; dst[i] = s_0 (or dst[i] + s_0 when
+// accumulating), then dst[i] + s_1, ... (deterministic, and the same
+// additions as reducing the snapshots one by one).
+__global__ void cnn_reduce_parts_kernel(const float* __restrict__ part, int n_blk, int n_snap, int n,
+                                        float* __restrict__ dst, int accumulate) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float s = 0.0f;
-    for (int b = 0; b < n_blk; ++b) s += part[(int64_t)b * n + i];
-    dst[i] = accumulate ? dst[i] + s : s;
+    float d = accumulate ? dst[i] : 0.0f;
+    for (int z = 0; z < n_snap; ++z) {
+      float s = 0.0f;
+      for (int b = 0; b < n_blk; ++b) s += part[((int64_t)z * n_blk + b) * n + i];
+      d = (z == 0 && !accumulate) ? s : d + s;
+    }
+    dst[i] = d;
   }
 }
 
@@ -343,13 +364,18 @@ __device__ __forceinline__ float warp_fmax(float v) {
   return v;
 }
 
-// Loss of one snapshot and dL/d out (two pixels per candidate), one warp:
-// candidates in chunks of 32 (lane = candidate), chunks in order
-// (deterministic).  g must be zeroed beforehand.
-__global__ void cnn_loss_kernel(const float* __restrict__ out, int W, const int32_t* __restrict__ pairs,
-                                const float* __restrict__ y, int n, float* __restrict__ g, float* __restrict__ loss,
-                                float scale) {
-  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+// Loss of snapshot blockIdx.x and dL/d out (two pixels per candidate), one
+// warp: candidates in chunks of 32 (lane = candidate), chunks in order
+// (deterministic).  out and g are [B][npix][2], pairs [B][n][2], y [B][n];
+// g must be zeroed beforehand; loss[z] receives the snapshot's loss.
+__global__ void cnn_loss_kernel(const float* __restrict__ out, int npix, const int32_t* __restrict__ pairs,
+                                const float* __restrict__ y, int n, float* __restrict__ g, float* __restrict__ loss) {
+  if (threadIdx.x >= 32) return;
+  const int z = blockIdx.x;
+  out += (int64_t)z * npix * 2;
+  g += (int64_t)z * npix * 2;
+  pairs += (int64_t)z * n * 2;
+  y += (int64_t)z * n;
   const int lane = threadIdx.x;
   float l = 0.0f;
   for (int i0 = 0; i0 < n; i0 += 32) {
@@ -366,16 +392,22 @@ __global__ void cnn_loss_kernel(const float* __restrict__ out, int W, const int3
     warp_scatter_add(g, 2 * a + 1, r / n, on);
     warp_scatter_add(g, 2 * b, r / n, on);
   }
-  if (lane == 0 && loss) *loss += l / n * scale;
+  if (lane == 0) loss[z] = l / n;
 }
 
 // Listwise loss of one snapshot: L = logsumexp(s) - sum_i q_i s_i with
 // s_i = s1[a_i] + s0[b_i] and q = softmax(y / beta); dL/ds_i = p_i - q_i on
-// both pixels of candidate i.  One warp, fixed reduction order (deterministic).
-__global__ void cnn_listwise_kernel(const float* __restrict__ out, const int32_t* __restrict__ pairs,
+// both pixels of candidate i.  One warp per snapshot (blockIdx.x; layouts as
+// cnn_loss_kernel), fixed reduction order (deterministic).
+__global__ void cnn_listwise_kernel(const float* __restrict__ out, int npix, const int32_t* __restrict__ pairs,
                                     const float* __restrict__ y, int n, float beta, float* __restrict__ g,
-                                    float* __restrict__ loss, float scale) {
-  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+                                    float* __restrict__ loss) {
+  if (threadIdx.x >= 32) return;
+  const int z = blockIdx.x;
+  out += (int64_t)z * npix * 2;
+  g += (int64_t)z * npix * 2;
+  pairs += (int64_t)z * n * 2;
+  y += (int64_t)z * n;
   const int lane = threadIdx.x;
   float smax = -3.0e38f, ymax = -3.0e38f;
   for (int i = lane; i < n; i += 32) {
@@ -409,7 +441,14 @@ __global__ void cnn_listwise_kernel(const float* __restrict__ out, const int32_t
     warp_scatter_add(g, 2 * b, d, on);
   }
   lq = warp_fsum(lq);
-  if (lane == 0 && loss) *loss += (smax + logf(zs) - lq) * scale;
+  if (lane == 0) loss[z] = smax + logf(zs) - lq;
+}
+
+// *total += loss[z] * scale for the snapshots in order (one thread).
+__global__ void cnn_add_losses_kernel(const float* __restrict__ loss, int n_snap, float scale,
+                                      float* __restrict__ total) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int z = 0; z < n_snap; ++z) *total += loss[z] * scale;
 }
 
 __global__ void cnn_to_bf16_kernel(const float* __restrict__ m, int n, __nv_bfloat16* __restrict__ w) {
@@ -445,11 +484,17 @@ struct lpf_cnn {
   float* d_g = nullptr;       // gradient accumulator
   __nv_bfloat16* d_wbf = nullptr;
   int* d_isw = nullptr;       // parameter index -> bf16 index (or -1 for biases)
-  float* d_act[lpf::kLayers + 1] = {};
-  float* d_gact = nullptr;    // gradient buffers (two, ping-pong)
+  float* d_act[lpf::kLayers + 1] = {};  // activations of the scored cell [H][W][C_l] (fixed at creation)
+  // Training: activations, gradients and partials for up to `cap` snapshots
+  // at once (allocated by the first training call, grown, never moved
+  // under the scoring buffers above, which captured graphs may hold).
+  int cap = 0;
+  float* d_tact[lpf::kLayers + 1] = {};  // [cap][H][W][C_l]
+  float* d_gact = nullptr;    // gradient buffers (two, ping-pong) [cap][H][W][64]
   float* d_gact2 = nullptr;
-  float* d_part = nullptr;    // per-block weight-gradient partials [blocks][9 * 64 * 64]
-  float* d_part_b = nullptr;  // per-block bias-gradient partials [blocks][64]
+  float* d_part = nullptr;    // per-block weight-gradient partials [cap][blocks][9 * 64 * 64]
+  float* d_part_b = nullptr;  // per-block bias-gradient partials [cap][blocks][64]
+  float* d_loss = nullptr;    // per-snapshot losses [cap]
   int n_blk = 0;              // output tiles (blocks) of a convolution
   int64_t step = 0;
   int loss_kind = 0;          // 0: squared error, 1: listwise cross-entropy
@@ -457,6 +502,29 @@ struct lpf_cnn {
 };
 
 namespace lpf {
+
+// Buffers for nb snapshots at once (grown, never shrunk; synchronises the
+// device when it grows).
+constexpr int kTrainChunk = 8;  // snapshots per batched forward/backward
+static int cnn_reserve(lpf_cnn* c, int nb) {
+  if (nb <= c->cap) return LPF_OK;
+  cudaDeviceSynchronize();
+  for (int l = 0; l <= kLayers; ++l) { cudaFree(c->d_tact[l]); c->d_tact[l] = nullptr; }
+  cudaFree(c->d_gact); cudaFree(c->d_gact2); cudaFree(c->d_part); cudaFree(c->d_part_b); cudaFree(c->d_loss);
+  c->d_gact = c->d_gact2 = c->d_part = c->d_part_b = c->d_loss = nullptr;
+  c->cap = 0;
+  const size_t npix = (size_t)c->H * c->W, b = (size_t)nb;
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l <= kLayers && e == cudaSuccess; ++l) e = cudaMalloc(&c->d_tact[l], b * npix * kCh[l] * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_gact, b * npix * 64 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_gact2, b * npix * 64 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_part, b * c->n_blk * 9 * 64 * 64 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_part_b, b * c->n_blk * 64 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_loss, b * 4);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  c->cap = nb;
+  return LPF_OK;
+}
 
 static int cnn_alloc(lpf_cnn* c) {
   int64_t off = 0, woff = 0;
@@ -478,12 +546,8 @@ static int cnn_alloc(lpf_cnn* c) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_g, np * 4);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_wbf, (size_t)woff * 2);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_isw, np * 4);
-  for (int l = 0; l <= kLayers && e == cudaSuccess; ++l) e = cudaMalloc(&c->d_act[l], npix * kCh[l] * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_gact, npix * 64 * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_gact2, npix * 64 * 4);
   c->n_blk = ((c->W + kTW - 1) / kTW) * ((c->H + kTH - 1) / kTH);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_part, (size_t)c->n_blk * 9 * 64 * 64 * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_part_b, (size_t)c->n_blk * 64 * 4);
+  for (int l = 0; l <= kLayers && e == cudaSuccess; ++l) e = cudaMalloc(&c->d_act[l], npix * kCh[l] * 4);
   if (e == cudaSuccess) e = cudaMemset(c->d_m, 0, np * 4);
   if (e == cudaSuccess) e = cudaMemset(c->d_v, 0, np * 4);
   if (e != cudaSuccess) return set_cuda_error(e);
@@ -507,8 +571,9 @@ static size_t dw_smem() { return (size_t)(kHalo * (KC + 8) + 2 * kTH * kTW * (NC
 // flip = 1 (the input gradient) carries the incoming gradient as two bfloat16 terms.
 template <int KC, int NC>
 static void conv_mma(const float* in, int H, int W, int K, int N, const __nv_bfloat16* w, int flip,
-                     const float* bias, int relu, const float* mask, float* out, cudaStream_t s) {
-  const dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
+                     const float* bias, int relu, const float* mask, float* out, int nb, cudaStream_t s) {
+  const dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, nb);
+  const int64_t in_stride = (int64_t)H * W * K, out_stride = (int64_t)H * W * N;
   static bool attr[2] = {false, false};  // dynamic shared memory above 48 KB must be allowed once per kernel
   if (flip) {
     const size_t smem = conv_smem<KC, NC, true>();
@@ -517,7 +582,7 @@ static void conv_mma(const float* in, int H, int W, int K, int N, const __nv_bfl
       attr[1] = true;
     }
     cnn_conv_mma_kernel<KC, NC, true><<<grid, kConvThreads, smem, s>>>(in, H, W, K, N, w, flip, bias, relu, mask,
-                                                                        out);
+                                                                        out, in_stride, out_stride);
   } else {
     const size_t smem = conv_smem<KC, NC, false>();
     if (!attr[0]) {
@@ -526,88 +591,100 @@ static void conv_mma(const float* in, int H, int W, int K, int N, const __nv_bfl
       attr[0] = true;
     }
     cnn_conv_mma_kernel<KC, NC, false><<<grid, kConvThreads, smem, s>>>(in, H, W, K, N, w, flip, bias, relu, mask,
-                                                                         out);
+                                                                         out, in_stride, out_stride);
   }
 }
 
 // Convolution with K input and N output channels of the GEMM (see the kernel).
 static void conv_any(int K, int N, const float* in, int H, int W, const __nv_bfloat16* w, int flip,
-                     const float* bias, int relu, const float* mask, float* out, cudaStream_t s) {
+                     const float* bias, int relu, const float* mask, float* out, int nb, cudaStream_t s) {
   const int key = K * 1000 + N;
   switch (key) {
     // forward layers
-    case 2 * 1000 + 32: conv_mma<16, 32>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
-    case 32 * 1000 + 64: conv_mma<32, 64>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
-    case 64 * 1000 + 48: conv_mma<64, 48>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
-    case 48 * 1000 + 32: conv_mma<48, 32>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
-    case 32 * 1000 + 2: conv_mma<32, 8>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
+    case 2 * 1000 + 32: conv_mma<16, 32>(in, H, W, K, N, w, flip, bias, relu, mask, out, nb, s); break;
+    case 32 * 1000 + 64: conv_mma<32, 64>(in, H, W, K, N, w, flip, bias, relu, mask, out, nb, s); break;
+    case 64 * 1000 + 48: conv_mma<64, 48>(in, H, W, K, N, w, flip, bias, relu, mask, out, nb, s); break;
+    case 48 * 1000 + 32: conv_mma<48, 32>(in, H, W, K, N, w, flip, bias, relu, mask, out, nb, s); break;
+    case 32 * 1000 + 2: conv_mma<32, 8>(in, H, W, K, N, w, flip, bias, relu, mask, out, nb, s); break;
     // transposed (input gradients of layers 1..4)
-    case 64 * 1000 + 32: conv_mma<64, 32>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
-    case 48 * 1000 + 64: conv_mma<48, 64>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
-    case 32 * 1000 + 48: conv_mma<32, 48>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;
-    default: conv_mma<16, 32>(in, H, W, K, N, w, flip, bias, relu, mask, out, s); break;  // 2 -> 32
+    case 64 * 1000 + 32: conv_mma<64, 32>(in, H, W, K, N, w, flip, bias, relu, mask, out, nb, s); break;
+    case 48 * 1000 + 64: conv_mma<48, 64>(in, H, W, K, N, w, flip, bias, relu, mask, out, nb, s); break;
+    case 32 * 1000 + 48: conv_mma<32, 48>(in, H, W, K, N, w, flip, bias, relu, mask, out, nb, s); break;
+    default: conv_mma<16, 32>(in, H, W, K, N, w, flip, bias, relu, mask, out, nb, s); break;  // 2 -> 32
   }
 }
 
 template <int KC, int NC>
 static void dw_mma(const float* in, const float* g, int H, int W, int CIN, int COUT, float* part, float* part_b,
-                   cudaStream_t s) {
+                   int nb, cudaStream_t s) {
   const size_t smem = dw_smem<KC, NC>();
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(cnn_dw_mma_kernel<KC, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  const dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
-  cnn_dw_mma_kernel<KC, NC><<<grid, kDwThreads, smem, s>>>(in, g, H, W, CIN, COUT, part, part_b);
+  const dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, nb);
+  cnn_dw_mma_kernel<KC, NC><<<grid, kDwThreads, smem, s>>>(in, g, H, W, CIN, COUT, part, part_b,
+                                                            (int64_t)H * W * CIN, (int64_t)H * W * COUT);
 }
 
 static void dw_any(int CIN, int COUT, const float* in, const float* g, int H, int W, float* part, float* part_b,
-                   cudaStream_t s) {
+                   int nb, cudaStream_t s) {
   switch (CIN * 1000 + COUT) {
-    case 2 * 1000 + 32: dw_mma<16, 32>(in, g, H, W, CIN, COUT, part, part_b, s); break;
-    case 32 * 1000 + 64: dw_mma<32, 64>(in, g, H, W, CIN, COUT, part, part_b, s); break;
-    case 64 * 1000 + 48: dw_mma<64, 48>(in, g, H, W, CIN, COUT, part, part_b, s); break;
-    case 48 * 1000 + 32: dw_mma<48, 32>(in, g, H, W, CIN, COUT, part, part_b, s); break;
-    default: dw_mma<32, 8>(in, g, H, W, CIN, COUT, part, part_b, s); break;  // 32 -> 2
+    case 2 * 1000 + 32: dw_mma<16, 32>(in, g, H, W, CIN, COUT, part, part_b, nb, s); break;
+    case 32 * 1000 + 64: dw_mma<32, 64>(in, g, H, W, CIN, COUT, part, part_b, nb, s); break;
+    case 64 * 1000 + 48: dw_mma<64, 48>(in, g, H, W, CIN, COUT, part, part_b, nb, s); break;
+    case 48 * 1000 + 32: dw_mma<48, 32>(in, g, H, W, CIN, COUT, part, part_b, nb, s); break;
+    default: dw_mma<32, 8>(in, g, H, W, CIN, COUT, part, part_b, nb, s); break;  // 32 -> 2
   }
 }
 
-void cnn_forward(lpf_cnn* c, const uint8_t* cell, cudaStream_t s) {
+// Forward pass of nb cells [nb][H][W] into act (room for nb snapshots).
+static void cnn_forward_batch(lpf_cnn* c, const uint8_t* cells, int nb, float* const* act, cudaStream_t s) {
   const int npix = c->H * c->W;
-  cnn_features_kernel<<<(npix + 255) / 256, 256, 0, s>>>(cell, c->H, c->W, c->d_act[0]);
+  cnn_features_kernel<<<dim3((npix + 255) / 256, nb), 256, 0, s>>>(cells, c->H, c->W, act[0]);
   for (int l = 0; l < kLayers; ++l)
-    conv_any(kCh[l], kCh[l + 1], c->d_act[l], c->H, c->W, c->d_wbf + c->wb_off[l], 0, c->d_p + c->b_off[l],
-             l < kLayers - 1, nullptr, c->d_act[l + 1], s);
+    conv_any(kCh[l], kCh[l + 1], act[l], c->H, c->W, c->d_wbf + c->wb_off[l], 0, c->d_p + c->b_off[l],
+             l < kLayers - 1, nullptr, act[l + 1], nb, s);
 }
 
-// Forward, loss and backward of one snapshot; gradients added into d_g
-// (or written when accumulate == 0); loss added into *loss_dev (scaled).
-static void cnn_fwd_bwd(lpf_cnn* c, const uint8_t* cell, const int32_t* pairs, const float* y, int n, int accumulate,
-                        float* loss_dev, float loss_scale, cudaStream_t s) {
+// Scores of one cell into the scoring buffers.
+void cnn_forward(lpf_cnn* c, const uint8_t* cell, cudaStream_t s) { cnn_forward_batch(c, cell, 1, c->d_act, s); }
+
+// Forward, loss and backward of nb snapshots in one set of launches (their
+// tiles side by side in each grid); their gradients are added into d_g in
+// snapshot order (written first when accumulate == 0) and their losses,
+// times loss_scale, into *loss_dev (when not null) in the same order -- the
+// same additions as running the snapshots one after another.
+static int cnn_fwd_bwd(lpf_cnn* c, const uint8_t* cells, int nb, const int32_t* pairs, const float* y, int n,
+                       int accumulate, float* loss_dev, float loss_scale, cudaStream_t s) {
   const int H = c->H, W = c->W, npix = H * W;
-  cnn_forward(c, cell, s);
+  int rc = cnn_reserve(c, nb);
+  if (rc) return rc;
+  cnn_forward_batch(c, cells, nb, c->d_tact, s);
   float* g = c->d_gact;
   float* g2 = c->d_gact2;
-  cudaMemsetAsync(g, 0, (size_t)npix * kCh[kLayers] * 4, s);
+  cudaMemsetAsync(g, 0, (size_t)nb * npix * kCh[kLayers] * 4, s);
   if (c->loss_kind == 1)
-    cnn_listwise_kernel<<<1, 32, 0, s>>>(c->d_act[kLayers], pairs, y, n, c->beta, g, loss_dev, loss_scale);
+    cnn_listwise_kernel<<<nb, 32, 0, s>>>(c->d_tact[kLayers], npix, pairs, y, n, c->beta, g, c->d_loss);
   else
-    cnn_loss_kernel<<<1, 32, 0, s>>>(c->d_act[kLayers], W, pairs, y, n, g, loss_dev, loss_scale);
+    cnn_loss_kernel<<<nb, 32, 0, s>>>(c->d_tact[kLayers], npix, pairs, y, n, g, c->d_loss);
+  if (loss_dev) cnn_add_losses_kernel<<<1, 1, 0, s>>>(c->d_loss, nb, loss_scale, loss_dev);
   for (int l = kLayers - 1; l >= 0; --l) {
     const int cin = kCh[l], cout = kCh[l + 1];
     // g = dL/d(pre-activation output of layer l) here (ReLU mask already applied)
-    dw_any(cin, cout, c->d_act[l], g, H, W, c->d_part, c->d_part_b, s);
+    dw_any(cin, cout, c->d_tact[l], g, H, W, c->d_part, c->d_part_b, nb, s);
     const int nw_l = 9 * cin * cout;
-    cnn_reduce_parts_kernel<<<(nw_l + 255) / 256, 256, 0, s>>>(c->d_part, c->n_blk, nw_l, c->d_g + c->w_off[l],
+    cnn_reduce_parts_kernel<<<(nw_l + 255) / 256, 256, 0, s>>>(c->d_part, c->n_blk, nb, nw_l, c->d_g + c->w_off[l],
                                                                 accumulate);
-    cnn_reduce_parts_kernel<<<1, 64, 0, s>>>(c->d_part_b, c->n_blk, cout, c->d_g + c->b_off[l], accumulate);
+    cnn_reduce_parts_kernel<<<1, 64, 0, s>>>(c->d_part_b, c->n_blk, nb, cout, c->d_g + c->b_off[l], accumulate);
     if (l > 0) {
       // dL/d act[l] = transposed conv of g, then times the ReLU mask of act[l]
-      conv_any(cout, cin, g, H, W, c->d_wbf + c->wb_off[l], 1, nullptr, 0, c->d_act[l], g2, s);
+      conv_any(cout, cin, g, H, W, c->d_wbf + c->wb_off[l], 1, nullptr, 0, c->d_tact[l], g2, nb, s);
       std::swap(g, g2);
     }
   }
+  return LPF_OK;
 }
 
 const float* cnn_scores(const lpf_cnn* c) { return c->d_act[kLayers]; }
@@ -679,7 +756,8 @@ int lpf_cnn_gradients(lpf_cnn* c, const uint8_t* cell_dev, const int32_t* pairs_
   cudaStream_t s = (cudaStream_t)stream;
   (void)cudaGetLastError();
   if (loss_dev) cudaMemsetAsync(loss_dev, 0, sizeof(float), s);
-  lpf::cnn_fwd_bwd(c, cell_dev, pairs_dev, y_dev, n, 0, loss_dev, 1.0f, s);
+  const int rc = lpf::cnn_fwd_bwd(c, cell_dev, 1, pairs_dev, y_dev, n, 0, loss_dev, 1.0f, s);
+  if (rc) return rc;
   if (grads_dev) cudaMemcpyAsync(grads_dev, c->d_g, (size_t)c->n_params * 4, cudaMemcpyDeviceToDevice, s);
   return lpf::set_cuda_error(cudaGetLastError());
 }
@@ -691,9 +769,12 @@ int lpf_cnn_train_step(lpf_cnn* c, const uint8_t* cells_dev, int32_t B, const in
   (void)cudaGetLastError();
   if (loss_dev) cudaMemsetAsync(loss_dev, 0, sizeof(float), s);
   const size_t npix = (size_t)c->H * c->W;
-  for (int b = 0; b < B; ++b)
-    lpf::cnn_fwd_bwd(c, cells_dev + b * npix, pairs_dev + (size_t)b * n * 2, y_dev + (size_t)b * n, n, b > 0,
-                     loss_dev, 1.0f / B, s);
+  for (int b0 = 0; b0 < B; b0 += lpf::kTrainChunk) {
+    const int nb = std::min(B - b0, lpf::kTrainChunk);
+    const int rc = lpf::cnn_fwd_bwd(c, cells_dev + b0 * npix, nb, pairs_dev + (size_t)b0 * n * 2,
+                                    y_dev + (size_t)b0 * n, n, b0 > 0, loss_dev, 1.0f / B, s);
+    if (rc) return rc;
+  }
   c->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.0f - std::pow(b1, (float)c->step), c2 = 1.0f - std::pow(b2, (float)c->step);
@@ -712,11 +793,15 @@ void lpf_cnn_free(lpf_cnn* c) {
   cudaFree(c->d_g);
   cudaFree(c->d_wbf);
   cudaFree(c->d_isw);
-  for (int l = 0; l <= lpf::kLayers; ++l) cudaFree(c->d_act[l]);
+  for (int l = 0; l <= lpf::kLayers; ++l) {
+    cudaFree(c->d_act[l]);
+    cudaFree(c->d_tact[l]);
+  }
   cudaFree(c->d_gact);
   cudaFree(c->d_gact2);
   cudaFree(c->d_part);
   cudaFree(c->d_part_b);
+  cudaFree(c->d_loss);
   delete c;
 }
 
