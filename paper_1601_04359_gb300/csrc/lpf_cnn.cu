@@ -127,25 +127,23 @@ __device__ __forceinline__ void stage_halo(const float* __restrict__ in, int H, 
 // layer's output channel, n = its input channel, B[tap][k][n] = w[8 - tap][n][k]
 // (w of shape [9][N][K]).  Optional ReLU; optional mask: out = 0 where
 // mask[p][n] <= 0 (the ReLU derivative of the layer input).  K <= KC, N <= NC.
-// blockIdx.z selects a snapshot of a batch: in, out and mask advance by
-// in_stride, out_stride and out_stride floats per snapshot.
+// A block stages the weights once and then takes output tiles t =
+// blockIdx.x, blockIdx.x + gridDim.x, ... of n_snap snapshots (tile t is
+// tile t mod tiles-per-snapshot of snapshot t / tiles-per-snapshot; in, out
+// and mask advance by in_stride, out_stride and out_stride floats per
+// snapshot).
 template <int KC, int NC, bool SPLIT>
 __global__ void __launch_bounds__(kConvThreads) cnn_conv_mma_kernel(const float* __restrict__ in, int H, int W,
                                                                     int K, int N, const __nv_bfloat16* __restrict__ w,
                                                                     int flip, const float* __restrict__ bias,
                                                                     int relu, const float* __restrict__ mask,
                                                                     float* __restrict__ out, int64_t in_stride,
-                                                                    int64_t out_stride) {
+                                                                    int64_t out_stride, int n_snap) {
   constexpr int KS = KC + 8;
-  in += blockIdx.z * in_stride;
-  out += blockIdx.z * out_stride;
-  if (mask) mask += blockIdx.z * out_stride;
   extern __shared__ __align__(16) __nv_bfloat16 csm[];
   __nv_bfloat16* s_in = csm;                 // [kHalo][KS]
   __nv_bfloat16* s_w = csm + kHalo * KS;     // [9][NC][KS]  (n rows, k contiguous)
   __nv_bfloat16* s_lo = s_w + 9 * NC * KS;   // SPLIT: [kHalo][KS], the input's low bfloat16 terms
-  const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-  stage_halo<KC>(in, H, W, K, x0, y0, s_in, SPLIT ? s_lo : nullptr);
   for (int i = threadIdx.x; i < 9 * NC * KC; i += blockDim.x) {
     const int k = i % KC, r = i / KC;
     const int n = r % NC, tap = r / NC;
@@ -155,63 +153,70 @@ __global__ void __launch_bounds__(kConvThreads) cnn_conv_mma_kernel(const float*
                : __bfloat162float(w[((int64_t)tap * K + k) * N + n]);
     s_w[r * KS + k] = __float2bfloat16(v);
   }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gid = lane >> 2, tig = lane & 3;
-  float acc[NC / 8][4];
+  const int tiles_x = (W + kTW - 1) / kTW, per_snap = tiles_x * ((H + kTH - 1) / kTH);
+  for (int t = blockIdx.x; t < per_snap * n_snap; t += gridDim.x) {
+    const int z = t / per_snap, tr = t - z * per_snap;
+    const int x0 = (tr % tiles_x) * kTW, y0 = (tr / tiles_x) * kTH;
+    __syncthreads();  // the previous tile's reads of s_in are done
+    stage_halo<KC>(in + z * in_stride, H, W, K, x0, y0, s_in, SPLIT ? s_lo : nullptr);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    float acc[NC / 8][4];
 #pragma unroll
-  for (int f = 0; f < NC / 8; ++f) {
-    const int n = f * 8 + tig * 2;
-    const float b0 = (bias && n < N) ? bias[n] : 0.0f, b1 = (bias && n + 1 < N) ? bias[n + 1] : 0.0f;
-    acc[f][0] = b0; acc[f][1] = b1; acc[f][2] = b0; acc[f][3] = b1;
-  }
+    for (int f = 0; f < NC / 8; ++f) {
+      const int n = f * 8 + tig * 2;
+      const float b0 = (bias && n < N) ? bias[n] : 0.0f, b1 = (bias && n + 1 < N) ? bias[n + 1] : 0.0f;
+      acc[f][0] = b0; acc[f][1] = b1; acc[f][2] = b0; acc[f][3] = b1;
+    }
 #pragma unroll 1
-  for (int tap = 0; tap < 9; ++tap) {
-    const int dy = tap / 3, dx = tap - dy * 3;
-    // A rows: the 16 output pixels of tile row `warp`, shifted by the tap
-    const __nv_bfloat16* arow = s_in + ((warp + dy) * (kTW + 2) + dx) * KS;
-    const __nv_bfloat16* brow = s_w + tap * NC * KS;
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3, dx = tap - dy * 3;
+      // A rows: the 16 output pixels of tile row `warp`, shifted by the tap
+      const __nv_bfloat16* arow = s_in + ((warp + dy) * (kTW + 2) + dx) * KS;
+      const __nv_bfloat16* brow = s_w + tap * NC * KS;
 #pragma unroll
-    for (int kk = 0; kk < KC / 16; ++kk) {
-      const int kc = kk * 16 + tig * 2;
-      const uint32_t a0 = *reinterpret_cast<const uint32_t*>(arow + gid * KS + kc);
-      const uint32_t a1 = *reinterpret_cast<const uint32_t*>(arow + (gid + 8) * KS + kc);
-      const uint32_t a2 = *reinterpret_cast<const uint32_t*>(arow + gid * KS + kc + 8);
-      const uint32_t a3 = *reinterpret_cast<const uint32_t*>(arow + (gid + 8) * KS + kc + 8);
-      uint32_t l0 = 0, l1 = 0, l2 = 0, l3 = 0;
-      if constexpr (SPLIT) {
-        const __nv_bfloat16* lrow = arow - s_in + s_lo;
-        l0 = *reinterpret_cast<const uint32_t*>(lrow + gid * KS + kc);
-        l1 = *reinterpret_cast<const uint32_t*>(lrow + (gid + 8) * KS + kc);
-        l2 = *reinterpret_cast<const uint32_t*>(lrow + gid * KS + kc + 8);
-        l3 = *reinterpret_cast<const uint32_t*>(lrow + (gid + 8) * KS + kc + 8);
-      }
+      for (int kk = 0; kk < KC / 16; ++kk) {
+        const int kc = kk * 16 + tig * 2;
+        const uint32_t a0 = *reinterpret_cast<const uint32_t*>(arow + gid * KS + kc);
+        const uint32_t a1 = *reinterpret_cast<const uint32_t*>(arow + (gid + 8) * KS + kc);
+        const uint32_t a2 = *reinterpret_cast<const uint32_t*>(arow + gid * KS + kc + 8);
+        const uint32_t a3 = *reinterpret_cast<const uint32_t*>(arow + (gid + 8) * KS + kc + 8);
+        uint32_t l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+        if constexpr (SPLIT) {
+          const __nv_bfloat16* lrow = arow - s_in + s_lo;
+          l0 = *reinterpret_cast<const uint32_t*>(lrow + gid * KS + kc);
+          l1 = *reinterpret_cast<const uint32_t*>(lrow + (gid + 8) * KS + kc);
+          l2 = *reinterpret_cast<const uint32_t*>(lrow + gid * KS + kc + 8);
+          l3 = *reinterpret_cast<const uint32_t*>(lrow + (gid + 8) * KS + kc + 8);
+        }
 #pragma unroll
-      for (int f = 0; f < NC / 8; ++f) {
-        const __nv_bfloat16* bn = brow + (f * 8 + gid) * KS + kc;
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bn), b1 = *reinterpret_cast<const uint32_t*>(bn + 8);
-        mma_bf16(acc[f], a0, a1, a2, a3, b0, b1);
-        if constexpr (SPLIT) mma_bf16(acc[f], l0, l1, l2, l3, b0, b1);
+        for (int f = 0; f < NC / 8; ++f) {
+          const __nv_bfloat16* bn = brow + (f * 8 + gid) * KS + kc;
+          const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bn), b1 = *reinterpret_cast<const uint32_t*>(bn + 8);
+          mma_bf16(acc[f], a0, a1, a2, a3, b0, b1);
+          if constexpr (SPLIT) mma_bf16(acc[f], l0, l1, l2, l3, b0, b1);
+        }
       }
     }
-  }
-  const int py = y0 + warp;
+    const int py = y0 + warp;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int px = x0 + gid + 8 * h;
-    if (py >= H || px >= W) continue;
-    const int64_t p = (int64_t)py * W + px;
+    for (int h = 0; h < 2; ++h) {
+      const int px = x0 + gid + 8 * h;
+      if (py >= H || px >= W) continue;
+      const int64_t p = (int64_t)py * W + px;
 #pragma unroll
-    for (int f = 0; f < NC / 8; ++f)
+      for (int f = 0; f < NC / 8; ++f)
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int n = f * 8 + tig * 2 + e;
-        if (n >= N) continue;
-        float v = acc[f][2 * h + e];
-        if (relu) v = fmaxf(v, 0.0f);
-        if (mask && !(mask[p * N + n] > 0.0f)) v = 0.0f;
-        out[p * N + n] = v;
-      }
+        for (int e = 0; e < 2; ++e) {
+          const int n = f * 8 + tig * 2 + e;
+          if (n >= N) continue;
+          float v = acc[f][2 * h + e];
+          if (relu) v = fmaxf(v, 0.0f);
+          if (mask && !(mask[z * out_stride + p * N + n] > 0.0f)) v = 0.0f;
+          out[z * out_stride + p * N + n] = v;
+        }
+    }
   }
 }
 
@@ -319,19 +324,35 @@ __global__ void __launch_bounds__(kDwThreads) cnn_dw_mma_kernel(const float* __r
       }
 }
 
-// For each snapshot z in order: s_z = sum over its blocks b of
-// part[z][b][i], blocks in order; dst[i] = s_0 (or dst[i] + s_0 when
-// accumulating), then dst[i] + s_1, ... (deterministic, and the same
-// additions as reducing the snapshots one by one).
-__global__ void cnn_reduce_parts_kernel(const float* __restrict__ part, int n_blk, int n_snap, int n,
-                                        float* __restrict__ dst, int accumulate) {
+// Reduction of the per-tile gradient partials, deterministic and with the
+// same additions as reducing the snapshots one by one:
+// s[z][i] = sum over the tiles b of snapshot z of part[z][b][i], tiles in
+// order (snapshot blockIdx.y; sixteen loads in flight, added in order) ...
+__global__ void cnn_reduce_tiles_kernel(const float* __restrict__ part, int n_blk, int n, float* __restrict__ s) {
+  const int z = blockIdx.y;
+  const float* pz = part + (int64_t)z * n_blk * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float acc = 0.0f;
+    int b = 0;
+    for (; b + 16 <= n_blk; b += 16) {
+      float v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = pz[(int64_t)(b + u) * n + i];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc += v[u];
+    }
+    for (; b < n_blk; ++b) acc += pz[(int64_t)b * n + i];
+    s[(int64_t)z * n + i] = acc;
+  }
+}
+
+// ... then dst[i] = s[0][i] (or dst[i] + s[0][i] when accumulating), then
+// dst[i] + s[1][i], ... in snapshot order.
+__global__ void cnn_reduce_snaps_kernel(const float* __restrict__ s, int n_snap, int n, float* __restrict__ dst,
+                                        int accumulate) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float d = accumulate ? dst[i] : 0.0f;
-    for (int z = 0; z < n_snap; ++z) {
-      float s = 0.0f;
-      for (int b = 0; b < n_blk; ++b) s += part[((int64_t)z * n_blk + b) * n + i];
-      d = (z == 0 && !accumulate) ? s : d + s;
-    }
+    for (int z = 0; z < n_snap; ++z) d = (z == 0 && !accumulate) ? s[(int64_t)z * n + i] : d + s[(int64_t)z * n + i];
     dst[i] = d;
   }
 }
@@ -495,6 +516,7 @@ struct lpf_cnn {
   float* d_part = nullptr;    // per-block weight-gradient partials [cap][blocks][9 * 64 * 64]
   float* d_part_b = nullptr;  // per-block bias-gradient partials [cap][blocks][64]
   float* d_loss = nullptr;    // per-snapshot losses [cap]
+  float* d_snap = nullptr;    // per-snapshot gradient sums [cap][9 * 64 * 64]
   int n_blk = 0;              // output tiles (blocks) of a convolution
   int64_t step = 0;
   int loss_kind = 0;          // 0: squared error, 1: listwise cross-entropy
@@ -511,7 +533,8 @@ static int cnn_reserve(lpf_cnn* c, int nb) {
   cudaDeviceSynchronize();
   for (int l = 0; l <= kLayers; ++l) { cudaFree(c->d_tact[l]); c->d_tact[l] = nullptr; }
   cudaFree(c->d_gact); cudaFree(c->d_gact2); cudaFree(c->d_part); cudaFree(c->d_part_b); cudaFree(c->d_loss);
-  c->d_gact = c->d_gact2 = c->d_part = c->d_part_b = c->d_loss = nullptr;
+  cudaFree(c->d_snap);
+  c->d_gact = c->d_gact2 = c->d_part = c->d_part_b = c->d_loss = c->d_snap = nullptr;
   c->cap = 0;
   const size_t npix = (size_t)c->H * c->W, b = (size_t)nb;
   cudaError_t e = cudaSuccess;
@@ -521,6 +544,7 @@ static int cnn_reserve(lpf_cnn* c, int nb) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_part, b * c->n_blk * 9 * 64 * 64 * 4);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_part_b, b * c->n_blk * 64 * 4);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_loss, b * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_snap, b * 9 * 64 * 64 * 4);
   if (e != cudaSuccess) return set_cuda_error(e);
   c->cap = nb;
   return LPF_OK;
@@ -568,11 +592,27 @@ static size_t conv_smem() { return (size_t)((SPLIT ? 2 : 1) * kHalo * (KC + 8) +
 template <int KC, int NC>
 static size_t dw_smem() { return (size_t)(kHalo * (KC + 8) + 2 * kTH * kTW * (NC + 8)) * 2; }
 
+// Blocks of a convolution launch: every output tile of the nb snapshots, at
+// most the blocks that fit on the GPU at once (each then loops over tiles).
+template <int KC, int NC, bool SPLIT>
+static int conv_blocks(int tiles) {
+  static int resident = 0;
+  if (!resident) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cnn_conv_mma_kernel<KC, NC, SPLIT>, kConvThreads,
+                                                  conv_smem<KC, NC, SPLIT>());
+    resident = std::max(1, per_sm) * std::max(1, sms);
+  }
+  return std::max(1, std::min(tiles, resident));
+}
+
 // flip = 1 (the input gradient) carries the incoming gradient as two bfloat16 terms.
 template <int KC, int NC>
 static void conv_mma(const float* in, int H, int W, int K, int N, const __nv_bfloat16* w, int flip,
                      const float* bias, int relu, const float* mask, float* out, int nb, cudaStream_t s) {
-  const dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, nb);
+  const int tiles = ((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH) * nb;
   const int64_t in_stride = (int64_t)H * W * K, out_stride = (int64_t)H * W * N;
   static bool attr[2] = {false, false};  // dynamic shared memory above 48 KB must be allowed once per kernel
   if (flip) {
@@ -581,8 +621,8 @@ static void conv_mma(const float* in, int H, int W, int K, int N, const __nv_bfl
       cudaFuncSetAttribute(cnn_conv_mma_kernel<KC, NC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attr[1] = true;
     }
-    cnn_conv_mma_kernel<KC, NC, true><<<grid, kConvThreads, smem, s>>>(in, H, W, K, N, w, flip, bias, relu, mask,
-                                                                        out, in_stride, out_stride);
+    cnn_conv_mma_kernel<KC, NC, true><<<conv_blocks<KC, NC, true>(tiles), kConvThreads, smem, s>>>(
+        in, H, W, K, N, w, flip, bias, relu, mask, out, in_stride, out_stride, nb);
   } else {
     const size_t smem = conv_smem<KC, NC, false>();
     if (!attr[0]) {
@@ -590,8 +630,8 @@ static void conv_mma(const float* in, int H, int W, int K, int N, const __nv_bfl
                            (int)smem);
       attr[0] = true;
     }
-    cnn_conv_mma_kernel<KC, NC, false><<<grid, kConvThreads, smem, s>>>(in, H, W, K, N, w, flip, bias, relu, mask,
-                                                                         out, in_stride, out_stride);
+    cnn_conv_mma_kernel<KC, NC, false><<<conv_blocks<KC, NC, false>(tiles), kConvThreads, smem, s>>>(
+        in, H, W, K, N, w, flip, bias, relu, mask, out, in_stride, out_stride, nb);
   }
 }
 
@@ -675,9 +715,10 @@ static int cnn_fwd_bwd(lpf_cnn* c, const uint8_t* cells, int nb, const int32_t* 
     // g = dL/d(pre-activation output of layer l) here (ReLU mask already applied)
     dw_any(cin, cout, c->d_tact[l], g, H, W, c->d_part, c->d_part_b, nb, s);
     const int nw_l = 9 * cin * cout;
-    cnn_reduce_parts_kernel<<<(nw_l + 255) / 256, 256, 0, s>>>(c->d_part, c->n_blk, nb, nw_l, c->d_g + c->w_off[l],
-                                                                accumulate);
-    cnn_reduce_parts_kernel<<<1, 64, 0, s>>>(c->d_part_b, c->n_blk, nb, cout, c->d_g + c->b_off[l], accumulate);
+    cnn_reduce_tiles_kernel<<<dim3((nw_l + 255) / 256, nb), 256, 0, s>>>(c->d_part, c->n_blk, nw_l, c->d_snap);
+    cnn_reduce_snaps_kernel<<<(nw_l + 255) / 256, 256, 0, s>>>(c->d_snap, nb, nw_l, c->d_g + c->w_off[l], accumulate);
+    cnn_reduce_tiles_kernel<<<dim3(1, nb), 64, 0, s>>>(c->d_part_b, c->n_blk, cout, c->d_snap);
+    cnn_reduce_snaps_kernel<<<1, 64, 0, s>>>(c->d_snap, nb, cout, c->d_g + c->b_off[l], accumulate);
     if (l > 0) {
       // dL/d act[l] = transposed conv of g, then times the ReLU mask of act[l]
       conv_any(cout, cin, g, H, W, c->d_wbf + c->wb_off[l], 1, nullptr, 0, c->d_tact[l], g2, nb, s);
@@ -802,6 +843,7 @@ void lpf_cnn_free(lpf_cnn* c) {
   cudaFree(c->d_part);
   cudaFree(c->d_part_b);
   cudaFree(c->d_loss);
+  cudaFree(c->d_snap);
   delete c;
 }
 
