@@ -90,11 +90,20 @@ def test_annealing_128_cell_reduces_error_and_is_deterministic(gpu_lib):
     finals = []
     for _ in range(2):
         d_cell = torch.from_numpy(cell0).cuda()
-        ann = gpu_lib.lpf_sa_create(d_cell, p, target, n_step=20000, seed=99)
+        counts = torch.empty((2, p.n_full), dtype=torch.int64, device="cuda")
+        ann = gpu_lib.lpf_sa_create(d_cell, p, target, counts, n_step=20000, seed=99)
         e0 = gpu_lib.lpf_sa_read(ann)["error"]
         st = _run_to_end(gpu_lib, ann, chunk=256)
         assert st["error"] < 0.5 * e0
         assert gpu_lib.lpf_paths_status(p) == 0
+        # thousands of accepted exchanges later, the counts the run kept
+        # current (from its per-translation phase-0 counts) are the exact
+        # counts of its cell; its error, a running sum of float32 changes,
+        # stays within a small relative drift of the recomputed one
+        assert st["n_accept"] > 5000
+        assert torch.equal(counts, gpu_lib.lpf_full(d_cell, p))
+        e_new = gpu_lib.lpf_sa_recompute_error(ann)
+        assert abs(st["error"] - e_new) <= 1e-3 * abs(e_new)
         finals.append(d_cell.cpu().numpy())
     np.testing.assert_array_equal(finals[0], finals[1])
     assert finals[0].sum() == cell0.sum()
