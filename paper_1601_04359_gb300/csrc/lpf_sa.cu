@@ -244,15 +244,20 @@ __device__ __forceinline__ bool sa_grid_barrier(unsigned int* count, unsigned in
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1u);
-    int ok = 0;
-    for (uint32_t it = 0; it < kBarrierPolls; ++it) {
-      if (*reinterpret_cast<volatile unsigned int*>(count) >= target) { ok = 1; break; }
-      __nanosleep(64);
+    // arrive with release and acquire semantics (this block's partials and,
+    // for block 0, the batch's candidates go out; the others' come in): the
+    // last block to arrive sees the full count at once, the others poll
+    // with acquiring loads
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+    int ok = old + 1u >= target;
+    for (uint32_t it = 0; !ok && it < kBarrierPolls; ++it) {
+      unsigned int v;
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if (v >= target) ok = 1;
+      else __nanosleep(32);
     }
     if (!ok) atomicOr(status, 4);
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
