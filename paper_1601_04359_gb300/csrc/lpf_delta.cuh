@@ -449,12 +449,14 @@ __device__ __forceinline__ void chunk_entry(const DeltaArgs& g, const ChunkTable
 // the one through b; kChunkUnroll lookups per thread in flight.  The tests
 // are those of delta_lookup_vectors_strided.  When the block has at most
 // kChunkUnroll entries per thread, *held receives the thread's counts as
-// read (one byte each, for delta_chunk_apply_held), else 0.  Every thread
-// calls it; thread 0 returns the chunk's error change, summed over the
-// vectors in a fixed order.
+// read (one byte each) and held_zi their offsets in z, for
+// delta_chunk_apply_held; else *held is 0.  Every thread calls it; thread 0
+// returns the chunk's error change, summed over the vectors in a fixed
+// order.
 __device__ __forceinline__ float delta_chunk_lookup(const DeltaArgs& g, const PixelPair& q, int v0,
                                                     const ChunkTables& ct, int32_t* dcounts_k,
-                                                    const DeltaTerms& dt, uint32_t* held) {
+                                                    const DeltaTerms& dt, uint32_t* held,
+                                                    uint32_t (&held_zi)[kChunkUnroll]) {
   const int E = ct.pre[ct.nv];
   for (int i = threadIdx.x; i < ct.nv; i += blockDim.x) {
     ct.d[i] = 0;
@@ -477,8 +479,10 @@ __device__ __forceinline__ float delta_chunk_lookup(const DeltaArgs& g, const Pi
       }
     }
 #pragma unroll
-    for (int u = 0; u < kChunkUnroll; ++u)  // read at L2 (other threads of the block update z)
+    for (int u = 0; u < kChunkUnroll; ++u) {  // read at L2 (other threads of the block update z)
       zs[u] = vi[u] >= 0 ? (int)__ldcg(g.z + zi[u]) : 0;
+      held_zi[u] = zi[u];
+    }
 #pragma unroll
     for (int u = 0; u < kChunkUnroll; ++u) {
       h |= (uint32_t)zs[u] << (8 * u);
@@ -553,14 +557,16 @@ __device__ __forceinline__ bool chunk_maybe_both(const DeltaArgs& g, int dx, int
 // After exchanging a (now phase 0) and b (now phase 1): z_v += 1 on the
 // translations through a and -= 1 on those through b, for the chunk's
 // vectors, with the counts delta_chunk_lookup read for this same exchange
-// and held by each thread (the block had at most kChunkUnroll entries per
-// thread): plain stores at L2 -- the block owns these bytes.  A
+// and their offsets, held by each thread (the block had at most
+// kChunkUnroll entries per thread): plain stores at L2 -- the block owns
+// these bytes.  A
 // translation through both pixels keeps its count (its two entries are
 // one byte, which neither stores); within one side a vector's translations
 // are distinct, so no two threads store the same byte.  Every thread calls
 // it with the same pixels as that lookup.
 __device__ __forceinline__ void delta_chunk_apply_held(const DeltaArgs& g, const PixelPair& q, int v0,
-                                                       const ChunkTables& ct, uint32_t held) {
+                                                       const ChunkTables& ct, uint32_t held,
+                                                       const uint32_t (&held_zi)[kChunkUnroll]) {
   const int E = ct.pre[ct.nv];
   const int nthr = blockDim.x;
   int ddx = q.bx - q.ax, ddy = q.by - q.ay;
@@ -573,15 +579,16 @@ __device__ __forceinline__ void delta_chunk_apply_held(const DeltaArgs& g, const
     const int e = u * nthr + (int)threadIdx.x;
     if (e >= 2 * E) continue;
     const bool side = e >= E;
-    int i, x, y;
-    uint32_t zi;
-    chunk_entry(g, ct, v0, side ? e - E : e, side ? q.bx : q.ax, side ? q.by : q.ay, i, x, y, zi);
-    const short2 dv = ct.vec[i];
-    if (chunk_maybe_both(g, dv.x, dv.y, ddx, ddy) &&
-        chunk_on_segment(g, ct, i, dv.x, dv.y, x, y, side ? q.ax : q.bx, side ? q.ay : q.by))
-      continue;
+    const int j = side ? e - E : e;
+    const short2 dv = ct.vec[ct.vid[j]];
+    if (chunk_maybe_both(g, dv.x, dv.y, ddx, ddy)) {  // rare: check the other pixel on the segment
+      int i, x, y;
+      uint32_t zi;
+      chunk_entry(g, ct, v0, j, side ? q.bx : q.ax, side ? q.by : q.ay, i, x, y, zi);
+      if (chunk_on_segment(g, ct, i, dv.x, dv.y, x, y, side ? q.ax : q.bx, side ? q.ay : q.by)) continue;
+    }
     const uint32_t z = (held >> (8 * u)) & 0xffu;
-    __stcg(g.z + zi, (uint8_t)(side ? z - 1u : z + 1u));
+    __stcg(g.z + held_zi[u], (uint8_t)(side ? z - 1u : z + 1u));
   }
 }
 

@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
   dt.c[1] = s_cnt + mv;
   dt.vbase = v0;
   uint32_t held = 0;  // the phase-0 counts this thread read for candidate held_k
+  uint32_t held_zi[kChunkUnroll] = {0, 0, 0, 0};  // and where they are in z
   int held_k = -1;
   // Candidate k of batch bi (warp 0): drawn from the block's own cell copy,
   // marked there, kept in *sa / *sb; block 0 also records it for the others.
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
       held_k = -1;
       if (a == b) delta_zero_vectors(g, v0, v1, dk);
       else if (g.z) {
-        acc = delta_chunk_lookup(g, q, v0, ct, dk, dt, &held);
+        acc = delta_chunk_lookup(g, q, v0, ct, dk, dt, &held, held_zi);
         if (2 * n_ent <= kChunkUnroll * (int)blockDim.x) held_k = k;  // this candidate's counts stay in registers
       }
       else acc = delta_walk_vectors(sm, g, a, b, v0, v1, warp, lane, dk, dt);
@@ -435,7 +436,7 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
         // this block's vectors: the phase-0 counts follow the exchange
         if (g.z) {
           if (held_k == kstar) {
-            delta_chunk_apply_held(g, last_q, v0, ct, held);
+            delta_chunk_apply_held(g, last_q, v0, ct, held, held_zi);
           } else {
             const PixelPair qk = {a % g.W, a / g.W, b % g.W, b / g.W};
             delta_chunk_update(g, qk, v0, ct);
