@@ -337,16 +337,18 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
   int held_k = -1;
   // Candidate k of batch bi (warp 0): drawn from the block's own cell copy,
   // marked there, kept in *sa / *sb; block 0 also records it for the others.
-  auto draw = [&](int bi, int k, int* sa, int* sb, PixelPair* sq) {
+  // (n0: the batch's first evaluation index; the draw reads only the run
+  // state's fixed fields, so it may run while warp 0 advances the rest)
+  auto draw = [&](int bi, unsigned long long n0, int k, int* sa, int* sb, PixelPair* sq) {
     int a, b;
     float uu;
-    draw_candidate_warp(sm, g, (unsigned long long)s_state.n_eval + (unsigned long long)k, s_state.key0,
-                        s_state.key1, a, b, uu, &s_state, lane);
+    draw_candidate_warp(sm, g, n0 + (unsigned long long)k, s_state.key0, s_state.key1, a, b, uu, &s_state, lane);
     if (lane == 0) {
       if (ch == 0) {
         pairs2[(size_t)(bi & 1) * 2 * k_max + 2 * k] = a;
         pairs2[(size_t)(bi & 1) * 2 * k_max + 2 * k + 1] = b;
         u2[(size_t)(bi & 1) * k_max + k] = uu;
+        __threadfence();  // written by a thread other than the one that arrives at the grid barrier
       }
       *sa = a;
       *sb = b;
@@ -357,20 +359,22 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
       if (a != b) { delta_mark(sm, a, kMarkA, g); delta_mark(sm, b, kMarkB, g); }
     }
   };
-  // The first candidate of every batch is drawn ahead, by warp 0 at the end
-  // of the batch before (while the other warps apply its exchange), into
-  // s_na, s_nb; later candidates of a batch go through s_a, s_b.
-  if (warp == 0 && !s_state.done && n_batches > 0) draw(0, 0, &s_na, &s_nb, &s_nq);
+  // The first candidate of every batch is drawn ahead, by warp 1 at the end
+  // of the batch before (while warp 0 advances the run state and the other
+  // warps apply the exchange), into s_na, s_nb; later candidates of a batch
+  // go through s_a, s_b.
+  if (warp == 1 && !s_state.done && n_batches > 0) draw(0, (unsigned long long)s_state.n_eval, 0, &s_na, &s_nb, &s_nq);
   __syncthreads();
   for (int bi = 0; bi < n_batches && !s_state.done; ++bi) {
     const int Keff = s_state.k_eff;
+    const unsigned long long n0 = (unsigned long long)s_state.n_eval;
     int32_t* pairs = pairs2 + (size_t)(bi & 1) * 2 * k_max;
     float* u = u2 + (size_t)(bi & 1) * k_max;
     float* partial = partial2 + (size_t)(bi & 1) * k_max * g.n_chunks;
     int last_a = 0, last_b = 0;  // the batch's last candidate
     PixelPair last_q = {0, 0, 0, 0};
     for (int k = 0; k < Keff; ++k) {
-      if (k > 0 && warp == 0) draw(bi, k, &s_a, &s_b, &s_q);
+      if (k > 0 && warp == 0) draw(bi, n0, k, &s_a, &s_b, &s_q);
       __syncthreads();
       const int a = k == 0 ? s_na : s_a, b = k == 0 ? s_nb : s_b;
       const PixelPair q = k == 0 ? s_nq : s_q;
@@ -444,24 +448,27 @@ __global__ void __launch_bounds__(kDeltaThreads, 3) sa_persistent_kernel(
         }
       }
     }
-    // warp 0: the exchange on the block's cell copy, the run state, and the
-    // next batch's first candidate (drawn on the updated cell)
+    // warp 0 advances the run state (and block 0 writes the exchange to the
+    // cell); warp 1 makes the exchange on the block's cell copy and draws
+    // the next batch's first candidate on it
     if (warp == 0) {
       if (lane == 0) {
-        if (kstar >= 0 && acc_a != acc_b) {
-          delta_mark(sm, acc_a, 0, g);
-          delta_mark(sm, acc_b, 1, g);
-          if (ch == 0) {
-            cell[acc_a] = 0;
-            cell[acc_b] = 1;
-            delta_mark(ext, acc_a, 0, g);
-            delta_mark(ext, acc_b, 1, g);
-          }
+        if (ch == 0 && kstar >= 0 && acc_a != acc_b) {
+          cell[acc_a] = 0;
+          cell[acc_b] = 1;
+          delta_mark(ext, acc_a, 0, g);
+          delta_mark(ext, acc_b, 1, g);
         }
         sa_advance(&s_state, Keff, Kv, kstar, de_star, acc_a, acc_b);
       }
+    } else if (warp == 1) {
+      if (lane == 0 && kstar >= 0 && acc_a != acc_b) {
+        delta_mark(sm, acc_a, 0, g);
+        delta_mark(sm, acc_b, 1, g);
+      }
       __syncwarp();
-      if (!s_state.done && bi + 1 < n_batches) draw(bi + 1, 0, &s_na, &s_nb, &s_nq);
+      const unsigned long long n_next = n0 + (unsigned long long)(kstar >= 0 ? kstar + 1 : Kv);
+      if ((long long)n_next < s_state.n_step && bi + 1 < n_batches) draw(bi + 1, n_next, 0, &s_na, &s_nb, &s_nq);
     }
     __syncthreads();
   }
