@@ -263,6 +263,34 @@ def extra_batch(lpf):
                                        "time of the whole graph (zero, pack, walk, mirror)"}}
 
 
+def extra_3d(lpf, reps: int = 5):
+    """The 3D extension: the full lineal path function of both phases of a
+    periodic 128^3 volume of overlapping balls (radius 5, fraction about
+    0.3), every vector |dx|, |dy|, |dz| <= 16."""
+    import torch
+
+    import synth
+    D = H = W = 128
+    R, r = 5.0, 16
+    n = int(round(-math.log(1.0 - 0.3) * D * H * W / (4.0 / 3.0 * math.pi * R ** 3)))
+    vol = torch.from_numpy(synth.boolean_spheres(D, H, W, R, n, seed=7)).cuda()
+    p = lpf.lpf_build_paths_3d(r, r, r)
+    c = lpf.lpf_full_3d(vol, p)
+    lpf.lpf_full_3d(vol, p, c)
+    a, b = _events()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        lpf.lpf_full_3d(vol, p, c)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    assert lpf.lpf_paths_status(p) == 0
+    tests = 2 * D * H * W * p.n_full
+    return {"workload": "lpf_full_3d 128^3 balls R=5 f~0.3, |dx|,|dy|,|dz|<=16, both phases",
+            "ms_per_call": ms, "tests_per_s": tests / (ms / 1000.0), "phase1_fraction": float(vol.float().mean())}
+
+
 def extra_s2(lpf, reps: int = 20):
     import torch
 
@@ -682,7 +710,8 @@ def main():
     if not args.no_extras and ws == 1:
         extras = {}
         for name, fn in (("delta_swap", extra_delta), ("annealing", extra_sa), ("batched", extra_batch),
-                         ("s2_fft", extra_s2), ("cnn_train", extra_cnn_train), ("proposer", extra_proposer)):
+                         ("lpf_full_3d", extra_3d), ("s2_fft", extra_s2), ("cnn_train", extra_cnn_train),
+                         ("proposer", extra_proposer)):
             try:
                 extras[name] = fn(lpf)
             except Exception as exc:  # report, do not hide, a failing extra

@@ -186,7 +186,8 @@ __device__ __forceinline__ int sa_first_accept(const SaDev* st, int Kv, const fl
     if (s_kstar != INT_MAX) break;  // the first accepted candidate is known
     __syncthreads();
   }
-  __syncthreads();
+  // (every exit from the loop, and an empty loop, follows a block barrier
+  // after the last writes of s_kstar and s_de)
   const int kstar = s_kstar == INT_MAX ? -1 : s_kstar;
   *de_star = kstar >= 0 ? s_de[kstar - k0] : 0.0f;
   return kstar;
