@@ -101,3 +101,23 @@ def test_prefix_property_along_rays():
         for j in range(1, 8):
             s = oracle.segment(j * ux, j * uy).tolist()
             assert longest[: len(s)] == s
+
+
+@pytest.mark.parametrize("r", [5, 12])
+def test_segment_pixels_within_half_a_step_of_the_line(r):
+    # Sec. 2.2's rounding keeps every pixel of S(v) within a/2 of the line
+    # along v, a = max(|dx|, |dy|): |sy dx - sx dy| <= a/2.  So two pixels of
+    # one segment differ by a vector within a of that line, inside the
+    # segment's box -- the bound the annealer uses to rule out translations
+    # whose segment holds both exchanged pixels.
+    for dx in range(-r, r + 1):
+        for dy in range(0, r + 1):
+            if dy == 0 and dx < 0:
+                continue
+            a = max(abs(dx), dy)
+            s = oracle.segment(dx, dy).astype(int)
+            cross = s[:, 1] * dx - s[:, 0] * dy
+            assert 2 * abs(cross).max() <= a
+            d = s[:, None, :] - s[None, :, :]
+            assert (abs(d[..., 0]) <= abs(dx)).all() and (abs(d[..., 1]) <= dy).all()
+            assert (abs(d[..., 1] * dx - d[..., 0] * dy) <= a).all()
