@@ -344,9 +344,14 @@ int delta_prepare(lpf_paths* p, int H, int W, int K) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, sa_persistent_kernel_entry(), kDeltaThreads, (size_t)ext);
   if (e != cudaSuccess) return set_cuda_error(e);
   const int occ = std::max(1, std::min(std::min(occ_d, occ_s), occ_p));
-  rc = bake_delta(p, W, occ * g_sms, p->delta);
-  if (rc) return rc;
-  {
+  // The tables stay as they are while the same cell width asks for the same
+  // chunking (annealing runs on this handle hold pointers into them): the
+  // chunking below is decided once per (width, occupancy) and remembered by
+  // its first request, so calling again (with any K) never re-bakes them.
+  const int want0 = occ * g_sms;
+  if (!(p->delta.d_doff && p->delta.We == delta_row_stride(W, p->host.rx) && p->delta.want_key == want0)) {
+    rc = bake_delta(p, W, want0, p->delta);
+    if (rc) return rc;
     // the persistent kernel also keeps its chunk's counts, targets and lookup tables: check
     // the chunking once more with the size it produced
     const size_t persist = persistent_smem_bytes(ext, p->delta.max_chunk_vecs, p->delta.max_chunk_entries);
@@ -359,6 +364,7 @@ int delta_prepare(lpf_paths* p, int H, int W, int K) {
       rc = bake_delta(p, W, occ2 * g_sms, p->delta);
       if (rc) return rc;
     }
+    p->delta.want_key = want0;
   }
   if (ext > p->ext_cap) {
     if (p->d_ext) { cudaDeviceSynchronize(); cudaFree(p->d_ext); p->d_ext = nullptr; p->ext_cap = 0; }

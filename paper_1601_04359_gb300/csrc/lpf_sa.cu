@@ -579,8 +579,37 @@ static int sa_device_state(lpf_sa* sa, SaDev& st, cudaStream_t s) {
 // some chunks hold the counts after a swap that the cell does not show.  So
 // the counts are recomputed from the cell (exact integers) and the error from
 // the counts, and the run continues from the cell's state.
+// A lineal-path run reads the swap-delta tables of its paths handle (vector
+// chunks, segment pixels, shears).  Another call on the handle with another
+// cell width re-bakes them, so before every launch the run asks for its own
+// width's tables again (a no-op when they are in place) and takes their
+// current addresses; the chunking of a width never changes.
+static int sa_bind_tables(lpf_sa* sa) {
+  if (sa->objective != kSaObjectiveLineal) return LPF_OK;
+  const int rc = delta_prepare(sa->paths, sa->H, sa->W, 1);
+  if (rc) return rc;
+  const DeltaTables& t = sa->paths->delta;
+  if (t.n_chunks != sa->g.n_chunks || t.max_chunk_vecs != sa->g.max_chunk_vecs ||
+      t.max_chunk_entries != sa->g.max_chunk_entries)
+    return LPF_EINVAL;
+  if (sa->g.chunk != t.d_chunk || sa->g.dptr != t.d_dptr || sa->g.doff != t.d_doff || sa->g.off16 != t.d_off16 ||
+      sa->g.vec16 != t.d_vec16 || sa->g.shear != t.d_shear) {
+    sa->g.chunk = t.d_chunk;
+    sa->g.dptr = t.d_dptr;
+    sa->g.doff = t.d_doff;
+    sa->g.off16 = t.d_off16;
+    sa->g.vec16 = t.d_vec16;
+    sa->g.shear = t.d_shear;
+    // a captured graph of batches holds the old addresses
+    if (sa->exec) { cudaGraphExecDestroy(sa->exec); sa->exec = nullptr; }
+    if (sa->graph) { cudaGraphDestroy(sa->graph); sa->graph = nullptr; }
+  }
+  return LPF_OK;
+}
+
 int sa_recover(lpf_sa* sa, cudaStream_t s) {
-  int rc;
+  int rc = sa_bind_tables(sa);
+  if (rc) return rc;
   if (sa->objective == kSaObjectiveS2) rc = s2_counts(sa->cell, sa->H, sa->W, sa->counts, s);
   else if (sa->d_sel) rc = lpf_full_mc(sa->cell, sa->H, sa->W, sa->paths, sa->d_sel, sa->counts, s);
   else rc = lpf_full(sa->cell, sa->H, sa->W, sa->paths, sa->counts, s);
@@ -796,6 +825,7 @@ int lpf_sa_run(lpf_sa* sa, int32_t n_batches, lpf_stream_t stream) {
   if (n_batches == 0) return LPF_OK;
   cudaStream_t s = (cudaStream_t)stream;
   (void)cudaGetLastError();
+  if (int rc = lpf::sa_bind_tables(sa)) return rc;
   if (sa->persistent) {
     // a proposer is re-scored every `refresh` batches, between launches
     for (int left = n_batches; left > 0;) {
@@ -841,6 +871,7 @@ int lpf_sa_selftest_timeout(lpf_sa* sa, int32_t block, lpf_stream_t stream) {
   if (!sa) return LPF_EINVAL;
   if (!sa->persistent) return LPF_EUNSUPPORTED;
   if (block < -1 || block >= sa->g.n_chunks) return LPF_EINVAL;
+  if (int rc = lpf::sa_bind_tables(sa)) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   lpf::SaDev before, after;
   int rc = lpf::sa_device_state(sa, before, s);

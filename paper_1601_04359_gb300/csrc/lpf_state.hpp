@@ -83,6 +83,7 @@ struct Baked {
 struct DeltaTables {
   int We = -1;
   int want = -1;               // vector chunks asked for (one wave of blocks)
+  int want_key = -1;           // the first request of delta_prepare that produced these tables
   int max_chunk_vecs = 0;      // vectors in the largest chunk
   int max_chunk_entries = 0;   // segment pixels of the largest chunk (by pixels)
   int32_t* d_doff = nullptr;   // per segment pixel: sy*We + sx

@@ -107,3 +107,49 @@ def test_annealing_128_cell_reduces_error_and_is_deterministic(gpu_lib):
         finals.append(d_cell.cpu().numpy())
     np.testing.assert_array_equal(finals[0], finals[1])
     assert finals[0].sum() == cell0.sum()
+
+
+def test_wide_window_annealer_keeps_exact_counts(gpu_lib):
+    # A 128x128 cell against a window of 100: the vector chunks hold more
+    # segment pixels than the block keeps in registers, so every accepted
+    # exchange updates the phase-0 counts by reading them again; after the
+    # run the counts it kept are the exact counts of its cell.
+    r = 100
+    orig = synth.clustered_disks(256, 256, 0.3, seed=12)
+    p = gpu_lib.lpf_build_paths(r, r)
+    c_orig = gpu_lib.lpf_full(torch.from_numpy(orig).cuda(), p)
+    target = (c_orig.double() / float(orig.size)).float()
+    cell0 = synth.exact_fraction_shuffle(128, 128, int(round(orig.mean() * 128 * 128)), seed=3)
+    d_cell = torch.from_numpy(cell0).cuda()
+    counts = torch.empty((2, p.n_full), dtype=torch.int64, device="cuda")
+    ann = gpu_lib.lpf_sa_create(d_cell, p, target, counts, n_step=3000, seed=5)
+    st = _run_to_end(gpu_lib, ann, chunk=256)
+    assert st["n_eval"] == 3000 and st["n_accept"] > 500
+    assert gpu_lib.lpf_paths_status(p) == 0
+    assert torch.equal(counts, gpu_lib.lpf_full(d_cell, p))
+    assert d_cell.sum().item() == cell0.sum()
+
+
+def test_run_continues_after_the_handle_serves_another_width(gpu_lib):
+    # The swap-delta tables of a paths handle belong to one cell width; a
+    # swap-delta call on another width re-bakes them.  An annealing run on the
+    # handle takes its own width's tables again before its next launch and
+    # carries on with exact counts.
+    r = 20
+    p = gpu_lib.lpf_build_paths(r, r)
+    orig = synth.clustered_disks(128, 128, 0.3, seed=21)
+    target = (gpu_lib.lpf_full(torch.from_numpy(orig).cuda(), p).double() / float(orig.size)).float()
+    cell0 = synth.exact_fraction_shuffle(64, 64, int(round(orig.mean() * 64 * 64)), seed=4)
+    d_cell = torch.from_numpy(cell0).cuda()
+    counts = torch.empty((2, p.n_full), dtype=torch.int64, device="cuda")
+    ann = gpu_lib.lpf_sa_create(d_cell, p, target, counts, n_step=4000, seed=8)
+    gpu_lib.lpf_sa_run(ann, 64)
+    other = synth.clustered_disks(48, 48, 0.3, seed=22)
+    d_other = torch.from_numpy(other).cuda()
+    pairs = torch.from_numpy(synth.swap_candidates(other, 8, seed=1)).cuda()
+    dc, _ = gpu_lib.lpf_delta_swap(d_other, p, pairs)
+    np.testing.assert_array_equal(dc.cpu().numpy(), oracle.delta_swap(other, r, r, pairs.cpu().numpy()))
+    st = _run_to_end(gpu_lib, ann, chunk=128)
+    assert st["n_eval"] == 4000
+    assert gpu_lib.lpf_paths_status(p) == 0
+    assert torch.equal(counts, gpu_lib.lpf_full(d_cell, p))
