@@ -586,9 +586,12 @@ static int sa_device_state(lpf_sa* sa, SaDev& st, cudaStream_t s) {
 // current addresses; the chunking of a width never changes.
 static int sa_bind_tables(lpf_sa* sa) {
   if (sa->objective != kSaObjectiveLineal) return LPF_OK;
-  const int rc = delta_prepare(sa->paths, sa->H, sa->W, 1);
-  if (rc) return rc;
   const DeltaTables& t = sa->paths->delta;
+  if (!(t.d_doff && t.We == sa->g.We && t.want_key == sa->delta_key)) {  // re-baked for another cell
+    const int rc = delta_prepare(sa->paths, sa->H, sa->W, 1);
+    if (rc) return rc;
+    if (t.want_key != sa->delta_key) return LPF_EINVAL;  // (a cell of this width but another height)
+  }
   if (t.n_chunks != sa->g.n_chunks || t.max_chunk_vecs != sa->g.max_chunk_vecs ||
       t.max_chunk_entries != sa->g.max_chunk_entries)
     return LPF_EINVAL;
@@ -777,6 +780,7 @@ static int sa_create_lineal(uint8_t* cell_dev, int32_t H, int32_t W, lpf_paths* 
   sa->err_base = paths->host.base;
   sa->threads = lpf::kDeltaThreads;
   lpf::delta_geometry(paths, H, W, sa->g);
+  sa->delta_key = paths->delta.want_key;
   sa->g.target = target_dev;
   sa->g.counts = counts_dev;
   sa->g.phase_mask = sa->phase_mask;

@@ -289,6 +289,7 @@ struct lpf_sa {
   int64_t* counts = nullptr;
   lpf_sa_params prm{};
   lpf::DeltaArgs g{};
+  int delta_key = -1;           // the swap-delta tables' key (DeltaTables::want_key) the run was built on
   dim3 grid;
   lpf::SaDev* d_st = nullptr;
   uint8_t* d_ext = nullptr;
