@@ -394,7 +394,7 @@ typedef struct lpf_batch lpf_batch; /* opaque, owned by the library */
  * runs read the images' current contents and overwrite the counts.
  * words_per_thread: NULL (cost model) or n_img values in {1,2,4,8} (the
  * walk kernel's words per thread for each image; each image's row words
- * must split into 1, 2, 4 or 8 warp groups).  Uploads the batch's own copy
+ * must split into at most 8 groups of that many words, else LPF_EUNSUPPORTED).  Uploads the batch's own copy
  * of each handle's program (so later calls with the handles alone, in any
  * launch shape, leave the batch intact; the handles must outlive the batch
  * only for lpf_batch_autotune) and allocates the batch's work area
@@ -406,11 +406,13 @@ int lpf_batch_create(int32_t n_img, const uint8_t *const *imgs_dev, const int32_
                      const int32_t *words_per_thread, lpf_batch **out);
 
 /*
- * Enqueue one evaluation of every image of the batch: four kernel launches
- * (zero counts, pack, one persistent walk whose blocks visit band groups of
- * the images and whose warps pull (tile, program piece) units, mirror), no
- * host-device copies.  use_graph != 0
- * captures those launches as a CUDA graph on the first call and replays it.
+ * Enqueue one evaluation of every image of the batch: zero counts, pack,
+ * one persistent walk kernel per words-per-thread choice present (blocks
+ * visit band groups of the images, warps pull (tile, program piece) units;
+ * the kernels after the first run on the batch's own streams, forked from
+ * `stream` and joined back before the next step), mirror; no host-device
+ * copies.  use_graph != 0 captures those launches as a CUDA graph on the
+ * first call and replays it.
  * Errors: LPF_EINVAL, LPF_ECUDA.
  */
 int lpf_batch_run(lpf_batch *batch, int32_t use_graph, lpf_stream_t stream);

@@ -1,20 +1,23 @@
 // Batched full lineal path functions of many independent images of uneven
-// sizes in one persistent kernel (the batching form of the evaluation; the
+// sizes in one run of persistent kernels (the batching form of the evaluation; the
 // paper evaluates one image at a time, Sec. 3.1).
 //
 // Every image brings its own window and program (its own paths handle).  A
 // batch is prepared once (programs uploaded, work area allocated, a device
-// table of per-image descriptors written); a run is then four launches with
+// table of per-image descriptors written); a run is then a few launches with
 // no host-device copies -- zero the counts, pack every image into bit rows,
-// one persistent walk kernel, fill the mirrored halves -- and can be replayed
-// as a CUDA graph.  All blocks have 8 warps, and each image gets its own
-// split of those warps into word groups x bands (G x BB, G*BB = 8 tiles of 32
-// rows x 32T translations) and its own words per thread T, chosen by a
-// waste/load cost model or by the batch autotuner.  The walk kernel visits a
-// host-built list of band-group slots (every band group of every image gets
-// slots in proportion to its work, heaviest first, then one more each), a
-// block claiming the next slot from a counter whenever it is free; for each
-// it stages the band group's rows (one bulk copy, skipped if already
+// one persistent walk kernel per words-per-thread choice present, fill the
+// mirrored halves -- and can be replayed as a CUDA graph.  All blocks have 8
+// warps; each image side gets its own words per thread T (chosen by a
+// waste/load cost model or by the batch autotuner), so its rows split into G
+// word groups of 32T translations, and its own band groups of BB bands of 32
+// rows (G x BB tiles, no band past the side's last where avoidable).  Each
+// walk kernel visits a host-built list of band-group slots of its images
+// (every band group gets slots in proportion to its work, heaviest first,
+// then one more each), a block claiming the next slot from a counter
+// whenever it is free; the kernels run side by side on forked streams, so
+// one's blocks take the SMs another's leave at its end.  For each slot a block
+// stages the band group's rows (one bulk copy, skipped if already
 // staged) and its warps pull units (tile, program piece) from that band
 // group's counter until none are left, so warps whose tiles skip zero-count
 // subtrees take more units instead of waiting for the others.
@@ -37,9 +40,11 @@ constexpr int kBatchWarps = 8;
 constexpr double kSlotsPerBlock = 12.0;
 constexpr int kBatchThreads = 32 * kBatchWarps;
 
-// control words: [0] status, [1] slot counter, [kBatchCtlUnits + g] unit counter of band group g
+// control words: [0] status, [kBatchCtlSlot + k] slot counter of the walk
+// kernel for T = 1 << k, [kBatchCtlUnits + g] unit counter of band group g
 constexpr int kBatchCtlSlot = 1;
-constexpr int kBatchCtlUnits = 4;
+constexpr int kBatchCtlUnits = 8;
+constexpr int kBatchTs = 4;  // T = 1, 2, 4, 8
 
 // One side of one image (the image with the x-major vectors' program, or
 // its transpose with the y-major vectors' program; both add to the image's
@@ -114,9 +119,16 @@ __device__ __forceinline__ uint32_t batch_unit(const BatchDesc& b, int bg, int t
                              lane, b.counts, b.n_full, b.base);
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 4) batch_walk_kernel(const BatchDesc* __restrict__ d,
+// The walk of the slots whose images take T words per thread (one kernel per
+// T: the four walks inlined behind one switch would share one register
+// allocation and spill).  slot_ctr is this kernel's slot counter in ctl.
+// T >= 4 keeps its masks and the image's fields in up to 80 registers (3
+// blocks per SM; with 64 it spills, measured 3 % slower on the 256 images).
+template <int T>
+__global__ void __launch_bounds__(kBatchThreads, (T >= 4 ? 3 : 4)) batch_walk_kernel(const BatchDesc* __restrict__ d,
                                                                    const BatchSlot* __restrict__ slots,
                                                                    int n_slots, int* __restrict__ ctl,
+                                                                   int slot_ctr,
                                                                    unsigned long long* __restrict__ executed) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ __align__(8) uint64_t bar;
@@ -132,7 +144,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_walk_kernel(const Batc
     // the next slot, claimed when this block is free (the slot list ends
     // with one more slot per band group, heaviest first, so that blocks
     // left without work help the band groups that still have units)
-    if (threadIdx.x == 0) s_slot = atomicAdd(ctl + kBatchCtlSlot, 1);
+    if (threadIdx.x == 0) s_slot = atomicAdd(ctl + slot_ctr, 1);
     __syncthreads();
     const int k = s_slot;
     __syncthreads();  // s_slot is rewritten next round
@@ -172,13 +184,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_walk_kernel(const Batc
       u = __shfl_sync(0xffffffffu, u, 0);
       if (u >= units) break;
       const int tile = u % n_tiles, pi = u / n_tiles;
-      uint32_t w;
-      switch (b.T) {
-        case 1: w = batch_unit<1>(b, sl.bg, tile, pi, sm, lane); break;
-        case 2: w = batch_unit<2>(b, sl.bg, tile, pi, sm, lane); break;
-        case 4: w = batch_unit<4>(b, sl.bg, tile, pi, sm, lane); break;
-        default: w = batch_unit<8>(b, sl.bg, tile, pi, sm, lane); break;
-      }
+      const uint32_t w = batch_unit<T>(b, sl.bg, tile, pi, sm, lane);
       if (lane == 0) s_walked[threadIdx.x >> 5] += w;
     }
     if (lane == 0 && s_walked[threadIdx.x >> 5])
@@ -191,14 +197,51 @@ __global__ void __launch_bounds__(kBatchThreads, 4) batch_walk_kernel(const Batc
   }
 }
 
-// Cost of a (T) choice for one image when a block has 8 warps split G x BB:
-// translation words covered per useful word, times shared loads per word.
+// T = 1 << k.
+static inline int t_index(int T) { return T == 1 ? 0 : T == 2 ? 1 : T == 4 ? 2 : 3; }
+
+static const void* batch_walk_fn(int k) {
+  switch (k) {
+    case 0: return (const void*)batch_walk_kernel<1>;
+    case 1: return (const void*)batch_walk_kernel<2>;
+    case 2: return (const void*)batch_walk_kernel<4>;
+    default: return (const void*)batch_walk_kernel<8>;
+  }
+}
+
+static void batch_walk_launch(int k, int blocks, uint32_t smem, cudaStream_t s, const BatchDesc* d,
+                              const BatchSlot* slots, int n_slots, int* ctl, int slot_ctr,
+                              unsigned long long* executed) {
+  switch (k) {
+    case 0: batch_walk_kernel<1><<<blocks, kBatchThreads, smem, s>>>(d, slots, n_slots, ctl, slot_ctr, executed); break;
+    case 1: batch_walk_kernel<2><<<blocks, kBatchThreads, smem, s>>>(d, slots, n_slots, ctl, slot_ctr, executed); break;
+    case 2: batch_walk_kernel<4><<<blocks, kBatchThreads, smem, s>>>(d, slots, n_slots, ctl, slot_ctr, executed); break;
+    default: batch_walk_kernel<8><<<blocks, kBatchThreads, smem, s>>>(d, slots, n_slots, ctl, slot_ctr, executed); break;
+  }
+}
+
+// Bands per band group for a side of nbands bands split into G word groups:
+// at most ceil(8 / G) (a band group holds about one tile per warp), the
+// fewest bands covered past the side's last one, then the most bands (fewer
+// copies of the halo rows).  The warps pull units, so G x BB need not be 8.
+static int band_group_bands(int nbands, int G) {
+  const int cap = std::max(1, std::min(nbands, (kBatchWarps + G - 1) / G));
+  int best = 1, best_cov = 1 << 30;
+  for (int bb = 1; bb <= cap; ++bb) {
+    const int cov = bb * ((nbands + bb - 1) / bb);
+    if (cov <= best_cov) { best_cov = cov; best = bb; }
+  }
+  return best;
+}
+
+// Cost of a (T) choice for one image: translation words covered per useful
+// word, times shared loads per word.
 static double shape_cost(int H, int W, int T) {
   const int nw = (W + 31) / 32;
   const int G = (nw + T - 1) / T;
-  if (G > kBatchWarps || kBatchWarps % G) return 1e30;
-  const int BB = kBatchWarps / G;
+  if (G > kBatchWarps) return 1e30;
   const int nbands = (H + 31) / 32;
+  const int BB = band_group_bands(nbands, G);
   const int nbg = (nbands + BB - 1) / BB;
   const double covered = (double)G * T * 32.0 * BB * 32.0 * nbg;
   const double useful = (double)W * H;
@@ -220,6 +263,15 @@ struct lpf_batch {
   int ctl_words = 0, ctl_cap = 0;
   lpf::BatchSlot* d_slots = nullptr;
   int n_slots = 0;
+  // the walk kernel of T = 1 << k visits slots [slot_off[k], slot_off[k + 1])
+  // with blocks_T[k] blocks; the kernels after the first run on the batch's
+  // own streams, forked from and joined to the caller's
+  int slot_off[lpf::kBatchTs + 1] = {0, 0, 0, 0, 0};
+  int run_order[lpf::kBatchTs] = {0, 1, 2, 3};  // T indices, most work first
+  int blocks_T[lpf::kBatchTs] = {0, 0, 0, 0};
+  cudaStream_t aux[lpf::kBatchTs - 1] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[lpf::kBatchTs - 1] = {nullptr, nullptr, nullptr};
   // The batch's own copies of the programs (one per handle and row stride):
   // evaluating a handle on its own afterwards (another launch shape) re-bakes
   // the handle's program and must not move the batch's.
@@ -228,7 +280,6 @@ struct lpf_batch {
   std::vector<lpf::Baked> baked;
   int desc_cap = 0;
   uint32_t max_band = 0;
-  int blocks = 0;
   int max_pack = 0, max_full = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -249,7 +300,7 @@ static int best_T(int H, int W) {
 
 static bool admissible(int W, int T) {
   const int G = ((W + 31) / 32 + T - 1) / T;
-  return G <= kBatchWarps && kBatchWarps % G == 0;
+  return (T == 1 || T == 2 || T == 4 || T == 8) && G <= kBatchWarps;
 }
 
 static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t* H, const int32_t* W,
@@ -288,15 +339,8 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
       if (T <= 0 || !admissible(Ws, T)) return LPF_EUNSUPPORTED;
       const int G = ((Ws + 31) / 32 + T - 1) / T;
       Geometry g;
-      // keep G*BB = 8 even if the side has fewer bands (the extra warps idle)
-      rc = layout_side(Hs, Ws, rxs, rys, T, kBatchWarps / G, g, up);
+      rc = layout_side(Hs, Ws, rxs, rys, T, band_group_bands((Hs + 31) / 32, G), g, up);
       if (rc) return rc;
-      g.BB = kBatchWarps / G;
-      g.nbg = (g.nbands + g.BB - 1) / g.BB;
-      g.rows = 32 * g.BB * g.nbg + g.ry + up;
-      const size_t band = (size_t)(32 * g.BB + g.ry + up) * g.S * 4;
-      g.band_bytes = (uint32_t)((band + 15) & ~size_t(15));
-      g.packed_words = (size_t)g.rows * g.S + 4;
       size_t k = 0;  // this handle's copy of this side's program for this row stride, else a new slot
       while (k < bt->baked.size() &&
              !(bt->baked_for[k] == p && bt->baked_side[k] == side && bt->baked[k].S == g.S)) ++k;
@@ -371,35 +415,52 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaFuncAttributes fa;
-  if ((e = cudaFuncGetAttributes(&fa, batch_walk_kernel)) != cudaSuccess) return set_cuda_error(e);
-  const int max_dyn = optin - (int)fa.sharedSizeBytes;
-  if ((int)bt->max_band > max_dyn) return LPF_EUNSUPPORTED;
-  if ((e = cudaFuncSetAttribute(batch_walk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn)) != cudaSuccess)
-    return set_cuda_error(e);
-  int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_walk_kernel, kBatchThreads, bt->max_band)) !=
-      cudaSuccess)
-    return set_cuda_error(e);
-  const int resident = std::max(1, per_sm) * sms;
-  // Slots: every band group at least one, more in proportion to its work
-  // (about kSlotsPerBlock slots per resident block in all), heaviest band groups first.
+  // each T's walk kernel: its shared-memory limit and resident blocks
+  int resident_T[kBatchTs];
+  for (int k = 0; k < kBatchTs; ++k) {
+    const void* fn = batch_walk_fn(k);
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return set_cuda_error(e);
+    const int max_dyn = optin - (int)fa.sharedSizeBytes;
+    if ((int)bt->max_band > max_dyn) return LPF_EUNSUPPORTED;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn)) != cudaSuccess)
+      return set_cuda_error(e);
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, bt->max_band)) != cudaSuccess)
+      return set_cuda_error(e);
+    resident_T[k] = std::max(1, per_sm) * sms;
+  }
+  // Slots, per T: every band group at least one, more in proportion to its
+  // work (about kSlotsPerBlock slots per resident block over the whole
+  // batch), heaviest band groups first, then the sweep: every band group once
+  // more, heaviest first.  The kernels run most work first.
   {
     std::vector<int> order(n_desc);
     for (int i = 0; i < n_desc; ++i) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return bg_work[a] > bg_work[b]; });
-    double total = 0;
-    for (int i = 0; i < n_desc; ++i) total += bg_work[i] * bt->desc[i].nbg;
-    const double per_slot = total / (kSlotsPerBlock * resident);
+    double total = 0, work_T[kBatchTs] = {0, 0, 0, 0};
+    for (int i = 0; i < n_desc; ++i) {
+      total += bg_work[i] * bt->desc[i].nbg;
+      work_T[t_index(bt->desc[i].T)] += bg_work[i] * bt->desc[i].nbg;
+    }
+    const double per_slot = total / (kSlotsPerBlock * resident_T[0]);
+    for (int k = 0; k < kBatchTs; ++k) bt->run_order[k] = k;
+    std::stable_sort(bt->run_order, bt->run_order + kBatchTs, [&](int a, int b) { return work_T[a] > work_T[b]; });
     std::vector<BatchSlot> slots;
-    for (int i : order)
-      for (int bg = 0; bg < bt->desc[i].nbg; ++bg) {
-        const int n = std::max(1, (int)std::lround(bg_work[i] / per_slot));
-        for (int c = 0; c < n; ++c) slots.push_back({i, bg, bt->desc[i].bg0 + bg});
-      }
-    // the sweep: every band group once more, heaviest first
-    for (int i : order)
-      for (int bg = 0; bg < bt->desc[i].nbg; ++bg) slots.push_back({i, bg, bt->desc[i].bg0 + bg});
+    for (int k = 0; k < kBatchTs; ++k) {
+      bt->slot_off[k] = (int)slots.size();
+      for (int i : order)
+        if (t_index(bt->desc[i].T) == k)
+          for (int bg = 0; bg < bt->desc[i].nbg; ++bg) {
+            const int n = std::max(1, (int)std::lround(bg_work[i] / per_slot));
+            for (int c = 0; c < n; ++c) slots.push_back({i, bg, bt->desc[i].bg0 + bg});
+          }
+      for (int i : order)
+        if (t_index(bt->desc[i].T) == k)
+          for (int bg = 0; bg < bt->desc[i].nbg; ++bg) slots.push_back({i, bg, bt->desc[i].bg0 + bg});
+      bt->blocks_T[k] = std::min(resident_T[k], (int)slots.size() - bt->slot_off[k]);
+    }
+    bt->slot_off[kBatchTs] = (int)slots.size();
     bt->n_slots = (int)slots.size();
     if (bt->d_slots) { cudaFree(bt->d_slots); bt->d_slots = nullptr; }
     if ((e = cudaMalloc(&bt->d_slots, sizeof(BatchSlot) * slots.size())) != cudaSuccess) return set_cuda_error(e);
@@ -407,7 +468,15 @@ static int batch_build(lpf_batch* bt, const uint8_t* const* imgs, const int32_t*
         cudaSuccess)
       return set_cuda_error(e);
   }
-  bt->blocks = std::min(resident, bt->n_slots);
+  // the batch's streams and events for the walks after the first
+  for (int k = 0; k < kBatchTs - 1; ++k) {
+    if (!bt->aux[k] && (e = cudaStreamCreateWithFlags(&bt->aux[k], cudaStreamNonBlocking)) != cudaSuccess)
+      return set_cuda_error(e);
+    if (!bt->ev_join[k] && (e = cudaEventCreateWithFlags(&bt->ev_join[k], cudaEventDisableTiming)) != cudaSuccess)
+      return set_cuda_error(e);
+  }
+  if (!bt->ev_fork && (e = cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming)) != cudaSuccess)
+    return set_cuda_error(e);
   if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
   if (bt->graph) { cudaGraphDestroy(bt->graph); bt->graph = nullptr; }
   return LPF_OK;
@@ -419,8 +488,29 @@ static void batch_enqueue(lpf_batch* bt, cudaStream_t s) {
   cudaMemsetAsync(bt->d_exec, 0, sizeof(unsigned long long) * n_desc, s);
   batch_zero_kernel<<<dim3(bt->max_full, n_desc), 256, 0, s>>>(bt->d_desc);
   batch_pack_kernel<<<dim3(bt->max_pack, n_desc), 256, 0, s>>>(bt->d_desc);
-  batch_walk_kernel<<<bt->blocks, kBatchThreads, bt->max_band, s>>>(bt->d_desc, bt->d_slots, bt->n_slots, bt->d_ctl,
-                                                                    bt->d_exec);
+  // one walk kernel per T present, the one with the most work on the
+  // caller's stream, the others on the batch's streams (their blocks take
+  // the SMs the first one's blocks leave at its end); joined before the mirror
+  int present = 0;
+  for (int k = 0; k < kBatchTs; ++k) present += bt->slot_off[k + 1] > bt->slot_off[k];
+  if (present > 1) cudaEventRecord(bt->ev_fork, s);
+  int n_fork = 0;
+  bool first = true;
+  for (int r = 0; r < kBatchTs; ++r) {
+    const int k = bt->run_order[r];
+    const int n = bt->slot_off[k + 1] - bt->slot_off[k];
+    if (n == 0) continue;
+    cudaStream_t ks = s;
+    if (!first) {
+      ks = bt->aux[n_fork];
+      cudaStreamWaitEvent(ks, bt->ev_fork, 0);
+    }
+    batch_walk_launch(k, bt->blocks_T[k], bt->max_band, ks, bt->d_desc, bt->d_slots + bt->slot_off[k], n,
+                      bt->d_ctl, kBatchCtlSlot + k, bt->d_exec);
+    if (!first) cudaEventRecord(bt->ev_join[n_fork++], ks);
+    first = false;
+  }
+  for (int f = 0; f < n_fork; ++f) cudaStreamWaitEvent(s, bt->ev_join[f], 0);
   batch_mirror_kernel<<<dim3(bt->max_full, n_desc), 256, 0, s>>>(bt->d_desc);
 }
 
@@ -541,8 +631,7 @@ int lpf_batch_autotune(lpf_batch* bt, const uint8_t* const* imgs_dev, const int3
     if (!present) continue;
     int bestT = -1;
     for (int t : {1, 2, 4, 8}) {
-      const int G = (nw + t - 1) / t;
-      if (G > lpf::kBatchWarps || lpf::kBatchWarps % G) continue;
+      if ((nw + t - 1) / t > lpf::kBatchWarps) continue;
       std::vector<int32_t> keep = T;
       for (int i = 0; i < bt->n; ++i)
         if ((W[i] + 31) / 32 == nw) T[i] = t;
@@ -576,6 +665,11 @@ void lpf_batch_free(lpf_batch* bt) {
     cudaFree(b.d_words);
     cudaFree(b.d_piece);
   }
+  for (int k = 0; k < lpf::kBatchTs - 1; ++k) {
+    if (bt->aux[k]) cudaStreamDestroy(bt->aux[k]);
+    if (bt->ev_join[k]) cudaEventDestroy(bt->ev_join[k]);
+  }
+  if (bt->ev_fork) cudaEventDestroy(bt->ev_fork);
   delete bt;
 }
 

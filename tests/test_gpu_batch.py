@@ -49,12 +49,14 @@ def test_batch_every_words_per_thread_choice(gpu_lib):
     paths = [gpu_lib.lpf_build_paths(W // 2, H // 2) for H, W in (i.shape for i in imgs)]
     d = [torch.from_numpy(i).cuda() for i in imgs]
     refs = [oracle.lpf_full(img, p.rx, p.ry) for img, p in zip(imgs, paths)]
+    # (word-group counts G = ceil(words / T) of 1 to 4, including 3, which does
+    # not divide a block's 8 warps; bands per group from 1 to 4)
     for T in (1, 2, 4, 8):
         choice = []
         for img in imgs:
             nw = (img.shape[1] + 31) // 32
             G = (nw + T - 1) // T
-            choice.append(T if 8 % G == 0 else 8)
+            choice.append(T if G <= 8 else 8)
         b = gpu_lib.lpf_batch_create(d, paths, words_per_thread=choice)
         counts = gpu_lib.lpf_batch_run(b, use_graph=False)
         for c, r in zip(counts, refs):
