@@ -6,7 +6,8 @@ device, is forbidden).  Its work area is a fixed array inside the library.
 Called through the C ABI with ctypes; each of two calls in a row must give
 exactly the counts of lpf_full (integer counts: bit-exact), on different
 images so that the shared fixed array cannot carry a stale result over.
-This file is collected last on purpose.
+Every test does its own set-up (an lpf_full call for its image size), so the
+tests do not depend on the order in which files are collected.
 """
 import ctypes
 
@@ -107,3 +108,29 @@ def test_noalloc_equals_the_oracle_and_reports_a_timeout(gpu_lib):
     assert _call(lib, d, paths, out) == 0
     assert gpu_lib.lpf_paths_status(paths) == 0
     np.testing.assert_array_equal(out.cpu().numpy(), oracle.lpf_full(img, 30, 20))
+
+
+def test_noalloc_captured_in_a_graph_and_replayed(gpu_lib):
+    # A stream capture in global mode fails on any call that allocates device
+    # memory or synchronises, so a successful capture shows the call does
+    # neither.  The graph is then replayed on two images copied into its
+    # input, each replay's counts equal to lpf_full's.
+    lib = gpu_lib.load()
+    imgs = [synth.ellipses(200, 184, 0.35, seed=31), synth.clustered_disks(200, 184, 0.3, seed=32)]
+    paths = gpu_lib.lpf_build_paths(60, 50)
+    refs = [gpu_lib.lpf_full(torch.from_numpy(i).cuda(), paths) for i in imgs]  # set-up
+    inp = torch.from_numpy(imgs[0]).cuda()
+    out = torch.full((2, paths.n_full), -1, dtype=torch.int64, device="cuda")
+    assert _call(lib, inp, paths, out) == 0  # the first call on the device, outside any capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="global"):
+        rc = _call(lib, inp, paths, out)
+    assert rc == 0
+    for img, ref in zip(imgs[::-1], refs[::-1]):
+        inp.copy_(torch.from_numpy(img).cuda())
+        out.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    assert gpu_lib.lpf_paths_status(paths) == 0
