@@ -380,7 +380,7 @@ int lpf_build_paths_3d(int32_t rx, int32_t ry, int32_t rz, lpf_paths **out);
 int lpf_full_3d(const uint8_t *vol_dev, int32_t D, int32_t H, int32_t W, lpf_paths *paths,
                 int64_t *counts_dev, lpf_stream_t stream);
 
-/* ---- Many independent images in one persistent launch ---- */
+/* ---- Many independent images in one run of persistent walk kernels ---- */
 
 typedef struct lpf_batch lpf_batch; /* opaque, owned by the library */
 
