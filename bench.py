@@ -263,17 +263,26 @@ def extra_batch(lpf):
                                        "time of the whole graph (zero, pack, walk, mirror)"}}
 
 
+def _volume_128():
+    """A periodic 128^3 volume of overlapping balls (radius 5, phase-1
+    fraction about 0.3) on the device, and the window radius 16."""
+    import torch
+
+    import synth
+    D = H = W = 128
+    R = 5.0
+    n = int(round(-math.log(1.0 - 0.3) * D * H * W / (4.0 / 3.0 * math.pi * R ** 3)))
+    return torch.from_numpy(synth.boolean_spheres(D, H, W, R, n, seed=7)).cuda(), 16
+
+
 def extra_3d(lpf, reps: int = 5):
     """The 3D extension: the full lineal path function of both phases of a
     periodic 128^3 volume of overlapping balls (radius 5, fraction about
     0.3), every vector |dx|, |dy|, |dz| <= 16."""
     import torch
 
-    import synth
     D = H = W = 128
-    R, r = 5.0, 16
-    n = int(round(-math.log(1.0 - 0.3) * D * H * W / (4.0 / 3.0 * math.pi * R ** 3)))
-    vol = torch.from_numpy(synth.boolean_spheres(D, H, W, R, n, seed=7)).cuda()
+    vol, r = _volume_128()
     p = lpf.lpf_build_paths_3d(r, r, r)
     c = lpf.lpf_full_3d(vol, p)
     lpf.lpf_full_3d(vol, p, c)
@@ -287,8 +296,23 @@ def extra_3d(lpf, reps: int = 5):
     ms = a.elapsed_time(b) / reps
     assert lpf.lpf_paths_status(p) == 0
     tests = 2 * D * H * W * p.n_full
+    # the walked work, counted as for lpf_full's roofline: 2 ALU ops per
+    # (prefix-tree node, 32-translation word) walked; one side (every vector)
+    # over D*H rows of ceil(W/32) words
+    executed, nominal = lpf.lpf_paths_work(p)
+    words = D * H * ((W + 31) // 32)
+    ops = 2.0 * lpf.lpf_paths_stats(p)["n_tree_nodes"] * words * (executed / nominal if nominal else 1.0)
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    peak = torch.cuda.get_device_properties(0).multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6
+    achieved = ops / (ms / 1000.0)
     return {"workload": "lpf_full_3d 128^3 balls R=5 f~0.3, |dx|,|dy|,|dz|<=16, both phases",
-            "ms_per_call": ms, "tests_per_s": tests / (ms / 1000.0), "phase1_fraction": float(vol.float().mean())}
+            "ms_per_call": ms, "tests_per_s": tests / (ms / 1000.0), "phase1_fraction": float(vol.float().mean()),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "ALU op/s",
+                         "frac": achieved / peak, "kernel_ms": ms,
+                         "walked_share": executed / nominal if nominal else 1.0,
+                         "work_basis": "2 ops x prefix-tree nodes x translation words x walked share; "
+                                       "time of the whole call (pack, walk, mirror)"}}
 
 
 def extra_s2(lpf, reps: int = 20):
@@ -506,6 +530,18 @@ def _only_s2(lpf, repeat, shape):
     torch.cuda.synchronize()
 
 
+def _only_3d_128(lpf, repeat, shape):
+    """lpf_full_3d of the 128^3 ball volume, every vector |dx|, |dy|, |dz| <= 16."""
+    import torch
+    vol, r = _volume_128()
+    p = lpf.lpf_build_paths_3d(r, r, r)
+    c = lpf.lpf_full_3d(vol, p)
+    for _ in range(repeat):
+        lpf.lpf_full_3d(vol, p, c)
+    torch.cuda.synchronize()
+    assert lpf.lpf_paths_status(p) == 0
+
+
 def _only_cnn_train(lpf, repeat, shape):
     import numpy as np
     import torch
@@ -530,6 +566,7 @@ PROFILE_WORKLOADS = {
     "sa_128": _only_sa_128,
     "batch_256": _only_batch_256,
     "s2": _only_s2,
+    "3d_128": _only_3d_128,
 }
 
 

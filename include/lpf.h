@@ -120,9 +120,10 @@ int lpf_paths_stats(const lpf_paths *paths, int64_t *n_tree_nodes, int32_t *stac
                     int32_t *n_pieces);
 
 /*
- * Work of the last lpf_full, lpf_full_standard, lpf_full_mc or
- * lpf_full_ensemble evaluation enqueued with this handle (for an ensemble:
- * its last cut; not the allocation-free variant), counted in pixel words
+ * Work of the last lpf_full, lpf_full_standard, lpf_full_mc,
+ * lpf_full_ensemble or lpf_full_3d evaluation enqueued with this handle (for
+ * an ensemble: its last cut; not the allocation-free variant), counted in
+ * pixel (voxel) words
  * ANDed by a warp (one word for each of the warp's 32 translation rows x T
  * words), summed over warps:
  *   executed  what the warps did, after skipping the subtrees of the

@@ -714,7 +714,10 @@ static int run_full3(const uint8_t* vol, int D, int H, int W, lpf_paths* p, int6
   sd.packed_words = g.packed_words;
   sd.band_bytes = g.band_bytes;
   sd.nbg = g.nbg;
-  sd.threads = 32 * std::min(16, g.G * g.BB);
+  // 16 warps per block whatever the band group's tile count: warps pull
+  // units of any tile of the staged band group, and a volume's band group
+  // (its slices with their rz halo) is large, so few blocks fit on an SM
+  sd.threads = 512;
   if ((int)g.band_bytes > g_max_dyn_smem) return LPF_EUNSUPPORTED;
   rc = ensure_device(p, g.packed_words);
   if (rc) return rc;

@@ -28,6 +28,10 @@ def test_full_3d_matches_oracle(gpu_lib, name, shape, window, R, n):
     got = gpu_lib.lpf_full_3d(torch.from_numpy(vol).cuda(), p)
     assert gpu_lib.lpf_paths_status(p) == 0
     np.testing.assert_array_equal(got.cpu().numpy(), oracle.lpf_full3(vol, rx, ry, rz))
+    # the walk's work counters cover the volume walk too: some of the program
+    # walked, at most all of it
+    executed, nominal = gpu_lib.lpf_paths_work(p)
+    assert 0 < executed <= nominal
 
 
 def test_full_3d_launch_shapes_and_sampled_large_volume(gpu_lib):
