@@ -629,7 +629,6 @@ int lpf_batch_autotune(lpf_batch* bt, const uint8_t* const* imgs_dev, const int3
     bool present = false;
     for (int i = 0; i < bt->n; ++i) present |= ((W[i] + 31) / 32 == nw);
     if (!present) continue;
-    int bestT = -1;
     for (int t : {1, 2, 4, 8}) {
       if ((nw + t - 1) / t > lpf::kBatchWarps) continue;
       std::vector<int32_t> keep = T;
@@ -638,10 +637,9 @@ int lpf_batch_autotune(lpf_batch* bt, const uint8_t* const* imgs_dev, const int3
       float ms = 0;
       rc = time_it(ms);
       if (rc) break;
-      if (ms < cur) { cur = ms; bestT = t; }
+      if (ms < cur) cur = ms;
       else T = keep;
     }
-    (void)bestT;
   }
   if (!rc) rc = lpf::batch_build(bt, imgs_dev, H, W, counts_dev, T.data());
   cudaEventDestroy(e0);
