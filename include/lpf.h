@@ -413,7 +413,8 @@ int lpf_batch_create(int32_t n_img, const uint8_t *const *imgs_dev, const int32_
  * the kernels after the first run on the batch's own streams, forked from
  * `stream` and joined back before the next step), mirror; no host-device
  * copies.  use_graph != 0 captures those launches as a CUDA graph on the
- * first call and replays it.
+ * first call and replays it.  Runs of one batch share its work area, counters
+ * and streams: order them (one stream, or events between streams).
  * Errors: LPF_EINVAL, LPF_ECUDA.
  */
 int lpf_batch_run(lpf_batch *batch, int32_t use_graph, lpf_stream_t stream);
