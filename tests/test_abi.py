@@ -90,3 +90,29 @@ def test_newer_entry_points_reject_bad_arguments_on_host():
     assert lpf.lpf_strerror(-6).startswith("pixel value")
     bad = lpf.SaParams(100, 10, 1, 1e-3, 0.01, 64, 1, 1, 7)   # phases outside {0..3}
     assert lib.lpf_sa_create(v, 8, 8, p.handle, v, v, ctypes.byref(bad), None, ctypes.byref(h)) == -1
+
+
+def test_readme_c_example_compiles_and_links(tmp_path):
+    # The C example of the README, compiled against include/lpf.h and linked
+    # with the built library and the CUDA runtime (not run: no GPU needed).
+    import shutil
+    import subprocess
+    gcc, nvcc = shutil.which("gcc"), shutil.which("nvcc")
+    if gcc is None or nvcc is None:
+        pytest.skip("gcc or the CUDA toolkit not available")
+    cuda = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    cudart = [d for d in ("lib64", "lib", "targets/x86_64-linux/lib", "targets/sbsa-linux/lib")
+              if os.path.exists(os.path.join(cuda, d, "libcudart.so"))]
+    if not cudart:
+        pytest.skip("libcudart.so not found")
+    readme = open(os.path.join(ROOT, "README.md")).read()
+    blocks = re.findall(r"```c\n(.*?)```", readme, flags=re.S)
+    assert len(blocks) == 1
+    src = tmp_path / "example.c"
+    src.write_text(blocks[0])
+    libdir = os.path.dirname(lpf.load()._name)
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", str(src), "-o", str(tmp_path / "example"),
+                        "-I", os.path.join(ROOT, "include"), "-I", os.path.join(cuda, "include"),
+                        "-L", libdir, "-llpf", "-L", os.path.join(cuda, cudart[0]), "-lcudart"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
